@@ -1,0 +1,277 @@
+"""Plain FP64 CPU oracle of the 2D implicit-FDTD PIC particle cycle.
+
+TEST INFRASTRUCTURE: only ``tests/``, ``__graft_entry__.smoke()`` and ``bench.py``'s
+CPU-baseline leg may import this package. The CUDA product never imports, links or
+calls it, and shares no code with it.
+
+The arithmetic lives in ``oracle.c`` (plain C, single-threaded, FP64); this module
+compiles it with gcc, loads it with ctypes and sequences one time step the way the
+paper orders it (Ikeya & Matsumoto, PASJ 2015, Sec. 2 and Sec. 3): gather and push with
+E^n, B^n; deposit J^{n+1/2}; right-hand side and CG solve of Eq. (7); field update from
+Eqs. (5)-(6).
+
+Parity pins (tests/test_oracle_*.py) tie every function to something other than
+itself: the paper's dispersion relation Eqs. (10) and (15), discrete charge
+conservation, exact Boris gyration, a spectral solve of Eq. (7), scipy's B-splines
+and closed-form current sums.
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+import subprocess
+import threading
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+_SRC = os.path.join(_HERE, "oracle.c")
+_HDR = os.path.join(_HERE, "oracle.h")
+_LIB = os.path.join(_HERE, "liboracle.so")
+_lock = threading.Lock()
+_lib = None
+
+
+def build(force: bool = False) -> str:
+    """Compile oracle.c into liboracle.so (plain gcc, -O2, no fast-math)."""
+    newest_src = max(os.path.getmtime(_SRC), os.path.getmtime(_HDR))
+    if not force and os.path.exists(_LIB) and os.path.getmtime(_LIB) >= newest_src:
+        return _LIB
+    tmp = _LIB + f".tmp{os.getpid()}"
+    cmd = ["gcc", "-O2", "-std=c11", "-fPIC", "-shared", "-fno-fast-math",
+           "-ffp-contract=off", "-o", tmp, _SRC, "-lm"]
+    subprocess.run(cmd, check=True)
+    os.replace(tmp, _LIB)
+    return _LIB
+
+
+class Grid(C.Structure):
+    _fields_ = [("nx", C.c_int32), ("ny", C.c_int32), ("dx", C.c_double),
+                ("dy", C.c_double), ("dt", C.c_double), ("theta", C.c_double),
+                ("order", C.c_int32)]
+
+
+_P = np.ctypeslib.ndpointer(dtype=np.float64, flags="C_CONTIGUOUS")
+
+
+def lib():
+    global _lib
+    with _lock:
+        if _lib is None:
+            L = C.CDLL(build())
+            G = C.POINTER(Grid)
+            L.or_shape.restype = C.c_double
+            L.or_shape.argtypes = [C.c_int32, C.c_double]
+            L.or_gather.argtypes = [G, _P, C.c_int64, _P, _P, _P]
+            L.or_boris.argtypes = [C.c_double, C.c_double, C.c_int64, _P, _P, _P]
+            L.or_deposit_move.argtypes = [G, C.c_double, C.c_double, C.c_double, C.c_double,
+                                          C.c_double, C.c_double, _P]
+            L.or_push_deposit.restype = C.c_int64
+            L.or_push_deposit.argtypes = [G, _P, C.c_double, C.c_double, C.c_int64, _P, _P, _P,
+                                          _P, _P, _P, C.c_int32]
+            L.or_deposit_rho.argtypes = [G, C.c_double, C.c_int64, _P, _P, _P]
+            L.or_rhs.argtypes = [G, _P, _P, _P]
+            L.or_apply_A.argtypes = [G, _P, _P]
+            L.or_pcg.restype = C.c_int32
+            L.or_pcg.argtypes = [G, _P, _P, C.c_double, C.c_int32, C.POINTER(C.c_double)]
+            L.or_field_update.argtypes = [G, _P, _P, _P]
+            for name in ("or_div_E", "or_div_B", "or_div_J"):
+                getattr(L, name).argtypes = [G, _P, _P]
+            L.or_field_energy.argtypes = [G, _P, C.POINTER(C.c_double), C.POINTER(C.c_double)]
+            _lib = L
+    return _lib
+
+
+def grid(nx, ny, dt, theta, order, dx=1.0, dy=1.0) -> Grid:
+    if nx < 8 or ny < 8:
+        raise ValueError("the oracle needs nx, ny >= 8")
+    return Grid(int(nx), int(ny), float(dx), float(dy), float(dt), float(theta), int(order))
+
+
+def _c(a):
+    return np.ascontiguousarray(a, dtype=np.float64)
+
+
+# ---- thin wrappers (one call = one C function) ----------------------------------
+
+def shape(p, d):
+    L = lib()
+    return np.array([L.or_shape(int(p), float(v)) for v in np.ravel(d)]).reshape(np.shape(d))
+
+
+def gather(g, F, x, y):
+    x, y = _c(x), _c(y)
+    out = np.zeros(6 * x.size)
+    lib().or_gather(C.byref(g), _c(F).ravel(), x.size, x, y, out)
+    return out.reshape(6, x.size)
+
+
+def boris(qm, dt, E, B, u):
+    """E, B, u: arrays of shape (n, 3). Returns the pushed momenta (n, 3)."""
+    u = _c(u).copy()
+    lib().or_boris(float(qm), float(dt), u.shape[0], _c(E).ravel(), _c(B).ravel(), u.ravel())
+    return u
+
+
+def deposit_move(g, qw, x0, y0, x1, y1, vz, J=None):
+    if J is None:
+        J = np.zeros(3 * g.nx * g.ny)
+    lib().or_deposit_move(C.byref(g), qw, x0, y0, x1, y1, vz, J)
+    return J
+
+
+def push_deposit(g, F, qm, qw, x, y, ux, uy, uz, J=None, deposit=True):
+    """One species' gather, push, move, deposit and wrap. Updates x..uz in place
+    (they must be float64 C-contiguous) and returns (J, number of bad moves)."""
+    if J is None:
+        J = np.zeros(3 * g.nx * g.ny)
+    for a in (x, y, ux, uy, uz):
+        if a.dtype != np.float64 or not a.flags.c_contiguous:
+            raise TypeError("particle arrays must be C-contiguous float64")
+    bad = lib().or_push_deposit(C.byref(g), _c(F).ravel(), float(qm), float(qw), x.size, x, y,
+                                ux, uy, uz, J, 1 if deposit else 0)
+    return J, int(bad)
+
+
+def deposit_rho(g, qw, x, y, rho=None):
+    x, y = _c(x), _c(y)
+    if rho is None:
+        rho = np.zeros(g.nx * g.ny)
+    lib().or_deposit_rho(C.byref(g), float(qw), x.size, x, y, rho)
+    return rho
+
+
+def rhs(g, F, J):
+    b = np.zeros(3 * g.nx * g.ny)
+    lib().or_rhs(C.byref(g), _c(F).ravel(), _c(J).ravel(), b)
+    return b
+
+
+def apply_A(g, x):
+    out = np.zeros(3 * g.nx * g.ny)
+    lib().or_apply_A(C.byref(g), _c(x).ravel(), out)
+    return out
+
+
+def pcg(g, b, x0=None, rtol=1e-10, maxit=1000):
+    x = np.zeros(3 * g.nx * g.ny) if x0 is None else _c(x0).ravel().copy()
+    rr = C.c_double(0.0)
+    it = lib().or_pcg(C.byref(g), _c(b).ravel(), x, float(rtol), int(maxit), C.byref(rr))
+    return x, int(it), rr.value
+
+
+def field_update(g, F, dB, J):
+    F = _c(F).ravel().copy()
+    lib().or_field_update(C.byref(g), F, _c(dB).ravel(), _c(J).ravel())
+    return F
+
+
+def div_E(g, F):
+    out = np.zeros(g.nx * g.ny)
+    lib().or_div_E(C.byref(g), _c(F).ravel(), out)
+    return out
+
+
+def div_B(g, F):
+    out = np.zeros(g.nx * g.ny)
+    lib().or_div_B(C.byref(g), _c(F).ravel(), out)
+    return out
+
+
+def div_J(g, J):
+    out = np.zeros(g.nx * g.ny)
+    lib().or_div_J(C.byref(g), _c(J).ravel(), out)
+    return out
+
+
+def field_energy(g, F):
+    ue, ub = C.c_double(), C.c_double()
+    lib().or_field_energy(C.byref(g), _c(F).ravel(), C.byref(ue), C.byref(ub))
+    return ue.value, ub.value
+
+
+# ---- one whole step --------------------------------------------------------------
+
+class Species:
+    """One particle species: charge-to-mass sign qm = +-1, macro weight w (charge
+    per macro-particle q = qm*w, mass w), physical positions and momenta u = gamma v."""
+
+    def __init__(self, qm, w, x, y, ux, uy, uz):
+        self.qm, self.w = float(qm), float(w)
+        self.x, self.y = _c(x).copy(), _c(y).copy()
+        self.ux, self.uy, self.uz = _c(ux).copy(), _c(uy).copy(), _c(uz).copy()
+
+    @property
+    def n(self):
+        return self.x.size
+
+    def kinetic_energy(self):
+        return self.w * float(np.sum(np.sqrt(1.0 + self.ux**2 + self.uy**2 + self.uz**2) - 1.0))
+
+
+class OracleSim:
+    """The per-step particle cycle, in the paper's order (Sec. 2, Sec. 3):
+
+    1. every species: gather E^n, B^n at x^n; Boris push u^{n-1/2} -> u^{n+1/2};
+       move; Esirkepov deposit of J^{n+1/2}; periodic wrap;
+    2. right-hand side b of Eq. (7) from B^n, E^n, J^{n+1/2};
+    3. PCG solve of [1 - (theta c dt)^2 Lap] dB = b from the initial guess
+       (zero, or the previous step's dB when warm_start == "prev");
+    4. E^{n+1}, B^{n+1} from Eqs. (5)-(6).
+    """
+
+    def __init__(self, nx, ny, cfl, theta, order, species, dx=1.0, dy=1.0,
+                 cg_rtol=1e-10, cg_max_iter=1000, warm_start="zero", fields=None,
+                 deposit=True):
+        self.g = grid(nx, ny, cfl * dx, theta, order, dx, dy)
+        self.N = nx * ny
+        self.species = list(species)
+        self.F = np.zeros(6 * self.N) if fields is None else _c(fields).ravel().copy()
+        self.J = np.zeros(3 * self.N)
+        self.dB = np.zeros(3 * self.N)
+        self.cg_rtol, self.cg_max_iter = float(cg_rtol), int(cg_max_iter)
+        self.warm_start = warm_start
+        self.deposit = bool(deposit)
+        self.step_count = 0
+        self.last_cg_iters = 0
+        self.last_cg_resid = 0.0
+        self.bad_moves = 0
+
+    def push_deposit(self):
+        L = lib()
+        self.J[:] = 0.0
+        for s in self.species:
+            self.bad_moves += int(L.or_push_deposit(
+                C.byref(self.g), self.F, s.qm, s.qm * s.w, s.n, s.x, s.y, s.ux, s.uy,
+                s.uz, self.J, 1 if self.deposit else 0))
+
+    def field_solve(self):
+        b = rhs(self.g, self.F, self.J)
+        x0 = self.dB if self.warm_start == "prev" else None
+        dB, it, rr = pcg(self.g, b, x0, self.cg_rtol, self.cg_max_iter)
+        if it < 0:
+            raise RuntimeError(f"oracle PCG did not converge in {self.cg_max_iter} iterations")
+        self.dB = dB
+        self.last_cg_iters, self.last_cg_resid = it, rr
+        self.F = field_update(self.g, self.F, dB, self.J)
+
+    def step(self, n=1):
+        for _ in range(int(n)):
+            self.push_deposit()
+            self.field_solve()
+            self.step_count += 1
+
+    # diagnostics
+    def fields(self):
+        return self.F.reshape(6, self.g.ny, self.g.nx)
+
+    def energies(self):
+        ue, ub = field_energy(self.g, self.F)
+        return ue, ub, sum(s.kinetic_energy() for s in self.species)
+
+    def rho(self):
+        r = np.zeros(self.N)
+        for s in self.species:
+            deposit_rho(self.g, s.qm * s.w, s.x, s.y, r)
+        return r
+
