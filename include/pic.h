@@ -1,0 +1,183 @@
+/*
+ * pic.h -- C ABI of the GB300 implicit-FDTD particle-in-cell library.
+ *
+ * The library advances 2D electromagnetic PIC simulations of relativistic pair
+ * plasmas with the particle cycle of Ikeya & Matsumoto, "Stability Property of
+ * Numerical Cherenkov Radiation and its Application to Relativistic Shock
+ * Simulations" (PASJ 2015, arXiv:1412.2480):
+ *   - momentum-conserving field gather (Sec. 1, Sec. 3) at shape order 1, 2 or 3;
+ *   - relativistic Buneman-Boris push (the paper gives no pusher; standard scheme);
+ *   - density-decomposition (Esirkepov) charge-conserving current deposit (Sec. 1, 3);
+ *   - implicit theta-FDTD Maxwell update, Eqs. (5)-(6), with the elliptic equation
+ *     Eq. (7) for dB = B^{n+1} - B^n solved by preconditioned conjugate gradient.
+ *
+ * Units: Gaussian, c = 1. Lengths in physical units with cell sizes dx, dy; the time
+ * step is dt = cfl * dx (CFL number sigma = c dt / dx, Sec. 3.1). Species 0 are
+ * positrons (q/m = +1), species 1 electrons (q/m = -1); each macro-particle carries
+ * charge +-w and mass w, with w fixed by the plasma frequency in the flow frame
+ * (Sec. 4): omega_pe^2 = 4 pi n q^2 / (m gamma0), n = ppc/(dx dy), omega_pe = 1/skin_depth.
+ *
+ * Grid storage (every grid quantity, nx*ny values, index k = j*nx + i) follows the
+ * 2D Yee arrangement (Sec. 2, Fig. 1): Ez, Jz, rho at (i, j); Ex, Jx, By at (i+1/2, j);
+ * Ey, Jy, Bx at (i, j+1/2); Bz at (i+1/2, j+1/2). Boundaries are periodic in x and y.
+ *
+ * Conventions for every call:
+ *   - return value PIC_OK (0) or a negative PIC_E* code; nothing aborts or exits;
+ *     pic_last_error() gives a message for the last failure on that handle;
+ *   - pointers passed in may be host or device memory (CUDA unified addressing
+ *     decides); the library copies and never keeps a caller pointer;
+ *   - the handle owns all device memory it allocates; pic_free releases it;
+ *   - a handle is not thread-safe; calls on one handle must not overlap.
+ */
+#ifndef PIC_H
+#define PIC_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#if defined(__GNUC__)
+#define PIC_API __attribute__((visibility("default")))
+#else
+#define PIC_API
+#endif
+
+/* ---- return codes ---- */
+#define PIC_OK 0
+#define PIC_EINVAL (-1)      /* invalid argument or parameter */
+#define PIC_ENOMEM (-2)      /* device or host allocation failed */
+#define PIC_ECUDA (-3)       /* a CUDA call failed (message has the CUDA error) */
+#define PIC_ECG_NOCONV (-4)  /* PCG reached cg_max_iter before cg_rtol */
+#define PIC_ECFL (-5)        /* a particle moved one cell or more in one step */
+#define PIC_ENAN (-6)        /* a non-finite particle momentum or position appeared */
+#define PIC_ESTATE (-8)      /* call not valid in the handle's current state */
+
+/* ---- precision of the particle half (the field solve is always FP64) ---- */
+#define PIC_FP64 0    /* positions, momenta, gather, push and deposit in FP64 */
+#define PIC_MIXED32 1 /* int cell + FP32 offset, FP32 momenta, FP32 gather/push/deposit */
+
+/* ---- initial guess of the PCG solve of Eq. (7) ---- */
+#define PIC_WS_ZERO 0 /* dB_0 = 0 */
+#define PIC_WS_PREV 1 /* dB_0 = the previous step's dB */
+
+/* ---- flags ---- */
+#define PIC_NO_DEPOSIT 1   /* test-particle mode: particles feel the fields, J = 0 */
+#define PIC_NO_GRAPH 2     /* launch kernels directly instead of a captured CUDA graph */
+
+/* ---- grid quantity ids for pic_fields / pic_set_fields ---- */
+#define PIC_EX 0
+#define PIC_EY 1
+#define PIC_EZ 2
+#define PIC_BX 3
+#define PIC_BY 4
+#define PIC_BZ 5
+#define PIC_JX 6 /* J^{n+1/2} of the last step */
+#define PIC_JY 7
+#define PIC_JZ 8
+#define PIC_DBX 9 /* dB of the last step's solve (x, y, z) */
+#define PIC_DBY 10
+#define PIC_DBZ 11
+
+typedef struct pic_params {
+    int32_t nx, ny;        /* cells (Sec. 3: 128 x 128; Sec. 4: 5650 x 990); >= 8 each */
+    double dx, dy;         /* cell size, default 1 */
+    double cfl;            /* CFL number sigma = c dt / dx (Sec. 3.1), 0 < cfl <= 1 */
+    double theta;          /* implicitness factor of Eqs. (5)-(6), 0.5 <= theta <= 1 */
+    int32_t shape_order;   /* particle shape order 1, 2 or 3 (Sec. 3.3) */
+    double gamma0;         /* drift Lorentz factor of the flow (Sec. 3) */
+    int32_t ppc;           /* macro-particles per cell per species (sets w and capacity) */
+    double skin_depth;     /* c / omega_pe in length units (Sec. 4 definition), default 10 */
+    int32_t precision;     /* PIC_FP64 or PIC_MIXED32 */
+    double cg_rtol;        /* stop when ||r||_2 <= cg_rtol ||b||_2, default 1e-10 */
+    int32_t cg_max_iter;   /* default 200 */
+    int32_t warm_start;    /* PIC_WS_ZERO or PIC_WS_PREV */
+    int32_t flags;         /* PIC_NO_DEPOSIT | PIC_NO_GRAPH */
+    int32_t tile_x, tile_y;/* MIXED32 tile size in cells; 0 = chosen by the library */
+    double bin_slack;      /* MIXED32 bin capacity factor over ppc * tile cells; 0 = 1.5 */
+} pic_params;
+
+typedef struct pic_moments_t {
+    int64_t step;            /* completed steps */
+    double time;             /* step * dt */
+    double U_E, U_B;         /* field energies sum |E|^2 dx dy / 8 pi, same for B (at step n) */
+    double U_K;              /* kinetic energy sum w (gamma - 1) with u^{n-1/2} of the last step */
+    double macro_weight;     /* w */
+    int64_t n_particles[2];  /* live macro-particles per species */
+    int32_t cg_iters_last;   /* PCG iterations of the last step */
+    int32_t cg_iters_max;    /* largest PCG iteration count since the last pic_moments */
+    int64_t cg_iters_total;  /* all PCG iterations so far */
+    double cg_rel_resid;     /* ||r|| / ||b|| at the end of the last solve */
+    int64_t cfl_violations;  /* moves of one cell or more seen so far (should stay 0) */
+    int64_t overflow_moves;  /* MIXED32: particles routed through the overflow path so far */
+    int64_t rebins;          /* MIXED32: full re-sorts performed so far */
+} pic_moments_t;
+
+typedef struct pic_sim pic_sim;
+
+/* Fill *p with the defaults above (64 x 64, dx = dy = 1, cfl 1, theta 0.5, order 1,
+ * gamma0 20, ppc 8, skin_depth 10, FP64, rtol 1e-10, 200 iterations, zero warm start). */
+PIC_API void pic_params_default(pic_params* p);
+
+/* Create one simulation on the current CUDA device. Validates *p (PIC_EINVAL with a
+ * message if out of range), allocates all device memory, zeroes the fields. The new
+ * handle is written to *out; the caller releases it with pic_free. On failure *out is
+ * NULL and the last-error message is available through pic_last_error(NULL). */
+PIC_API int pic_init(const pic_params* p, pic_sim** out);
+
+/* Run subsequent work of this handle on the given CUDA stream (cudaStream_t, passed as
+ * void*). NULL selects the handle's own non-blocking stream, which is also the default.
+ * The legacy default stream cannot be used (steps are captured into CUDA graphs).
+ * Waits for work already enqueued on the previous stream; drops the captured graph. */
+PIC_API int pic_set_stream(pic_sim* s, void* cuda_stream);
+
+/* Replace the particles of one species (0 = positrons, 1 = electrons) with n
+ * macro-particles: physical positions x in [0, nx dx), y in [0, ny dy) and momenta
+ * u = gamma v (units of c). Arrays are FP64, host or device; they are copied. Positions
+ * outside the box are wrapped periodically. MIXED32 converts to cell + FP32 offset and
+ * FP32 momenta and sorts into tiles. Returns PIC_EINVAL for bad species, n < 0, NULL
+ * arrays with n > 0, or non-finite values. */
+PIC_API int pic_load_particles(pic_sim* s, int32_t species, const double* x, const double* y,
+                       const double* ux, const double* uy, const double* uz, int64_t n);
+
+/* Overwrite one field component (PIC_EX..PIC_BZ) with nx*ny FP64 values (host or
+ * device). The caller keeps ownership of data. */
+PIC_API int pic_set_fields(pic_sim* s, int32_t which, const double* data, size_t len);
+
+/* Advance n >= 0 steps of the particle cycle (Sec. 2, Sec. 3): for each step, gather
+ * E^n, B^n; push; move; deposit J^{n+1/2}; solve Eq. (7) by PCG; update E, B by
+ * Eqs. (5)-(6). Work is enqueued on the handle's stream and the call returns after the
+ * stream has finished (one host synchronisation per call, not per step). Errors
+ * detected on the device (PIC_ECG_NOCONV, PIC_ECFL, PIC_ENAN) stop the remaining
+ * steps of the call; the fields and particles then hold the state after the failing
+ * step and pic_moments reports its step count. */
+PIC_API int pic_step(pic_sim* s, int32_t n);
+
+/* Copy grid quantity `which` (PIC_EX..PIC_DBZ) into out (len >= nx*ny FP64 values,
+ * host or device, caller-owned). */
+PIC_API int pic_fields(pic_sim* s, int32_t which, double* out, size_t len);
+
+/* Fill *out with diagnostics at the current step (energies, PCG statistics, counts). */
+PIC_API int pic_moments(pic_sim* s, pic_moments_t* out);
+
+/* Number of live macro-particles of a species. */
+PIC_API int64_t pic_particle_count(pic_sim* s, int32_t species);
+
+/* Copy the particles of a species into out: 5 arrays of n FP64 values laid out as
+ * [x(n), y(n), ux(n), uy(n), uz(n)] (host or device, caller-owned); n must equal
+ * pic_particle_count. FP64 mode keeps the load order; MIXED32 returns tile order. */
+PIC_API int pic_particles(pic_sim* s, int32_t species, double* out5xn, int64_t n);
+
+/* Message of the last failure on this handle (or of the last failed pic_init when s
+ * is NULL). The string stays valid until the next call on the handle. */
+PIC_API const char* pic_last_error(const pic_sim* s);
+
+/* Release the handle and all its device memory. NULL is a no-op. */
+PIC_API void pic_free(pic_sim* s);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* PIC_H */

@@ -1,0 +1,220 @@
+"""Python binding of the GB300 implicit-FDTD PIC library (C ABI in include/pic.h).
+
+Argument marshalling only: every function forwards to the function of the same name in
+libpic.so, which runs all of the particle cycle in CUDA kernels. Arrays may be numpy
+arrays (host) or torch tensors (host or CUDA); FP64, C-contiguous. Nonzero return codes
+raise PicError carrying pic_last_error(). There is no CPU fallback: if libpic.so is not
+built, importing succeeds but the first call raises.
+
+Build with ``python -c "import __graft_entry__ as g; g.build()"`` from the repository root
+(or ``python paper_1412_2480_gb300/build.py``).
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+import threading
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIBPATH = os.path.join(_HERE, "libpic.so")
+
+PIC_OK = 0
+PIC_EINVAL = -1
+PIC_ENOMEM = -2
+PIC_ECUDA = -3
+PIC_ECG_NOCONV = -4
+PIC_ECFL = -5
+PIC_ENAN = -6
+PIC_ESTATE = -8
+PIC_FP64 = 0
+PIC_MIXED32 = 1
+PIC_WS_ZERO = 0
+PIC_WS_PREV = 1
+PIC_NO_DEPOSIT = 1
+PIC_NO_GRAPH = 2
+PIC_EX, PIC_EY, PIC_EZ, PIC_BX, PIC_BY, PIC_BZ = range(6)
+PIC_JX, PIC_JY, PIC_JZ, PIC_DBX, PIC_DBY, PIC_DBZ = range(6, 12)
+
+EXPORTED = ("pic_params_default", "pic_init", "pic_set_stream", "pic_load_particles",
+            "pic_set_fields", "pic_step", "pic_fields", "pic_moments", "pic_particle_count",
+            "pic_particles", "pic_last_error", "pic_free")
+
+
+class pic_params(C.Structure):
+    _fields_ = [("nx", C.c_int32), ("ny", C.c_int32), ("dx", C.c_double), ("dy", C.c_double),
+                ("cfl", C.c_double), ("theta", C.c_double), ("shape_order", C.c_int32),
+                ("gamma0", C.c_double), ("ppc", C.c_int32), ("skin_depth", C.c_double),
+                ("precision", C.c_int32), ("cg_rtol", C.c_double), ("cg_max_iter", C.c_int32),
+                ("warm_start", C.c_int32), ("flags", C.c_int32), ("tile_x", C.c_int32),
+                ("tile_y", C.c_int32), ("bin_slack", C.c_double)]
+
+
+class pic_moments_t(C.Structure):
+    _fields_ = [("step", C.c_int64), ("time", C.c_double), ("U_E", C.c_double),
+                ("U_B", C.c_double), ("U_K", C.c_double), ("macro_weight", C.c_double),
+                ("n_particles", C.c_int64 * 2), ("cg_iters_last", C.c_int32),
+                ("cg_iters_max", C.c_int32), ("cg_iters_total", C.c_int64),
+                ("cg_rel_resid", C.c_double), ("cfl_violations", C.c_int64),
+                ("overflow_moves", C.c_int64), ("rebins", C.c_int64)]
+
+
+class PicError(RuntimeError):
+    def __init__(self, code, msg):
+        super().__init__(f"pic error {code}: {msg}")
+        self.code = code
+
+
+_lock = threading.Lock()
+_lib = None
+
+
+def lib():
+    """Load libpic.so (the CUDA product). Raises if it has not been built."""
+    global _lib
+    with _lock:
+        if _lib is None:
+            if not os.path.exists(LIBPATH):
+                raise RuntimeError(f"{LIBPATH} is not built; the CUDA library is required "
+                                   "(run __graft_entry__.build())")
+            L = C.CDLL(LIBPATH)
+            vp = C.c_void_p
+            L.pic_params_default.argtypes = [C.POINTER(pic_params)]
+            L.pic_params_default.restype = None
+            L.pic_init.argtypes = [C.POINTER(pic_params), C.POINTER(vp)]
+            L.pic_set_stream.argtypes = [vp, vp]
+            L.pic_load_particles.argtypes = [vp, C.c_int32, vp, vp, vp, vp, vp, C.c_int64]
+            L.pic_set_fields.argtypes = [vp, C.c_int32, vp, C.c_size_t]
+            L.pic_step.argtypes = [vp, C.c_int32]
+            L.pic_fields.argtypes = [vp, C.c_int32, vp, C.c_size_t]
+            L.pic_moments.argtypes = [vp, C.POINTER(pic_moments_t)]
+            L.pic_particle_count.argtypes = [vp, C.c_int32]
+            L.pic_particle_count.restype = C.c_int64
+            L.pic_particles.argtypes = [vp, C.c_int32, vp, C.c_int64]
+            L.pic_last_error.argtypes = [vp]
+            L.pic_last_error.restype = C.c_char_p
+            L.pic_free.argtypes = [vp]
+            L.pic_free.restype = None
+            for name in ("pic_init", "pic_set_stream", "pic_load_particles", "pic_set_fields",
+                         "pic_step", "pic_fields", "pic_moments", "pic_particles"):
+                getattr(L, name).restype = C.c_int
+            _lib = L
+    return _lib
+
+
+def _check(rc, h):
+    if rc != PIC_OK:
+        msg = lib().pic_last_error(h)
+        raise PicError(rc, msg.decode() if msg else "")
+    return rc
+
+
+def _ptr(a, writable=False):
+    """Device or host address of a float64 C-contiguous numpy array or torch tensor."""
+    if a is None:
+        return None
+    if hasattr(a, "data_ptr"):  # torch tensor
+        import torch
+        if a.dtype != torch.float64 or not a.is_contiguous():
+            raise TypeError("tensor must be contiguous float64")
+        return a.data_ptr()
+    if not isinstance(a, np.ndarray) or a.dtype != np.float64 or not a.flags.c_contiguous:
+        raise TypeError("array must be a C-contiguous float64 numpy array")
+    if writable and not a.flags.writeable:
+        raise TypeError("output array is read-only")
+    return a.ctypes.data
+
+
+def _len(a):
+    return a.numel() if hasattr(a, "numel") else a.size
+
+
+# ---- the C ABI, one function each -------------------------------------------------
+
+def pic_params_default(**overrides) -> pic_params:
+    p = pic_params()
+    lib().pic_params_default(C.byref(p))
+    for k, v in overrides.items():
+        if not hasattr(p, k):
+            raise AttributeError(f"pic_params has no field {k}")
+        setattr(p, k, v)
+    return p
+
+
+def pic_init(params: pic_params) -> int:
+    h = C.c_void_p()
+    _check(lib().pic_init(C.byref(params), C.byref(h)), None)
+    return h.value
+
+
+def pic_set_stream(h, stream) -> None:
+    """stream: torch.cuda.Stream, an integer cudaStream_t, or None (legacy default)."""
+    sp = getattr(stream, "cuda_stream", stream)
+    _check(lib().pic_set_stream(h, sp), h)
+
+
+def pic_load_particles(h, species, x, y, ux, uy, uz) -> None:
+    n = _len(x)
+    for a in (y, ux, uy, uz):
+        if _len(a) != n:
+            raise ValueError("particle arrays must have equal length")
+    _check(lib().pic_load_particles(h, species, _ptr(x), _ptr(y), _ptr(ux), _ptr(uy), _ptr(uz), n), h)
+
+
+def pic_set_fields(h, which, data) -> None:
+    _check(lib().pic_set_fields(h, which, _ptr(data), _len(data)), h)
+
+
+def pic_step(h, n=1) -> None:
+    _check(lib().pic_step(h, int(n)), h)
+
+
+def pic_fields(h, which, out=None, shape=None):
+    """Copy one grid quantity into `out` (numpy or torch, nx*ny float64). With out=None a
+    numpy array is returned, reshaped to `shape` when given."""
+    if out is None:
+        raise ValueError("pass out= (an array of nx*ny float64) or use fields_numpy()")
+    _check(lib().pic_fields(h, which, _ptr(out, True), _len(out)), h)
+    return out
+
+
+def pic_moments(h) -> dict:
+    m = pic_moments_t()
+    _check(lib().pic_moments(h, C.byref(m)), h)
+    d = {k: getattr(m, k) for k, _ in pic_moments_t._fields_}
+    d["n_particles"] = (m.n_particles[0], m.n_particles[1])
+    return d
+
+
+def pic_particle_count(h, species) -> int:
+    n = lib().pic_particle_count(h, species)
+    if n < 0:
+        raise PicError(PIC_EINVAL, "bad handle or species")
+    return n
+
+
+def pic_particles(h, species, out=None):
+    """Returns (or fills) a (5, n) float64 array [x, y, ux, uy, uz]."""
+    n = pic_particle_count(h, species)
+    if out is None:
+        out = np.empty((5, n), dtype=np.float64)
+    _check(lib().pic_particles(h, species, _ptr(out, True), n), h)
+    return out
+
+
+def pic_last_error(h) -> str:
+    m = lib().pic_last_error(h)
+    return m.decode() if m else ""
+
+
+def pic_free(h) -> None:
+    lib().pic_free(h)
+
+
+# ---- conveniences built only from the calls above ----------------------------------
+
+def fields_numpy(h, which, nx, ny):
+    out = np.empty(nx * ny, dtype=np.float64)
+    pic_fields(h, which, out)
+    return out.reshape(ny, nx)

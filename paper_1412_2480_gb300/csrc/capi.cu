@@ -1,0 +1,708 @@
+// capi.cu -- the C ABI (include/pic.h): handle lifecycle, parameter validation, particle
+// and field I/O, and the step sequence.
+//
+// One step (Sec. 2, Sec. 3 of Ikeya & Matsumoto 2015):
+//   step_begin -> J = 0 -> particle half (gather E^n,B^n; push; move; deposit J^{n+1/2})
+//   -> rhs of Eq. (7) -> WHILE(any simulation active) { PCG iteration } -> E,B update
+//   (Eqs. (5)-(6)) -> step_end.
+// The step is captured once into a CUDA graph whose PCG loop is a WHILE conditional
+// node driven from the device, so pic_step(n) launches n graphs and synchronises once.
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <cmath>
+#include <cstdio>
+#include <cstring>
+#include <string>
+#include <vector>
+
+#include "engine.h"
+#include "mixed.h"
+#include "pic.h"
+
+using namespace pic;
+
+struct pic_sim {
+    std::string err;
+    int device = 0;
+    cudaStream_t stream = nullptr;      // stream all work of the handle is enqueued on
+    cudaStream_t own_stream = nullptr;  // the handle's own non-blocking stream (default)
+    pic_params prm{};
+    int ngrids = 1;
+    std::vector<GridDev> hgrids;
+    GridDev* dgrids = nullptr;
+    std::vector<int> hblk_grid;
+    int* dblk_grid = nullptr;
+    int nblk = 0;
+    long long ntot = 0;
+    // grid arrays
+    double* F = nullptr;    // 6 ntot
+    double* J64 = nullptr;  // 3 ntot (FP64)
+    float* J32 = nullptr;   // 3 ntot (MIXED32)
+    float* F32 = nullptr;   // 6 ntot (MIXED32)
+    double *x = nullptr, *r = nullptr, *p = nullptr, *q = nullptr;
+    double* part = nullptr;
+    CgState* cg = nullptr;
+    unsigned int* done = nullptr;
+    DevStatus* st = nullptr;
+    double* tmp = nullptr;  // ntot scratch for conversions (pic_fields of J in MIXED32)
+    // FP64 particles, one set of arrays per species (grid units)
+    double* pa[2][5] = {{nullptr}};
+    long long np[2] = {0, 0};
+    long long pcap[2] = {0, 0};
+    SegDev* dsegs = nullptr;   // [2]
+    int* dblk_seg[2] = {nullptr, nullptr};
+    int nblk_push[2] = {0, 0};
+    // MIXED32 particles
+    MixedState* mixed = nullptr;
+    // graph
+    cudaGraph_t graph = nullptr;
+    cudaGraphExec_t gexec = nullptr;
+    cudaStream_t body_stream = nullptr;
+    // bookkeeping
+    long long steps = 0;
+    unsigned long long seen_cfl = 0, seen_nan = 0;
+    unsigned int seen_noconv = 0;
+};
+
+namespace {
+
+std::string g_init_err;
+
+int fail(pic_sim* s, int code, const std::string& msg) {
+    if (s) s->err = msg;
+    else g_init_err = msg;
+    return code;
+}
+
+#define CK(call)                                                                            \
+    do {                                                                                    \
+        cudaError_t e_ = (call);                                                            \
+        if (e_ != cudaSuccess)                                                              \
+            return fail(s, PIC_ECUDA, std::string(#call) + " failed: " + cudaGetErrorString(e_)); \
+    } while (0)
+
+template <typename T>
+cudaError_t dalloc(T** p, size_t n) {
+    *p = nullptr;
+    if (n == 0) n = 1;
+    return cudaMalloc((void**)p, n * sizeof(T));
+}
+
+void dfree(void* p) {
+    if (p) cudaFree(p);
+}
+
+int validate(const pic_params* p, std::string& why) {
+    char buf[256];
+    auto bad = [&](const char* m) {
+        why = m;
+        return PIC_EINVAL;
+    };
+    if (!p) return bad("params is NULL");
+    if (p->nx < 8 || p->ny < 8 || p->nx > 32768 || p->ny > 32768)
+        return bad("nx and ny must lie in [8, 32768]");
+    if (!(p->dx > 0) || !(p->dy > 0)) return bad("dx and dy must be > 0");
+    if (!(p->cfl > 0) || p->cfl > 1.0) return bad("cfl must lie in (0, 1]");
+    if (p->cfl * p->dx > p->dy * (1.0 + 1e-12))
+        return bad("dt = cfl*dx must not exceed dy (a move must stay below one cell)");
+    if (!(p->theta >= 0.5) || p->theta > 1.0) return bad("theta must lie in [0.5, 1]");
+    if (p->shape_order < 1 || p->shape_order > 3) return bad("shape_order must be 1, 2 or 3");
+    if (!(p->gamma0 >= 1.0)) return bad("gamma0 must be >= 1");
+    if (p->ppc < 1) return bad("ppc must be >= 1");
+    if (!(p->skin_depth > 0)) return bad("skin_depth must be > 0");
+    if (p->precision != PIC_FP64 && p->precision != PIC_MIXED32)
+        return bad("precision must be PIC_FP64 or PIC_MIXED32");
+    if (!(p->cg_rtol > 0) || p->cg_rtol >= 1) return bad("cg_rtol must lie in (0, 1)");
+    if (p->cg_max_iter < 1 || p->cg_max_iter > 100000) return bad("cg_max_iter must lie in [1, 1e5]");
+    if (p->warm_start != PIC_WS_ZERO && p->warm_start != PIC_WS_PREV)
+        return bad("warm_start must be PIC_WS_ZERO or PIC_WS_PREV");
+    if (p->tile_x < 0 || p->tile_y < 0) return bad("tile sizes must be >= 0");
+    if ((p->tile_x + 5) * (p->tile_y + 5) > kMaxWinCells && p->tile_x && p->tile_y) {
+        snprintf(buf, sizeof buf, "(tile_x+5)*(tile_y+5) must not exceed %d", kMaxWinCells);
+        return bad(buf);
+    }
+    if (p->bin_slack < 0) return bad("bin_slack must be >= 0");
+    return PIC_OK;
+}
+
+void fill_grid(const pic_params& p, GridDev& G) {
+    memset(&G, 0, sizeof G);
+    G.nx = p.nx;
+    G.ny = p.ny;
+    G.order = p.shape_order;
+    G.ncell = p.nx * p.ny;
+    G.dx = p.dx;
+    G.dy = p.dy;
+    G.dt = p.cfl * p.dx;
+    G.theta = p.theta;
+    G.idx = 1.0 / p.dx;
+    G.idy = 1.0 / p.dy;
+    G.a = (p.theta * G.dt) * (p.theta * G.dt);
+    G.cx = G.a / (p.dx * p.dx);
+    G.cy = G.a / (p.dy * p.dy);
+    G.c0 = 1.0 + 2.0 * G.cx + 2.0 * G.cy;
+    // omega_pe^2 = 4 pi n q^2 / (m gamma0), n = ppc/(dx dy), q = m = w (Sec. 4 definition)
+    const double wpe = 1.0 / p.skin_depth;
+    G.w = wpe * wpe * p.gamma0 * p.dx * p.dy / (4.0 * kPi * p.ppc);
+    G.qm[0] = 1.0;
+    G.qm[1] = -1.0;
+    G.qw[0] = G.w;
+    G.qw[1] = -G.w;
+    G.rtol = p.cg_rtol;
+    G.maxit = p.cg_max_iter;
+    G.warm = p.warm_start == PIC_WS_PREV ? 1 : 0;
+    G.deposit = (p.flags & PIC_NO_DEPOSIT) ? 0 : 1;
+}
+
+FieldArgs field_args(pic_sim* s, int use_cond, cudaGraphConditionalHandle cond) {
+    FieldArgs a{};
+    a.grids = s->dgrids;
+    a.blk_grid = s->dblk_grid;
+    a.ngrids = s->ngrids;
+    a.nblk = s->nblk;
+    a.ntot = s->ntot;
+    a.F = s->F;
+    a.J64 = s->prm.precision == PIC_FP64 ? s->J64 : nullptr;
+    a.J32 = s->prm.precision == PIC_MIXED32 ? s->J32 : nullptr;
+    a.F32 = s->F32;
+    a.x = s->x;
+    a.r = s->r;
+    a.p = s->p;
+    a.q = s->q;
+    a.cg = s->cg;
+    a.part = s->part;
+    a.done = s->done;
+    a.st = s->st;
+    a.cond = cond;
+    a.use_cond = use_cond;
+    return a;
+}
+
+void drop_graph(pic_sim* s) {
+    if (s->gexec) cudaGraphExecDestroy(s->gexec);
+    if (s->graph) cudaGraphDestroy(s->graph);
+    s->gexec = nullptr;
+    s->graph = nullptr;
+}
+
+// The particle half of the step.
+void enqueue_particles(pic_sim* s, cudaStream_t st) {
+    if (s->prm.precision == PIC_FP64) {
+        cudaMemsetAsync(s->J64, 0, 3 * s->ntot * sizeof(double), st);
+        for (int sp = 0; sp < 2; sp++) {
+            if (s->np[sp] == 0) continue;
+            Fp64PushArgs a{};
+            a.grids = s->dgrids;
+            a.segs = s->dsegs + sp;
+            a.blk_seg = s->dblk_seg[sp];
+            a.nblk = s->nblk_push[sp];
+            a.nsegs = 1;
+            a.ntot = s->ntot;
+            a.F = s->F;
+            a.J = s->J64;
+            a.x = s->pa[sp][0];
+            a.y = s->pa[sp][1];
+            a.ux = s->pa[sp][2];
+            a.uy = s->pa[sp][3];
+            a.uz = s->pa[sp][4];
+            a.cg = s->cg;
+            a.st = s->st;
+            launch_push_fp64(a, s->prm.shape_order, st);
+        }
+    } else {
+        cudaMemsetAsync(s->J32, 0, 3 * s->ntot * sizeof(float), st);
+        mixed_enqueue_step(s->mixed, st);
+    }
+}
+
+void enqueue_pre(pic_sim* s, cudaStream_t st, int use_cond, cudaGraphConditionalHandle h) {
+    const FieldArgs a = field_args(s, use_cond, h);
+    launch_step_begin(a, st);
+    enqueue_particles(s, st);
+    launch_rhs(a, st);
+}
+
+void enqueue_post(pic_sim* s, cudaStream_t st) {
+    const FieldArgs a = field_args(s, 0, 0);
+    launch_field_update(a, st);
+    launch_step_end(a, st);
+}
+
+int build_graph(pic_sim* s) {
+    drop_graph(s);
+    cudaStream_t st = s->stream;
+    CK(cudaStreamBeginCapture(st, cudaStreamCaptureModeThreadLocal));
+    cudaStreamCaptureStatus cs;
+    cudaGraph_t cap = nullptr;
+    const cudaGraphNode_t* deps = nullptr;
+    size_t nd = 0;
+    cudaGraphConditionalHandle h{};
+    cudaError_t e = cudaStreamGetCaptureInfo(st, &cs, nullptr, &cap, &deps, nullptr, &nd);
+    if (e == cudaSuccess) e = cudaGraphConditionalHandleCreate(&h, cap, 0, cudaGraphCondAssignDefault);
+    if (e == cudaSuccess) {
+        enqueue_pre(s, st, 1, h);
+        e = cudaStreamGetCaptureInfo(st, &cs, nullptr, &cap, &deps, nullptr, &nd);
+    }
+    cudaGraphNode_t wnode{};
+    cudaGraphNodeParams cp{};
+    if (e == cudaSuccess) {
+        cp.type = cudaGraphNodeTypeConditional;
+        cp.conditional.handle = h;
+        cp.conditional.type = cudaGraphCondTypeWhile;
+        cp.conditional.size = 1;
+        e = cudaGraphAddNode(&wnode, cap, deps, nullptr, nd, &cp);
+    }
+    if (e == cudaSuccess)
+        e = cudaStreamUpdateCaptureDependencies(st, &wnode, nullptr, 1,
+                                                cudaStreamSetCaptureDependencies);
+    if (e == cudaSuccess) {
+        cudaGraph_t body = cp.conditional.phGraph_out[0];
+        e = cudaStreamBeginCaptureToGraph(s->body_stream, body, nullptr, nullptr, 0,
+                                          cudaStreamCaptureModeThreadLocal);
+        if (e == cudaSuccess) {
+            launch_cg_iteration(field_args(s, 1, h), s->body_stream);
+            cudaGraph_t out = nullptr;
+            e = cudaStreamEndCapture(s->body_stream, &out);
+        }
+    }
+    if (e == cudaSuccess) enqueue_post(s, st);
+    cudaGraph_t g = nullptr;
+    cudaError_t e2 = cudaStreamEndCapture(st, &g);
+    if (e == cudaSuccess) e = e2;
+    if (e != cudaSuccess) {
+        if (g) cudaGraphDestroy(g);
+        cudaGetLastError();
+        return fail(s, PIC_ECUDA, std::string("step graph capture failed: ") + cudaGetErrorString(e));
+    }
+    s->graph = g;
+    e = cudaGraphInstantiate(&s->gexec, g, 0);
+    if (e != cudaSuccess) {
+        drop_graph(s);
+        return fail(s, PIC_ECUDA, std::string("cudaGraphInstantiate failed: ") + cudaGetErrorString(e));
+    }
+    return PIC_OK;
+}
+
+// Direct launches (PIC_NO_GRAPH): the PCG loop is driven from the host.
+int run_step_direct(pic_sim* s) {
+    cudaStream_t st = s->stream;
+    enqueue_pre(s, st, 0, 0);
+    unsigned int nact = 0;
+    CK(cudaMemcpyAsync(&nact, &s->st->n_active, sizeof nact, cudaMemcpyDeviceToHost, st));
+    CK(cudaStreamSynchronize(st));
+    while (nact > 0) {
+        launch_cg_iteration(field_args(s, 0, 0), st);
+        CK(cudaMemcpyAsync(&nact, &s->st->n_active, sizeof nact, cudaMemcpyDeviceToHost, st));
+        CK(cudaStreamSynchronize(st));
+    }
+    enqueue_post(s, st);
+    CK(cudaGetLastError());
+    return PIC_OK;
+}
+
+int check_species(pic_sim* s, int sp) {
+    if (sp < 0 || sp > 1) return fail(s, PIC_EINVAL, "species must be 0 (positrons) or 1 (electrons)");
+    return PIC_OK;
+}
+
+// Device-side conversion of loaded FP64 particles: wrap into the box and scale to grid
+// units; count non-finite entries.
+__global__ void k_load_fp64(long long n, double* x, double* y, const double* ux, const double* uy,
+                            const double* uz, double Lx, double Ly, double idx, double idy, int nx,
+                            int ny, unsigned long long* nbad) {
+    const long long k = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (k >= n) return;
+    double X = x[k], Y = y[k];
+    if (!isfinite(X) || !isfinite(Y) || !isfinite(ux[k]) || !isfinite(uy[k]) || !isfinite(uz[k])) {
+        atomicAdd(nbad, 1ull);
+        x[k] = 0.0;
+        y[k] = 0.0;
+        return;
+    }
+    X = X - floor(X / Lx) * Lx;
+    Y = Y - floor(Y / Ly) * Ly;
+    X *= idx;
+    Y *= idy;
+    if (X >= nx || X < 0) X = 0.0;
+    if (Y >= ny || Y < 0) Y = 0.0;
+    x[k] = X;
+    y[k] = Y;
+}
+
+__global__ void k_unload_fp64(long long n, const double* x, const double* y, double dx, double dy,
+                              double* ox, double* oy) {
+    const long long k = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (k >= n) return;
+    ox[k] = x[k] * dx;
+    oy[k] = y[k] * dy;
+}
+
+__global__ void k_f32_to_f64(long long n, const float* a, double* b) {
+    const long long k = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (k < n) b[k] = (double)a[k];
+}
+
+int finish_call(pic_sim* s) {
+    CK(cudaStreamSynchronize(s->stream));
+    CK(cudaGetLastError());
+    return PIC_OK;
+}
+
+}  // namespace
+
+// =====================================================================================
+extern "C" {
+
+void pic_params_default(pic_params* p) {
+    if (!p) return;
+    memset(p, 0, sizeof *p);
+    p->nx = 64;
+    p->ny = 64;
+    p->dx = 1.0;
+    p->dy = 1.0;
+    p->cfl = 1.0;
+    p->theta = 0.5;
+    p->shape_order = 1;
+    p->gamma0 = 20.0;
+    p->ppc = 8;
+    p->skin_depth = 10.0;
+    p->precision = PIC_FP64;
+    p->cg_rtol = 1e-10;
+    p->cg_max_iter = 200;
+    p->warm_start = PIC_WS_ZERO;
+    p->flags = 0;
+    p->tile_x = 0;
+    p->tile_y = 0;
+    p->bin_slack = 0.0;
+}
+
+int pic_init(const pic_params* prm, pic_sim** out) {
+    pic_sim* s = nullptr;
+    if (!out) return fail(nullptr, PIC_EINVAL, "out is NULL");
+    *out = nullptr;
+    std::string why;
+    if (validate(prm, why) != PIC_OK) return fail(nullptr, PIC_EINVAL, why);
+    s = new (std::nothrow) pic_sim();
+    if (!s) return fail(nullptr, PIC_ENOMEM, "host allocation failed");
+    s->prm = *prm;
+    if (cudaGetDevice(&s->device) != cudaSuccess) {
+        delete s;
+        return fail(nullptr, PIC_ECUDA, "no CUDA device");
+    }
+    auto bail = [&](int code) {
+        g_init_err = s->err;
+        pic_free(s);
+        return code;
+    };
+    s->ngrids = 1;
+    s->hgrids.resize(1);
+    fill_grid(*prm, s->hgrids[0]);
+    s->ntot = (long long)prm->nx * prm->ny;
+    s->hgrids[0].cell_off = 0;
+    s->hgrids[0].blk_first = 0;
+    s->hgrids[0].nblk = (int)((s->ntot + kFieldThreads - 1) / kFieldThreads);
+    s->nblk = s->hgrids[0].nblk;
+    s->hblk_grid.assign(s->nblk, 0);
+    const long long n3 = 3 * s->ntot;
+    cudaError_t e = cudaSuccess;
+    auto A = [&](cudaError_t r) {
+        if (e == cudaSuccess) e = r;
+    };
+    A(cudaStreamCreateWithFlags(&s->body_stream, cudaStreamNonBlocking));
+    A(cudaStreamCreateWithFlags(&s->own_stream, cudaStreamNonBlocking));
+    s->stream = s->own_stream;
+    A(dalloc(&s->F, 6 * s->ntot));
+    A(dalloc(&s->x, n3));
+    A(dalloc(&s->r, n3));
+    A(dalloc(&s->p, n3));
+    A(dalloc(&s->q, n3));
+    A(dalloc(&s->part, 4 * (size_t)s->nblk));
+    A(dalloc(&s->cg, s->ngrids));
+    A(dalloc(&s->done, s->ngrids));
+    A(dalloc(&s->st, 1));
+    A(dalloc(&s->tmp, s->ntot));
+    A(dalloc(&s->dgrids, s->ngrids));
+    A(dalloc(&s->dblk_grid, s->nblk));
+    A(dalloc(&s->dsegs, 2));
+    if (prm->precision == PIC_FP64) {
+        A(dalloc(&s->J64, n3));
+    } else {
+        A(dalloc(&s->J32, n3));
+        A(dalloc(&s->F32, 6 * s->ntot));
+    }
+    if (e != cudaSuccess) {
+        s->err = std::string("device allocation failed: ") + cudaGetErrorString(e);
+        cudaGetLastError();
+        return bail(PIC_ENOMEM);
+    }
+    A(cudaMemset(s->F, 0, 6 * s->ntot * sizeof(double)));
+    A(cudaMemset(s->x, 0, n3 * sizeof(double)));
+    A(cudaMemset(s->r, 0, n3 * sizeof(double)));
+    A(cudaMemset(s->p, 0, n3 * sizeof(double)));
+    A(cudaMemset(s->q, 0, n3 * sizeof(double)));
+    A(cudaMemset(s->cg, 0, s->ngrids * sizeof(CgState)));
+    A(cudaMemset(s->done, 0, s->ngrids * sizeof(unsigned int)));
+    A(cudaMemset(s->st, 0, sizeof(DevStatus)));
+    if (s->J64) A(cudaMemset(s->J64, 0, n3 * sizeof(double)));
+    if (s->J32) A(cudaMemset(s->J32, 0, n3 * sizeof(float)));
+    if (s->F32) A(cudaMemset(s->F32, 0, 6 * s->ntot * sizeof(float)));
+    if (prm->precision == PIC_MIXED32) {
+        int rc = mixed_create(&s->mixed, *prm, s->hgrids[0], s->dgrids, s->ntot, s->F32, s->J32,
+                              s->cg, s->st, s->err);
+        if (rc != PIC_OK) return bail(rc);
+    }
+    A(cudaMemcpy(s->dgrids, s->hgrids.data(), s->ngrids * sizeof(GridDev), cudaMemcpyHostToDevice));
+    A(cudaMemcpy(s->dblk_grid, s->hblk_grid.data(), s->nblk * sizeof(int), cudaMemcpyHostToDevice));
+    A(cudaDeviceSynchronize());
+    if (e != cudaSuccess) {
+        s->err = std::string("initialisation failed: ") + cudaGetErrorString(e);
+        cudaGetLastError();
+        return bail(PIC_ECUDA);
+    }
+    *out = s;
+    return PIC_OK;
+}
+
+int pic_set_stream(pic_sim* s, void* stream) {
+    if (!s) return PIC_EINVAL;
+    cudaSetDevice(s->device);
+    if (s->stream) cudaStreamSynchronize(s->stream);
+    drop_graph(s);
+    s->stream = stream ? (cudaStream_t)stream : s->own_stream;
+    return PIC_OK;
+}
+
+int pic_load_particles(pic_sim* s, int32_t sp, const double* x, const double* y, const double* ux,
+                       const double* uy, const double* uz, int64_t n) {
+    if (!s) return PIC_EINVAL;
+    cudaSetDevice(s->device);
+    if (int rc = check_species(s, sp)) return rc;
+    if (n < 0) return fail(s, PIC_EINVAL, "n must be >= 0");
+    if (n > 0 && (!x || !y || !ux || !uy || !uz)) return fail(s, PIC_EINVAL, "NULL particle array");
+    if (n > (int64_t)1 << 40) return fail(s, PIC_EINVAL, "n too large");
+    drop_graph(s);
+    if (s->prm.precision == PIC_MIXED32) {
+        int rc = mixed_load(s->mixed, sp, x, y, ux, uy, uz, n, s->stream, s->err);
+        if (rc == PIC_OK) rc = finish_call(s);
+        return rc;
+    }
+    // FP64: (re)allocate exactly n per array
+    if (n > s->pcap[sp]) {
+        for (int a = 0; a < 5; a++) {
+            dfree(s->pa[sp][a]);
+            s->pa[sp][a] = nullptr;
+        }
+        s->pcap[sp] = 0;
+        for (int a = 0; a < 5; a++) {
+            if (dalloc(&s->pa[sp][a], (size_t)n) != cudaSuccess) {
+                cudaGetLastError();
+                return fail(s, PIC_ENOMEM, "particle allocation failed");
+            }
+        }
+        s->pcap[sp] = n;
+    }
+    const double* src[5] = {x, y, ux, uy, uz};
+    for (int a = 0; a < 5; a++)
+        if (n) CK(cudaMemcpyAsync(s->pa[sp][a], src[a], n * sizeof(double), cudaMemcpyDefault, s->stream));
+    unsigned long long* nbad = (unsigned long long*)s->tmp;
+    CK(cudaMemsetAsync(nbad, 0, sizeof(unsigned long long), s->stream));
+    const GridDev& G = s->hgrids[0];
+    if (n) {
+        k_load_fp64<<<(unsigned)((n + 255) / 256), 256, 0, s->stream>>>(
+            n, s->pa[sp][0], s->pa[sp][1], s->pa[sp][2], s->pa[sp][3], s->pa[sp][4], G.nx * G.dx,
+            G.ny * G.dy, G.idx, G.idy, G.nx, G.ny, nbad);
+    }
+    unsigned long long hbad = 0;
+    CK(cudaMemcpyAsync(&hbad, nbad, sizeof hbad, cudaMemcpyDeviceToHost, s->stream));
+    CK(cudaStreamSynchronize(s->stream));
+    if (hbad) {
+        s->np[sp] = 0;
+        return fail(s, PIC_EINVAL, "non-finite particle position or momentum");
+    }
+    s->np[sp] = n;
+    SegDev seg{};
+    seg.start = 0;
+    seg.count = n;
+    seg.grid = 0;
+    seg.species = sp;
+    seg.blk_first = 0;
+    seg.nblk = (int)((n + kPushThreads - 1) / kPushThreads);
+    s->nblk_push[sp] = seg.nblk;
+    CK(cudaMemcpy(s->dsegs + sp, &seg, sizeof seg, cudaMemcpyHostToDevice));
+    dfree(s->dblk_seg[sp]);
+    s->dblk_seg[sp] = nullptr;
+    if (seg.nblk) {
+        std::vector<int> t(seg.nblk, 0);
+        CK(dalloc(&s->dblk_seg[sp], seg.nblk));
+        CK(cudaMemcpy(s->dblk_seg[sp], t.data(), seg.nblk * sizeof(int), cudaMemcpyHostToDevice));
+    }
+    return PIC_OK;
+}
+
+int pic_set_fields(pic_sim* s, int32_t which, const double* data, size_t len) {
+    if (!s) return PIC_EINVAL;
+    cudaSetDevice(s->device);
+    if (which < PIC_EX || which > PIC_BZ) return fail(s, PIC_EINVAL, "which must be PIC_EX..PIC_BZ");
+    if (!data || len < (size_t)s->ntot) return fail(s, PIC_EINVAL, "data must hold nx*ny values");
+    CK(cudaMemcpyAsync(s->F + which * s->ntot, data, s->ntot * sizeof(double), cudaMemcpyDefault,
+                       s->stream));
+    launch_fields_to_f32(field_args(s, 0, 0), s->stream);
+    return finish_call(s);
+}
+
+int pic_step(pic_sim* s, int32_t n) {
+    if (!s) return PIC_EINVAL;
+    cudaSetDevice(s->device);
+    if (n < 0) return fail(s, PIC_EINVAL, "n must be >= 0");
+    if (n == 0) return PIC_OK;
+    // a new call starts clean: errors stop the rest of the call that raised them only
+    DevStatus hs{};
+    CK(cudaMemcpyAsync(&hs, s->st, sizeof hs, cudaMemcpyDeviceToHost, s->stream));
+    CK(cudaStreamSynchronize(s->stream));
+    const unsigned long long steps0 = hs.steps_done;
+    hs.stop = 0;
+    hs.stop_next = 0;
+    CK(cudaMemcpyAsync(s->st, &hs, sizeof hs, cudaMemcpyHostToDevice, s->stream));
+    if (s->prm.precision == PIC_MIXED32) {
+        int rc = mixed_before_steps(s->mixed, s->stream, s->err);
+        if (rc) return rc;
+    }
+    const bool graph = !(s->prm.flags & PIC_NO_GRAPH);
+    if (graph && !s->gexec) {
+        if (int rc = build_graph(s)) return rc;
+    }
+    for (int k = 0; k < n; k++) {
+        if (graph) {
+            CK(cudaGraphLaunch(s->gexec, s->stream));
+        } else {
+            if (int rc = run_step_direct(s)) return rc;
+        }
+    }
+    CK(cudaMemcpyAsync(&hs, s->st, sizeof hs, cudaMemcpyDeviceToHost, s->stream));
+    if (int rc = finish_call(s)) return rc;
+    s->steps += (long long)(hs.steps_done - steps0);
+    int rc = PIC_OK;
+    if (hs.cg_noconv != s->seen_noconv) {
+        rc = fail(s, PIC_ECG_NOCONV, "PCG reached cg_max_iter before cg_rtol");
+    } else if (hs.nan_count != s->seen_nan) {
+        rc = fail(s, PIC_ENAN, "non-finite particle momentum or position");
+    } else if (hs.cfl_viol != s->seen_cfl) {
+        rc = fail(s, PIC_ECFL, "a particle moved one cell or more in one step");
+    }
+    s->seen_noconv = hs.cg_noconv;
+    s->seen_nan = hs.nan_count;
+    s->seen_cfl = hs.cfl_viol;
+    if (rc == PIC_OK && s->prm.precision == PIC_MIXED32) rc = mixed_after_steps(s->mixed, s->stream, s->err);
+    return rc;
+}
+
+int pic_fields(pic_sim* s, int32_t which, double* out, size_t len) {
+    if (!s) return PIC_EINVAL;
+    cudaSetDevice(s->device);
+    if (which < PIC_EX || which > PIC_DBZ) return fail(s, PIC_EINVAL, "which must be PIC_EX..PIC_DBZ");
+    if (!out || len < (size_t)s->ntot) return fail(s, PIC_EINVAL, "out must hold nx*ny values");
+    const double* src = nullptr;
+    if (which <= PIC_BZ) {
+        src = s->F + which * s->ntot;
+    } else if (which <= PIC_JZ) {
+        const int c = which - PIC_JX;
+        if (s->J64) {
+            src = s->J64 + c * s->ntot;
+        } else {
+            k_f32_to_f64<<<(unsigned)((s->ntot + 255) / 256), 256, 0, s->stream>>>(
+                s->ntot, s->J32 + c * s->ntot, s->tmp);
+            src = s->tmp;
+        }
+    } else {
+        src = s->x + (which - PIC_DBX) * s->ntot;
+    }
+    CK(cudaMemcpyAsync(out, src, s->ntot * sizeof(double), cudaMemcpyDefault, s->stream));
+    return finish_call(s);
+}
+
+int pic_moments(pic_sim* s, pic_moments_t* m) {
+    if (!s) return PIC_EINVAL;
+    cudaSetDevice(s->device);
+    if (!m) return fail(s, PIC_EINVAL, "out is NULL");
+    CgState c{};
+    DevStatus hs{};
+    CK(cudaMemcpyAsync(&c, s->cg, sizeof c, cudaMemcpyDeviceToHost, s->stream));
+    CK(cudaMemcpyAsync(&hs, s->st, sizeof hs, cudaMemcpyDeviceToHost, s->stream));
+    if (int rc = finish_call(s)) return rc;
+    memset(m, 0, sizeof *m);
+    const GridDev& G = s->hgrids[0];
+    m->step = s->steps;
+    m->time = s->steps * G.dt;
+    m->U_E = c.ue;
+    m->U_B = c.ub;
+    m->U_K = c.uk;
+    m->macro_weight = G.w;
+    m->n_particles[0] = pic_particle_count(s, 0);
+    m->n_particles[1] = pic_particle_count(s, 1);
+    m->cg_iters_last = c.last_iters;
+    m->cg_iters_max = c.max_iters;
+    m->cg_iters_total = c.total_iters;
+    m->cg_rel_resid = c.rel;
+    m->cfl_violations = (int64_t)hs.cfl_viol;
+    m->overflow_moves = (int64_t)hs.overflow;
+    if (s->mixed) m->rebins = mixed_rebins(s->mixed);
+    // the largest-iteration counter restarts at every pic_moments call
+    const int zero = 0;
+    CK(cudaMemcpyAsync(&s->cg->max_iters, &zero, sizeof zero, cudaMemcpyHostToDevice, s->stream));
+    return finish_call(s);
+}
+
+int64_t pic_particle_count(pic_sim* s, int32_t sp) {
+    if (!s || sp < 0 || sp > 1) return -1;
+    if (s->mixed) return mixed_count(s->mixed, sp);
+    return s->np[sp];
+}
+
+int pic_particles(pic_sim* s, int32_t sp, double* out, int64_t n) {
+    if (!s) return PIC_EINVAL;
+    cudaSetDevice(s->device);
+    if (int rc = check_species(s, sp)) return rc;
+    if (n != pic_particle_count(s, sp)) return fail(s, PIC_EINVAL, "n must equal pic_particle_count");
+    if (n == 0) return PIC_OK;
+    if (!out) return fail(s, PIC_EINVAL, "out is NULL");
+    if (s->mixed) {
+        int rc = mixed_particles(s->mixed, sp, out, n, s->stream, s->err);
+        if (rc == PIC_OK) rc = finish_call(s);
+        return rc;
+    }
+    const GridDev& G = s->hgrids[0];
+    double* t = nullptr;
+    CK(dalloc(&t, 2 * (size_t)n));
+    k_unload_fp64<<<(unsigned)((n + 255) / 256), 256, 0, s->stream>>>(n, s->pa[sp][0], s->pa[sp][1],
+                                                                      G.dx, G.dy, t, t + n);
+    cudaError_t e = cudaMemcpyAsync(out, t, 2 * n * sizeof(double), cudaMemcpyDefault, s->stream);
+    for (int a = 2; a < 5 && e == cudaSuccess; a++)
+        e = cudaMemcpyAsync(out + a * n, s->pa[sp][a], n * sizeof(double), cudaMemcpyDefault, s->stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(s->stream);
+    cudaFree(t);
+    if (e != cudaSuccess) return fail(s, PIC_ECUDA, std::string("pic_particles: ") + cudaGetErrorString(e));
+    return PIC_OK;
+}
+
+const char* pic_last_error(const pic_sim* s) {
+    return s ? s->err.c_str() : g_init_err.c_str();
+}
+
+void pic_free(pic_sim* s) {
+    if (!s) return;
+    cudaSetDevice(s->device);
+    if (s->stream) cudaStreamSynchronize(s->stream);
+    drop_graph(s);
+    if (s->mixed) mixed_destroy(s->mixed);
+    void* ptrs[] = {s->dgrids, s->dblk_grid, s->F, s->J64, s->J32, s->F32, s->x, s->r, s->p, s->q,
+                    s->part, s->cg, s->done, s->st, s->tmp, s->dsegs, s->dblk_seg[0], s->dblk_seg[1]};
+    for (void* p : ptrs) dfree(p);
+    for (int sp = 0; sp < 2; sp++)
+        for (int a = 0; a < 5; a++) dfree(s->pa[sp][a]);
+    if (s->body_stream) cudaStreamDestroy(s->body_stream);
+    if (s->own_stream) cudaStreamDestroy(s->own_stream);
+    delete s;
+}
+
+}  // extern "C"

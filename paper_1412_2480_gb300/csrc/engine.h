@@ -1,0 +1,58 @@
+// engine.h -- host-side launch interface between the C ABI (capi.cu) and the kernels.
+#pragma once
+
+#include <cuda_runtime.h>
+
+#include "pic_internal.cuh"
+
+namespace pic {
+
+// Device buffers and launch geometry of the grid (field-solve) kernels.
+struct FieldArgs {
+    const GridDev* grids;   // [ngrids]
+    const int* blk_grid;    // [nblk] simulation of each field block
+    int ngrids, nblk;
+    long long ntot;         // total cells over all simulations
+    double* F;              // 6 * ntot: Ex Ey Ez Bx By Bz (component-major)
+    const double* J64;      // 3 * ntot, FP64 current (FP64 particle path) or nullptr
+    const float* J32;       // 3 * ntot, FP32 current (MIXED32 particle path) or nullptr
+    float* F32;             // 6 * ntot FP32 copy of the fields for MIXED32 gathers, or nullptr
+    double *x, *r, *p, *q;  // 3 * ntot each: dB (solution), residual, direction, A p
+    CgState* cg;            // [ngrids]
+    double* part;           // 4 * nblk block partials
+    unsigned int* done;     // [ngrids] block-completion counters
+    DevStatus* st;
+    cudaGraphConditionalHandle cond;  // WHILE-node handle of the PCG loop
+    int use_cond;                      // 1 when running inside the captured step graph
+};
+
+// Per-step prologue (deferred stop, step counter, accumulators) and epilogue.
+void launch_step_begin(const FieldArgs& a, cudaStream_t s);
+void launch_step_end(const FieldArgs& a, cudaStream_t s);
+// b of Eq. (7), initial residual, energies at time level n.
+void launch_rhs(const FieldArgs& a, cudaStream_t s);
+// One PCG iteration: A-product and direction update, then solution/residual update.
+void launch_cg_iteration(const FieldArgs& a, cudaStream_t s);
+// E, B from Eqs. (5)-(6) with dB; FP32 copies when a.F32 is set.
+void launch_field_update(const FieldArgs& a, cudaStream_t s);
+// FP32 copy of the FP64 fields (after pic_set_fields / init).
+void launch_fields_to_f32(const FieldArgs& a, cudaStream_t s);
+
+// Arguments of the FP64 particle kernel.
+struct Fp64PushArgs {
+    const GridDev* grids;
+    const SegDev* segs;
+    const int* blk_seg;   // [nblk] segment of each block
+    int nblk;
+    int nsegs;
+    long long ntot;
+    const double* F;      // 6 * ntot
+    double* J;            // 3 * ntot
+    double *x, *y, *ux, *uy, *uz;  // positions in grid units (x/dx, y/dy)
+    CgState* cg;          // kinetic energy accumulates into cg[g].uk
+    DevStatus* st;
+};
+// One launch over all blocks of the table; every segment must have shape order `order`.
+void launch_push_fp64(const Fp64PushArgs& a, int order, cudaStream_t s);
+
+}  // namespace pic

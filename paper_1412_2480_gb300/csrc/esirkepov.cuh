@@ -1,0 +1,99 @@
+// esirkepov.cuh -- the particle kernels' shared device arithmetic: momentum-conserving
+// gather weights, the relativistic Boris push and the density-decomposition deposit.
+#pragma once
+
+#include "pic_internal.cuh"
+
+namespace pic {
+
+// Relativistic Buneman-Boris push (standard scheme; the paper specifies none), c = 1:
+// half electric kick, rotation by t = h B / gamma(u-), s = 2t / (1 + t^2), half kick.
+// h = (q/m) dt / 2.
+template <typename R>
+__device__ __forceinline__ void boris(R h, const R E[3], const R B[3], R u[3]) {
+    R um0 = u[0] + h * E[0], um1 = u[1] + h * E[1], um2 = u[2] + h * E[2];
+    const R ig = R(1) / sqrt(R(1) + um0 * um0 + um1 * um1 + um2 * um2);
+    const R t0 = h * B[0] * ig, t1 = h * B[1] * ig, t2 = h * B[2] * ig;
+    const R f = R(2) / (R(1) + t0 * t0 + t1 * t1 + t2 * t2);
+    const R s0 = f * t0, s1 = f * t1, s2 = f * t2;
+    const R p0 = um0 + (um1 * t2 - um2 * t1);
+    const R p1 = um1 + (um2 * t0 - um0 * t2);
+    const R p2 = um2 + (um0 * t1 - um1 * t0);
+    um0 += p1 * s2 - p2 * s1;
+    um1 += p2 * s0 - p0 * s2;
+    um2 += p0 * s1 - p1 * s0;
+    u[0] = um0 + h * E[0];
+    u[1] = um1 + h * E[1];
+    u[2] = um2 + h * E[2];
+}
+
+// Weight of node k (0..P+1) of a (P+2)-wide window, for a particle whose P+1 weights
+// start `sh` (0 or 1) nodes into the window.
+template <int P, typename R>
+__device__ __forceinline__ R window_weight(const R w[P + 1], int sh, int k) {
+    const int m = k - sh;
+    R v = R(0);
+#pragma unroll
+    for (int t = 0; t <= P; t++) v = (m == t) ? w[t] : v;
+    return v;
+}
+
+// Density-decomposition (Esirkepov) current of one particle moving from cell/fraction
+// (i0+f0x, j0+f0y) to (i1+f1x, j1+f1y), less than one cell in each direction. On the
+// common (P+2)^2 window of node weights S0 (old) and S1 (new), DS = S1 - S0:
+//   Wx = DSx (S0y + DSy/2),  Wy = DSy (S0x + DSx/2),
+//   Wz = S0x S0y + (DSx S0y + S0x DSy)/2 + DSx DSy/3,
+//   Jx(i+1/2) = Jx(i-1/2) - fx Wx, Jy(j+1/2) = Jy(j-1/2) - fy Wy, Jz += fz Wz,
+// with fx = q dx/(dt dx dy), fy = q dy/(dt dx dy), fz = q vz/(dx dy). The Jx running sum
+// over the last window column is zero (charge conservation), so only P+1 columns of Jx
+// (and P+1 rows of Jy) are written. `add(comp, ix, iy, value)` receives window-origin
+// node indices (unwrapped).
+template <int P, typename R, typename Add>
+__device__ __forceinline__ void esirkepov(int i0, R f0x, int j0, R f0y, int i1, R f1x, int j1,
+                                          R f1y, R fx, R fy, R fz, Add add) {
+    int b0x, b1x, b0y, b1y;
+    R s0x[P + 1], s1x[P + 1], s0y[P + 1], s1y[P + 1];
+    shape_nodes<P, R>(i0, f0x, b0x, s0x);
+    shape_nodes<P, R>(i1, f1x, b1x, s1x);
+    shape_nodes<P, R>(j0, f0y, b0y, s0y);
+    shape_nodes<P, R>(j1, f1y, b1y, s1y);
+    const int ox = min(b0x, b1x), oy = min(b0y, b1y);
+    const int h0x = b0x - ox, h1x = b1x - ox, h0y = b0y - oy, h1y = b1y - oy;
+    R S0x[P + 2], DSx[P + 2], S0y[P + 2], DSy[P + 2];
+#pragma unroll
+    for (int k = 0; k < P + 2; k++) {
+        S0x[k] = window_weight<P, R>(s0x, h0x, k);
+        DSx[k] = window_weight<P, R>(s1x, h1x, k) - S0x[k];
+        S0y[k] = window_weight<P, R>(s0y, h0y, k);
+        DSy[k] = window_weight<P, R>(s1y, h1y, k) - S0y[k];
+    }
+#pragma unroll
+    for (int b = 0; b < P + 2; b++) {
+        const R ry = fx * (S0y[b] + R(0.5) * DSy[b]);
+        R run = R(0);
+#pragma unroll
+        for (int a = 0; a <= P; a++) {
+            run -= DSx[a] * ry;
+            add(0, ox + a, oy + b, run);
+        }
+    }
+#pragma unroll
+    for (int a = 0; a < P + 2; a++) {
+        const R rx = fy * (S0x[a] + R(0.5) * DSx[a]);
+        R run = R(0);
+#pragma unroll
+        for (int b = 0; b <= P; b++) {
+            run -= DSy[b] * rx;
+            add(1, ox + a, oy + b, run);
+        }
+    }
+#pragma unroll
+    for (int b = 0; b < P + 2; b++) {
+        const R cy0 = fz * (S0y[b] + R(0.5) * DSy[b]);
+        const R cy1 = fz * (R(0.5) * S0y[b] + R(1.0 / 3.0) * DSy[b]);
+#pragma unroll
+        for (int a = 0; a < P + 2; a++) add(2, ox + a, oy + b, S0x[a] * cy0 + DSx[a] * cy1);
+    }
+}
+
+}  // namespace pic

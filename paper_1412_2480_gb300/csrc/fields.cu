@@ -1,0 +1,396 @@
+// fields.cu -- the implicit field solve of the particle cycle, FP64 throughout:
+//   right-hand side of Eq. (7), PCG iterations on [1 - (theta c dt)^2 Lap] dB = b, and
+//   the E, B update from Eqs. (5)-(6).
+//
+// One thread per cell handles the three components of every vector. Reductions use
+// per-block partials and a "last block finishes" step per simulation (fixed summation
+// order, so results do not depend on block scheduling); the last simulation to finish
+// sets the WHILE condition of the captured PCG loop, so the loop runs exactly as many
+// iterations as the slowest simulation needs, with no host round trip.
+//
+// Staggering (Sec. 2, Fig. 1; index k = j*nx + i): Ez at (i,j); Ex, By at (i+1/2,j);
+// Ey, Bx at (i,j+1/2); Bz at (i+1/2,j+1/2). J shares the E lattices.
+#include "engine.h"
+
+namespace pic {
+
+namespace {
+
+struct Cell {
+    int g, i, j;
+    long long k;   // global cell index (cell_off + j*nx + i)
+    long long ke, kw, kn, ks;  // neighbours (i+1), (i-1), (j+1), (j-1), wrapped
+    bool valid;
+};
+
+__device__ __forceinline__ Cell locate(const GridDev* grids, const int* blk_grid) {
+    Cell c;
+    c.g = blk_grid[blockIdx.x];
+    const GridDev& G = grids[c.g];
+    const int local = (blockIdx.x - G.blk_first) * blockDim.x + threadIdx.x;
+    c.valid = local < G.ncell;
+    const int l = c.valid ? local : 0;
+    c.j = l / G.nx;
+    c.i = l - c.j * G.nx;
+    const long long row = G.cell_off + (long long)c.j * G.nx;
+    c.k = row + c.i;
+    c.ke = row + (c.i + 1 == G.nx ? 0 : c.i + 1);
+    c.kw = row + (c.i == 0 ? G.nx - 1 : c.i - 1);
+    const int jn = c.j + 1 == G.ny ? 0 : c.j + 1;
+    const int js = c.j == 0 ? G.ny - 1 : c.j - 1;
+    c.kn = G.cell_off + (long long)jn * G.nx + c.i;
+    c.ks = G.cell_off + (long long)js * G.nx + c.i;
+    return c;
+}
+
+template <typename T>
+__device__ __forceinline__ double ld(const T* p, long long k) {
+    return (double)p[k];
+}
+
+// Sum `nv` values per thread over the block, store them as this block's partials, and
+// return true in every thread of the block that completes its simulation last. The
+// finishing block then holds the simulation-wide sums in `tot`.
+template <int NV>
+__device__ bool reduce_and_finish(const GridDev& G, int g, double v[NV], double* part,
+                                  int nblk_total, unsigned int* done, double tot[NV]) {
+    __shared__ double scratch[32];
+    __shared__ bool last;
+#pragma unroll
+    for (int a = 0; a < NV; a++) {
+        const double s = block_sum(v[a], scratch);
+        if (threadIdx.x == 0) part[a * nblk_total + blockIdx.x] = s;
+    }
+    if (threadIdx.x == 0) {
+        __threadfence();
+        const unsigned t = atomicAdd(&done[g], 1u);
+        last = (t == (unsigned)G.nblk - 1u);
+    }
+    __syncthreads();
+    if (!last) return false;
+    __threadfence();
+#pragma unroll
+    for (int a = 0; a < NV; a++) {
+        double acc = 0.0;
+        for (int b = threadIdx.x; b < G.nblk; b += blockDim.x)
+            acc += __ldcg(&part[a * nblk_total + G.blk_first + b]);
+        tot[a] = block_sum(acc, scratch);
+    }
+    if (threadIdx.x == 0) done[g] = 0u;
+    return true;
+}
+
+// Called by the finishing block of each simulation after it updated cg[g]: the last
+// simulation to finish counts the simulations still iterating and sets the condition.
+__device__ void finish_all_grids(int ngrids, int n_participating, CgState* cg, DevStatus* st,
+                                 cudaGraphConditionalHandle cond, int use_cond) {
+    if (threadIdx.x != 0) return;
+    __threadfence();
+    const unsigned t = atomicAdd(&st->grids_done, 1u);
+    if (t != (unsigned)n_participating - 1u) return;
+    __threadfence();
+    unsigned n = 0;
+    for (int g = 0; g < ngrids; g++) n += (unsigned)__ldcg(&cg[g].active);
+    st->n_active = n;
+    st->grids_done = 0u;
+    if (use_cond) cudaGraphSetConditional(cond, n > 0u ? 1u : 0u);
+}
+
+// ---- Eq. (7) right-hand side --------------------------------------------------------
+// b = theta (c dt)^2 (Lap B^n + (4 pi / c) curl J^{n+1/2}) - c dt curl E^n  (c = 1)
+// Initial residual r = b - A x0 (x0 = previous dB with warm start, else 0), p = r.
+template <typename JT>
+__global__ void __launch_bounds__(kFieldThreads)
+k_rhs(const GridDev* __restrict__ grids, const int* __restrict__ blk_grid, int ngrids,
+      int nblk_total, long long ntot, const double* __restrict__ F, const JT* __restrict__ J,
+      double* __restrict__ x, double* __restrict__ r, CgState* cg, double* part,
+      unsigned int* done, DevStatus* st, cudaGraphConditionalHandle cond, int use_cond) {
+    const Cell c = locate(grids, blk_grid);
+    const GridDev& G = grids[c.g];
+    double v[4] = {0.0, 0.0, 0.0, 0.0};  // b.b, r.r, |E|^2, |B|^2
+    if (c.valid && !st->stop) {
+        const double* Ex = F;
+        const double* Ey = F + ntot;
+        const double* Ez = F + 2 * ntot;
+        const JT* Jx = J;
+        const JT* Jy = J + ntot;
+        const JT* Jz = J + 2 * ntot;
+        const double th_dt2 = G.theta * G.dt * G.dt;
+        const double idx = G.idx, idy = G.idy;
+        // curl E and curl J on the B lattices
+        const double ez = Ez[c.k];
+        const double cEx = (Ez[c.kn] - ez) * idy;
+        const double cEy = -(Ez[c.ke] - ez) * idx;
+        const double cEz = (Ey[c.ke] - Ey[c.k]) * idx - (Ex[c.kn] - Ex[c.k]) * idy;
+        const double jz = ld(Jz, c.k);
+        const double cJx = (ld(Jz, c.kn) - jz) * idy;
+        const double cJy = -(ld(Jz, c.ke) - jz) * idx;
+        const double cJz = (ld(Jy, c.ke) - ld(Jy, c.k)) * idx - (ld(Jx, c.kn) - ld(Jx, c.k)) * idy;
+        const double cE[3] = {cEx, cEy, cEz};
+        const double cJ[3] = {cJx, cJy, cJz};
+        const double idx2 = idx * idx, idy2 = idy * idy;
+#pragma unroll
+        for (int a = 0; a < 3; a++) {
+            const double* B = F + (3 + a) * ntot;
+            const double bc = B[c.k];
+            const double lap = (B[c.ke] - 2.0 * bc + B[c.kw]) * idx2 +
+                               (B[c.kn] - 2.0 * bc + B[c.ks]) * idy2;
+            const double b = th_dt2 * (lap + 4.0 * kPi * cJ[a]) - G.dt * cE[a];
+            double res = b;
+            const long long o = a * ntot;
+            if (G.warm) {
+                const double* X = x + o;
+                const double Ax = G.c0 * X[c.k] - G.cx * (X[c.ke] + X[c.kw]) -
+                                  G.cy * (X[c.kn] + X[c.ks]);
+                res = b - Ax;
+            }
+            r[o + c.k] = res;
+            v[0] += b * b;
+            v[1] += res * res;
+            v[3] += bc * bc;
+        }
+        v[2] = Ex[c.k] * Ex[c.k] + Ey[c.k] * Ey[c.k] + ez * ez;
+    }
+    double tot[4];
+    if (!reduce_and_finish<4>(G, c.g, v, part, nblk_total, done, tot)) return;
+    if (threadIdx.x == 0) {
+        CgState& s = cg[c.g];
+        const double e = G.dx * G.dy / (8.0 * kPi);
+        s.ue = tot[2] * e;
+        s.ub = tot[3] * e;
+        s.bb = tot[0];
+        s.rr = tot[1];
+        s.beta = 0.0;
+        s.iters = 0;
+        s.rel = tot[0] > 0.0 ? sqrt(tot[1] / tot[0]) : 0.0;
+        s.active = (!st->stop && tot[0] > 0.0 && s.rel > G.rtol) ? 1 : 0;
+    }
+    finish_all_grids(ngrids, ngrids, cg, st, cond, use_cond);
+}
+
+// Zero the solution where the warm start is off (x0 = 0). Separate from k_rhs because
+// k_rhs reads x at neighbours when warm starting.
+__global__ void __launch_bounds__(kFieldThreads)
+k_zero_x(const GridDev* __restrict__ grids, const int* __restrict__ blk_grid, long long ntot,
+         double* __restrict__ x) {
+    const Cell c = locate(grids, blk_grid);
+    if (!c.valid || grids[c.g].warm) return;
+    x[c.k] = 0.0;
+    x[ntot + c.k] = 0.0;
+    x[2 * ntot + c.k] = 0.0;
+}
+
+// ---- PCG iteration, part 1 ------------------------------------------------------
+// With the Jacobi preconditioner of a constant-coefficient operator (diagonal c0), the
+// preconditioned iterates equal plain CG's, so z = r is used. The A-product of the new
+// direction p = r + beta p_old is formed as A r + beta (A p_old): A is linear, so this
+// equals A p while touching only r at neighbours.
+__global__ void __launch_bounds__(kFieldThreads)
+k_cg_direction(const GridDev* __restrict__ grids, const int* __restrict__ blk_grid, int ngrids,
+               int nblk_total, long long ntot, const double* __restrict__ r,
+               double* __restrict__ p, double* __restrict__ q, CgState* cg, double* part,
+               unsigned int* done) {
+    const int g = blk_grid[blockIdx.x];
+    if (!cg[g].active) return;
+    const Cell c = locate(grids, blk_grid);
+    const GridDev& G = grids[c.g];
+    const double beta = cg[g].beta;
+    double v[1] = {0.0};
+    if (c.valid) {
+#pragma unroll
+        for (int a = 0; a < 3; a++) {
+            const long long o = a * ntot;
+            const double* R = r + o;
+            const double rc = R[c.k];
+            const double Ar = G.c0 * rc - G.cx * (R[c.ke] + R[c.kw]) - G.cy * (R[c.kn] + R[c.ks]);
+            double pn, qn;
+            if (beta == 0.0) {
+                pn = rc;
+                qn = Ar;
+            } else {
+                pn = rc + beta * p[o + c.k];
+                qn = Ar + beta * q[o + c.k];
+            }
+            p[o + c.k] = pn;
+            q[o + c.k] = qn;
+            v[0] += pn * qn;
+        }
+    }
+    double tot[1];
+    if (!reduce_and_finish<1>(G, g, v, part, nblk_total, done, tot)) return;
+    if (threadIdx.x == 0) cg[g].alpha = cg[g].rr / tot[0];
+}
+
+// ---- PCG iteration, part 2 ------------------------------------------------------
+// x += alpha p; r -= alpha A p; convergence test ||r|| <= rtol ||b||.
+__global__ void __launch_bounds__(kFieldThreads)
+k_cg_update(const GridDev* __restrict__ grids, const int* __restrict__ blk_grid, int ngrids,
+            int nblk_total, long long ntot, double* __restrict__ x, double* __restrict__ r,
+            const double* __restrict__ p, const double* __restrict__ q, CgState* cg,
+            double* part, unsigned int* done, DevStatus* st, cudaGraphConditionalHandle cond,
+            int use_cond) {
+    const int g = blk_grid[blockIdx.x];
+    const unsigned n_part = st->n_active;  // simulations iterating in this launch
+    if (!cg[g].active) return;
+    const Cell c = locate(grids, blk_grid);
+    const GridDev& G = grids[c.g];
+    const double alpha = cg[g].alpha;
+    double v[1] = {0.0};
+    if (c.valid) {
+#pragma unroll
+        for (int a = 0; a < 3; a++) {
+            const long long o = a * ntot + c.k;
+            x[o] += alpha * p[o];
+            const double rn = r[o] - alpha * q[o];
+            r[o] = rn;
+            v[0] += rn * rn;
+        }
+    }
+    double tot[1];
+    if (!reduce_and_finish<1>(G, g, v, part, nblk_total, done, tot)) return;
+    if (threadIdx.x == 0) {
+        CgState& s = cg[g];
+        s.beta = tot[0] / s.rr;
+        s.rr = tot[0];
+        s.iters += 1;
+        s.rel = sqrt(tot[0] / s.bb);
+        if (s.rel <= G.rtol) {
+            s.active = 0;
+        } else if (s.iters >= G.maxit) {
+            s.active = 0;
+            atomicAdd(&st->cg_noconv, 1u);
+            st->stop_next = 1u;
+        }
+    }
+    finish_all_grids(ngrids, (int)n_part, cg, st, cond, use_cond);
+}
+
+// ---- Field update, Eqs. (5)-(6) --------------------------------------------------
+// E^{n+1} = E^n + c dt curl(B^n + theta dB) - 4 pi dt J^{n+1/2}; the curl of a
+// B-lattice vector lands on the E lattices.
+template <typename JT>
+__global__ void __launch_bounds__(kFieldThreads)
+k_update_E(const GridDev* __restrict__ grids, const int* __restrict__ blk_grid, long long ntot,
+           double* __restrict__ F, const JT* __restrict__ J, const double* __restrict__ x,
+           const CgState* __restrict__ cg, const DevStatus* st) {
+    const Cell c = locate(grids, blk_grid);
+    if (!c.valid || st->stop) return;
+    const GridDev& G = grids[c.g];
+    const double th = cg[c.g].bb > 0.0 ? G.theta : 0.0;  // dB = 0 when b = 0
+    const double* Bx = F + 3 * ntot;
+    const double* By = F + 4 * ntot;
+    const double* Bz = F + 5 * ntot;
+    const double* Xx = x;
+    const double* Xy = x + ntot;
+    const double* Xz = x + 2 * ntot;
+    auto hx = [&](long long k) { return Bx[k] + th * Xx[k]; };
+    auto hy = [&](long long k) { return By[k] + th * Xy[k]; };
+    auto hz = [&](long long k) { return Bz[k] + th * Xz[k]; };
+    const double hzc = hz(c.k);
+    const double cx = (hzc - hz(c.ks)) * G.idy;
+    const double cy = -(hzc - hz(c.kw)) * G.idx;
+    const double cz = (hy(c.k) - hy(c.kw)) * G.idx - (hx(c.k) - hx(c.ks)) * G.idy;
+    const double f = 4.0 * kPi * G.dt;
+    F[c.k] += G.dt * cx - f * ld(J, c.k);
+    F[ntot + c.k] += G.dt * cy - f * ld(J, ntot + c.k);
+    F[2 * ntot + c.k] += G.dt * cz - f * ld(J, 2 * ntot + c.k);
+}
+
+// B^{n+1} = B^n + dB, then the FP32 copies used by the MIXED32 gather.
+__global__ void __launch_bounds__(kFieldThreads)
+k_update_B(const GridDev* __restrict__ grids, const int* __restrict__ blk_grid, long long ntot,
+           double* __restrict__ F, const double* __restrict__ x, const CgState* __restrict__ cg,
+           const DevStatus* st, float* __restrict__ F32) {
+    const Cell c = locate(grids, blk_grid);
+    if (!c.valid || st->stop) return;
+    const bool have = cg[c.g].bb > 0.0;
+#pragma unroll
+    for (int a = 0; a < 3; a++) {
+        const long long o = (3 + a) * ntot + c.k;
+        const double b = F[o] + (have ? x[a * ntot + c.k] : 0.0);
+        F[o] = b;
+        if (F32) F32[o] = (float)b;
+    }
+    if (F32) {
+#pragma unroll
+        for (int a = 0; a < 3; a++) F32[a * ntot + c.k] = (float)F[a * ntot + c.k];
+    }
+}
+
+__global__ void __launch_bounds__(kFieldThreads)
+k_to_f32(const GridDev* __restrict__ grids, const int* __restrict__ blk_grid, long long ntot,
+         const double* __restrict__ F, float* __restrict__ F32) {
+    const Cell c = locate(grids, blk_grid);
+    if (!c.valid) return;
+#pragma unroll
+    for (int a = 0; a < 6; a++) F32[a * ntot + c.k] = (float)F[a * ntot + c.k];
+}
+
+// Start of a step: an error raised during the previous step stops this one; clear the
+// per-step kinetic-energy accumulators.
+__global__ void k_step_begin(int ngrids, CgState* cg, DevStatus* st) {
+    if (threadIdx.x == 0) {
+        if (st->stop_next) st->stop = 1u;
+        if (!st->stop) st->steps_done += 1ull;
+        st->leaver_count = 0ull;
+    }
+    for (int g = threadIdx.x; g < ngrids; g += blockDim.x) cg[g].uk = 0.0;
+}
+
+// End of a step: PCG statistics.
+__global__ void k_step_end(int ngrids, CgState* cg, const DevStatus* st) {
+    if (st->stop) return;
+    for (int g = threadIdx.x; g < ngrids; g += blockDim.x) {
+        CgState& s = cg[g];
+        s.last_iters = s.iters;
+        s.max_iters = s.iters > s.max_iters ? s.iters : s.max_iters;
+        s.total_iters += s.iters;
+    }
+}
+
+}  // namespace
+
+void launch_step_begin(const FieldArgs& a, cudaStream_t s) {
+    k_step_begin<<<1, 128, 0, s>>>(a.ngrids, a.cg, a.st);
+}
+
+void launch_step_end(const FieldArgs& a, cudaStream_t s) {
+    k_step_end<<<1, 128, 0, s>>>(a.ngrids, a.cg, a.st);
+}
+
+void launch_rhs(const FieldArgs& a, cudaStream_t s) {
+    k_zero_x<<<a.nblk, kFieldThreads, 0, s>>>(a.grids, a.blk_grid, a.ntot, a.x);
+    if (a.J32)
+        k_rhs<float><<<a.nblk, kFieldThreads, 0, s>>>(a.grids, a.blk_grid, a.ngrids, a.nblk,
+                                                      a.ntot, a.F, a.J32, a.x, a.r, a.cg,
+                                                      a.part, a.done, a.st, a.cond, a.use_cond);
+    else
+        k_rhs<double><<<a.nblk, kFieldThreads, 0, s>>>(a.grids, a.blk_grid, a.ngrids, a.nblk,
+                                                       a.ntot, a.F, a.J64, a.x, a.r, a.cg,
+                                                       a.part, a.done, a.st, a.cond, a.use_cond);
+}
+
+void launch_cg_iteration(const FieldArgs& a, cudaStream_t s) {
+    k_cg_direction<<<a.nblk, kFieldThreads, 0, s>>>(a.grids, a.blk_grid, a.ngrids, a.nblk,
+                                                    a.ntot, a.r, a.p, a.q, a.cg, a.part, a.done);
+    k_cg_update<<<a.nblk, kFieldThreads, 0, s>>>(a.grids, a.blk_grid, a.ngrids, a.nblk, a.ntot,
+                                                 a.x, a.r, a.p, a.q, a.cg, a.part, a.done, a.st,
+                                                 a.cond, a.use_cond);
+}
+
+void launch_field_update(const FieldArgs& a, cudaStream_t s) {
+    if (a.J32)
+        k_update_E<float><<<a.nblk, kFieldThreads, 0, s>>>(a.grids, a.blk_grid, a.ntot, a.F,
+                                                           a.J32, a.x, a.cg, a.st);
+    else
+        k_update_E<double><<<a.nblk, kFieldThreads, 0, s>>>(a.grids, a.blk_grid, a.ntot, a.F,
+                                                            a.J64, a.x, a.cg, a.st);
+    k_update_B<<<a.nblk, kFieldThreads, 0, s>>>(a.grids, a.blk_grid, a.ntot, a.F, a.x, a.cg,
+                                                a.st, a.F32);
+}
+
+void launch_fields_to_f32(const FieldArgs& a, cudaStream_t s) {
+    if (a.F32) k_to_f32<<<a.nblk, kFieldThreads, 0, s>>>(a.grids, a.blk_grid, a.ntot, a.F, a.F32);
+}
+
+}  // namespace pic

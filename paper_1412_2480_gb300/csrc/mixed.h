@@ -1,0 +1,35 @@
+// mixed.h -- the MIXED32 particle half (int cell + FP32 offset, FP32 gather/push/deposit,
+// tile-binned particles with shared-memory field and current windows).
+#pragma once
+
+#include <cuda_runtime.h>
+
+#include <string>
+
+#include "pic.h"
+#include "pic_internal.cuh"
+
+namespace pic {
+
+struct MixedState;
+
+// Choose tiles and allocate bins for the single simulation G (fills G's tile fields).
+int mixed_create(MixedState** out, const pic_params& p, GridDev& G, const GridDev* dgrids,
+                 long long ntot, float* F32, float* J32, CgState* cg, DevStatus* st,
+                 std::string& err);
+void mixed_destroy(MixedState* m);
+// Replace one species' particles (FP64 physical positions and momenta, host or device).
+int mixed_load(MixedState* m, int sp, const double* x, const double* y, const double* ux,
+               const double* uy, const double* uz, long long n, cudaStream_t s, std::string& err);
+// Enqueue the particle half of one step (J32 already zeroed).
+void mixed_enqueue_step(MixedState* m, cudaStream_t s);
+// Host bookkeeping around a pic_step call (re-sort when bins overflowed).
+int mixed_before_steps(MixedState* m, cudaStream_t s, std::string& err);
+int mixed_after_steps(MixedState* m, cudaStream_t s, std::string& err);
+long long mixed_count(MixedState* m, int sp);
+long long mixed_rebins(MixedState* m);
+// Copy out one species as FP64 [x, y, ux, uy, uz] (physical units), tile order.
+int mixed_particles(MixedState* m, int sp, double* out5xn, long long n, cudaStream_t s,
+                    std::string& err);
+
+}  // namespace pic

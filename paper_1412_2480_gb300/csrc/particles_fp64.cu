@@ -1,0 +1,132 @@
+// particles_fp64.cu -- the plain FP64 particle half of the step: one thread per particle
+// gathers E^n, B^n straight from the FP64 grid arrays, pushes, moves, and deposits
+// J^{n+1/2} with FP64 global atomics. No sorting, no shared-memory tiles: this is the
+// reference GPU form that the MIXED32 tiled path is measured against.
+//
+// Positions are kept in grid units (x/dx, y/dy) in [0, nx) x [0, ny).
+#include "engine.h"
+#include "esirkepov.cuh"
+
+namespace pic {
+namespace {
+
+// Momentum-conserving gather (Sec. 1, Sec. 3): each component is interpolated with the
+// order-P shape on its own staggered lattice, the same weights that assign charge.
+template <int P>
+__device__ __forceinline__ double gather(const double* __restrict__ A, int nx, const int col[P + 1],
+                                         const double wx[P + 1], const int row[P + 1],
+                                         const double wy[P + 1]) {
+    double acc = 0.0;
+#pragma unroll
+    for (int b = 0; b <= P; b++) {
+        const double* R = A + row[b];
+        double ra = 0.0;
+#pragma unroll
+        for (int a = 0; a <= P; a++) ra += wx[a] * __ldg(R + col[a]);
+        acc += wy[b] * ra;
+    }
+    return acc;
+}
+
+template <int P>
+__global__ void __launch_bounds__(kPushThreads)
+k_push_fp64(const GridDev* __restrict__ grids, const SegDev* __restrict__ segs,
+            const int* __restrict__ blk_seg, long long ntot, const double* __restrict__ F,
+            double* __restrict__ J, double* __restrict__ xs, double* __restrict__ ys,
+            double* __restrict__ uxs, double* __restrict__ uys, double* __restrict__ uzs,
+            CgState* cg, DevStatus* st) {
+    if (st->stop) return;
+    const SegDev S = segs[blk_seg[blockIdx.x]];
+    const GridDev& G = grids[S.grid];
+    const long long local = (long long)(blockIdx.x - S.blk_first) * blockDim.x + threadIdx.x;
+    double ek = 0.0;
+    if (local < S.count) {
+        const long long k = S.start + local;
+        const int nx = G.nx, ny = G.ny;
+        const double X = xs[k], Y = ys[k];
+        const int i = (int)floor(X), j = (int)floor(Y);
+        const double fxp = X - i, fyp = Y - j;
+        int bx0, bxh, by0, byh;
+        double wx0[P + 1], wxh[P + 1], wy0[P + 1], wyh[P + 1];
+        shape_nodes<P, double>(i, fxp, bx0, wx0);
+        shape_nodes_half<P, double>(i, fxp, bxh, wxh);
+        shape_nodes<P, double>(j, fyp, by0, wy0);
+        shape_nodes_half<P, double>(j, fyp, byh, wyh);
+        int c0[P + 1], ch[P + 1], r0[P + 1], rh[P + 1];
+#pragma unroll
+        for (int a = 0; a <= P; a++) {
+            c0[a] = wrapi(bx0 + a, nx);
+            ch[a] = wrapi(bxh + a, nx);
+            r0[a] = wrapi(by0 + a, ny) * nx;
+            rh[a] = wrapi(byh + a, ny) * nx;
+        }
+        const double* base = F + G.cell_off;
+        // Ex (i+1/2, j), Ey (i, j+1/2), Ez (i, j), Bx (i, j+1/2), By (i+1/2, j), Bz (i+1/2, j+1/2)
+        const double E[3] = {gather<P>(base, nx, ch, wxh, r0, wy0),
+                             gather<P>(base + ntot, nx, c0, wx0, rh, wyh),
+                             gather<P>(base + 2 * ntot, nx, c0, wx0, r0, wy0)};
+        const double B[3] = {gather<P>(base + 3 * ntot, nx, c0, wx0, rh, wyh),
+                             gather<P>(base + 4 * ntot, nx, ch, wxh, r0, wy0),
+                             gather<P>(base + 5 * ntot, nx, ch, wxh, rh, wyh)};
+        double u[3] = {uxs[k], uys[k], uzs[k]};
+        const double g_old = sqrt(1.0 + u[0] * u[0] + u[1] * u[1] + u[2] * u[2]);
+        const double qm = G.qm[S.species];
+        boris<double>(0.5 * qm * G.dt, E, B, u);
+        const double gam = sqrt(1.0 + u[0] * u[0] + u[1] * u[1] + u[2] * u[2]);
+        const double dX = G.dt * u[0] / gam * G.idx;
+        const double dY = G.dt * u[1] / gam * G.idy;
+        if (!(fabs(dX) < 1.0 && fabs(dY) < 1.0)) {
+            if (!isfinite(dX + dY)) atomicAdd(&st->nan_count, 1ull);
+            else atomicAdd(&st->cfl_viol, 1ull);
+            st->stop_next = 1u;
+        } else {
+            double X1 = X + dX, Y1 = Y + dY;
+            if (G.deposit) {
+                const int i1 = (int)floor(X1), j1 = (int)floor(Y1);
+                const double area = G.dx * G.dy;
+                const double q = G.qw[S.species];
+                double* Jb = J + G.cell_off;
+                esirkepov<P, double>(i, fxp, j, fyp, i1, X1 - i1, j1, Y1 - j1,
+                                     q * G.dx / (G.dt * area), q * G.dy / (G.dt * area),
+                                     q * (u[2] / gam) / area,
+                                     [&](int comp, int ix, int iy, double v) {
+                                         atomicAdd(Jb + comp * ntot + (long long)wrapi(iy, ny) * nx +
+                                                       wrapi(ix, nx),
+                                                   v);
+                                     });
+            }
+            // periodic wrap (Sec. 3)
+            if (X1 < 0.0) X1 += nx;
+            if (X1 >= nx) X1 -= nx;
+            if (X1 >= nx) X1 = 0.0;
+            if (Y1 < 0.0) Y1 += ny;
+            if (Y1 >= ny) Y1 -= ny;
+            if (Y1 >= ny) Y1 = 0.0;
+            xs[k] = X1;
+            ys[k] = Y1;
+        }
+        uxs[k] = u[0];
+        uys[k] = u[1];
+        uzs[k] = u[2];
+        ek = G.w * (0.5 * (g_old + gam) - 1.0);
+    }
+    __shared__ double scratch[32];
+    const double s = block_sum(ek, scratch);
+    if (threadIdx.x == 0 && s != 0.0) atomicAdd(&cg[S.grid].uk, s);
+}
+
+}  // namespace
+
+void launch_push_fp64(const Fp64PushArgs& a, int order, cudaStream_t s) {
+    if (a.nblk == 0) return;
+#define PIC_PUSH_ARGS                                                                      \
+    a.grids, a.segs, a.blk_seg, a.ntot, a.F, a.J, a.x, a.y, a.ux, a.uy, a.uz, a.cg, a.st
+    switch (order) {
+    case 1: k_push_fp64<1><<<a.nblk, kPushThreads, 0, s>>>(PIC_PUSH_ARGS); break;
+    case 2: k_push_fp64<2><<<a.nblk, kPushThreads, 0, s>>>(PIC_PUSH_ARGS); break;
+    default: k_push_fp64<3><<<a.nblk, kPushThreads, 0, s>>>(PIC_PUSH_ARGS); break;
+    }
+#undef PIC_PUSH_ARGS
+}
+
+}  // namespace pic

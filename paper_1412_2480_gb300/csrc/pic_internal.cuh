@@ -1,0 +1,153 @@
+// pic_internal.cuh -- device-side data structures and helpers of the GB300 PIC library.
+//
+// Everything a kernel needs to know about one simulation lives in GridDev; several
+// simulations can share one launch (the batched parameter scan), so every kernel maps
+// its block to a simulation through a small table instead of assuming one grid.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+namespace pic {
+
+constexpr double kPi = 3.14159265358979323846;
+constexpr int kFieldThreads = 256;  // threads per block of the grid (field) kernels
+constexpr int kPushThreads = 256;   // threads per block of the FP64 particle kernel
+constexpr int kMaxWinCells = 6144;  // largest tile window (cells) of the MIXED32 kernel
+
+// One simulation, as the kernels see it. Grid arrays of all simulations are
+// concatenated; cell_off is this simulation's first cell.
+struct GridDev {
+    int nx, ny, order, ncell;
+    double dx, dy, dt, theta;
+    double idx, idy;      // 1/dx, 1/dy
+    double a;             // (theta dt)^2, the coefficient of Eq. (7)
+    double c0, cx, cy;    // A v = c0 v - cx (v_e + v_w) - cy (v_n + v_s)
+    long long cell_off;
+    int blk_first, nblk;  // this simulation's blocks in field-kernel launches
+    double qw[2], qm[2];  // charge per macro-particle and charge-to-mass sign per species
+    double w;             // macro weight (mass per macro-particle)
+    double rtol;
+    int maxit, warm;
+    int deposit;          // 0 in test-particle mode
+    // MIXED32 tiling
+    int tx, ty, ntx, nty; // tile size and tile counts
+    int tile_first, ntiles;
+    int wx, wy;           // tile window size: (tx + 5) x (ty + 5), origin (X0-2, Y0-2)
+    long long cap;        // bin capacity (particles) per (tile, species)
+    long long bin_off;    // first particle slot of this simulation's bins
+};
+
+// Per-simulation state of the PCG solve of Eq. (7).
+struct CgState {
+    double bb, rr, pq, alpha, beta, rel;
+    double ue, ub, uk;    // energies of the step being computed (time level n)
+    int active, iters, last_iters, max_iters;
+    long long total_iters;
+};
+
+// Device status words shared by all kernels of a handle.
+struct DevStatus {
+    unsigned long long cfl_viol;     // moves of >= 1 cell
+    unsigned long long nan_count;    // non-finite momenta or positions
+    unsigned long long overflow;     // MIXED32: particles sent through the overflow path
+    unsigned int cg_noconv;          // PCG hit maxit
+    unsigned int stop;               // nonzero: this and later steps of the call are skipped
+    unsigned int stop_next;          // set during a step; becomes `stop` at the next step
+    unsigned long long steps_done;   // steps completed (the failing step included)
+    unsigned int grids_done;         // counter of the last-grid-finished pattern
+    unsigned int n_active;           // simulations whose PCG is still iterating
+    unsigned long long leaver_count; // MIXED32: leavers queued this step
+    unsigned long long overflow_count; // MIXED32: particles in the overflow list
+    unsigned long long leaver_full;  // MIXED32: leavers kept in place (queue full)
+};
+
+// One contiguous range of FP64 particles of one species in one simulation.
+struct SegDev {
+    long long start, count;
+    int grid, species, blk_first, nblk;
+};
+
+// ---------------------------------------------------------------------------------
+// Particle shapes: centred B-splines of order P. Given a coordinate split into an
+// integer cell i and a fraction f in [0,1) on a lattice whose node k sits at k, return
+// the first node `base` and the P+1 weights of nodes base .. base+P.
+// ---------------------------------------------------------------------------------
+template <int P, typename R>
+__device__ __forceinline__ void shape_nodes(int i, R f, int& base, R w[P + 1]) {
+    if constexpr (P == 1) {
+        base = i;
+        w[0] = R(1) - f;
+        w[1] = f;
+    } else if constexpr (P == 2) {
+        // nearest node c = i (f < 1/2) or i+1; d = x - c in [-1/2, 1/2)
+        R d;
+        if (f < R(0.5)) {
+            base = i - 1;
+            d = f;
+        } else {
+            base = i;
+            d = f - R(1);
+        }
+        const R hm = R(0.5) - d, hp = R(0.5) + d;
+        w[0] = R(0.5) * hm * hm;
+        w[1] = R(0.75) - d * d;
+        w[2] = R(0.5) * hp * hp;
+    } else {
+        base = i - 1;
+        const R g = R(1) - f;
+        const R f2 = f * f, f3 = f2 * f;
+        w[0] = g * g * g * R(1.0 / 6.0);
+        w[1] = (R(4) - R(6) * f2 + R(3) * f3) * R(1.0 / 6.0);
+        w[2] = (R(1) + R(3) * (f + f2 - f3)) * R(1.0 / 6.0);
+        w[3] = f3 * R(1.0 / 6.0);
+    }
+}
+
+// Same, on the lattice shifted by +1/2 (nodes at k + 1/2, stored at index k).
+template <int P, typename R>
+__device__ __forceinline__ void shape_nodes_half(int i, R f, int& base, R w[P + 1]) {
+    R s = f - R(0.5);
+    int c = i;
+    if (s < R(0)) {
+        s += R(1);
+        c -= 1;
+        if (s >= R(1)) {  // s was a tiny negative number and s + 1 rounded up to 1
+            s = R(0);
+            c += 1;
+        }
+    }
+    shape_nodes<P, R>(c, s, base, w);
+}
+
+// Periodic wrap of a lattice index that is at most a few cells out of range.
+__device__ __forceinline__ int wrapi(int k, int n) {
+    k = (k < 0) ? k + n : k;
+    return (k >= n) ? k - n : k;
+}
+
+// ---------------------------------------------------------------------------------
+// Reductions
+// ---------------------------------------------------------------------------------
+template <typename T>
+__device__ __forceinline__ T warp_sum(T v) {
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+    return v;
+}
+
+// Block-wide sum; the result is valid in every thread. `scratch` holds >= 32 T.
+template <typename T>
+__device__ __forceinline__ T block_sum(T v, T* scratch) {
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+    const int nw = (blockDim.x + 31) >> 5;
+    v = warp_sum(v);
+    __syncthreads();
+    if (lane == 0) scratch[wid] = v;
+    __syncthreads();
+    T r = (lane < nw) ? scratch[lane] : T(0);
+    r = warp_sum(r);
+    return r;
+}
+
+}  // namespace pic

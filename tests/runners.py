@@ -1,0 +1,60 @@
+"""Runs the same seeded workload through the CUDA library (C ABI) and through the oracle.
+
+Inputs come only from paper_1412_2480_gb300.inputs; nothing the CUDA path produces is
+ever fed to the oracle."""
+from __future__ import annotations
+
+import numpy as np
+
+import oracle
+import paper_1412_2480_gb300 as pic
+from paper_1412_2480_gb300 import inputs
+
+
+def workload(nx, ny, ppc, gamma0=20.0, u_th=1e-3, seed=1, field_amp=0.0, colocated=True):
+    w, sp = inputs.drifting_pair_plasma(nx, ny, ppc, gamma0, u_th, seed, colocated=colocated)
+    F0 = inputs.random_fields(nx, ny, field_amp, seed) if field_amp else np.zeros((6, ny, nx))
+    return w, sp, F0
+
+
+def run_gpu(nx, ny, ppc, sp, F0, steps, order, cfl=1.0, theta=0.5, gamma0=20.0,
+            precision=pic.PIC_FP64, want_particles=True, **kw):
+    prm = pic.pic_params_default(nx=nx, ny=ny, cfl=cfl, theta=theta, shape_order=order,
+                                 gamma0=gamma0, ppc=ppc, precision=precision, **kw)
+    h = pic.pic_init(prm)
+    try:
+        if np.any(F0):
+            for c in range(6):
+                pic.pic_set_fields(h, c, np.ascontiguousarray(F0[c], dtype=np.float64).ravel())
+        for s in range(len(sp)):
+            d = sp[s]
+            pic.pic_load_particles(h, s, d["x"], d["y"], d["ux"], d["uy"], d["uz"])
+        pic.pic_step(h, steps)
+        F = np.stack([pic.fields_numpy(h, c, nx, ny) for c in range(12)])
+        parts = [pic.pic_particles(h, s) for s in range(len(sp))] if want_particles else None
+        mom = pic.pic_moments(h)
+    finally:
+        pic.pic_free(h)
+    return F, parts, mom
+
+
+def run_oracle(nx, ny, w, sp, F0, steps, order, cfl=1.0, theta=0.5, cg_rtol=1e-10,
+               warm_start="zero", deposit=True):
+    species = [oracle.Species(d["qm"], w, d["x"], d["y"], d["ux"], d["uy"], d["uz"]) for d in sp]
+    sim = oracle.OracleSim(nx, ny, cfl, theta, order, species, cg_rtol=cg_rtol, fields=F0,
+                           warm_start=warm_start, deposit=deposit)
+    sim.step(steps)
+    F = np.concatenate([sim.fields(), sim.J.reshape(3, ny, nx), sim.dB.reshape(3, ny, nx)])
+    parts = [np.stack([s.x, s.y, s.ux, s.uy, s.uz]) for s in sim.species]
+    return F, parts, sim
+
+
+def rel(a, b):
+    nb = np.linalg.norm(b)
+    return float(np.linalg.norm(a - b) / (nb if nb > 0 else 1.0))
+
+
+def periodic_pos_err(a, b, L):
+    """Largest position difference modulo the box length."""
+    d = np.abs(a - b)
+    return float(np.max(np.minimum(d, L - d))) if d.size else 0.0
