@@ -155,6 +155,16 @@ PIC_API int pic_set_fields(pic_sim* s, int32_t which, const double* data, size_t
  * step and pic_moments reports its step count. */
 PIC_API int pic_step(pic_sim* s, int32_t n);
 
+/* Advance n >= 1 steps like pic_step, timing each with CUDA events recorded on the
+ * handle's stream inside the step graph, and synchronising after every step. Writes up
+ * to n_out averages (milliseconds per step unless noted) into out:
+ *   out[0] whole step; out[1] particle half (J reset, push, deposit, migration);
+ *   out[2] the dominant particle kernel alone (the FP64 push kernels, or the MIXED32
+ *          tile kernel); out[3] field solve (rhs of Eq. (7), PCG, Eqs. (5)-(6) update);
+ *   out[4] PCG iterations per step (count, not ms).
+ * Device-detected errors are reported as by pic_step. */
+PIC_API int pic_profile(pic_sim* s, int32_t n, double* out, int32_t n_out);
+
 /* Copy grid quantity `which` (PIC_EX..PIC_DBZ) into out (len >= nx*ny FP64 values,
  * host or device, caller-owned). */
 PIC_API int pic_fields(pic_sim* s, int32_t which, double* out, size_t len);

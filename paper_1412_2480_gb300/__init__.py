@@ -38,7 +38,7 @@ PIC_EX, PIC_EY, PIC_EZ, PIC_BX, PIC_BY, PIC_BZ = range(6)
 PIC_JX, PIC_JY, PIC_JZ, PIC_DBX, PIC_DBY, PIC_DBZ = range(6, 12)
 
 EXPORTED = ("pic_params_default", "pic_init", "pic_set_stream", "pic_load_particles",
-            "pic_set_fields", "pic_step", "pic_fields", "pic_moments", "pic_particle_count",
+            "pic_set_fields", "pic_step", "pic_profile", "pic_fields", "pic_moments", "pic_particle_count",
             "pic_particles", "pic_last_error", "pic_free")
 
 
@@ -88,6 +88,7 @@ def lib():
             L.pic_set_fields.argtypes = [vp, C.c_int32, vp, C.c_size_t]
             L.pic_step.argtypes = [vp, C.c_int32]
             L.pic_fields.argtypes = [vp, C.c_int32, vp, C.c_size_t]
+            L.pic_profile.argtypes = [vp, C.c_int32, C.POINTER(C.c_double), C.c_int32]
             L.pic_moments.argtypes = [vp, C.POINTER(pic_moments_t)]
             L.pic_particle_count.argtypes = [vp, C.c_int32]
             L.pic_particle_count.restype = C.c_int64
@@ -97,7 +98,7 @@ def lib():
             L.pic_free.argtypes = [vp]
             L.pic_free.restype = None
             for name in ("pic_init", "pic_set_stream", "pic_load_particles", "pic_set_fields",
-                         "pic_step", "pic_fields", "pic_moments", "pic_particles"):
+                         "pic_step", "pic_profile", "pic_fields", "pic_moments", "pic_particles"):
                 getattr(L, name).restype = C.c_int
             _lib = L
     return _lib
@@ -168,6 +169,14 @@ def pic_set_fields(h, which, data) -> None:
 
 def pic_step(h, n=1) -> None:
     _check(lib().pic_step(h, int(n)), h)
+
+
+def pic_profile(h, n) -> dict:
+    """Advance n steps with per-phase CUDA-event timing (see include/pic.h)."""
+    out = (C.c_double * 5)()
+    _check(lib().pic_profile(h, int(n), out, 5), h)
+    return {"step_ms": out[0], "particle_ms": out[1], "push_kernel_ms": out[2],
+            "field_ms": out[3], "cg_iters": out[4]}
 
 
 def pic_fields(h, which, out=None, shape=None):

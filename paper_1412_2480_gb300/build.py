@@ -41,6 +41,8 @@ def build(force: bool = False, verbose: bool = False, ptxas_info: bool = False) 
     os.makedirs(BUILD, exist_ok=True)
     nvcc = _nvcc()
     extra = ["-Xptxas", "-v"] if ptxas_info else []
+    # extra nvcc flags for tuning builds, e.g. PIC_NVCC_EXTRA="-DPIC_TILE_MIN_BLOCKS_P2=2"
+    extra += os.environ.get("PIC_NVCC_EXTRA", "").split()
 
     def compile_one(src):
         obj = os.path.join(BUILD, os.path.splitext(src)[0] + ".o")

@@ -38,7 +38,7 @@ struct pic_sim {
     // grid arrays
     double* F = nullptr;    // 6 ntot
     double* J64 = nullptr;  // 3 ntot (FP64)
-    float* J32 = nullptr;   // 3 ntot (MIXED32)
+    long long* Jfix = nullptr;  // 3 ntot fixed-point current (MIXED32)
     float* F32 = nullptr;   // 6 ntot (MIXED32)
     double *x = nullptr, *r = nullptr, *p = nullptr, *q = nullptr;
     double* part = nullptr;
@@ -58,14 +58,20 @@ struct pic_sim {
     // graph
     cudaGraph_t graph = nullptr;
     cudaGraphExec_t gexec = nullptr;
+    // profiling: one graph per part of the step, CUDA events recorded between them
+    cudaEvent_t ev[6] = {nullptr};
+    cudaGraph_t pgraph[5] = {nullptr};
+    cudaGraphExec_t pexec[5] = {nullptr};
     cudaStream_t body_stream = nullptr;
     // bookkeeping
     long long steps = 0;
-    unsigned long long seen_cfl = 0, seen_nan = 0;
+    unsigned long long seen_cfl = 0, seen_nan = 0, seen_lost = 0;
     unsigned int seen_noconv = 0;
 };
 
 namespace {
+
+enum { kPartPre = 0, kPartPush = 1, kPartPost = 2, kPartField = 3, kPartEnd = 4, kNumParts = 5 };
 
 std::string g_init_err;
 
@@ -149,6 +155,13 @@ void fill_grid(const pic_params& p, GridDev& G) {
     G.qm[1] = -1.0;
     G.qw[0] = G.w;
     G.qw[1] = -G.w;
+    // MIXED32 fixed-point current: a single particle adds at most u/2 to one node, with
+    // u = 2 max(q/(dt dy), q/(dt dx), q/(dx dy)); u maps to 2^40, so one unit is 9e-13 u
+    // (far below FP32 rounding) and 2^23 u fits in int64.
+    const double u = 2.0 * G.w * std::max(std::max(1.0 / (G.dt * p.dy), 1.0 / (G.dt * p.dx)),
+                                          1.0 / (p.dx * p.dy));
+    G.jscale = std::ldexp(1.0, 40) / u;
+    G.jinv = 1.0 / G.jscale;
     G.rtol = p.cg_rtol;
     G.maxit = p.cg_max_iter;
     G.warm = p.warm_start == PIC_WS_PREV ? 1 : 0;
@@ -164,7 +177,7 @@ FieldArgs field_args(pic_sim* s, int use_cond, cudaGraphConditionalHandle cond) 
     a.ntot = s->ntot;
     a.F = s->F;
     a.J64 = s->prm.precision == PIC_FP64 ? s->J64 : nullptr;
-    a.J32 = s->prm.precision == PIC_MIXED32 ? s->J32 : nullptr;
+    a.Jfix = s->prm.precision == PIC_MIXED32 ? s->Jfix : nullptr;
     a.F32 = s->F32;
     a.x = s->x;
     a.r = s->r;
@@ -184,89 +197,111 @@ void drop_graph(pic_sim* s) {
     if (s->graph) cudaGraphDestroy(s->graph);
     s->gexec = nullptr;
     s->graph = nullptr;
+    for (int k = 0; k < kNumParts; k++) {
+        if (s->pexec[k]) cudaGraphExecDestroy(s->pexec[k]);
+        if (s->pgraph[k]) cudaGraphDestroy(s->pgraph[k]);
+        s->pexec[k] = nullptr;
+        s->pgraph[k] = nullptr;
+    }
 }
 
-// The particle half of the step.
-void enqueue_particles(pic_sim* s, cudaStream_t st) {
-    if (s->prm.precision == PIC_FP64) {
-        cudaMemsetAsync(s->J64, 0, 3 * s->ntot * sizeof(double), st);
+// The step in five parts: [step_begin, J = 0, (overflow push)] [dominant particle
+// kernel] [migration] [field solve: rhs, PCG loop, E/B update] [step_end].
+void enqueue_part(pic_sim* s, int part, cudaStream_t st) {
+    const FieldArgs a = field_args(s, 0, 0);
+    const bool fp64 = s->prm.precision == PIC_FP64;
+    switch (part) {
+    case kPartPre:
+        launch_step_begin(a, st);
+        if (fp64) cudaMemsetAsync(s->J64, 0, 3 * s->ntot * sizeof(double), st);
+        else cudaMemsetAsync(s->Jfix, 0, 3 * s->ntot * sizeof(long long), st);
+        if (!fp64) mixed_enqueue(s->mixed, st, 0);
+        break;
+    case kPartPush:
+        if (!fp64) {
+            mixed_enqueue(s->mixed, st, 1);
+            break;
+        }
         for (int sp = 0; sp < 2; sp++) {
             if (s->np[sp] == 0) continue;
-            Fp64PushArgs a{};
-            a.grids = s->dgrids;
-            a.segs = s->dsegs + sp;
-            a.blk_seg = s->dblk_seg[sp];
-            a.nblk = s->nblk_push[sp];
-            a.nsegs = 1;
-            a.ntot = s->ntot;
-            a.F = s->F;
-            a.J = s->J64;
-            a.x = s->pa[sp][0];
-            a.y = s->pa[sp][1];
-            a.ux = s->pa[sp][2];
-            a.uy = s->pa[sp][3];
-            a.uz = s->pa[sp][4];
-            a.cg = s->cg;
-            a.st = s->st;
-            launch_push_fp64(a, s->prm.shape_order, st);
+            Fp64PushArgs p{};
+            p.grids = s->dgrids;
+            p.segs = s->dsegs + sp;
+            p.blk_seg = s->dblk_seg[sp];
+            p.nblk = s->nblk_push[sp];
+            p.nsegs = 1;
+            p.ntot = s->ntot;
+            p.F = s->F;
+            p.J = s->J64;
+            p.x = s->pa[sp][0];
+            p.y = s->pa[sp][1];
+            p.ux = s->pa[sp][2];
+            p.uy = s->pa[sp][3];
+            p.uz = s->pa[sp][4];
+            p.cg = s->cg;
+            p.st = s->st;
+            launch_push_fp64(p, s->prm.shape_order, st);
         }
-    } else {
-        cudaMemsetAsync(s->J32, 0, 3 * s->ntot * sizeof(float), st);
-        mixed_enqueue_step(s->mixed, st);
+        break;
+    case kPartPost:
+        if (!fp64) mixed_enqueue(s->mixed, st, 2);
+        break;
+    case kPartEnd:
+        launch_step_end(a, st);
+        break;
+    default:
+        break;
     }
 }
 
-void enqueue_pre(pic_sim* s, cudaStream_t st, int use_cond, cudaGraphConditionalHandle h) {
-    const FieldArgs a = field_args(s, use_cond, h);
-    launch_step_begin(a, st);
-    enqueue_particles(s, st);
-    launch_rhs(a, st);
-}
-
-void enqueue_post(pic_sim* s, cudaStream_t st) {
-    const FieldArgs a = field_args(s, 0, 0);
-    launch_field_update(a, st);
-    launch_step_end(a, st);
-}
-
-int build_graph(pic_sim* s) {
-    drop_graph(s);
+// Capture the parts in `mask` (in order) into one graph. The field-solve part becomes
+// rhs -> WHILE(any simulation active){PCG iteration} -> E/B update, the WHILE condition
+// being set on the device by the rhs and PCG kernels.
+int capture(pic_sim* s, int mask, cudaGraph_t* gout, cudaGraphExec_t* xout) {
     cudaStream_t st = s->stream;
     CK(cudaStreamBeginCapture(st, cudaStreamCaptureModeThreadLocal));
-    cudaStreamCaptureStatus cs;
-    cudaGraph_t cap = nullptr;
-    const cudaGraphNode_t* deps = nullptr;
-    size_t nd = 0;
-    cudaGraphConditionalHandle h{};
-    cudaError_t e = cudaStreamGetCaptureInfo(st, &cs, nullptr, &cap, &deps, nullptr, &nd);
-    if (e == cudaSuccess) e = cudaGraphConditionalHandleCreate(&h, cap, 0, cudaGraphCondAssignDefault);
-    if (e == cudaSuccess) {
-        enqueue_pre(s, st, 1, h);
-        e = cudaStreamGetCaptureInfo(st, &cs, nullptr, &cap, &deps, nullptr, &nd);
-    }
-    cudaGraphNode_t wnode{};
-    cudaGraphNodeParams cp{};
-    if (e == cudaSuccess) {
-        cp.type = cudaGraphNodeTypeConditional;
-        cp.conditional.handle = h;
-        cp.conditional.type = cudaGraphCondTypeWhile;
-        cp.conditional.size = 1;
-        e = cudaGraphAddNode(&wnode, cap, deps, nullptr, nd, &cp);
-    }
-    if (e == cudaSuccess)
-        e = cudaStreamUpdateCaptureDependencies(st, &wnode, nullptr, 1,
-                                                cudaStreamSetCaptureDependencies);
-    if (e == cudaSuccess) {
-        cudaGraph_t body = cp.conditional.phGraph_out[0];
-        e = cudaStreamBeginCaptureToGraph(s->body_stream, body, nullptr, nullptr, 0,
-                                          cudaStreamCaptureModeThreadLocal);
-        if (e == cudaSuccess) {
-            launch_cg_iteration(field_args(s, 1, h), s->body_stream);
-            cudaGraph_t out = nullptr;
-            e = cudaStreamEndCapture(s->body_stream, &out);
+    cudaError_t e = cudaSuccess;
+    for (int part = 0; part < kNumParts && e == cudaSuccess; part++) {
+        if (!(mask & (1 << part))) continue;
+        if (part != kPartField) {
+            enqueue_part(s, part, st);
+            continue;
         }
+        cudaStreamCaptureStatus cs;
+        cudaGraph_t cap = nullptr;
+        const cudaGraphNode_t* deps = nullptr;
+        size_t nd = 0;
+        cudaGraphConditionalHandle h{};
+        e = cudaStreamGetCaptureInfo(st, &cs, nullptr, &cap, &deps, nullptr, &nd);
+        if (e == cudaSuccess) e = cudaGraphConditionalHandleCreate(&h, cap, 0, cudaGraphCondAssignDefault);
+        if (e == cudaSuccess) {
+            launch_rhs(field_args(s, 1, h), st);
+            e = cudaStreamGetCaptureInfo(st, &cs, nullptr, &cap, &deps, nullptr, &nd);
+        }
+        cudaGraphNode_t wnode{};
+        cudaGraphNodeParams cp{};
+        if (e == cudaSuccess) {
+            cp.type = cudaGraphNodeTypeConditional;
+            cp.conditional.handle = h;
+            cp.conditional.type = cudaGraphCondTypeWhile;
+            cp.conditional.size = 1;
+            e = cudaGraphAddNode(&wnode, cap, deps, nullptr, nd, &cp);
+        }
+        if (e == cudaSuccess)
+            e = cudaStreamUpdateCaptureDependencies(st, &wnode, nullptr, 1,
+                                                    cudaStreamSetCaptureDependencies);
+        if (e == cudaSuccess) {
+            cudaGraph_t body = cp.conditional.phGraph_out[0];
+            e = cudaStreamBeginCaptureToGraph(s->body_stream, body, nullptr, nullptr, 0,
+                                              cudaStreamCaptureModeThreadLocal);
+            if (e == cudaSuccess) {
+                launch_cg_iteration(field_args(s, 1, h), s->body_stream);
+                cudaGraph_t out = nullptr;
+                e = cudaStreamEndCapture(s->body_stream, &out);
+            }
+        }
+        if (e == cudaSuccess) launch_field_update(field_args(s, 0, 0), st);
     }
-    if (e == cudaSuccess) enqueue_post(s, st);
     cudaGraph_t g = nullptr;
     cudaError_t e2 = cudaStreamEndCapture(st, &g);
     if (e == cudaSuccess) e = e2;
@@ -275,19 +310,29 @@ int build_graph(pic_sim* s) {
         cudaGetLastError();
         return fail(s, PIC_ECUDA, std::string("step graph capture failed: ") + cudaGetErrorString(e));
     }
-    s->graph = g;
-    e = cudaGraphInstantiate(&s->gexec, g, 0);
+    cudaGraphExec_t x = nullptr;
+    e = cudaGraphInstantiate(&x, g, 0);
     if (e != cudaSuccess) {
-        drop_graph(s);
+        cudaGraphDestroy(g);
         return fail(s, PIC_ECUDA, std::string("cudaGraphInstantiate failed: ") + cudaGetErrorString(e));
     }
+    *gout = g;
+    *xout = x;
     return PIC_OK;
+}
+
+int build_graph(pic_sim* s) {
+    drop_graph(s);
+    return capture(s, (1 << kNumParts) - 1, &s->graph, &s->gexec);
 }
 
 // Direct launches (PIC_NO_GRAPH): the PCG loop is driven from the host.
 int run_step_direct(pic_sim* s) {
     cudaStream_t st = s->stream;
-    enqueue_pre(s, st, 0, 0);
+    enqueue_part(s, kPartPre, st);
+    enqueue_part(s, kPartPush, st);
+    enqueue_part(s, kPartPost, st);
+    launch_rhs(field_args(s, 0, 0), st);
     unsigned int nact = 0;
     CK(cudaMemcpyAsync(&nact, &s->st->n_active, sizeof nact, cudaMemcpyDeviceToHost, st));
     CK(cudaStreamSynchronize(st));
@@ -296,7 +341,8 @@ int run_step_direct(pic_sim* s) {
         CK(cudaMemcpyAsync(&nact, &s->st->n_active, sizeof nact, cudaMemcpyDeviceToHost, st));
         CK(cudaStreamSynchronize(st));
     }
-    enqueue_post(s, st);
+    launch_field_update(field_args(s, 0, 0), st);
+    enqueue_part(s, kPartEnd, st);
     CK(cudaGetLastError());
     return PIC_OK;
 }
@@ -338,9 +384,28 @@ __global__ void k_unload_fp64(long long n, const double* x, const double* y, dou
     oy[k] = y[k] * dy;
 }
 
-__global__ void k_f32_to_f64(long long n, const float* a, double* b) {
+__global__ void k_fix_to_f64(long long n, const long long* a, double jinv, double* b) {
     const long long k = (long long)blockIdx.x * blockDim.x + threadIdx.x;
-    if (k < n) b[k] = (double)a[k];
+    if (k < n) b[k] = (double)a[k] * jinv;
+}
+
+// Map device status counters that changed since the last check to a return code.
+int device_errors(pic_sim* s, const DevStatus& hs) {
+    int rc = PIC_OK;
+    if (hs.cg_noconv != s->seen_noconv) {
+        rc = fail(s, PIC_ECG_NOCONV, "PCG reached cg_max_iter before cg_rtol");
+    } else if (hs.nan_count != s->seen_nan) {
+        rc = fail(s, PIC_ENAN, "non-finite particle momentum or position");
+    } else if (hs.lost != s->seen_lost) {
+        rc = fail(s, PIC_ENOMEM, "particle storage exhausted (overflow list full)");
+    } else if (hs.cfl_viol != s->seen_cfl) {
+        rc = fail(s, PIC_ECFL, "a particle moved one cell or more in one step");
+    }
+    s->seen_noconv = hs.cg_noconv;
+    s->seen_nan = hs.nan_count;
+    s->seen_cfl = hs.cfl_viol;
+    s->seen_lost = hs.lost;
+    return rc;
 }
 
 int finish_call(pic_sim* s) {
@@ -428,7 +493,7 @@ int pic_init(const pic_params* prm, pic_sim** out) {
     if (prm->precision == PIC_FP64) {
         A(dalloc(&s->J64, n3));
     } else {
-        A(dalloc(&s->J32, n3));
+        A(dalloc(&s->Jfix, n3));
         A(dalloc(&s->F32, 6 * s->ntot));
     }
     if (e != cudaSuccess) {
@@ -445,10 +510,10 @@ int pic_init(const pic_params* prm, pic_sim** out) {
     A(cudaMemset(s->done, 0, s->ngrids * sizeof(unsigned int)));
     A(cudaMemset(s->st, 0, sizeof(DevStatus)));
     if (s->J64) A(cudaMemset(s->J64, 0, n3 * sizeof(double)));
-    if (s->J32) A(cudaMemset(s->J32, 0, n3 * sizeof(float)));
+    if (s->Jfix) A(cudaMemset(s->Jfix, 0, n3 * sizeof(long long)));
     if (s->F32) A(cudaMemset(s->F32, 0, 6 * s->ntot * sizeof(float)));
     if (prm->precision == PIC_MIXED32) {
-        int rc = mixed_create(&s->mixed, *prm, s->hgrids[0], s->dgrids, s->ntot, s->F32, s->J32,
+        int rc = mixed_create(&s->mixed, *prm, s->hgrids[0], s->dgrids, s->ntot, s->F32, s->Jfix,
                               s->cg, s->st, s->err);
         if (rc != PIC_OK) return bail(rc);
     }
@@ -582,17 +647,55 @@ int pic_step(pic_sim* s, int32_t n) {
     CK(cudaMemcpyAsync(&hs, s->st, sizeof hs, cudaMemcpyDeviceToHost, s->stream));
     if (int rc = finish_call(s)) return rc;
     s->steps += (long long)(hs.steps_done - steps0);
-    int rc = PIC_OK;
-    if (hs.cg_noconv != s->seen_noconv) {
-        rc = fail(s, PIC_ECG_NOCONV, "PCG reached cg_max_iter before cg_rtol");
-    } else if (hs.nan_count != s->seen_nan) {
-        rc = fail(s, PIC_ENAN, "non-finite particle momentum or position");
-    } else if (hs.cfl_viol != s->seen_cfl) {
-        rc = fail(s, PIC_ECFL, "a particle moved one cell or more in one step");
+    int rc = device_errors(s, hs);
+    if (rc == PIC_OK && s->prm.precision == PIC_MIXED32) rc = mixed_after_steps(s->mixed, s->stream, s->err);
+    return rc;
+}
+
+int pic_profile(pic_sim* s, int32_t n, double* out, int32_t n_out) {
+    if (!s) return PIC_EINVAL;
+    cudaSetDevice(s->device);
+    if (n < 1 || !out || n_out < 1) return fail(s, PIC_EINVAL, "need n >= 1 and an output array");
+    for (int k = 0; k < 6; k++)
+        if (!s->ev[k]) CK(cudaEventCreate(&s->ev[k]));
+    if (s->prm.precision == PIC_MIXED32) {
+        int rc = mixed_before_steps(s->mixed, s->stream, s->err);
+        if (rc) return rc;
     }
-    s->seen_noconv = hs.cg_noconv;
-    s->seen_nan = hs.nan_count;
-    s->seen_cfl = hs.cfl_viol;
+    for (int k = 0; k < kNumParts; k++)
+        if (!s->pexec[k])
+            if (int rc = capture(s, 1 << k, &s->pgraph[k], &s->pexec[k])) return rc;
+    double acc[5] = {0, 0, 0, 0, 0};
+    CgState c0{}, c1{};
+    DevStatus hs{};
+    CK(cudaMemcpyAsync(&c0, s->cg, sizeof c0, cudaMemcpyDeviceToHost, s->stream));
+    CK(cudaMemcpyAsync(&hs, s->st, sizeof hs, cudaMemcpyDeviceToHost, s->stream));
+    CK(cudaStreamSynchronize(s->stream));
+    const unsigned long long steps0 = hs.steps_done;
+    hs.stop = 0;
+    hs.stop_next = 0;
+    CK(cudaMemcpyAsync(s->st, &hs, sizeof hs, cudaMemcpyHostToDevice, s->stream));
+    for (int k = 0; k < n; k++) {
+        for (int part = 0; part < kNumParts; part++) {
+            CK(cudaEventRecord(s->ev[part], s->stream));
+            CK(cudaGraphLaunch(s->pexec[part], s->stream));
+        }
+        CK(cudaEventRecord(s->ev[5], s->stream));
+        CK(cudaStreamSynchronize(s->stream));
+        float t[5];
+        CK(cudaEventElapsedTime(&t[0], s->ev[0], s->ev[5]));  // whole step
+        CK(cudaEventElapsedTime(&t[1], s->ev[0], s->ev[3]));  // particle half
+        CK(cudaEventElapsedTime(&t[2], s->ev[1], s->ev[2]));  // dominant particle kernel
+        CK(cudaEventElapsedTime(&t[3], s->ev[3], s->ev[4]));  // field solve
+        for (int a = 0; a < 4; a++) acc[a] += t[a];
+    }
+    CK(cudaMemcpyAsync(&c1, s->cg, sizeof c1, cudaMemcpyDeviceToHost, s->stream));
+    CK(cudaMemcpyAsync(&hs, s->st, sizeof hs, cudaMemcpyDeviceToHost, s->stream));
+    CK(cudaStreamSynchronize(s->stream));
+    s->steps += (long long)(hs.steps_done - steps0);
+    acc[4] = (double)(c1.total_iters - c0.total_iters);
+    for (int a = 0; a < n_out && a < 5; a++) out[a] = acc[a] / n;
+    int rc = device_errors(s, hs);
     if (rc == PIC_OK && s->prm.precision == PIC_MIXED32) rc = mixed_after_steps(s->mixed, s->stream, s->err);
     return rc;
 }
@@ -610,8 +713,8 @@ int pic_fields(pic_sim* s, int32_t which, double* out, size_t len) {
         if (s->J64) {
             src = s->J64 + c * s->ntot;
         } else {
-            k_f32_to_f64<<<(unsigned)((s->ntot + 255) / 256), 256, 0, s->stream>>>(
-                s->ntot, s->J32 + c * s->ntot, s->tmp);
+            k_fix_to_f64<<<(unsigned)((s->ntot + 255) / 256), 256, 0, s->stream>>>(
+                s->ntot, s->Jfix + c * s->ntot, s->hgrids[0].jinv, s->tmp);
             src = s->tmp;
         }
     } else {
@@ -695,13 +798,15 @@ void pic_free(pic_sim* s) {
     if (s->stream) cudaStreamSynchronize(s->stream);
     drop_graph(s);
     if (s->mixed) mixed_destroy(s->mixed);
-    void* ptrs[] = {s->dgrids, s->dblk_grid, s->F, s->J64, s->J32, s->F32, s->x, s->r, s->p, s->q,
+    void* ptrs[] = {s->dgrids, s->dblk_grid, s->F, s->J64, s->Jfix, s->F32, s->x, s->r, s->p, s->q,
                     s->part, s->cg, s->done, s->st, s->tmp, s->dsegs, s->dblk_seg[0], s->dblk_seg[1]};
     for (void* p : ptrs) dfree(p);
     for (int sp = 0; sp < 2; sp++)
         for (int a = 0; a < 5; a++) dfree(s->pa[sp][a]);
     if (s->body_stream) cudaStreamDestroy(s->body_stream);
     if (s->own_stream) cudaStreamDestroy(s->own_stream);
+    for (int k = 0; k < 6; k++)
+        if (s->ev[k]) cudaEventDestroy(s->ev[k]);
     delete s;
 }
 

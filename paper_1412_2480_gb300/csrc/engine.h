@@ -15,7 +15,7 @@ struct FieldArgs {
     long long ntot;         // total cells over all simulations
     double* F;              // 6 * ntot: Ex Ey Ez Bx By Bz (component-major)
     const double* J64;      // 3 * ntot, FP64 current (FP64 particle path) or nullptr
-    const float* J32;       // 3 * ntot, FP32 current (MIXED32 particle path) or nullptr
+    const long long* Jfix;  // 3 * ntot, fixed-point current (MIXED32 particle path) or nullptr
     float* F32;             // 6 * ntot FP32 copy of the fields for MIXED32 gathers, or nullptr
     double *x, *r, *p, *q;  // 3 * ntot each: dB (solution), residual, direction, A p
     CgState* cg;            // [ngrids]

@@ -43,9 +43,11 @@ __device__ __forceinline__ Cell locate(const GridDev* grids, const int* blk_grid
     return c;
 }
 
+// Current value at k: FP64 as is; the MIXED32 current is 64-bit fixed point.
 template <typename T>
-__device__ __forceinline__ double ld(const T* p, long long k) {
-    return (double)p[k];
+__device__ __forceinline__ double ld(const T* p, long long k, double jinv) {
+    if constexpr (sizeof(T) == 8 && T(1) / T(2) == T(0)) return (double)p[k] * jinv;
+    else return (double)p[k];
 }
 
 // Sum `nv` values per thread over the block, store them as this block's partials, and
@@ -122,10 +124,12 @@ k_rhs(const GridDev* __restrict__ grids, const int* __restrict__ blk_grid, int n
         const double cEx = (Ez[c.kn] - ez) * idy;
         const double cEy = -(Ez[c.ke] - ez) * idx;
         const double cEz = (Ey[c.ke] - Ey[c.k]) * idx - (Ex[c.kn] - Ex[c.k]) * idy;
-        const double jz = ld(Jz, c.k);
-        const double cJx = (ld(Jz, c.kn) - jz) * idy;
-        const double cJy = -(ld(Jz, c.ke) - jz) * idx;
-        const double cJz = (ld(Jy, c.ke) - ld(Jy, c.k)) * idx - (ld(Jx, c.kn) - ld(Jx, c.k)) * idy;
+        const double ji = G.jinv;
+        const double jz = ld(Jz, c.k, ji);
+        const double cJx = (ld(Jz, c.kn, ji) - jz) * idy;
+        const double cJy = -(ld(Jz, c.ke, ji) - jz) * idx;
+        const double cJz = (ld(Jy, c.ke, ji) - ld(Jy, c.k, ji)) * idx -
+                           (ld(Jx, c.kn, ji) - ld(Jx, c.k, ji)) * idy;
         const double cE[3] = {cEx, cEy, cEz};
         const double cJ[3] = {cJx, cJy, cJz};
         const double idx2 = idx * idx, idy2 = idy * idy;
@@ -291,9 +295,9 @@ k_update_E(const GridDev* __restrict__ grids, const int* __restrict__ blk_grid, 
     const double cy = -(hzc - hz(c.kw)) * G.idx;
     const double cz = (hy(c.k) - hy(c.kw)) * G.idx - (hx(c.k) - hx(c.ks)) * G.idy;
     const double f = 4.0 * kPi * G.dt;
-    F[c.k] += G.dt * cx - f * ld(J, c.k);
-    F[ntot + c.k] += G.dt * cy - f * ld(J, ntot + c.k);
-    F[2 * ntot + c.k] += G.dt * cz - f * ld(J, 2 * ntot + c.k);
+    F[c.k] += G.dt * cx - f * ld(J, c.k, G.jinv);
+    F[ntot + c.k] += G.dt * cy - f * ld(J, ntot + c.k, G.jinv);
+    F[2 * ntot + c.k] += G.dt * cz - f * ld(J, 2 * ntot + c.k, G.jinv);
 }
 
 // B^{n+1} = B^n + dB, then the FP32 copies used by the MIXED32 gather.
@@ -332,7 +336,6 @@ __global__ void k_step_begin(int ngrids, CgState* cg, DevStatus* st) {
     if (threadIdx.x == 0) {
         if (st->stop_next) st->stop = 1u;
         if (!st->stop) st->steps_done += 1ull;
-        st->leaver_count = 0ull;
     }
     for (int g = threadIdx.x; g < ngrids; g += blockDim.x) cg[g].uk = 0.0;
 }
@@ -360,10 +363,10 @@ void launch_step_end(const FieldArgs& a, cudaStream_t s) {
 
 void launch_rhs(const FieldArgs& a, cudaStream_t s) {
     k_zero_x<<<a.nblk, kFieldThreads, 0, s>>>(a.grids, a.blk_grid, a.ntot, a.x);
-    if (a.J32)
-        k_rhs<float><<<a.nblk, kFieldThreads, 0, s>>>(a.grids, a.blk_grid, a.ngrids, a.nblk,
-                                                      a.ntot, a.F, a.J32, a.x, a.r, a.cg,
-                                                      a.part, a.done, a.st, a.cond, a.use_cond);
+    if (a.Jfix)
+        k_rhs<long long><<<a.nblk, kFieldThreads, 0, s>>>(a.grids, a.blk_grid, a.ngrids, a.nblk,
+                                                          a.ntot, a.F, a.Jfix, a.x, a.r, a.cg,
+                                                          a.part, a.done, a.st, a.cond, a.use_cond);
     else
         k_rhs<double><<<a.nblk, kFieldThreads, 0, s>>>(a.grids, a.blk_grid, a.ngrids, a.nblk,
                                                        a.ntot, a.F, a.J64, a.x, a.r, a.cg,
@@ -379,9 +382,9 @@ void launch_cg_iteration(const FieldArgs& a, cudaStream_t s) {
 }
 
 void launch_field_update(const FieldArgs& a, cudaStream_t s) {
-    if (a.J32)
-        k_update_E<float><<<a.nblk, kFieldThreads, 0, s>>>(a.grids, a.blk_grid, a.ntot, a.F,
-                                                           a.J32, a.x, a.cg, a.st);
+    if (a.Jfix)
+        k_update_E<long long><<<a.nblk, kFieldThreads, 0, s>>>(a.grids, a.blk_grid, a.ntot, a.F,
+                                                               a.Jfix, a.x, a.cg, a.st);
     else
         k_update_E<double><<<a.nblk, kFieldThreads, 0, s>>>(a.grids, a.blk_grid, a.ntot, a.F,
                                                             a.J64, a.x, a.cg, a.st);

@@ -1,32 +1,1062 @@
-// mixed.cu -- MIXED32 particle half (placeholder until the tiled kernels land).
+// mixed.cu -- the MIXED32 particle half of the step.
+//
+// Particles: int32 cell (i | j << 16) + FP32 in-cell offsets (ox, oy) in [0,1) + FP32
+// momenta: 24 bytes per particle, structure-of-arrays, binned by (tile, species); a tile
+// is tx x ty cells. Each bin has a stayer segment (capacity cap) and eight outboxes
+// (capacity capo each), one per neighbouring tile. Bins are double-buffered: a step reads
+// buffer `parity` and writes buffer `parity ^ 1`.
+//
+// Per step (inside the captured step graph):
+//   0. k_mixed_begin / k_push_overflow: particles parked in the overflow list (no room
+//      in a bin; normally none) are pushed straight from global memory;
+//   1. k_push_tile: one CTA per tile stages the FP32 field window (tile + 2 cells below,
+//      3 above, in x and y) into shared memory and zeroes a 64-bit fixed-point current
+//      window of the same size. Its particles are its own stayer segment plus the eight
+//      neighbours' outboxes addressed to it. Warps run independently (no block barrier in
+//      the particle loop): each gathers E^n, B^n, pushes (Boris), moves and deposits
+//      J^{n+1/2} (Esirkepov) with native integer shared-memory atomics, then writes each
+//      particle to the next buffer's stayer segment or to the outbox of the neighbour it
+//      moved into, taking slots from warp-aggregated shared-memory counters. The current
+//      window is added to the global fixed-point current at the end;
+//   2. k_mixed_swap: the buffers swap.
+// No global atomics are needed in steady state and no migration kernel runs. A particle
+// found outside its tile is pushed with the same arithmetic on global memory, so
+// correctness never depends on bin capacity; a particle that finds no room goes to the
+// overflow list and the host re-sorts with larger bins after the pic_step call.
+#include <cub/cub.cuh>
+
+#include <algorithm>
+#include <cmath>
+#include <vector>
+
+#include "esirkepov.cuh"
 #include "mixed.h"
 
 namespace pic {
 
-struct MixedState {
-    int unused;
+constexpr int kTileThreads = 256;
+constexpr int kNbr = 8;          // outboxes per bin, one per neighbouring tile
+constexpr int kSegs = 1 + kNbr;  // count slots per bin: [0] stayers, [1 + o] outbox o
+
+struct PartArrays {  // staging: one plain array per attribute
+    int* cij;
+    float *ox, *oy, *ux, *uy, *uz;
+    int* gs;
 };
 
-int mixed_create(MixedState** out, const pic_params&, GridDev&, const GridDev*, long long, float*,
-                 float*, CgState*, DevStatus*, std::string& err) {
+// Bins and overflow lists: AoSoA of 32-particle chunks, each chunk holding its 32 cells,
+// then 32 x-offsets, y-offsets, ux, uy, uz (6 x 128 bytes): a warp touches whole lines
+// and one base pointer addresses every attribute.
+constexpr int kFields = 6;
+struct Slots {
+    unsigned* p;
+    int* gs;  // species of each slot (overflow lists only)
+};
+
+__host__ __device__ __forceinline__ size_t aos(long long k, int f) {
+    return (size_t)(k >> 5) * (32 * kFields) + (size_t)f * 32 + (size_t)(k & 31);
+}
+
+struct MixedArgs {
+    const GridDev* grids;
+    int g;
+    long long ntot;
+    const float* F32;
+    long long* Jfix;
+    unsigned* buf[2];
+    int* cnt[2];  // [nbins * kSegs] per parity
+    Slots ovf[2];
+    long long ovf_cap;
+    CgState* cg;
+    DevStatus* st;
+};
+
+struct MixedState {
+    pic_params prm{};
+    GridDev* G = nullptr;  // host copy owned by the caller (grid 0)
+    const GridDev* dgrids = nullptr;
+    long long ntot = 0;
+    float* F32 = nullptr;
+    long long* Jfix = nullptr;
+    CgState* cg = nullptr;
+    DevStatus* st = nullptr;
+    unsigned* buf[2] = {nullptr, nullptr};
+    Slots ovf[2]{};
+    int* cnt[2] = {nullptr, nullptr};
+    long long nslots = 0, ovf_cap = 0;
+    long long n[2] = {0, 0};
+    long long rebins = 0;
+    size_t smem = 0;
+};
+
+namespace {
+
+__host__ __device__ __forceinline__ long long bin_stride(const GridDev& G) {
+    return G.cap + kNbr * G.capo;
+}
+
+// Outbox index of a move by (dx, dy) tiles, (dx, dy) != (0, 0).
+__host__ __device__ __forceinline__ int outbox_of(int dx, int dy) {
+    const int d = (dy + 1) * 3 + (dx + 1);
+    return d < 4 ? d : d - 1;
+}
+
+__host__ __device__ __forceinline__ void dir_of(int o, int& dx, int& dy) {
+    const int d = o < 4 ? o : o + 1;
+    dx = d % 3 - 1;
+    dy = d / 3 - 1;
+}
+
+// ---------------------------------------------------------------------------------
+// Memory views used by the shared push arithmetic.
+// ---------------------------------------------------------------------------------
+// The tile's current window accumulates fixed point in two 32-bit words per node: 32-bit
+// integer shared atomics are single native instructions, while float and 64-bit ones
+// loop on compare-and-swap. Every single-particle contribution to a node is bounded by
+// u/2 (GridDev::jscale = 2^40/u). A contribution v becomes x = v 2^k/u, split into its
+// nearest integer hi and the rest r = x - hi in [-1/2, 1/2], and lo = round(r 2^lb);
+// integers come from one FMA with 1.5 * 2^23 (exact below 2^22 in magnitude). Each tile
+// picks k, lb <= 30 - log2(n + 1) from its particle count n (no word can wrap, whatever
+// the distribution) with k <= 22 and lb <= 16, i.e. a resolution of 2^-(k+lb) u. The
+// flush adds hi 2^(40-k) + lo 2^(40-k-lb) exactly into the 64-bit global current.
+constexpr float kMagic = 12582912.0f;  // 1.5 * 2^23
+constexpr int kMagicBits = 0x4B400000;
+
+struct WinMem {  // tile window in shared memory; indices are window-local
+    const float* fw;
+    int* jhi;
+    int* jlo;
+    int wx, nw;
+    float js;   // window scale 2^k / u
+    float jlb;  // 2^lb
+    __device__ __forceinline__ float ld(int c, int ix, int iy) const { return fw[c * nw + iy * wx + ix]; }
+    __device__ __forceinline__ void add(int c, int ix, int iy, float v) const {
+        const float x = v * js;
+        const float xr = x + kMagic;
+        const int hi = __float_as_int(xr) - kMagicBits;
+        const float r = x - (xr - kMagic);  // exact: |r| <= 1/2
+        const int lo = __float_as_int(fmaf(r, jlb, kMagic)) - kMagicBits;
+        const int k = c * nw + iy * wx + ix;
+        atomicAdd(&jhi[k], hi);
+        atomicAdd(&jlo[k], lo);
+    }
+};
+
+struct GlobalMem {  // global grid arrays of one simulation; indices are global
+    const float* F;
+    unsigned long long* J;
+    long long ntot;
+    int nx, ny;
+    float js;
+    __device__ __forceinline__ long long at(int ix, int iy) const {
+        return (long long)wrapi(iy, ny) * nx + wrapi(ix, nx);
+    }
+    __device__ __forceinline__ float ld(int c, int ix, int iy) const { return __ldg(F + c * ntot + at(ix, iy)); }
+    __device__ __forceinline__ void add(int c, int ix, int iy, float v) const {
+        atomicAdd(J + c * ntot + at(ix, iy), (unsigned long long)__float2ll_rn(v * js));
+    }
+};
+
+template <int P, typename Mem>
+__device__ __forceinline__ float gather(const Mem& M, int c, int bx, const float wx[P + 1], int by,
+                                        const float wy[P + 1]) {
+    float acc = 0.f;
+#pragma unroll
+    for (int b = 0; b <= P; b++) {
+        float ra = 0.f;
+#pragma unroll
+        for (int a = 0; a <= P; a++) ra = fmaf(wx[a], M.ld(c, bx + a, by + b), ra);
+        acc = fmaf(wy[b], ra, acc);
+    }
+    return acc;
+}
+
+struct PushConst {
+    float h;        // (q/m) dt / 2
+    float dt_idx;   // dt / dx
+    float dt_idy;   // dt / dy
+    float fx, fy;   // q dx / (dt dx dy), q dy / (dt dx dy)
+    float fz;       // q / (dx dy)   (times vz)
+    int deposit;
+};
+
+// Gather, Boris push, move with carry into the neighbouring cell, and deposit, for one
+// particle at cell (i, j) of M's index space with offsets (ox, oy). On return ox, oy, u
+// hold the new state and di, dj the cell carry (-1, 0, +1). Returns false (and leaves
+// the position unchanged) if the move is not below one cell or is not finite.
+template <int P, typename Mem>
+__device__ __forceinline__ bool push_one(const Mem& M, const PushConst& K, int i, int j, float& ox,
+                                         float& oy, float u[3], int& di, int& dj, float& ek) {
+    int bx0, bxh, by0, byh;
+    float wx0[P + 1], wxh[P + 1], wy0[P + 1], wyh[P + 1];
+    shape_nodes<P, float>(i, ox, bx0, wx0);
+    shape_nodes_half<P, float>(i, ox, bxh, wxh);
+    shape_nodes<P, float>(j, oy, by0, wy0);
+    shape_nodes_half<P, float>(j, oy, byh, wyh);
+    // Ex (i+1/2, j), Ey (i, j+1/2), Ez (i, j), Bx (i, j+1/2), By (i+1/2, j), Bz (i+1/2, j+1/2)
+    const float E[3] = {gather<P>(M, 0, bxh, wxh, by0, wy0), gather<P>(M, 1, bx0, wx0, byh, wyh),
+                        gather<P>(M, 2, bx0, wx0, by0, wy0)};
+    const float B[3] = {gather<P>(M, 3, bx0, wx0, byh, wyh), gather<P>(M, 4, bxh, wxh, by0, wy0),
+                        gather<P>(M, 5, bxh, wxh, byh, wyh)};
+    const float g_old = sqrtf(1.f + u[0] * u[0] + u[1] * u[1] + u[2] * u[2]);
+    boris<float>(K.h, E, B, u);
+    const float ig = rsqrtf(1.f + u[0] * u[0] + u[1] * u[1] + u[2] * u[2]);
+    const float dX = K.dt_idx * u[0] * ig, dY = K.dt_idy * u[1] * ig;
+    di = 0;
+    dj = 0;
+    if (!(fabsf(dX) < 1.f && fabsf(dY) < 1.f)) return false;
+    ek += g_old + 1.f / ig - 2.f;
+    float x1 = ox + dX, y1 = oy + dY;
+    if (x1 >= 1.f) { x1 -= 1.f; di = 1; }
+    else if (x1 < 0.f) { x1 += 1.f; di = -1; if (x1 >= 1.f) { x1 = 0.f; di = 0; } }
+    if (y1 >= 1.f) { y1 -= 1.f; dj = 1; }
+    else if (y1 < 0.f) { y1 += 1.f; dj = -1; if (y1 >= 1.f) { y1 = 0.f; dj = 0; } }
+    if (K.deposit)
+        esirkepov<P, float>(i, ox, j, oy, i + di, x1, j + dj, y1, K.fx, K.fy, K.fz * (u[2] * ig),
+                            [M](int c, int ix, int iy, float v) { M.add(c, ix, iy, v); });
+    ox = x1;
+    oy = y1;
+    return true;
+}
+
+__device__ __forceinline__ PushConst push_const(const GridDev& G, int s) {
+    PushConst K;
+    K.h = (float)(0.5 * G.qm[s] * G.dt);
+    K.dt_idx = (float)(G.dt * G.idx);
+    K.dt_idy = (float)(G.dt * G.idy);
+    const double area = G.dx * G.dy;
+    K.fx = (float)(G.qw[s] * G.dx / (G.dt * area));
+    K.fy = (float)(G.qw[s] * G.dy / (G.dt * area));
+    K.fz = (float)(G.qw[s] / area);
+    K.deposit = G.deposit;
+    return K;
+}
+
+__device__ __forceinline__ void flag_bad(DevStatus* st, const float u[3]) {
+    if (isfinite(u[0] + u[1] + u[2])) atomicAdd(&st->cfl_viol, 1ull);
+    else atomicAdd(&st->nan_count, 1ull);
+    st->stop_next = 1u;
+}
+
+__device__ __forceinline__ void put(unsigned* P, long long k, int c, float ox, float oy,
+                                    const float u[3]) {
+    __stcs(P + aos(k, 0), (unsigned)c);
+    __stcs(reinterpret_cast<float*>(P) + aos(k, 1), ox);
+    __stcs(reinterpret_cast<float*>(P) + aos(k, 2), oy);
+    __stcs(reinterpret_cast<float*>(P) + aos(k, 3), u[0]);
+    __stcs(reinterpret_cast<float*>(P) + aos(k, 4), u[1]);
+    __stcs(reinterpret_cast<float*>(P) + aos(k, 5), u[2]);
+}
+
+__device__ __forceinline__ void get(const unsigned* P, long long k, int& c, float& ox, float& oy,
+                                    float u[3]) {
+    const float* F = reinterpret_cast<const float*>(P);
+    c = (int)__ldcs(P + aos(k, 0));
+    ox = __ldcs(F + aos(k, 1));
+    oy = __ldcs(F + aos(k, 2));
+    u[0] = __ldcs(F + aos(k, 3));
+    u[1] = __ldcs(F + aos(k, 4));
+    u[2] = __ldcs(F + aos(k, 5));
+}
+
+// Append to the overflow list of the next buffer; a full list is a fatal error.
+__device__ __forceinline__ void to_overflow(unsigned* op, int* ogs, long long ovf_cap, DevStatus* st,
+                                         int nxt, int c, float ox, float oy, float u0, float u1,
+                                         float u2, int s) {
+    const unsigned long long o = atomicAdd(&st->ovf_count[nxt], 1ull);
+    atomicAdd(&st->overflow, 1ull);
+    if ((long long)o < ovf_cap) {
+        const float u[3] = {u0, u1, u2};
+        put(op, (long long)o, c, ox, oy, u);
+        ogs[o] = s;
+    } else {
+        atomicAdd(&st->lost, 1ull);  // storage exhausted: the step fails with PIC_ENOMEM
+        st->stop_next = 1u;
+    }
+}
+
+// ---------------------------------------------------------------------------------
+// 1. Tile kernel
+// ---------------------------------------------------------------------------------
+// Resident CTAs per SM the order-2 tile kernel is compiled for (register budget).
+#ifndef PIC_TILE_MIN_BLOCKS_P2
+#define PIC_TILE_MIN_BLOCKS_P2 3
+#endif
+
+template <int P>
+__global__ void __launch_bounds__(kTileThreads, P == 1 ? 3 : (P == 2 ? PIC_TILE_MIN_BLOCKS_P2 : 2))
+k_push_tile(const MixedArgs a) {
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    __shared__ int s_start[2][kSegs + 1];     // virtual start of each segment, per species
+    __shared__ long long s_base[2][kSegs];     // physical first slot of each segment
+    __shared__ int s_out[2][kSegs];            // next-buffer counts (stayers, outboxes)
+    __shared__ double s_red[32];
+    DevStatus* st = a.st;
+    if (st->stop) return;
+    const int par = (int)st->parity, nxp = par ^ 1;
+    const GridDev& G = a.grids[a.g];
+    const int t = blockIdx.x;
+    const int tyi = t / G.ntx, txi = t - tyi * G.ntx;
+    const int X0 = txi * G.tx, Y0 = tyi * G.ty;
+    const int X1 = min(X0 + G.tx, G.nx), Y1 = min(Y0 + G.ty, G.ny);
+    const int nx = G.nx, ny = G.ny;
+    const int WX = G.wx, NW = G.wx * G.wy;
+    const long long cap = G.cap, capo = G.capo, stride = bin_stride(G);
+    int* jw = reinterpret_cast<int*>(smem_raw);  // [0, 3 NW) hi words, [3 NW, 6 NW) lo words
+    float* fw = reinterpret_cast<float*>(smem_raw + (size_t)6 * NW * sizeof(int));
+    if (threadIdx.x < 2 * kSegs) {
+        const int s = threadIdx.x / kSegs, k = threadIdx.x - (threadIdx.x / kSegs) * kSegs;
+        int src = t;
+        long long off = 0, lim = cap;
+        if (k > 0) {
+            int dx, dy;
+            dir_of(k - 1, dx, dy);
+            const int sx = (txi - dx + G.ntx) % G.ntx, sy = (tyi - dy + G.nty) % G.nty;
+            src = sy * G.ntx + sx;
+            off = cap + (long long)(k - 1) * capo;
+            lim = capo;
+        }
+        const long long b = (long long)src * 2 + s;
+        const int* ccur = par ? a.cnt[1] : a.cnt[0];
+        const int cnt = (int)min((long long)ccur[b * kSegs + k], lim);
+        s_start[s][k + 1] = cnt;  // prefix-summed below
+        s_base[s][k] = G.bin_off + b * stride + off;
+        s_out[s][k] = 0;
+    }
+    const float* Fg = a.F32 + G.cell_off;
+    for (int idx = threadIdx.x; idx < 6 * NW; idx += blockDim.x) {
+        const int c = idx / NW;
+        const int w = idx - c * NW;
+        const int wy = w / WX;
+        const int wx = w - wy * WX;
+        const int gx = ((X0 - 2 + wx) % nx + nx) % nx;
+        const int gy = ((Y0 - 2 + wy) % ny + ny) % ny;
+        fw[idx] = Fg[c * a.ntot + (long long)gy * nx + gx];
+    }
+    for (int idx = threadIdx.x; idx < 6 * NW; idx += blockDim.x) jw[idx] = 0;
+    __syncthreads();
+    if (threadIdx.x < 2) {
+        const int s = threadIdx.x;
+        s_start[s][0] = 0;
+        for (int k = 1; k <= kSegs; k++) s_start[s][k] += s_start[s][k - 1];
+    }
+    __syncthreads();
+    const float js = (float)G.jscale;
+    const int n_tile = s_start[0][kSegs] + s_start[1][kSegs];
+    const int room = 30 - (32 - __clz(n_tile));  // n_tile < 2^(30 - room)
+    const int kwin = min(22, room), lbits = min(16, room);
+    const WinMem W{fw, jw, jw + 3 * NW, WX, NW, (float)(G.jscale * exp2((double)(kwin - 40))),
+                   (float)(1 << lbits)};
+    const GlobalMem M{a.F32 + G.cell_off, reinterpret_cast<unsigned long long*>(a.Jfix + G.cell_off),
+                      a.ntot, nx, ny, js};
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nwarp = blockDim.x >> 5;
+    const unsigned* cur = par ? a.buf[1] : a.buf[0];
+    unsigned* nxt = par ? a.buf[0] : a.buf[1];
+    float ek = 0.f;
+    for (int s = 0; s < 2; s++) {
+        const PushConst K = push_const(G, s);
+        const int total = s_start[s][kSegs];
+        const long long own = G.bin_off + ((long long)t * 2 + s) * stride;
+        for (int c0 = warp * 32; c0 < total; c0 += nwarp * 32) {
+            const int v = c0 + lane;
+            const bool valid = v < total;
+            int dest = -1, cnew = 0;
+            float ox = 0.f, oy = 0.f, u[3] = {0.f, 0.f, 0.f};
+            if (valid) {
+                int seg = 0;
+#pragma unroll
+                for (int k = 1; k < kSegs; k++) seg += (v >= s_start[s][k]) ? 1 : 0;
+                const long long e = s_base[s][seg] + (v - s_start[s][seg]);
+                int c;
+                get(cur, e, c, ox, oy, u);
+                const int ci = c & 0xffff, cj = c >> 16;
+                int di, dj;
+                bool ok;
+                if (ci >= X0 && ci < X1 && cj >= Y0 && cj < Y1)
+                    ok = push_one<P>(W, K, ci - X0 + 2, cj - Y0 + 2, ox, oy, u, di, dj, ek);
+                else
+                    ok = push_one<P>(M, K, ci, cj, ox, oy, u, di, dj, ek);
+                if (!ok) flag_bad(st, u);
+                const int ni = wrapi(ci + di, nx), nj = wrapi(cj + dj, ny);
+                cnew = ni | (nj << 16);
+                if (ni >= X0 && ni < X1 && nj >= Y0 && nj < Y1) {
+                    dest = 0;
+                } else {
+                    int dtx = ni / G.tx - txi, dty = nj / G.ty - tyi;
+                    if (dtx > 1) dtx -= G.ntx;
+                    if (dtx < -1) dtx += G.ntx;
+                    if (dty > 1) dty -= G.nty;
+                    if (dty < -1) dty += G.nty;
+                    dest = (abs(dtx) <= 1 && abs(dty) <= 1 && (dtx | dty)) ? 1 + outbox_of(dtx, dty) : -1;
+                }
+            }
+            const unsigned act = __ballot_sync(0xffffffffu, valid);
+            if (valid) {
+                const unsigned grp = __match_any_sync(act, dest);
+                const int leader = __ffs(grp) - 1;
+                const int rank = __popc(grp & ((1u << lane) - 1u));
+                int b0 = 0;
+                if (lane == leader && dest >= 0) b0 = atomicAdd(&s_out[s][dest], __popc(grp));
+                b0 = __shfl_sync(grp, b0, leader) + rank;
+                long long slot = -1;
+                if (dest == 0 && b0 < cap) slot = own + b0;
+                else if (dest > 0 && b0 < capo) slot = own + cap + (long long)(dest - 1) * capo + b0;
+                if (slot >= 0) put(nxt, slot, cnew, ox, oy, u);
+                else
+                    to_overflow(nxp ? a.ovf[1].p : a.ovf[0].p, nxp ? a.ovf[1].gs : a.ovf[0].gs,
+                                a.ovf_cap, st, nxp, cnew, ox, oy, u[0], u[1], u[2], s);
+            }
+        }
+    }
+    __syncthreads();
+    if (threadIdx.x < 2 * kSegs) {
+        const int s = threadIdx.x / kSegs, k = threadIdx.x - (threadIdx.x / kSegs) * kSegs;
+        const long long lim = k == 0 ? cap : capo;
+        int* cnxt = nxp ? a.cnt[1] : a.cnt[0];
+        cnxt[((long long)t * 2 + s) * kSegs + k] = (int)min((long long)s_out[s][k], lim);
+    }
+    // add the current window into the global fixed-point current
+    unsigned long long* Jg = reinterpret_cast<unsigned long long*>(a.Jfix + G.cell_off);
+    for (int idx = threadIdx.x; idx < 3 * NW; idx += blockDim.x) {
+        const int hi = jw[idx], lo = jw[3 * NW + idx];
+        if ((hi | lo) == 0) continue;
+        const unsigned long long v = (unsigned long long)((long long)hi * (1ll << (40 - kwin)) +
+                                                          (long long)lo * (1ll << (40 - kwin - lbits)));
+        const int c = idx / NW;
+        const int w = idx - c * NW;
+        const int wy = w / WX;
+        const int wx = w - wy * WX;
+        const int gx = ((X0 - 2 + wx) % nx + nx) % nx;
+        const int gy = ((Y0 - 2 + wy) % ny + ny) % ny;
+        atomicAdd(Jg + c * a.ntot + (long long)gy * nx + gx, v);
+    }
+    const double sum = block_sum((double)ek, s_red);
+    if (threadIdx.x == 0 && sum != 0.0) atomicAdd(&a.cg[a.g].uk, 0.5 * G.w * sum);
+}
+
+// ---------------------------------------------------------------------------------
+// 0. Overflow particles: global-memory push; they stay in the overflow list until the
+// host re-sorts after the pic_step call.
+// ---------------------------------------------------------------------------------
+__global__ void k_mixed_begin(DevStatus* st) {
+    if (threadIdx.x == 0 && !st->stop) st->ovf_count[st->parity ^ 1u] = 0ull;
+}
+
+template <int P>
+__global__ void __launch_bounds__(kTileThreads)
+k_push_overflow(const MixedArgs a) {
+    __shared__ double s_red[32];
+    DevStatus* st = a.st;
+    if (st->stop) return;
+    const int par = (int)st->parity;
+    const long long n = min((long long)st->ovf_count[par], a.ovf_cap);
+    const GridDev& G = a.grids[a.g];
+    const GlobalMem M{a.F32 + G.cell_off, reinterpret_cast<unsigned long long*>(a.Jfix + G.cell_off),
+                      a.ntot, G.nx, G.ny, (float)G.jscale};
+    float ek = 0.f;
+    const Slots O = par ? a.ovf[1] : a.ovf[0];
+    for (long long k = (long long)blockIdx.x * blockDim.x + threadIdx.x; k < n;
+         k += (long long)gridDim.x * blockDim.x) {
+        int c;
+        float ox, oy, u[3];
+        get(O.p, k, c, ox, oy, u);
+        const int s = O.gs[k];
+        const int ci = c & 0xffff, cj = c >> 16;
+        int di, dj;
+        if (!push_one<P>(M, push_const(G, s), ci, cj, ox, oy, u, di, dj, ek)) flag_bad(st, u);
+        const int cnew = wrapi(ci + di, G.nx) | (wrapi(cj + dj, G.ny) << 16);
+        to_overflow(par ? a.ovf[0].p : a.ovf[1].p, par ? a.ovf[0].gs : a.ovf[1].gs, a.ovf_cap, st,
+                    par ^ 1, cnew, ox, oy, u[0], u[1], u[2], s);
+    }
+    const double sum = block_sum((double)ek, s_red);
+    if (threadIdx.x == 0 && sum != 0.0) atomicAdd(&a.cg[a.g].uk, 0.5 * G.w * sum);
+}
+
+__global__ void k_mixed_swap(DevStatus* st) {
+    if (threadIdx.x == 0 && !st->stop) st->parity ^= 1u;
+}
+
+// ---------------------------------------------------------------------------------
+// Loading and re-sorting
+// ---------------------------------------------------------------------------------
+// FP64 physical particles -> staging (cell + FP32 offsets, FP32 momenta).
+__global__ void k_stage_fp64(long long n, const double* x, const double* y, const double* ux,
+                             const double* uy, const double* uz, GridDev G, PartArrays S,
+                             unsigned long long* nbad) {
+    const long long k = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (k >= n) return;
+    double X = x[k], Y = y[k];
+    const double a = ux[k], b = uy[k], c = uz[k];
+    if (!isfinite(X) || !isfinite(Y) || !isfinite(a) || !isfinite(b) || !isfinite(c)) {
+        atomicAdd(nbad, 1ull);
+        X = 0.0;
+        Y = 0.0;
+    }
+    const double Lx = G.nx * G.dx, Ly = G.ny * G.dy;
+    X = (X - floor(X / Lx) * Lx) * G.idx;
+    Y = (Y - floor(Y / Ly) * Ly) * G.idy;
+    int i = (int)floor(X), j = (int)floor(Y);
+    float fx = (float)(X - i), fy = (float)(Y - j);
+    if (fx >= 1.f) { fx = 0.f; i += 1; }
+    if (fy >= 1.f) { fy = 0.f; j += 1; }
+    i = ((i % G.nx) + G.nx) % G.nx;
+    j = ((j % G.ny) + G.ny) % G.ny;
+    S.cij[k] = i | (j << 16);
+    S.ox[k] = fx;
+    S.oy[k] = fy;
+    S.ux[k] = (float)a;
+    S.uy[k] = (float)b;
+    S.uz[k] = (float)c;
+}
+
+// Sort key of a staged particle: (tile, rank in its cell, cell in tile). Sorted, a bin
+// lists one particle of every cell, then a second of every cell, and so on, so the 32
+// lanes of a warp work on 32 different cells (no shared-memory address conflicts).
+__global__ void k_keys(long long n, GridDev G, const int* cij, unsigned int* cellcnt,
+                       int* bincnt, unsigned long long* keys, unsigned int* idx) {
+    const long long k = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    const bool valid = k < n;
+    const int c = valid ? cij[k] : 0;
+    const int i = c & 0xffff, j = c >> 16;
+    const long long cell = (long long)j * G.nx + i;
+    // warp-aggregated rank within the cell (neighbouring particles often share a cell)
+    const unsigned act = __ballot_sync(0xffffffffu, valid);
+    if (!valid) return;
+    const unsigned grp = __match_any_sync(act, cell);
+    const int lane = threadIdx.x & 31;
+    const int leader = __ffs(grp) - 1;
+    unsigned base = 0;
+    if (lane == leader) base = atomicAdd(&cellcnt[cell], (unsigned)__popc(grp));
+    const unsigned rank = __shfl_sync(grp, base, leader) + __popc(grp & ((1u << lane) - 1u));
+    const int t = (j / G.ty) * G.ntx + i / G.tx;
+    const unsigned grpt = __match_any_sync(act, t);
+    if (lane == __ffs(grpt) - 1) atomicAdd(&bincnt[t], __popc(grpt));
+    const unsigned cin = (unsigned)((j - (j / G.ty) * G.ty) * G.tx + (i - (i / G.tx) * G.tx));
+    const unsigned cpt = (unsigned)(G.tx * G.ty);
+    const unsigned r = min(rank, (0xffffffffu / cpt) - 1u);
+    keys[k] = ((unsigned long long)t << 32) | (unsigned long long)(r * cpt + cin);
+    idx[k] = (unsigned)k;
+}
+
+__global__ void k_scatter(long long n, GridDev G, int s, const unsigned long long* keys,
+                          const unsigned int* idx, const long long* binstart, PartArrays S,
+                          unsigned* B) {
+    const long long p = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (p >= n) return;
+    const int t = (int)(keys[p] >> 32);
+    const long long r = p - binstart[t];
+    const long long dst = G.bin_off + ((long long)t * 2 + s) * bin_stride(G) + r;
+    const unsigned src = idx[p];
+    const float u[3] = {S.ux[src], S.uy[src], S.uz[src]};
+    put(B, dst, S.cij[src], S.ox[src], S.oy[src], u);
+}
+
+__global__ void k_set_counts(int ntiles, int s, const int* bincnt, int* cnt) {
+    const int t = blockIdx.x * blockDim.x + threadIdx.x;
+    if (t >= ntiles) return;
+    int* c = cnt + ((long long)t * 2 + s) * kSegs;
+    c[0] = bincnt[t];
+    for (int k = 1; k < kSegs; k++) c[k] = 0;
+}
+
+// Copy every segment of species s's bins (offsets from a host prefix sum, one entry per
+// (tile, segment)) into staging form.
+__device__ __forceinline__ void to_staging(const unsigned* P, long long k, PartArrays S, long long d) {
+    int c;
+    float ox, oy, u[3];
+    get(P, k, c, ox, oy, u);
+    S.cij[d] = c;
+    S.ox[d] = ox;
+    S.oy[d] = oy;
+    S.ux[d] = u[0];
+    S.uy[d] = u[1];
+    S.uz[d] = u[2];
+}
+
+__global__ void k_gather_bins(GridDev G, int s, const int* cnt, const long long* off, const unsigned* B,
+                              PartArrays S) {
+    const int t = blockIdx.x / kSegs, k = blockIdx.x - (blockIdx.x / kSegs) * kSegs;
+    const long long b = (long long)t * 2 + s;
+    const long long lim = k == 0 ? G.cap : G.capo;
+    const int n = (int)min((long long)cnt[b * kSegs + k], lim);
+    const long long src0 = G.bin_off + b * bin_stride(G) + (k == 0 ? 0 : G.cap + (long long)(k - 1) * G.capo);
+    const long long dst0 = off[blockIdx.x];
+    for (int q = threadIdx.x; q < n; q += blockDim.x) to_staging(B, src0 + q, S, dst0 + q);
+}
+
+// Overflow-list entries of species s appended after `base` in staging form.
+__global__ void k_gather_overflow(long long n_over, int s, Slots O, long long base,
+                                  unsigned long long* cursor, PartArrays S) {
+    const long long k = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (k >= n_over || O.gs[k] != s) return;
+    const long long d = base + (long long)atomicAdd(cursor, 1ull);
+    to_staging(O.p, k, S, d);
+}
+
+__global__ void k_unstage(long long n, GridDev G, PartArrays S, double* out) {
+    const long long k = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (k >= n) return;
+    const int c = S.cij[k];
+    out[k] = ((double)(c & 0xffff) + (double)S.ox[k]) * G.dx;
+    out[n + k] = ((double)(c >> 16) + (double)S.oy[k]) * G.dy;
+    out[2 * n + k] = S.ux[k];
+    out[3 * n + k] = S.uy[k];
+    out[4 * n + k] = S.uz[k];
+}
+
+// ---- host helpers -------------------------------------------------------------------
+
+template <typename T>
+cudaError_t dalloc(T** p, size_t n) {
+    *p = nullptr;
+    return cudaMalloc((void**)p, (n ? n : 1) * sizeof(T));
+}
+
+void free_parts(PartArrays& A) {
+    void* ps[] = {A.cij, A.ox, A.oy, A.ux, A.uy, A.uz, A.gs};
+    for (void* p : ps)
+        if (p) cudaFree(p);
+    A = PartArrays{};
+}
+
+cudaError_t alloc_parts(PartArrays& A, size_t n, bool with_gs) {
+    A = PartArrays{};
+    cudaError_t e = dalloc(&A.cij, n);
+    if (e == cudaSuccess) e = dalloc(&A.ox, n);
+    if (e == cudaSuccess) e = dalloc(&A.oy, n);
+    if (e == cudaSuccess) e = dalloc(&A.ux, n);
+    if (e == cudaSuccess) e = dalloc(&A.uy, n);
+    if (e == cudaSuccess) e = dalloc(&A.uz, n);
+    if (e == cudaSuccess && with_gs) e = dalloc(&A.gs, n);
+    if (e != cudaSuccess) free_parts(A);
+    return e;
+}
+
+MixedArgs make_args(MixedState* m) {
+    MixedArgs a{};
+    a.grids = m->dgrids;
+    a.g = 0;
+    a.ntot = m->ntot;
+    a.F32 = m->F32;
+    a.Jfix = m->Jfix;
+    for (int p = 0; p < 2; p++) {
+        a.buf[p] = m->buf[p];
+        a.cnt[p] = m->cnt[p];
+        a.ovf[p] = m->ovf[p];
+    }
+    a.ovf_cap = m->ovf_cap;
+    a.ovf_cap = m->ovf_cap;
+    a.cg = m->cg;
+    a.st = m->st;
+    return a;
+}
+
+unsigned grid1(long long n, int b = 256) { return (unsigned)std::max<long long>(1, (n + b - 1) / b); }
+
+#define MCK(call)                                                                     \
+    do {                                                                              \
+        cudaError_t e_ = (call);                                                      \
+        if (e_ != cudaSuccess) {                                                      \
+            err = std::string(#call) + " failed: " + cudaGetErrorString(e_);          \
+            return PIC_ECUDA;                                                         \
+        }                                                                             \
+    } while (0)
+
+int read_status(MixedState* m, DevStatus& hs, cudaStream_t st, std::string& err) {
+    MCK(cudaMemcpyAsync(&hs, m->st, sizeof hs, cudaMemcpyDeviceToHost, st));
+    MCK(cudaStreamSynchronize(st));
+    return PIC_OK;
+}
+
+// Sort n staged particles of species s into the stayer segments of buffer `par`.
+// Returns PIC_ENOMEM (nothing written) when a bin would overflow.
+int sort_into_bins(MixedState* m, int par, int s, PartArrays S, long long n, cudaStream_t st,
+                   std::string& err) {
+    const GridDev& G = *m->G;
+    const int ntiles = G.ntiles;
+    unsigned int* cellcnt = nullptr;
+    int* bincnt = nullptr;
+    long long* binstart = nullptr;
+    unsigned long long *k0 = nullptr, *k1 = nullptr;
+    unsigned int *i0 = nullptr, *i1 = nullptr;
+    void* tmp = nullptr;
+    size_t tmpb = 0;
+    int rc = PIC_OK;
+    cudaError_t e = cudaSuccess;
+    auto A = [&](cudaError_t r) {
+        if (e == cudaSuccess) e = r;
+    };
+    A(dalloc(&cellcnt, (size_t)G.ncell));
+    A(dalloc(&bincnt, (size_t)ntiles));
+    A(dalloc(&binstart, (size_t)ntiles + 1));
+    A(dalloc(&k0, (size_t)n));
+    A(dalloc(&k1, (size_t)n));
+    A(dalloc(&i0, (size_t)n));
+    A(dalloc(&i1, (size_t)n));
+    if (e == cudaSuccess) {
+        A(cudaMemsetAsync(cellcnt, 0, G.ncell * sizeof(unsigned), st));
+        A(cudaMemsetAsync(bincnt, 0, ntiles * sizeof(int), st));
+        if (n) k_keys<<<grid1(n), 256, 0, st>>>(n, G, S.cij, cellcnt, bincnt, k0, i0);
+        A(cudaGetLastError());
+    }
+    std::vector<int> hcnt(ntiles);
+    if (e == cudaSuccess) {
+        A(cudaMemcpyAsync(hcnt.data(), bincnt, ntiles * sizeof(int), cudaMemcpyDeviceToHost, st));
+        A(cudaStreamSynchronize(st));
+    }
+    if (e == cudaSuccess) {
+        long long mx = 0;
+        std::vector<long long> start(ntiles + 1, 0);
+        for (int t = 0; t < ntiles; t++) {
+            mx = std::max<long long>(mx, hcnt[t]);
+            start[t + 1] = start[t] + hcnt[t];
+        }
+        if (mx > G.cap) {
+            rc = PIC_ENOMEM;  // caller grows the bins and retries
+        } else {
+            A(cudaMemcpyAsync(binstart, start.data(), (ntiles + 1) * sizeof(long long),
+                              cudaMemcpyHostToDevice, st));
+            cub::DoubleBuffer<unsigned long long> kb(k0, k1);
+            cub::DoubleBuffer<unsigned int> vb(i0, i1);
+            int endbit = 32;
+            while ((1ll << (endbit - 32)) < ntiles) endbit++;
+            A(cub::DeviceRadixSort::SortPairs(nullptr, tmpb, kb, vb, (int)n, 0, endbit, st));
+            A(dalloc((char**)&tmp, tmpb));
+            if (e == cudaSuccess && n)
+                A(cub::DeviceRadixSort::SortPairs(tmp, tmpb, kb, vb, (int)n, 0, endbit, st));
+            if (e == cudaSuccess && n)
+                k_scatter<<<grid1(n), 256, 0, st>>>(n, G, s, kb.Current(), vb.Current(), binstart, S,
+                                                    m->buf[par]);
+            k_set_counts<<<grid1(ntiles), 256, 0, st>>>(ntiles, s, bincnt, m->cnt[par]);
+            A(cudaGetLastError());
+            A(cudaStreamSynchronize(st));
+        }
+    }
+    void* ps[] = {cellcnt, bincnt, binstart, k0, k1, i0, i1, tmp};
+    for (void* p : ps)
+        if (p) cudaFree(p);
+    if (e != cudaSuccess) {
+        err = std::string("bin sort failed: ") + cudaGetErrorString(e);
+        return PIC_ECUDA;
+    }
+    return rc;
+}
+
+// All live particles of species s (every bin segment of buffer `par` + its overflow
+// list) into a new staging set.
+int gather_species(MixedState* m, int par, int s, PartArrays& S, long long& n, cudaStream_t st,
+                   std::string& err) {
+    const GridDev& G = *m->G;
+    const long long nb_seg = (long long)G.ntiles * kSegs;
+    std::vector<int> cnt(2 * nb_seg);
+    MCK(cudaMemcpyAsync(cnt.data(), m->cnt[par], cnt.size() * sizeof(int), cudaMemcpyDeviceToHost, st));
+    DevStatus hs{};
+    MCK(cudaMemcpyAsync(&hs, m->st, sizeof hs, cudaMemcpyDeviceToHost, st));
+    MCK(cudaStreamSynchronize(st));
+    std::vector<long long> off(nb_seg + 1, 0);
+    for (int t = 0; t < G.ntiles; t++)
+        for (int k = 0; k < kSegs; k++) {
+            const long long lim = k == 0 ? G.cap : G.capo;
+            const long long q = (long long)t * kSegs + k;
+            off[q + 1] = off[q] + std::min<long long>(cnt[((long long)t * 2 + s) * kSegs + k], lim);
+        }
+    const long long nb = off[nb_seg];
+    const long long no = std::min<long long>((long long)hs.ovf_count[par], m->ovf_cap);
+    MCK(alloc_parts(S, (size_t)(nb + no), false));
+    long long* doff = nullptr;
+    unsigned long long* cursor = nullptr;
+    MCK(dalloc(&doff, off.size()));
+    MCK(dalloc(&cursor, 1));
+    MCK(cudaMemcpyAsync(doff, off.data(), off.size() * sizeof(long long), cudaMemcpyHostToDevice, st));
+    MCK(cudaMemsetAsync(cursor, 0, sizeof(unsigned long long), st));
+    k_gather_bins<<<(unsigned)nb_seg, 256, 0, st>>>(G, s, m->cnt[par], doff, m->buf[par], S);
+    if (no) k_gather_overflow<<<grid1(no), 256, 0, st>>>(no, s, m->ovf[par], nb, cursor, S);
+    unsigned long long hcur = 0;
+    MCK(cudaMemcpyAsync(&hcur, cursor, sizeof hcur, cudaMemcpyDeviceToHost, st));
+    MCK(cudaStreamSynchronize(st));
+    cudaFree(doff);
+    cudaFree(cursor);
+    n = nb + (long long)hcur;
+    return PIC_OK;
+}
+
+long long round32(double c) { return ((long long)std::ceil(c) + 31) / 32 * 32; }
+
+// (Re)allocate both bin buffers for stayer capacity cap and outbox capacity capo
+// (contents are not preserved; all counts are zeroed).
+int alloc_bins(MixedState* m, long long cap, long long capo, cudaStream_t st, std::string& err) {
+    GridDev& G = *m->G;
+    for (int p = 0; p < 2; p++) {
+        if (m->buf[p]) cudaFree(m->buf[p]);
+        m->buf[p] = nullptr;
+    }
+    G.cap = cap;
+    G.capo = capo;
+    G.bin_off = 0;
+    m->nslots = (long long)G.ntiles * 2 * bin_stride(G);
+    for (int p = 0; p < 2; p++) {
+        cudaError_t e = dalloc(&m->buf[p], (size_t)m->nslots * kFields);
+        if (e != cudaSuccess) {
+            cudaGetLastError();
+            err = "bin allocation failed (" + std::to_string(m->nslots) + " slots per buffer)";
+            return PIC_ENOMEM;
+        }
+        MCK(cudaMemsetAsync(m->cnt[p], 0, (size_t)G.ntiles * 2 * kSegs * sizeof(int), st));
+    }
+    return PIC_OK;
+}
+
+// Re-sort both species into fresh bins with capacities at least (cap_min, capo_min).
+int rebuild(MixedState* m, long long cap_min, long long capo_min, cudaStream_t st, std::string& err) {
+    DevStatus hs{};
+    if (int rc = read_status(m, hs, st, err)) return rc;
+    const int par = (int)hs.parity;
+    PartArrays S[2]{};
+    long long n[2] = {0, 0};
+    for (int s = 0; s < 2; s++) {
+        int rc = gather_species(m, par, s, S[s], n[s], st, err);
+        if (rc) {
+            free_parts(S[0]);
+            free_parts(S[1]);
+            return rc;
+        }
+    }
+    long long cap = std::max(cap_min, m->G->cap), capo = std::max(capo_min, m->G->capo);
+    int rc = PIC_OK;
+    for (int attempt = 0; attempt < 8; attempt++) {
+        rc = alloc_bins(m, cap, capo, st, err);
+        if (rc) break;
+        rc = sort_into_bins(m, par, 0, S[0], n[0], st, err);
+        if (rc == PIC_OK) rc = sort_into_bins(m, par, 1, S[1], n[1], st, err);
+        if (rc != PIC_ENOMEM) break;
+        cap = cap * 3 / 2 + 32;  // a bin would overflow: grow and retry
+    }
+    free_parts(S[0]);
+    free_parts(S[1]);
+    if (rc) return rc;
+    MCK(cudaMemcpyAsync((void*)m->dgrids, m->G, sizeof(GridDev), cudaMemcpyHostToDevice, st));
+    MCK(cudaMemsetAsync(&m->st->ovf_count, 0, sizeof(hs.ovf_count), st));
+    MCK(cudaStreamSynchronize(st));
+    m->n[0] = n[0];
+    m->n[1] = n[1];
+    m->rebins++;
+    return PIC_OK;
+}
+
+}  // namespace
+
+// =====================================================================================
+
+int mixed_create(MixedState** out, const pic_params& p, GridDev& G, const GridDev* dgrids,
+                 long long ntot, float* F32, long long* Jfix, CgState* cg, DevStatus* st,
+                 std::string& err) {
     *out = nullptr;
-    err = "PIC_MIXED32 is not available in this build";
-    return PIC_EINVAL;
+    MixedState* m = new MixedState();
+    m->prm = p;
+    m->G = &G;
+    m->dgrids = dgrids;
+    m->ntot = ntot;
+    m->F32 = F32;
+    m->Jfix = Jfix;
+    m->cg = cg;
+    m->st = st;
+    int tx = p.tile_x, ty = p.tile_y;
+    if (tx <= 0) tx = std::min(32, p.nx);
+    if (ty <= 0) ty = std::min(16, p.ny);
+    tx = std::min(tx, p.nx);
+    ty = std::min(ty, p.ny);
+    G.tx = tx;
+    G.ty = ty;
+    G.ntx = (p.nx + tx - 1) / tx;
+    G.nty = (p.ny + ty - 1) / ty;
+    G.ntiles = G.ntx * G.nty;
+    G.tile_first = 0;
+    G.wx = tx + 5;
+    G.wy = ty + 5;
+    m->smem = (size_t)6 * G.wx * G.wy * sizeof(int) + (size_t)6 * G.wx * G.wy * sizeof(float);
+    const double slack = p.bin_slack > 0 ? p.bin_slack : 1.25;
+    const long long expect = 2ll * p.ppc * (long long)p.nx * p.ny;
+    m->ovf_cap = std::max<long long>(65536, expect / 8);
+    cudaError_t e = cudaSuccess;
+    m->ovf_cap = (m->ovf_cap + 31) / 32 * 32;
+    for (int q = 0; q < 2 && e == cudaSuccess; q++) {
+        e = cudaMalloc(&m->cnt[q], (size_t)G.ntiles * 2 * kSegs * sizeof(int));
+        if (e == cudaSuccess) e = dalloc(&m->ovf[q].p, (size_t)m->ovf_cap * kFields);
+        if (e == cudaSuccess) e = dalloc(&m->ovf[q].gs, (size_t)m->ovf_cap);
+    }
+    int rc = PIC_OK;
+    if (e == cudaSuccess) {
+        const long long cap = round32((double)p.ppc * tx * ty * slack + 64.0);
+        const long long capo = round32((double)p.ppc * std::max(tx, ty) * 1.5 + 32.0);
+        rc = alloc_bins(m, cap, capo, 0, err);
+        if (rc == PIC_OK) e = cudaDeviceSynchronize();
+    }
+    if (rc == PIC_OK && e == cudaSuccess) {
+        auto set = [&](auto kern) {
+            return cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)m->smem);
+        };
+        e = set(k_push_tile<1>);
+        if (e == cudaSuccess) e = set(k_push_tile<2>);
+        if (e == cudaSuccess) e = set(k_push_tile<3>);
+    }
+    if (rc == PIC_OK && e != cudaSuccess) {
+        err = std::string("MIXED32 setup failed: ") + cudaGetErrorString(e);
+        cudaGetLastError();
+        rc = PIC_ENOMEM;
+    }
+    if (rc != PIC_OK) {
+        mixed_destroy(m);
+        return rc;
+    }
+    *out = m;
+    return PIC_OK;
 }
-void mixed_destroy(MixedState* m) { delete m; }
-int mixed_load(MixedState*, int, const double*, const double*, const double*, const double*,
-               const double*, long long, cudaStream_t, std::string& err) {
-    err = "PIC_MIXED32 is not available in this build";
-    return PIC_EINVAL;
+
+void mixed_destroy(MixedState* m) {
+    if (!m) return;
+    for (int p = 0; p < 2; p++) {
+        void* ps[] = {m->buf[p], m->ovf[p].p, m->ovf[p].gs, m->cnt[p]};
+        for (void* q : ps)
+            if (q) cudaFree(q);
+    }
+    delete m;
 }
-void mixed_enqueue_step(MixedState*, cudaStream_t) {}
+
+int mixed_load(MixedState* m, int s, const double* x, const double* y, const double* ux,
+               const double* uy, const double* uz, long long n, cudaStream_t st, std::string& err) {
+    DevStatus hs{};
+    if (int rc = read_status(m, hs, st, err)) return rc;
+    // fold any overflow-list particles back into bins first so the list holds none of s
+    if (hs.ovf_count[hs.parity]) {
+        int rc = rebuild(m, m->G->cap, m->G->capo, st, err);
+        if (rc) return rc;
+    }
+    const int par = (int)hs.parity;
+    double* in = nullptr;
+    PartArrays S{};
+    unsigned long long* nbad = nullptr;
+    MCK(dalloc(&in, 5 * (size_t)std::max<long long>(n, 1)));
+    const double* src[5] = {x, y, ux, uy, uz};
+    for (int a = 0; a < 5 && n; a++)
+        MCK(cudaMemcpyAsync(in + a * n, src[a], n * sizeof(double), cudaMemcpyDefault, st));
+    MCK(alloc_parts(S, (size_t)n, false));
+    MCK(dalloc(&nbad, 1));
+    MCK(cudaMemsetAsync(nbad, 0, sizeof(unsigned long long), st));
+    if (n)
+        k_stage_fp64<<<grid1(n), 256, 0, st>>>(n, in, in + n, in + 2 * n, in + 3 * n, in + 4 * n, *m->G,
+                                               S, nbad);
+    unsigned long long hbad = 0;
+    MCK(cudaMemcpyAsync(&hbad, nbad, sizeof hbad, cudaMemcpyDeviceToHost, st));
+    MCK(cudaStreamSynchronize(st));
+    cudaFree(in);
+    cudaFree(nbad);
+    if (hbad) {
+        free_parts(S);
+        err = "non-finite particle position or momentum";
+        return PIC_EINVAL;
+    }
+    int rc = sort_into_bins(m, par, s, S, n, st, err);  // also zeroes s's outbox counts
+    if (rc == PIC_ENOMEM) {
+        // a bin would overflow: rebuild both species with larger bins
+        PartArrays other{};
+        long long no = 0;
+        rc = gather_species(m, par, 1 - s, other, no, st, err);
+        if (rc == PIC_OK) {
+            long long cap = m->G->cap;
+            for (int attempt = 0; attempt < 8; attempt++) {
+                cap = cap * 3 / 2 + 32;
+                rc = alloc_bins(m, cap, m->G->capo, st, err);
+                if (rc) break;
+                rc = sort_into_bins(m, par, s, S, n, st, err);
+                if (rc == PIC_OK) rc = sort_into_bins(m, par, 1 - s, other, no, st, err);
+                if (rc != PIC_ENOMEM) break;
+            }
+            m->rebins++;
+        }
+        free_parts(other);
+    }
+    free_parts(S);
+    if (rc) return rc;
+    MCK(cudaMemcpyAsync((void*)m->dgrids, m->G, sizeof(GridDev), cudaMemcpyHostToDevice, st));
+    MCK(cudaStreamSynchronize(st));
+    m->n[s] = n;
+    return PIC_OK;
+}
+
+void mixed_enqueue(MixedState* m, cudaStream_t st, int part) {
+    const MixedArgs a = make_args(m);
+    const GridDev& G = *m->G;
+    const int P = G.order;
+    if (part == 0) {
+        k_mixed_begin<<<1, 32, 0, st>>>(m->st);
+        const unsigned ob = 152;
+        switch (P) {
+        case 1: k_push_overflow<1><<<ob, kTileThreads, 0, st>>>(a); break;
+        case 2: k_push_overflow<2><<<ob, kTileThreads, 0, st>>>(a); break;
+        default: k_push_overflow<3><<<ob, kTileThreads, 0, st>>>(a); break;
+        }
+    } else if (part == 1) {
+        switch (P) {
+        case 1: k_push_tile<1><<<G.ntiles, kTileThreads, m->smem, st>>>(a); break;
+        case 2: k_push_tile<2><<<G.ntiles, kTileThreads, m->smem, st>>>(a); break;
+        default: k_push_tile<3><<<G.ntiles, kTileThreads, m->smem, st>>>(a); break;
+        }
+    } else {
+        k_mixed_swap<<<1, 32, 0, st>>>(m->st);
+    }
+}
+
 int mixed_before_steps(MixedState*, cudaStream_t, std::string&) { return PIC_OK; }
-int mixed_after_steps(MixedState*, cudaStream_t, std::string&) { return PIC_OK; }
-long long mixed_count(MixedState*, int) { return 0; }
-long long mixed_rebins(MixedState*) { return 0; }
-int mixed_particles(MixedState*, int, double*, long long, cudaStream_t, std::string& err) {
-    err = "PIC_MIXED32 is not available in this build";
-    return PIC_EINVAL;
+
+int mixed_after_steps(MixedState* m, cudaStream_t st, std::string& err) {
+    DevStatus hs{};
+    if (int rc = read_status(m, hs, st, err)) return rc;
+    const int par = (int)hs.parity;
+    if (hs.ovf_count[par] == 0) return PIC_OK;
+    // particles are parked in the overflow list: re-sort with room to spare. Grow the
+    // stayer capacity to 1.25x the fullest tile and double the outboxes if any is full.
+    const GridDev& G = *m->G;
+    std::vector<int> cnt((size_t)G.ntiles * 2 * kSegs);
+    MCK(cudaMemcpyAsync(cnt.data(), m->cnt[par], cnt.size() * sizeof(int), cudaMemcpyDeviceToHost, st));
+    MCK(cudaStreamSynchronize(st));
+    long long mx = 0;
+    bool outbox_full = false;
+    for (long long b = 0; b < (long long)G.ntiles * 2; b++) {
+        long long tot = 0;
+        for (int k = 0; k < kSegs; k++) {
+            tot += cnt[b * kSegs + k];
+            if (k > 0 && cnt[b * kSegs + k] >= G.capo) outbox_full = true;
+        }
+        mx = std::max(mx, tot);
+    }
+    const long long per_tile_ovf = (long long)hs.ovf_count[par];  // upper bound on any tile's excess
+    const long long want = round32(1.25 * (double)std::min(mx + per_tile_ovf, 2 * mx + 64));
+    return rebuild(m, std::max(want, G.cap), outbox_full ? 2 * G.capo : G.capo, st, err);
+}
+
+long long mixed_count(MixedState* m, int s) { return m->n[s]; }
+long long mixed_rebins(MixedState* m) { return m->rebins; }
+
+int mixed_particles(MixedState* m, int s, double* out, long long n, cudaStream_t st, std::string& err) {
+    DevStatus hs{};
+    if (int rc = read_status(m, hs, st, err)) return rc;
+    PartArrays S{};
+    long long got = 0;
+    int rc = gather_species(m, (int)hs.parity, s, S, got, st, err);
+    if (rc) return rc;
+    if (got != n) {
+        free_parts(S);
+        err = "particle count mismatch (" + std::to_string(got) + " live, " + std::to_string(n) + " requested)";
+        return PIC_ESTATE;
+    }
+    double* t = nullptr;
+    MCK(dalloc(&t, 5 * (size_t)std::max<long long>(n, 1)));
+    if (n) k_unstage<<<grid1(n), 256, 0, st>>>(n, *m->G, S, t);
+    MCK(cudaMemcpyAsync(out, t, 5 * n * sizeof(double), cudaMemcpyDefault, st));
+    MCK(cudaStreamSynchronize(st));
+    cudaFree(t);
+    free_parts(S);
+    return PIC_OK;
 }
 
 }  // namespace pic

@@ -15,20 +15,21 @@ struct MixedState;
 
 // Choose tiles and allocate bins for the single simulation G (fills G's tile fields).
 int mixed_create(MixedState** out, const pic_params& p, GridDev& G, const GridDev* dgrids,
-                 long long ntot, float* F32, float* J32, CgState* cg, DevStatus* st,
+                 long long ntot, float* F32, long long* Jfix, CgState* cg, DevStatus* st,
                  std::string& err);
 void mixed_destroy(MixedState* m);
 // Replace one species' particles (FP64 physical positions and momenta, host or device).
 int mixed_load(MixedState* m, int sp, const double* x, const double* y, const double* ux,
                const double* uy, const double* uz, long long n, cudaStream_t s, std::string& err);
-// Enqueue the particle half of one step (J32 already zeroed).
-void mixed_enqueue_step(MixedState* m, cudaStream_t s);
+// Enqueue one part of the particle half of a step (the fixed-point current already
+// zeroed): part 0 = overflow-list push, 1 = tile kernel, 2 = buffer swap.
+void mixed_enqueue(MixedState* m, cudaStream_t s, int part);
 // Host bookkeeping around a pic_step call (re-sort when bins overflowed).
 int mixed_before_steps(MixedState* m, cudaStream_t s, std::string& err);
 int mixed_after_steps(MixedState* m, cudaStream_t s, std::string& err);
 long long mixed_count(MixedState* m, int sp);
 long long mixed_rebins(MixedState* m);
-// Copy out one species as FP64 [x, y, ux, uy, uz] (physical units), tile order.
+// Copy out one species as FP64 [x, y, ux, uy, uz] (physical units), bin order.
 int mixed_particles(MixedState* m, int sp, double* out5xn, long long n, cudaStream_t s,
                     std::string& err);
 

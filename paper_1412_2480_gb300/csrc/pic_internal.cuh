@@ -34,8 +34,11 @@ struct GridDev {
     int tx, ty, ntx, nty; // tile size and tile counts
     int tile_first, ntiles;
     int wx, wy;           // tile window size: (tx + 5) x (ty + 5), origin (X0-2, Y0-2)
-    long long cap;        // bin capacity (particles) per (tile, species)
+    long long cap;        // stayer capacity (particles) per (tile, species) bin
+    long long capo;       // capacity of each of the 8 outboxes of a bin
     long long bin_off;    // first particle slot of this simulation's bins
+    // MIXED32 current: 64-bit fixed point, J = (double)Jfix * jinv
+    double jscale, jinv;
 };
 
 // Per-simulation state of the PCG solve of Eq. (7).
@@ -57,9 +60,9 @@ struct DevStatus {
     unsigned long long steps_done;   // steps completed (the failing step included)
     unsigned int grids_done;         // counter of the last-grid-finished pattern
     unsigned int n_active;           // simulations whose PCG is still iterating
-    unsigned long long leaver_count; // MIXED32: leavers queued this step
-    unsigned long long overflow_count; // MIXED32: particles in the overflow list
-    unsigned long long leaver_full;  // MIXED32: leavers kept in place (queue full)
+    unsigned long long lost;         // MIXED32: particles dropped because the overflow list was full
+    unsigned int parity;             // MIXED32: which of the two bin buffers is current
+    unsigned long long ovf_count[2]; // MIXED32: particles in each overflow list
 };
 
 // One contiguous range of FP64 particles of one species in one simulation.

@@ -1,0 +1,147 @@
+"""MIXED32 CUDA path (int cell + FP32 offset, FP32 gather/push/deposit, FP64 field solve)
+vs the FP64 oracle on the same seeded inputs, through the C ABI.
+
+Tolerance (2e-5, FP32 mode): applied relative to the scale of the terms each result is
+summed from, which is the bound FP32 arithmetic can promise. For momenta and fields
+that is their own norm. For the current of a co-located pair plasma, where positron
+and electron currents cancel to ~1e-6 of either, it is the norm of one species' current.
+
+Particles come back in tile order, so they are matched to the oracle's by nearest
+neighbour in (x, y, ux, uy, uz); positions are compared modulo the box."""
+import math
+
+import numpy as np
+import pytest
+
+import oracle
+import paper_1412_2480_gb300 as pic
+from runners import rel, run_gpu, run_oracle, workload
+
+pytestmark = pytest.mark.gpu
+TOL32 = 2e-5
+
+
+def match(pg, po, nx, ny):
+    """Index into pg for each oracle particle (nearest in position-momentum space)."""
+    from scipy.spatial import cKDTree
+    su = max(np.abs(po[2:]).max(), 1e-30)
+    # unwrap-safe: use sin/cos embedding of the periodic coordinates
+    def emb(p):
+        return np.stack([np.cos(2 * np.pi * p[0] / nx) * nx, np.sin(2 * np.pi * p[0] / nx) * nx,
+                         np.cos(2 * np.pi * p[1] / ny) * ny, np.sin(2 * np.pi * p[1] / ny) * ny,
+                         p[2] / su, p[3] / su, p[4] / su], axis=1)
+    tree = cKDTree(emb(pg))
+    d, idx = tree.query(emb(po))
+    assert len(np.unique(idx)) == po.shape[1], "particle matching is not one-to-one"
+    return idx
+
+
+def pos_err(a, b, L):
+    d = np.abs(a - b)
+    return float(np.max(np.minimum(d, L - d)))
+
+
+@pytest.mark.parametrize("order", [1, 2, 3])
+def test_mixed_step_matches_oracle(order):
+    nx, ny, ppc = 72, 40, 3  # 3 x 3 tiles of 32 x 16, ragged in both directions
+    w, sp, F0 = workload(nx, ny, ppc, gamma0=5.0, u_th=0.2, seed=10 + order, field_amp=0.05,
+                         colocated=False)
+    Fg, pg, mom = run_gpu(nx, ny, ppc, sp, F0, 1, order, gamma0=5.0, cg_rtol=1e-13,
+                          precision=pic.PIC_MIXED32, tile_x=32, tile_y=16)
+    Fo, po, sim = run_oracle(nx, ny, w, sp, F0, 1, order, cg_rtol=1e-13)
+    assert mom["n_particles"] == (nx * ny * ppc, nx * ny * ppc)
+    for c in range(6):
+        assert rel(Fg[c], Fo[c]) < TOL32, f"field {c}: {rel(Fg[c], Fo[c]):.2e}"
+    for c in range(6, 9):
+        assert rel(Fg[c], Fo[c]) < TOL32, f"current {c - 6}: {rel(Fg[c], Fo[c]):.2e}"
+    for s in range(2):
+        idx = match(pg[s], po[s], nx, ny)
+        g = pg[s][:, idx]
+        assert pos_err(g[0], po[s][0], nx) < TOL32
+        assert pos_err(g[1], po[s][1], ny) < TOL32
+        assert rel(g[2:], po[s][2:]) < TOL32
+
+
+def test_mixed_colocated_pair_plasma_currents():
+    # the production workload shape (co-located pairs, gamma0 = 20, 1e-3 spread)
+    nx = ny = 64
+    ppc = 8
+    w, sp, F0 = workload(nx, ny, ppc, gamma0=20.0, u_th=1e-3, seed=1)
+    Fg, pg, mom = run_gpu(nx, ny, ppc, sp, F0, 1, 1, gamma0=20.0, precision=pic.PIC_MIXED32,
+                          tile_x=16, tile_y=8)
+    Fo, po, sim = run_oracle(nx, ny, w, sp, F0, 1, 1)
+    Jp, _, _ = run_oracle(nx, ny, w, sp[:1], F0, 1, 1)  # one species' current: the scale
+    scale = np.linalg.norm(Jp[6:9])
+    assert np.linalg.norm(Fg[6:9] - Fo[6:9]) / scale < TOL32
+    e_scale = 4 * math.pi * sim.g.dt * scale
+    assert np.linalg.norm(Fg[:3] - Fo[:3]) / e_scale < TOL32
+    for s in range(2):
+        idx = match(pg[s], po[s], nx, ny)
+        assert rel(pg[s][2:, idx], po[s][2:]) < TOL32
+
+
+def test_mixed_many_steps_conserve_charge_and_particles():
+    # 20 steps: every particle crosses tiles (drift ~1 cell/step with 8-cell tiles);
+    # Gauss's law residual div E - 4 pi rho stays constant (Esirkepov) to FP32 level.
+    nx, ny, ppc = 48, 24, 4
+    w, sp, F0 = workload(nx, ny, ppc, gamma0=3.0, u_th=0.3, seed=3, colocated=False)
+    prm = pic.pic_params_default(nx=nx, ny=ny, ppc=ppc, gamma0=3.0, shape_order=2,
+                                 precision=pic.PIC_MIXED32, tile_x=8, tile_y=8)
+    g = oracle.grid(nx, ny, 1.0, 0.5, 2)
+    h = pic.pic_init(prm)
+    try:
+        for s in range(2):
+            d = sp[s]
+            pic.pic_load_particles(h, s, d["x"], d["y"], d["ux"], d["uy"], d["uz"])
+
+        def gauss():
+            F = np.stack([pic.fields_numpy(h, c, nx, ny) for c in range(6)])
+            rho = np.zeros(nx * ny)
+            for s in range(2):
+                p = pic.pic_particles(h, s)
+                oracle.deposit_rho(g, (1 if s == 0 else -1) * w, p[0], p[1], rho)
+            return oracle.div_E(g, F) - 4 * math.pi * rho, rho
+
+        g0, rho0 = gauss()
+        for _ in range(4):
+            pic.pic_step(h, 5)
+            m = pic.pic_moments(h)
+            assert m["n_particles"] == (nx * ny * ppc, nx * ny * ppc)
+            assert m["cfl_violations"] == 0
+            gk, rho = gauss()
+            scale = 4 * math.pi * np.abs(rho).max() + 4 * math.pi * w
+            assert np.abs(gk - g0).max() < 1e-5 * scale
+        assert m["step"] == 20
+    finally:
+        pic.pic_free(h)
+
+
+def test_mixed_bin_overflow_path_matches_oracle():
+    # Counter-streaming halves pile up in the middle tiles, exceeding bins sized with
+    # little slack: particles go through the overflow path and are re-sorted after the
+    # call; results still match the oracle.
+    nx, ny, ppc = 64, 16, 6
+    w, sp, F0 = workload(nx, ny, ppc, gamma0=2.0, u_th=0.01, seed=4, colocated=False)
+    for d in sp:
+        left = d["x"] < nx / 2
+        d["ux"] = np.where(left, 6.0, -6.0) + d["ux"] * 0
+    Fg, pg, mom = run_gpu(nx, ny, ppc, sp, F0, 6, 1, gamma0=2.0, cg_rtol=1e-13,
+                          precision=pic.PIC_MIXED32, tile_x=8, tile_y=8, bin_slack=1.05)
+    Fo, po, sim = run_oracle(nx, ny, w, sp, F0, 6, 1, cg_rtol=1e-13)
+    assert mom["overflow_moves"] > 0 and mom["rebins"] >= 1
+    assert rel(Fg[6:9], Fo[6:9]) < 1e-4
+    for s in range(2):
+        idx = match(pg[s], po[s], nx, ny)
+        assert pos_err(pg[s][0, idx], po[s][0], nx) < 1e-4
+
+
+def test_mixed_empty_and_single_species():
+    nx, ny = 16, 16
+    Fg, pg, mom = run_gpu(nx, ny, 1, [], np.zeros((6, ny, nx)), 2, 2,
+                          precision=pic.PIC_MIXED32, want_particles=False)
+    assert np.all(Fg == 0) and mom["n_particles"] == (0, 0)
+    w, sp, F0 = workload(nx, ny, 2, gamma0=3.0, u_th=0.3, seed=8, field_amp=0.05, colocated=False)
+    Fg, pg, mom = run_gpu(nx, ny, 2, sp[:1], F0, 2, 2, gamma0=3.0, precision=pic.PIC_MIXED32,
+                          cg_rtol=1e-13)
+    Fo, po, _ = run_oracle(nx, ny, w, sp[:1], F0, 2, 2, cg_rtol=1e-13)
+    assert rel(Fg[:9], Fo[:9]) < TOL32
