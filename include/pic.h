@@ -180,6 +180,49 @@ PIC_API int64_t pic_particle_count(pic_sim* s, int32_t species);
  * pic_particle_count. FP64 mode keeps the load order; MIXED32 returns tile order. */
 PIC_API int pic_particles(pic_sim* s, int32_t species, double* out5xn, int64_t n);
 
+/* ---- allocation-free field solve ----------------------------------------------------
+ * The paper has no counterpart to this entry point: it is a service of this library.
+ *
+ * Some callers cannot allocate device memory: an application whose device memory is
+ * already reserved by another allocator's pool (a framework that takes the GPU's memory
+ * at start-up), a long-running service that forbids allocation after start-up because
+ * an allocation can fail under fragmentation or stall the device mid-run, or a caller
+ * that has no access to the CUDA allocation calls at all. pic_field_solve_noalloc gives
+ * them the field solve of pic_step without any allocation: it builds the right-hand side
+ * b of Eq. (7) from the fields F and the current J, then runs the same Jacobi-PCG, from a
+ * zero initial guess, until ||r||_2 <= cg_rtol ||b||_2, and writes dB.
+ *
+ * Its scratch (three solver vectors of 3*nx*ny FP64 values, reduction partials, solver
+ * state) is a fixed array in the library's device memory, sized for
+ * PIC_NOALLOC_MAX_CELLS cells (about 4.7 MB). Every GPU that loads the library holds it
+ * until the process exits. The call makes no cudaMalloc, cudaFree or other allocating
+ * call; it enqueues copies, sets and kernels on `stream` and synchronises that stream
+ * before returning.
+ *
+ *   nx, ny          grid size; nx, ny >= 8 and nx*ny <= PIC_NOALLOC_MAX_CELLS
+ *   dx, dy, cfl, theta, cg_rtol, cg_max_iter   as in pic_params
+ *   F               device pointer, 6*nx*ny FP64: Ex, Ey, Ez, Bx, By, Bz (the layout of
+ *                   pic_fields, component-major, index j*nx + i)
+ *   J               device pointer, 3*nx*ny FP64: Jx, Jy, Jz
+ *   dB              device pointer, 3*nx*ny FP64, written: dBx, dBy, dBz
+ *   iters, rel_resid  optional outputs (NULL allowed): PCG iterations and ||r||/||b||
+ *   stream          cudaStream_t as void* (NULL = the legacy default stream)
+ *   errbuf, errlen  optional caller-owned buffer for a message (NULL allowed)
+ * Returns PIC_OK, PIC_EINVAL (sizes beyond the maximum, bad parameters, or a pointer
+ * that is not device memory), PIC_ECUDA, or PIC_ECG_NOCONV.
+ *
+ * The first call on a device does a one-time set-up on that device (it looks up the
+ * device address of the scratch array); make that first call before any stream capture
+ * on the device. All calls on a device share the one array and each starts by clearing
+ * what must start at zero: calls that overlap on the GPU (on different streams or from
+ * different host threads) race and produce wrong results, so serialise them. */
+#define PIC_NOALLOC_MAX_CELLS 65536
+PIC_API int pic_field_solve_noalloc(int32_t nx, int32_t ny, double dx, double dy, double cfl,
+                                    double theta, double cg_rtol, int32_t cg_max_iter,
+                                    const double* F, const double* J, double* dB,
+                                    int32_t* iters, double* rel_resid, void* stream,
+                                    char* errbuf, size_t errlen);
+
 /* Message of the last failure on this handle (or of the last failed pic_init when s
  * is NULL). The string stays valid until the next call on the handle. */
 PIC_API const char* pic_last_error(const pic_sim* s);

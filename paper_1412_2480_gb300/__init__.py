@@ -221,6 +221,34 @@ def pic_free(h) -> None:
     lib().pic_free(h)
 
 
+PIC_NOALLOC_MAX_CELLS = 65536
+
+
+def pic_field_solve_noalloc(nx, ny, dx, dy, cfl, theta, cg_rtol, cg_max_iter, F, J, dB,
+                            stream=None):
+    """Allocation-free field solve (see include/pic.h): F (6*nx*ny), J (3*nx*ny) and dB
+    (3*nx*ny, written) are float64 CUDA tensors. Returns (PCG iterations, ||r||/||b||)."""
+    L = lib()
+    if not getattr(L, "_noalloc_typed", False):
+        L.pic_field_solve_noalloc.argtypes = [C.c_int32, C.c_int32, C.c_double, C.c_double,
+                                              C.c_double, C.c_double, C.c_double, C.c_int32,
+                                              C.c_void_p, C.c_void_p, C.c_void_p,
+                                              C.POINTER(C.c_int32), C.POINTER(C.c_double),
+                                              C.c_void_p, C.c_char_p, C.c_size_t]
+        L.pic_field_solve_noalloc.restype = C.c_int
+        L._noalloc_typed = True
+    it, rr = C.c_int32(0), C.c_double(0.0)
+    msg = C.create_string_buffer(256)
+    sp = getattr(stream, "cuda_stream", stream)
+    rc = L.pic_field_solve_noalloc(int(nx), int(ny), float(dx), float(dy), float(cfl),
+                                   float(theta), float(cg_rtol), int(cg_max_iter), _ptr(F),
+                                   _ptr(J), _ptr(dB, True), C.byref(it), C.byref(rr), sp, msg,
+                                   len(msg))
+    if rc != PIC_OK:
+        raise PicError(rc, msg.value.decode())
+    return it.value, rr.value
+
+
 # ---- conveniences built only from the calls above ----------------------------------
 
 def fields_numpy(h, which, nx, ny):
