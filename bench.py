@@ -144,11 +144,15 @@ def make_inputs(name, seed_offset=0, pinned=False):
     return w, sp
 
 
+NO_GRAPH = False  # --no-graph: direct launches (profilers skip kernels of conditional graphs)
+
+
 def new_sim(name, precision, stream=None):
     import paper_1412_2480_gb300 as pic
     nx, ny, ppc, order, g0, uth, cfl, theta, seed = WORKLOADS[name]
     prm = pic.pic_params_default(nx=nx, ny=ny, cfl=cfl, theta=theta, shape_order=order, gamma0=g0,
-                                 ppc=ppc, precision=precision, cg_rtol=1e-10, cg_max_iter=200)
+                                 ppc=ppc, precision=precision, cg_rtol=1e-10, cg_max_iter=200,
+                                 flags=pic.PIC_NO_GRAPH if NO_GRAPH else 0)
     h = pic.pic_init(prm)
     if stream is not None:
         pic.pic_set_stream(h, stream)
@@ -299,8 +303,12 @@ def main():
     ap.add_argument("--prof-steps", type=int, default=4)
     ap.add_argument("--skip-fp64", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-graph", action="store_true",
+                    help="launch kernels directly (for profiler launch lists), not a bench number")
     args = ap.parse_args()
     args.warmup = max(args.warmup, 3)
+    global NO_GRAPH
+    NO_GRAPH = args.no_graph
 
     world = int(os.environ.get("WORLD_SIZE", "1"))
     rank = int(os.environ.get("RANK", "0"))

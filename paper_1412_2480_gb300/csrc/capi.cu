@@ -63,6 +63,10 @@ struct pic_sim {
     cudaGraph_t pgraph[5] = {nullptr};
     cudaGraphExec_t pexec[5] = {nullptr};
     cudaStream_t body_stream = nullptr;
+    cudaStream_t body_stream2 = nullptr;  // captures the inner loop of the MIXED32 solve
+    // MIXED32 mixed-precision PCG: FP64 right-hand side and FP32 inner vectors
+    double* bvec = nullptr;
+    float *r32 = nullptr, *p32 = nullptr, *q32 = nullptr, *e32 = nullptr;
     // bookkeeping
     long long steps = 0;
     unsigned long long seen_cfl = 0, seen_nan = 0, seen_lost = 0;
@@ -189,6 +193,11 @@ FieldArgs field_args(pic_sim* s, int use_cond, cudaGraphConditionalHandle cond) 
     a.st = s->st;
     a.cond = cond;
     a.use_cond = use_cond;
+    a.b = s->bvec;
+    a.r32 = s->r32;
+    a.p32 = s->p32;
+    a.q32 = s->q32;
+    a.e32 = s->e32;
     return a;
 }
 
@@ -254,6 +263,48 @@ void enqueue_part(pic_sim* s, int part, cudaStream_t st) {
     }
 }
 
+// A conditional handle on the graph that stream `st` is capturing into.
+cudaError_t new_handle(cudaStream_t st, cudaGraphConditionalHandle* h) {
+    cudaStreamCaptureStatus cs;
+    cudaGraph_t cap = nullptr;
+    cudaError_t e = cudaStreamGetCaptureInfo(st, &cs, nullptr, &cap, nullptr, nullptr, nullptr);
+    if (e == cudaSuccess) e = cudaGraphConditionalHandleCreate(h, cap, 0, cudaGraphCondAssignDefault);
+    return e;
+}
+
+// Append WHILE(h) { body } at the capture position of `st`; the body is captured on
+// stream `bs` into the conditional node's body graph.
+template <typename Body>
+cudaError_t add_while(cudaStream_t st, cudaGraphConditionalHandle h, cudaStream_t bs, Body body) {
+    cudaStreamCaptureStatus cs;
+    cudaGraph_t cap = nullptr;
+    const cudaGraphNode_t* deps = nullptr;
+    size_t nd = 0;
+    cudaError_t e = cudaStreamGetCaptureInfo(st, &cs, nullptr, &cap, &deps, nullptr, &nd);
+    cudaGraphNode_t wnode{};
+    cudaGraphNodeParams cp{};
+    if (e == cudaSuccess) {
+        cp.type = cudaGraphNodeTypeConditional;
+        cp.conditional.handle = h;
+        cp.conditional.type = cudaGraphCondTypeWhile;
+        cp.conditional.size = 1;
+        e = cudaGraphAddNode(&wnode, cap, deps, nullptr, nd, &cp);
+    }
+    if (e == cudaSuccess)
+        e = cudaStreamUpdateCaptureDependencies(st, &wnode, nullptr, 1, cudaStreamSetCaptureDependencies);
+    if (e == cudaSuccess) {
+        e = cudaStreamBeginCaptureToGraph(bs, cp.conditional.phGraph_out[0], nullptr, nullptr, 0,
+                                          cudaStreamCaptureModeThreadLocal);
+        if (e == cudaSuccess) {
+            const cudaError_t eb = body(bs);
+            cudaGraph_t out = nullptr;
+            e = cudaStreamEndCapture(bs, &out);
+            if (e == cudaSuccess) e = eb;
+        }
+    }
+    return e;
+}
+
 // Capture the parts in `mask` (in order) into one graph. The field-solve part becomes
 // rhs -> WHILE(any simulation active){PCG iteration} -> E/B update, the WHILE condition
 // being set on the device by the rhs and PCG kernels.
@@ -267,38 +318,29 @@ int capture(pic_sim* s, int mask, cudaGraph_t* gout, cudaGraphExec_t* xout) {
             enqueue_part(s, part, st);
             continue;
         }
-        cudaStreamCaptureStatus cs;
-        cudaGraph_t cap = nullptr;
-        const cudaGraphNode_t* deps = nullptr;
-        size_t nd = 0;
         cudaGraphConditionalHandle h{};
-        e = cudaStreamGetCaptureInfo(st, &cs, nullptr, &cap, &deps, nullptr, &nd);
-        if (e == cudaSuccess) e = cudaGraphConditionalHandleCreate(&h, cap, 0, cudaGraphCondAssignDefault);
-        if (e == cudaSuccess) {
-            launch_rhs(field_args(s, 1, h), st);
-            e = cudaStreamGetCaptureInfo(st, &cs, nullptr, &cap, &deps, nullptr, &nd);
-        }
-        cudaGraphNode_t wnode{};
-        cudaGraphNodeParams cp{};
-        if (e == cudaSuccess) {
-            cp.type = cudaGraphNodeTypeConditional;
-            cp.conditional.handle = h;
-            cp.conditional.type = cudaGraphCondTypeWhile;
-            cp.conditional.size = 1;
-            e = cudaGraphAddNode(&wnode, cap, deps, nullptr, nd, &cp);
-        }
-        if (e == cudaSuccess)
-            e = cudaStreamUpdateCaptureDependencies(st, &wnode, nullptr, 1,
-                                                    cudaStreamSetCaptureDependencies);
-        if (e == cudaSuccess) {
-            cudaGraph_t body = cp.conditional.phGraph_out[0];
-            e = cudaStreamBeginCaptureToGraph(s->body_stream, body, nullptr, nullptr, 0,
-                                              cudaStreamCaptureModeThreadLocal);
-            if (e == cudaSuccess) {
-                launch_cg_iteration(field_args(s, 1, h), s->body_stream);
-                cudaGraph_t out = nullptr;
-                e = cudaStreamEndCapture(s->body_stream, &out);
-            }
+        e = new_handle(st, &h);
+        if (e == cudaSuccess) launch_rhs(field_args(s, 1, h), st);
+        if (e == cudaSuccess && s->prm.precision == PIC_FP64) {
+            e = add_while(st, h, s->body_stream,
+                          [&](cudaStream_t bs) { launch_cg_iteration(field_args(s, 1, h), bs); return cudaSuccess; });
+        } else if (e == cudaSuccess) {
+            // mixed precision: WHILE(outer) { inner begin; WHILE(inner) { FP32 iteration };
+            // x += e, r = b - A x }
+            e = add_while(st, h, s->body_stream, [&](cudaStream_t bs) {
+                cudaGraphConditionalHandle hin{};
+                cudaError_t ei = new_handle(bs, &hin);
+                if (ei != cudaSuccess) return ei;
+                FieldArgs a = field_args(s, 1, h);
+                a.cond_in = hin;
+                launch_mp_inner_begin(a, bs);
+                ei = add_while(bs, hin, s->body_stream2, [&](cudaStream_t bs2) {
+                    launch_mp_inner_iteration(a, bs2);
+                    return cudaSuccess;
+                });
+                if (ei == cudaSuccess) launch_mp_refine(a, bs);
+                return ei;
+            });
         }
         if (e == cudaSuccess) launch_field_update(field_args(s, 0, 0), st);
     }
@@ -332,16 +374,29 @@ int run_step_direct(pic_sim* s) {
     enqueue_part(s, kPartPre, st);
     enqueue_part(s, kPartPush, st);
     enqueue_part(s, kPartPost, st);
-    launch_rhs(field_args(s, 0, 0), st);
-    unsigned int nact = 0;
+    const FieldArgs a = field_args(s, 0, 0);
+    launch_rhs(a, st);
+    unsigned int nact = 0, nin = 0;
     CK(cudaMemcpyAsync(&nact, &s->st->n_active, sizeof nact, cudaMemcpyDeviceToHost, st));
     CK(cudaStreamSynchronize(st));
     while (nact > 0) {
-        launch_cg_iteration(field_args(s, 0, 0), st);
+        if (s->prm.precision == PIC_FP64) {
+            launch_cg_iteration(a, st);
+        } else {
+            launch_mp_inner_begin(a, st);
+            CK(cudaMemcpyAsync(&nin, &s->st->n_in_active, sizeof nin, cudaMemcpyDeviceToHost, st));
+            CK(cudaStreamSynchronize(st));
+            while (nin > 0) {
+                launch_mp_inner_iteration(a, st);
+                CK(cudaMemcpyAsync(&nin, &s->st->n_in_active, sizeof nin, cudaMemcpyDeviceToHost, st));
+                CK(cudaStreamSynchronize(st));
+            }
+            launch_mp_refine(a, st);
+        }
         CK(cudaMemcpyAsync(&nact, &s->st->n_active, sizeof nact, cudaMemcpyDeviceToHost, st));
         CK(cudaStreamSynchronize(st));
     }
-    launch_field_update(field_args(s, 0, 0), st);
+    launch_field_update(a, st);
     enqueue_part(s, kPartEnd, st);
     CK(cudaGetLastError());
     return PIC_OK;
@@ -466,7 +521,11 @@ int pic_init(const pic_params* prm, pic_sim** out) {
     s->ntot = (long long)prm->nx * prm->ny;
     s->hgrids[0].cell_off = 0;
     s->hgrids[0].blk_first = 0;
-    s->hgrids[0].nblk = (int)((s->ntot + kFieldThreads - 1) / kFieldThreads);
+    // field kernels: grid-stride loops over at most 4 blocks per SM
+    int nsm = 152;
+    cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, s->device);
+    s->hgrids[0].nblk = (int)std::min<long long>((s->ntot + kFieldThreads - 1) / kFieldThreads,
+                                                 4ll * std::max(nsm, 1));
     s->nblk = s->hgrids[0].nblk;
     s->hblk_grid.assign(s->nblk, 0);
     const long long n3 = 3 * s->ntot;
@@ -475,6 +534,7 @@ int pic_init(const pic_params* prm, pic_sim** out) {
         if (e == cudaSuccess) e = r;
     };
     A(cudaStreamCreateWithFlags(&s->body_stream, cudaStreamNonBlocking));
+    A(cudaStreamCreateWithFlags(&s->body_stream2, cudaStreamNonBlocking));
     A(cudaStreamCreateWithFlags(&s->own_stream, cudaStreamNonBlocking));
     s->stream = s->own_stream;
     A(dalloc(&s->F, 6 * s->ntot));
@@ -494,6 +554,11 @@ int pic_init(const pic_params* prm, pic_sim** out) {
         A(dalloc(&s->J64, n3));
     } else {
         A(dalloc(&s->Jfix, n3));
+        A(dalloc(&s->bvec, n3));
+        A(dalloc(&s->r32, n3));
+        A(dalloc(&s->p32, n3));
+        A(dalloc(&s->q32, n3));
+        A(dalloc(&s->e32, n3));
         A(dalloc(&s->F32, 6 * s->ntot));
     }
     if (e != cudaSuccess) {
@@ -799,11 +864,13 @@ void pic_free(pic_sim* s) {
     drop_graph(s);
     if (s->mixed) mixed_destroy(s->mixed);
     void* ptrs[] = {s->dgrids, s->dblk_grid, s->F, s->J64, s->Jfix, s->F32, s->x, s->r, s->p, s->q,
-                    s->part, s->cg, s->done, s->st, s->tmp, s->dsegs, s->dblk_seg[0], s->dblk_seg[1]};
+                    s->part, s->cg, s->done, s->st, s->tmp, s->dsegs, s->dblk_seg[0], s->dblk_seg[1],
+                    s->bvec, s->r32, s->p32, s->q32, s->e32};
     for (void* p : ptrs) dfree(p);
     for (int sp = 0; sp < 2; sp++)
         for (int a = 0; a < 5; a++) dfree(s->pa[sp][a]);
     if (s->body_stream) cudaStreamDestroy(s->body_stream);
+    if (s->body_stream2) cudaStreamDestroy(s->body_stream2);
     if (s->own_stream) cudaStreamDestroy(s->own_stream);
     for (int k = 0; k < 6; k++)
         if (s->ev[k]) cudaEventDestroy(s->ev[k]);

@@ -24,7 +24,17 @@ struct FieldArgs {
     DevStatus* st;
     cudaGraphConditionalHandle cond;  // WHILE-node handle of the PCG loop
     int use_cond;                      // 1 when running inside the captured step graph
+    // mixed-precision refinement (MIXED32 only; nullptr otherwise)
+    double* b;                         // 3 * ntot right-hand side of Eq. (7)
+    float *r32, *p32, *q32, *e32;      // 3 * ntot each, inner FP32 CG vectors
+    cudaGraphConditionalHandle cond_in;  // WHILE-node handle of the inner loop
 };
+
+// Mixed-precision PCG pieces (see fields.cu): inner start, one inner iteration, and the
+// FP64 refinement x += e, r = b - A x.
+void launch_mp_inner_begin(const FieldArgs& a, cudaStream_t s);
+void launch_mp_inner_iteration(const FieldArgs& a, cudaStream_t s);
+void launch_mp_refine(const FieldArgs& a, cudaStream_t s);
 
 // Per-step prologue (deferred stop, step counter, accumulators) and epilogue.
 void launch_step_begin(const FieldArgs& a, cudaStream_t s);

@@ -23,13 +23,11 @@ struct Cell {
     bool valid;
 };
 
-__device__ __forceinline__ Cell locate(const GridDev* grids, const int* blk_grid) {
+// Cell l (0 <= l < ncell) of simulation g.
+__device__ __forceinline__ Cell cell_at(const GridDev& G, int g, int l) {
     Cell c;
-    c.g = blk_grid[blockIdx.x];
-    const GridDev& G = grids[c.g];
-    const int local = (blockIdx.x - G.blk_first) * blockDim.x + threadIdx.x;
-    c.valid = local < G.ncell;
-    const int l = c.valid ? local : 0;
+    c.g = g;
+    c.valid = true;
     c.j = l / G.nx;
     c.i = l - c.j * G.nx;
     const long long row = G.cell_off + (long long)c.j * G.nx;
@@ -42,6 +40,14 @@ __device__ __forceinline__ Cell locate(const GridDev* grids, const int* blk_grid
     c.ks = G.cell_off + (long long)js * G.nx + c.i;
     return c;
 }
+
+// Grid-stride loop over the cells of simulation g. A simulation gets a bounded number
+// of blocks (a few per SM), so the per-simulation completion counter of the reductions
+// sees few same-address atomics per kernel.
+#define FOR_CELLS(G, g, c)                                                                  \
+    for (int l_ = (blockIdx.x - (G).blk_first) * blockDim.x + threadIdx.x; l_ < (G).ncell;  \
+         l_ += (G).nblk * blockDim.x)                                                       \
+        if (const Cell c = cell_at((G), (g), l_); true)
 
 // Current value at k: FP64 as is; the MIXED32 current is 64-bit fixed point.
 template <typename T>
@@ -83,7 +89,9 @@ __device__ bool reduce_and_finish(const GridDev& G, int g, double v[NV], double*
 }
 
 // Called by the finishing block of each simulation after it updated cg[g]: the last
-// simulation to finish counts the simulations still iterating and sets the condition.
+// simulation to finish counts the simulations still iterating (the outer PCG, or the
+// inner FP32 loop when INNER) and sets the loop's WHILE condition.
+template <bool INNER = false>
 __device__ void finish_all_grids(int ngrids, int n_participating, CgState* cg, DevStatus* st,
                                  cudaGraphConditionalHandle cond, int use_cond) {
     if (threadIdx.x != 0) return;
@@ -92,8 +100,10 @@ __device__ void finish_all_grids(int ngrids, int n_participating, CgState* cg, D
     if (t != (unsigned)n_participating - 1u) return;
     __threadfence();
     unsigned n = 0;
-    for (int g = 0; g < ngrids; g++) n += (unsigned)__ldcg(&cg[g].active);
-    st->n_active = n;
+    for (int g = 0; g < ngrids; g++)
+        n += (unsigned)(INNER ? __ldcg(&cg[g].in_active) : __ldcg(&cg[g].active));
+    if (INNER) st->n_in_active = n;
+    else st->n_active = n;
     st->grids_done = 0u;
     if (use_cond) cudaGraphSetConditional(cond, n > 0u ? 1u : 0u);
 }
@@ -106,11 +116,12 @@ __global__ void __launch_bounds__(kFieldThreads)
 k_rhs(const GridDev* __restrict__ grids, const int* __restrict__ blk_grid, int ngrids,
       int nblk_total, long long ntot, const double* __restrict__ F, const JT* __restrict__ J,
       double* __restrict__ x, double* __restrict__ r, CgState* cg, double* part,
-      unsigned int* done, DevStatus* st, cudaGraphConditionalHandle cond, int use_cond) {
-    const Cell c = locate(grids, blk_grid);
-    const GridDev& G = grids[c.g];
+      unsigned int* done, DevStatus* st, cudaGraphConditionalHandle cond, int use_cond,
+      double* __restrict__ bout) {
+    const int g = blk_grid[blockIdx.x];
+    const GridDev& G = grids[g];
     double v[4] = {0.0, 0.0, 0.0, 0.0};  // b.b, r.r, |E|^2, |B|^2
-    if (c.valid && !st->stop) {
+    if (!st->stop) FOR_CELLS(G, g, c) {
         const double* Ex = F;
         const double* Ey = F + ntot;
         const double* Ez = F + 2 * ntot;
@@ -149,16 +160,17 @@ k_rhs(const GridDev* __restrict__ grids, const int* __restrict__ blk_grid, int n
                 res = b - Ax;
             }
             r[o + c.k] = res;
+            if (bout) bout[o + c.k] = b;
             v[0] += b * b;
             v[1] += res * res;
             v[3] += bc * bc;
         }
-        v[2] = Ex[c.k] * Ex[c.k] + Ey[c.k] * Ey[c.k] + ez * ez;
+        v[2] += Ex[c.k] * Ex[c.k] + Ey[c.k] * Ey[c.k] + ez * ez;
     }
     double tot[4];
-    if (!reduce_and_finish<4>(G, c.g, v, part, nblk_total, done, tot)) return;
+    if (!reduce_and_finish<4>(G, g, v, part, nblk_total, done, tot)) return;
     if (threadIdx.x == 0) {
-        CgState& s = cg[c.g];
+        CgState& s = cg[g];
         const double e = G.dx * G.dy / (8.0 * kPi);
         s.ue = tot[2] * e;
         s.ub = tot[3] * e;
@@ -166,6 +178,7 @@ k_rhs(const GridDev* __restrict__ grids, const int* __restrict__ blk_grid, int n
         s.rr = tot[1];
         s.beta = 0.0;
         s.iters = 0;
+        s.outer = 0;
         s.rel = tot[0] > 0.0 ? sqrt(tot[1] / tot[0]) : 0.0;
         s.active = (!st->stop && tot[0] > 0.0 && s.rel > G.rtol) ? 1 : 0;
     }
@@ -177,11 +190,14 @@ k_rhs(const GridDev* __restrict__ grids, const int* __restrict__ blk_grid, int n
 __global__ void __launch_bounds__(kFieldThreads)
 k_zero_x(const GridDev* __restrict__ grids, const int* __restrict__ blk_grid, long long ntot,
          double* __restrict__ x) {
-    const Cell c = locate(grids, blk_grid);
-    if (!c.valid || grids[c.g].warm) return;
-    x[c.k] = 0.0;
-    x[ntot + c.k] = 0.0;
-    x[2 * ntot + c.k] = 0.0;
+    const int g = blk_grid[blockIdx.x];
+    const GridDev& G = grids[g];
+    if (G.warm) return;
+    FOR_CELLS(G, g, c) {
+        x[c.k] = 0.0;
+        x[ntot + c.k] = 0.0;
+        x[2 * ntot + c.k] = 0.0;
+    }
 }
 
 // ---- PCG iteration, part 1 ------------------------------------------------------
@@ -196,11 +212,10 @@ k_cg_direction(const GridDev* __restrict__ grids, const int* __restrict__ blk_gr
                unsigned int* done) {
     const int g = blk_grid[blockIdx.x];
     if (!cg[g].active) return;
-    const Cell c = locate(grids, blk_grid);
-    const GridDev& G = grids[c.g];
+    const GridDev& G = grids[g];
     const double beta = cg[g].beta;
     double v[1] = {0.0};
-    if (c.valid) {
+    FOR_CELLS(G, g, c) {
 #pragma unroll
         for (int a = 0; a < 3; a++) {
             const long long o = a * ntot;
@@ -236,11 +251,10 @@ k_cg_update(const GridDev* __restrict__ grids, const int* __restrict__ blk_grid,
     const int g = blk_grid[blockIdx.x];
     const unsigned n_part = st->n_active;  // simulations iterating in this launch
     if (!cg[g].active) return;
-    const Cell c = locate(grids, blk_grid);
-    const GridDev& G = grids[c.g];
+    const GridDev& G = grids[g];
     const double alpha = cg[g].alpha;
     double v[1] = {0.0};
-    if (c.valid) {
+    FOR_CELLS(G, g, c) {
 #pragma unroll
         for (int a = 0; a < 3; a++) {
             const long long o = a * ntot + c.k;
@@ -277,10 +291,10 @@ __global__ void __launch_bounds__(kFieldThreads)
 k_update_E(const GridDev* __restrict__ grids, const int* __restrict__ blk_grid, long long ntot,
            double* __restrict__ F, const JT* __restrict__ J, const double* __restrict__ x,
            const CgState* __restrict__ cg, const DevStatus* st) {
-    const Cell c = locate(grids, blk_grid);
-    if (!c.valid || st->stop) return;
-    const GridDev& G = grids[c.g];
-    const double th = cg[c.g].bb > 0.0 ? G.theta : 0.0;  // dB = 0 when b = 0
+    if (st->stop) return;
+    const int g = blk_grid[blockIdx.x];
+    const GridDev& G = grids[g];
+    const double th = cg[g].bb > 0.0 ? G.theta : 0.0;  // dB = 0 when b = 0
     const double* Bx = F + 3 * ntot;
     const double* By = F + 4 * ntot;
     const double* Bz = F + 5 * ntot;
@@ -290,14 +304,16 @@ k_update_E(const GridDev* __restrict__ grids, const int* __restrict__ blk_grid, 
     auto hx = [&](long long k) { return Bx[k] + th * Xx[k]; };
     auto hy = [&](long long k) { return By[k] + th * Xy[k]; };
     auto hz = [&](long long k) { return Bz[k] + th * Xz[k]; };
-    const double hzc = hz(c.k);
-    const double cx = (hzc - hz(c.ks)) * G.idy;
-    const double cy = -(hzc - hz(c.kw)) * G.idx;
-    const double cz = (hy(c.k) - hy(c.kw)) * G.idx - (hx(c.k) - hx(c.ks)) * G.idy;
     const double f = 4.0 * kPi * G.dt;
-    F[c.k] += G.dt * cx - f * ld(J, c.k, G.jinv);
-    F[ntot + c.k] += G.dt * cy - f * ld(J, ntot + c.k, G.jinv);
-    F[2 * ntot + c.k] += G.dt * cz - f * ld(J, 2 * ntot + c.k, G.jinv);
+    FOR_CELLS(G, g, c) {
+        const double hzc = hz(c.k);
+        const double cx = (hzc - hz(c.ks)) * G.idy;
+        const double cy = -(hzc - hz(c.kw)) * G.idx;
+        const double cz = (hy(c.k) - hy(c.kw)) * G.idx - (hx(c.k) - hx(c.ks)) * G.idy;
+        F[c.k] += G.dt * cx - f * ld(J, c.k, G.jinv);
+        F[ntot + c.k] += G.dt * cy - f * ld(J, ntot + c.k, G.jinv);
+        F[2 * ntot + c.k] += G.dt * cz - f * ld(J, 2 * ntot + c.k, G.jinv);
+    }
 }
 
 // B^{n+1} = B^n + dB, then the FP32 copies used by the MIXED32 gather.
@@ -305,29 +321,34 @@ __global__ void __launch_bounds__(kFieldThreads)
 k_update_B(const GridDev* __restrict__ grids, const int* __restrict__ blk_grid, long long ntot,
            double* __restrict__ F, const double* __restrict__ x, const CgState* __restrict__ cg,
            const DevStatus* st, float* __restrict__ F32) {
-    const Cell c = locate(grids, blk_grid);
-    if (!c.valid || st->stop) return;
-    const bool have = cg[c.g].bb > 0.0;
+    if (st->stop) return;
+    const int g = blk_grid[blockIdx.x];
+    const GridDev& G = grids[g];
+    const bool have = cg[g].bb > 0.0;
+    FOR_CELLS(G, g, c) {
 #pragma unroll
-    for (int a = 0; a < 3; a++) {
-        const long long o = (3 + a) * ntot + c.k;
-        const double b = F[o] + (have ? x[a * ntot + c.k] : 0.0);
-        F[o] = b;
-        if (F32) F32[o] = (float)b;
-    }
-    if (F32) {
+        for (int a = 0; a < 3; a++) {
+            const long long o = (3 + a) * ntot + c.k;
+            const double b = F[o] + (have ? x[a * ntot + c.k] : 0.0);
+            F[o] = b;
+            if (F32) F32[o] = (float)b;
+        }
+        if (F32) {
 #pragma unroll
-        for (int a = 0; a < 3; a++) F32[a * ntot + c.k] = (float)F[a * ntot + c.k];
+            for (int a = 0; a < 3; a++) F32[a * ntot + c.k] = (float)F[a * ntot + c.k];
+        }
     }
 }
 
 __global__ void __launch_bounds__(kFieldThreads)
 k_to_f32(const GridDev* __restrict__ grids, const int* __restrict__ blk_grid, long long ntot,
          const double* __restrict__ F, float* __restrict__ F32) {
-    const Cell c = locate(grids, blk_grid);
-    if (!c.valid) return;
+    const int g = blk_grid[blockIdx.x];
+    const GridDev& G = grids[g];
+    FOR_CELLS(G, g, c) {
 #pragma unroll
-    for (int a = 0; a < 6; a++) F32[a * ntot + c.k] = (float)F[a * ntot + c.k];
+        for (int a = 0; a < 6; a++) F32[a * ntot + c.k] = (float)F[a * ntot + c.k];
+    }
 }
 
 // Start of a step: an error raised during the previous step stops this one; clear the
@@ -351,6 +372,178 @@ __global__ void k_step_end(int ngrids, CgState* cg, const DevStatus* st) {
     }
 }
 
+// ---- Mixed-precision PCG (MIXED32) ----------------------------------------------
+// Iterative refinement around an FP32 inner CG: with the FP64 residual r = b - A x, the
+// inner loop solves A e = r in FP32 vectors (dot products accumulated in FP64) to a
+// relative tolerance tol_in, then x += e and r = b - A x are formed in FP64. The outer
+// test is the same ||r||_2 <= rtol ||b||_2 on the FP64 residual, so the solution meets
+// the tolerance of the plain FP64 PCG while most vector traffic and arithmetic is FP32.
+constexpr int kMaxInnerIters = 64;
+
+__global__ void __launch_bounds__(kFieldThreads)
+k_mp_begin(const GridDev* __restrict__ grids, const int* __restrict__ blk_grid, int ngrids,
+           int nblk_total, long long ntot, const double* __restrict__ r, float* __restrict__ r32,
+           float* __restrict__ e32, CgState* cg, double* part, unsigned int* done, DevStatus* st,
+           cudaGraphConditionalHandle cond_in, int use_cond) {
+    const int g = blk_grid[blockIdx.x];
+    const unsigned n_part = st->n_active;
+    if (!cg[g].active) return;
+    const GridDev& G = grids[g];
+    const double scale = sqrt(3.0 * G.ncell / cg[g].rr);  // r32 of unit RMS
+    float acc = 0.f;
+    FOR_CELLS(G, g, c) {
+#pragma unroll
+        for (int a = 0; a < 3; a++) {
+            const long long o = a * ntot + c.k;
+            const float f = (float)(r[o] * scale);
+            r32[o] = f;
+            e32[o] = 0.f;
+            acc = fmaf(f, f, acc);
+        }
+    }
+    double v[1] = {(double)acc};
+    double tot[1];
+    if (!reduce_and_finish<1>(G, g, v, part, nblk_total, done, tot)) return;
+    if (threadIdx.x == 0) {
+        CgState& s = cg[g];
+        s.rr_in0 = tot[0];
+        s.rr_in = tot[0];
+        s.beta_in = 0.0;
+        s.in_iters = 0;
+        s.in_scale = scale;
+        // ask the inner loop for what the outer test still needs, within FP32's reach
+        s.tol_in = fmax(2e-6, 0.5 * G.rtol * sqrt(s.bb / fmax(s.rr, 1e-300)));
+        s.in_active = tot[0] > 0.0 ? 1 : 0;
+    }
+    finish_all_grids<true>(ngrids, (int)n_part, cg, st, cond_in, use_cond);
+}
+
+__global__ void __launch_bounds__(kFieldThreads)
+k_mp_direction(const GridDev* __restrict__ grids, const int* __restrict__ blk_grid, int ngrids,
+               int nblk_total, long long ntot, const float* __restrict__ r32, float* __restrict__ p32,
+               float* __restrict__ q32, CgState* cg, double* part, unsigned int* done) {
+    const int g = blk_grid[blockIdx.x];
+    if (!cg[g].in_active) return;
+    const GridDev& G = grids[g];
+    const float beta = (float)cg[g].beta_in;
+    const float c0 = (float)G.c0, cx = (float)G.cx, cy = (float)G.cy;
+    float acc = 0.f;  // a thread's few products in FP32, summed across threads in FP64
+    FOR_CELLS(G, g, c) {
+#pragma unroll
+        for (int a = 0; a < 3; a++) {
+            const long long o = a * ntot;
+            const float* R = r32 + o;
+            const float rc = R[c.k];
+            const float Ar = c0 * rc - cx * (R[c.ke] + R[c.kw]) - cy * (R[c.kn] + R[c.ks]);
+            float pn, qn;
+            if (beta == 0.f) {
+                pn = rc;
+                qn = Ar;
+            } else {
+                pn = fmaf(beta, p32[o + c.k], rc);
+                qn = fmaf(beta, q32[o + c.k], Ar);
+            }
+            p32[o + c.k] = pn;
+            q32[o + c.k] = qn;
+            acc = fmaf(pn, qn, acc);
+        }
+    }
+    double v[1] = {(double)acc};
+    double tot[1];
+    if (!reduce_and_finish<1>(G, g, v, part, nblk_total, done, tot)) return;
+    if (threadIdx.x == 0) cg[g].alpha_in = cg[g].rr_in / tot[0];
+}
+
+__global__ void __launch_bounds__(kFieldThreads)
+k_mp_update(const GridDev* __restrict__ grids, const int* __restrict__ blk_grid, int ngrids,
+            int nblk_total, long long ntot, float* __restrict__ e32, float* __restrict__ r32,
+            const float* __restrict__ p32, const float* __restrict__ q32, CgState* cg, double* part,
+            unsigned int* done, DevStatus* st, cudaGraphConditionalHandle cond_in, int use_cond) {
+    const int g = blk_grid[blockIdx.x];
+    const unsigned n_part = st->n_in_active;
+    if (!cg[g].in_active) return;
+    const GridDev& G = grids[g];
+    const float alpha = (float)cg[g].alpha_in;
+    float acc = 0.f;
+    FOR_CELLS(G, g, c) {
+#pragma unroll
+        for (int a = 0; a < 3; a++) {
+            const long long o = a * ntot + c.k;
+            e32[o] = fmaf(alpha, p32[o], e32[o]);
+            const float rn = fmaf(-alpha, q32[o], r32[o]);
+            r32[o] = rn;
+            acc = fmaf(rn, rn, acc);
+        }
+    }
+    double v[1] = {(double)acc};
+    double tot[1];
+    if (!reduce_and_finish<1>(G, g, v, part, nblk_total, done, tot)) return;
+    if (threadIdx.x == 0) {
+        CgState& s = cg[g];
+        s.beta_in = tot[0] / s.rr_in;
+        s.rr_in = tot[0];
+        s.in_iters += 1;
+        s.iters += 1;
+        if (sqrt(tot[0] / s.rr_in0) <= s.tol_in || s.in_iters >= kMaxInnerIters || s.iters >= G.maxit)
+            s.in_active = 0;
+    }
+    finish_all_grids<true>(ngrids, (int)n_part, cg, st, cond_in, use_cond);
+}
+
+// x += e (FP64).
+__global__ void __launch_bounds__(kFieldThreads)
+k_mp_x(const GridDev* __restrict__ grids, const int* __restrict__ blk_grid, long long ntot,
+       double* __restrict__ x, const float* __restrict__ e32, const CgState* __restrict__ cg) {
+    const int g = blk_grid[blockIdx.x];
+    if (!cg[g].active) return;
+    const GridDev& G = grids[g];
+    const double inv = 1.0 / cg[g].in_scale;
+    FOR_CELLS(G, g, c) {
+#pragma unroll
+        for (int a = 0; a < 3; a++) x[a * ntot + c.k] += (double)e32[a * ntot + c.k] * inv;
+    }
+}
+
+// r = b - A x (FP64) and the outer convergence test.
+__global__ void __launch_bounds__(kFieldThreads)
+k_mp_r(const GridDev* __restrict__ grids, const int* __restrict__ blk_grid, int ngrids,
+       int nblk_total, long long ntot, const double* __restrict__ b, const double* __restrict__ x,
+       double* __restrict__ r, CgState* cg, double* part, unsigned int* done, DevStatus* st,
+       cudaGraphConditionalHandle cond, int use_cond) {
+    const int g = blk_grid[blockIdx.x];
+    const unsigned n_part = st->n_active;
+    if (!cg[g].active) return;
+    const GridDev& G = grids[g];
+    double v[1] = {0.0};
+    FOR_CELLS(G, g, c) {
+#pragma unroll
+        for (int a = 0; a < 3; a++) {
+            const long long o = a * ntot;
+            const double* X = x + o;
+            const double Ax = G.c0 * X[c.k] - G.cx * (X[c.ke] + X[c.kw]) - G.cy * (X[c.kn] + X[c.ks]);
+            const double rn = b[o + c.k] - Ax;
+            r[o + c.k] = rn;
+            v[0] += rn * rn;
+        }
+    }
+    double tot[1];
+    if (!reduce_and_finish<1>(G, g, v, part, nblk_total, done, tot)) return;
+    if (threadIdx.x == 0) {
+        CgState& s = cg[g];
+        s.rr = tot[0];
+        s.rel = sqrt(tot[0] / s.bb);
+        s.outer += 1;
+        if (s.rel <= G.rtol) {
+            s.active = 0;
+        } else if (s.iters >= G.maxit || s.outer >= G.maxit) {
+            s.active = 0;
+            atomicAdd(&st->cg_noconv, 1u);
+            st->stop_next = 1u;
+        }
+    }
+    finish_all_grids(ngrids, (int)n_part, cg, st, cond, use_cond);
+}
+
 }  // namespace
 
 void launch_step_begin(const FieldArgs& a, cudaStream_t s) {
@@ -366,11 +559,34 @@ void launch_rhs(const FieldArgs& a, cudaStream_t s) {
     if (a.Jfix)
         k_rhs<long long><<<a.nblk, kFieldThreads, 0, s>>>(a.grids, a.blk_grid, a.ngrids, a.nblk,
                                                           a.ntot, a.F, a.Jfix, a.x, a.r, a.cg,
-                                                          a.part, a.done, a.st, a.cond, a.use_cond);
+                                                          a.part, a.done, a.st, a.cond, a.use_cond,
+                                                          a.b);
     else
         k_rhs<double><<<a.nblk, kFieldThreads, 0, s>>>(a.grids, a.blk_grid, a.ngrids, a.nblk,
                                                        a.ntot, a.F, a.J64, a.x, a.r, a.cg,
-                                                       a.part, a.done, a.st, a.cond, a.use_cond);
+                                                       a.part, a.done, a.st, a.cond, a.use_cond,
+                                                       a.b);
+}
+
+void launch_mp_inner_begin(const FieldArgs& a, cudaStream_t s) {
+    k_mp_begin<<<a.nblk, kFieldThreads, 0, s>>>(a.grids, a.blk_grid, a.ngrids, a.nblk, a.ntot, a.r,
+                                                a.r32, a.e32, a.cg, a.part, a.done, a.st, a.cond_in,
+                                                a.use_cond);
+}
+
+void launch_mp_inner_iteration(const FieldArgs& a, cudaStream_t s) {
+    k_mp_direction<<<a.nblk, kFieldThreads, 0, s>>>(a.grids, a.blk_grid, a.ngrids, a.nblk, a.ntot,
+                                                    a.r32, a.p32, a.q32, a.cg, a.part, a.done);
+    k_mp_update<<<a.nblk, kFieldThreads, 0, s>>>(a.grids, a.blk_grid, a.ngrids, a.nblk, a.ntot,
+                                                 a.e32, a.r32, a.p32, a.q32, a.cg, a.part, a.done,
+                                                 a.st, a.cond_in, a.use_cond);
+}
+
+void launch_mp_refine(const FieldArgs& a, cudaStream_t s) {
+    k_mp_x<<<a.nblk, kFieldThreads, 0, s>>>(a.grids, a.blk_grid, a.ntot, a.x, a.e32, a.cg);
+    k_mp_r<<<a.nblk, kFieldThreads, 0, s>>>(a.grids, a.blk_grid, a.ngrids, a.nblk, a.ntot, a.b,
+                                            a.x, a.r, a.cg, a.part, a.done, a.st, a.cond,
+                                            a.use_cond);
 }
 
 void launch_cg_iteration(const FieldArgs& a, cudaStream_t s) {

@@ -47,6 +47,10 @@ struct CgState {
     double ue, ub, uk;    // energies of the step being computed (time level n)
     int active, iters, last_iters, max_iters;
     long long total_iters;
+    // mixed-precision refinement (MIXED32): FP32 inner CG on A e = r
+    double rr_in, rr_in0, alpha_in, beta_in, tol_in;
+    double in_scale;  // r32 = r * in_scale (unit RMS), e = e32 / in_scale
+    int in_active, in_iters, outer, pad;
 };
 
 // Device status words shared by all kernels of a handle.
@@ -60,6 +64,7 @@ struct DevStatus {
     unsigned long long steps_done;   // steps completed (the failing step included)
     unsigned int grids_done;         // counter of the last-grid-finished pattern
     unsigned int n_active;           // simulations whose PCG is still iterating
+    unsigned int n_in_active;        // simulations whose inner FP32 CG is still iterating
     unsigned long long lost;         // MIXED32: particles dropped because the overflow list was full
     unsigned int parity;             // MIXED32: which of the two bin buffers is current
     unsigned long long ovf_count[2]; // MIXED32: particles in each overflow list

@@ -145,3 +145,22 @@ def test_mixed_empty_and_single_species():
                           cg_rtol=1e-13)
     Fo, po, _ = run_oracle(nx, ny, w, sp[:1], F0, 2, 2, cg_rtol=1e-13)
     assert rel(Fg[:9], Fo[:9]) < TOL32
+
+
+@pytest.mark.parametrize("theta,cfl", [(0.5, 1.0), (0.75, 0.9)])
+def test_mixed_precision_field_solve_meets_fp64_tolerance(theta, cfl):
+    # The MIXED32 solve refines FP32 inner CG sweeps against the FP64 residual, so the
+    # vacuum mode must still follow the exact root of Eq. (10) to FP64 accuracy.
+    import math
+    from closed_forms import amplification
+    nx, ny, mx, my = 48, 32, 5, 3
+    kx, ky = 2 * math.pi * mx / nx, 2 * math.pi * my / ny
+    jj, ii = np.meshgrid(np.arange(ny), np.arange(nx), indexing="ij")
+    F0 = np.zeros((6, ny, nx))
+    F0[5] = np.cos(kx * (ii + 0.5) + ky * (jj + 0.5))
+    lam = amplification(theta, cfl * math.hypot(math.sin(kx / 2), math.sin(ky / 2)))
+    for n in (1, 6):
+        Fg, _, mom = run_gpu(nx, ny, 1, [], F0, n, 2, cfl=cfl, theta=theta, cg_rtol=1e-13,
+                             precision=pic.PIC_MIXED32, want_particles=False)
+        np.testing.assert_allclose(Fg[5], (lam**n).real * F0[5], rtol=0, atol=1e-12)
+        assert 0 < mom["cg_rel_resid"] <= 1e-13
