@@ -62,6 +62,7 @@ struct pic_sim {
     cudaEvent_t ev[6] = {nullptr};
     cudaGraph_t pgraph[5] = {nullptr};
     cudaGraphExec_t pexec[5] = {nullptr};
+    long long graph_gen = 0;  // MIXED32 buffer generation the captured graphs point into
     cudaStream_t body_stream = nullptr;
     cudaStream_t body_stream2 = nullptr;  // captures the inner loop of the MIXED32 solve
     // MIXED32 mixed-precision PCG: FP64 right-hand side and FP32 inner vectors
@@ -199,6 +200,17 @@ FieldArgs field_args(pic_sim* s, int use_cond, cudaGraphConditionalHandle cond) 
     a.q32 = s->q32;
     a.e32 = s->e32;
     return a;
+}
+
+void drop_graph(pic_sim* s);
+
+// Graphs hold buffer pointers as kernel arguments: drop them once MIXED32 re-binning
+// has reallocated its buffers.
+void check_graph_generation(pic_sim* s) {
+    if (s->mixed && mixed_generation(s->mixed) != s->graph_gen) {
+        drop_graph(s);
+        s->graph_gen = mixed_generation(s->mixed);
+    }
 }
 
 void drop_graph(pic_sim* s) {
@@ -699,6 +711,7 @@ int pic_step(pic_sim* s, int32_t n) {
         if (rc) return rc;
     }
     const bool graph = !(s->prm.flags & PIC_NO_GRAPH);
+    check_graph_generation(s);
     if (graph && !s->gexec) {
         if (int rc = build_graph(s)) return rc;
     }
@@ -727,6 +740,7 @@ int pic_profile(pic_sim* s, int32_t n, double* out, int32_t n_out) {
         int rc = mixed_before_steps(s->mixed, s->stream, s->err);
         if (rc) return rc;
     }
+    check_graph_generation(s);
     for (int k = 0; k < kNumParts; k++)
         if (!s->pexec[k])
             if (int rc = capture(s, 1 << k, &s->pgraph[k], &s->pexec[k])) return rc;

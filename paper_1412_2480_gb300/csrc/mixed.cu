@@ -86,6 +86,7 @@ struct MixedState {
     long long nslots = 0, ovf_cap = 0;
     long long n[2] = {0, 0};
     long long rebins = 0;
+    long long gen = 0;  // allocation generation of the bin buffers
     size_t smem = 0;
 };
 
@@ -790,6 +791,7 @@ int alloc_bins(MixedState* m, long long cap, long long capo, cudaStream_t st, st
         if (m->buf[p]) cudaFree(m->buf[p]);
         m->buf[p] = nullptr;
     }
+    m->gen++;
     G.cap = cap;
     G.capo = capo;
     G.bin_off = 0;
@@ -1036,6 +1038,7 @@ int mixed_after_steps(MixedState* m, cudaStream_t st, std::string& err) {
 
 long long mixed_count(MixedState* m, int s) { return m->n[s]; }
 long long mixed_rebins(MixedState* m) { return m->rebins; }
+long long mixed_generation(MixedState* m) { return m->gen; }
 
 int mixed_particles(MixedState* m, int s, double* out, long long n, cudaStream_t st, std::string& err) {
     DevStatus hs{};

@@ -29,6 +29,9 @@ int mixed_before_steps(MixedState* m, cudaStream_t s, std::string& err);
 int mixed_after_steps(MixedState* m, cudaStream_t s, std::string& err);
 long long mixed_count(MixedState* m, int sp);
 long long mixed_rebins(MixedState* m);
+// Bumped whenever device buffers are reallocated: step graphs captured before hold stale
+// pointers and must be rebuilt.
+long long mixed_generation(MixedState* m);
 // Copy out one species as FP64 [x, y, ux, uy, uz] (physical units), bin order.
 int mixed_particles(MixedState* m, int sp, double* out5xn, long long n, cudaStream_t s,
                     std::string& err);

@@ -34,7 +34,9 @@ struct GridDev {
     int tx, ty, ntx, nty; // tile size and tile counts
     int tile_first, ntiles;
     int wx, wy;           // tile window size: (tx + 5) x (ty + 5), origin (X0-2, Y0-2)
-    long long cap;        // stayer capacity (particles) per (tile, species) bin
+    int cpt, cpt_pad;     // cells per tile (tx ty) and that rounded up to a multiple of 32
+    int rcap;             // layers of a bin: particles per cell it can hold
+    long long cap;        // layered capacity rcap * cpt_pad per (tile, species) bin
     long long capo;       // capacity of each of the 8 outboxes of a bin
     long long bin_off;    // first particle slot of this simulation's bins
     // MIXED32 current: 64-bit fixed point, J = (double)Jfix * jinv
