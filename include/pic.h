@@ -110,8 +110,8 @@ typedef struct pic_moments_t {
     int32_t cg_iters_max;    /* largest PCG iteration count since the last pic_moments */
     int64_t cg_iters_total;  /* all PCG iterations so far */
     double cg_rel_resid;     /* ||r|| / ||b|| at the end of the last solve */
-    int64_t cfl_violations;  /* moves of one cell or more seen so far (should stay 0) */
-    int64_t overflow_moves;  /* MIXED32: particles routed through the overflow path so far */
+    int64_t cfl_violations;  /* moves of one cell or more seen so far (should stay 0; handle-wide) */
+    int64_t overflow_moves;  /* MIXED32: particles routed through the overflow path so far (handle-wide) */
     int64_t rebins;          /* MIXED32: full re-sorts performed so far */
 } pic_moments_t;
 
@@ -126,6 +126,40 @@ PIC_API void pic_params_default(pic_params* p);
  * handle is written to *out; the caller releases it with pic_free. On failure *out is
  * NULL and the last-error message is available through pic_last_error(NULL). */
 PIC_API int pic_init(const pic_params* p, pic_sim** out);
+
+/* ---- batched parameter scan ----------------------------------------------------------
+ * One handle can hold n independent simulations, each with its own grid size, cell
+ * size, CFL number, theta, shape order, gamma0, ppc, skin depth, PCG settings and tile
+ * shape (the paper's scan over sigma, theta and shape order, Sec. 3.2-3.3). pic_step
+ * advances all of them together: every kernel of the step covers every simulation, the
+ * particle tiles of each shape order are one persistent launch whose CTAs take tiles from
+ * a device work counter (largest first), and the PCG loop runs until the last simulation
+ * has converged, each simulation stopping its own iterations at its own tolerance.
+ *
+ * pic_init_batch: like pic_init for the n parameter sets p[0..n), 1 <= n <= 4096. A batch
+ * of more than one simulation requires PIC_MIXED32 in every set and the same
+ * PIC_NO_GRAPH flag. Simulation 0 is selected.
+ * pic_select: per-simulation calls (pic_load_particles, pic_set_fields, pic_fields,
+ * pic_moments, pic_particle_count, pic_particles, and the PCG iteration count of
+ * pic_profile) address simulation k from now on. The counters cfl_violations and
+ * overflow_moves of pic_moments, and error returns of pic_step, are handle-wide.
+ * pic_batch_size: number of simulations of the handle (0 for NULL). */
+PIC_API int pic_init_batch(const pic_params* p, int32_t n, pic_sim** out);
+PIC_API int pic_select(pic_sim* s, int32_t k);
+PIC_API int pic_batch_size(const pic_sim* s);
+
+/* Tile-shape autotuner for PIC_MIXED32 (the paper has no counterpart: tiles are a
+ * storage detail of this library and do not change the method). For each shape order
+ * present in p[0..n), it builds a scratch batch of those simulations for each candidate
+ * tile shape (32x16, 16x16, 32x8, 64x8, 64x16, 16x8, 32x32 cells, clamped to each grid),
+ * fills it with a synthetic drifting pair plasma of each set's ppc and gamma0, runs two
+ * warm-up steps and `steps` timed steps (1..1000), and writes the fastest shape into
+ * tile_x, tile_y of those sets. best_ms (NULL allowed, else 3 doubles) receives the
+ * tile-kernel milliseconds per step of the chosen shape for orders 1, 2, 3 (0 if the
+ * order is absent). The scratch handles are freed before returning; the simulations
+ * described by p are not touched. Errors: PIC_EINVAL (bad sets), PIC_ECUDA (no shape
+ * could be run); the message is in pic_last_error(NULL). */
+PIC_API int pic_autotune_tiles(pic_params* p, int32_t n, int32_t steps, double* best_ms);
 
 /* Run subsequent work of this handle on the given CUDA stream (cudaStream_t, passed as
  * void*). NULL selects the handle's own non-blocking stream, which is also the default.

@@ -37,9 +37,10 @@ PIC_NO_GRAPH = 2
 PIC_EX, PIC_EY, PIC_EZ, PIC_BX, PIC_BY, PIC_BZ = range(6)
 PIC_JX, PIC_JY, PIC_JZ, PIC_DBX, PIC_DBY, PIC_DBZ = range(6, 12)
 
-EXPORTED = ("pic_params_default", "pic_init", "pic_set_stream", "pic_load_particles",
-            "pic_set_fields", "pic_step", "pic_profile", "pic_fields", "pic_moments", "pic_particle_count",
-            "pic_particles", "pic_last_error", "pic_free")
+EXPORTED = ("pic_params_default", "pic_init", "pic_init_batch", "pic_select", "pic_batch_size",
+            "pic_autotune_tiles", "pic_set_stream", "pic_load_particles", "pic_set_fields",
+            "pic_step", "pic_profile", "pic_fields", "pic_moments", "pic_particle_count",
+            "pic_particles", "pic_field_solve_noalloc", "pic_last_error", "pic_free")
 
 
 class pic_params(C.Structure):
@@ -83,6 +84,11 @@ def lib():
             L.pic_params_default.argtypes = [C.POINTER(pic_params)]
             L.pic_params_default.restype = None
             L.pic_init.argtypes = [C.POINTER(pic_params), C.POINTER(vp)]
+            L.pic_init_batch.argtypes = [C.POINTER(pic_params), C.c_int32, C.POINTER(vp)]
+            L.pic_select.argtypes = [vp, C.c_int32]
+            L.pic_batch_size.argtypes = [vp]
+            L.pic_autotune_tiles.argtypes = [C.POINTER(pic_params), C.c_int32, C.c_int32,
+                                             C.POINTER(C.c_double)]
             L.pic_set_stream.argtypes = [vp, vp]
             L.pic_load_particles.argtypes = [vp, C.c_int32, vp, vp, vp, vp, vp, C.c_int64]
             L.pic_set_fields.argtypes = [vp, C.c_int32, vp, C.c_size_t]
@@ -97,7 +103,8 @@ def lib():
             L.pic_last_error.restype = C.c_char_p
             L.pic_free.argtypes = [vp]
             L.pic_free.restype = None
-            for name in ("pic_init", "pic_set_stream", "pic_load_particles", "pic_set_fields",
+            for name in ("pic_init", "pic_init_batch", "pic_select", "pic_batch_size",
+                         "pic_autotune_tiles", "pic_set_stream", "pic_load_particles", "pic_set_fields",
                          "pic_step", "pic_profile", "pic_fields", "pic_moments", "pic_particles"):
                 getattr(L, name).restype = C.c_int
             _lib = L
@@ -147,6 +154,41 @@ def pic_init(params: pic_params) -> int:
     h = C.c_void_p()
     _check(lib().pic_init(C.byref(params), C.byref(h)), None)
     return h.value
+
+
+def _param_array(params):
+    arr = (pic_params * len(params))()
+    for k, p in enumerate(params):
+        arr[k] = p
+    return arr
+
+
+def pic_init_batch(params) -> int:
+    """One handle holding len(params) simulations (a list of pic_params)."""
+    arr = _param_array(params)
+    h = C.c_void_p()
+    _check(lib().pic_init_batch(arr, len(params), C.byref(h)), None)
+    return h.value
+
+
+def pic_select(h, k) -> None:
+    _check(lib().pic_select(h, int(k)), h)
+
+
+def pic_batch_size(h) -> int:
+    return lib().pic_batch_size(h)
+
+
+def pic_autotune_tiles(params, steps=5):
+    """Pick tile_x, tile_y for every set in `params` (updated in place); returns the
+    tile-kernel ms per step of the chosen shape for shape orders 1, 2, 3."""
+    arr = _param_array(params)
+    best = (C.c_double * 3)()
+    _check(lib().pic_autotune_tiles(arr, len(params), int(steps), best), None)
+    for k in range(len(params)):
+        params[k].tile_x = arr[k].tile_x
+        params[k].tile_y = arr[k].tile_y
+    return [best[0], best[1], best[2]]
 
 
 def pic_set_stream(h, stream) -> None:

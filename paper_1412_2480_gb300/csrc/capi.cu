@@ -27,8 +27,10 @@ struct pic_sim {
     int device = 0;
     cudaStream_t stream = nullptr;      // stream all work of the handle is enqueued on
     cudaStream_t own_stream = nullptr;  // the handle's own non-blocking stream (default)
-    pic_params prm{};
+    pic_params prm{};                // the first simulation's parameters (handle-wide settings)
+    std::vector<pic_params> prms;    // every simulation's parameters
     int ngrids = 1;
+    int sel = 0;                     // simulation addressed by per-simulation calls
     std::vector<GridDev> hgrids;
     GridDev* dgrids = nullptr;
     std::vector<int> hblk_grid;
@@ -129,7 +131,9 @@ int validate(const pic_params* p, std::string& why) {
     if (p->warm_start != PIC_WS_ZERO && p->warm_start != PIC_WS_PREV)
         return bad("warm_start must be PIC_WS_ZERO or PIC_WS_PREV");
     if (p->tile_x < 0 || p->tile_y < 0) return bad("tile sizes must be >= 0");
-    if ((p->tile_x + 5) * (p->tile_y + 5) > kMaxWinCells && p->tile_x && p->tile_y) {
+    const int tx = std::min(p->tile_x > 0 ? p->tile_x : 32, p->nx);
+    const int ty = std::min(p->tile_y > 0 ? p->tile_y : 16, p->ny);
+    if ((tx + 5) * (ty + 5) > kMaxWinCells) {
         snprintf(buf, sizeof buf, "(tile_x+5)*(tile_y+5) must not exceed %d", kMaxWinCells);
         return bad(buf);
     }
@@ -481,6 +485,177 @@ int finish_call(pic_sim* s) {
     return PIC_OK;
 }
 
+constexpr int kMaxBatch = 4096;
+
+int init_handle(const pic_params* prm, int n, pic_sim** out) {
+    pic_sim* s = nullptr;
+    if (!out) return fail(nullptr, PIC_EINVAL, "out is NULL");
+    *out = nullptr;
+    std::string why;
+    if (!prm) return fail(nullptr, PIC_EINVAL, "params is NULL");
+    for (int k = 0; k < n; k++) {
+        if (validate(prm + k, why) != PIC_OK) {
+            if (n > 1) why = "simulation " + std::to_string(k) + ": " + why;
+            return fail(nullptr, PIC_EINVAL, why);
+        }
+    }
+    s = new (std::nothrow) pic_sim();
+    if (!s) return fail(nullptr, PIC_ENOMEM, "host allocation failed");
+    s->prm = prm[0];
+    s->prms.assign(prm, prm + n);
+    if (cudaGetDevice(&s->device) != cudaSuccess) {
+        delete s;
+        return fail(nullptr, PIC_ECUDA, "no CUDA device");
+    }
+    auto bail = [&](int code) {
+        g_init_err = s->err;
+        pic_free(s);
+        return code;
+    };
+    // simulations side by side in every grid array; field kernels give each simulation a
+    // grid-stride range of at most 4 blocks per SM
+    int nsm = 152;
+    cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, s->device);
+    s->ngrids = n;
+    s->hgrids.resize(n);
+    s->ntot = 0;
+    s->nblk = 0;
+    s->hblk_grid.clear();
+    for (int g = 0; g < n; g++) {
+        GridDev& G = s->hgrids[g];
+        fill_grid(prm[g], G);
+        G.cell_off = s->ntot;
+        s->ntot += (long long)G.ncell;
+        G.blk_first = s->nblk;
+        G.nblk = (int)std::min<long long>((G.ncell + kFieldThreads - 1) / kFieldThreads,
+                                          4ll * std::max(nsm, 1));
+        s->nblk += G.nblk;
+        s->hblk_grid.insert(s->hblk_grid.end(), G.nblk, g);
+    }
+    const long long n3 = 3 * s->ntot;
+    cudaError_t e = cudaSuccess;
+    auto A = [&](cudaError_t r) {
+        if (e == cudaSuccess) e = r;
+    };
+    A(cudaStreamCreateWithFlags(&s->body_stream, cudaStreamNonBlocking));
+    A(cudaStreamCreateWithFlags(&s->body_stream2, cudaStreamNonBlocking));
+    A(cudaStreamCreateWithFlags(&s->own_stream, cudaStreamNonBlocking));
+    s->stream = s->own_stream;
+    A(dalloc(&s->F, 6 * s->ntot));
+    A(dalloc(&s->x, n3));
+    A(dalloc(&s->r, n3));
+    A(dalloc(&s->p, n3));
+    A(dalloc(&s->q, n3));
+    A(dalloc(&s->part, 4 * (size_t)s->nblk));
+    A(dalloc(&s->cg, s->ngrids));
+    A(dalloc(&s->done, s->ngrids));
+    A(dalloc(&s->st, 1));
+    A(dalloc(&s->tmp, s->ntot));
+    A(dalloc(&s->dgrids, s->ngrids));
+    A(dalloc(&s->dblk_grid, s->nblk));
+    A(dalloc(&s->dsegs, 2));
+    if (prm[0].precision == PIC_FP64) {
+        A(dalloc(&s->J64, n3));
+    } else {
+        A(dalloc(&s->Jfix, n3));
+        A(dalloc(&s->bvec, n3));
+        A(dalloc(&s->r32, n3));
+        A(dalloc(&s->p32, n3));
+        A(dalloc(&s->q32, n3));
+        A(dalloc(&s->e32, n3));
+        A(dalloc(&s->F32, 6 * s->ntot));
+    }
+    if (e != cudaSuccess) {
+        s->err = std::string("device allocation failed: ") + cudaGetErrorString(e);
+        cudaGetLastError();
+        return bail(PIC_ENOMEM);
+    }
+    A(cudaMemset(s->F, 0, 6 * s->ntot * sizeof(double)));
+    A(cudaMemset(s->x, 0, n3 * sizeof(double)));
+    A(cudaMemset(s->r, 0, n3 * sizeof(double)));
+    A(cudaMemset(s->p, 0, n3 * sizeof(double)));
+    A(cudaMemset(s->q, 0, n3 * sizeof(double)));
+    A(cudaMemset(s->cg, 0, s->ngrids * sizeof(CgState)));
+    A(cudaMemset(s->done, 0, s->ngrids * sizeof(unsigned int)));
+    A(cudaMemset(s->st, 0, sizeof(DevStatus)));
+    if (s->J64) A(cudaMemset(s->J64, 0, n3 * sizeof(double)));
+    if (s->Jfix) A(cudaMemset(s->Jfix, 0, n3 * sizeof(long long)));
+    if (s->F32) A(cudaMemset(s->F32, 0, 6 * s->ntot * sizeof(float)));
+    if (prm[0].precision == PIC_MIXED32) {
+        int rc = mixed_create(&s->mixed, prm, s->ngrids, s->hgrids.data(), s->dgrids, s->ntot, s->F32,
+                              s->Jfix, s->cg, s->st, s->err);
+        if (rc != PIC_OK) return bail(rc);
+    }
+    A(cudaMemcpy(s->dgrids, s->hgrids.data(), s->ngrids * sizeof(GridDev), cudaMemcpyHostToDevice));
+    A(cudaMemcpy(s->dblk_grid, s->hblk_grid.data(), s->nblk * sizeof(int), cudaMemcpyHostToDevice));
+    A(cudaDeviceSynchronize());
+    if (e != cudaSuccess) {
+        s->err = std::string("initialisation failed: ") + cudaGetErrorString(e);
+        cudaGetLastError();
+        return bail(PIC_ECUDA);
+    }
+    *out = s;
+    return PIC_OK;
+}
+
+// ---- tile autotuning ------------------------------------------------------------------
+// splitmix64 (Steele, Lea & Flood 2014) as a stateless hash: uniform double in [0, 1).
+__device__ __forceinline__ double hash01(unsigned long long k) {
+    k += 0x9E3779B97F4A7C15ull;
+    k = (k ^ (k >> 30)) * 0xBF58476D1CE4E5B9ull;
+    k = (k ^ (k >> 27)) * 0x94D049BB133111EBull;
+    k ^= k >> 31;
+    return (double)(k >> 11) * (1.0 / 9007199254740992.0);
+}
+
+// A timing workload shaped like a drifting pair plasma: ppc particles per cell at hashed
+// offsets, u_x near sqrt(gamma0^2 - 1), transverse momenta of order 1e-3. Output
+// [x(n), y(n), ux(n), uy(n), uz(n)] in physical units.
+__global__ void k_synth(long long n, int nx, int ppc, double dx, double dy, double u0,
+                        unsigned long long seed, double* out) {
+    const long long k = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (k >= n) return;
+    const long long cell = k / ppc;
+    const int i = (int)(cell % nx), j = (int)(cell / nx);
+    const unsigned long long b = seed * 0x100000001B3ull + 8ull * (unsigned long long)k;
+    out[k] = (i + hash01(b)) * dx;
+    out[n + k] = (j + hash01(b + 1)) * dy;
+    out[2 * n + k] = u0 + 2e-3 * (hash01(b + 2) - 0.5) * u0;
+    out[3 * n + k] = 2e-3 * (hash01(b + 3) - 0.5);
+    out[4 * n + k] = 2e-3 * (hash01(b + 4) - 0.5);
+}
+
+// Milliseconds per step of the tile kernels of a batch built from `sub` with synthetic
+// particles (warm-up steps first); a negative value if the batch cannot be run.
+double time_tiles(const std::vector<pic_params>& sub, int steps) {
+    pic_sim* h = nullptr;
+    if (init_handle(sub.data(), (int)sub.size(), &h) != PIC_OK) return -1.0;
+    double ms = -1.0;
+    long long nmax = 0;
+    for (const pic_params& q : sub) nmax = std::max(nmax, (long long)q.ppc * q.nx * q.ny);
+    double* d = nullptr;
+    bool ok = dalloc(&d, 5 * (size_t)nmax) == cudaSuccess;
+    for (int k = 0; ok && k < (int)sub.size(); k++) {
+        const pic_params& q = sub[k];
+        const long long n = (long long)q.ppc * q.nx * q.ny;
+        ok = pic_select(h, k) == PIC_OK;
+        for (int sp = 0; ok && sp < 2; sp++) {
+            k_synth<<<(unsigned)((n + 255) / 256), 256, 0, h->stream>>>(
+                n, q.nx, q.ppc, q.dx, q.dy, std::sqrt(q.gamma0 * q.gamma0 - 1.0), 1000ull * k + sp, d);
+            ok = pic_load_particles(h, sp, d, d + n, d + 2 * n, d + 3 * n, d + 4 * n, n) == PIC_OK;
+        }
+    }
+    if (d) cudaFree(d);
+    double out[3] = {0, 0, 0};
+    if (ok) ok = pic_step(h, 2) == PIC_OK;
+    if (ok) ok = pic_profile(h, steps, out, 3) == PIC_OK;
+    if (ok) ms = out[2];
+    else g_init_err = h->err;
+    pic_free(h);
+    cudaGetLastError();
+    return ms;
+}
+
 }  // namespace
 
 // =====================================================================================
@@ -509,100 +684,84 @@ void pic_params_default(pic_params* p) {
     p->bin_slack = 0.0;
 }
 
-int pic_init(const pic_params* prm, pic_sim** out) {
-    pic_sim* s = nullptr;
+int pic_init(const pic_params* prm, pic_sim** out) { return init_handle(prm, 1, out); }
+
+int pic_init_batch(const pic_params* prm, int32_t n, pic_sim** out) {
     if (!out) return fail(nullptr, PIC_EINVAL, "out is NULL");
     *out = nullptr;
+    if (n < 1 || n > kMaxBatch) return fail(nullptr, PIC_EINVAL, "n must lie in [1, 4096]");
+    if (!prm) return fail(nullptr, PIC_EINVAL, "params is NULL");
+    if (n > 1) {
+        for (int k = 0; k < n; k++)
+            if (prm[k].precision != PIC_MIXED32)
+                return fail(nullptr, PIC_EINVAL, "a batch of more than one simulation requires PIC_MIXED32");
+        for (int k = 1; k < n; k++)
+            if ((prm[k].flags & PIC_NO_GRAPH) != (prm[0].flags & PIC_NO_GRAPH))
+                return fail(nullptr, PIC_EINVAL, "PIC_NO_GRAPH must be the same for every simulation");
+    }
+    return init_handle(prm, n, out);
+}
+
+int pic_batch_size(const pic_sim* s) { return s ? s->ngrids : 0; }
+
+int pic_select(pic_sim* s, int32_t k) {
+    if (!s) return PIC_EINVAL;
+    if (k < 0 || k >= s->ngrids) return fail(s, PIC_EINVAL, "simulation index out of range");
+    s->sel = k;
+    return PIC_OK;
+}
+
+int pic_autotune_tiles(pic_params* prm, int32_t n, int32_t steps, double* best_ms) {
+    if (!prm || n < 1 || n > kMaxBatch) return fail(nullptr, PIC_EINVAL, "need 1 <= n <= 4096 parameter sets");
+    if (steps < 1 || steps > 1000) return fail(nullptr, PIC_EINVAL, "steps must lie in [1, 1000]");
     std::string why;
-    if (validate(prm, why) != PIC_OK) return fail(nullptr, PIC_EINVAL, why);
-    s = new (std::nothrow) pic_sim();
-    if (!s) return fail(nullptr, PIC_ENOMEM, "host allocation failed");
-    s->prm = *prm;
-    if (cudaGetDevice(&s->device) != cudaSuccess) {
-        delete s;
-        return fail(nullptr, PIC_ECUDA, "no CUDA device");
+    for (int k = 0; k < n; k++) {
+        pic_params q = prm[k];
+        q.precision = PIC_MIXED32;
+        if (validate(&q, why) != PIC_OK) return fail(nullptr, PIC_EINVAL, "simulation " + std::to_string(k) + ": " + why);
     }
-    auto bail = [&](int code) {
-        g_init_err = s->err;
-        pic_free(s);
-        return code;
-    };
-    s->ngrids = 1;
-    s->hgrids.resize(1);
-    fill_grid(*prm, s->hgrids[0]);
-    s->ntot = (long long)prm->nx * prm->ny;
-    s->hgrids[0].cell_off = 0;
-    s->hgrids[0].blk_first = 0;
-    // field kernels: grid-stride loops over at most 4 blocks per SM
-    int nsm = 152;
-    cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, s->device);
-    s->hgrids[0].nblk = (int)std::min<long long>((s->ntot + kFieldThreads - 1) / kFieldThreads,
-                                                 4ll * std::max(nsm, 1));
-    s->nblk = s->hgrids[0].nblk;
-    s->hblk_grid.assign(s->nblk, 0);
-    const long long n3 = 3 * s->ntot;
-    cudaError_t e = cudaSuccess;
-    auto A = [&](cudaError_t r) {
-        if (e == cudaSuccess) e = r;
-    };
-    A(cudaStreamCreateWithFlags(&s->body_stream, cudaStreamNonBlocking));
-    A(cudaStreamCreateWithFlags(&s->body_stream2, cudaStreamNonBlocking));
-    A(cudaStreamCreateWithFlags(&s->own_stream, cudaStreamNonBlocking));
-    s->stream = s->own_stream;
-    A(dalloc(&s->F, 6 * s->ntot));
-    A(dalloc(&s->x, n3));
-    A(dalloc(&s->r, n3));
-    A(dalloc(&s->p, n3));
-    A(dalloc(&s->q, n3));
-    A(dalloc(&s->part, 4 * (size_t)s->nblk));
-    A(dalloc(&s->cg, s->ngrids));
-    A(dalloc(&s->done, s->ngrids));
-    A(dalloc(&s->st, 1));
-    A(dalloc(&s->tmp, s->ntot));
-    A(dalloc(&s->dgrids, s->ngrids));
-    A(dalloc(&s->dblk_grid, s->nblk));
-    A(dalloc(&s->dsegs, 2));
-    if (prm->precision == PIC_FP64) {
-        A(dalloc(&s->J64, n3));
-    } else {
-        A(dalloc(&s->Jfix, n3));
-        A(dalloc(&s->bvec, n3));
-        A(dalloc(&s->r32, n3));
-        A(dalloc(&s->p32, n3));
-        A(dalloc(&s->q32, n3));
-        A(dalloc(&s->e32, n3));
-        A(dalloc(&s->F32, 6 * s->ntot));
+    static const int cand[][2] = {{32, 16}, {16, 16}, {32, 8}, {64, 8}, {64, 16}, {16, 8}, {32, 32}};
+    for (int P = 1; P <= 3; P++) {
+        std::vector<int> idx;
+        for (int k = 0; k < n; k++)
+            if (prm[k].shape_order == P) idx.push_back(k);
+        if (best_ms) best_ms[P - 1] = 0.0;
+        if (idx.empty()) continue;
+        double best = -1.0;
+        int bx = 0, by = 0;
+        std::vector<std::vector<int>> seen;
+        for (const auto& c : cand) {
+            std::vector<pic_params> sub;
+            std::vector<int> eff;
+            bool fits = true;
+            for (int k : idx) {
+                pic_params q = prm[k];
+                q.precision = PIC_MIXED32;
+                q.flags &= ~PIC_NO_GRAPH;
+                q.tile_x = c[0];
+                q.tile_y = c[1];
+                const int tx = std::min(c[0], q.nx), ty = std::min(c[1], q.ny);
+                if ((tx + 5) * (ty + 5) > kMaxWinCells) fits = false;
+                eff.push_back(tx);
+                eff.push_back(ty);
+                sub.push_back(q);
+            }
+            if (!fits || std::find(seen.begin(), seen.end(), eff) != seen.end()) continue;
+            seen.push_back(eff);
+            const double ms = time_tiles(sub, steps);
+            if (ms > 0 && (best < 0 || ms < best)) {
+                best = ms;
+                bx = c[0];
+                by = c[1];
+            }
+        }
+        if (best < 0) return fail(nullptr, PIC_ECUDA, "no tile shape could be timed (" + g_init_err + ")");
+        for (int k : idx) {
+            prm[k].tile_x = bx;
+            prm[k].tile_y = by;
+        }
+        if (best_ms) best_ms[P - 1] = best;
     }
-    if (e != cudaSuccess) {
-        s->err = std::string("device allocation failed: ") + cudaGetErrorString(e);
-        cudaGetLastError();
-        return bail(PIC_ENOMEM);
-    }
-    A(cudaMemset(s->F, 0, 6 * s->ntot * sizeof(double)));
-    A(cudaMemset(s->x, 0, n3 * sizeof(double)));
-    A(cudaMemset(s->r, 0, n3 * sizeof(double)));
-    A(cudaMemset(s->p, 0, n3 * sizeof(double)));
-    A(cudaMemset(s->q, 0, n3 * sizeof(double)));
-    A(cudaMemset(s->cg, 0, s->ngrids * sizeof(CgState)));
-    A(cudaMemset(s->done, 0, s->ngrids * sizeof(unsigned int)));
-    A(cudaMemset(s->st, 0, sizeof(DevStatus)));
-    if (s->J64) A(cudaMemset(s->J64, 0, n3 * sizeof(double)));
-    if (s->Jfix) A(cudaMemset(s->Jfix, 0, n3 * sizeof(long long)));
-    if (s->F32) A(cudaMemset(s->F32, 0, 6 * s->ntot * sizeof(float)));
-    if (prm->precision == PIC_MIXED32) {
-        int rc = mixed_create(&s->mixed, *prm, s->hgrids[0], s->dgrids, s->ntot, s->F32, s->Jfix,
-                              s->cg, s->st, s->err);
-        if (rc != PIC_OK) return bail(rc);
-    }
-    A(cudaMemcpy(s->dgrids, s->hgrids.data(), s->ngrids * sizeof(GridDev), cudaMemcpyHostToDevice));
-    A(cudaMemcpy(s->dblk_grid, s->hblk_grid.data(), s->nblk * sizeof(int), cudaMemcpyHostToDevice));
-    A(cudaDeviceSynchronize());
-    if (e != cudaSuccess) {
-        s->err = std::string("initialisation failed: ") + cudaGetErrorString(e);
-        cudaGetLastError();
-        return bail(PIC_ECUDA);
-    }
-    *out = s;
     return PIC_OK;
 }
 
@@ -625,7 +784,7 @@ int pic_load_particles(pic_sim* s, int32_t sp, const double* x, const double* y,
     if (n > (int64_t)1 << 40) return fail(s, PIC_EINVAL, "n too large");
     drop_graph(s);
     if (s->prm.precision == PIC_MIXED32) {
-        int rc = mixed_load(s->mixed, sp, x, y, ux, uy, uz, n, s->stream, s->err);
+        int rc = mixed_load(s->mixed, s->sel, sp, x, y, ux, uy, uz, n, s->stream, s->err);
         if (rc == PIC_OK) rc = finish_call(s);
         return rc;
     }
@@ -686,9 +845,10 @@ int pic_set_fields(pic_sim* s, int32_t which, const double* data, size_t len) {
     if (!s) return PIC_EINVAL;
     cudaSetDevice(s->device);
     if (which < PIC_EX || which > PIC_BZ) return fail(s, PIC_EINVAL, "which must be PIC_EX..PIC_BZ");
-    if (!data || len < (size_t)s->ntot) return fail(s, PIC_EINVAL, "data must hold nx*ny values");
-    CK(cudaMemcpyAsync(s->F + which * s->ntot, data, s->ntot * sizeof(double), cudaMemcpyDefault,
-                       s->stream));
+    const GridDev& G = s->hgrids[s->sel];
+    if (!data || len < (size_t)G.ncell) return fail(s, PIC_EINVAL, "data must hold nx*ny values");
+    CK(cudaMemcpyAsync(s->F + which * s->ntot + G.cell_off, data, G.ncell * sizeof(double),
+                       cudaMemcpyDefault, s->stream));
     launch_fields_to_f32(field_args(s, 0, 0), s->stream);
     return finish_call(s);
 }
@@ -747,7 +907,7 @@ int pic_profile(pic_sim* s, int32_t n, double* out, int32_t n_out) {
     double acc[5] = {0, 0, 0, 0, 0};
     CgState c0{}, c1{};
     DevStatus hs{};
-    CK(cudaMemcpyAsync(&c0, s->cg, sizeof c0, cudaMemcpyDeviceToHost, s->stream));
+    CK(cudaMemcpyAsync(&c0, s->cg + s->sel, sizeof c0, cudaMemcpyDeviceToHost, s->stream));
     CK(cudaMemcpyAsync(&hs, s->st, sizeof hs, cudaMemcpyDeviceToHost, s->stream));
     CK(cudaStreamSynchronize(s->stream));
     const unsigned long long steps0 = hs.steps_done;
@@ -768,7 +928,7 @@ int pic_profile(pic_sim* s, int32_t n, double* out, int32_t n_out) {
         CK(cudaEventElapsedTime(&t[3], s->ev[3], s->ev[4]));  // field solve
         for (int a = 0; a < 4; a++) acc[a] += t[a];
     }
-    CK(cudaMemcpyAsync(&c1, s->cg, sizeof c1, cudaMemcpyDeviceToHost, s->stream));
+    CK(cudaMemcpyAsync(&c1, s->cg + s->sel, sizeof c1, cudaMemcpyDeviceToHost, s->stream));
     CK(cudaMemcpyAsync(&hs, s->st, sizeof hs, cudaMemcpyDeviceToHost, s->stream));
     CK(cudaStreamSynchronize(s->stream));
     s->steps += (long long)(hs.steps_done - steps0);
@@ -783,23 +943,25 @@ int pic_fields(pic_sim* s, int32_t which, double* out, size_t len) {
     if (!s) return PIC_EINVAL;
     cudaSetDevice(s->device);
     if (which < PIC_EX || which > PIC_DBZ) return fail(s, PIC_EINVAL, "which must be PIC_EX..PIC_DBZ");
-    if (!out || len < (size_t)s->ntot) return fail(s, PIC_EINVAL, "out must hold nx*ny values");
+    const GridDev& G = s->hgrids[s->sel];
+    const long long nc = G.ncell, off = G.cell_off;
+    if (!out || len < (size_t)nc) return fail(s, PIC_EINVAL, "out must hold nx*ny values");
     const double* src = nullptr;
     if (which <= PIC_BZ) {
-        src = s->F + which * s->ntot;
+        src = s->F + which * s->ntot + off;
     } else if (which <= PIC_JZ) {
         const int c = which - PIC_JX;
         if (s->J64) {
-            src = s->J64 + c * s->ntot;
+            src = s->J64 + c * s->ntot + off;
         } else {
-            k_fix_to_f64<<<(unsigned)((s->ntot + 255) / 256), 256, 0, s->stream>>>(
-                s->ntot, s->Jfix + c * s->ntot, s->hgrids[0].jinv, s->tmp);
+            k_fix_to_f64<<<(unsigned)((nc + 255) / 256), 256, 0, s->stream>>>(
+                nc, s->Jfix + c * s->ntot + off, G.jinv, s->tmp);
             src = s->tmp;
         }
     } else {
-        src = s->x + (which - PIC_DBX) * s->ntot;
+        src = s->x + (which - PIC_DBX) * s->ntot + off;
     }
-    CK(cudaMemcpyAsync(out, src, s->ntot * sizeof(double), cudaMemcpyDefault, s->stream));
+    CK(cudaMemcpyAsync(out, src, nc * sizeof(double), cudaMemcpyDefault, s->stream));
     return finish_call(s);
 }
 
@@ -809,11 +971,11 @@ int pic_moments(pic_sim* s, pic_moments_t* m) {
     if (!m) return fail(s, PIC_EINVAL, "out is NULL");
     CgState c{};
     DevStatus hs{};
-    CK(cudaMemcpyAsync(&c, s->cg, sizeof c, cudaMemcpyDeviceToHost, s->stream));
+    CK(cudaMemcpyAsync(&c, s->cg + s->sel, sizeof c, cudaMemcpyDeviceToHost, s->stream));
     CK(cudaMemcpyAsync(&hs, s->st, sizeof hs, cudaMemcpyDeviceToHost, s->stream));
     if (int rc = finish_call(s)) return rc;
     memset(m, 0, sizeof *m);
-    const GridDev& G = s->hgrids[0];
+    const GridDev& G = s->hgrids[s->sel];
     m->step = s->steps;
     m->time = s->steps * G.dt;
     m->U_E = c.ue;
@@ -831,13 +993,13 @@ int pic_moments(pic_sim* s, pic_moments_t* m) {
     if (s->mixed) m->rebins = mixed_rebins(s->mixed);
     // the largest-iteration counter restarts at every pic_moments call
     const int zero = 0;
-    CK(cudaMemcpyAsync(&s->cg->max_iters, &zero, sizeof zero, cudaMemcpyHostToDevice, s->stream));
+    CK(cudaMemcpyAsync(&s->cg[s->sel].max_iters, &zero, sizeof zero, cudaMemcpyHostToDevice, s->stream));
     return finish_call(s);
 }
 
 int64_t pic_particle_count(pic_sim* s, int32_t sp) {
     if (!s || sp < 0 || sp > 1) return -1;
-    if (s->mixed) return mixed_count(s->mixed, sp);
+    if (s->mixed) return mixed_count(s->mixed, s->sel, sp);
     return s->np[sp];
 }
 
@@ -849,7 +1011,7 @@ int pic_particles(pic_sim* s, int32_t sp, double* out, int64_t n) {
     if (n == 0) return PIC_OK;
     if (!out) return fail(s, PIC_EINVAL, "out is NULL");
     if (s->mixed) {
-        int rc = mixed_particles(s->mixed, sp, out, n, s->stream, s->err);
+        int rc = mixed_particles(s->mixed, s->sel, sp, out, n, s->stream, s->err);
         if (rc == PIC_OK) rc = finish_call(s);
         return rc;
     }

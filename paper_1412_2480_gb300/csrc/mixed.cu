@@ -6,12 +6,18 @@
 // (capacity capo each), one per neighbouring tile. Bins are double-buffered: a step reads
 // buffer `parity` and writes buffer `parity ^ 1`.
 //
+// A handle may hold many simulations of different sizes and shape orders (the batched
+// parameter scan). Their tiles form one global list; each simulation's bins and count
+// slots sit at its own offsets.
+//
 // Per step (inside the captured step graph):
 //   0. k_mixed_begin / k_push_overflow: particles parked in the overflow list (no room
 //      in a bin; normally none) are pushed straight from global memory;
-//   1. k_push_tile: one CTA per tile stages the FP32 field window (tile + 2 cells below,
-//      3 above, in x and y) into shared memory and zeroes a 64-bit fixed-point current
-//      window of the same size. Its particles are its own stayer segment plus the eight
+//   1. k_push_tile<P>, one persistent launch per shape order P present: each CTA takes
+//      the next tile of that order from a device work counter (tiles listed largest
+//      first, so uneven simulations balance across the SMs), stages the FP32 field window
+//      (tile + 2 cells below, 3 above, in x and y) into shared memory and zeroes a
+//      fixed-point current window of the same size. Its particles are its own stayer segment plus the eight
 //      neighbours' outboxes addressed to it. Warps run independently (no block barrier in
 //      the particle loop): each gathers E^n, B^n, pushes (Boris), moves and deposits
 //      J^{n+1/2} (Esirkepov) with native integer shared-memory atomics, then writes each
@@ -59,7 +65,10 @@ __host__ __device__ __forceinline__ size_t aos(long long k, int f) {
 
 struct MixedArgs {
     const GridDev* grids;
-    int g;
+    const int* tile_grid;  // simulation of each global tile
+    const int* tlist;      // tiles of this launch's shape order, largest first
+    int ntl;               // entries of tlist
+    int* work;             // next entry of tlist to take (zeroed every step)
     long long ntot;
     const float* F32;
     long long* Jfix;
@@ -72,8 +81,8 @@ struct MixedArgs {
 };
 
 struct MixedState {
-    pic_params prm{};
-    GridDev* G = nullptr;  // host copy owned by the caller (grid 0)
+    int ngrids = 0;
+    GridDev* G = nullptr;  // host descriptors [ngrids], owned by the caller
     const GridDev* dgrids = nullptr;
     long long ntot = 0;
     float* F32 = nullptr;
@@ -82,12 +91,18 @@ struct MixedState {
     DevStatus* st = nullptr;
     unsigned* buf[2] = {nullptr, nullptr};
     Slots ovf[2]{};
-    int* cnt[2] = {nullptr, nullptr};
+    int* cnt[2] = {nullptr, nullptr};  // [ntiles_total * 2 * kSegs] per parity
     long long nslots = 0, ovf_cap = 0;
-    long long n[2] = {0, 0};
+    int ntiles_total = 0;
+    int* tile_grid = nullptr;     // device [ntiles_total]
+    int* tlist = nullptr;         // device: tiles grouped by shape order, largest first
+    int* work = nullptr;          // device [4]: work counter of each order's launch
+    int order_first[4] = {0, 0, 0, 0}, order_n[4] = {0, 0, 0, 0};
+    size_t smem[4] = {0, 0, 0, 0};  // dynamic shared memory of each order's launch
+    int pblocks[4] = {0, 0, 0, 0};  // persistent CTAs of each order's launch
+    std::vector<long long> n;     // live particles [2 g + species]
     long long rebins = 0;
     long long gen = 0;  // allocation generation of the bin buffers
-    size_t smem = 0;
 };
 
 namespace {
@@ -260,16 +275,17 @@ __device__ __forceinline__ void get(const unsigned* P, long long k, int& c, floa
     u[2] = __ldcs(F + aos(k, 5));
 }
 
-// Append to the overflow list of the next buffer; a full list is a fatal error.
+// Append to the overflow list of the next buffer; a full list is a fatal error. An
+// entry records its simulation and species as gs = species | (simulation << 1).
 __device__ __forceinline__ void to_overflow(unsigned* op, int* ogs, long long ovf_cap, DevStatus* st,
                                          int nxt, int c, float ox, float oy, float u0, float u1,
-                                         float u2, int s) {
+                                         float u2, int gs) {
     const unsigned long long o = atomicAdd(&st->ovf_count[nxt], 1ull);
     atomicAdd(&st->overflow, 1ull);
     if ((long long)o < ovf_cap) {
         const float u[3] = {u0, u1, u2};
         put(op, (long long)o, c, ox, oy, u);
-        ogs[o] = s;
+        ogs[o] = gs;
     } else {
         atomicAdd(&st->lost, 1ull);  // storage exhausted: the step fails with PIC_ENOMEM
         st->stop_next = 1u;
@@ -292,185 +308,209 @@ k_push_tile(const MixedArgs a) {
     __shared__ long long s_base[2][kSegs];     // physical first slot of each segment
     __shared__ int s_out[2][kSegs];            // next-buffer counts (stayers, outboxes)
     __shared__ double s_red[32];
+    __shared__ int s_item;
     DevStatus* st = a.st;
     if (st->stop) return;
     const int par = (int)st->parity, nxp = par ^ 1;
-    const GridDev& G = a.grids[a.g];
-    const int t = blockIdx.x;
-    const int tyi = t / G.ntx, txi = t - tyi * G.ntx;
-    const int X0 = txi * G.tx, Y0 = tyi * G.ty;
-    const int X1 = min(X0 + G.tx, G.nx), Y1 = min(Y0 + G.ty, G.ny);
-    const int nx = G.nx, ny = G.ny;
-    const int WX = G.wx, NW = G.wx * G.wy;
-    const long long cap = G.cap, capo = G.capo, stride = bin_stride(G);
-    int* jw = reinterpret_cast<int*>(smem_raw);  // [0, 3 NW) hi words, [3 NW, 6 NW) lo words
-    float* fw = reinterpret_cast<float*>(smem_raw + (size_t)6 * NW * sizeof(int));
-    if (threadIdx.x < 2 * kSegs) {
-        const int s = threadIdx.x / kSegs, k = threadIdx.x - (threadIdx.x / kSegs) * kSegs;
-        int src = t;
-        long long off = 0, lim = cap;
-        if (k > 0) {
-            int dx, dy;
-            dir_of(k - 1, dx, dy);
-            const int sx = (txi - dx + G.ntx) % G.ntx, sy = (tyi - dy + G.nty) % G.nty;
-            src = sy * G.ntx + sx;
-            off = cap + (long long)(k - 1) * capo;
-            lim = capo;
-        }
-        const long long b = (long long)src * 2 + s;
-        const int* ccur = par ? a.cnt[1] : a.cnt[0];
-        const int cnt = (int)min((long long)ccur[b * kSegs + k], lim);
-        s_start[s][k + 1] = cnt;  // prefix-summed below
-        s_base[s][k] = G.bin_off + b * stride + off;
-        s_out[s][k] = 0;
-    }
-    const float* Fg = a.F32 + G.cell_off;
-    for (int idx = threadIdx.x; idx < 6 * NW; idx += blockDim.x) {
-        const int c = idx / NW;
-        const int w = idx - c * NW;
-        const int wy = w / WX;
-        const int wx = w - wy * WX;
-        const int gx = ((X0 - 2 + wx) % nx + nx) % nx;
-        const int gy = ((Y0 - 2 + wy) % ny + ny) % ny;
-        fw[idx] = Fg[c * a.ntot + (long long)gy * nx + gx];
-    }
-    for (int idx = threadIdx.x; idx < 6 * NW; idx += blockDim.x) jw[idx] = 0;
-    __syncthreads();
-    if (threadIdx.x < 2) {
-        const int s = threadIdx.x;
-        s_start[s][0] = 0;
-        for (int k = 1; k <= kSegs; k++) s_start[s][k] += s_start[s][k - 1];
-    }
-    __syncthreads();
-    const float js = (float)G.jscale;
-    const int n_tile = s_start[0][kSegs] + s_start[1][kSegs];
-    const int room = 30 - (32 - __clz(n_tile));  // n_tile < 2^(30 - room)
-    const int kwin = min(22, room), lbits = min(16, room);
-    const WinMem W{fw, jw, jw + 3 * NW, WX, NW, (float)(G.jscale * exp2((double)(kwin - 40))),
-                   (float)(1 << lbits)};
-    const GlobalMem M{a.F32 + G.cell_off, reinterpret_cast<unsigned long long*>(a.Jfix + G.cell_off),
-                      a.ntot, nx, ny, js};
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nwarp = blockDim.x >> 5;
-    const unsigned* cur = par ? a.buf[1] : a.buf[0];
-    unsigned* nxt = par ? a.buf[0] : a.buf[1];
-    float ek = 0.f;
-    for (int s = 0; s < 2; s++) {
-        const PushConst K = push_const(G, s);
-        const int total = s_start[s][kSegs];
-        const long long own = G.bin_off + ((long long)t * 2 + s) * stride;
-        for (int c0 = warp * 32; c0 < total; c0 += nwarp * 32) {
-            const int v = c0 + lane;
-            const bool valid = v < total;
-            int dest = -1, cnew = 0;
-            float ox = 0.f, oy = 0.f, u[3] = {0.f, 0.f, 0.f};
-            if (valid) {
-                int seg = 0;
+    for (;;) {
+        // every thread reads s_item between these two barriers; thread 0 writes it again
+        // only after the barriers inside the tile body
+        if (threadIdx.x == 0) s_item = atomicAdd(a.work, 1);
+        __syncthreads();
+        const int item = s_item;
+        if (item >= a.ntl) break;
+        const int t = __ldg(a.tlist + item);  // global tile
+        const int g = __ldg(a.tile_grid + t);
+        const GridDev& G = a.grids[g];
+        const int lt = t - G.tile_first;      // tile within its simulation
+        const int tyi = lt / G.ntx, txi = lt - tyi * G.ntx;
+        const int X0 = txi * G.tx, Y0 = tyi * G.ty;
+        const int X1 = min(X0 + G.tx, G.nx), Y1 = min(Y0 + G.ty, G.ny);
+        const int nx = G.nx, ny = G.ny;
+        const int WX = G.wx, NW = G.wx * G.wy;
+        const long long cap = G.cap, capo = G.capo, stride = bin_stride(G);
+        int* jw = reinterpret_cast<int*>(smem_raw);  // [0, 3 NW) hi words, [3 NW, 6 NW) lo words
+        float* fw = reinterpret_cast<float*>(smem_raw + (size_t)6 * NW * sizeof(int));
+        if (threadIdx.x < 2 * kSegs) {
+            const int s = threadIdx.x / kSegs, k = threadIdx.x - (threadIdx.x / kSegs) * kSegs;
+            int src = lt;
+            long long off = 0, lim = cap;
+            if (k > 0) {
+                int dx, dy;
+                dir_of(k - 1, dx, dy);
+                const int sx = (txi - dx + G.ntx) % G.ntx, sy = (tyi - dy + G.nty) % G.nty;
+                src = sy * G.ntx + sx;
+                off = cap + (long long)(k - 1) * capo;
+                lim = capo;
+            }
+            const long long b = (long long)src * 2 + s;
+            const int* ccur = par ? a.cnt[1] : a.cnt[0];
+            const int cnt = (int)min((long long)ccur[((long long)G.tile_first * 2 + b) * kSegs + k], lim);
+            s_start[s][k + 1] = cnt;  // prefix-summed below
+            s_base[s][k] = G.bin_off + b * stride + off;
+            s_out[s][k] = 0;
+        }
+        const float* Fg = a.F32 + G.cell_off;
+        for (int idx = threadIdx.x; idx < 6 * NW; idx += blockDim.x) {
+            const int c = idx / NW;
+            const int w = idx - c * NW;
+            const int wy = w / WX;
+            const int wx = w - wy * WX;
+            const int gx = ((X0 - 2 + wx) % nx + nx) % nx;
+            const int gy = ((Y0 - 2 + wy) % ny + ny) % ny;
+            fw[idx] = Fg[c * a.ntot + (long long)gy * nx + gx];
+        }
+        for (int idx = threadIdx.x; idx < 6 * NW; idx += blockDim.x) jw[idx] = 0;
+        __syncthreads();
+        if (threadIdx.x < 2) {
+            const int s = threadIdx.x;
+            s_start[s][0] = 0;
+            for (int k = 1; k <= kSegs; k++) s_start[s][k] += s_start[s][k - 1];
+        }
+        __syncthreads();
+        const float js = (float)G.jscale;
+        const int n_tile = s_start[0][kSegs] + s_start[1][kSegs];
+        const int room = 30 - (32 - __clz(n_tile));  // n_tile < 2^(30 - room)
+        const int kwin = min(22, room), lbits = min(16, room);
+        const WinMem W{fw, jw, jw + 3 * NW, WX, NW, (float)(G.jscale * exp2((double)(kwin - 40))),
+                       (float)(1 << lbits)};
+        const GlobalMem M{a.F32 + G.cell_off, reinterpret_cast<unsigned long long*>(a.Jfix + G.cell_off),
+                          a.ntot, nx, ny, js};
+        const unsigned* cur = par ? a.buf[1] : a.buf[0];
+        unsigned* nxt = par ? a.buf[0] : a.buf[1];
+        float ek = 0.f;
+        for (int s = 0; s < 2; s++) {
+            const PushConst K = push_const(G, s);
+            const int total = s_start[s][kSegs];
+            const long long own = G.bin_off + ((long long)lt * 2 + s) * stride;
+            for (int c0 = warp * 32; c0 < total; c0 += nwarp * 32) {
+                const int v = c0 + lane;
+                const bool valid = v < total;
+                int dest = -1, cnew = 0;
+                float ox = 0.f, oy = 0.f, u[3] = {0.f, 0.f, 0.f};
+                if (valid) {
+                    int seg = 0;
 #pragma unroll
-                for (int k = 1; k < kSegs; k++) seg += (v >= s_start[s][k]) ? 1 : 0;
-                const long long e = s_base[s][seg] + (v - s_start[s][seg]);
-                int c;
-                get(cur, e, c, ox, oy, u);
-                const int ci = c & 0xffff, cj = c >> 16;
-                int di, dj;
-                bool ok;
-                if (ci >= X0 && ci < X1 && cj >= Y0 && cj < Y1)
-                    ok = push_one<P>(W, K, ci - X0 + 2, cj - Y0 + 2, ox, oy, u, di, dj, ek);
-                else
-                    ok = push_one<P>(M, K, ci, cj, ox, oy, u, di, dj, ek);
-                if (!ok) flag_bad(st, u);
-                const int ni = wrapi(ci + di, nx), nj = wrapi(cj + dj, ny);
-                cnew = ni | (nj << 16);
-                if (ni >= X0 && ni < X1 && nj >= Y0 && nj < Y1) {
-                    dest = 0;
-                } else {
-                    int dtx = ni / G.tx - txi, dty = nj / G.ty - tyi;
-                    if (dtx > 1) dtx -= G.ntx;
-                    if (dtx < -1) dtx += G.ntx;
-                    if (dty > 1) dty -= G.nty;
-                    if (dty < -1) dty += G.nty;
-                    dest = (abs(dtx) <= 1 && abs(dty) <= 1 && (dtx | dty)) ? 1 + outbox_of(dtx, dty) : -1;
+                    for (int k = 1; k < kSegs; k++) seg += (v >= s_start[s][k]) ? 1 : 0;
+                    const long long e = s_base[s][seg] + (v - s_start[s][seg]);
+                    int c;
+                    get(cur, e, c, ox, oy, u);
+                    const int ci = c & 0xffff, cj = c >> 16;
+                    int di, dj;
+                    bool ok;
+                    if (ci >= X0 && ci < X1 && cj >= Y0 && cj < Y1)
+                        ok = push_one<P>(W, K, ci - X0 + 2, cj - Y0 + 2, ox, oy, u, di, dj, ek);
+                    else
+                        ok = push_one<P>(M, K, ci, cj, ox, oy, u, di, dj, ek);
+                    if (!ok) flag_bad(st, u);
+                    const int ni = wrapi(ci + di, nx), nj = wrapi(cj + dj, ny);
+                    cnew = ni | (nj << 16);
+                    if (ni >= X0 && ni < X1 && nj >= Y0 && nj < Y1) {
+                        dest = 0;
+                    } else {
+                        int dtx = ni / G.tx - txi, dty = nj / G.ty - tyi;
+                        if (dtx > 1) dtx -= G.ntx;
+                        if (dtx < -1) dtx += G.ntx;
+                        if (dty > 1) dty -= G.nty;
+                        if (dty < -1) dty += G.nty;
+                        dest = (abs(dtx) <= 1 && abs(dty) <= 1 && (dtx | dty)) ? 1 + outbox_of(dtx, dty) : -1;
+                    }
+                }
+                const unsigned act = __ballot_sync(0xffffffffu, valid);
+                if (valid) {
+                    const unsigned grp = __match_any_sync(act, dest);
+                    const int leader = __ffs(grp) - 1;
+                    const int rank = __popc(grp & ((1u << lane) - 1u));
+                    int b0 = 0;
+                    if (lane == leader && dest >= 0) b0 = atomicAdd(&s_out[s][dest], __popc(grp));
+                    b0 = __shfl_sync(grp, b0, leader) + rank;
+                    long long slot = -1;
+                    if (dest == 0 && b0 < cap) slot = own + b0;
+                    else if (dest > 0 && b0 < capo) slot = own + cap + (long long)(dest - 1) * capo + b0;
+                    if (slot >= 0) put(nxt, slot, cnew, ox, oy, u);
+                    else
+                        to_overflow(nxp ? a.ovf[1].p : a.ovf[0].p, nxp ? a.ovf[1].gs : a.ovf[0].gs,
+                                    a.ovf_cap, st, nxp, cnew, ox, oy, u[0], u[1], u[2], s | (g << 1));
                 }
             }
-            const unsigned act = __ballot_sync(0xffffffffu, valid);
-            if (valid) {
-                const unsigned grp = __match_any_sync(act, dest);
-                const int leader = __ffs(grp) - 1;
-                const int rank = __popc(grp & ((1u << lane) - 1u));
-                int b0 = 0;
-                if (lane == leader && dest >= 0) b0 = atomicAdd(&s_out[s][dest], __popc(grp));
-                b0 = __shfl_sync(grp, b0, leader) + rank;
-                long long slot = -1;
-                if (dest == 0 && b0 < cap) slot = own + b0;
-                else if (dest > 0 && b0 < capo) slot = own + cap + (long long)(dest - 1) * capo + b0;
-                if (slot >= 0) put(nxt, slot, cnew, ox, oy, u);
-                else
-                    to_overflow(nxp ? a.ovf[1].p : a.ovf[0].p, nxp ? a.ovf[1].gs : a.ovf[0].gs,
-                                a.ovf_cap, st, nxp, cnew, ox, oy, u[0], u[1], u[2], s);
-            }
         }
+        __syncthreads();
+        if (threadIdx.x < 2 * kSegs) {
+            const int s = threadIdx.x / kSegs, k = threadIdx.x - (threadIdx.x / kSegs) * kSegs;
+            const long long lim = k == 0 ? cap : capo;
+            int* cnxt = nxp ? a.cnt[1] : a.cnt[0];
+            cnxt[((long long)t * 2 + s) * kSegs + k] = (int)min((long long)s_out[s][k], lim);
+        }
+        // add the current window into the global fixed-point current
+        unsigned long long* Jg = reinterpret_cast<unsigned long long*>(a.Jfix + G.cell_off);
+        for (int idx = threadIdx.x; idx < 3 * NW; idx += blockDim.x) {
+            const int hi = jw[idx], lo = jw[3 * NW + idx];
+            if ((hi | lo) == 0) continue;
+            const unsigned long long v = (unsigned long long)((long long)hi * (1ll << (40 - kwin)) +
+                                                              (long long)lo * (1ll << (40 - kwin - lbits)));
+            const int c = idx / NW;
+            const int w = idx - c * NW;
+            const int wy = w / WX;
+            const int wx = w - wy * WX;
+            const int gx = ((X0 - 2 + wx) % nx + nx) % nx;
+            const int gy = ((Y0 - 2 + wy) % ny + ny) % ny;
+            atomicAdd(Jg + c * a.ntot + (long long)gy * nx + gx, v);
+        }
+        const double sum = block_sum((double)ek, s_red);  // begins with a block barrier
+        if (threadIdx.x == 0 && sum != 0.0) atomicAdd(&a.cg[g].uk, 0.5 * G.w * sum);
+        __syncthreads();
     }
-    __syncthreads();
-    if (threadIdx.x < 2 * kSegs) {
-        const int s = threadIdx.x / kSegs, k = threadIdx.x - (threadIdx.x / kSegs) * kSegs;
-        const long long lim = k == 0 ? cap : capo;
-        int* cnxt = nxp ? a.cnt[1] : a.cnt[0];
-        cnxt[((long long)t * 2 + s) * kSegs + k] = (int)min((long long)s_out[s][k], lim);
-    }
-    // add the current window into the global fixed-point current
-    unsigned long long* Jg = reinterpret_cast<unsigned long long*>(a.Jfix + G.cell_off);
-    for (int idx = threadIdx.x; idx < 3 * NW; idx += blockDim.x) {
-        const int hi = jw[idx], lo = jw[3 * NW + idx];
-        if ((hi | lo) == 0) continue;
-        const unsigned long long v = (unsigned long long)((long long)hi * (1ll << (40 - kwin)) +
-                                                          (long long)lo * (1ll << (40 - kwin - lbits)));
-        const int c = idx / NW;
-        const int w = idx - c * NW;
-        const int wy = w / WX;
-        const int wx = w - wy * WX;
-        const int gx = ((X0 - 2 + wx) % nx + nx) % nx;
-        const int gy = ((Y0 - 2 + wy) % ny + ny) % ny;
-        atomicAdd(Jg + c * a.ntot + (long long)gy * nx + gx, v);
-    }
-    const double sum = block_sum((double)ek, s_red);
-    if (threadIdx.x == 0 && sum != 0.0) atomicAdd(&a.cg[a.g].uk, 0.5 * G.w * sum);
 }
 
 // ---------------------------------------------------------------------------------
 // 0. Overflow particles: global-memory push; they stay in the overflow list until the
 // host re-sorts after the pic_step call.
 // ---------------------------------------------------------------------------------
-__global__ void k_mixed_begin(DevStatus* st) {
+__global__ void k_mixed_begin(DevStatus* st, int* work) {
+    if (threadIdx.x < 4) work[threadIdx.x] = 0;
     if (threadIdx.x == 0 && !st->stop) st->ovf_count[st->parity ^ 1u] = 0ull;
 }
 
 template <int P>
+__device__ __forceinline__ bool push_global(const GridDev& G, const GlobalMem& M, int s, int ci, int cj,
+                                            float& ox, float& oy, float u[3], int& di, int& dj,
+                                            float& ek) {
+    return push_one<P>(M, push_const(G, s), ci, cj, ox, oy, u, di, dj, ek);
+}
+
 __global__ void __launch_bounds__(kTileThreads)
 k_push_overflow(const MixedArgs a) {
-    __shared__ double s_red[32];
     DevStatus* st = a.st;
     if (st->stop) return;
     const int par = (int)st->parity;
     const long long n = min((long long)st->ovf_count[par], a.ovf_cap);
-    const GridDev& G = a.grids[a.g];
-    const GlobalMem M{a.F32 + G.cell_off, reinterpret_cast<unsigned long long*>(a.Jfix + G.cell_off),
-                      a.ntot, G.nx, G.ny, (float)G.jscale};
-    float ek = 0.f;
     const Slots O = par ? a.ovf[1] : a.ovf[0];
     for (long long k = (long long)blockIdx.x * blockDim.x + threadIdx.x; k < n;
          k += (long long)gridDim.x * blockDim.x) {
         int c;
         float ox, oy, u[3];
         get(O.p, k, c, ox, oy, u);
-        const int s = O.gs[k];
+        const int gs = O.gs[k];
+        const int s = gs & 1, g = gs >> 1;
+        const GridDev& G = a.grids[g];
+        const GlobalMem M{a.F32 + G.cell_off, reinterpret_cast<unsigned long long*>(a.Jfix + G.cell_off),
+                          a.ntot, G.nx, G.ny, (float)G.jscale};
         const int ci = c & 0xffff, cj = c >> 16;
         int di, dj;
-        if (!push_one<P>(M, push_const(G, s), ci, cj, ox, oy, u, di, dj, ek)) flag_bad(st, u);
+        float ek = 0.f;
+        bool ok;
+        switch (G.order) {
+        case 1: ok = push_global<1>(G, M, s, ci, cj, ox, oy, u, di, dj, ek); break;
+        case 2: ok = push_global<2>(G, M, s, ci, cj, ox, oy, u, di, dj, ek); break;
+        default: ok = push_global<3>(G, M, s, ci, cj, ox, oy, u, di, dj, ek); break;
+        }
+        if (!ok) flag_bad(st, u);
+        if (ek != 0.f) atomicAdd(&a.cg[g].uk, 0.5 * G.w * (double)ek);
         const int cnew = wrapi(ci + di, G.nx) | (wrapi(cj + dj, G.ny) << 16);
         to_overflow(par ? a.ovf[0].p : a.ovf[1].p, par ? a.ovf[0].gs : a.ovf[1].gs, a.ovf_cap, st,
-                    par ^ 1, cnew, ox, oy, u[0], u[1], u[2], s);
+                    par ^ 1, cnew, ox, oy, u[0], u[1], u[2], gs);
     }
-    const double sum = block_sum((double)ek, s_red);
-    if (threadIdx.x == 0 && sum != 0.0) atomicAdd(&a.cg[a.g].uk, 0.5 * G.w * sum);
 }
 
 __global__ void k_mixed_swap(DevStatus* st) {
@@ -478,7 +518,7 @@ __global__ void k_mixed_swap(DevStatus* st) {
 }
 
 // ---------------------------------------------------------------------------------
-// Loading and re-sorting
+// Loading and re-sorting (one simulation at a time; tile indices are local to it)
 // ---------------------------------------------------------------------------------
 // FP64 physical particles -> staging (cell + FP32 offsets, FP32 momenta).
 __global__ void k_stage_fp64(long long n, const double* x, const double* y, const double* ux,
@@ -552,6 +592,7 @@ __global__ void k_scatter(long long n, GridDev G, int s, const unsigned long lon
     put(B, dst, S.cij[src], S.ox[src], S.oy[src], u);
 }
 
+// cnt points at the simulation's first count slot.
 __global__ void k_set_counts(int ntiles, int s, const int* bincnt, int* cnt) {
     const int t = blockIdx.x * blockDim.x + threadIdx.x;
     if (t >= ntiles) return;
@@ -585,11 +626,11 @@ __global__ void k_gather_bins(GridDev G, int s, const int* cnt, const long long*
     for (int q = threadIdx.x; q < n; q += blockDim.x) to_staging(B, src0 + q, S, dst0 + q);
 }
 
-// Overflow-list entries of species s appended after `base` in staging form.
-__global__ void k_gather_overflow(long long n_over, int s, Slots O, long long base,
+// Overflow-list entries with code gs (species | simulation << 1) appended after `base`.
+__global__ void k_gather_overflow(long long n_over, int gs, Slots O, long long base,
                                   unsigned long long* cursor, PartArrays S) {
     const long long k = (long long)blockIdx.x * blockDim.x + threadIdx.x;
-    if (k >= n_over || O.gs[k] != s) return;
+    if (k >= n_over || O.gs[k] != gs) return;
     const long long d = base + (long long)atomicAdd(cursor, 1ull);
     to_staging(O.p, k, S, d);
 }
@@ -633,10 +674,23 @@ cudaError_t alloc_parts(PartArrays& A, size_t n, bool with_gs) {
     return e;
 }
 
-MixedArgs make_args(MixedState* m) {
+// Staged particles of every (simulation, species), index 2 g + s.
+struct Staged {
+    std::vector<PartArrays> S;
+    std::vector<long long> n;
+    explicit Staged(int ngrids) : S(2 * ngrids), n(2 * ngrids, 0) {}
+    ~Staged() {
+        for (PartArrays& a : S) free_parts(a);
+    }
+};
+
+MixedArgs make_args(MixedState* m, int order) {
     MixedArgs a{};
     a.grids = m->dgrids;
-    a.g = 0;
+    a.tile_grid = m->tile_grid;
+    a.tlist = m->tlist + m->order_first[order];
+    a.ntl = m->order_n[order];
+    a.work = m->work + order;
     a.ntot = m->ntot;
     a.F32 = m->F32;
     a.Jfix = m->Jfix;
@@ -645,7 +699,6 @@ MixedArgs make_args(MixedState* m) {
         a.cnt[p] = m->cnt[p];
         a.ovf[p] = m->ovf[p];
     }
-    a.ovf_cap = m->ovf_cap;
     a.ovf_cap = m->ovf_cap;
     a.cg = m->cg;
     a.st = m->st;
@@ -669,11 +722,18 @@ int read_status(MixedState* m, DevStatus& hs, cudaStream_t st, std::string& err)
     return PIC_OK;
 }
 
-// Sort n staged particles of species s into the stayer segments of buffer `par`.
-// Returns PIC_ENOMEM (nothing written) when a bin would overflow.
-int sort_into_bins(MixedState* m, int par, int s, PartArrays S, long long n, cudaStream_t st,
-                   std::string& err) {
-    const GridDev& G = *m->G;
+long long round32(double c) { return ((long long)std::ceil(c) + 31) / 32 * 32; }
+
+int* cnt_of(MixedState* m, int par, int g) {
+    return m->cnt[par] + (long long)m->G[g].tile_first * 2 * kSegs;
+}
+
+// Sort n staged particles of species s of simulation g into the stayer segments of
+// buffer `par`. Returns PIC_ENOMEM (nothing written) when a bin would overflow, with
+// the fullest bin's count in *need.
+int sort_into_bins(MixedState* m, int g, int par, int s, PartArrays S, long long n, cudaStream_t st,
+                   long long* need, std::string& err) {
+    const GridDev& G = m->G[g];
     const int ntiles = G.ntiles;
     unsigned int* cellcnt = nullptr;
     int* bincnt = nullptr;
@@ -712,6 +772,7 @@ int sort_into_bins(MixedState* m, int par, int s, PartArrays S, long long n, cud
             mx = std::max<long long>(mx, hcnt[t]);
             start[t + 1] = start[t] + hcnt[t];
         }
+        if (need) *need = mx;
         if (mx > G.cap) {
             rc = PIC_ENOMEM;  // caller grows the bins and retries
         } else {
@@ -728,7 +789,7 @@ int sort_into_bins(MixedState* m, int par, int s, PartArrays S, long long n, cud
             if (e == cudaSuccess && n)
                 k_scatter<<<grid1(n), 256, 0, st>>>(n, G, s, kb.Current(), vb.Current(), binstart, S,
                                                     m->buf[par]);
-            k_set_counts<<<grid1(ntiles), 256, 0, st>>>(ntiles, s, bincnt, m->cnt[par]);
+            k_set_counts<<<grid1(ntiles), 256, 0, st>>>(ntiles, s, bincnt, cnt_of(m, par, g));
             A(cudaGetLastError());
             A(cudaStreamSynchronize(st));
         }
@@ -743,14 +804,14 @@ int sort_into_bins(MixedState* m, int par, int s, PartArrays S, long long n, cud
     return rc;
 }
 
-// All live particles of species s (every bin segment of buffer `par` + its overflow
-// list) into a new staging set.
-int gather_species(MixedState* m, int par, int s, PartArrays& S, long long& n, cudaStream_t st,
+// All live particles of species s of simulation g (every bin segment of buffer `par` +
+// its overflow-list entries) into a new staging set.
+int gather_species(MixedState* m, int g, int par, int s, PartArrays& S, long long& n, cudaStream_t st,
                    std::string& err) {
-    const GridDev& G = *m->G;
+    const GridDev& G = m->G[g];
     const long long nb_seg = (long long)G.ntiles * kSegs;
     std::vector<int> cnt(2 * nb_seg);
-    MCK(cudaMemcpyAsync(cnt.data(), m->cnt[par], cnt.size() * sizeof(int), cudaMemcpyDeviceToHost, st));
+    MCK(cudaMemcpyAsync(cnt.data(), cnt_of(m, par, g), cnt.size() * sizeof(int), cudaMemcpyDeviceToHost, st));
     DevStatus hs{};
     MCK(cudaMemcpyAsync(&hs, m->st, sizeof hs, cudaMemcpyDeviceToHost, st));
     MCK(cudaStreamSynchronize(st));
@@ -770,8 +831,8 @@ int gather_species(MixedState* m, int par, int s, PartArrays& S, long long& n, c
     MCK(dalloc(&cursor, 1));
     MCK(cudaMemcpyAsync(doff, off.data(), off.size() * sizeof(long long), cudaMemcpyHostToDevice, st));
     MCK(cudaMemsetAsync(cursor, 0, sizeof(unsigned long long), st));
-    k_gather_bins<<<(unsigned)nb_seg, 256, 0, st>>>(G, s, m->cnt[par], doff, m->buf[par], S);
-    if (no) k_gather_overflow<<<grid1(no), 256, 0, st>>>(no, s, m->ovf[par], nb, cursor, S);
+    k_gather_bins<<<(unsigned)nb_seg, 256, 0, st>>>(G, s, cnt_of(m, par, g), doff, m->buf[par], S);
+    if (no) k_gather_overflow<<<grid1(no), 256, 0, st>>>(no, s | (g << 1), m->ovf[par], nb, cursor, S);
     unsigned long long hcur = 0;
     MCK(cudaMemcpyAsync(&hcur, cursor, sizeof hcur, cudaMemcpyDeviceToHost, st));
     MCK(cudaStreamSynchronize(st));
@@ -781,21 +842,24 @@ int gather_species(MixedState* m, int par, int s, PartArrays& S, long long& n, c
     return PIC_OK;
 }
 
-long long round32(double c) { return ((long long)std::ceil(c) + 31) / 32 * 32; }
-
-// (Re)allocate both bin buffers for stayer capacity cap and outbox capacity capo
-// (contents are not preserved; all counts are zeroed).
-int alloc_bins(MixedState* m, long long cap, long long capo, cudaStream_t st, std::string& err) {
-    GridDev& G = *m->G;
+// (Re)allocate both bin buffers with per-simulation stayer capacity cap[g] and outbox
+// capacity capo[g] (contents are not preserved; all counts are zeroed).
+int alloc_bins(MixedState* m, const std::vector<long long>& cap, const std::vector<long long>& capo,
+               cudaStream_t st, std::string& err) {
     for (int p = 0; p < 2; p++) {
         if (m->buf[p]) cudaFree(m->buf[p]);
         m->buf[p] = nullptr;
     }
     m->gen++;
-    G.cap = cap;
-    G.capo = capo;
-    G.bin_off = 0;
-    m->nslots = (long long)G.ntiles * 2 * bin_stride(G);
+    long long off = 0;
+    for (int g = 0; g < m->ngrids; g++) {
+        GridDev& G = m->G[g];
+        G.cap = cap[g];
+        G.capo = capo[g];
+        G.bin_off = off;
+        off += (long long)G.ntiles * 2 * bin_stride(G);
+    }
+    m->nslots = off;
     for (int p = 0; p < 2; p++) {
         cudaError_t e = dalloc(&m->buf[p], (size_t)m->nslots * kFields);
         if (e != cudaSuccess) {
@@ -803,103 +867,181 @@ int alloc_bins(MixedState* m, long long cap, long long capo, cudaStream_t st, st
             err = "bin allocation failed (" + std::to_string(m->nslots) + " slots per buffer)";
             return PIC_ENOMEM;
         }
-        MCK(cudaMemsetAsync(m->cnt[p], 0, (size_t)G.ntiles * 2 * kSegs * sizeof(int), st));
+        MCK(cudaMemsetAsync(m->cnt[p], 0, (size_t)m->ntiles_total * 2 * kSegs * sizeof(int), st));
     }
     return PIC_OK;
 }
 
-// Re-sort both species into fresh bins with capacities at least (cap_min, capo_min).
-int rebuild(MixedState* m, long long cap_min, long long capo_min, cudaStream_t st, std::string& err) {
-    DevStatus hs{};
-    if (int rc = read_status(m, hs, st, err)) return rc;
-    const int par = (int)hs.parity;
-    PartArrays S[2]{};
-    long long n[2] = {0, 0};
-    for (int s = 0; s < 2; s++) {
-        int rc = gather_species(m, par, s, S[s], n[s], st, err);
-        if (rc) {
-            free_parts(S[0]);
-            free_parts(S[1]);
-            return rc;
-        }
-    }
-    long long cap = std::max(cap_min, m->G->cap), capo = std::max(capo_min, m->G->capo);
+// Gather every simulation's particles of buffer `par` into staging.
+int gather_all(MixedState* m, int par, Staged& A, cudaStream_t st, std::string& err) {
+    for (int g = 0; g < m->ngrids; g++)
+        for (int s = 0; s < 2; s++)
+            if (int rc = gather_species(m, g, par, s, A.S[2 * g + s], A.n[2 * g + s], st, err)) return rc;
+    return PIC_OK;
+}
+
+// Allocate bins of at least the given capacities and sort everything staged in A into
+// buffer `par`, growing a simulation's stayer capacity whenever one of its bins would
+// overflow. Uploads the descriptors and clears the overflow lists.
+int place_all(MixedState* m, int par, Staged& A, std::vector<long long> cap, std::vector<long long> capo,
+              cudaStream_t st, std::string& err) {
     int rc = PIC_OK;
     for (int attempt = 0; attempt < 8; attempt++) {
         rc = alloc_bins(m, cap, capo, st, err);
-        if (rc) break;
-        rc = sort_into_bins(m, par, 0, S[0], n[0], st, err);
-        if (rc == PIC_OK) rc = sort_into_bins(m, par, 1, S[1], n[1], st, err);
-        if (rc != PIC_ENOMEM) break;
-        cap = cap * 3 / 2 + 32;  // a bin would overflow: grow and retry
+        if (rc) return rc;
+        bool grown = false;
+        for (int g = 0; g < m->ngrids && rc == PIC_OK; g++)
+            for (int s = 0; s < 2 && rc == PIC_OK; s++) {
+                long long need = 0;
+                rc = sort_into_bins(m, g, par, s, A.S[2 * g + s], A.n[2 * g + s], st, &need, err);
+                if (rc == PIC_ENOMEM) {
+                    cap[g] = std::max(cap[g] * 3 / 2 + 32, round32(1.25 * (double)need + 32.0));
+                    grown = true;
+                }
+            }
+        if (!grown) break;
+        rc = PIC_ENOMEM;
     }
-    free_parts(S[0]);
-    free_parts(S[1]);
     if (rc) return rc;
-    MCK(cudaMemcpyAsync((void*)m->dgrids, m->G, sizeof(GridDev), cudaMemcpyHostToDevice, st));
-    MCK(cudaMemsetAsync(&m->st->ovf_count, 0, sizeof(hs.ovf_count), st));
+    MCK(cudaMemcpyAsync((void*)m->dgrids, m->G, m->ngrids * sizeof(GridDev), cudaMemcpyHostToDevice, st));
+    MCK(cudaMemsetAsync(&m->st->ovf_count, 0, sizeof(DevStatus::ovf_count), st));
     MCK(cudaStreamSynchronize(st));
-    m->n[0] = n[0];
-    m->n[1] = n[1];
+    for (int q = 0; q < 2 * m->ngrids; q++) m->n[q] = A.n[q];
+    return PIC_OK;
+}
+
+// Re-sort every simulation into fresh bins with capacities at least (cap_min, capo_min).
+int rebuild(MixedState* m, std::vector<long long> cap_min, std::vector<long long> capo_min,
+            cudaStream_t st, std::string& err) {
+    DevStatus hs{};
+    if (int rc = read_status(m, hs, st, err)) return rc;
+    const int par = (int)hs.parity;
+    Staged A(m->ngrids);
+    if (int rc = gather_all(m, par, A, st, err)) return rc;
+    for (int g = 0; g < m->ngrids; g++) {
+        cap_min[g] = std::max(cap_min[g], m->G[g].cap);
+        capo_min[g] = std::max(capo_min[g], m->G[g].capo);
+    }
+    if (int rc = place_all(m, par, A, cap_min, capo_min, st, err)) return rc;
     m->rebins++;
     return PIC_OK;
+}
+
+std::vector<long long> current_caps(MixedState* m, bool outboxes) {
+    std::vector<long long> v(m->ngrids);
+    for (int g = 0; g < m->ngrids; g++) v[g] = outboxes ? m->G[g].capo : m->G[g].cap;
+    return v;
 }
 
 }  // namespace
 
 // =====================================================================================
 
-int mixed_create(MixedState** out, const pic_params& p, GridDev& G, const GridDev* dgrids,
-                 long long ntot, float* F32, long long* Jfix, CgState* cg, DevStatus* st,
-                 std::string& err) {
+int mixed_create(MixedState** out, const pic_params* p, int ngrids, GridDev* G,
+                 const GridDev* dgrids, long long ntot, float* F32, long long* Jfix, CgState* cg,
+                 DevStatus* st, std::string& err) {
     *out = nullptr;
     MixedState* m = new MixedState();
-    m->prm = p;
-    m->G = &G;
+    m->ngrids = ngrids;
+    m->G = G;
     m->dgrids = dgrids;
     m->ntot = ntot;
     m->F32 = F32;
     m->Jfix = Jfix;
     m->cg = cg;
     m->st = st;
-    int tx = p.tile_x, ty = p.tile_y;
-    if (tx <= 0) tx = std::min(32, p.nx);
-    if (ty <= 0) ty = std::min(16, p.ny);
-    tx = std::min(tx, p.nx);
-    ty = std::min(ty, p.ny);
-    G.tx = tx;
-    G.ty = ty;
-    G.ntx = (p.nx + tx - 1) / tx;
-    G.nty = (p.ny + ty - 1) / ty;
-    G.ntiles = G.ntx * G.nty;
-    G.tile_first = 0;
-    G.wx = tx + 5;
-    G.wy = ty + 5;
-    m->smem = (size_t)6 * G.wx * G.wy * sizeof(int) + (size_t)6 * G.wx * G.wy * sizeof(float);
-    const double slack = p.bin_slack > 0 ? p.bin_slack : 1.25;
-    const long long expect = 2ll * p.ppc * (long long)p.nx * p.ny;
+    m->n.assign(2 * ngrids, 0);
+    // tiles of every simulation, one global numbering
+    int ntiles = 0;
+    long long expect = 0;
+    std::vector<long long> cap(ngrids), capo(ngrids);
+    for (int g = 0; g < ngrids; g++) {
+        const pic_params& q = p[g];
+        GridDev& D = G[g];
+        int tx = q.tile_x, ty = q.tile_y;
+        if (tx <= 0) tx = std::min(32, q.nx);
+        if (ty <= 0) ty = std::min(16, q.ny);
+        D.tx = std::min(tx, q.nx);
+        D.ty = std::min(ty, q.ny);
+        D.ntx = (q.nx + D.tx - 1) / D.tx;
+        D.nty = (q.ny + D.ty - 1) / D.ty;
+        D.ntiles = D.ntx * D.nty;
+        D.tile_first = ntiles;
+        ntiles += D.ntiles;
+        D.wx = D.tx + 5;
+        D.wy = D.ty + 5;
+        const size_t sm = (size_t)6 * D.wx * D.wy * sizeof(int) + (size_t)6 * D.wx * D.wy * sizeof(float);
+        m->smem[D.order] = std::max(m->smem[D.order], sm);
+        const double slack = q.bin_slack > 0 ? q.bin_slack : 1.25;
+        cap[g] = round32((double)q.ppc * D.tx * D.ty * slack + 64.0);
+        capo[g] = round32((double)q.ppc * std::max(D.tx, D.ty) * 1.5 + 32.0);
+        expect += 2ll * q.ppc * (long long)q.nx * q.ny;
+    }
+    m->ntiles_total = ntiles;
+    // per-order tile lists, largest expected work first
+    std::vector<int> tg(ntiles), tl;
+    std::vector<std::pair<long long, int>> order_tiles[4];
+    for (int g = 0; g < ngrids; g++) {
+        const GridDev& D = G[g];
+        for (int t = 0; t < D.ntiles; t++) {
+            tg[D.tile_first + t] = g;
+            const int tyi = t / D.ntx, txi = t - tyi * D.ntx;
+            const long long cells = (long long)(std::min(D.tx, D.nx - txi * D.tx)) *
+                                    std::min(D.ty, D.ny - tyi * D.ty);
+            order_tiles[D.order].push_back({cells * p[g].ppc, D.tile_first + t});
+        }
+    }
+    for (int P = 1; P <= 3; P++) {
+        std::stable_sort(order_tiles[P].begin(), order_tiles[P].end(),
+                         [](const std::pair<long long, int>& x, const std::pair<long long, int>& y) {
+                             return x.first > y.first;
+                         });
+        m->order_first[P] = (int)tl.size();
+        m->order_n[P] = (int)order_tiles[P].size();
+        for (auto& e : order_tiles[P]) tl.push_back(e.second);
+    }
     m->ovf_cap = std::max<long long>(65536, expect / 8);
-    cudaError_t e = cudaSuccess;
     m->ovf_cap = (m->ovf_cap + 31) / 32 * 32;
+    cudaError_t e = cudaSuccess;
     for (int q = 0; q < 2 && e == cudaSuccess; q++) {
-        e = cudaMalloc(&m->cnt[q], (size_t)G.ntiles * 2 * kSegs * sizeof(int));
+        e = dalloc(&m->cnt[q], (size_t)ntiles * 2 * kSegs);
         if (e == cudaSuccess) e = dalloc(&m->ovf[q].p, (size_t)m->ovf_cap * kFields);
         if (e == cudaSuccess) e = dalloc(&m->ovf[q].gs, (size_t)m->ovf_cap);
     }
+    if (e == cudaSuccess) e = dalloc(&m->tile_grid, (size_t)ntiles);
+    if (e == cudaSuccess) e = dalloc(&m->tlist, (size_t)ntiles);
+    if (e == cudaSuccess) e = dalloc(&m->work, 4);
+    if (e == cudaSuccess) e = cudaMemcpy(m->tile_grid, tg.data(), ntiles * sizeof(int), cudaMemcpyHostToDevice);
+    if (e == cudaSuccess) e = cudaMemcpy(m->tlist, tl.data(), ntiles * sizeof(int), cudaMemcpyHostToDevice);
+    if (e == cudaSuccess) e = cudaMemset(m->work, 0, 4 * sizeof(int));
     int rc = PIC_OK;
     if (e == cudaSuccess) {
-        const long long cap = round32((double)p.ppc * tx * ty * slack + 64.0);
-        const long long capo = round32((double)p.ppc * std::max(tx, ty) * 1.5 + 32.0);
         rc = alloc_bins(m, cap, capo, 0, err);
         if (rc == PIC_OK) e = cudaDeviceSynchronize();
     }
+    // Shared-memory opt-in: only ever raised, since the attribute belongs to the kernel
+    // and other handles in the process may need more than this one.
+    int dev = 0, nsm = 152;
+    if (e == cudaSuccess) e = cudaGetDevice(&dev);
+    if (e == cudaSuccess) e = cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
+    auto setup = [&](auto kern, int P) {
+        if (m->order_n[P] == 0) return cudaSuccess;
+        cudaFuncAttributes fa{};
+        cudaError_t r = cudaFuncGetAttributes(&fa, kern);
+        if (r == cudaSuccess && (size_t)fa.maxDynamicSharedSizeBytes < m->smem[P])
+            r = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)m->smem[P]);
+        int nb = 0;
+        if (r == cudaSuccess)
+            r = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, kern, kTileThreads, m->smem[P]);
+        if (r == cudaSuccess && nb < 1) r = cudaErrorInvalidConfiguration;
+        m->pblocks[P] = std::min(m->order_n[P], nb * nsm);
+        return r;
+    };
+    if (rc == PIC_OK && e == cudaSuccess) e = setup(k_push_tile<1>, 1);
+    if (rc == PIC_OK && e == cudaSuccess) e = setup(k_push_tile<2>, 2);
+    if (rc == PIC_OK && e == cudaSuccess) e = setup(k_push_tile<3>, 3);
     if (rc == PIC_OK && e == cudaSuccess) {
-        auto set = [&](auto kern) {
-            return cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)m->smem);
-        };
-        e = set(k_push_tile<1>);
-        if (e == cudaSuccess) e = set(k_push_tile<2>);
-        if (e == cudaSuccess) e = set(k_push_tile<3>);
+        e = cudaMemcpy((void*)dgrids, G, ngrids * sizeof(GridDev), cudaMemcpyHostToDevice);
     }
     if (rc == PIC_OK && e != cudaSuccess) {
         err = std::string("MIXED32 setup failed: ") + cudaGetErrorString(e);
@@ -921,16 +1063,19 @@ void mixed_destroy(MixedState* m) {
         for (void* q : ps)
             if (q) cudaFree(q);
     }
+    void* ps[] = {m->tile_grid, m->tlist, m->work};
+    for (void* q : ps)
+        if (q) cudaFree(q);
     delete m;
 }
 
-int mixed_load(MixedState* m, int s, const double* x, const double* y, const double* ux,
+int mixed_load(MixedState* m, int g, int s, const double* x, const double* y, const double* ux,
                const double* uy, const double* uz, long long n, cudaStream_t st, std::string& err) {
     DevStatus hs{};
     if (int rc = read_status(m, hs, st, err)) return rc;
     // fold any overflow-list particles back into bins first so the list holds none of s
     if (hs.ovf_count[hs.parity]) {
-        int rc = rebuild(m, m->G->cap, m->G->capo, st, err);
+        int rc = rebuild(m, current_caps(m, false), current_caps(m, true), st, err);
         if (rc) return rc;
     }
     const int par = (int)hs.parity;
@@ -945,7 +1090,7 @@ int mixed_load(MixedState* m, int s, const double* x, const double* y, const dou
     MCK(dalloc(&nbad, 1));
     MCK(cudaMemsetAsync(nbad, 0, sizeof(unsigned long long), st));
     if (n)
-        k_stage_fp64<<<grid1(n), 256, 0, st>>>(n, in, in + n, in + 2 * n, in + 3 * n, in + 4 * n, *m->G,
+        k_stage_fp64<<<grid1(n), 256, 0, st>>>(n, in, in + n, in + 2 * n, in + 3 * n, in + 4 * n, m->G[g],
                                                S, nbad);
     unsigned long long hbad = 0;
     MCK(cudaMemcpyAsync(&hbad, nbad, sizeof hbad, cudaMemcpyDeviceToHost, st));
@@ -957,51 +1102,45 @@ int mixed_load(MixedState* m, int s, const double* x, const double* y, const dou
         err = "non-finite particle position or momentum";
         return PIC_EINVAL;
     }
-    int rc = sort_into_bins(m, par, s, S, n, st, err);  // also zeroes s's outbox counts
+    long long need = 0;
+    int rc = sort_into_bins(m, g, par, s, S, n, st, &need, err);  // also zeroes s's outbox counts
     if (rc == PIC_ENOMEM) {
-        // a bin would overflow: rebuild both species with larger bins
-        PartArrays other{};
-        long long no = 0;
-        rc = gather_species(m, par, 1 - s, other, no, st, err);
+        // a bin would overflow: re-sort everything with larger bins for this simulation
+        Staged A(m->ngrids);
+        rc = gather_all(m, par, A, st, err);
         if (rc == PIC_OK) {
-            long long cap = m->G->cap;
-            for (int attempt = 0; attempt < 8; attempt++) {
-                cap = cap * 3 / 2 + 32;
-                rc = alloc_bins(m, cap, m->G->capo, st, err);
-                if (rc) break;
-                rc = sort_into_bins(m, par, s, S, n, st, err);
-                if (rc == PIC_OK) rc = sort_into_bins(m, par, 1 - s, other, no, st, err);
-                if (rc != PIC_ENOMEM) break;
-            }
+            free_parts(A.S[2 * g + s]);
+            A.S[2 * g + s] = S;
+            A.n[2 * g + s] = n;
+            S = PartArrays{};
+            std::vector<long long> cap = current_caps(m, false);
+            cap[g] = std::max(cap[g], round32(1.25 * (double)need + 32.0));
+            rc = place_all(m, par, A, cap, current_caps(m, true), st, err);
             m->rebins++;
         }
-        free_parts(other);
+    } else if (rc == PIC_OK) {
+        MCK(cudaMemcpyAsync((void*)(m->dgrids + g), m->G + g, sizeof(GridDev), cudaMemcpyHostToDevice, st));
+        MCK(cudaStreamSynchronize(st));
+        m->n[2 * g + s] = n;
     }
     free_parts(S);
-    if (rc) return rc;
-    MCK(cudaMemcpyAsync((void*)m->dgrids, m->G, sizeof(GridDev), cudaMemcpyHostToDevice, st));
-    MCK(cudaStreamSynchronize(st));
-    m->n[s] = n;
-    return PIC_OK;
+    return rc;
 }
 
 void mixed_enqueue(MixedState* m, cudaStream_t st, int part) {
-    const MixedArgs a = make_args(m);
-    const GridDev& G = *m->G;
-    const int P = G.order;
     if (part == 0) {
-        k_mixed_begin<<<1, 32, 0, st>>>(m->st);
-        const unsigned ob = 152;
-        switch (P) {
-        case 1: k_push_overflow<1><<<ob, kTileThreads, 0, st>>>(a); break;
-        case 2: k_push_overflow<2><<<ob, kTileThreads, 0, st>>>(a); break;
-        default: k_push_overflow<3><<<ob, kTileThreads, 0, st>>>(a); break;
-        }
+        k_mixed_begin<<<1, 32, 0, st>>>(m->st, m->work);
+        k_push_overflow<<<152, kTileThreads, 0, st>>>(make_args(m, 0));
     } else if (part == 1) {
-        switch (P) {
-        case 1: k_push_tile<1><<<G.ntiles, kTileThreads, m->smem, st>>>(a); break;
-        case 2: k_push_tile<2><<<G.ntiles, kTileThreads, m->smem, st>>>(a); break;
-        default: k_push_tile<3><<<G.ntiles, kTileThreads, m->smem, st>>>(a); break;
+        for (int P = 1; P <= 3; P++) {
+            if (m->order_n[P] == 0) continue;
+            const MixedArgs a = make_args(m, P);
+            const unsigned nb = (unsigned)m->pblocks[P];
+            switch (P) {
+            case 1: k_push_tile<1><<<nb, kTileThreads, m->smem[1], st>>>(a); break;
+            case 2: k_push_tile<2><<<nb, kTileThreads, m->smem[2], st>>>(a); break;
+            default: k_push_tile<3><<<nb, kTileThreads, m->smem[3], st>>>(a); break;
+            }
         }
     } else {
         k_mixed_swap<<<1, 32, 0, st>>>(m->st);
@@ -1015,37 +1154,43 @@ int mixed_after_steps(MixedState* m, cudaStream_t st, std::string& err) {
     if (int rc = read_status(m, hs, st, err)) return rc;
     const int par = (int)hs.parity;
     if (hs.ovf_count[par] == 0) return PIC_OK;
-    // particles are parked in the overflow list: re-sort with room to spare. Grow the
-    // stayer capacity to 1.25x the fullest tile and double the outboxes if any is full.
-    const GridDev& G = *m->G;
-    std::vector<int> cnt((size_t)G.ntiles * 2 * kSegs);
+    // particles are parked in the overflow list: re-sort with room to spare. Grow each
+    // simulation's stayer capacity to 1.25x its fullest tile and double its outboxes if
+    // any is full.
+    std::vector<int> cnt((size_t)m->ntiles_total * 2 * kSegs);
     MCK(cudaMemcpyAsync(cnt.data(), m->cnt[par], cnt.size() * sizeof(int), cudaMemcpyDeviceToHost, st));
     MCK(cudaStreamSynchronize(st));
-    long long mx = 0;
-    bool outbox_full = false;
-    for (long long b = 0; b < (long long)G.ntiles * 2; b++) {
-        long long tot = 0;
-        for (int k = 0; k < kSegs; k++) {
-            tot += cnt[b * kSegs + k];
-            if (k > 0 && cnt[b * kSegs + k] >= G.capo) outbox_full = true;
+    std::vector<long long> cap(m->ngrids), capo(m->ngrids);
+    const long long excess = (long long)hs.ovf_count[par];  // upper bound on any tile's excess
+    for (int g = 0; g < m->ngrids; g++) {
+        const GridDev& G = m->G[g];
+        long long mx = 0;
+        bool outbox_full = false;
+        for (long long b = (long long)G.tile_first * 2; b < (long long)(G.tile_first + G.ntiles) * 2; b++) {
+            long long tot = 0;
+            for (int k = 0; k < kSegs; k++) {
+                tot += cnt[b * kSegs + k];
+                if (k > 0 && cnt[b * kSegs + k] >= G.capo) outbox_full = true;
+            }
+            mx = std::max(mx, tot);
         }
-        mx = std::max(mx, tot);
+        cap[g] = std::max(round32(1.25 * (double)std::min(mx + excess, 2 * mx + 64)), G.cap);
+        capo[g] = outbox_full ? 2 * G.capo : G.capo;
     }
-    const long long per_tile_ovf = (long long)hs.ovf_count[par];  // upper bound on any tile's excess
-    const long long want = round32(1.25 * (double)std::min(mx + per_tile_ovf, 2 * mx + 64));
-    return rebuild(m, std::max(want, G.cap), outbox_full ? 2 * G.capo : G.capo, st, err);
+    return rebuild(m, cap, capo, st, err);
 }
 
-long long mixed_count(MixedState* m, int s) { return m->n[s]; }
+long long mixed_count(MixedState* m, int g, int s) { return m->n[2 * g + s]; }
 long long mixed_rebins(MixedState* m) { return m->rebins; }
 long long mixed_generation(MixedState* m) { return m->gen; }
 
-int mixed_particles(MixedState* m, int s, double* out, long long n, cudaStream_t st, std::string& err) {
+int mixed_particles(MixedState* m, int g, int s, double* out, long long n, cudaStream_t st,
+                    std::string& err) {
     DevStatus hs{};
     if (int rc = read_status(m, hs, st, err)) return rc;
     PartArrays S{};
     long long got = 0;
-    int rc = gather_species(m, (int)hs.parity, s, S, got, st, err);
+    int rc = gather_species(m, g, (int)hs.parity, s, S, got, st, err);
     if (rc) return rc;
     if (got != n) {
         free_parts(S);
@@ -1054,7 +1199,7 @@ int mixed_particles(MixedState* m, int s, double* out, long long n, cudaStream_t
     }
     double* t = nullptr;
     MCK(dalloc(&t, 5 * (size_t)std::max<long long>(n, 1)));
-    if (n) k_unstage<<<grid1(n), 256, 0, st>>>(n, *m->G, S, t);
+    if (n) k_unstage<<<grid1(n), 256, 0, st>>>(n, m->G[g], S, t);
     MCK(cudaMemcpyAsync(out, t, 5 * n * sizeof(double), cudaMemcpyDefault, st));
     MCK(cudaStreamSynchronize(st));
     cudaFree(t);

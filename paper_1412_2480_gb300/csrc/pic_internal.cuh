@@ -13,7 +13,9 @@ namespace pic {
 constexpr double kPi = 3.14159265358979323846;
 constexpr int kFieldThreads = 256;  // threads per block of the grid (field) kernels
 constexpr int kPushThreads = 256;   // threads per block of the FP64 particle kernel
-constexpr int kMaxWinCells = 6144;  // largest tile window (cells) of the MIXED32 kernel
+// Largest tile window (cells) of the MIXED32 kernel: 48 bytes of shared memory per cell
+// (six FP32 field words and six fixed-point current words) within the 227 KB of a CTA.
+constexpr int kMaxWinCells = 4800;
 
 // One simulation, as the kernels see it. Grid arrays of all simulations are
 // concatenated; cell_off is this simulation's first cell.

@@ -80,3 +80,25 @@ def random_fields(nx: int, ny: int, amplitude: float, seed: int) -> np.ndarray:
             ph = rng.random() * 2 * math.pi
             F[c] += rng.standard_normal() * np.cos(2 * math.pi * (mx * ii / nx + my * jj / ny) + ph)
     return F * amplitude
+
+
+# ---- the batched parameter scan: 48 uneven simulations ------------------------------
+# The paper scans the CFL number (Sec. 3.2), theta and the shape order (Sec. 3.3); the
+# scan table crosses those values with uneven grid sizes. Row k: CFL = SCAN_CFL[k mod 6],
+# theta = SCAN_THETA[floor(k/6) mod 4], shape order 1 + (k + floor(k/24)) mod 3, grid
+# SCAN_GRIDS[5k mod 8], gamma0 = 20, 16 particles per cell per species, 1e-3 spread,
+# seed 3 + k. The committed copy is scan48.json beside this module.
+SCAN_CFL = (0.5, 0.6, 0.7, 0.8, 0.9, 1.0)
+SCAN_THETA = (0.5, 0.55, 0.6, 0.75)
+SCAN_GRIDS = ((128, 128), (192, 128), (256, 128), (192, 192), (256, 192), (256, 256),
+              (384, 256), (512, 256))
+
+
+def scan_table(n: int = 48) -> list:
+    rows = []
+    for k in range(n):
+        nx, ny = SCAN_GRIDS[(5 * k) % len(SCAN_GRIDS)]
+        rows.append({"k": k, "nx": nx, "ny": ny, "cfl": SCAN_CFL[k % 6],
+                     "theta": SCAN_THETA[(k // 6) % 4], "order": 1 + (k + k // 24) % 3,
+                     "gamma0": 20.0, "ppc": 16, "u_th": 1e-3, "seed": 3 + k})
+    return rows

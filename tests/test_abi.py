@@ -72,3 +72,24 @@ def test_init_without_gpu_fails_cleanly():
     with pytest.raises(pic.PicError) as e:
         pic.pic_init(pic.pic_params_default())
     assert e.value.code in (pic.PIC_ECUDA, pic.PIC_ENOMEM)
+
+
+def test_batch_validation_on_host():
+    mixed = pic.pic_params_default(precision=pic.PIC_MIXED32)
+    fp64 = pic.pic_params_default()
+    cases = [[fp64, fp64],                                   # FP64 batches of > 1 are refused
+             [mixed, pic.pic_params_default(precision=pic.PIC_MIXED32, flags=pic.PIC_NO_GRAPH)],
+             [mixed, pic.pic_params_default(precision=pic.PIC_MIXED32, nx=4)],
+             [pic.pic_params_default(precision=pic.PIC_MIXED32, nx=256, ny=256, tile_x=200, tile_y=200)]]
+    for ps in cases:
+        with pytest.raises(pic.PicError) as e:
+            pic.pic_init_batch(ps)
+        assert e.value.code == pic.PIC_EINVAL
+        assert pic.pic_last_error(None)
+    with pytest.raises(pic.PicError) as e:
+        pic.pic_init_batch([])
+    assert e.value.code == pic.PIC_EINVAL
+    with pytest.raises(pic.PicError) as e:
+        pic.pic_autotune_tiles([mixed], steps=0)
+    assert e.value.code == pic.PIC_EINVAL
+    assert pic.pic_batch_size(None) == 0
