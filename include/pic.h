@@ -113,6 +113,10 @@ typedef struct pic_moments_t {
     int64_t cfl_violations;  /* moves of one cell or more seen so far (should stay 0; handle-wide) */
     int64_t overflow_moves;  /* MIXED32: particles routed through the overflow path so far (handle-wide) */
     int64_t rebins;          /* MIXED32: full re-sorts performed so far */
+    int64_t cg_refinements;  /* MIXED32: FP64 residual refinements (outer PCG iterations) so far */
+    int64_t loop_iters;      /* handle-wide: CG iterations the PCG loop ran (in a batch, as many
+                                per step as its slowest simulation needed) */
+    int64_t loop_refinements;/* handle-wide, MIXED32: FP64 refinements the PCG loop ran */
 } pic_moments_t;
 
 typedef struct pic_sim pic_sim;

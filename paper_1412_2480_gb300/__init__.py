@@ -58,7 +58,9 @@ class pic_moments_t(C.Structure):
                 ("n_particles", C.c_int64 * 2), ("cg_iters_last", C.c_int32),
                 ("cg_iters_max", C.c_int32), ("cg_iters_total", C.c_int64),
                 ("cg_rel_resid", C.c_double), ("cfl_violations", C.c_int64),
-                ("overflow_moves", C.c_int64), ("rebins", C.c_int64)]
+                ("overflow_moves", C.c_int64), ("rebins", C.c_int64),
+                ("cg_refinements", C.c_int64), ("loop_iters", C.c_int64),
+                ("loop_refinements", C.c_int64)]
 
 
 class PicError(RuntimeError):

@@ -991,6 +991,9 @@ int pic_moments(pic_sim* s, pic_moments_t* m) {
     m->cfl_violations = (int64_t)hs.cfl_viol;
     m->overflow_moves = (int64_t)hs.overflow;
     if (s->mixed) m->rebins = mixed_rebins(s->mixed);
+    m->cg_refinements = c.total_outer;
+    m->loop_iters = (int64_t)hs.loop_iters[0];
+    m->loop_refinements = (int64_t)hs.loop_iters[1];
     // the largest-iteration counter restarts at every pic_moments call
     const int zero = 0;
     CK(cudaMemcpyAsync(&s->cg[s->sel].max_iters, &zero, sizeof zero, cudaMemcpyHostToDevice, s->stream));

@@ -93,7 +93,7 @@ __device__ bool reduce_and_finish(const GridDev& G, int g, double v[NV], double*
 // inner FP32 loop when INNER) and sets the loop's WHILE condition.
 template <bool INNER = false>
 __device__ void finish_all_grids(int ngrids, int n_participating, CgState* cg, DevStatus* st,
-                                 cudaGraphConditionalHandle cond, int use_cond) {
+                                 cudaGraphConditionalHandle cond, int use_cond, int count_slot = -1) {
     if (threadIdx.x != 0) return;
     __threadfence();
     const unsigned t = atomicAdd(&st->grids_done, 1u);
@@ -104,6 +104,7 @@ __device__ void finish_all_grids(int ngrids, int n_participating, CgState* cg, D
         n += (unsigned)(INNER ? __ldcg(&cg[g].in_active) : __ldcg(&cg[g].active));
     if (INNER) st->n_in_active = n;
     else st->n_active = n;
+    if (count_slot >= 0) st->loop_iters[count_slot] += 1ull;  // loop iterations the handle ran
     st->grids_done = 0u;
     if (use_cond) cudaGraphSetConditional(cond, n > 0u ? 1u : 0u);
 }
@@ -280,7 +281,7 @@ k_cg_update(const GridDev* __restrict__ grids, const int* __restrict__ blk_grid,
             st->stop_next = 1u;
         }
     }
-    finish_all_grids(ngrids, (int)n_part, cg, st, cond, use_cond);
+    finish_all_grids(ngrids, (int)n_part, cg, st, cond, use_cond, 0);
 }
 
 // ---- Field update, Eqs. (5)-(6) --------------------------------------------------
@@ -487,7 +488,7 @@ k_mp_update(const GridDev* __restrict__ grids, const int* __restrict__ blk_grid,
         if (sqrt(tot[0] / s.rr_in0) <= s.tol_in || s.in_iters >= kMaxInnerIters || s.iters >= G.maxit)
             s.in_active = 0;
     }
-    finish_all_grids<true>(ngrids, (int)n_part, cg, st, cond_in, use_cond);
+    finish_all_grids<true>(ngrids, (int)n_part, cg, st, cond_in, use_cond, 0);
 }
 
 // x += e (FP64).
@@ -533,6 +534,7 @@ k_mp_r(const GridDev* __restrict__ grids, const int* __restrict__ blk_grid, int 
         s.rr = tot[0];
         s.rel = sqrt(tot[0] / s.bb);
         s.outer += 1;
+        s.total_outer += 1;
         if (s.rel <= G.rtol) {
             s.active = 0;
         } else if (s.iters >= G.maxit || s.outer >= G.maxit) {
@@ -541,7 +543,7 @@ k_mp_r(const GridDev* __restrict__ grids, const int* __restrict__ blk_grid, int 
             st->stop_next = 1u;
         }
     }
-    finish_all_grids(ngrids, (int)n_part, cg, st, cond, use_cond);
+    finish_all_grids(ngrids, (int)n_part, cg, st, cond, use_cond, 1);
 }
 
 }  // namespace

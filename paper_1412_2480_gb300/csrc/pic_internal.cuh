@@ -55,6 +55,7 @@ struct CgState {
     double rr_in, rr_in0, alpha_in, beta_in, tol_in;
     double in_scale;  // r32 = r * in_scale (unit RMS), e = e32 / in_scale
     int in_active, in_iters, outer, pad;
+    long long total_outer;  // FP64 refinements (outer iterations) of all steps
 };
 
 // Device status words shared by all kernels of a handle.
@@ -72,6 +73,8 @@ struct DevStatus {
     unsigned long long lost;         // MIXED32: particles dropped because the overflow list was full
     unsigned int parity;             // MIXED32: which of the two bin buffers is current
     unsigned long long ovf_count[2]; // MIXED32: particles in each overflow list
+    unsigned long long loop_iters[2]; // PCG loop iterations run: [0] CG (inner) iterations,
+                                      // [1] FP64 refinements (MIXED32 outer iterations)
 };
 
 // One contiguous range of FP64 particles of one species in one simulation.
