@@ -62,6 +62,8 @@ extern "C" {
 /* ---- initial guess of the PCG solve of Eq. (7) ---- */
 #define PIC_WS_ZERO 0 /* dB_0 = 0 */
 #define PIC_WS_PREV 1 /* dB_0 = the previous step's dB */
+#define PIC_WS_LEARNED 2 /* dB_0 from the learned network set by pic_set_cnn (PIC_MIXED32 only;
+                            nx*ny a multiple of 128) */
 
 /* ---- flags ---- */
 #define PIC_NO_DEPOSIT 1   /* test-particle mode: particles feel the fields, J = 0 */
@@ -80,6 +82,9 @@ extern "C" {
 #define PIC_DBX 9 /* dB of the last step's solve (x, y, z) */
 #define PIC_DBY 10
 #define PIC_DBZ 11
+#define PIC_RHSX 12 /* right-hand side b of Eq. (7) of the last step (PIC_MIXED32 only) */
+#define PIC_RHSY 13
+#define PIC_RHSZ 14
 
 typedef struct pic_params {
     int32_t nx, ny;        /* cells (Sec. 3: 128 x 128; Sec. 4: 5650 x 990); >= 8 each */
@@ -93,7 +98,7 @@ typedef struct pic_params {
     int32_t precision;     /* PIC_FP64 or PIC_MIXED32 */
     double cg_rtol;        /* stop when ||r||_2 <= cg_rtol ||b||_2, default 1e-10 */
     int32_t cg_max_iter;   /* default 200 */
-    int32_t warm_start;    /* PIC_WS_ZERO or PIC_WS_PREV */
+    int32_t warm_start;    /* PIC_WS_ZERO, PIC_WS_PREV or PIC_WS_LEARNED */
     int32_t flags;         /* PIC_NO_DEPOSIT | PIC_NO_GRAPH */
     int32_t tile_x, tile_y;/* MIXED32 tile size in cells; 0 = chosen by the library */
     double bin_slack;      /* MIXED32 bin capacity factor over ppc * tile cells; 0 = 1.5 */
@@ -190,7 +195,8 @@ PIC_API int pic_set_fields(pic_sim* s, int32_t which, const double* data, size_t
  * stream has finished (one host synchronisation per call, not per step). Errors
  * detected on the device (PIC_ECG_NOCONV, PIC_ECFL, PIC_ENAN) stop the remaining
  * steps of the call; the fields and particles then hold the state after the failing
- * step and pic_moments reports its step count. */
+ * step and pic_moments reports its step count. PIC_ESTATE if warm_start is
+ * PIC_WS_LEARNED and no network has been set with pic_set_cnn. */
 PIC_API int pic_step(pic_sim* s, int32_t n);
 
 /* Advance n >= 1 steps like pic_step, timing each with CUDA events recorded on the
@@ -203,7 +209,7 @@ PIC_API int pic_step(pic_sim* s, int32_t n);
  * Device-detected errors are reported as by pic_step. */
 PIC_API int pic_profile(pic_sim* s, int32_t n, double* out, int32_t n_out);
 
-/* Copy grid quantity `which` (PIC_EX..PIC_DBZ) into out (len >= nx*ny FP64 values,
+/* Copy grid quantity `which` (PIC_EX..PIC_RHSZ) into out (len >= nx*ny FP64 values,
  * host or device, caller-owned). */
 PIC_API int pic_fields(pic_sim* s, int32_t which, double* out, size_t len);
 
@@ -260,6 +266,55 @@ PIC_API int pic_field_solve_noalloc(int32_t nx, int32_t ny, double dx, double dy
                                     const double* F, const double* J, double* dB,
                                     int32_t* iters, double* rel_resid, void* stream,
                                     char* errbuf, size_t errlen);
+
+/* ---- learned warm start --------------------------------------------------------------
+ * The paper solves Eq. (7) by PCG from a plain initial guess; this library can start it
+ * from a guess made by a small convolutional network instead (PIC_WS_LEARNED). The CG
+ * still iterates to the same tolerance cg_rtol, so the solution is the plain solver's;
+ * the network only changes how many iterations that takes.
+ *
+ * Network: four 3x3 convolutions with periodic padding and biases, 3 -> 32 -> 32 ->
+ * 32 -> 3 channels, no activation (the map b -> dB = A^{-1} b it approximates is
+ * linear). Its input is b / rms(b) with the three components of b as channels on the
+ * cell grid (rms over the 3 nx ny values), its output dB_0 / rms(b). Convolutions run
+ * on the tensor cores with BF16 operands and FP32 accumulation: the input, the weights
+ * and every hidden activation and back-propagated gradient are rounded to BF16 (to
+ * nearest even); the output and loss are FP32.
+ *
+ * Parameters (PIC_CNN_NPARAMS FP32 values), layer by layer (cin, cout) = (3, 32),
+ * (32, 32), (32, 32), (32, 3): W[cout][tap][cin] with tap = 3 (dy + 1) + (dx + 1) for
+ * the neighbour at (i + dx, j + dy), then b[cout].
+ *
+ * Image arrays (in, out, target) hold nimg images of [3][ny][nx] FP32 values, host or
+ * device; nx*ny must be a multiple of 128. Every call synchronises the network's own
+ * stream. Errors: PIC_EINVAL (sizes, NULL arrays), PIC_ENOMEM, PIC_ECUDA (including a
+ * tensor-core completion wait that timed out); pic_cnn_last_error gives the message. */
+typedef struct pic_cnn pic_cnn;
+#define PIC_CNN_NPARAMS 20259
+PIC_API int pic_cnn_create(pic_cnn** out); /* all parameters zero */
+PIC_API void pic_cnn_free(pic_cnn* c);
+PIC_API const char* pic_cnn_last_error(const pic_cnn* c); /* c == NULL: last create failure */
+PIC_API int pic_cnn_set_params(pic_cnn* c, const float* p, int64_t n); /* resets Adam state */
+PIC_API int pic_cnn_get_params(pic_cnn* c, float* p, int64_t n);
+/* out = network(in). */
+PIC_API int pic_cnn_forward(pic_cnn* c, int32_t nimg, int32_t nx, int32_t ny, const float* in, float* out);
+/* Gradient of the loss L = mean over images, channels and pixels of (network(in) -
+ * target)^2 with respect to the parameters (grad: PIC_CNN_NPARAMS values, layout as
+ * above), and L itself (loss may be NULL). */
+PIC_API int pic_cnn_gradient(pic_cnn* c, int32_t nimg, int32_t nx, int32_t ny, const float* in,
+                             const float* target, float* grad, double* loss);
+/* One Adam step (beta1 0.9, beta2 0.999, eps 1e-8, learning rate lr) on that loss. */
+PIC_API int pic_cnn_train_step(pic_cnn* c, int32_t nimg, int32_t nx, int32_t ny, const float* in,
+                               const float* target, float lr, double* loss);
+/* Copy the network's current parameters into the handle for PIC_WS_LEARNED (every
+ * simulation of the handle needs nx*ny a multiple of 128). Later training of c does
+ * not affect the handle until the next pic_set_cnn. */
+PIC_API int pic_set_cnn(pic_sim* s, const pic_cnn* c);
+/* The tensor-core building block: D = A B^T with A [M x K], B [N x K] row-major BF16
+ * bit patterns and D [M x N] FP32 (host or device; M a multiple of 128, N and K
+ * multiples of 16 in [16, 256]). Errors are reported through pic_cnn_last_error(NULL). */
+PIC_API int pic_tc_gemm_bf16(int32_t M, int32_t N, int32_t K, const uint16_t* A, const uint16_t* B,
+                             float* D);
 
 /* Message of the last failure on this handle (or of the last failed pic_init when s
  * is NULL). The string stays valid until the next call on the handle. */

@@ -32,15 +32,21 @@ PIC_FP64 = 0
 PIC_MIXED32 = 1
 PIC_WS_ZERO = 0
 PIC_WS_PREV = 1
+PIC_WS_LEARNED = 2
+PIC_CNN_NPARAMS = 20259
 PIC_NO_DEPOSIT = 1
 PIC_NO_GRAPH = 2
 PIC_EX, PIC_EY, PIC_EZ, PIC_BX, PIC_BY, PIC_BZ = range(6)
 PIC_JX, PIC_JY, PIC_JZ, PIC_DBX, PIC_DBY, PIC_DBZ = range(6, 12)
+PIC_RHSX, PIC_RHSY, PIC_RHSZ = range(12, 15)
 
 EXPORTED = ("pic_params_default", "pic_init", "pic_init_batch", "pic_select", "pic_batch_size",
             "pic_autotune_tiles", "pic_set_stream", "pic_load_particles", "pic_set_fields",
             "pic_step", "pic_profile", "pic_fields", "pic_moments", "pic_particle_count",
-            "pic_particles", "pic_field_solve_noalloc", "pic_last_error", "pic_free")
+            "pic_particles", "pic_field_solve_noalloc", "pic_last_error", "pic_free",
+            "pic_cnn_create", "pic_cnn_free", "pic_cnn_last_error", "pic_cnn_set_params",
+            "pic_cnn_get_params", "pic_cnn_forward", "pic_cnn_gradient", "pic_cnn_train_step",
+            "pic_set_cnn", "pic_tc_gemm_bf16")
 
 
 class pic_params(C.Structure):
@@ -105,6 +111,23 @@ def lib():
             L.pic_last_error.restype = C.c_char_p
             L.pic_free.argtypes = [vp]
             L.pic_free.restype = None
+            L.pic_cnn_create.argtypes = [C.POINTER(vp)]
+            L.pic_cnn_free.argtypes = [vp]
+            L.pic_cnn_free.restype = None
+            L.pic_cnn_last_error.argtypes = [vp]
+            L.pic_cnn_last_error.restype = C.c_char_p
+            L.pic_cnn_set_params.argtypes = [vp, vp, C.c_int64]
+            L.pic_cnn_get_params.argtypes = [vp, vp, C.c_int64]
+            L.pic_cnn_forward.argtypes = [vp, C.c_int32, C.c_int32, C.c_int32, vp, vp]
+            L.pic_cnn_gradient.argtypes = [vp, C.c_int32, C.c_int32, C.c_int32, vp, vp, vp,
+                                           C.POINTER(C.c_double)]
+            L.pic_cnn_train_step.argtypes = [vp, C.c_int32, C.c_int32, C.c_int32, vp, vp, C.c_float,
+                                             C.POINTER(C.c_double)]
+            L.pic_set_cnn.argtypes = [vp, vp]
+            L.pic_tc_gemm_bf16.argtypes = [C.c_int32, C.c_int32, C.c_int32, vp, vp, vp]
+            for name in ("pic_cnn_create", "pic_cnn_set_params", "pic_cnn_get_params", "pic_cnn_forward",
+                         "pic_cnn_gradient", "pic_cnn_train_step", "pic_set_cnn", "pic_tc_gemm_bf16"):
+                getattr(L, name).restype = C.c_int
             for name in ("pic_init", "pic_init_batch", "pic_select", "pic_batch_size",
                          "pic_autotune_tiles", "pic_set_stream", "pic_load_particles", "pic_set_fields",
                          "pic_step", "pic_profile", "pic_fields", "pic_moments", "pic_particles"):
@@ -291,6 +314,101 @@ def pic_field_solve_noalloc(nx, ny, dx, dy, cfl, theta, cg_rtol, cg_max_iter, F,
     if rc != PIC_OK:
         raise PicError(rc, msg.value.decode())
     return it.value, rr.value
+
+
+# ---- learned warm start (include/pic.h) -----------------------------------------------
+
+def _fptr(a, dtype, writable=False):
+    """Address of a C-contiguous numpy array or torch tensor of the given dtype."""
+    if hasattr(a, "data_ptr"):
+        import torch
+        want = {np.float32: torch.float32, np.uint16: torch.int16}[dtype]
+        if a.dtype not in (want, torch.bfloat16 if dtype is np.uint16 else want) or not a.is_contiguous():
+            raise TypeError(f"tensor must be contiguous {want}")
+        return a.data_ptr()
+    if not isinstance(a, np.ndarray) or a.dtype != dtype or not a.flags.c_contiguous:
+        raise TypeError(f"array must be a C-contiguous {np.dtype(dtype).name} numpy array")
+    if writable and not a.flags.writeable:
+        raise TypeError("output array is read-only")
+    return a.ctypes.data
+
+
+def _ccheck(rc, c):
+    if rc != PIC_OK:
+        msg = lib().pic_cnn_last_error(c)
+        raise PicError(rc, msg.decode() if msg else "")
+    return rc
+
+
+def pic_cnn_create() -> int:
+    c = C.c_void_p()
+    _ccheck(lib().pic_cnn_create(C.byref(c)), None)
+    return c.value
+
+
+def pic_cnn_free(c) -> None:
+    lib().pic_cnn_free(c)
+
+
+def pic_cnn_set_params(c, p) -> None:
+    _ccheck(lib().pic_cnn_set_params(c, _fptr(p, np.float32), _len(p)), c)
+
+
+def pic_cnn_get_params(c, out=None):
+    if out is None:
+        out = np.empty(PIC_CNN_NPARAMS, dtype=np.float32)
+    _ccheck(lib().pic_cnn_get_params(c, _fptr(out, np.float32, True), _len(out)), c)
+    return out
+
+
+def _img_shape(a):
+    s = tuple(a.shape)
+    if len(s) != 4 or s[1] != 3:
+        raise ValueError("images must have shape (nimg, 3, ny, nx)")
+    return s[0], s[3], s[2]
+
+
+def pic_cnn_forward(c, inp, out=None):
+    """inp: (nimg, 3, ny, nx) float32 (numpy or torch); returns/fills out of the same shape."""
+    nimg, nx, ny = _img_shape(inp)
+    if out is None:
+        out = np.empty((nimg, 3, ny, nx), dtype=np.float32)
+    _ccheck(lib().pic_cnn_forward(c, nimg, nx, ny, _fptr(inp, np.float32), _fptr(out, np.float32, True)), c)
+    return out
+
+
+def pic_cnn_gradient(c, inp, target, grad=None):
+    """Returns (grad, loss) of the mean squared error."""
+    nimg, nx, ny = _img_shape(inp)
+    if grad is None:
+        grad = np.empty(PIC_CNN_NPARAMS, dtype=np.float32)
+    loss = C.c_double(0.0)
+    _ccheck(lib().pic_cnn_gradient(c, nimg, nx, ny, _fptr(inp, np.float32), _fptr(target, np.float32),
+                                   _fptr(grad, np.float32, True), C.byref(loss)), c)
+    return grad, loss.value
+
+
+def pic_cnn_train_step(c, inp, target, lr=1e-3) -> float:
+    nimg, nx, ny = _img_shape(inp)
+    loss = C.c_double(0.0)
+    _ccheck(lib().pic_cnn_train_step(c, nimg, nx, ny, _fptr(inp, np.float32), _fptr(target, np.float32),
+                                     C.c_float(lr), C.byref(loss)), c)
+    return loss.value
+
+
+def pic_set_cnn(h, c) -> None:
+    _check(lib().pic_set_cnn(h, c), h)
+
+
+def pic_tc_gemm_bf16(A, B, D=None):
+    """D = A B^T on the tensor cores; A (M, K) and B (N, K) uint16 BF16 bit patterns."""
+    M, K = A.shape
+    N = B.shape[0]
+    if D is None:
+        D = np.empty((M, N), dtype=np.float32)
+    _ccheck(lib().pic_tc_gemm_bf16(M, N, K, _fptr(A, np.uint16), _fptr(B, np.uint16),
+                                   _fptr(D, np.float32, True)), None)
+    return D
 
 
 # ---- conveniences built only from the calls above ----------------------------------

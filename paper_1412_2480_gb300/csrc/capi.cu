@@ -16,6 +16,7 @@
 #include <string>
 #include <vector>
 
+#include "cnn.h"
 #include "engine.h"
 #include "mixed.h"
 #include "pic.h"
@@ -70,10 +71,15 @@ struct pic_sim {
     // MIXED32 mixed-precision PCG: FP64 right-hand side and FP32 inner vectors
     double* bvec = nullptr;
     float *r32 = nullptr, *p32 = nullptr, *q32 = nullptr, *e32 = nullptr;
+    // learned warm start: the network's forward weights and its buffers
+    bool learned = false;
+    bool has_cnn = false;
+    CnnWeights cnnw;
+    CnnWork cnnk;
     // bookkeeping
     long long steps = 0;
     unsigned long long seen_cfl = 0, seen_nan = 0, seen_lost = 0;
-    unsigned int seen_noconv = 0;
+    unsigned int seen_noconv = 0, seen_tc = 0;
 };
 
 namespace {
@@ -128,8 +134,12 @@ int validate(const pic_params* p, std::string& why) {
         return bad("precision must be PIC_FP64 or PIC_MIXED32");
     if (!(p->cg_rtol > 0) || p->cg_rtol >= 1) return bad("cg_rtol must lie in (0, 1)");
     if (p->cg_max_iter < 1 || p->cg_max_iter > 100000) return bad("cg_max_iter must lie in [1, 1e5]");
-    if (p->warm_start != PIC_WS_ZERO && p->warm_start != PIC_WS_PREV)
-        return bad("warm_start must be PIC_WS_ZERO or PIC_WS_PREV");
+    if (p->warm_start != PIC_WS_ZERO && p->warm_start != PIC_WS_PREV && p->warm_start != PIC_WS_LEARNED)
+        return bad("warm_start must be PIC_WS_ZERO, PIC_WS_PREV or PIC_WS_LEARNED");
+    if (p->warm_start == PIC_WS_LEARNED && p->precision != PIC_MIXED32)
+        return bad("PIC_WS_LEARNED requires PIC_MIXED32");
+    if (p->warm_start == PIC_WS_LEARNED && ((long long)p->nx * p->ny) % 128)
+        return bad("PIC_WS_LEARNED requires nx*ny to be a multiple of 128");
     if (p->tile_x < 0 || p->tile_y < 0) return bad("tile sizes must be >= 0");
     const int tx = std::min(p->tile_x > 0 ? p->tile_x : 32, p->nx);
     const int ty = std::min(p->tile_y > 0 ? p->tile_y : 16, p->ny);
@@ -173,7 +183,7 @@ void fill_grid(const pic_params& p, GridDev& G) {
     G.jinv = 1.0 / G.jscale;
     G.rtol = p.cg_rtol;
     G.maxit = p.cg_max_iter;
-    G.warm = p.warm_start == PIC_WS_PREV ? 1 : 0;
+    G.warm = p.warm_start == PIC_WS_PREV ? 1 : (p.warm_start == PIC_WS_LEARNED ? 2 : 0);
     G.deposit = (p.flags & PIC_NO_DEPOSIT) ? 0 : 1;
 }
 
@@ -337,6 +347,10 @@ int capture(pic_sim* s, int mask, cudaGraph_t* gout, cudaGraphExec_t* xout) {
         cudaGraphConditionalHandle h{};
         e = new_handle(st, &h);
         if (e == cudaSuccess) launch_rhs(field_args(s, 1, h), st);
+        if (e == cudaSuccess && s->learned) {
+            launch_learned_guess(s->cnnw, s->cnnk, s->dgrids, s->cg, s->ntot, s->bvec, s->x, &s->st->tc_timeout, st);
+            launch_guess_residual(field_args(s, 1, h), st);
+        }
         if (e == cudaSuccess && s->prm.precision == PIC_FP64) {
             e = add_while(st, h, s->body_stream,
                           [&](cudaStream_t bs) { launch_cg_iteration(field_args(s, 1, h), bs); return cudaSuccess; });
@@ -392,6 +406,10 @@ int run_step_direct(pic_sim* s) {
     enqueue_part(s, kPartPost, st);
     const FieldArgs a = field_args(s, 0, 0);
     launch_rhs(a, st);
+    if (s->learned) {
+        launch_learned_guess(s->cnnw, s->cnnk, s->dgrids, s->cg, s->ntot, s->bvec, s->x, &s->st->tc_timeout, st);
+        launch_guess_residual(a, st);
+    }
     unsigned int nact = 0, nin = 0;
     CK(cudaMemcpyAsync(&nact, &s->st->n_active, sizeof nact, cudaMemcpyDeviceToHost, st));
     CK(cudaStreamSynchronize(st));
@@ -463,7 +481,9 @@ __global__ void k_fix_to_f64(long long n, const long long* a, double jinv, doubl
 // Map device status counters that changed since the last check to a return code.
 int device_errors(pic_sim* s, const DevStatus& hs) {
     int rc = PIC_OK;
-    if (hs.cg_noconv != s->seen_noconv) {
+    if (hs.tc_timeout != s->seen_tc) {
+        rc = fail(s, PIC_ECUDA, "a tensor-core completion wait of the learned guess timed out");
+    } else if (hs.cg_noconv != s->seen_noconv) {
         rc = fail(s, PIC_ECG_NOCONV, "PCG reached cg_max_iter before cg_rtol");
     } else if (hs.nan_count != s->seen_nan) {
         rc = fail(s, PIC_ENAN, "non-finite particle momentum or position");
@@ -476,6 +496,7 @@ int device_errors(pic_sim* s, const DevStatus& hs) {
     s->seen_nan = hs.nan_count;
     s->seen_cfl = hs.cfl_viol;
     s->seen_lost = hs.lost;
+    s->seen_tc = hs.tc_timeout;
     return rc;
 }
 
@@ -503,6 +524,7 @@ int init_handle(const pic_params* prm, int n, pic_sim** out) {
     if (!s) return fail(nullptr, PIC_ENOMEM, "host allocation failed");
     s->prm = prm[0];
     s->prms.assign(prm, prm + n);
+    s->learned = prm[0].warm_start == PIC_WS_LEARNED;
     if (cudaGetDevice(&s->device) != cudaSuccess) {
         delete s;
         return fail(nullptr, PIC_ECUDA, "no CUDA device");
@@ -698,6 +720,9 @@ int pic_init_batch(const pic_params* prm, int32_t n, pic_sim** out) {
         for (int k = 1; k < n; k++)
             if ((prm[k].flags & PIC_NO_GRAPH) != (prm[0].flags & PIC_NO_GRAPH))
                 return fail(nullptr, PIC_EINVAL, "PIC_NO_GRAPH must be the same for every simulation");
+        for (int k = 1; k < n; k++)
+            if ((prm[k].warm_start == PIC_WS_LEARNED) != (prm[0].warm_start == PIC_WS_LEARNED))
+                return fail(nullptr, PIC_EINVAL, "PIC_WS_LEARNED must be used by all simulations or none");
     }
     return init_handle(prm, n, out);
 }
@@ -762,6 +787,23 @@ int pic_autotune_tiles(pic_params* prm, int32_t n, int32_t steps, double* best_m
         }
         if (best_ms) best_ms[P - 1] = best;
     }
+    return PIC_OK;
+}
+
+int pic_set_cnn(pic_sim* s, const pic_cnn* net) {
+    if (!s) return PIC_EINVAL;
+    cudaSetDevice(s->device);
+    if (!net) return fail(s, PIC_EINVAL, "network is NULL");
+    if (s->prm.precision != PIC_MIXED32) return fail(s, PIC_EINVAL, "the learned warm start needs PIC_MIXED32");
+    CK(cudaStreamSynchronize(s->stream));
+    drop_graph(s);
+    if (!s->cnnk.npix) {
+        int rc = cnn_alloc_work(&s->cnnk, s->hgrids.data(), s->ngrids, s->ntot, s->err);
+        if (rc) return rc;
+    }
+    int rc = cnn_copy_weights(net, &s->cnnw, s->err);
+    if (rc) return rc;
+    s->has_cnn = true;
     return PIC_OK;
 }
 
@@ -858,6 +900,7 @@ int pic_step(pic_sim* s, int32_t n) {
     cudaSetDevice(s->device);
     if (n < 0) return fail(s, PIC_EINVAL, "n must be >= 0");
     if (n == 0) return PIC_OK;
+    if (s->learned && !s->has_cnn) return fail(s, PIC_ESTATE, "PIC_WS_LEARNED needs a network (pic_set_cnn)");
     // a new call starts clean: errors stop the rest of the call that raised them only
     DevStatus hs{};
     CK(cudaMemcpyAsync(&hs, s->st, sizeof hs, cudaMemcpyDeviceToHost, s->stream));
@@ -894,6 +937,7 @@ int pic_profile(pic_sim* s, int32_t n, double* out, int32_t n_out) {
     if (!s) return PIC_EINVAL;
     cudaSetDevice(s->device);
     if (n < 1 || !out || n_out < 1) return fail(s, PIC_EINVAL, "need n >= 1 and an output array");
+    if (s->learned && !s->has_cnn) return fail(s, PIC_ESTATE, "PIC_WS_LEARNED needs a network (pic_set_cnn)");
     for (int k = 0; k < 6; k++)
         if (!s->ev[k]) CK(cudaEventCreate(&s->ev[k]));
     if (s->prm.precision == PIC_MIXED32) {
@@ -942,7 +986,8 @@ int pic_profile(pic_sim* s, int32_t n, double* out, int32_t n_out) {
 int pic_fields(pic_sim* s, int32_t which, double* out, size_t len) {
     if (!s) return PIC_EINVAL;
     cudaSetDevice(s->device);
-    if (which < PIC_EX || which > PIC_DBZ) return fail(s, PIC_EINVAL, "which must be PIC_EX..PIC_DBZ");
+    if (which < PIC_EX || which > PIC_RHSZ) return fail(s, PIC_EINVAL, "which must be PIC_EX..PIC_RHSZ");
+    if (which >= PIC_RHSX && !s->bvec) return fail(s, PIC_ESTATE, "the right-hand side is kept in PIC_MIXED32 only");
     const GridDev& G = s->hgrids[s->sel];
     const long long nc = G.ncell, off = G.cell_off;
     if (!out || len < (size_t)nc) return fail(s, PIC_EINVAL, "out must hold nx*ny values");
@@ -958,8 +1003,10 @@ int pic_fields(pic_sim* s, int32_t which, double* out, size_t len) {
                 nc, s->Jfix + c * s->ntot + off, G.jinv, s->tmp);
             src = s->tmp;
         }
-    } else {
+    } else if (which <= PIC_DBZ) {
         src = s->x + (which - PIC_DBX) * s->ntot + off;
+    } else {
+        src = s->bvec + (which - PIC_RHSX) * s->ntot + off;
     }
     CK(cudaMemcpyAsync(out, src, nc * sizeof(double), cudaMemcpyDefault, s->stream));
     return finish_call(s);
@@ -1042,6 +1089,8 @@ void pic_free(pic_sim* s) {
     if (s->stream) cudaStreamSynchronize(s->stream);
     drop_graph(s);
     if (s->mixed) mixed_destroy(s->mixed);
+    cnn_free_weights(&s->cnnw);
+    cnn_free_work(&s->cnnk);
     void* ptrs[] = {s->dgrids, s->dblk_grid, s->F, s->J64, s->Jfix, s->F32, s->x, s->r, s->p, s->q,
                     s->part, s->cg, s->done, s->st, s->tmp, s->dsegs, s->dblk_seg[0], s->dblk_seg[1],
                     s->bvec, s->r32, s->p32, s->q32, s->e32};

@@ -41,6 +41,8 @@ void launch_step_begin(const FieldArgs& a, cudaStream_t s);
 void launch_step_end(const FieldArgs& a, cudaStream_t s);
 // b of Eq. (7), initial residual, energies at time level n.
 void launch_rhs(const FieldArgs& a, cudaStream_t s);
+// r = b - A x for an initial guess x written after launch_rhs (the learned guess).
+void launch_guess_residual(const FieldArgs& a, cudaStream_t s);
 // One PCG iteration: A-product and direction update, then solution/residual update.
 void launch_cg_iteration(const FieldArgs& a, cudaStream_t s);
 // E, B from Eqs. (5)-(6) with dB; FP32 copies when a.F32 is set.

@@ -154,7 +154,7 @@ k_rhs(const GridDev* __restrict__ grids, const int* __restrict__ blk_grid, int n
             const double b = th_dt2 * (lap + 4.0 * kPi * cJ[a]) - G.dt * cE[a];
             double res = b;
             const long long o = a * ntot;
-            if (G.warm) {
+            if (G.warm == 1) {  // previous step's dB as the initial guess
                 const double* X = x + o;
                 const double Ax = G.c0 * X[c.k] - G.cx * (X[c.ke] + X[c.kw]) -
                                   G.cy * (X[c.kn] + X[c.ks]);
@@ -193,7 +193,7 @@ k_zero_x(const GridDev* __restrict__ grids, const int* __restrict__ blk_grid, lo
          double* __restrict__ x) {
     const int g = blk_grid[blockIdx.x];
     const GridDev& G = grids[g];
-    if (G.warm) return;
+    if (G.warm == 1) return;
     FOR_CELLS(G, g, c) {
         x[c.k] = 0.0;
         x[ntot + c.k] = 0.0;
@@ -546,7 +546,44 @@ k_mp_r(const GridDev* __restrict__ grids, const int* __restrict__ blk_grid, int 
     finish_all_grids(ngrids, (int)n_part, cg, st, cond, use_cond, 1);
 }
 
+// After a learned initial guess x0 (every simulation): r = b - A x0 (FP64) and the
+// starting state of the PCG loop, as k_rhs sets it for the plain guesses.
+__global__ void __launch_bounds__(kFieldThreads)
+k_guess_residual(const GridDev* __restrict__ grids, const int* __restrict__ blk_grid, int ngrids,
+                 int nblk_total, long long ntot, const double* __restrict__ b, const double* __restrict__ x,
+                 double* __restrict__ r, CgState* cg, double* part, unsigned int* done, DevStatus* st,
+                 cudaGraphConditionalHandle cond, int use_cond) {
+    const int g = blk_grid[blockIdx.x];
+    const GridDev& G = grids[g];
+    double v[1] = {0.0};
+    if (!st->stop) FOR_CELLS(G, g, c) {
+#pragma unroll
+        for (int a = 0; a < 3; a++) {
+            const long long o = a * ntot;
+            const double* X = x + o;
+            const double Ax = G.c0 * X[c.k] - G.cx * (X[c.ke] + X[c.kw]) - G.cy * (X[c.kn] + X[c.ks]);
+            const double rn = b[o + c.k] - Ax;
+            r[o + c.k] = rn;
+            v[0] += rn * rn;
+        }
+    }
+    double tot[1];
+    if (!reduce_and_finish<1>(G, g, v, part, nblk_total, done, tot)) return;
+    if (threadIdx.x == 0) {
+        CgState& s = cg[g];
+        s.rr = tot[0];
+        s.rel = s.bb > 0.0 ? sqrt(tot[0] / s.bb) : 0.0;
+        s.active = (!st->stop && s.bb > 0.0 && s.rel > G.rtol) ? 1 : 0;
+    }
+    finish_all_grids(ngrids, ngrids, cg, st, cond, use_cond);
+}
+
 }  // namespace
+
+void launch_guess_residual(const FieldArgs& a, cudaStream_t s) {
+    k_guess_residual<<<a.nblk, kFieldThreads, 0, s>>>(a.grids, a.blk_grid, a.ngrids, a.nblk, a.ntot, a.b, a.x,
+                                                      a.r, a.cg, a.part, a.done, a.st, a.cond, a.use_cond);
+}
 
 void launch_step_begin(const FieldArgs& a, cudaStream_t s) {
     k_step_begin<<<1, 128, 0, s>>>(a.ngrids, a.cg, a.st);

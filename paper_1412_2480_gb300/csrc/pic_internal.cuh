@@ -30,7 +30,7 @@ struct GridDev {
     double qw[2], qm[2];  // charge per macro-particle and charge-to-mass sign per species
     double w;             // macro weight (mass per macro-particle)
     double rtol;
-    int maxit, warm;
+    int maxit, warm;      // warm: 0 zero guess, 1 previous dB, 2 learned guess
     int deposit;          // 0 in test-particle mode
     // MIXED32 tiling
     int tx, ty, ntx, nty; // tile size and tile counts
@@ -75,6 +75,7 @@ struct DevStatus {
     unsigned long long ovf_count[2]; // MIXED32: particles in each overflow list
     unsigned long long loop_iters[2]; // PCG loop iterations run: [0] CG (inner) iterations,
                                       // [1] FP64 refinements (MIXED32 outer iterations)
+    unsigned int tc_timeout;          // a tensor-core completion wait ran out (learned guess)
 };
 
 // One contiguous range of FP64 particles of one species in one simulation.

@@ -1,0 +1,206 @@
+"""Learned warm start on the tensor cores, through the C ABI.
+
+- the tcgen05 GEMM building block against numpy on the same BF16 values;
+- network forward and gradient against the FP64 reference (oracle/cnn.py) that rounds
+  to BF16 at the same points. What remains is FP32 accumulation order, which can move a
+  value across a BF16 rounding boundary (one BF16 step, 2^-8 relative) in isolated
+  elements: the bounds below allow for that and for nothing larger;
+- GPU training learns A^{-1} on spectral-solve pairs;
+- in a PIC run, the learned guess lowers the PCG iteration count while the solve still
+  reaches the same tolerance."""
+import math
+
+import numpy as np
+import pytest
+
+import paper_1412_2480_gb300 as pic
+from closed_forms import spectral_solve
+from oracle import cnn
+from runners import workload
+
+pytestmark = pytest.mark.gpu
+
+
+def to_bf16_bits(x):
+    f = np.asarray(x, dtype=np.float32)
+    u = f.view(np.uint32).astype(np.uint64)
+    return (((u + 0x7FFF + ((u >> 16) & 1)) >> 16) & 0xFFFF).astype(np.uint16)
+
+
+def from_bf16_bits(b):
+    return (b.astype(np.uint32) << 16).view(np.float32).astype(np.float64)
+
+
+def rand_params(rng, scale=1.0):
+    p = np.zeros(cnn.NPARAMS)
+    for (ci, co), (wo, bo) in zip(cnn.LAYERS, cnn.offsets()):
+        p[wo:bo] = rng.standard_normal(co * 9 * ci) * scale / math.sqrt(9 * ci)
+        p[bo:bo + co] = rng.standard_normal(co) * 0.05
+    return p
+
+
+def relnorm(a, b):
+    return float(np.linalg.norm(np.ravel(a) - np.ravel(b)) / max(np.linalg.norm(np.ravel(b)), 1e-300))
+
+
+@pytest.mark.parametrize("M,N,K", [(128, 16, 16), (128, 32, 288 // 2 + 16), (256, 256, 256), (384, 48, 64)])
+def test_tc_gemm_matches_numpy(M, N, K):
+    rng = np.random.default_rng(M + N + K)
+    A = to_bf16_bits(rng.standard_normal((M, K)))
+    B = to_bf16_bits(rng.standard_normal((N, K)))
+    D = pic.pic_tc_gemm_bf16(A, B)
+    ref = from_bf16_bits(A) @ from_bf16_bits(B).T
+    scale = np.abs(from_bf16_bits(A)) @ np.abs(from_bf16_bits(B)).T
+    assert np.all(np.abs(D - ref) <= 2e-5 * scale + 1e-30)
+
+
+def network(params):
+    c = pic.pic_cnn_create()
+    pic.pic_cnn_set_params(c, np.asarray(params, dtype=np.float32))
+    return c
+
+
+def test_forward_matches_reference():
+    rng = np.random.default_rng(5)
+    p = rand_params(rng).astype(np.float32).astype(np.float64)
+    x = rng.standard_normal((2, 3, 16, 16)).astype(np.float32)
+    c = network(p)
+    try:
+        y = pic.pic_cnn_forward(c, x)
+    finally:
+        pic.pic_cnn_free(c)
+    yq = cnn.forward(p, x.astype(np.float64), quantize=True)
+    y64 = cnn.forward(p, x.astype(np.float64), quantize=False)
+    assert relnorm(y, yq) < 2e-3
+    assert relnorm(y, y64) < 3e-2  # the BF16 rounding itself, for scale
+
+
+def test_gradient_matches_reference():
+    rng = np.random.default_rng(6)
+    p = rand_params(rng).astype(np.float32).astype(np.float64)
+    x = rng.standard_normal((2, 3, 16, 24)).astype(np.float32)
+    t = rng.standard_normal((2, 3, 16, 24)).astype(np.float32)
+    c = network(p)
+    try:
+        g, L = pic.pic_cnn_gradient(c, x, t)
+    finally:
+        pic.pic_cnn_free(c)
+    Lq, gq = cnn.loss_and_grad(p, x.astype(np.float64), t.astype(np.float64), quantize=True)
+    assert abs(L - Lq) < 2e-3 * Lq
+    for (ci, co), (wo, bo) in zip(cnn.LAYERS, cnn.offsets()):
+        assert relnorm(g[wo:bo], gq[wo:bo]) < 1e-2, (ci, co, "weights")
+        assert relnorm(g[bo:bo + co], gq[bo:bo + co]) < 1e-2, (ci, co, "biases")
+
+
+def spectral_pairs(rng, n, nx, ny, theta=0.5, dt=1.0):
+    """b with white and smooth parts; target A^{-1} b by FFT; both scaled by rms(b)."""
+    b = rng.standard_normal((n, 3, ny, nx))
+    kx = 2 * np.pi * np.fft.fftfreq(nx)
+    ky = 2 * np.pi * np.fft.fftfreq(ny)
+    KY, KX = np.meshgrid(ky, kx, indexing="ij")
+    smooth = np.real(np.fft.ifft2(np.fft.fft2(b) * np.exp(-4 * (KX ** 2 + KY ** 2))))
+    b = 0.3 * b + 5 * smooth
+    x = np.stack([spectral_solve(bi, nx, ny, theta, dt) for bi in b])
+    rms = np.sqrt(np.mean(b ** 2, axis=(1, 2, 3), keepdims=True))
+    return (b / rms).astype(np.float32), (x / rms).astype(np.float32)
+
+
+def apply_A(x, theta=0.5, dt=1.0):
+    a = (theta * dt) ** 2
+    lap = (np.roll(x, 1, -1) + np.roll(x, -1, -1) + np.roll(x, 1, -2) + np.roll(x, -1, -2) - 4 * x)
+    return x - a * lap
+
+
+def test_training_learns_the_inverse_operator():
+    rng = np.random.default_rng(7)
+    c = network(rand_params(rng, scale=0.5))
+    try:
+        losses = []
+        for it in range(600):
+            b, x = spectral_pairs(rng, 8, 32, 32)
+            losses.append(pic.pic_cnn_train_step(c, b, x, lr=2e-3))
+        b, x = spectral_pairs(rng, 4, 32, 32)
+        x0 = pic.pic_cnn_forward(c, b).astype(np.float64)
+    finally:
+        pic.pic_cnn_free(c)
+    assert np.mean(losses[-50:]) < 0.02 * np.mean(losses[:10])
+    r = b - apply_A(x0)
+    # the zero guess has residual 1; a guess of b / (1 + 4 a) about 0.44
+    assert np.linalg.norm(r) / np.linalg.norm(b) < 0.05
+
+
+def pic_pairs(nsteps, nx=64, ny=64):
+    """(b, dB) of every step of a config-1-shaped MIXED32 run, scaled by rms(b)."""
+    w, sp, F0 = workload(nx, ny, 8, gamma0=20.0, u_th=1e-3, seed=11, field_amp=1e-3)
+    prm = pic.pic_params_default(nx=nx, ny=ny, shape_order=1, gamma0=20.0, ppc=8,
+                                 precision=pic.PIC_MIXED32, cg_rtol=1e-10)
+    h = pic.pic_init(prm)
+    B, X = [], []
+    try:
+        for c in range(6):
+            pic.pic_set_fields(h, c, np.ascontiguousarray(F0[c]).ravel())
+        for s, d in enumerate(sp):
+            pic.pic_load_particles(h, s, d["x"], d["y"], d["ux"], d["uy"], d["uz"])
+        for _ in range(nsteps):
+            pic.pic_step(h, 1)
+            b = np.stack([pic.fields_numpy(h, pic.PIC_RHSX + k, nx, ny) for k in range(3)])
+            x = np.stack([pic.fields_numpy(h, pic.PIC_DBX + k, nx, ny) for k in range(3)])
+            rms = np.sqrt(np.mean(b ** 2))
+            if rms > 0:
+                B.append(b / rms)
+                X.append(x / rms)
+    finally:
+        pic.pic_free(h)
+    return np.array(B, dtype=np.float32), np.array(X, dtype=np.float32), (w, sp, F0)
+
+
+def run_warm(ws, net, inputs, steps, nx=64, ny=64):
+    w, sp, F0 = inputs
+    prm = pic.pic_params_default(nx=nx, ny=ny, shape_order=1, gamma0=20.0, ppc=8,
+                                 precision=pic.PIC_MIXED32, cg_rtol=1e-10, warm_start=ws)
+    h = pic.pic_init(prm)
+    try:
+        if net is not None:
+            pic.pic_set_cnn(h, net)
+        for c in range(6):
+            pic.pic_set_fields(h, c, np.ascontiguousarray(F0[c]).ravel())
+        for s, d in enumerate(sp):
+            pic.pic_load_particles(h, s, d["x"], d["y"], d["ux"], d["uy"], d["uz"])
+        iters = []
+        for _ in range(steps):
+            m0 = pic.pic_moments(h)["loop_iters"]
+            pic.pic_step(h, 1)
+            m = pic.pic_moments(h)
+            iters.append(m["loop_iters"] - m0)
+            assert m["cg_rel_resid"] <= 1e-10
+        F = np.stack([pic.fields_numpy(h, c, nx, ny) for c in range(6)])
+    finally:
+        pic.pic_free(h)
+    return np.array(iters), F
+
+
+def test_learned_warm_start_cuts_pcg_iterations_in_a_pic_run():
+    B, X, inputs = pic_pairs(160)
+    rng = np.random.default_rng(8)
+    c = network(rand_params(rng, scale=0.5))
+    try:
+        ntrain = len(B) - 16  # the last 16 pairs are held out
+        for it in range(3000):
+            k = rng.integers(0, ntrain, 8)
+            pic.pic_cnn_train_step(c, B[k], X[k], lr=2e-3 if it < 2000 else 3e-4)
+        x0 = pic.pic_cnn_forward(c, B[ntrain:]).astype(np.float64)
+        guess_resid = np.linalg.norm(B[ntrain:] - apply_A(x0)) / np.linalg.norm(B[ntrain:])
+        print(f"held-out relative residual of the learned guess: {guess_resid:.2e}")
+        assert guess_resid < 0.02
+        with pytest.raises(pic.PicError) as e:
+            run_warm(pic.PIC_WS_LEARNED, None, inputs, 1)
+        assert e.value.code == pic.PIC_ESTATE
+        it_learned, F_learned = run_warm(pic.PIC_WS_LEARNED, c, inputs, 40)
+    finally:
+        pic.pic_cnn_free(c)
+    it_zero, F_zero = run_warm(pic.PIC_WS_ZERO, None, inputs, 40)
+    print(f"PCG iterations over 40 steps: zero guess {it_zero.sum()}, learned {it_learned.sum()}; "
+          f"fields differ by {relnorm(F_learned, F_zero):.2e}")
+    # same solution to the solver tolerance, in fewer iterations
+    assert relnorm(F_learned, F_zero) < 1e-6
+    assert it_learned.sum() <= 0.85 * it_zero.sum(), (it_learned.sum(), it_zero.sum())
