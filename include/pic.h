@@ -62,12 +62,13 @@ extern "C" {
 /* ---- initial guess of the PCG solve of Eq. (7) ---- */
 #define PIC_WS_ZERO 0 /* dB_0 = 0 */
 #define PIC_WS_PREV 1 /* dB_0 = the previous step's dB */
-#define PIC_WS_LEARNED 2 /* dB_0 from the learned network set by pic_set_cnn (PIC_MIXED32 only;
-                            nx*ny a multiple of 128) */
+#define PIC_WS_LEARNED 2 /* dB_0 from the learned network set by pic_set_cnn (PIC_MIXED32 only) */
 
 /* ---- flags ---- */
 #define PIC_NO_DEPOSIT 1   /* test-particle mode: particles feel the fields, J = 0 */
 #define PIC_NO_GRAPH 2     /* launch kernels directly instead of a captured CUDA graph */
+#define PIC_NO_COOP 4      /* PIC_MIXED32: run the PCG loop as graph-driven kernel launches instead
+                              of one cooperative persistent kernel (same arithmetic) */
 
 /* ---- grid quantity ids for pic_fields / pic_set_fields ---- */
 #define PIC_EX 0
@@ -281,6 +282,12 @@ PIC_API int pic_field_solve_noalloc(int32_t nx, int32_t ny, double dx, double dy
  * and every hidden activation and back-propagated gradient are rounded to BF16 (to
  * nearest even); the output and loss are FP32.
  *
+ * In the solver (PIC_WS_LEARNED) the network is not run layer by layer: being linear,
+ * its four layers compose exactly into one 9x9 stencil from the 3 channels to the 3
+ * channels plus a bias, which pic_set_cnn computes in FP64 from the FP32 parameters and
+ * the step applies in FP32 to b (x0 = K * b + bias rms(b)): about 1.5 kFLOP per cell
+ * instead of 40 kFLOP, and no BF16 rounding. pic_cnn_stencil returns that stencil.
+ *
  * Parameters (PIC_CNN_NPARAMS FP32 values), layer by layer (cin, cout) = (3, 32),
  * (32, 32), (32, 32), (32, 3): W[cout][tap][cin] with tap = 3 (dy + 1) + (dx + 1) for
  * the neighbour at (i + dx, j + dy), then b[cout].
@@ -306,9 +313,14 @@ PIC_API int pic_cnn_gradient(pic_cnn* c, int32_t nimg, int32_t nx, int32_t ny, c
 /* One Adam step (beta1 0.9, beta2 0.999, eps 1e-8, learning rate lr) on that loss. */
 PIC_API int pic_cnn_train_step(pic_cnn* c, int32_t nimg, int32_t nx, int32_t ny, const float* in,
                                const float* target, float lr, double* loss);
-/* Copy the network's current parameters into the handle for PIC_WS_LEARNED (every
- * simulation of the handle needs nx*ny a multiple of 128). Later training of c does
- * not affect the handle until the next pic_set_cnn. */
+/* The collapsed stencil of the current parameters: PIC_CNN_STENCIL FP32 values,
+ * K[co][ci][dy + 4][dx + 4] for the neighbour (i + dx, j + dy), then bias[co] (host or
+ * device). */
+#define PIC_CNN_STENCIL 732
+PIC_API int pic_cnn_stencil(pic_cnn* c, float* out, int64_t n);
+/* Collapse the network's current parameters into the handle's learned guess for
+ * PIC_WS_LEARNED. Later training of c does not affect the handle until the next
+ * pic_set_cnn. */
 PIC_API int pic_set_cnn(pic_sim* s, const pic_cnn* c);
 /* The tensor-core building block: D = A B^T with A [M x K], B [N x K] row-major BF16
  * bit patterns and D [M x N] FP32 (host or device; M a multiple of 128, N and K

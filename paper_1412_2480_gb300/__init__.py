@@ -36,6 +36,7 @@ PIC_WS_LEARNED = 2
 PIC_CNN_NPARAMS = 20259
 PIC_NO_DEPOSIT = 1
 PIC_NO_GRAPH = 2
+PIC_NO_COOP = 4
 PIC_EX, PIC_EY, PIC_EZ, PIC_BX, PIC_BY, PIC_BZ = range(6)
 PIC_JX, PIC_JY, PIC_JZ, PIC_DBX, PIC_DBY, PIC_DBZ = range(6, 12)
 PIC_RHSX, PIC_RHSY, PIC_RHSZ = range(12, 15)
@@ -46,7 +47,7 @@ EXPORTED = ("pic_params_default", "pic_init", "pic_init_batch", "pic_select", "p
             "pic_particles", "pic_field_solve_noalloc", "pic_last_error", "pic_free",
             "pic_cnn_create", "pic_cnn_free", "pic_cnn_last_error", "pic_cnn_set_params",
             "pic_cnn_get_params", "pic_cnn_forward", "pic_cnn_gradient", "pic_cnn_train_step",
-            "pic_set_cnn", "pic_tc_gemm_bf16")
+            "pic_cnn_stencil", "pic_set_cnn", "pic_tc_gemm_bf16")
 
 
 class pic_params(C.Structure):
@@ -124,9 +125,11 @@ def lib():
             L.pic_cnn_train_step.argtypes = [vp, C.c_int32, C.c_int32, C.c_int32, vp, vp, C.c_float,
                                              C.POINTER(C.c_double)]
             L.pic_set_cnn.argtypes = [vp, vp]
+            L.pic_cnn_stencil.argtypes = [vp, vp, C.c_int64]
             L.pic_tc_gemm_bf16.argtypes = [C.c_int32, C.c_int32, C.c_int32, vp, vp, vp]
             for name in ("pic_cnn_create", "pic_cnn_set_params", "pic_cnn_get_params", "pic_cnn_forward",
-                         "pic_cnn_gradient", "pic_cnn_train_step", "pic_set_cnn", "pic_tc_gemm_bf16"):
+                         "pic_cnn_gradient", "pic_cnn_train_step", "pic_set_cnn", "pic_tc_gemm_bf16",
+                         "pic_cnn_stencil"):
                 getattr(L, name).restype = C.c_int
             for name in ("pic_init", "pic_init_batch", "pic_select", "pic_batch_size",
                          "pic_autotune_tiles", "pic_set_stream", "pic_load_particles", "pic_set_fields",
@@ -394,6 +397,16 @@ def pic_cnn_train_step(c, inp, target, lr=1e-3) -> float:
     _ccheck(lib().pic_cnn_train_step(c, nimg, nx, ny, _fptr(inp, np.float32), _fptr(target, np.float32),
                                      C.c_float(lr), C.byref(loss)), c)
     return loss.value
+
+
+PIC_CNN_STENCIL = 732
+
+
+def pic_cnn_stencil(c):
+    """The network collapsed into one stencil: (K [3, 3, 9, 9], bias [3]) as float32."""
+    out = np.empty(PIC_CNN_STENCIL, dtype=np.float32)
+    _ccheck(lib().pic_cnn_stencil(c, _fptr(out, np.float32, True), PIC_CNN_STENCIL), c)
+    return out[:729].reshape(3, 3, 9, 9), out[729:]
 
 
 def pic_set_cnn(h, c) -> None:

@@ -74,12 +74,14 @@ struct pic_sim {
     // learned warm start: the network's forward weights and its buffers
     bool learned = false;
     bool has_cnn = false;
-    CnnWeights cnnw;
-    CnnWork cnnk;
+    CnnGuess guess;
+    // MIXED32 solve as one cooperative kernel
+    bool use_coop = false;
+    CoopSolve coop;
     // bookkeeping
     long long steps = 0;
     unsigned long long seen_cfl = 0, seen_nan = 0, seen_lost = 0;
-    unsigned int seen_noconv = 0, seen_tc = 0;
+    unsigned int seen_noconv = 0, seen_sync = 0;
 };
 
 namespace {
@@ -138,8 +140,6 @@ int validate(const pic_params* p, std::string& why) {
         return bad("warm_start must be PIC_WS_ZERO, PIC_WS_PREV or PIC_WS_LEARNED");
     if (p->warm_start == PIC_WS_LEARNED && p->precision != PIC_MIXED32)
         return bad("PIC_WS_LEARNED requires PIC_MIXED32");
-    if (p->warm_start == PIC_WS_LEARNED && ((long long)p->nx * p->ny) % 128)
-        return bad("PIC_WS_LEARNED requires nx*ny to be a multiple of 128");
     if (p->tile_x < 0 || p->tile_y < 0) return bad("tile sizes must be >= 0");
     const int tx = std::min(p->tile_x > 0 ? p->tile_x : 32, p->nx);
     const int ty = std::min(p->tile_y > 0 ? p->tile_y : 16, p->ny);
@@ -344,11 +344,22 @@ int capture(pic_sim* s, int mask, cudaGraph_t* gout, cudaGraphExec_t* xout) {
             enqueue_part(s, part, st);
             continue;
         }
+        if (s->use_coop) {
+            // rhs -> (learned guess) -> one cooperative kernel for the whole PCG -> update
+            launch_rhs(field_args(s, 0, 0), st);
+            if (s->learned) {
+                launch_learned_guess(s->guess, s->dgrids, s->cg, s->ntot, s->bvec, s->x, st);
+                launch_guess_residual(field_args(s, 0, 0), st);
+            }
+            e = launch_mp_coop(s->coop, field_args(s, 0, 0), st);
+            if (e == cudaSuccess) launch_field_update(field_args(s, 0, 0), st);
+            continue;
+        }
         cudaGraphConditionalHandle h{};
         e = new_handle(st, &h);
         if (e == cudaSuccess) launch_rhs(field_args(s, 1, h), st);
         if (e == cudaSuccess && s->learned) {
-            launch_learned_guess(s->cnnw, s->cnnk, s->dgrids, s->cg, s->ntot, s->bvec, s->x, &s->st->tc_timeout, st);
+            launch_learned_guess(s->guess, s->dgrids, s->cg, s->ntot, s->bvec, s->x, st);
             launch_guess_residual(field_args(s, 1, h), st);
         }
         if (e == cudaSuccess && s->prm.precision == PIC_FP64) {
@@ -407,8 +418,15 @@ int run_step_direct(pic_sim* s) {
     const FieldArgs a = field_args(s, 0, 0);
     launch_rhs(a, st);
     if (s->learned) {
-        launch_learned_guess(s->cnnw, s->cnnk, s->dgrids, s->cg, s->ntot, s->bvec, s->x, &s->st->tc_timeout, st);
+        launch_learned_guess(s->guess, s->dgrids, s->cg, s->ntot, s->bvec, s->x, st);
         launch_guess_residual(a, st);
+    }
+    if (s->use_coop) {
+        CK(launch_mp_coop(s->coop, a, st));
+        launch_field_update(a, st);
+        enqueue_part(s, kPartEnd, st);
+        CK(cudaGetLastError());
+        return PIC_OK;
     }
     unsigned int nact = 0, nin = 0;
     CK(cudaMemcpyAsync(&nact, &s->st->n_active, sizeof nact, cudaMemcpyDeviceToHost, st));
@@ -481,8 +499,8 @@ __global__ void k_fix_to_f64(long long n, const long long* a, double jinv, doubl
 // Map device status counters that changed since the last check to a return code.
 int device_errors(pic_sim* s, const DevStatus& hs) {
     int rc = PIC_OK;
-    if (hs.tc_timeout != s->seen_tc) {
-        rc = fail(s, PIC_ECUDA, "a tensor-core completion wait of the learned guess timed out");
+    if (hs.sync_timeout != s->seen_sync) {
+        rc = fail(s, PIC_ECUDA, "a grid barrier of the cooperative PCG timed out");
     } else if (hs.cg_noconv != s->seen_noconv) {
         rc = fail(s, PIC_ECG_NOCONV, "PCG reached cg_max_iter before cg_rtol");
     } else if (hs.nan_count != s->seen_nan) {
@@ -496,7 +514,7 @@ int device_errors(pic_sim* s, const DevStatus& hs) {
     s->seen_nan = hs.nan_count;
     s->seen_cfl = hs.cfl_viol;
     s->seen_lost = hs.lost;
-    s->seen_tc = hs.tc_timeout;
+    s->seen_sync = hs.sync_timeout;
     return rc;
 }
 
@@ -603,6 +621,11 @@ int init_handle(const pic_params* prm, int n, pic_sim** out) {
     if (s->J64) A(cudaMemset(s->J64, 0, n3 * sizeof(double)));
     if (s->Jfix) A(cudaMemset(s->Jfix, 0, n3 * sizeof(long long)));
     if (s->F32) A(cudaMemset(s->F32, 0, 6 * s->ntot * sizeof(float)));
+    if (prm[0].precision == PIC_MIXED32 && !(prm[0].flags & PIC_NO_COOP)) {
+        const int rc = coop_create(&s->coop, s->hgrids.data(), s->ngrids, s->err);
+        if (rc == PIC_ECUDA) return bail(rc);
+        s->use_coop = rc == PIC_OK;
+    }
     if (prm[0].precision == PIC_MIXED32) {
         int rc = mixed_create(&s->mixed, prm, s->ngrids, s->hgrids.data(), s->dgrids, s->ntot, s->F32,
                               s->Jfix, s->cg, s->st, s->err);
@@ -797,11 +820,7 @@ int pic_set_cnn(pic_sim* s, const pic_cnn* net) {
     if (s->prm.precision != PIC_MIXED32) return fail(s, PIC_EINVAL, "the learned warm start needs PIC_MIXED32");
     CK(cudaStreamSynchronize(s->stream));
     drop_graph(s);
-    if (!s->cnnk.npix) {
-        int rc = cnn_alloc_work(&s->cnnk, s->hgrids.data(), s->ngrids, s->ntot, s->err);
-        if (rc) return rc;
-    }
-    int rc = cnn_copy_weights(net, &s->cnnw, s->err);
+    int rc = cnn_make_guess(net, s->hgrids.data(), s->ngrids, &s->guess, s->err);
     if (rc) return rc;
     s->has_cnn = true;
     return PIC_OK;
@@ -1089,8 +1108,8 @@ void pic_free(pic_sim* s) {
     if (s->stream) cudaStreamSynchronize(s->stream);
     drop_graph(s);
     if (s->mixed) mixed_destroy(s->mixed);
-    cnn_free_weights(&s->cnnw);
-    cnn_free_work(&s->cnnk);
+    cnn_free_guess(&s->guess);
+    coop_free(&s->coop);
     void* ptrs[] = {s->dgrids, s->dblk_grid, s->F, s->J64, s->Jfix, s->F32, s->x, s->r, s->p, s->q,
                     s->part, s->cg, s->done, s->st, s->tmp, s->dsegs, s->dblk_seg[0], s->dblk_seg[1],
                     s->bvec, s->r32, s->p32, s->q32, s->e32};

@@ -408,29 +408,48 @@ __global__ void k_adam(long long n, float* w, const float* g, float* m1, float* 
     w[k] -= lr * (a / c1) / (sqrtf(b / c2) + eps);
 }
 
-// Solver input: X0[p] = b[p] / rms(b) of p's simulation (0 where b = 0).
-__global__ void k_ws_in(long long P, long long ntot, const CnnImg* imgs, const int* tile_img, const GridDev* grids,
-                        const CgState* cg, const double* __restrict__ b, bf16* __restrict__ X0) {
-    const long long p = (long long)blockIdx.x * blockDim.x + threadIdx.x;
-    if (p >= P) return;
-    const int g = tile_img[p / kTile];
-    const double bb = cg[g].bb;
-    const double inv = bb > 0.0 ? sqrt(3.0 * grids[g].ncell / bb) : 0.0;
-    __align__(16) bf16 v[16];
-#pragma unroll
-    for (int c = 0; c < 16; c++) v[c] = __float2bfloat16_rn(c < 3 ? (float)(b[c * ntot + p] * inv) : 0.f);
-    reinterpret_cast<uint4*>(X0 + p * 16)[0] = reinterpret_cast<const uint4*>(v)[0];
-    reinterpret_cast<uint4*>(X0 + p * 16)[1] = reinterpret_cast<const uint4*>(v)[1];
-}
+// The learned guess of the solver: x0 = K * b + bias rms(b), K the network collapsed
+// into one 9x9 stencil (3 -> 3 channels). One CTA per 32 x 8 cell tile; b (FP64) of the
+// tile and a 4-cell periodic halo is staged in shared memory as FP32.
+constexpr int kGX = 32, kGY = 8, kGH = 4;
 
-__global__ void k_ws_out(long long P, long long ntot, const int* tile_img, const GridDev* grids, const CgState* cg,
-                         const float* __restrict__ out, double* __restrict__ x) {
-    const long long p = (long long)blockIdx.x * blockDim.x + threadIdx.x;
-    if (p >= P) return;
-    const int g = tile_img[p / kTile];
-    const double rms = sqrt(cg[g].bb / (3.0 * grids[g].ncell));
+__global__ void __launch_bounds__(kGX * kGY) k_guess(const GridDev* __restrict__ grids, const int* __restrict__ tile_grid,
+                                                  const int* __restrict__ tile_local, long long ntot,
+                                                  const double* __restrict__ b, double* __restrict__ x,
+                                                  const float* __restrict__ Kg, const CgState* __restrict__ cg) {
+    constexpr int WX = kGX + 2 * kGH, WY = kGY + 2 * kGH;
+    __shared__ float sK[kGuessParams];
+    __shared__ float sb[3][WY][WX];
+    const int tid = threadIdx.x;
+    const int g = tile_grid[blockIdx.x];
+    const GridDev& G = grids[g];
+    const int lt = tile_local[blockIdx.x];
+    const int ntx = (G.nx + kGX - 1) / kGX;
+    const int x0 = (lt % ntx) * kGX, y0 = (lt / ntx) * kGY;
+    for (int k = tid; k < kGuessParams; k += blockDim.x) sK[k] = Kg[k];
+    for (int k = tid; k < 3 * WY * WX; k += blockDim.x) {
+        const int c = k / (WY * WX), r = k - c * (WY * WX), yy = r / WX, xx = r - yy * WX;
+        const int gx = ((x0 - kGH + xx) % G.nx + G.nx) % G.nx;
+        const int gy = ((y0 - kGH + yy) % G.ny + G.ny) % G.ny;
+        sb[c][yy][xx] = (float)b[c * ntot + G.cell_off + (long long)gy * G.nx + gx];
+    }
+    __syncthreads();
+    const int tx = tid % kGX, ty = tid / kGX;
+    const int i = x0 + tx, j = y0 + ty;
+    if (i >= G.nx || j >= G.ny) return;
+    const double rms = sqrt(cg[g].bb / (3.0 * G.ncell));
 #pragma unroll
-    for (int c = 0; c < 3; c++) x[c * ntot + p] = (double)out[p * 16 + c] * rms;
+    for (int co = 0; co < 3; co++) {
+        float acc = 0.f;
+#pragma unroll
+        for (int ci = 0; ci < 3; ci++)
+#pragma unroll
+            for (int dy = 0; dy < kGuessTaps; dy++)
+#pragma unroll
+                for (int dx = 0; dx < kGuessTaps; dx++)
+                    acc = fmaf(sK[((co * 3 + ci) * kGuessTaps + dy) * kGuessTaps + dx], sb[ci][ty + dy][tx + dx], acc);
+        x[co * ntot + G.cell_off + (long long)j * G.nx + i] = (double)acc + (double)sK[kGuessWeights + co] * rms;
+    }
 }
 
 // ---- the GEMM building block, exposed for testing -----------------------------------
@@ -560,84 +579,94 @@ void forward(uint16_t* const wf[4], float* const bias[4], const float* prm, long
 
 // ---- handle integration ------------------------------------------------------------------
 
-int cnn_copy_weights(const pic_cnn* net, CnnWeights* dst, std::string& err) {
-    cnn_free_weights(dst);
-    for (int L = 0; L < 4; L++) {
-        const size_t nw = (size_t)kL[L].cout_pad * 9 * kL[L].cin_pad;
-        cudaError_t e = dalloc(&dst->wf[L], nw);
-        if (e == cudaSuccess) e = dalloc(&dst->bias[L], (size_t)kL[L].cout);
-        if (e == cudaSuccess) e = cudaMemcpy(dst->wf[L], net->wf[L], nw * 2, cudaMemcpyDeviceToDevice);
-        if (e == cudaSuccess)
-            e = cudaMemcpy(dst->bias[L], net->params + kL[L].b_off, kL[L].cout * sizeof(float), cudaMemcpyDeviceToDevice);
-        if (e != cudaSuccess) {
-            err = std::string("network weight copy failed: ") + cudaGetErrorString(e);
-            cudaGetLastError();
-            cnn_free_weights(dst);
-            return PIC_ENOMEM;
-        }
+// The four layers composed exactly (FP64, from the FP32 parameters): a chain of 3x3
+// convolutions y(p) = sum_t W[t] x(p + off(t)) + b composes into one stencil whose
+// offsets are the sums of the layers' offsets, and a bias that carries each earlier
+// bias through the later layers' weights.
+void collapse(const float* prm, double* K, double* bias) {
+    // running composite: C x 3 channels, S x S taps (offset index = offset + (S - 1) / 2)
+    int S = 3, C = kL[0].cout;
+    std::vector<double> cur((size_t)C * 3 * S * S, 0.0), cb(C, 0.0);
+    for (int o = 0; o < C; o++) {
+        for (int t = 0; t < 9; t++)
+            for (int i = 0; i < 3; i++)
+                cur[((size_t)(o * 3 + i) * S + t / 3) * S + t % 3] = prm[kL[0].w_off + (o * 9 + t) * 3 + i];
+        cb[o] = prm[kL[0].b_off + o];
     }
-    return PIC_OK;
+    for (int L = 1; L < 4; L++) {
+        const Layer& y = kL[L];
+        const int S2 = S + 2, C2 = y.cout;
+        std::vector<double> nxt((size_t)C2 * 3 * S2 * S2, 0.0), nb(C2, 0.0);
+        for (int o = 0; o < C2; o++) {
+            nb[o] = prm[y.b_off + o];
+            for (int t = 0; t < 9; t++) {
+                const int ty = t / 3, tx = t % 3;  // offset + 1
+                for (int m = 0; m < y.cin; m++) {
+                    const double w = prm[y.w_off + (o * 9 + t) * y.cin + m];
+                    nb[o] += w * cb[m];
+                    for (int i = 0; i < 3; i++)
+                        for (int a = 0; a < S; a++)
+                            for (int c = 0; c < S; c++)
+                                nxt[((size_t)(o * 3 + i) * S2 + a + ty) * S2 + c + tx] +=
+                                    w * cur[((size_t)(m * 3 + i) * S + a) * S + c];
+                }
+            }
+        }
+        cur.swap(nxt);
+        cb.swap(nb);
+        S = S2;
+        C = C2;
+    }
+    for (size_t k = 0; k < (size_t)kGuessWeights; k++) K[k] = cur[k];
+    for (int o = 0; o < 3; o++) bias[o] = cb[o];
 }
 
-void cnn_free_weights(CnnWeights* w) {
-    for (int L = 0; L < 4; L++) {
-        if (w->wf[L]) cudaFree(w->wf[L]);
-        if (w->bias[L]) cudaFree(w->bias[L]);
-        w->wf[L] = nullptr;
-        w->bias[L] = nullptr;
-    }
-}
-
-int cnn_alloc_work(CnnWork* w, const GridDev* hg, int ngrids, long long ntot, std::string& err) {
-    cnn_free_work(w);
-    std::vector<CnnImg> imgs(ngrids);
-    std::vector<int> ti(ntot / kTile);
-    for (int g = 0; g < ngrids; g++) {
-        if (hg[g].ncell % kTile) {
-            err = "the learned warm start needs nx*ny to be a multiple of 128 in every simulation";
-            return PIC_EINVAL;
+int cnn_make_guess(const pic_cnn* net, const GridDev* hg, int ngrids, CnnGuess* out, std::string& err) {
+    cnn_free_guess(out);
+    std::vector<float> prm(kNParams);
+    std::vector<double> K(kGuessWeights), bias(3);
+    cudaError_t e = cudaStreamSynchronize(net->stream);
+    if (e == cudaSuccess) e = cudaMemcpy(prm.data(), net->params, kNParams * sizeof(float), cudaMemcpyDeviceToHost);
+    std::vector<float> kf(kGuessParams);
+    std::vector<int> tg, tl;
+    if (e == cudaSuccess) {
+        collapse(prm.data(), K.data(), bias.data());
+        for (int k = 0; k < kGuessWeights; k++) kf[k] = (float)K[k];
+        for (int o = 0; o < 3; o++) kf[kGuessWeights + o] = (float)bias[o];
+        for (int g = 0; g < ngrids; g++) {
+            const int nt = ((hg[g].nx + kGX - 1) / kGX) * ((hg[g].ny + kGY - 1) / kGY);
+            for (int t = 0; t < nt; t++) {
+                tg.push_back(g);
+                tl.push_back(t);
+            }
         }
-        imgs[g] = CnnImg{hg[g].cell_off, hg[g].nx, hg[g].ny};
-        for (long long t = hg[g].cell_off / kTile; t < (hg[g].cell_off + hg[g].ncell) / kTile; t++) ti[t] = g;
+        e = dalloc(&out->K, (size_t)kGuessParams);
     }
-    cudaError_t e = dalloc(&w->X0, (size_t)ntot * 16);
-    if (e == cudaSuccess) e = dalloc(&w->Xa, (size_t)ntot * 32);
-    if (e == cudaSuccess) e = dalloc(&w->Xb, (size_t)ntot * 32);
-    if (e == cudaSuccess) e = dalloc(&w->out, (size_t)ntot * 16);
-    if (e == cudaSuccess) e = dalloc(&w->imgs, imgs.size());
-    if (e == cudaSuccess) e = dalloc(&w->tile_img, ti.size());
-    if (e == cudaSuccess) e = cudaMemcpy(w->imgs, imgs.data(), imgs.size() * sizeof(CnnImg), cudaMemcpyHostToDevice);
-    if (e == cudaSuccess) e = cudaMemcpy(w->tile_img, ti.data(), ti.size() * sizeof(int), cudaMemcpyHostToDevice);
-    if (e == cudaSuccess) e = set_smem_once();
+    if (e == cudaSuccess) e = dalloc(&out->tile_grid, tg.size());
+    if (e == cudaSuccess) e = dalloc(&out->tile_local, tl.size());
+    if (e == cudaSuccess) e = cudaMemcpy(out->K, kf.data(), kf.size() * sizeof(float), cudaMemcpyHostToDevice);
+    if (e == cudaSuccess) e = cudaMemcpy(out->tile_grid, tg.data(), tg.size() * sizeof(int), cudaMemcpyHostToDevice);
+    if (e == cudaSuccess) e = cudaMemcpy(out->tile_local, tl.data(), tl.size() * sizeof(int), cudaMemcpyHostToDevice);
     if (e != cudaSuccess) {
-        err = std::string("network buffers: ") + cudaGetErrorString(e);
+        err = std::string("learned guess set-up failed: ") + cudaGetErrorString(e);
         cudaGetLastError();
-        cnn_free_work(w);
-        return PIC_ENOMEM;
+        cnn_free_guess(out);
+        return PIC_ECUDA;
     }
-    w->npix = ntot;
+    out->ntiles = (int)tg.size();
     return PIC_OK;
 }
 
-void cnn_free_work(CnnWork* w) {
-    void* ps[] = {w->X0, w->Xa, w->Xb, w->out, w->imgs, w->tile_img};
+void cnn_free_guess(CnnGuess* g) {
+    void* ps[] = {g->K, g->tile_grid, g->tile_local};
     for (void* p : ps)
         if (p) cudaFree(p);
-    *w = CnnWork{};
+    *g = CnnGuess{};
 }
 
-void launch_learned_guess(const CnnWeights& w, const CnnWork& k, const GridDev* grids, const CgState* cg,
-                          long long ntot, const double* b, double* x, unsigned int* tc_timeout, cudaStream_t st) {
-    const long long P = k.npix;
-    k_ws_in<<<blocks(P), 256, 0, st>>>(P, ntot, k.imgs, k.tile_img, grids, cg, b, reinterpret_cast<bf16*>(k.X0));
-    uint16_t* const wf[4] = {w.wf[0], w.wf[1], w.wf[2], w.wf[3]};
-    float* const bias[4] = {w.bias[0], w.bias[1], w.bias[2], w.bias[3]};
-    const long long nt = P / kTile;
-    conv<16, 32, false>(nt, k.imgs, k.tile_img, k.X0, wf[0], bias[0], 32, k.Xa, tc_timeout, st);
-    conv<32, 32, false>(nt, k.imgs, k.tile_img, k.Xa, wf[1], bias[1], 32, k.Xb, tc_timeout, st);
-    conv<32, 32, false>(nt, k.imgs, k.tile_img, k.Xb, wf[2], bias[2], 32, k.Xa, tc_timeout, st);
-    conv<32, 16, true>(nt, k.imgs, k.tile_img, k.Xa, wf[3], bias[3], 3, k.out, tc_timeout, st);
-    k_ws_out<<<blocks(P), 256, 0, st>>>(P, ntot, k.tile_img, grids, cg, k.out, x);
+void launch_learned_guess(const CnnGuess& g, const GridDev* grids, const CgState* cg, long long ntot,
+                          const double* b, double* x, cudaStream_t st) {
+    k_guess<<<(unsigned)g.ntiles, kGX * kGY, 0, st>>>(grids, g.tile_grid, g.tile_local, ntot, b, x, g.K, cg);
 }
 
 }  // namespace pic
@@ -883,6 +912,22 @@ int pic_cnn_train_step(pic_cnn* c, int32_t nimg, int32_t nx, int32_t ny, const f
     k_adam<<<blocks(kNParams), 256, 0, c->stream>>>(kNParams, c->params, c->grads, c->m1, c->m2, lr, c1, c2);
     CCK(cudaGetLastError());
     CCK(cudaStreamSynchronize(c->stream));
+    return PIC_OK;
+}
+
+int pic_cnn_stencil(pic_cnn* c, float* out, int64_t n) {
+    if (!c) return PIC_EINVAL;
+    cudaSetDevice(c->device);
+    if (!out || n != kGuessParams) return cfail(c, PIC_EINVAL, "need PIC_CNN_STENCIL values");
+    std::vector<float> prm(kNParams);
+    std::vector<double> K(kGuessWeights), bias(3);
+    CCK(cudaStreamSynchronize(c->stream));
+    CCK(cudaMemcpy(prm.data(), c->params, kNParams * sizeof(float), cudaMemcpyDeviceToHost));
+    collapse(prm.data(), K.data(), bias.data());
+    std::vector<float> kf(kGuessParams);
+    for (int k = 0; k < kGuessWeights; k++) kf[k] = (float)K[k];
+    for (int o = 0; o < 3; o++) kf[kGuessWeights + o] = (float)bias[o];
+    CCK(cudaMemcpy(out, kf.data(), kf.size() * sizeof(float), cudaMemcpyDefault));
     return PIC_OK;
 }
 

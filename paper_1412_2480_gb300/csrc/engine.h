@@ -3,6 +3,8 @@
 
 #include <cuda_runtime.h>
 
+#include <string>
+
 #include "pic_internal.cuh"
 
 namespace pic {
@@ -49,6 +51,23 @@ void launch_cg_iteration(const FieldArgs& a, cudaStream_t s);
 void launch_field_update(const FieldArgs& a, cudaStream_t s);
 // FP32 copy of the FP64 fields (after pic_set_fields / init).
 void launch_fields_to_f32(const FieldArgs& a, cudaStream_t s);
+
+// The MIXED32 solve as one cooperative persistent kernel (solve_coop.cu), used when the
+// device supports cooperative launches and a handle holds at most kCoopMaxGrids
+// simulations; otherwise the WHILE-node solve above runs.
+constexpr int kCoopMaxGrids = 64;
+struct CoopSolve {
+    int2* gchunk = nullptr;       // per simulation: first chunk, chunk count
+    int* chunk_grid = nullptr;    // per chunk: simulation
+    double* part = nullptr;       // 2 x nchunks chunk partial sums
+    unsigned int* bar = nullptr;  // grid barrier: arrivals, generation
+    int nchunks = 0, nblocks = 0, ngrids = 0;
+};
+// PIC_OK, PIC_EINVAL (not applicable: keep the WHILE-node solve) or PIC_ECUDA.
+int coop_create(CoopSolve* cs, const GridDev* hgrids, int ngrids, std::string& err);
+void coop_free(CoopSolve* cs);
+// The solve after launch_rhs (and a learned guess): needs a.b, a.x, a.r and the FP32 vectors.
+cudaError_t launch_mp_coop(const CoopSolve& cs, const FieldArgs& a, cudaStream_t s);
 
 // Arguments of the FP64 particle kernel.
 struct Fp64PushArgs {

@@ -56,6 +56,15 @@ __device__ __forceinline__ double ld(const T* p, long long k, double jinv) {
     else return (double)p[k];
 }
 
+// Difference p[k1] - p[k2] of the current, times s: fixed-point values are subtracted
+// exactly as integers and converted once (int64 -> FP64 conversions and FP64 products
+// are slow on this part), with the fixed-point unit folded into s by the caller.
+template <typename T>
+__device__ __forceinline__ double dld(const T* p, long long k1, long long k2, double s) {
+    if constexpr (sizeof(T) == 8 && T(1) / T(2) == T(0)) return (double)(p[k1] - p[k2]) * s;
+    else return (p[k1] - p[k2]) * s;
+}
+
 // Sum `nv` values per thread over the block, store them as this block's partials, and
 // return true in every thread of the block that completes its simulation last. The
 // finishing block then holds the simulation-wide sums in `tot`.
@@ -136,12 +145,12 @@ k_rhs(const GridDev* __restrict__ grids, const int* __restrict__ blk_grid, int n
         const double cEx = (Ez[c.kn] - ez) * idy;
         const double cEy = -(Ez[c.ke] - ez) * idx;
         const double cEz = (Ey[c.ke] - Ey[c.k]) * idx - (Ex[c.kn] - Ex[c.k]) * idy;
-        const double ji = G.jinv;
-        const double jz = ld(Jz, c.k, ji);
-        const double cJx = (ld(Jz, c.kn, ji) - jz) * idy;
-        const double cJy = -(ld(Jz, c.ke, ji) - jz) * idx;
-        const double cJz = (ld(Jy, c.ke, ji) - ld(Jy, c.k, ji)) * idx -
-                           (ld(Jx, c.kn, ji) - ld(Jx, c.k, ji)) * idy;
+        // (the fixed-point unit jinv is 1 for an FP64 current)
+        const double ji = (sizeof(JT) == 8 && JT(1) / JT(2) == JT(0)) ? G.jinv : 1.0;
+        const double jx_ = ji * idx, jy_ = ji * idy;
+        const double cJx = dld(Jz, c.kn, c.k, jy_);
+        const double cJy = -dld(Jz, c.ke, c.k, jx_);
+        const double cJz = dld(Jy, c.ke, c.k, jx_) - dld(Jx, c.kn, c.k, jy_);
         const double cE[3] = {cEx, cEy, cEz};
         const double cJ[3] = {cJx, cJy, cJz};
         const double idx2 = idx * idx, idy2 = idy * idy;

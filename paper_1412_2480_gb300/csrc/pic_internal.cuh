@@ -75,7 +75,7 @@ struct DevStatus {
     unsigned long long ovf_count[2]; // MIXED32: particles in each overflow list
     unsigned long long loop_iters[2]; // PCG loop iterations run: [0] CG (inner) iterations,
                                       // [1] FP64 refinements (MIXED32 outer iterations)
-    unsigned int tc_timeout;          // a tensor-core completion wait ran out (learned guess)
+    unsigned int sync_timeout;        // a grid barrier of the cooperative solve ran out
 };
 
 // One contiguous range of FP64 particles of one species in one simulation.

@@ -1,0 +1,499 @@
+// solve_coop.cu -- the MIXED32 solve of Eq. (7) as one persistent cooperative kernel.
+//
+// After the right-hand side b and the initial residual r = b - A x0 (FP64), the whole
+// mixed-precision PCG runs inside one launch: iterative refinement in FP64 around an
+// FP32 inner CG on A e = r, as the WHILE-node version in fields.cu does, but with grid
+// barriers between the phases of an iteration instead of kernel boundaries, so an inner
+// iteration costs two barriers and two passes over L2-resident FP32 vectors.
+//
+// Work is cut into fixed chunks of 2048 cells of one simulation; a chunk's partial sums
+// are formed in a fixed order and written to its own slot, and every CTA forms each
+// simulation's sums from its chunk partials in a fixed order. Results therefore depend
+// neither on the number of CTAs nor on the other simulations of a batch: every CTA
+// holds the same per-simulation scalars (alpha, beta, tolerances, convergence flags)
+// without a further exchange.
+#include <algorithm>
+#include <string>
+#include <vector>
+
+#include "engine.h"
+#include "pic.h"
+
+namespace pic {
+
+namespace {
+
+constexpr int kCoopThreads = 256;
+constexpr int kChunkCells = 2048;
+constexpr int kPerThread = kChunkCells / kCoopThreads;
+constexpr int kInnerMax = 64;  // inner iterations per refinement, as in the WHILE-node solve
+constexpr int kCoopMaxChunks = 4096;  // partials staged in shared memory: 32 KB
+
+struct CoopArgs {
+    const GridDev* grids;
+    int ngrids;
+    const int2* gchunk;     // per simulation: first chunk, chunk count
+    const int* chunk_grid;  // per chunk: simulation
+    int nchunks;
+    long long ntot;
+    const double* b;
+    double* x;
+    double* r;
+    float* r32;
+    float* p32;
+    float* q32;
+    float* e32;
+    double* part;           // 2 x nchunks, alternating between phases
+    unsigned int* bar;      // [0] arrivals, [1] generation
+    CgState* cg;
+    DevStatus* st;
+};
+
+struct GState {
+    double rr, bb, scale, rr_in0, rr_in, alpha, beta, tol_in, rel, rtol;
+    int active, in_active, iters, in_iters, outer, maxit;
+};
+
+// Grid-wide barrier of a cooperative launch (all CTAs resident). Bounded: false if the
+// other CTAs did not arrive within the limit.
+__device__ bool grid_barrier(unsigned int* bar, unsigned int nblocks, unsigned int* timeout) {
+    __shared__ int s_ok;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        volatile unsigned int* gen = bar + 1;
+        const unsigned int g0 = *gen;
+        int ok = 1;
+        __threadfence();
+        if (atomicAdd(bar, 1u) == nblocks - 1u) {
+            atomicExch(bar, 0u);
+            __threadfence();
+            atomicAdd(bar + 1, 1u);
+        } else {
+            unsigned int it = 0;
+            while (*gen == g0) {
+                if (++it > (1u << 22)) {
+                    atomicExch(timeout, 1u);
+                    ok = 0;
+                    break;
+                }
+                __nanosleep(32);
+            }
+        }
+        __threadfence();
+        s_ok = ok;
+    }
+    __syncthreads();
+    return s_ok != 0;
+}
+
+// Sum of one simulation's chunk partials (staged in shared memory), by one warp, in a
+// fixed order.
+__device__ __forceinline__ double chunk_sum(const double* sp, int2 gc) {
+    double s = 0.0;
+    for (int k = threadIdx.x & 31; k < gc.y; k += 32) s += sp[gc.x + k];
+    return warp_sum(s);
+}
+
+// All chunk partials into shared memory, eight independent loads in flight per thread.
+__device__ __forceinline__ void stage_partials(const double* part, int n, double* sp) {
+    for (int base = 0; base < n; base += 8 * kCoopThreads) {
+        double v[8];
+#pragma unroll
+        for (int u = 0; u < 8; u++) {
+            const int k = base + u * kCoopThreads + threadIdx.x;
+            v[u] = k < n ? __ldcg(part + k) : 0.0;
+        }
+#pragma unroll
+        for (int u = 0; u < 8; u++) {
+            const int k = base + u * kCoopThreads + threadIdx.x;
+            if (k < n) sp[k] = v[u];
+        }
+    }
+    __syncthreads();
+}
+
+enum Phase { kBegin, kDirection, kUpdate, kX, kResidual };
+
+// Per-chunk constants, in registers.
+struct ChunkC {
+    int nx, ny, ncell, l0;
+    long long off, ntot;
+    double c0, cx, cy, scale, inv;
+    float c0f, cxf, cyf, betaf, alphaf;
+};
+
+__device__ __forceinline__ float4 ld4(const float* p) { return __ldcg(reinterpret_cast<const float4*>(p)); }
+__device__ __forceinline__ void st4(float* p, float4 v) { *reinterpret_cast<float4*>(p) = v; }
+__device__ __forceinline__ void ld4d(const double* p, double v[4]) {
+    const double2 a = __ldcg(reinterpret_cast<const double2*>(p));
+    const double2 b = __ldcg(reinterpret_cast<const double2*>(p) + 1);
+    v[0] = a.x;
+    v[1] = a.y;
+    v[2] = b.x;
+    v[3] = b.y;
+}
+__device__ __forceinline__ void st4d(double* p, const double v[4]) {
+    reinterpret_cast<double2*>(p)[0] = make_double2(v[0], v[1]);
+    reinterpret_cast<double2*>(p)[1] = make_double2(v[2], v[3]);
+}
+
+// One phase on the cells of a chunk this thread owns: quads of 4 cells along x (cells
+// 4 (q0 + qq 256 + tid) .. + 3 of the simulation), read and written as float4 / double2
+// vectors; the west and east neighbours of a quad are two scalar loads. nx is a
+// multiple of 4, so a quad never crosses a row. FULL: the chunk has all its cells, so
+// there is no bounds test and the loads of both quads can be in flight together.
+template <int PH, bool FULL>
+__device__ __forceinline__ void chunk_cells(const CoopArgs& a, const ChunkC& q, float& accf, double& accd) {
+    const long long ntot = q.ntot;
+#pragma unroll
+    for (int qq = 0; qq < kPerThread / 4; qq++) {
+        const int l = q.l0 + 4 * (qq * kCoopThreads + (int)threadIdx.x);
+        if (!FULL && l >= q.ncell) continue;
+        const int j = l / q.nx, i = l - j * q.nx;
+        const long long row = q.off + (long long)j * q.nx;
+        const long long k = row + i;
+        if constexpr (PH == kBegin) {
+#pragma unroll
+            for (int c = 0; c < 3; c++) {
+                double rv[4];
+                ld4d(a.r + c * ntot + k, rv);
+                const float4 f = make_float4((float)(rv[0] * q.scale), (float)(rv[1] * q.scale),
+                                             (float)(rv[2] * q.scale), (float)(rv[3] * q.scale));
+                st4(a.r32 + c * ntot + k, f);
+                st4(a.e32 + c * ntot + k, make_float4(0.f, 0.f, 0.f, 0.f));
+                accf = fmaf(f.x, f.x, fmaf(f.y, f.y, fmaf(f.z, f.z, fmaf(f.w, f.w, accf))));
+            }
+        } else if constexpr (PH == kDirection) {
+            const long long kwv = row + (i == 0 ? q.nx - 1 : i - 1);
+            const long long kev = row + (i + 4 == q.nx ? 0 : i + 4);
+            const long long kn = q.off + (long long)(j + 1 == q.ny ? 0 : j + 1) * q.nx + i;
+            const long long ks = q.off + (long long)(j == 0 ? q.ny - 1 : j - 1) * q.nx + i;
+#pragma unroll
+            for (int c = 0; c < 3; c++) {
+                const float* R = a.r32 + c * ntot;
+                const float4 rc = ld4(R + k), rn = ld4(R + kn), rs = ld4(R + ks);
+                const float rw = __ldcg(R + kwv), re = __ldcg(R + kev);
+                const float4 po = ld4(a.p32 + c * ntot + k), qo = ld4(a.q32 + c * ntot + k);
+                float4 Ar;
+                Ar.x = q.c0f * rc.x - q.cxf * (rw + rc.y) - q.cyf * (rn.x + rs.x);
+                Ar.y = q.c0f * rc.y - q.cxf * (rc.x + rc.z) - q.cyf * (rn.y + rs.y);
+                Ar.z = q.c0f * rc.z - q.cxf * (rc.y + rc.w) - q.cyf * (rn.z + rs.z);
+                Ar.w = q.c0f * rc.w - q.cxf * (rc.z + re) - q.cyf * (rn.w + rs.w);
+                // beta = 0 on the first iteration: p and q of the last solve are not used
+                const bool first = q.betaf == 0.f;
+                const float4 pn = first ? rc
+                                        : make_float4(fmaf(q.betaf, po.x, rc.x), fmaf(q.betaf, po.y, rc.y),
+                                                      fmaf(q.betaf, po.z, rc.z), fmaf(q.betaf, po.w, rc.w));
+                const float4 qn = first ? Ar
+                                        : make_float4(fmaf(q.betaf, qo.x, Ar.x), fmaf(q.betaf, qo.y, Ar.y),
+                                                      fmaf(q.betaf, qo.z, Ar.z), fmaf(q.betaf, qo.w, Ar.w));
+                st4(a.p32 + c * ntot + k, pn);
+                st4(a.q32 + c * ntot + k, qn);
+                accf = fmaf(pn.x, qn.x, fmaf(pn.y, qn.y, fmaf(pn.z, qn.z, fmaf(pn.w, qn.w, accf))));
+            }
+        } else if constexpr (PH == kUpdate) {
+#pragma unroll
+            for (int c = 0; c < 3; c++) {
+                const long long o = c * ntot + k;
+                const float4 e = ld4(a.e32 + o), pp = ld4(a.p32 + o), qv = ld4(a.q32 + o), r = ld4(a.r32 + o);
+                const float al = q.alphaf;
+                st4(a.e32 + o, make_float4(fmaf(al, pp.x, e.x), fmaf(al, pp.y, e.y), fmaf(al, pp.z, e.z),
+                                           fmaf(al, pp.w, e.w)));
+                const float4 rn = make_float4(fmaf(-al, qv.x, r.x), fmaf(-al, qv.y, r.y), fmaf(-al, qv.z, r.z),
+                                              fmaf(-al, qv.w, r.w));
+                st4(a.r32 + o, rn);
+                accf = fmaf(rn.x, rn.x, fmaf(rn.y, rn.y, fmaf(rn.z, rn.z, fmaf(rn.w, rn.w, accf))));
+            }
+        } else if constexpr (PH == kX) {
+#pragma unroll
+            for (int c = 0; c < 3; c++) {
+                const long long o = c * ntot + k;
+                double xv[4];
+                ld4d(a.x + o, xv);
+                const float4 e = ld4(a.e32 + o);
+                xv[0] += (double)e.x * q.inv;
+                xv[1] += (double)e.y * q.inv;
+                xv[2] += (double)e.z * q.inv;
+                xv[3] += (double)e.w * q.inv;
+                st4d(a.x + o, xv);
+            }
+        } else {  // kResidual: r = b - A x in FP64
+            const long long kwv = row + (i == 0 ? q.nx - 1 : i - 1);
+            const long long kev = row + (i + 4 == q.nx ? 0 : i + 4);
+            const long long kn = q.off + (long long)(j + 1 == q.ny ? 0 : j + 1) * q.nx + i;
+            const long long ks = q.off + (long long)(j == 0 ? q.ny - 1 : j - 1) * q.nx + i;
+#pragma unroll
+            for (int c = 0; c < 3; c++) {
+                const double* X = a.x + c * ntot;
+                double xc[4], xn[4], xs[4], bv[4], rv[4];
+                ld4d(X + k, xc);
+                ld4d(X + kn, xn);
+                ld4d(X + ks, xs);
+                ld4d(a.b + c * ntot + k, bv);
+                const double xw = __ldcg(X + kwv), xe = __ldcg(X + kev);
+#pragma unroll
+                for (int u = 0; u < 4; u++) {
+                    const double w = u == 0 ? xw : xc[u - 1];
+                    const double e = u == 3 ? xe : xc[u + 1];
+                    rv[u] = bv[u] - (q.c0 * xc[u] - q.cx * (w + e) - q.cy * (xn[u] + xs[u]));
+                    accd += rv[u] * rv[u];
+                }
+                st4d(a.r + c * ntot + k, rv);
+            }
+        }
+    }
+}
+
+template <int PH>
+__device__ __forceinline__ void chunk_phase(const CoopArgs& a, const ChunkC& q, float& accf, double& accd) {
+    if (q.l0 + kChunkCells <= q.ncell) chunk_cells<PH, true>(a, q, accf, accd);
+    else chunk_cells<PH, false>(a, q, accf, accd);
+}
+
+__global__ void __launch_bounds__(kCoopThreads) k_mp_coop(const CoopArgs a) {
+    __shared__ GState gs[kCoopMaxGrids];
+    __shared__ double red[32];
+    extern __shared__ double sp[];  // nchunks staged partial sums
+    DevStatus* st = a.st;
+    if (st->stop) return;  // the same for every CTA: stop changes only between launches
+    const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+    const unsigned int nb = gridDim.x;
+    for (int g = tid; g < a.ngrids; g += blockDim.x) {
+        const CgState& c = a.cg[g];
+        GState s{};
+        s.rr = c.rr;
+        s.bb = c.bb;
+        s.rel = c.rel;
+        s.active = c.active;
+        s.iters = 0;
+        s.outer = 0;
+        s.rtol = a.grids[g].rtol;
+        s.maxit = a.grids[g].maxit;
+        gs[g] = s;
+    }
+    __syncthreads();
+    int buf = 0;
+    bool ok = true;
+
+    // One pass over this CTA's chunks of the simulations taking part in `ph`, with
+    // per-chunk partial sums into buffer `buf` where the phase reduces.
+    auto pass = [&](Phase ph) {
+        double* part = a.part + (size_t)buf * a.nchunks;
+        for (int ch = blockIdx.x; ch < a.nchunks; ch += nb) {
+            const int g = __ldg(a.chunk_grid + ch);
+            const GState& s = gs[g];
+            const bool on = (ph == kDirection || ph == kUpdate) ? (s.active && s.in_active) : s.active;
+            if (!on) continue;  // uniform over the CTA
+            // per-chunk constants in registers (FP64 -> FP32 conversions run on the slow
+            // FP64 pipe: once per chunk, not per cell)
+            const GridDev* Gp = a.grids + g;
+            ChunkC q;
+            q.nx = __ldg(&Gp->nx);
+            q.ny = __ldg(&Gp->ny);
+            q.ncell = __ldg(&Gp->ncell);
+            q.off = __ldg(&Gp->cell_off);
+            q.ntot = a.ntot;
+            q.c0 = __ldg(&Gp->c0);
+            q.cx = __ldg(&Gp->cx);
+            q.cy = __ldg(&Gp->cy);
+            q.c0f = (float)q.c0;
+            q.cxf = (float)q.cx;
+            q.cyf = (float)q.cy;
+            q.betaf = (float)s.beta;
+            q.alphaf = (float)s.alpha;
+            q.scale = s.scale;
+            q.inv = 1.0 / s.scale;
+            q.l0 = (ch - __ldg(&a.gchunk[g].x)) * kChunkCells;
+            float accf = 0.f;
+            double accd = 0.0;
+            switch (ph) {
+            case kBegin: chunk_phase<kBegin>(a, q, accf, accd); break;
+            case kDirection: chunk_phase<kDirection>(a, q, accf, accd); break;
+            case kUpdate: chunk_phase<kUpdate>(a, q, accf, accd); break;
+            case kX: chunk_phase<kX>(a, q, accf, accd); break;
+            default: chunk_phase<kResidual>(a, q, accf, accd); break;
+            }
+            if (ph != kX) {
+                const double tot = block_sum(ph == kResidual ? accd : (double)accf, red);
+                if (tid == 0) part[ch] = tot;
+                __syncthreads();  // red is reused by the next chunk
+            }
+        }
+    };
+    // After a barrier: every CTA forms the sums of the phase for all simulations taking
+    // part, then updates their scalars identically.
+    auto reduce = [&](Phase ph) {
+        stage_partials(a.part + (size_t)buf * a.nchunks, a.nchunks, sp);
+        for (int g = warp; g < a.ngrids; g += kCoopThreads / 32) {
+            GState& s = gs[g];
+            const bool on = (ph == kDirection || ph == kUpdate) ? (s.active && s.in_active) : s.active;
+            if (!on) continue;
+            const double t = chunk_sum(sp, a.gchunk[g]);
+            if (lane != 0) continue;
+            if (ph == kBegin) {
+                s.rr_in0 = t;
+                s.rr_in = t;
+                s.beta = 0.0;
+                s.in_iters = 0;
+                s.tol_in = fmax(2e-6, 0.5 * s.rtol * sqrt(s.bb / fmax(s.rr, 1e-300)));
+                s.in_active = t > 0.0 ? 1 : 0;
+            } else if (ph == kDirection) {
+                s.alpha = s.rr_in / t;
+            } else if (ph == kUpdate) {
+                s.beta = t / s.rr_in;
+                s.rr_in = t;
+                s.in_iters += 1;
+                s.iters += 1;
+                if (sqrt(t / s.rr_in0) <= s.tol_in || s.in_iters >= kInnerMax || s.iters >= s.maxit) s.in_active = 0;
+            } else if (ph == kResidual) {
+                s.rr = t;
+                s.rel = sqrt(t / s.bb);
+                s.outer += 1;
+                if (s.rel <= s.rtol) {
+                    s.active = 0;
+                } else if (s.iters >= s.maxit || s.outer >= s.maxit) {
+                    s.active = 0;
+                    if (blockIdx.x == 0) {
+                        atomicAdd(&st->cg_noconv, 1u);
+                        st->stop_next = 1u;
+                    }
+                }
+            }
+        }
+        __syncthreads();
+        buf ^= 1;
+    };
+    auto any = [&](bool inner) {
+        int n = 0;
+        for (int g = 0; g < a.ngrids; g++) n += inner ? (gs[g].active && gs[g].in_active) : gs[g].active;
+        return n > 0;
+    };
+
+    while (ok && any(false)) {
+        for (int g = tid; g < a.ngrids; g += blockDim.x)
+            if (gs[g].active) gs[g].scale = sqrt(3.0 * a.grids[g].ncell / gs[g].rr);  // r32 of unit RMS
+        __syncthreads();
+        pass(kBegin);
+        ok = grid_barrier(a.bar, nb, &st->sync_timeout);
+        if (!ok) break;
+        reduce(kBegin);
+        while (any(true)) {
+            pass(kDirection);
+            ok = grid_barrier(a.bar, nb, &st->sync_timeout);
+            if (!ok) break;
+            reduce(kDirection);
+            pass(kUpdate);
+            ok = grid_barrier(a.bar, nb, &st->sync_timeout);
+            if (!ok) break;
+            reduce(kUpdate);
+            if (blockIdx.x == 0 && tid == 0) st->loop_iters[0] += 1ull;
+        }
+        if (!ok) break;
+        pass(kX);
+        ok = grid_barrier(a.bar, nb, &st->sync_timeout);
+        if (!ok) break;
+        pass(kResidual);
+        ok = grid_barrier(a.bar, nb, &st->sync_timeout);
+        if (!ok) break;
+        reduce(kResidual);
+        if (blockIdx.x == 0 && tid == 0) st->loop_iters[1] += 1ull;
+    }
+    if (!ok) {
+        if (tid == 0) st->stop_next = 1u;
+        return;
+    }
+    if (blockIdx.x == 0) {
+        for (int g = tid; g < a.ngrids; g += blockDim.x) {
+            CgState& c = a.cg[g];
+            const GState& s = gs[g];
+            c.rr = s.rr;
+            c.rel = s.rel;
+            c.active = 0;
+            c.iters = s.iters;
+            c.outer = s.outer;
+            c.total_outer += s.outer;
+        }
+    }
+}
+
+}  // namespace
+
+int coop_create(CoopSolve* cs, const GridDev* hg, int ngrids, std::string& err) {
+    coop_free(cs);
+    if (ngrids > kCoopMaxGrids) return PIC_EINVAL;  // the caller keeps the WHILE-node solve
+    for (int g = 0; g < ngrids; g++)
+        if (hg[g].nx % 4) return PIC_EINVAL;  // quads of 4 cells along x
+    std::vector<int2> gc(ngrids);
+    std::vector<int> cg;
+    for (int g = 0; g < ngrids; g++) {
+        const int n = (hg[g].ncell + kChunkCells - 1) / kChunkCells;
+        gc[g] = make_int2((int)cg.size(), n);
+        cg.insert(cg.end(), n, g);
+    }
+    int dev = 0, nsm = 0, occ = 0, coop = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e == cudaSuccess) e = cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
+    if (e == cudaSuccess) e = cudaDeviceGetAttribute(&coop, cudaDevAttrCooperativeLaunch, dev);
+    if ((int)cg.size() > kCoopMaxChunks) return PIC_EINVAL;
+    const size_t smem = cg.size() * sizeof(double);
+    if (e == cudaSuccess) e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k_mp_coop, kCoopThreads, smem);
+    if (e == cudaSuccess && (!coop || occ < 1)) return PIC_EINVAL;
+    if (e == cudaSuccess) e = cudaMalloc(&cs->gchunk, ngrids * sizeof(int2));
+    if (e == cudaSuccess) e = cudaMalloc(&cs->chunk_grid, cg.size() * sizeof(int));
+    if (e == cudaSuccess) e = cudaMalloc(&cs->part, 2 * cg.size() * sizeof(double));
+    if (e == cudaSuccess) e = cudaMalloc(&cs->bar, 2 * sizeof(unsigned int));
+    if (e == cudaSuccess) e = cudaMemcpy(cs->gchunk, gc.data(), ngrids * sizeof(int2), cudaMemcpyHostToDevice);
+    if (e == cudaSuccess) e = cudaMemcpy(cs->chunk_grid, cg.data(), cg.size() * sizeof(int), cudaMemcpyHostToDevice);
+    if (e == cudaSuccess) e = cudaMemset(cs->bar, 0, 2 * sizeof(unsigned int));
+    if (e != cudaSuccess) {
+        err = std::string("cooperative solve set-up failed: ") + cudaGetErrorString(e);
+        cudaGetLastError();
+        coop_free(cs);
+        return PIC_ECUDA;
+    }
+    cs->ngrids = ngrids;
+    cs->nchunks = (int)cg.size();
+    cs->nblocks = std::max(1, std::min(cs->nchunks, occ * nsm));
+    return PIC_OK;
+}
+
+void coop_free(CoopSolve* cs) {
+    void* ps[] = {cs->gchunk, cs->chunk_grid, cs->part, cs->bar};
+    for (void* p : ps)
+        if (p) cudaFree(p);
+    *cs = CoopSolve{};
+}
+
+cudaError_t launch_mp_coop(const CoopSolve& cs, const FieldArgs& f, cudaStream_t s) {
+    CoopArgs a{};
+    a.grids = f.grids;
+    a.ngrids = f.ngrids;
+    a.gchunk = cs.gchunk;
+    a.chunk_grid = cs.chunk_grid;
+    a.nchunks = cs.nchunks;
+    a.ntot = f.ntot;
+    a.b = f.b;
+    a.x = f.x;
+    a.r = f.r;
+    a.r32 = f.r32;
+    a.p32 = f.p32;
+    a.q32 = f.q32;
+    a.e32 = f.e32;
+    a.part = cs.part;
+    a.bar = cs.bar;
+    a.cg = f.cg;
+    a.st = f.st;
+    cudaLaunchConfig_t cfg{};
+    cfg.gridDim = dim3((unsigned)cs.nblocks);
+    cfg.blockDim = dim3(kCoopThreads);
+    cfg.dynamicSmemBytes = (size_t)cs.nchunks * sizeof(double);
+    cfg.stream = s;
+    cudaLaunchAttribute at[1];
+    at[0].id = cudaLaunchAttributeCooperative;
+    at[0].val.cooperative = 1;
+    cfg.attrs = at;
+    cfg.numAttrs = 1;
+    return cudaLaunchKernelEx(&cfg, k_mp_coop, a);
+}
+
+}  // namespace pic

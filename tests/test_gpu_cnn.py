@@ -179,25 +179,83 @@ def run_warm(ws, net, inputs, steps, nx=64, ny=64):
     return np.array(iters), F
 
 
-def test_learned_warm_start_cuts_pcg_iterations_in_a_pic_run():
+def apply_stencil(K, bias, b):
+    """x = K * b + bias rms(b) with K [co, ci, dy + 4, dx + 4] (numpy, FP64)."""
+    x = np.zeros_like(b, dtype=np.float64)
+    for co in range(3):
+        for ci in range(3):
+            for dy in range(-4, 5):
+                for dx in range(-4, 5):
+                    x[..., co, :, :] += K[co, ci, dy + 4, dx + 4] * np.roll(b[..., ci, :, :], (-dy, -dx), axis=(-2, -1))
+    rms = np.sqrt(np.mean(b.astype(np.float64) ** 2, axis=(-3, -2, -1), keepdims=True))
+    return x + bias.reshape(3, 1, 1) * rms
+
+
+def test_collapsed_stencil_equals_the_layered_network():
+    # the solver applies the four layers composed into one 9x9 stencil: it must equal
+    # the exact FP64 network on any input
+    rng = np.random.default_rng(9)
+    p = rand_params(rng).astype(np.float32).astype(np.float64)
+    c = network(p)
+    try:
+        K, bias = pic.pic_cnn_stencil(c)
+    finally:
+        pic.pic_cnn_free(c)
+    x = rng.standard_normal((2, 3, 12, 20))
+    rms = np.sqrt(np.mean(x ** 2, axis=(1, 2, 3), keepdims=True))
+    want = cnn.forward(p, x / rms) * rms
+    assert relnorm(apply_stencil(K.astype(np.float64), bias.astype(np.float64), x), want) < 1e-6
+
+
+@pytest.fixture(scope="module")
+def trained():
     B, X, inputs = pic_pairs(160)
     rng = np.random.default_rng(8)
     c = network(rand_params(rng, scale=0.5))
+    ntrain = len(B) - 16  # the last 16 pairs are held out
+    for it in range(3000):
+        k = rng.integers(0, ntrain, 8)
+        pic.pic_cnn_train_step(c, B[k], X[k], lr=2e-3 if it < 2000 else 3e-4)
+    yield c, B[ntrain:], inputs
+    pic.pic_cnn_free(c)
+
+
+def test_solver_applies_the_learned_guess(trained):
+    # with a loose tolerance the learned guess already satisfies it: dB is the guess
+    c, Bh, inputs = trained
+    w, sp, F0 = inputs
+    nx = ny = 64
+    prm = pic.pic_params_default(nx=nx, ny=ny, shape_order=1, gamma0=20.0, ppc=8,
+                                 precision=pic.PIC_MIXED32, cg_rtol=0.5, warm_start=pic.PIC_WS_LEARNED)
+    h = pic.pic_init(prm)
     try:
-        ntrain = len(B) - 16  # the last 16 pairs are held out
-        for it in range(3000):
-            k = rng.integers(0, ntrain, 8)
-            pic.pic_cnn_train_step(c, B[k], X[k], lr=2e-3 if it < 2000 else 3e-4)
-        x0 = pic.pic_cnn_forward(c, B[ntrain:]).astype(np.float64)
-        guess_resid = np.linalg.norm(B[ntrain:] - apply_A(x0)) / np.linalg.norm(B[ntrain:])
-        print(f"held-out relative residual of the learned guess: {guess_resid:.2e}")
-        assert guess_resid < 0.02
-        with pytest.raises(pic.PicError) as e:
-            run_warm(pic.PIC_WS_LEARNED, None, inputs, 1)
-        assert e.value.code == pic.PIC_ESTATE
-        it_learned, F_learned = run_warm(pic.PIC_WS_LEARNED, c, inputs, 40)
+        pic.pic_set_cnn(h, c)
+        for k in range(6):
+            pic.pic_set_fields(h, k, np.ascontiguousarray(F0[k]).ravel())
+        for s, d in enumerate(sp):
+            pic.pic_load_particles(h, s, d["x"], d["y"], d["ux"], d["uy"], d["uz"])
+        pic.pic_step(h, 1)
+        m = pic.pic_moments(h)
+        b = np.stack([pic.fields_numpy(h, pic.PIC_RHSX + k, nx, ny) for k in range(3)])
+        x = np.stack([pic.fields_numpy(h, pic.PIC_DBX + k, nx, ny) for k in range(3)])
+        K, bias = pic.pic_cnn_stencil(c)
     finally:
-        pic.pic_cnn_free(c)
+        pic.pic_free(h)
+    assert m["loop_iters"] == 0 and m["cg_rel_resid"] <= 0.5
+    # FP32 application of an FP32 stencil to b rounded to FP32
+    assert relnorm(x, apply_stencil(K.astype(np.float64), bias.astype(np.float64), b)) < 1e-5
+
+
+def test_learned_warm_start_cuts_pcg_iterations_in_a_pic_run(trained):
+    c, Bh, inputs = trained
+    x0 = pic.pic_cnn_forward(c, Bh).astype(np.float64)
+    guess_resid = np.linalg.norm(Bh - apply_A(x0)) / np.linalg.norm(Bh)
+    print(f"held-out relative residual of the learned guess: {guess_resid:.2e}")
+    assert guess_resid < 0.02
+    with pytest.raises(pic.PicError) as e:
+        run_warm(pic.PIC_WS_LEARNED, None, inputs, 1)
+    assert e.value.code == pic.PIC_ESTATE
+    it_learned, F_learned = run_warm(pic.PIC_WS_LEARNED, c, inputs, 40)
     it_zero, F_zero = run_warm(pic.PIC_WS_ZERO, None, inputs, 40)
     print(f"PCG iterations over 40 steps: zero guess {it_zero.sum()}, learned {it_learned.sum()}; "
           f"fields differ by {relnorm(F_learned, F_zero):.2e}")

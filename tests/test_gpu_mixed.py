@@ -164,3 +164,21 @@ def test_mixed_precision_field_solve_meets_fp64_tolerance(theta, cfl):
                              precision=pic.PIC_MIXED32, want_particles=False)
         np.testing.assert_allclose(Fg[5], (lam**n).real * F0[5], rtol=0, atol=1e-12)
         assert 0 < mom["cg_rel_resid"] <= 1e-13
+
+
+@pytest.mark.parametrize("order", [1, 3])
+def test_cooperative_solve_agrees_with_graph_loop_solve(order):
+    # the one-kernel cooperative PCG and the WHILE-node PCG run the same mixed-precision
+    # iteration; their reductions are partitioned differently, so they agree to the
+    # solver tolerance rather than bit for bit
+    nx, ny, ppc = 96, 64, 3
+    w, sp, F0 = workload(nx, ny, ppc, gamma0=5.0, u_th=0.2, seed=30 + order, field_amp=0.05,
+                         colocated=False)
+    Fc, pc, mc = run_gpu(nx, ny, ppc, sp, F0, 3, order, gamma0=5.0, cg_rtol=1e-12,
+                         precision=pic.PIC_MIXED32)
+    Fl, pl, ml = run_gpu(nx, ny, ppc, sp, F0, 3, order, gamma0=5.0, cg_rtol=1e-12,
+                         precision=pic.PIC_MIXED32, flags=pic.PIC_NO_COOP)
+    for c in range(12):
+        assert rel(Fc[c], Fl[c]) < 1e-9, c
+    assert mc["cg_rel_resid"] <= 1e-12 and ml["cg_rel_resid"] <= 1e-12
+    assert abs(mc["cg_iters_total"] - ml["cg_iters_total"]) <= 3
