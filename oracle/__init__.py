@@ -48,7 +48,7 @@ def build(force: bool = False) -> str:
 class Grid(C.Structure):
     _fields_ = [("nx", C.c_int32), ("ny", C.c_int32), ("dx", C.c_double),
                 ("dy", C.c_double), ("dt", C.c_double), ("theta", C.c_double),
-                ("order", C.c_int32)]
+                ("order", C.c_int32), ("walls", C.c_int32)]
 
 
 _P = np.ctypeslib.ndpointer(dtype=np.float64, flags="C_CONTIGUOUS")
@@ -82,10 +82,18 @@ def lib():
     return _lib
 
 
-def grid(nx, ny, dt, theta, order, dx=1.0, dy=1.0) -> Grid:
+def grid(nx, ny, dt, theta, order, dx=1.0, dy=1.0, walls=False) -> Grid:
     if nx < 8 or ny < 8:
         raise ValueError("the oracle needs nx, ny >= 8")
-    return Grid(int(nx), int(ny), float(dx), float(dy), float(dt), float(theta), int(order))
+    return Grid(int(nx), int(ny), float(dx), float(dy), float(dt), float(theta), int(order),
+                1 if walls else 0)
+
+
+def wall_nodes_zeroed(F, nx, ny):
+    """Fields with the conductor's zeros on the wall column (Ey, Ez, Bx at x = 0)."""
+    F = _c(F).reshape(6, ny, nx).copy()
+    F[[1, 2, 3], :, 0] = 0.0
+    return F.ravel()
 
 
 def _c(a):
@@ -222,11 +230,13 @@ class OracleSim:
 
     def __init__(self, nx, ny, cfl, theta, order, species, dx=1.0, dy=1.0,
                  cg_rtol=1e-10, cg_max_iter=1000, warm_start="zero", fields=None,
-                 deposit=True):
-        self.g = grid(nx, ny, cfl * dx, theta, order, dx, dy)
+                 deposit=True, walls=False):
+        self.g = grid(nx, ny, cfl * dx, theta, order, dx, dy, walls)
         self.N = nx * ny
         self.species = list(species)
         self.F = np.zeros(6 * self.N) if fields is None else _c(fields).ravel().copy()
+        if walls:
+            self.F = wall_nodes_zeroed(self.F, nx, ny)
         self.J = np.zeros(3 * self.N)
         self.dB = np.zeros(3 * self.N)
         self.cg_rtol, self.cg_max_iter = float(cg_rtol), int(cg_max_iter)

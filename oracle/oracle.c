@@ -32,6 +32,47 @@ static int64_t at(const or_grid* g, int i, int j) {
     return (int64_t)wrap(j, g->ny) * g->nx + wrap(i, g->nx);
 }
 
+/* Stored index of node (i, j) of a lattice that sits at integer x (half = 0) or at
+ * half-integer x (half = 1; node i at x = i + 1/2), for a quantity that is odd (odd = 1)
+ * or even under reflection at the walls x = 0 and x = nx, with the image sign in *sign;
+ * -1 where the value is zero by symmetry (an odd quantity on a wall node) or is not
+ * stored (the wall node x = nx). Periodic in x without walls. */
+static int64_t node(const or_grid* g, int half, int odd, int i, int j, double* sign) {
+    *sign = 1.0;
+    if (!g->walls) return at(g, i, j);
+    const int nx = g->nx;
+    if (half) {
+        if (i < 0) i = -i - 1;
+        else if (i >= nx) i = 2 * nx - i - 1;
+        else return (int64_t)wrap(j, g->ny) * nx + i;
+    } else {
+        if (i < 0) i = -i;
+        else if (i > nx) i = 2 * nx - i;
+        else if (i > 0 && i < nx) return (int64_t)wrap(j, g->ny) * nx + i;
+        if (i == nx || (odd && i == 0)) return -1;
+    }
+    if (odd) *sign = -1.0;
+    return (int64_t)wrap(j, g->ny) * nx + i;
+}
+
+/* Value of a field-like quantity at node (i, j), images of a perfect conductor
+ * included: odd on integer-x lattices (Ey, Ez, Bx, and Jy, Jz as the solver sees them:
+ * the conductor carries the wall nodes' current), even on half-integer ones. */
+static double val(const or_grid* g, const double* v, int half, int i, int j) {
+    double s;
+    const int64_t k = node(g, half, !half, i, j, &s);
+    return k < 0 ? 0.0 : s * v[k];
+}
+
+/* Add a particle's contribution to node (i, j), folded onto the stored node. A particle
+ * reflected at a wall continues as its mirror image (same charge, ux reversed): rho,
+ * Jy, Jz fold even and Jx odd (odd = 1). */
+static void add_at(const or_grid* g, double* v, int half, int odd, int i, int j, double c) {
+    double s;
+    const int64_t k = node(g, half, odd, i, j, &s);
+    if (k >= 0) v[k] += s * c;
+}
+
 /* Centred B-spline shapes W_p (Sec. 3: first- and second-order shape functions; the
  * third order extends the same family). W_p is the (p+1)-fold convolution of the
  * unit box, written out piecewise. */
@@ -71,7 +112,7 @@ static void gather_one(const or_grid* g, const double* F, double x, double y, do
             for (int i = i0; i <= i0 + 5; i++) {
                 const double wx = or_shape(g->order, sx - i);
                 if (wx == 0.0) continue;
-                acc += wx * wy * F[c * N + at(g, i, j)];
+                acc += wx * wy * val(g, F + c * N, OFF_X[c] != 0.0, i, j);
             }
         }
         f[c] = acc;
@@ -154,7 +195,7 @@ void or_deposit_move(const or_grid* g, double qw, double x0, double y0, double x
         for (int a = 0; a < W; a++) {
             const double Wx = DSx[a] * (S0y[b] + 0.5 * DSy[b]);
             acc -= fx * Wx;
-            Jx[at(g, i0 + a, j0 + b)] += acc;
+            add_at(g, Jx, 1, 1, i0 + a, j0 + b, acc);
         }
     }
     for (int a = 0; a < W; a++) {
@@ -162,14 +203,14 @@ void or_deposit_move(const or_grid* g, double qw, double x0, double y0, double x
         for (int b = 0; b < W; b++) {
             const double Wy = DSy[b] * (S0x[a] + 0.5 * DSx[a]);
             acc -= fy * Wy;
-            Jy[at(g, i0 + a, j0 + b)] += acc;
+            add_at(g, Jy, 0, 0, i0 + a, j0 + b, acc);
         }
     }
     for (int b = 0; b < W; b++) {
         for (int a = 0; a < W; a++) {
             const double Wz = S0x[a] * S0y[b] + 0.5 * DSx[a] * S0y[b] + 0.5 * S0x[a] * DSy[b] +
                               DSx[a] * DSy[b] / 3.0;
-            Jz[at(g, i0 + a, j0 + b)] += fz * Wz;
+            add_at(g, Jz, 0, 0, i0 + a, j0 + b, fz * Wz);
         }
     }
 }
@@ -185,7 +226,10 @@ static double wrap_coord(double s, int n) {
 
 /* The particle half of one step n -> n+1 for one species: gather E^n, B^n at x^n,
  * push u^{n-1/2} -> u^{n+1/2}, move x^{n+1} = x^n + dt u^{n+1/2} / gamma^{n+1/2},
- * deposit J^{n+1/2} from the unwrapped move, then wrap into the periodic box. */
+ * deposit J^{n+1/2} from the unwrapped move, then wrap into the periodic box, or, with
+ * walls, reflect a particle that crossed one: x -> -x (or 2 nx dx - x) and ux -> -ux.
+ * Its deposit is that of the unreflected move folded back at the wall: the particle
+ * and its mirror image, which carries on after the reflection. */
 int64_t or_push_deposit(const or_grid* g, const double* F, double qm, double qw, int64_t n,
                         double* x, double* y, double* ux, double* uy, double* uz,
                         double* J, int32_t deposit) {
@@ -202,7 +246,15 @@ int64_t or_push_deposit(const or_grid* g, const double* F, double qm, double qw,
         if (!(fabs(x1g - x0g) < 1.0 && fabs(y1g - y0g) < 1.0)) bad++;
         if (deposit)
             or_deposit_move(g, qw, x[k], y[k], x1g * g->dx, y1g * g->dy, u[2] / gam, J);
-        x[k] = wrap_coord(x1g, g->nx) * g->dx;
+        double xn = x1g;
+        if (g->walls && xn < 0.0) {
+            xn = -xn;
+            u[0] = -u[0];
+        } else if (g->walls && xn >= g->nx) {
+            xn = 2.0 * g->nx - xn;
+            u[0] = -u[0];
+        }
+        x[k] = (g->walls ? xn : wrap_coord(xn, g->nx)) * g->dx;
         y[k] = wrap_coord(y1g, g->ny) * g->dy;
         ux[k] = u[0];
         uy[k] = u[1];
@@ -219,8 +271,7 @@ void or_deposit_rho(const or_grid* g, double qw, int64_t n, const double* x,
         const int i0 = (int)floor(xg) - 2, j0 = (int)floor(yg) - 2;
         for (int j = j0; j <= j0 + 5; j++)
             for (int i = i0; i <= i0 + 5; i++)
-                rho[at(g, i, j)] +=
-                    qw * or_shape(g->order, xg - i) * or_shape(g->order, yg - j) / area;
+                add_at(g, rho, 0, 0, i, j, qw * or_shape(g->order, xg - i) * or_shape(g->order, yg - j) / area);
     }
 }
 
@@ -234,13 +285,13 @@ static void curl_E_lattice(const or_grid* g, const double* V, double* out) {
     for (int j = 0; j < ny; j++)
         for (int i = 0; i < nx; i++) {
             const int64_t k = at(g, i, j);
-            /* x at (i, j+1/2):      d/dy Vz */
-            out[k] = (Vz[at(g, i, j + 1)] - Vz[k]) / g->dy;
+            /* x at (i, j+1/2):      d/dy Vz      (Vz, Vy on integer-x lattices) */
+            out[k] = (val(g, Vz, 0, i, j + 1) - val(g, Vz, 0, i, j)) / g->dy;
             /* y at (i+1/2, j):     -d/dx Vz */
-            out[N + k] = -(Vz[at(g, i + 1, j)] - Vz[k]) / g->dx;
+            out[N + k] = -(val(g, Vz, 0, i + 1, j) - val(g, Vz, 0, i, j)) / g->dx;
             /* z at (i+1/2, j+1/2):  d/dx Vy - d/dy Vx */
-            out[2 * N + k] =
-                (Vy[at(g, i + 1, j)] - Vy[k]) / g->dx - (Vx[at(g, i, j + 1)] - Vx[k]) / g->dy;
+            out[2 * N + k] = (val(g, Vy, 0, i + 1, j) - val(g, Vy, 0, i, j)) / g->dx -
+                             (val(g, Vx, 1, i, j + 1) - val(g, Vx, 1, i, j)) / g->dy;
         }
 }
 
@@ -252,13 +303,14 @@ static void curl_B_lattice(const or_grid* g, const double* V, double* out) {
     for (int j = 0; j < ny; j++)
         for (int i = 0; i < nx; i++) {
             const int64_t k = at(g, i, j);
-            /* x at (i+1/2, j):      d/dy Vz */
-            out[k] = (Vz[k] - Vz[at(g, i, j - 1)]) / g->dy;
+            /* x at (i+1/2, j):      d/dy Vz      (Vz, Vy on half-integer-x lattices) */
+            out[k] = (val(g, Vz, 1, i, j) - val(g, Vz, 1, i, j - 1)) / g->dy;
             /* y at (i, j+1/2):     -d/dx Vz */
-            out[N + k] = -(Vz[k] - Vz[at(g, i - 1, j)]) / g->dx;
+            out[N + k] = -(val(g, Vz, 1, i, j) - val(g, Vz, 1, i - 1, j)) / g->dx;
             /* z at (i, j):          d/dx Vy - d/dy Vx */
-            out[2 * N + k] =
-                (Vy[k] - Vy[at(g, i - 1, j)]) / g->dx - (Vx[k] - Vx[at(g, i, j - 1)]) / g->dy;
+            out[2 * N + k] = (val(g, Vy, 1, i, j) - val(g, Vy, 1, i - 1, j)) / g->dx -
+                             (val(g, Vx, 0, i, j) - val(g, Vx, 0, i, j - 1)) / g->dy;
+            if (g->walls && i == 0) out[N + k] = out[2 * N + k] = 0.0; /* Ey, Ez on the wall */
         }
 }
 
@@ -268,12 +320,14 @@ static void laplacian3(const or_grid* g, const double* V, double* out) {
     const int64_t N = (int64_t)nx * ny;
     for (int c = 0; c < 3; c++) {
         const double* v = V + c * N;
+        const int half = c > 0; /* Bx on an integer-x lattice, By and Bz on half-integer ones */
         for (int j = 0; j < ny; j++)
             for (int i = 0; i < nx; i++) {
                 const int64_t k = at(g, i, j);
-                out[c * N + k] = (v[at(g, i + 1, j)] - 2.0 * v[k] + v[at(g, i - 1, j)]) /
+                const double vc = val(g, v, half, i, j);
+                out[c * N + k] = (val(g, v, half, i + 1, j) - 2.0 * vc + val(g, v, half, i - 1, j)) /
                                      (g->dx * g->dx) +
-                                 (v[at(g, i, j + 1)] - 2.0 * v[k] + v[at(g, i, j - 1)]) /
+                                 (val(g, v, half, i, j + 1) - 2.0 * vc + val(g, v, half, i, j - 1)) /
                                      (g->dy * g->dy);
             }
     }
@@ -380,6 +434,8 @@ void or_field_update(const or_grid* g, double* F, const double* dB, const double
     curl_B_lattice(g, Bh, curlBh);
     for (int64_t k = 0; k < 3 * N; k++) F[k] += g->dt * (curlBh[k] - 4.0 * PI * J[k]);
     for (int64_t k = 0; k < 3 * N; k++) F[3 * N + k] += dB[k];
+    if (g->walls) /* the conductor keeps Ey = Ez = 0 on the wall: it carries that current */
+        for (int j = 0; j < g->ny; j++) F[N + at(g, 0, j)] = F[2 * N + at(g, 0, j)] = 0.0;
     free(Bh);
     free(curlBh);
 }
@@ -390,7 +446,8 @@ void or_div_E(const or_grid* g, const double* F, double* out) {
     for (int j = 0; j < g->ny; j++)
         for (int i = 0; i < g->nx; i++) {
             const int64_t k = at(g, i, j);
-            out[k] = (Ex[k] - Ex[at(g, i - 1, j)]) / g->dx + (Ey[k] - Ey[at(g, i, j - 1)]) / g->dy;
+            out[k] = (val(g, Ex, 1, i, j) - val(g, Ex, 1, i - 1, j)) / g->dx +
+                     (val(g, Ey, 0, i, j) - val(g, Ey, 0, i, j - 1)) / g->dy;
         }
 }
 
@@ -404,7 +461,8 @@ void or_div_B(const or_grid* g, const double* F, double* out) {
     for (int j = 0; j < g->ny; j++)
         for (int i = 0; i < g->nx; i++) {
             const int64_t k = at(g, i, j);
-            out[k] = (Bx[at(g, i + 1, j)] - Bx[k]) / g->dx + (By[at(g, i, j + 1)] - By[k]) / g->dy;
+            out[k] = (val(g, Bx, 0, i + 1, j) - val(g, Bx, 0, i, j)) / g->dx +
+                     (val(g, By, 1, i, j + 1) - val(g, By, 1, i, j)) / g->dy;
         }
 }
 

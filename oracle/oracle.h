@@ -9,7 +9,16 @@
  * code, header, table or helper.
  *
  * Units and conventions (the paper's Sec. 2 uses Gaussian units; c = 1 here):
- *   grid     nx x ny periodic cells of size dx x dy; node (i,j) sits at (i dx, j dy).
+ *   grid     nx x ny cells of size dx x dy; node (i,j) sits at (i dx, j dy); periodic in
+ *            y, and in x either periodic or closed by two conducting, reflecting walls
+ *            at x = 0 and x = nx dx (walls != 0; the shock configuration, Sec. 4).
+ *   walls    mirror images (the method of images for a perfect conductor): a quantity
+ *            on an integer-x lattice (Ey, Ez, Bx, Jy, Jz, rho) is odd under reflection
+ *            at a wall, so it vanishes on the wall nodes; one on a half-integer lattice
+ *            (Ex, By, Bz, Jx) is even. Values beyond a wall are read from the image;
+ *            deposits beyond a wall fold back with the image's sign. This gives the
+ *            conductor conditions Ey = Ez = Bx = 0 on the walls, Neumann conditions for
+ *            By and Bz, and a symmetric positive definite operator in Eq. (7).
  *   storage  every grid quantity is an nx*ny array, index k = j*nx + i; the value
  *            stored at k lives at the quantity's own staggered position (Fig. 1 of
  *            the paper has no content; the standard 2D Yee arrangement is used):
@@ -38,6 +47,7 @@ typedef struct {
     double dt;        /* time step; CFL number sigma = c dt / dx (Sec. 3.1) */
     double theta;     /* implicitness factor of Eqs. (5)-(6), 0.5 <= theta <= 1 */
     int32_t order;    /* particle shape order 1, 2 or 3 */
+    int32_t walls;    /* 0: periodic in x; 1: conducting, reflecting walls at x = 0, nx dx */
 } or_grid;
 
 /* Centred cardinal B-spline of order p (degree p): the particle shape. */
