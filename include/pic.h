@@ -70,6 +70,20 @@ extern "C" {
 #define PIC_NO_COOP 4      /* PIC_MIXED32: run the PCG loop as graph-driven kernel launches instead
                               of one cooperative persistent kernel (same arithmetic) */
 
+/* ---- x boundaries ----
+ * PIC_BC_WALLS closes the box in x with two perfectly conducting walls at x = 0 and
+ * x = nx dx that reflect particles specularly (x -> -x, ux -> -ux), as the shock
+ * configuration does at its reflecting wall (Sec. 4). Fields take the images of a
+ * perfect conductor: Ey = Ez = Bx = 0 on the wall nodes (the x = 0 column; the x = nx
+ * nodes are not stored), Ex, By, Bz even about the walls; Eq. (7) then has Dirichlet
+ * rows for Bx and Neumann rows for By, Bz and stays symmetric positive definite. A
+ * particle's deposit folds back at a wall as its mirror image's (Jx odd, Jy, Jz even);
+ * the conductor carries the current of its wall nodes. Loaded positions must lie in
+ * [0, nx dx). pic_set_fields zeroes Ey, Ez, Bx on the wall column. Not combinable with
+ * PIC_WS_LEARNED (its guess is periodic). */
+#define PIC_BC_PERIODIC 0
+#define PIC_BC_WALLS 1
+
 /* ---- grid quantity ids for pic_fields / pic_set_fields ---- */
 #define PIC_EX 0
 #define PIC_EY 1
@@ -103,6 +117,7 @@ typedef struct pic_params {
     int32_t flags;         /* PIC_NO_DEPOSIT | PIC_NO_GRAPH */
     int32_t tile_x, tile_y;/* MIXED32 tile size in cells; 0 = chosen by the library */
     double bin_slack;      /* MIXED32 bin capacity factor over ppc * tile cells; 0 = 1.5 */
+    int32_t bc_x;          /* PIC_BC_PERIODIC or PIC_BC_WALLS (x boundaries; y is periodic) */
 } pic_params;
 
 typedef struct pic_moments_t {

@@ -37,6 +37,8 @@ PIC_CNN_NPARAMS = 20259
 PIC_NO_DEPOSIT = 1
 PIC_NO_GRAPH = 2
 PIC_NO_COOP = 4
+PIC_BC_PERIODIC = 0
+PIC_BC_WALLS = 1
 PIC_EX, PIC_EY, PIC_EZ, PIC_BX, PIC_BY, PIC_BZ = range(6)
 PIC_JX, PIC_JY, PIC_JZ, PIC_DBX, PIC_DBY, PIC_DBZ = range(6, 12)
 PIC_RHSX, PIC_RHSY, PIC_RHSZ = range(12, 15)
@@ -56,7 +58,7 @@ class pic_params(C.Structure):
                 ("gamma0", C.c_double), ("ppc", C.c_int32), ("skin_depth", C.c_double),
                 ("precision", C.c_int32), ("cg_rtol", C.c_double), ("cg_max_iter", C.c_int32),
                 ("warm_start", C.c_int32), ("flags", C.c_int32), ("tile_x", C.c_int32),
-                ("tile_y", C.c_int32), ("bin_slack", C.c_double)]
+                ("tile_y", C.c_int32), ("bin_slack", C.c_double), ("bc_x", C.c_int32)]
 
 
 class pic_moments_t(C.Structure):

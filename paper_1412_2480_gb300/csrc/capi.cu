@@ -148,6 +148,9 @@ int validate(const pic_params* p, std::string& why) {
         return bad(buf);
     }
     if (p->bin_slack < 0) return bad("bin_slack must be >= 0");
+    if (p->bc_x != PIC_BC_PERIODIC && p->bc_x != PIC_BC_WALLS) return bad("bc_x must be PIC_BC_PERIODIC or PIC_BC_WALLS");
+    if (p->bc_x == PIC_BC_WALLS && p->warm_start == PIC_WS_LEARNED)
+        return bad("PIC_WS_LEARNED cannot be combined with PIC_BC_WALLS");
     return PIC_OK;
 }
 
@@ -185,6 +188,7 @@ void fill_grid(const pic_params& p, GridDev& G) {
     G.maxit = p.cg_max_iter;
     G.warm = p.warm_start == PIC_WS_PREV ? 1 : (p.warm_start == PIC_WS_LEARNED ? 2 : 0);
     G.deposit = (p.flags & PIC_NO_DEPOSIT) ? 0 : 1;
+    G.walls = p.bc_x == PIC_BC_WALLS ? 1 : 0;
 }
 
 FieldArgs field_args(pic_sim* s, int use_cond, cudaGraphConditionalHandle cond) {
@@ -460,14 +464,15 @@ int check_species(pic_sim* s, int sp) {
 }
 
 // Device-side conversion of loaded FP64 particles: wrap into the box and scale to grid
-// units; count non-finite entries.
+// units; count non-finite entries (and, with walls, positions outside [0, Lx)).
 __global__ void k_load_fp64(long long n, double* x, double* y, const double* ux, const double* uy,
                             const double* uz, double Lx, double Ly, double idx, double idy, int nx,
-                            int ny, unsigned long long* nbad) {
+                            int ny, int walls, unsigned long long* nbad) {
     const long long k = (long long)blockIdx.x * blockDim.x + threadIdx.x;
     if (k >= n) return;
     double X = x[k], Y = y[k];
-    if (!isfinite(X) || !isfinite(Y) || !isfinite(ux[k]) || !isfinite(uy[k]) || !isfinite(uz[k])) {
+    if (!isfinite(X) || !isfinite(Y) || !isfinite(ux[k]) || !isfinite(uy[k]) || !isfinite(uz[k]) ||
+        (walls && !(X >= 0.0 && X < Lx))) {
         atomicAdd(nbad, 1ull);
         x[k] = 0.0;
         y[k] = 0.0;
@@ -873,14 +878,14 @@ int pic_load_particles(pic_sim* s, int32_t sp, const double* x, const double* y,
     if (n) {
         k_load_fp64<<<(unsigned)((n + 255) / 256), 256, 0, s->stream>>>(
             n, s->pa[sp][0], s->pa[sp][1], s->pa[sp][2], s->pa[sp][3], s->pa[sp][4], G.nx * G.dx,
-            G.ny * G.dy, G.idx, G.idy, G.nx, G.ny, nbad);
+            G.ny * G.dy, G.idx, G.idy, G.nx, G.ny, G.walls, nbad);
     }
     unsigned long long hbad = 0;
     CK(cudaMemcpyAsync(&hbad, nbad, sizeof hbad, cudaMemcpyDeviceToHost, s->stream));
     CK(cudaStreamSynchronize(s->stream));
     if (hbad) {
         s->np[sp] = 0;
-        return fail(s, PIC_EINVAL, "non-finite particle position or momentum");
+        return fail(s, PIC_EINVAL, "non-finite particle position or momentum, or a position outside the walls");
     }
     s->np[sp] = n;
     SegDev seg{};
@@ -910,6 +915,9 @@ int pic_set_fields(pic_sim* s, int32_t which, const double* data, size_t len) {
     if (!data || len < (size_t)G.ncell) return fail(s, PIC_EINVAL, "data must hold nx*ny values");
     CK(cudaMemcpyAsync(s->F + which * s->ntot + G.cell_off, data, G.ncell * sizeof(double),
                        cudaMemcpyDefault, s->stream));
+    if (G.walls && (which == PIC_EY || which == PIC_EZ || which == PIC_BX))  // zero on the wall
+        CK(cudaMemset2DAsync(s->F + which * s->ntot + G.cell_off, G.nx * sizeof(double), 0, sizeof(double),
+                             G.ny, s->stream));
     launch_fields_to_f32(field_args(s, 0, 0), s->stream);
     return finish_call(s);
 }

@@ -20,6 +20,7 @@ struct Cell {
     int g, i, j;
     long long k;   // global cell index (cell_off + j*nx + i)
     long long ke, kw, kn, ks;  // neighbours (i+1), (i-1), (j+1), (j-1), wrapped
+    bool ew, ww;   // with walls: the east / west neighbour lies beyond a wall
     bool valid;
 };
 
@@ -38,7 +39,27 @@ __device__ __forceinline__ Cell cell_at(const GridDev& G, int g, int l) {
     const int js = c.j == 0 ? G.ny - 1 : c.j - 1;
     c.kn = G.cell_off + (long long)jn * G.nx + c.i;
     c.ks = G.cell_off + (long long)js * G.nx + c.i;
+    c.ew = G.walls && c.i + 1 == G.nx;
+    c.ww = G.walls && c.i == 0;
     return c;
+}
+
+// x-neighbours with conducting walls (images of a perfect conductor): a quantity on an
+// integer-x lattice (Ey, Ez, Bx, and the currents Jy, Jz as the field solve sees them) is
+// odd under reflection at a wall and vanishes on the wall nodes; one on a half-integer
+// lattice (Ex, By, Bz, Jx) is even. Without walls these are the periodic neighbours.
+template <typename T>
+__device__ __forceinline__ T east_odd(const T* V, const Cell& c) { return c.ew ? T(0) : V[c.ke]; }
+template <typename T>
+__device__ __forceinline__ T west_odd(const T* V, const Cell& c) { return c.ww ? -V[c.k + 1] : V[c.kw]; }
+template <typename T>
+__device__ __forceinline__ T east_even(const T* V, const Cell& c) { return c.ew ? V[c.k] : V[c.ke]; }
+template <typename T>
+__device__ __forceinline__ T west_even(const T* V, const Cell& c) { return c.ww ? V[c.k] : V[c.kw]; }
+// Sum of the two x-neighbours of component a of a B-lattice vector (a = 0: Bx, odd).
+template <typename T>
+__device__ __forceinline__ T nbx(const T* V, const Cell& c, int a) {
+    return a == 0 ? east_odd(V, c) + west_odd(V, c) : east_even(V, c) + west_even(V, c);
 }
 
 // Grid-stride loop over the cells of simulation g. A simulation gets a bounded number
@@ -143,14 +164,26 @@ k_rhs(const GridDev* __restrict__ grids, const int* __restrict__ blk_grid, int n
         // curl E and curl J on the B lattices
         const double ez = Ez[c.k];
         const double cEx = (Ez[c.kn] - ez) * idy;
-        const double cEy = -(Ez[c.ke] - ez) * idx;
-        const double cEz = (Ey[c.ke] - Ey[c.k]) * idx - (Ex[c.kn] - Ex[c.k]) * idy;
+        const double cEy = -(east_odd(Ez, c) - ez) * idx;
+        const double cEz = (east_odd(Ey, c) - Ey[c.k]) * idx - (Ex[c.kn] - Ex[c.k]) * idy;
         // (the fixed-point unit jinv is 1 for an FP64 current)
         const double ji = (sizeof(JT) == 8 && JT(1) / JT(2) == JT(0)) ? G.jinv : 1.0;
         const double jx_ = ji * idx, jy_ = ji * idy;
-        const double cJx = dld(Jz, c.kn, c.k, jy_);
-        const double cJy = -dld(Jz, c.ke, c.k, jx_);
-        const double cJz = dld(Jy, c.ke, c.k, jx_) - dld(Jx, c.kn, c.k, jy_);
+        double cJx, cJy, cJz;
+        if (!G.walls) {
+            cJx = dld(Jz, c.kn, c.k, jy_);
+            cJy = -dld(Jz, c.ke, c.k, jx_);
+            cJz = dld(Jy, c.ke, c.k, jx_) - dld(Jx, c.kn, c.k, jy_);
+        } else {
+            // the conductor carries the current of its wall nodes: Jy = Jz = 0 there
+            const bool w0 = c.i == 0;
+            const double jzc = w0 ? 0.0 : ld(Jz, c.k, ji), jzn = w0 ? 0.0 : ld(Jz, c.kn, ji);
+            const double jze = c.ew ? 0.0 : ld(Jz, c.ke, ji);
+            const double jyc = w0 ? 0.0 : ld(Jy, c.k, ji), jye = c.ew ? 0.0 : ld(Jy, c.ke, ji);
+            cJx = (jzn - jzc) * idy;
+            cJy = -(jze - jzc) * idx;
+            cJz = (jye - jyc) * idx - (ld(Jx, c.kn, ji) - ld(Jx, c.k, ji)) * idy;
+        }
         const double cE[3] = {cEx, cEy, cEz};
         const double cJ[3] = {cJx, cJy, cJz};
         const double idx2 = idx * idx, idy2 = idy * idy;
@@ -158,15 +191,13 @@ k_rhs(const GridDev* __restrict__ grids, const int* __restrict__ blk_grid, int n
         for (int a = 0; a < 3; a++) {
             const double* B = F + (3 + a) * ntot;
             const double bc = B[c.k];
-            const double lap = (B[c.ke] - 2.0 * bc + B[c.kw]) * idx2 +
-                               (B[c.kn] - 2.0 * bc + B[c.ks]) * idy2;
+            const double lap = (nbx(B, c, a) - 2.0 * bc) * idx2 + (B[c.kn] - 2.0 * bc + B[c.ks]) * idy2;
             const double b = th_dt2 * (lap + 4.0 * kPi * cJ[a]) - G.dt * cE[a];
             double res = b;
             const long long o = a * ntot;
             if (G.warm == 1) {  // previous step's dB as the initial guess
                 const double* X = x + o;
-                const double Ax = G.c0 * X[c.k] - G.cx * (X[c.ke] + X[c.kw]) -
-                                  G.cy * (X[c.kn] + X[c.ks]);
+                const double Ax = G.c0 * X[c.k] - G.cx * nbx(X, c, a) - G.cy * (X[c.kn] + X[c.ks]);
                 res = b - Ax;
             }
             r[o + c.k] = res;
@@ -231,7 +262,7 @@ k_cg_direction(const GridDev* __restrict__ grids, const int* __restrict__ blk_gr
             const long long o = a * ntot;
             const double* R = r + o;
             const double rc = R[c.k];
-            const double Ar = G.c0 * rc - G.cx * (R[c.ke] + R[c.kw]) - G.cy * (R[c.kn] + R[c.ks]);
+            const double Ar = G.c0 * rc - G.cx * nbx(R, c, a) - G.cy * (R[c.kn] + R[c.ks]);
             double pn, qn;
             if (beta == 0.0) {
                 pn = rc;
@@ -318,11 +349,16 @@ k_update_E(const GridDev* __restrict__ grids, const int* __restrict__ blk_grid, 
     FOR_CELLS(G, g, c) {
         const double hzc = hz(c.k);
         const double cx = (hzc - hz(c.ks)) * G.idy;
-        const double cy = -(hzc - hz(c.kw)) * G.idx;
-        const double cz = (hy(c.k) - hy(c.kw)) * G.idx - (hx(c.k) - hx(c.ks)) * G.idy;
+        const double cy = -(hzc - hz(c.ww ? c.k : c.kw)) * G.idx;  // Bz, By even at a wall
+        const double cz = (hy(c.k) - hy(c.ww ? c.k : c.kw)) * G.idx - (hx(c.k) - hx(c.ks)) * G.idy;
         F[c.k] += G.dt * cx - f * ld(J, c.k, G.jinv);
-        F[ntot + c.k] += G.dt * cy - f * ld(J, ntot + c.k, G.jinv);
-        F[2 * ntot + c.k] += G.dt * cz - f * ld(J, 2 * ntot + c.k, G.jinv);
+        if (c.ww) {  // the conductor keeps Ey = Ez = 0 on the wall
+            F[ntot + c.k] = 0.0;
+            F[2 * ntot + c.k] = 0.0;
+        } else {
+            F[ntot + c.k] += G.dt * cy - f * ld(J, ntot + c.k, G.jinv);
+            F[2 * ntot + c.k] += G.dt * cz - f * ld(J, 2 * ntot + c.k, G.jinv);
+        }
     }
 }
 
@@ -444,7 +480,7 @@ k_mp_direction(const GridDev* __restrict__ grids, const int* __restrict__ blk_gr
             const long long o = a * ntot;
             const float* R = r32 + o;
             const float rc = R[c.k];
-            const float Ar = c0 * rc - cx * (R[c.ke] + R[c.kw]) - cy * (R[c.kn] + R[c.ks]);
+            const float Ar = c0 * rc - cx * nbx(R, c, a) - cy * (R[c.kn] + R[c.ks]);
             float pn, qn;
             if (beta == 0.f) {
                 pn = rc;
@@ -530,7 +566,7 @@ k_mp_r(const GridDev* __restrict__ grids, const int* __restrict__ blk_grid, int 
         for (int a = 0; a < 3; a++) {
             const long long o = a * ntot;
             const double* X = x + o;
-            const double Ax = G.c0 * X[c.k] - G.cx * (X[c.ke] + X[c.kw]) - G.cy * (X[c.kn] + X[c.ks]);
+            const double Ax = G.c0 * X[c.k] - G.cx * nbx(X, c, a) - G.cy * (X[c.kn] + X[c.ks]);
             const double rn = b[o + c.k] - Ax;
             r[o + c.k] = rn;
             v[0] += rn * rn;
@@ -570,7 +606,7 @@ k_guess_residual(const GridDev* __restrict__ grids, const int* __restrict__ blk_
         for (int a = 0; a < 3; a++) {
             const long long o = a * ntot;
             const double* X = x + o;
-            const double Ax = G.c0 * X[c.k] - G.cx * (X[c.ke] + X[c.kw]) - G.cy * (X[c.kn] + X[c.ks]);
+            const double Ax = G.c0 * X[c.k] - G.cx * nbx(X, c, a) - G.cy * (X[c.kn] + X[c.ks]);
             const double rn = b[o + c.k] - Ax;
             r[o + c.k] = rn;
             v[0] += rn * rn;

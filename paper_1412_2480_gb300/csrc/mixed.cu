@@ -164,12 +164,27 @@ struct GlobalMem {  // global grid arrays of one simulation; indices are global
     long long ntot;
     int nx, ny;
     float js;
+    int walls;
     __device__ __forceinline__ long long at(int ix, int iy) const {
         return (long long)wrapi(iy, ny) * nx + wrapi(ix, nx);
     }
-    __device__ __forceinline__ float ld(int c, int ix, int iy) const { return __ldg(F + c * ntot + at(ix, iy)); }
+    __device__ __forceinline__ float ld(int c, int ix, int iy) const {
+        if (!walls) return __ldg(F + c * ntot + at(ix, iy));
+        const bool half = c == 0 || c == 4 || c == 5;  // Ex, By, Bz at half-integer x
+        int s;
+        const int cx = wall_col(ix, nx, half, !half, s);
+        return s == 0 ? 0.f : (float)s * __ldg(F + c * ntot + (long long)wrapi(iy, ny) * nx + cx);
+    }
     __device__ __forceinline__ void add(int c, int ix, int iy, float v) const {
-        atomicAdd(J + c * ntot + at(ix, iy), (unsigned long long)__float2ll_rn(v * js));
+        if (!walls) {
+            atomicAdd(J + c * ntot + at(ix, iy), (unsigned long long)__float2ll_rn(v * js));
+            return;
+        }
+        int s;
+        const int cx = wall_col(ix, nx, c == 0, c == 0, s);  // mirror image: Jx odd
+        if (s != 0)
+            atomicAdd(J + c * ntot + (long long)wrapi(iy, ny) * nx + cx,
+                      (unsigned long long)__float2ll_rn((float)s * v * js));
     }
 };
 
@@ -357,9 +372,13 @@ k_push_tile(const MixedArgs a) {
             const int w = idx - c * NW;
             const int wy = w / WX;
             const int wx = w - wy * WX;
-            const int gx = ((X0 - 2 + wx) % nx + nx) % nx;
+            int gx = ((X0 - 2 + wx) % nx + nx) % nx, s = 1;
+            if (G.walls) {  // conductor images: Ex, By, Bz even, Ey, Ez, Bx odd
+                const bool half = c == 0 || c == 4 || c == 5;
+                gx = wall_col(X0 - 2 + wx, nx, half, !half, s);
+            }
             const int gy = ((Y0 - 2 + wy) % ny + ny) % ny;
-            fw[idx] = Fg[c * a.ntot + (long long)gy * nx + gx];
+            fw[idx] = s == 0 ? 0.f : (float)s * Fg[c * a.ntot + (long long)gy * nx + gx];
         }
         for (int idx = threadIdx.x; idx < 6 * NW; idx += blockDim.x) jw[idx] = 0;
         __syncthreads();
@@ -376,7 +395,7 @@ k_push_tile(const MixedArgs a) {
         const WinMem W{fw, jw, jw + 3 * NW, WX, NW, (float)(G.jscale * exp2((double)(kwin - 40))),
                        (float)(1 << lbits)};
         const GlobalMem M{a.F32 + G.cell_off, reinterpret_cast<unsigned long long*>(a.Jfix + G.cell_off),
-                          a.ntot, nx, ny, js};
+                          a.ntot, nx, ny, js, G.walls};
         const unsigned* cur = par ? a.buf[1] : a.buf[0];
         unsigned* nxt = par ? a.buf[0] : a.buf[1];
         float ek = 0.f;
@@ -404,7 +423,8 @@ k_push_tile(const MixedArgs a) {
                     else
                         ok = push_one<P>(M, K, ci, cj, ox, oy, u, di, dj, ek);
                     if (!ok) flag_bad(st, u);
-                    const int ni = wrapi(ci + di, nx), nj = wrapi(cj + dj, ny);
+                    const int ni = G.walls ? reflect_x(ci + di, nx, ox, u[0]) : wrapi(ci + di, nx);
+                    const int nj = wrapi(cj + dj, ny);
                     cnew = ni | (nj << 16);
                     if (ni >= X0 && ni < X1 && nj >= Y0 && nj < Y1) {
                         dest = 0;
@@ -453,9 +473,11 @@ k_push_tile(const MixedArgs a) {
             const int w = idx - c * NW;
             const int wy = w / WX;
             const int wx = w - wy * WX;
-            const int gx = ((X0 - 2 + wx) % nx + nx) % nx;
+            int gx = ((X0 - 2 + wx) % nx + nx) % nx, s = 1;
+            if (G.walls) gx = wall_col(X0 - 2 + wx, nx, c == 0, c == 0, s);  // mirror: Jx odd
+            if (s == 0) continue;
             const int gy = ((Y0 - 2 + wy) % ny + ny) % ny;
-            atomicAdd(Jg + c * a.ntot + (long long)gy * nx + gx, v);
+            atomicAdd(Jg + c * a.ntot + (long long)gy * nx + gx, s > 0 ? v : 0ull - v);
         }
         const double sum = block_sum((double)ek, s_red);  // begins with a block barrier
         if (threadIdx.x == 0 && sum != 0.0) atomicAdd(&a.cg[g].uk, 0.5 * G.w * sum);
@@ -495,7 +517,7 @@ k_push_overflow(const MixedArgs a) {
         const int s = gs & 1, g = gs >> 1;
         const GridDev& G = a.grids[g];
         const GlobalMem M{a.F32 + G.cell_off, reinterpret_cast<unsigned long long*>(a.Jfix + G.cell_off),
-                          a.ntot, G.nx, G.ny, (float)G.jscale};
+                          a.ntot, G.nx, G.ny, (float)G.jscale, G.walls};
         const int ci = c & 0xffff, cj = c >> 16;
         int di, dj;
         float ek = 0.f;
@@ -507,7 +529,8 @@ k_push_overflow(const MixedArgs a) {
         }
         if (!ok) flag_bad(st, u);
         if (ek != 0.f) atomicAdd(&a.cg[g].uk, 0.5 * G.w * (double)ek);
-        const int cnew = wrapi(ci + di, G.nx) | (wrapi(cj + dj, G.ny) << 16);
+        const int ni = G.walls ? reflect_x(ci + di, G.nx, ox, u[0]) : wrapi(ci + di, G.nx);
+        const int cnew = ni | (wrapi(cj + dj, G.ny) << 16);
         to_overflow(par ? a.ovf[0].p : a.ovf[1].p, par ? a.ovf[0].gs : a.ovf[1].gs, a.ovf_cap, st,
                     par ^ 1, cnew, ox, oy, u[0], u[1], u[2], gs);
     }
@@ -528,7 +551,8 @@ __global__ void k_stage_fp64(long long n, const double* x, const double* y, cons
     if (k >= n) return;
     double X = x[k], Y = y[k];
     const double a = ux[k], b = uy[k], c = uz[k];
-    if (!isfinite(X) || !isfinite(Y) || !isfinite(a) || !isfinite(b) || !isfinite(c)) {
+    if (!isfinite(X) || !isfinite(Y) || !isfinite(a) || !isfinite(b) || !isfinite(c) ||
+        (G.walls && !(X >= 0.0 && X < G.nx * G.dx))) {
         atomicAdd(nbad, 1ull);
         X = 0.0;
         Y = 0.0;
@@ -1099,7 +1123,7 @@ int mixed_load(MixedState* m, int g, int s, const double* x, const double* y, co
     cudaFree(nbad);
     if (hbad) {
         free_parts(S);
-        err = "non-finite particle position or momentum";
+        err = "non-finite particle position or momentum, or a position outside the walls";
         return PIC_EINVAL;
     }
     long long need = 0;

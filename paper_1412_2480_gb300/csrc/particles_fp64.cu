@@ -53,19 +53,27 @@ k_push_fp64(const GridDev* __restrict__ grids, const SegDev* __restrict__ segs,
         shape_nodes<P, double>(j, fyp, by0, wy0);
         shape_nodes_half<P, double>(j, fyp, byh, wyh);
         int c0[P + 1], ch[P + 1], r0[P + 1], rh[P + 1];
+        double wx0s[P + 1];  // integer-x weights with the conductor's image signs (Ey, Ez, Bx)
 #pragma unroll
         for (int a = 0; a <= P; a++) {
             c0[a] = wrapi(bx0 + a, nx);
             ch[a] = wrapi(bxh + a, nx);
             r0[a] = wrapi(by0 + a, ny) * nx;
             rh[a] = wrapi(byh + a, ny) * nx;
+            wx0s[a] = wx0[a];
+            if (G.walls) {
+                int s;
+                c0[a] = wall_col(bx0 + a, nx, false, true, s);
+                wx0s[a] = wx0[a] * s;
+                ch[a] = wall_col(bxh + a, nx, true, false, s);
+            }
         }
         const double* base = F + G.cell_off;
         // Ex (i+1/2, j), Ey (i, j+1/2), Ez (i, j), Bx (i, j+1/2), By (i+1/2, j), Bz (i+1/2, j+1/2)
         const double E[3] = {gather<P>(base, nx, ch, wxh, r0, wy0),
-                             gather<P>(base + ntot, nx, c0, wx0, rh, wyh),
-                             gather<P>(base + 2 * ntot, nx, c0, wx0, r0, wy0)};
-        const double B[3] = {gather<P>(base + 3 * ntot, nx, c0, wx0, rh, wyh),
+                             gather<P>(base + ntot, nx, c0, wx0s, rh, wyh),
+                             gather<P>(base + 2 * ntot, nx, c0, wx0s, r0, wy0)};
+        const double B[3] = {gather<P>(base + 3 * ntot, nx, c0, wx0s, rh, wyh),
                              gather<P>(base + 4 * ntot, nx, ch, wxh, r0, wy0),
                              gather<P>(base + 5 * ntot, nx, ch, wxh, rh, wyh)};
         double u[3] = {uxs[k], uys[k], uzs[k]};
@@ -90,15 +98,28 @@ k_push_fp64(const GridDev* __restrict__ grids, const SegDev* __restrict__ segs,
                                      q * G.dx / (G.dt * area), q * G.dy / (G.dt * area),
                                      q * (u[2] / gam) / area,
                                      [&](int comp, int ix, int iy, double v) {
-                                         atomicAdd(Jb + comp * ntot + (long long)wrapi(iy, ny) * nx +
-                                                       wrapi(ix, nx),
-                                                   v);
+                                         int cx = wrapi(ix, nx), s = 1;
+                                         // with walls a reflected particle continues as its
+                                         // mirror image: Jx folds odd, Jy and Jz even
+                                         if (G.walls) cx = wall_col(ix, nx, comp == 0, comp == 0, s);
+                                         if (s != 0)
+                                             atomicAdd(Jb + comp * ntot + (long long)wrapi(iy, ny) * nx + cx,
+                                                       s * v);
                                      });
             }
-            // periodic wrap (Sec. 3)
-            if (X1 < 0.0) X1 += nx;
-            if (X1 >= nx) X1 -= nx;
-            if (X1 >= nx) X1 = 0.0;
+            if (G.walls) {  // specular reflection at the walls
+                if (X1 < 0.0) {
+                    X1 = -X1;
+                    u[0] = -u[0];
+                } else if (X1 >= nx) {
+                    X1 = 2.0 * nx - X1;
+                    u[0] = -u[0];
+                }
+            } else {  // periodic wrap (Sec. 3)
+                if (X1 < 0.0) X1 += nx;
+                if (X1 >= nx) X1 -= nx;
+                if (X1 >= nx) X1 = 0.0;
+            }
             if (Y1 < 0.0) Y1 += ny;
             if (Y1 >= ny) Y1 -= ny;
             if (Y1 >= ny) Y1 = 0.0;

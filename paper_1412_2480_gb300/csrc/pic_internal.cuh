@@ -32,6 +32,7 @@ struct GridDev {
     double rtol;
     int maxit, warm;      // warm: 0 zero guess, 1 previous dB, 2 learned guess
     int deposit;          // 0 in test-particle mode
+    int walls;            // conducting, reflecting walls at x = 0 and x = nx dx (else periodic)
     // MIXED32 tiling
     int tx, ty, ntx, nty; // tile size and tile counts
     int tile_first, ntiles;
@@ -134,6 +135,51 @@ __device__ __forceinline__ void shape_nodes_half(int i, R f, int& base, R w[P + 
         }
     }
     shape_nodes<P, R>(c, s, base, w);
+}
+
+// Column of node i of an x-lattice with conducting walls at x = 0 and x = nx (method of
+// images): sign 0 where the node is a wall node of an odd quantity or the unstored wall
+// node x = nx, -1 for the image of an odd quantity, +1 otherwise. half: the lattice sits
+// at half-integer x (node i at i + 1/2). Fields read with the conductor's parity (odd
+// on integer-x lattices); particle deposits fold with the mirror image's (Jx odd, Jy,
+// Jz and rho even).
+__host__ __device__ __forceinline__ int wall_col(int i, int nx, bool half, bool odd, int& sign) {
+    sign = 1;
+    if (half) {
+        if (i < 0) i = -i - 1;
+        else if (i >= nx) i = 2 * nx - i - 1;
+        else return i;
+    } else {
+        if (i < 0) i = -i;
+        else if (i > nx) i = 2 * nx - i;
+        else if (i > 0 && i < nx) return i;
+        if (i == nx || (odd && i == 0)) {
+            sign = 0;
+            return 0;
+        }
+    }
+    if (odd) sign = -1;
+    return i < 0 ? 0 : (i >= nx ? nx - 1 : i);  // (padding nodes of a tile window only)
+}
+
+// Specular reflection at the walls of a particle whose move ended in cell `cell` (-1 or
+// nx: beyond a wall) at offset `off` in [0, 1): returns the cell in [0, nx), updates the
+// offset to the mirrored position and reverses ux.
+template <typename R>
+__device__ __forceinline__ int reflect_x(int cell, int nx, R& off, R& ux) {
+    if (cell >= 0 && cell < nx) return cell;
+    ux = -ux;
+    R o = R(1) - off;  // the position mirrored about the wall, within the wall cell
+    if (cell < 0) {
+        if (o >= R(1)) {  // exactly one cell beyond x = 0: lands on node 1
+            off = R(0);
+            return 1;
+        }
+        off = o;
+        return 0;
+    }
+    off = o >= R(1) ? R(1) - R(1) / R(16777216) : o;  // exactly on x = nx: stay just inside
+    return nx - 1;
 }
 
 // Periodic wrap of a lattice index that is at most a few cells out of range.

@@ -116,7 +116,7 @@ enum Phase { kBegin, kDirection, kUpdate, kX, kResidual };
 
 // Per-chunk constants, in registers.
 struct ChunkC {
-    int nx, ny, ncell, l0;
+    int nx, ny, ncell, l0, walls;
     long long off, ntot;
     double c0, cx, cy, scale, inv;
     float c0f, cxf, cyf, betaf, alphaf;
@@ -172,7 +172,11 @@ __device__ __forceinline__ void chunk_cells(const CoopArgs& a, const ChunkC& q, 
             for (int c = 0; c < 3; c++) {
                 const float* R = a.r32 + c * ntot;
                 const float4 rc = ld4(R + k), rn = ld4(R + kn), rs = ld4(R + ks);
-                const float rw = __ldcg(R + kwv), re = __ldcg(R + kev);
+                float rw = __ldcg(R + kwv), re = __ldcg(R + kev);
+                if (q.walls) {  // images at a conducting wall: Bx odd, By and Bz even
+                    if (i == 0) rw = c == 0 ? -rc.y : rc.x;
+                    if (i + 4 == q.nx) re = c == 0 ? 0.f : rc.w;
+                }
                 const float4 po = ld4(a.p32 + c * ntot + k), qo = ld4(a.q32 + c * ntot + k);
                 float4 Ar;
                 Ar.x = q.c0f * rc.x - q.cxf * (rw + rc.y) - q.cyf * (rn.x + rs.x);
@@ -230,7 +234,11 @@ __device__ __forceinline__ void chunk_cells(const CoopArgs& a, const ChunkC& q, 
                 ld4d(X + kn, xn);
                 ld4d(X + ks, xs);
                 ld4d(a.b + c * ntot + k, bv);
-                const double xw = __ldcg(X + kwv), xe = __ldcg(X + kev);
+                double xw = __ldcg(X + kwv), xe = __ldcg(X + kev);
+                if (q.walls) {
+                    if (i == 0) xw = c == 0 ? -xc[1] : xc[0];
+                    if (i + 4 == q.nx) xe = c == 0 ? 0.0 : xc[3];
+                }
 #pragma unroll
                 for (int u = 0; u < 4; u++) {
                     const double w = u == 0 ? xw : xc[u - 1];
@@ -291,6 +299,7 @@ __global__ void __launch_bounds__(kCoopThreads) k_mp_coop(const CoopArgs a) {
             q.nx = __ldg(&Gp->nx);
             q.ny = __ldg(&Gp->ny);
             q.ncell = __ldg(&Gp->ncell);
+            q.walls = __ldg(&Gp->walls);
             q.off = __ldg(&Gp->cell_off);
             q.ntot = a.ntot;
             q.c0 = __ldg(&Gp->c0);

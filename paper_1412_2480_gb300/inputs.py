@@ -102,3 +102,27 @@ def scan_table(n: int = 48) -> list:
                      "theta": SCAN_THETA[(k // 6) % 4], "order": 1 + (k + k // 24) % 3,
                      "gamma0": 20.0, "ppc": 16, "u_th": 1e-3, "seed": 3 + k})
     return rows
+
+
+# ---- the shock configuration: a magnetised pair beam flowing into a reflecting wall ----
+def shock_beam(nx: int, ny: int, ppc: int, gamma0: float, u_th: float, seed: int,
+               sigma_b: float = 0.1, dx: float = 1.0, dy: float = 1.0, skin_depth: float = 10.0):
+    """Co-located pairs filling [0, nx dx) x [0, ny dy), drifting toward the wall at
+    x = 0 with Lorentz factor gamma0 (the paper's shock set-up mirrored: it injects at
+    the left and reflects at the right, Sec. 4), in a uniform out-of-plane field Bz = B0
+    of magnetisation sigma_b = B0^2 / (4 pi gamma0 n m c^2) (n: both species) and the
+    motional field Ey = -v B0 that lets the beam drift undeflected (zero on the wall
+    column). Returns (macro weight, species list, fields (6, ny, nx))."""
+    w, sp = drifting_pair_plasma(nx, ny, ppc, gamma0, u_th, seed, dx=dx, dy=dy,
+                                 skin_depth=skin_depth)
+    for d in sp:
+        d["ux"] = -d["ux"]
+    wpe = 1.0 / skin_depth
+    # n m c^2 over both species = 2 ppc w / (dx dy) = omega_pe^2 gamma0 / (2 pi)
+    b0 = math.sqrt(sigma_b * 4.0 * math.pi * gamma0 * 2.0 * ppc * w / (dx * dy))
+    v = math.sqrt(1.0 - 1.0 / (gamma0 * gamma0))
+    F = np.zeros((6, ny, nx))
+    F[5] = b0
+    F[1] = -v * b0
+    F[1][:, 0] = 0.0
+    return w, sp, F

@@ -93,3 +93,11 @@ def test_batch_validation_on_host():
         pic.pic_autotune_tiles([mixed], steps=0)
     assert e.value.code == pic.PIC_EINVAL
     assert pic.pic_batch_size(None) == 0
+
+
+def test_walls_parameter_validation_on_host():
+    for kw in (dict(bc_x=2), dict(bc_x=pic.PIC_BC_WALLS, precision=pic.PIC_MIXED32,
+                                  warm_start=pic.PIC_WS_LEARNED)):
+        with pytest.raises(pic.PicError) as e:
+            pic.pic_init(pic.pic_params_default(**kw))
+        assert e.value.code == pic.PIC_EINVAL

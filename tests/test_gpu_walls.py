@@ -1,0 +1,101 @@
+"""Conducting, reflecting walls in x (the shock configuration), GPU against the oracle
+through the C ABI: one step of a hot plasma crossing both walls (FP64 to 1e-12, MIXED32
+to 2e-5, orders 1-3), and a magnetised pair beam flowing into the wall at x = 0 over
+many steps (the shock set-up of Sec. 4 mirrored), FP64 and MIXED32 against the oracle."""
+import numpy as np
+import pytest
+
+import paper_1412_2480_gb300 as pic
+from paper_1412_2480_gb300 import inputs
+from runners import rel, run_gpu, run_oracle, workload
+
+pytestmark = pytest.mark.gpu
+TOL32 = 2e-5
+
+
+def hot_near_walls(nx, ny, ppc, seed):
+    """A hot plasma with random fields (zero on the wall column), particles near both
+    walls moving into them."""
+    w, sp, F0 = workload(nx, ny, ppc, gamma0=3.0, u_th=0.3, seed=seed, field_amp=0.05,
+                         colocated=False)
+    rng = np.random.default_rng(seed)
+    for d in sp:
+        n = d["x"].size
+        left = rng.random(n) < 0.5
+        d["x"] = np.where(left, rng.uniform(0, 2.0, n), rng.uniform(nx - 2.0, nx, n))
+        d["ux"] = np.where(left, -np.abs(d["ux"]) - 1.0, np.abs(d["ux"]) + 1.0)
+    F0 = F0.copy()
+    F0[[1, 2, 3], :, 0] = 0.0
+    return w, sp, F0
+
+
+def sorted_particles(p):
+    return p[:, np.lexsort(p[::-1])]
+
+
+@pytest.mark.parametrize("order", [1, 2, 3])
+def test_fp64_step_with_walls_matches_oracle(order):
+    nx, ny, ppc = 40, 24, 3
+    w, sp, F0 = hot_near_walls(nx, ny, ppc, 40 + order)
+    Fg, pg, mom = run_gpu(nx, ny, ppc, sp, F0, 1, order, gamma0=3.0, cg_rtol=1e-13,
+                          bc_x=pic.PIC_BC_WALLS)
+    Fo, po, sim = run_oracle(nx, ny, w, sp, F0, 1, order, cg_rtol=1e-13, walls=True)
+    for c in range(12):
+        assert rel(Fg[c], Fo[c]) < 1e-12, f"quantity {c}: {rel(Fg[c], Fo[c]):.2e}"
+    for s in range(2):
+        assert rel(pg[s], po[s]) < 1e-12
+        assert pg[s][0].min() >= 0 and pg[s][0].max() < nx
+    assert np.all(Fg[[1, 2, 3]][:, :, 0] == 0.0)  # Ey, Ez, Bx on the wall
+
+
+@pytest.mark.parametrize("order", [1, 2, 3])
+def test_mixed32_step_with_walls_matches_oracle(order):
+    nx, ny, ppc = 40, 24, 3
+    w, sp, F0 = hot_near_walls(nx, ny, ppc, 50 + order)
+    Fg, pg, mom = run_gpu(nx, ny, ppc, sp, F0, 1, order, gamma0=3.0, cg_rtol=1e-13,
+                          precision=pic.PIC_MIXED32, tile_x=16, tile_y=8, bc_x=pic.PIC_BC_WALLS)
+    Fo, po, sim = run_oracle(nx, ny, w, sp, F0, 1, order, cg_rtol=1e-13, walls=True)
+    for c in range(9):
+        assert rel(Fg[c], Fo[c]) < TOL32, f"quantity {c}: {rel(Fg[c], Fo[c]):.2e}"
+    for s in range(2):
+        g, o = sorted_particles(pg[s]), sorted_particles(po[s])
+        assert np.max(np.abs(g[0] - o[0])) < TOL32 * nx
+        assert rel(g[2:], o[2:]) < TOL32
+        assert g[0].min() >= 0 and g[0].max() < nx
+
+
+@pytest.mark.parametrize("precision", [pic.PIC_FP64, pic.PIC_MIXED32])
+def test_magnetised_beam_into_the_wall_matches_oracle(precision):
+    # gamma0 = 10 pairs at sigma_B = 0.1 hit the wall at x = 0 and reflect; after 40
+    # steps the reflected beam has built up the shock transition near the wall
+    nx, ny, ppc, steps = 64, 16, 4, 40
+    w, sp, F0 = inputs.shock_beam(nx, ny, ppc, 10.0, 1e-3, seed=5, sigma_b=0.1)
+    kw = {} if precision == pic.PIC_FP64 else {"tile_x": 16, "tile_y": 8}
+    Fg, pg, mom = run_gpu(nx, ny, ppc, sp, F0, steps, 2, gamma0=10.0, cg_rtol=1e-12,
+                          precision=precision, bc_x=pic.PIC_BC_WALLS, **kw)
+    Fo, po, sim = run_oracle(nx, ny, w, sp, F0, steps, 2, cg_rtol=1e-12, walls=True)
+    tol = 1e-9 if precision == pic.PIC_FP64 else 1e-3
+    for c in range(6):
+        assert rel(Fg[c], Fo[c]) < tol, f"field {c}: {rel(Fg[c], Fo[c]):.2e}"
+    # the beam reversed at the wall: some particles now move in +x
+    assert np.any(pg[0][2] > 0) and np.any(po[0][2] > 0)
+    # magnetic energy of the final fields (pic_moments reports the level the last step
+    # started from, so compare the arrays themselves)
+    ub_g, ub_o = np.sum(Fg[3:6] ** 2), sim.energies()[1] * 8 * np.pi
+    assert abs(ub_g - ub_o) < tol * ub_o
+
+
+def test_walls_validation_and_set_fields_zeroes_the_wall():
+    prm = pic.pic_params_default(nx=16, ny=16, bc_x=pic.PIC_BC_WALLS)
+    h = pic.pic_init(prm)
+    try:
+        data = np.ones(16 * 16)
+        pic.pic_set_fields(h, pic.PIC_EY, data)
+        out = pic.fields_numpy(h, pic.PIC_EY, 16, 16)
+        assert np.all(out[:, 0] == 0.0) and np.all(out[:, 1:] == 1.0)
+        with pytest.raises(pic.PicError) as e:
+            pic.pic_load_particles(h, 0, np.array([16.5]), np.array([1.0]), np.zeros(1), np.zeros(1),
+                                   np.zeros(1))
+        assert e.value.code == pic.PIC_EINVAL
+    finally:
+        pic.pic_free(h)
