@@ -242,7 +242,7 @@ def run_ours(args, dist):
     if nsim > 1 and prec != pic.PIC_MIXED32:
         raise SystemExit("the batched scan runs in MIXED32 (its FP64 comparison is built in)")
     tune = None
-    if nsim > 1:
+    if prec == pic.PIC_MIXED32:
         # tile shapes per shape order from the autotuner (synthetic scratch batches)
         ps = params_of(rows, prec)
         t0 = time.perf_counter()

@@ -258,7 +258,9 @@ __device__ __forceinline__ void chunk_phase(const CoopArgs& a, const ChunkC& q, 
     else chunk_cells<PH, false>(a, q, accf, accd);
 }
 
-__global__ void __launch_bounds__(kCoopThreads) k_mp_coop(const CoopArgs a) {
+// 4 CTAs per SM (64 registers): 608 resident CTAs, so a 2048 x 512 grid (512 chunks)
+// gives every CTA at most one chunk per phase
+__global__ void __launch_bounds__(kCoopThreads, 4) k_mp_coop(const CoopArgs a) {
     __shared__ GState gs[kCoopMaxGrids];
     __shared__ double red[32];
     extern __shared__ double sp[];  // nchunks staged partial sums
