@@ -84,6 +84,26 @@ extern "C" {
 #define PIC_BC_PERIODIC 0
 #define PIC_BC_WALLS 1
 
+/* ---- the moving injector (PIC_BC_WALLS, inject_x0 >= 0) ----
+ * The shock set-up feeds the wall at x = 0 with a pair beam from a plane that starts at
+ * x_f(0) = inject_x0 (cells) and moves toward +x at c: x_f(n) = inject_x0 + n cfl. The
+ * paper injects from a fixed boundary (Sec. 4); a plane moving at c keeps every
+ * injected and reflected particle behind it, so no particle ever leaves the box. At the
+ * end of step n (n = steps completed before it, counted from pic_init) the slab
+ * [x_f(n+1) - (1 + v) cfl, x_f(n+1)) of every row j, which the beam has uncovered by
+ * moving at -v while the plane moved at +c, receives N_n = floor(ppc w (n+1)) -
+ * floor(ppc w n) co-located pairs, w = (1 + v) cfl the slab width: the beam's density
+ * ppc per cell per species over time. Pair k of row j at step n sits at
+ * x = x_f(n+1) - w U0, y = j + U1; species s gets rest-frame momenta u_th (z0, z1, z2)
+ * from Box-Muller pairs (U2, U3) and (U4, U5), boosted toward -x: ux = -gamma0
+ * (u_th z0 + beta0 gamma'), uy = u_th z1, uz = u_th z2, gamma' = sqrt(1 + u_th^2 |z|^2).
+ * U_d = ((h >> 11) + 1/2) 2^-53, h = splitmix64 (Steele, Lea & Flood 2014) of the counter
+ * seed K0 + n K1 + j K2 + k K3 + s K4 + d (mod 2^64), with K0..K4 = 0xD1B54A32D192ED03,
+ * 0xABC98388FB8FAC03, 0x8CB92BA72F3D8DD7, 0x9E3779B97F4A7C15, 0xC2B2AE3D27D4EB4F
+ * (positions use s = 0). Injection stops once x_f(n+1) > nx. The fields ahead of the
+ * plane are whatever the caller set (a uniform Bz and the beam's motional Ey make a
+ * static vacuum solution). */
+
 /* ---- grid quantity ids for pic_fields / pic_set_fields ---- */
 #define PIC_EX 0
 #define PIC_EY 1
@@ -118,6 +138,9 @@ typedef struct pic_params {
     int32_t tile_x, tile_y;/* MIXED32 tile size in cells; 0 = chosen by the library */
     double bin_slack;      /* MIXED32 bin capacity factor over ppc * tile cells; 0 = 1.5 */
     int32_t bc_x;          /* PIC_BC_PERIODIC or PIC_BC_WALLS (x boundaries; y is periodic) */
+    double inject_x0;      /* PIC_BC_WALLS: start of the moving injector in cells (< 0: none) */
+    double u_th;           /* injector: rest-frame thermal momentum spread (units of c) */
+    uint64_t seed;         /* injector: seed of its counter-based random numbers */
 } pic_params;
 
 typedef struct pic_moments_t {

@@ -18,6 +18,7 @@ and closed-form current sums.
 from __future__ import annotations
 
 import ctypes as C
+import math
 import os
 import subprocess
 import threading
@@ -217,6 +218,66 @@ class Species:
         return self.w * float(np.sum(np.sqrt(1.0 + self.ux**2 + self.uy**2 + self.uz**2) - 1.0))
 
 
+# ---- the moving injector of the shock set-up ------------------------------------------
+# A plane starting at x_f(0) = x0 (cells) moves toward +x at c, x_f(n) = x0 + n cfl, and
+# keeps the beam flowing toward the wall at x = 0 uninterrupted behind it: at the end of
+# step n the slab [x_f(n+1) - w, x_f(n+1)) of every row, w = (1 + v) cfl (uncovered
+# because the beam moved -v dt while the plane moved c dt), receives
+# floor(ppc w (n+1)) - floor(ppc w n) co-located pairs (the beam density over time), at
+# uniform random positions, with rest-frame Gaussian momenta of spread u_th boosted to
+# gamma0 toward -x; none once x_f(n+1) > nx. Random numbers: splitmix64 (Steele, Lea &
+# Flood 2014) of the counter seed K0 + n K1 + j K2 + k K3 + s K4 + d, uniform
+# ((h >> 11) + 1/2) 2^-53; Box-Muller for the Gaussians.
+_INJ_K = (0xD1B54A32D192ED03, 0xABC98388FB8FAC03, 0x8CB92BA72F3D8DD7, 0x9E3779B97F4A7C15,
+          0xC2B2AE3D27D4EB4F)
+
+
+def splitmix64(z):
+    """The splitmix64 output function of the counter z (uint64 array)."""
+    with np.errstate(over="ignore"):
+        z = np.asarray(z, dtype=np.uint64) + np.uint64(0x9E3779B97F4A7C15)
+        z = (z ^ (z >> np.uint64(30))) * np.uint64(0xBF58476D1CE4E5B9)
+        z = (z ^ (z >> np.uint64(27))) * np.uint64(0x94D049BB133111EB)
+        return z ^ (z >> np.uint64(31))
+
+
+def inject_uniform(seed, n, j, k, s, d):
+    """Uniform in (0, 1) for draw d of pair k (array) of row j (array) at step n, species s."""
+    with np.errstate(over="ignore"):
+        key = (np.uint64(seed) * np.uint64(_INJ_K[0]) + np.uint64(n) * np.uint64(_INJ_K[1]) +
+               np.asarray(j, dtype=np.uint64) * np.uint64(_INJ_K[2]) +
+               np.asarray(k, dtype=np.uint64) * np.uint64(_INJ_K[3]) +
+               np.uint64(s) * np.uint64(_INJ_K[4]) + np.uint64(d))
+    h = splitmix64(key)
+    return ((h >> np.uint64(11)).astype(np.float64) + 0.5) * (1.0 / 9007199254740992.0)
+
+
+def inject_pairs(n, nx, ny, cfl, x0, ppc, gamma0, u_th, seed):
+    """Pairs entering at the end of step n: (x, y) in cells and [(ux, uy, uz)] per species."""
+    w = (1.0 + math.sqrt(1.0 - 1.0 / (gamma0 * gamma0))) * cfl
+    xf = x0 + (n + 1) * cfl
+    if xf > nx:
+        return None
+    per_row = int(math.floor((ppc * w) * (n + 1))) - int(math.floor((ppc * w) * n))
+    if per_row <= 0:
+        return None
+    j = np.repeat(np.arange(ny), per_row)
+    k = np.tile(np.arange(per_row), ny)
+    x = xf - w * inject_uniform(seed, n, j, k, 0, 0)
+    y = j + inject_uniform(seed, n, j, k, 0, 1)
+    beta0 = math.sqrt(1.0 - 1.0 / (gamma0 * gamma0))
+    mom = []
+    for s in (0, 1):
+        r0 = np.sqrt(-2.0 * np.log(inject_uniform(seed, n, j, k, s, 2)))
+        a0 = 2.0 * math.pi * inject_uniform(seed, n, j, k, s, 3)
+        r1 = np.sqrt(-2.0 * np.log(inject_uniform(seed, n, j, k, s, 4)))
+        a1 = 2.0 * math.pi * inject_uniform(seed, n, j, k, s, 5)
+        upx, upy, upz = u_th * r0 * np.cos(a0), u_th * r0 * np.sin(a0), u_th * r1 * np.cos(a1)
+        gp = np.sqrt(1.0 + upx * upx + upy * upy + upz * upz)
+        mom.append((-gamma0 * (upx + beta0 * gp), upy, upz))
+    return x, y, mom
+
+
 class OracleSim:
     """The per-step particle cycle, in the paper's order (Sec. 2, Sec. 3):
 
@@ -230,13 +291,16 @@ class OracleSim:
 
     def __init__(self, nx, ny, cfl, theta, order, species, dx=1.0, dy=1.0,
                  cg_rtol=1e-10, cg_max_iter=1000, warm_start="zero", fields=None,
-                 deposit=True, walls=False):
+                 deposit=True, walls=False, injector=None):
         self.g = grid(nx, ny, cfl * dx, theta, order, dx, dy, walls)
         self.N = nx * ny
         self.species = list(species)
         self.F = np.zeros(6 * self.N) if fields is None else _c(fields).ravel().copy()
         if walls:
             self.F = wall_nodes_zeroed(self.F, nx, ny)
+        # injector: dict(x0=, ppc=, gamma0=, u_th=, seed=) (with walls); needs both species
+        self.injector = dict(injector) if injector else None
+        self.cfl = float(cfl)
         self.J = np.zeros(3 * self.N)
         self.dB = np.zeros(3 * self.N)
         self.cg_rtol, self.cg_max_iter = float(cg_rtol), int(cg_max_iter)
@@ -265,9 +329,25 @@ class OracleSim:
         self.last_cg_iters, self.last_cg_resid = it, rr
         self.F = field_update(self.g, self.F, dB, self.J)
 
+    def inject(self):
+        q = self.injector
+        new = inject_pairs(self.step_count, self.g.nx, self.g.ny, self.cfl, q["x0"], q["ppc"],
+                           q["gamma0"], q["u_th"], q["seed"])
+        if new is None:
+            return
+        x, y, mom = new
+        for s, sp in enumerate(self.species):
+            sp.x = np.concatenate([sp.x, x * self.g.dx])
+            sp.y = np.concatenate([sp.y, y * self.g.dy])
+            sp.ux = np.concatenate([sp.ux, mom[s][0]])
+            sp.uy = np.concatenate([sp.uy, mom[s][1]])
+            sp.uz = np.concatenate([sp.uz, mom[s][2]])
+
     def step(self, n=1):
         for _ in range(int(n)):
             self.push_deposit()
+            if self.injector:
+                self.inject()
             self.field_solve()
             self.step_count += 1
 

@@ -58,7 +58,8 @@ class pic_params(C.Structure):
                 ("gamma0", C.c_double), ("ppc", C.c_int32), ("skin_depth", C.c_double),
                 ("precision", C.c_int32), ("cg_rtol", C.c_double), ("cg_max_iter", C.c_int32),
                 ("warm_start", C.c_int32), ("flags", C.c_int32), ("tile_x", C.c_int32),
-                ("tile_y", C.c_int32), ("bin_slack", C.c_double), ("bc_x", C.c_int32)]
+                ("tile_y", C.c_int32), ("bin_slack", C.c_double), ("bc_x", C.c_int32),
+                ("inject_x0", C.c_double), ("u_th", C.c_double), ("seed", C.c_uint64)]
 
 
 class pic_moments_t(C.Structure):

@@ -151,6 +151,11 @@ int validate(const pic_params* p, std::string& why) {
     if (p->bc_x != PIC_BC_PERIODIC && p->bc_x != PIC_BC_WALLS) return bad("bc_x must be PIC_BC_PERIODIC or PIC_BC_WALLS");
     if (p->bc_x == PIC_BC_WALLS && p->warm_start == PIC_WS_LEARNED)
         return bad("PIC_WS_LEARNED cannot be combined with PIC_BC_WALLS");
+    if (p->inject_x0 >= 0.0) {
+        if (p->bc_x != PIC_BC_WALLS) return bad("the injector needs PIC_BC_WALLS");
+        if (p->inject_x0 < 2.0 * p->cfl || p->inject_x0 > p->nx) return bad("inject_x0 must lie in [2 cfl, nx]");
+        if (!(p->u_th >= 0.0) || p->u_th > 1.0) return bad("u_th must lie in [0, 1]");
+    }
     return PIC_OK;
 }
 
@@ -189,6 +194,13 @@ void fill_grid(const pic_params& p, GridDev& G) {
     G.warm = p.warm_start == PIC_WS_PREV ? 1 : (p.warm_start == PIC_WS_LEARNED ? 2 : 0);
     G.deposit = (p.flags & PIC_NO_DEPOSIT) ? 0 : 1;
     G.walls = p.bc_x == PIC_BC_WALLS ? 1 : 0;
+    G.inject = (G.walls && p.inject_x0 >= 0.0) ? 1 : 0;
+    G.ppc = p.ppc;
+    G.inj_x0 = p.inject_x0;
+    G.cfl = p.cfl;
+    G.gamma0 = p.gamma0;
+    G.u_th = p.u_th;
+    G.inj_seed = p.seed;
 }
 
 FieldArgs field_args(pic_sim* s, int use_cond, cudaGraphConditionalHandle cond) {
@@ -262,7 +274,7 @@ void enqueue_part(pic_sim* s, int part, cudaStream_t st) {
             break;
         }
         for (int sp = 0; sp < 2; sp++) {
-            if (s->np[sp] == 0) continue;
+            if (s->nblk_push[sp] == 0) continue;
             Fp64PushArgs p{};
             p.grids = s->dgrids;
             p.segs = s->dsegs + sp;
@@ -283,7 +295,26 @@ void enqueue_part(pic_sim* s, int part, cudaStream_t st) {
         }
         break;
     case kPartPost:
-        if (!fp64) mixed_enqueue(s->mixed, st, 2);
+        if (!fp64) {
+            mixed_enqueue(s->mixed, st, 2);  // the injector's pairs, then the bin swap
+        } else if (s->hgrids[0].inject) {
+            Fp64InjectArgs in{};
+            in.grids = s->dgrids;
+            in.segs = s->dsegs;
+            for (int sp = 0; sp < 2; sp++) {
+                in.cap[sp] = s->pcap[sp];
+                in.x[sp] = s->pa[sp][0];
+                in.y[sp] = s->pa[sp][1];
+                in.ux[sp] = s->pa[sp][2];
+                in.uy[sp] = s->pa[sp][3];
+                in.uz[sp] = s->pa[sp][4];
+            }
+            in.st = s->st;
+            in.ny = s->hgrids[0].ny;
+            const GridDev& G = s->hgrids[0];
+            in.kmax = (long long)std::ceil(G.ppc * (1.0 + std::sqrt(1.0 - 1.0 / (G.gamma0 * G.gamma0))) * G.cfl) + 1;
+            launch_inject_fp64(in, st);
+        }
         break;
     case kPartEnd:
         launch_step_end(a, st);
@@ -455,6 +486,64 @@ int run_step_direct(pic_sim* s) {
     launch_field_update(a, st);
     enqueue_part(s, kPartEnd, st);
     CK(cudaGetLastError());
+    return PIC_OK;
+}
+
+// Pairs per species the moving injector can add over a whole run (it stops at x = nx).
+long long inj_capacity(const GridDev& G) {
+    if (!G.inject) return 0;
+    const double w = (1.0 + std::sqrt(1.0 - 1.0 / (G.gamma0 * G.gamma0))) * G.cfl;
+    const double steps = std::ceil((G.nx - G.inj_x0) / G.cfl) + 1.0;
+    return (long long)G.ny * ((long long)std::ceil(G.ppc * w * steps) + 2);
+}
+
+// FP64 particle arrays of species sp with room for at least `need` particles, `n`
+// of them live (contents kept when growing), and the push segment covering them: with
+// the injector the segment covers the whole capacity and its count grows on the device.
+int fp64_arrays(pic_sim* s, int sp, long long need, long long n) {
+    if (need > s->pcap[sp]) {
+        double* na[5] = {nullptr, nullptr, nullptr, nullptr, nullptr};
+        for (int a = 0; a < 5; a++) {
+            if (dalloc(&na[a], (size_t)need) != cudaSuccess) {
+                cudaGetLastError();
+                for (int b = 0; b < 5; b++) dfree(na[b]);
+                return fail(s, PIC_ENOMEM, "particle allocation failed");
+            }
+            if (s->pa[sp][a] && s->np[sp])
+                CK(cudaMemcpy(na[a], s->pa[sp][a], s->np[sp] * sizeof(double), cudaMemcpyDeviceToDevice));
+            dfree(s->pa[sp][a]);
+            s->pa[sp][a] = na[a];
+        }
+        s->pcap[sp] = need;
+    }
+    const bool inj = s->hgrids[0].inject != 0;
+    SegDev seg{};
+    seg.start = 0;
+    seg.count = n;
+    seg.grid = 0;
+    seg.species = sp;
+    seg.blk_first = 0;
+    seg.nblk = (int)(((inj ? s->pcap[sp] : n) + kPushThreads - 1) / kPushThreads);
+    s->nblk_push[sp] = seg.nblk;
+    s->np[sp] = n;
+    CK(cudaMemcpy(s->dsegs + sp, &seg, sizeof seg, cudaMemcpyHostToDevice));
+    dfree(s->dblk_seg[sp]);
+    s->dblk_seg[sp] = nullptr;
+    if (seg.nblk) {
+        std::vector<int> t(seg.nblk, 0);
+        CK(dalloc(&s->dblk_seg[sp], seg.nblk));
+        CK(cudaMemcpy(s->dblk_seg[sp], t.data(), seg.nblk * sizeof(int), cudaMemcpyHostToDevice));
+    }
+    return PIC_OK;
+}
+
+// Live FP64 particle counts after steps that may have injected.
+int fp64_counts(pic_sim* s) {
+    if (s->prm.precision != PIC_FP64 || !s->hgrids[0].inject) return PIC_OK;
+    SegDev seg[2];
+    CK(cudaMemcpy(seg, s->dsegs, sizeof seg, cudaMemcpyDeviceToHost));
+    s->np[0] = seg[0].count;
+    s->np[1] = seg[1].count;
     return PIC_OK;
 }
 
@@ -639,6 +728,11 @@ int init_handle(const pic_params* prm, int n, pic_sim** out) {
     A(cudaMemcpy(s->dgrids, s->hgrids.data(), s->ngrids * sizeof(GridDev), cudaMemcpyHostToDevice));
     A(cudaMemcpy(s->dblk_grid, s->hblk_grid.data(), s->nblk * sizeof(int), cudaMemcpyHostToDevice));
     A(cudaDeviceSynchronize());
+    if (e == cudaSuccess && prm[0].precision == PIC_FP64 && s->hgrids[0].inject) {
+        // room for the injector's pairs even in a species that is never loaded
+        for (int sp = 0; sp < 2; sp++)
+            if (int rc = fp64_arrays(s, sp, inj_capacity(s->hgrids[0]), 0)) return bail(rc);
+    }
     if (e != cudaSuccess) {
         s->err = std::string("initialisation failed: ") + cudaGetErrorString(e);
         cudaGetLastError();
@@ -732,6 +826,10 @@ void pic_params_default(pic_params* p) {
     p->tile_x = 0;
     p->tile_y = 0;
     p->bin_slack = 0.0;
+    p->bc_x = PIC_BC_PERIODIC;
+    p->inject_x0 = -1.0;
+    p->u_th = 0.0;
+    p->seed = 0;
 }
 
 int pic_init(const pic_params* prm, pic_sim** out) { return init_handle(prm, 1, out); }
@@ -854,21 +952,9 @@ int pic_load_particles(pic_sim* s, int32_t sp, const double* x, const double* y,
         if (rc == PIC_OK) rc = finish_call(s);
         return rc;
     }
-    // FP64: (re)allocate exactly n per array
-    if (n > s->pcap[sp]) {
-        for (int a = 0; a < 5; a++) {
-            dfree(s->pa[sp][a]);
-            s->pa[sp][a] = nullptr;
-        }
-        s->pcap[sp] = 0;
-        for (int a = 0; a < 5; a++) {
-            if (dalloc(&s->pa[sp][a], (size_t)n) != cudaSuccess) {
-                cudaGetLastError();
-                return fail(s, PIC_ENOMEM, "particle allocation failed");
-            }
-        }
-        s->pcap[sp] = n;
-    }
+    // FP64: arrays for n particles (plus what the injector can add)
+    s->np[sp] = 0;
+    if (int rc = fp64_arrays(s, sp, n + inj_capacity(s->hgrids[0]), 0)) return rc;
     const double* src[5] = {x, y, ux, uy, uz};
     for (int a = 0; a < 5; a++)
         if (n) CK(cudaMemcpyAsync(s->pa[sp][a], src[a], n * sizeof(double), cudaMemcpyDefault, s->stream));
@@ -885,26 +971,10 @@ int pic_load_particles(pic_sim* s, int32_t sp, const double* x, const double* y,
     CK(cudaStreamSynchronize(s->stream));
     if (hbad) {
         s->np[sp] = 0;
+        fp64_arrays(s, sp, 0, 0);
         return fail(s, PIC_EINVAL, "non-finite particle position or momentum, or a position outside the walls");
     }
-    s->np[sp] = n;
-    SegDev seg{};
-    seg.start = 0;
-    seg.count = n;
-    seg.grid = 0;
-    seg.species = sp;
-    seg.blk_first = 0;
-    seg.nblk = (int)((n + kPushThreads - 1) / kPushThreads);
-    s->nblk_push[sp] = seg.nblk;
-    CK(cudaMemcpy(s->dsegs + sp, &seg, sizeof seg, cudaMemcpyHostToDevice));
-    dfree(s->dblk_seg[sp]);
-    s->dblk_seg[sp] = nullptr;
-    if (seg.nblk) {
-        std::vector<int> t(seg.nblk, 0);
-        CK(dalloc(&s->dblk_seg[sp], seg.nblk));
-        CK(cudaMemcpy(s->dblk_seg[sp], t.data(), seg.nblk * sizeof(int), cudaMemcpyHostToDevice));
-    }
-    return PIC_OK;
+    return fp64_arrays(s, sp, 0, n);
 }
 
 int pic_set_fields(pic_sim* s, int32_t which, const double* data, size_t len) {
@@ -955,6 +1025,7 @@ int pic_step(pic_sim* s, int32_t n) {
     CK(cudaMemcpyAsync(&hs, s->st, sizeof hs, cudaMemcpyDeviceToHost, s->stream));
     if (int rc = finish_call(s)) return rc;
     s->steps += (long long)(hs.steps_done - steps0);
+    if (int rc0 = fp64_counts(s)) return rc0;
     int rc = device_errors(s, hs);
     if (rc == PIC_OK && s->prm.precision == PIC_MIXED32) rc = mixed_after_steps(s->mixed, s->stream, s->err);
     return rc;
@@ -1003,6 +1074,7 @@ int pic_profile(pic_sim* s, int32_t n, double* out, int32_t n_out) {
     CK(cudaMemcpyAsync(&hs, s->st, sizeof hs, cudaMemcpyDeviceToHost, s->stream));
     CK(cudaStreamSynchronize(s->stream));
     s->steps += (long long)(hs.steps_done - steps0);
+    if (int rc0 = fp64_counts(s)) return rc0;
     acc[4] = (double)(c1.total_iters - c0.total_iters);
     for (int a = 0; a < n_out && a < 5; a++) out[a] = acc[a] / n;
     int rc = device_errors(s, hs);

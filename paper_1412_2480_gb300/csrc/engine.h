@@ -86,4 +86,17 @@ struct Fp64PushArgs {
 // One launch over all blocks of the table; every segment must have shape order `order`.
 void launch_push_fp64(const Fp64PushArgs& a, int order, cudaStream_t s);
 
+// The moving injector's pairs of the current step for the FP64 particle arrays (one
+// simulation; segment counts grow on the device).
+struct Fp64InjectArgs {
+    const GridDev* grids;
+    SegDev* segs;          // [2], count incremented
+    long long cap[2];      // allocated slots per species
+    double *x[2], *y[2], *ux[2], *uy[2], *uz[2];
+    DevStatus* st;
+    int ny;
+    long long kmax;        // most pairs per row in one step
+};
+void launch_inject_fp64(const Fp64InjectArgs& a, cudaStream_t s);
+
 }  // namespace pic

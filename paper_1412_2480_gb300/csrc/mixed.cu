@@ -36,6 +36,7 @@
 #include <vector>
 
 #include "esirkepov.cuh"
+#include "inject.cuh"
 #include "mixed.h"
 
 namespace pic {
@@ -101,6 +102,11 @@ struct MixedState {
     size_t smem[4] = {0, 0, 0, 0};  // dynamic shared memory of each order's launch
     int pblocks[4] = {0, 0, 0, 0};  // persistent CTAs of each order's launch
     std::vector<long long> n;     // live particles [2 g + species]
+    unsigned long long* injected = nullptr;  // device [2 ngrids]: pairs added by the injector
+    int inject_grids = 0;         // simulations with an injector
+    long long inject_threads = 0; // rows x most pairs per row, over those simulations
+    int* inj_grid = nullptr;      // device [inject_grids]: their indices
+    long long* inj_first = nullptr;  // device [inject_grids + 1]: first thread of each
     long long rebins = 0;
     long long gen = 0;  // allocation generation of the bin buffers
 };
@@ -536,6 +542,56 @@ k_push_overflow(const MixedArgs a) {
     }
 }
 
+// The injector's pairs of this step, straight into the next buffer: the stayer segment
+// of the tile holding their cell (the tile kernels have finished with it), or the
+// overflow list when it is full. One thread per (simulation, row, pair).
+__global__ void k_inject_mixed(const MixedArgs a, const int* inj_grid, const long long* inj_first, int ngr,
+                               unsigned long long* injected) {
+    DevStatus* st = a.st;
+    if (st->stop) return;
+    const long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    int q = 0;
+    while (q + 1 < ngr && t >= inj_first[q + 1]) q++;
+    if (t >= inj_first[ngr]) return;
+    const int g = inj_grid[q];
+    const GridDev& G = a.grids[g];
+    const long long local = t - inj_first[q];
+    const long long kmax = (long long)ceil(G.ppc * inj_width(G)) + 1;
+    const int j = (int)(local / kmax);
+    const long long k = local - (long long)j * kmax;
+    const long long n = (long long)st->steps_done - 1;
+    if (j >= G.ny || k >= inj_count(G, n)) return;
+    double x, y;
+    inj_position(G, n, j, k, x, y);
+    int ci = (int)floor(x);
+    float ox = (float)(x - ci);
+    if (ox >= 1.f) {
+        ox = 0.f;
+        ci += 1;
+    }
+    if (ci < 0 || ci >= G.nx) return;  // (the plane starts at least two cells from the wall)
+    const int cj = j;
+    const float oy = (float)(y - cj);
+    const int nxp = (int)st->parity ^ 1;
+    unsigned* nxt = nxp ? a.buf[1] : a.buf[0];
+    int* cnxt = nxp ? a.cnt[1] : a.cnt[0];
+    const int lt = (cj / G.ty) * G.ntx + ci / G.tx;
+    const long long stride = bin_stride(G);
+    for (int s = 0; s < 2; s++) {
+        double u[3];
+        inj_momentum(G, n, j, k, s, u);
+        const float uf[3] = {(float)u[0], (float)u[1], (float)u[2]};
+        const int cell = ci | (cj << 16);
+        const int slot = atomicAdd(&cnxt[((long long)(G.tile_first + lt) * 2 + s) * kSegs], 1);
+        if (slot < G.cap)
+            put(nxt, G.bin_off + ((long long)lt * 2 + s) * stride + slot, cell, ox, oy, uf);
+        else
+            to_overflow(nxp ? a.ovf[1].p : a.ovf[0].p, nxp ? a.ovf[1].gs : a.ovf[0].gs, a.ovf_cap, st, nxp,
+                        cell, ox, oy, uf[0], uf[1], uf[2], s | (g << 1));
+        atomicAdd(&injected[2 * g + s], 1ull);
+    }
+}
+
 __global__ void k_mixed_swap(DevStatus* st) {
     if (threadIdx.x == 0 && !st->stop) st->parity ^= 1u;
 }
@@ -929,6 +985,8 @@ int place_all(MixedState* m, int par, Staged& A, std::vector<long long> cap, std
     if (rc) return rc;
     MCK(cudaMemcpyAsync((void*)m->dgrids, m->G, m->ngrids * sizeof(GridDev), cudaMemcpyHostToDevice, st));
     MCK(cudaMemsetAsync(&m->st->ovf_count, 0, sizeof(DevStatus::ovf_count), st));
+    // the counts now come from the bins themselves, injected pairs included
+    MCK(cudaMemsetAsync(m->injected, 0, 2 * m->ngrids * sizeof(unsigned long long), st));
     MCK(cudaStreamSynchronize(st));
     for (int q = 0; q < 2 * m->ngrids; q++) m->n[q] = A.n[q];
     return PIC_OK;
@@ -1032,6 +1090,29 @@ int mixed_create(MixedState** out, const pic_params* p, int ngrids, GridDev* G,
         if (e == cudaSuccess) e = dalloc(&m->ovf[q].p, (size_t)m->ovf_cap * kFields);
         if (e == cudaSuccess) e = dalloc(&m->ovf[q].gs, (size_t)m->ovf_cap);
     }
+    // injector tables
+    {
+        std::vector<int> ig;
+        std::vector<long long> first(1, 0);
+        for (int g = 0; g < ngrids; g++) {
+            if (!G[g].inject) continue;
+            const double w = (1.0 + std::sqrt(1.0 - 1.0 / (G[g].gamma0 * G[g].gamma0))) * G[g].cfl;
+            const long long kmax = (long long)std::ceil(G[g].ppc * w) + 1;
+            ig.push_back(g);
+            first.push_back(first.back() + (long long)G[g].ny * kmax);
+        }
+        m->inject_grids = (int)ig.size();
+        m->inject_threads = first.back();
+        if (e == cudaSuccess) e = dalloc(&m->injected, (size_t)2 * ngrids);
+        if (e == cudaSuccess) e = cudaMemset(m->injected, 0, 2 * ngrids * sizeof(unsigned long long));
+        if (e == cudaSuccess && !ig.empty()) {
+            e = dalloc(&m->inj_grid, ig.size());
+            if (e == cudaSuccess) e = dalloc(&m->inj_first, first.size());
+            if (e == cudaSuccess) e = cudaMemcpy(m->inj_grid, ig.data(), ig.size() * sizeof(int), cudaMemcpyHostToDevice);
+            if (e == cudaSuccess)
+                e = cudaMemcpy(m->inj_first, first.data(), first.size() * sizeof(long long), cudaMemcpyHostToDevice);
+        }
+    }
     if (e == cudaSuccess) e = dalloc(&m->tile_grid, (size_t)ntiles);
     if (e == cudaSuccess) e = dalloc(&m->tlist, (size_t)ntiles);
     if (e == cudaSuccess) e = dalloc(&m->work, 4);
@@ -1087,7 +1168,7 @@ void mixed_destroy(MixedState* m) {
         for (void* q : ps)
             if (q) cudaFree(q);
     }
-    void* ps[] = {m->tile_grid, m->tlist, m->work};
+    void* ps[] = {m->tile_grid, m->tlist, m->work, m->injected, m->inj_grid, m->inj_first};
     for (void* q : ps)
         if (q) cudaFree(q);
     delete m;
@@ -1167,6 +1248,9 @@ void mixed_enqueue(MixedState* m, cudaStream_t st, int part) {
             }
         }
     } else {
+        if (m->inject_grids)
+            k_inject_mixed<<<(unsigned)((m->inject_threads + 255) / 256), 256, 0, st>>>(
+                make_args(m, 0), m->inj_grid, m->inj_first, m->inject_grids, m->injected);
         k_mixed_swap<<<1, 32, 0, st>>>(m->st);
     }
 }
@@ -1176,6 +1260,13 @@ int mixed_before_steps(MixedState*, cudaStream_t, std::string&) { return PIC_OK;
 int mixed_after_steps(MixedState* m, cudaStream_t st, std::string& err) {
     DevStatus hs{};
     if (int rc = read_status(m, hs, st, err)) return rc;
+    if (m->inject_grids) {  // the injector's pairs join the live counts
+        std::vector<unsigned long long> add((size_t)2 * m->ngrids);
+        MCK(cudaMemcpyAsync(add.data(), m->injected, add.size() * sizeof(unsigned long long), cudaMemcpyDeviceToHost, st));
+        MCK(cudaMemsetAsync(m->injected, 0, add.size() * sizeof(unsigned long long), st));
+        MCK(cudaStreamSynchronize(st));
+        for (size_t q = 0; q < add.size(); q++) m->n[q] += (long long)add[q];
+    }
     const int par = (int)hs.parity;
     if (hs.ovf_count[par] == 0) return PIC_OK;
     // particles are parked in the overflow list: re-sort with room to spare. Grow each

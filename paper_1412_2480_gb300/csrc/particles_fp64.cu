@@ -6,6 +6,7 @@
 // Positions are kept in grid units (x/dx, y/dy) in [0, nx) x [0, ny).
 #include "engine.h"
 #include "esirkepov.cuh"
+#include "inject.cuh"
 
 namespace pic {
 namespace {
@@ -136,7 +137,44 @@ k_push_fp64(const GridDev* __restrict__ grids, const SegDev* __restrict__ segs,
     if (threadIdx.x == 0 && s != 0.0) atomicAdd(&cg[S.grid].uk, s);
 }
 
+// The injector's pairs of this step appended to the species arrays (one thread per
+// row and pair); their slots come from the segment counts, so the order is arbitrary.
+__global__ void k_inject_fp64(const Fp64InjectArgs a) {
+    const DevStatus* st = a.st;
+    if (st->stop) return;
+    const GridDev& G = a.grids[0];
+    const long long n = (long long)st->steps_done - 1;
+    const long long per_row = inj_count(G, n);
+    const long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    const int j = (int)(t / a.kmax);
+    const long long k = t - (long long)j * a.kmax;
+    if (j >= G.ny || k >= per_row) return;
+    double x, y;
+    inj_position(G, n, j, k, x, y);
+    for (int s = 0; s < 2; s++) {
+        double u[3];
+        inj_momentum(G, n, j, k, s, u);
+        const unsigned long long idx =
+            atomicAdd(reinterpret_cast<unsigned long long*>(&a.segs[s].count), 1ull);
+        if ((long long)idx >= a.cap[s]) {
+            atomicAdd(&a.st->lost, 1ull);  // arrays full: the step fails with PIC_ENOMEM
+            a.st->stop_next = 1u;
+            continue;
+        }
+        a.x[s][idx] = x;
+        a.y[s][idx] = y;
+        a.ux[s][idx] = u[0];
+        a.uy[s][idx] = u[1];
+        a.uz[s][idx] = u[2];
+    }
+}
+
 }  // namespace
+
+void launch_inject_fp64(const Fp64InjectArgs& a, cudaStream_t s) {
+    const long long threads = (long long)a.ny * a.kmax;
+    k_inject_fp64<<<(unsigned)((threads + 255) / 256), 256, 0, s>>>(a);
+}
 
 void launch_push_fp64(const Fp64PushArgs& a, int order, cudaStream_t s) {
     if (a.nblk == 0) return;

@@ -33,6 +33,10 @@ struct GridDev {
     int maxit, warm;      // warm: 0 zero guess, 1 previous dB, 2 learned guess
     int deposit;          // 0 in test-particle mode
     int walls;            // conducting, reflecting walls at x = 0 and x = nx dx (else periodic)
+    // moving injector (walls only; include/pic.h)
+    int inject, ppc;
+    double inj_x0, cfl, gamma0, u_th;
+    unsigned long long inj_seed;
     // MIXED32 tiling
     int tx, ty, ntx, nty; // tile size and tile counts
     int tile_first, ntiles;

@@ -99,3 +99,48 @@ def test_walls_validation_and_set_fields_zeroes_the_wall():
         assert e.value.code == pic.PIC_EINVAL
     finally:
         pic.pic_free(h)
+
+
+def injector_setup(nx, ny, ppc, gamma0, seed):
+    """The shock set-up with the moving injector: the magnetised beam behind the plane
+    (x < x0), the fields of the beam everywhere (a static vacuum solution ahead)."""
+    x0 = 12.0
+    w, sp, F0 = inputs.shock_beam(nx, ny, ppc, gamma0, 1e-3, seed=seed, sigma_b=0.1)
+    for d in sp:
+        keep = d["x"] < x0
+        for key in ("x", "y", "ux", "uy", "uz"):
+            d[key] = np.ascontiguousarray(d[key][keep])
+    inj = dict(x0=x0, ppc=ppc, gamma0=gamma0, u_th=1e-3, seed=11)
+    return w, sp, F0, inj
+
+
+def run_oracle_injected(nx, ny, w, sp, F0, steps, order, inj):
+    import oracle
+    species = [oracle.Species(d["qm"], w, d["x"], d["y"], d["ux"], d["uy"], d["uz"]) for d in sp]
+    sim = oracle.OracleSim(nx, ny, 1.0, 0.5, order, species, cg_rtol=1e-12, fields=F0, walls=True,
+                           injector=inj)
+    sim.step(steps)
+    return sim
+
+
+@pytest.mark.parametrize("precision", [pic.PIC_FP64, pic.PIC_MIXED32])
+def test_moving_injector_matches_oracle(precision):
+    nx, ny, ppc, steps, gamma0 = 64, 16, 4, 30, 10.0
+    w, sp, F0, inj = injector_setup(nx, ny, ppc, gamma0, seed=9)
+    kw = {} if precision == pic.PIC_FP64 else {"tile_x": 16, "tile_y": 8}
+    Fg, pg, mom = run_gpu(nx, ny, ppc, sp, F0, steps, 2, gamma0=gamma0, cg_rtol=1e-12,
+                          precision=precision, bc_x=pic.PIC_BC_WALLS, inject_x0=inj["x0"],
+                          u_th=inj["u_th"], seed=inj["seed"], **kw)
+    sim = run_oracle_injected(nx, ny, w, sp, F0, steps, 2, inj)
+    n_o = sim.species[0].n
+    assert n_o > sum(d["x"].size for d in sp[:1])  # the injector added pairs
+    assert mom["n_particles"] == (n_o, n_o)
+    tol = 1e-9 if precision == pic.PIC_FP64 else 1e-3
+    Fo = sim.fields()
+    for c in range(6):
+        assert rel(Fg[c], Fo[c]) < tol, f"field {c}: {rel(Fg[c], Fo[c]):.2e}"
+    for s in range(2):
+        g = sorted_particles(pg[s])
+        o = sorted_particles(np.stack([sim.species[s].x, sim.species[s].y, sim.species[s].ux,
+                                       sim.species[s].uy, sim.species[s].uz]))
+        assert rel(g, o) < (1e-10 if precision == pic.PIC_FP64 else 1e-4)

@@ -188,3 +188,57 @@ def test_gauss_law_holds_off_the_wall_with_reflecting_plasma():
     assert np.abs(gauss() - g0).max() < 1e-11
     for s in sim.species:
         assert s.x.min() >= 0 and s.x.max() < nx
+
+
+# ---- the moving injector ---------------------------------------------------------------
+
+def test_splitmix64_published_stream():
+    # the splitmix64 stream seeded with 0 (Steele, Lea & Flood 2014): its first outputs
+    z = np.array([0, 0x9E3779B97F4A7C15], dtype=np.uint64)
+    assert [int(v) for v in oracle.splitmix64(z)] == [0xE220A8397B1DCDAF, 0x6E789E6AA1B965F4]
+
+
+def test_injector_counts_positions_and_momenta():
+    nx, ny, cfl, x0, ppc, gamma0, u_th = 400, 16, 1.0, 4.0, 8, 10.0, 0.05
+    w = (1 + math.sqrt(1 - 1 / gamma0 ** 2)) * cfl
+    total, xs, mom = 0, [], []
+    for n in range(300):
+        new = oracle.inject_pairs(n, nx, ny, cfl, x0, ppc, gamma0, u_th, seed=7)
+        xf = x0 + (n + 1) * cfl
+        assert new is not None
+        x, y, m = new
+        total += x.size // ny
+        assert total == math.floor(ppc * w * (n + 1))  # the beam's density over time
+        assert np.all((x >= xf - w) & (x < xf)) and np.all(np.floor(y) == np.repeat(np.arange(ny), x.size // ny))
+        xs.append((x - (xf - w)) / w)
+        mom.append(m[0])
+    assert oracle.inject_pairs(int(nx - x0), nx, ny, cfl, x0, ppc, gamma0, u_th, 7) is None
+    u = np.concatenate(xs)
+    assert abs(u.mean() - 0.5) < 0.01 and abs(u.var() - 1 / 12) < 0.003
+    ux = np.concatenate([m[0] for m in mom])
+    uy = np.concatenate([m[1] for m in mom])
+    # back to the beam frame: u'x = gamma0 (ux + beta0 gamma) with ux toward -x
+    beta0 = math.sqrt(1 - 1 / gamma0 ** 2)
+    uz = np.concatenate([m[2] for m in mom])
+    gam = np.sqrt(1 + ux ** 2 + uy ** 2 + uz ** 2)
+    upx = -gamma0 * (ux + beta0 * gam)
+    for comp in (upx, uy, uz):
+        assert abs(comp.mean()) < 0.05 * u_th and abs(comp.std() / u_th - 1) < 0.05
+
+
+def test_injected_beam_keeps_gauss_law():
+    nx, ny, ppc = 48, 12, 4
+    F = np.zeros((6, ny, nx))
+    sim = oracle.OracleSim(nx, ny, 1.0, 0.5, 2, [oracle.Species(q, 0.05, [], [], [], [], []) for q in (1.0, -1.0)],
+                           cg_rtol=1e-13, fields=F, walls=True,
+                           injector=dict(x0=4.0, ppc=ppc, gamma0=5.0, u_th=0.1, seed=3))
+
+    def gauss():
+        return (oracle.div_E(sim.g, sim.F) - 4 * math.pi * sim.rho()).reshape(ny, nx)[:, 1:]
+
+    g0 = gauss()
+    for _ in range(25):
+        sim.step()
+    assert sim.species[0].n > 0 and sim.species[0].n == sim.species[1].n
+    assert np.abs(gauss() - g0).max() < 1e-11
+    assert sim.species[0].x.max() < nx
