@@ -120,6 +120,7 @@ extern "C" {
 #define PIC_RHSX 12 /* right-hand side b of Eq. (7) of the last step (PIC_MIXED32 only) */
 #define PIC_RHSY 13
 #define PIC_RHSZ 14
+#define PIC_RHO 15  /* node charge density of the current particles (computed on demand) */
 
 typedef struct pic_params {
     int32_t nx, ny;        /* cells (Sec. 3: 128 x 128; Sec. 4: 5650 x 990); >= 8 each */
@@ -248,7 +249,7 @@ PIC_API int pic_step(pic_sim* s, int32_t n);
  * Device-detected errors are reported as by pic_step. */
 PIC_API int pic_profile(pic_sim* s, int32_t n, double* out, int32_t n_out);
 
-/* Copy grid quantity `which` (PIC_EX..PIC_RHSZ) into out (len >= nx*ny FP64 values,
+/* Copy grid quantity `which` (PIC_EX..PIC_RHO) into out (len >= nx*ny FP64 values,
  * host or device, caller-owned). */
 PIC_API int pic_fields(pic_sim* s, int32_t which, double* out, size_t len);
 
@@ -365,6 +366,27 @@ PIC_API int pic_set_cnn(pic_sim* s, const pic_cnn* c);
  * multiples of 16 in [16, 256]). Errors are reported through pic_cnn_last_error(NULL). */
 PIC_API int pic_tc_gemm_bf16(int32_t M, int32_t N, int32_t K, const uint16_t* A, const uint16_t* B,
                              float* D);
+
+/* Conservation diagnostics of the selected simulation, computed on demand from the
+ * particles and fields (a pass over all particles: not for every step): up to n_out of
+ *   out[0..2] total momentum sum w u of both species (units of m c),
+ *   out[3]    total charge sum rho dx dy,
+ *   out[4]    max |div E - 4 pi rho| over the nodes (off the wall column with walls),
+ *   out[5]    its root mean square.
+ * With charge-conserving deposits out[4] stays at its initial value to round-off. */
+PIC_API int pic_conservation(pic_sim* s, double* out, int32_t n_out);
+
+/* Checkpoints. pic_save writes every simulation of the handle to `path`: its parameters,
+ * E, B, the last dB (the previous-step warm start), both species' particles (FP64
+ * physical positions and momenta) and the step counters (the injector's schedule
+ * follows them). pic_restore reads such a file into a handle created with the same
+ * parameters (same precision and number of simulations; PIC_EINVAL otherwise) and
+ * replaces its state. The file is read and checked in full first: an unreadable,
+ * truncated or mismatched file gives PIC_EINVAL and leaves the handle unchanged.
+ * MIXED32 particles round-trip exactly when dx = dy = 1. PCG statistics and a learned
+ * network are not saved. */
+PIC_API int pic_save(pic_sim* s, const char* path);
+PIC_API int pic_restore(pic_sim* s, const char* path);
 
 /* Message of the last failure on this handle (or of the last failed pic_init when s
  * is NULL). The string stays valid until the next call on the handle. */

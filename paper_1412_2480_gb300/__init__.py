@@ -42,6 +42,7 @@ PIC_BC_WALLS = 1
 PIC_EX, PIC_EY, PIC_EZ, PIC_BX, PIC_BY, PIC_BZ = range(6)
 PIC_JX, PIC_JY, PIC_JZ, PIC_DBX, PIC_DBY, PIC_DBZ = range(6, 12)
 PIC_RHSX, PIC_RHSY, PIC_RHSZ = range(12, 15)
+PIC_RHO = 15
 
 EXPORTED = ("pic_params_default", "pic_init", "pic_init_batch", "pic_select", "pic_batch_size",
             "pic_autotune_tiles", "pic_set_stream", "pic_load_particles", "pic_set_fields",
@@ -49,7 +50,8 @@ EXPORTED = ("pic_params_default", "pic_init", "pic_init_batch", "pic_select", "p
             "pic_particles", "pic_field_solve_noalloc", "pic_last_error", "pic_free",
             "pic_cnn_create", "pic_cnn_free", "pic_cnn_last_error", "pic_cnn_set_params",
             "pic_cnn_get_params", "pic_cnn_forward", "pic_cnn_gradient", "pic_cnn_train_step",
-            "pic_cnn_stencil", "pic_set_cnn", "pic_tc_gemm_bf16")
+            "pic_cnn_stencil", "pic_set_cnn", "pic_tc_gemm_bf16", "pic_conservation", "pic_save",
+            "pic_restore")
 
 
 class pic_params(C.Structure):
@@ -128,6 +130,11 @@ def lib():
             L.pic_cnn_train_step.argtypes = [vp, C.c_int32, C.c_int32, C.c_int32, vp, vp, C.c_float,
                                              C.POINTER(C.c_double)]
             L.pic_set_cnn.argtypes = [vp, vp]
+            L.pic_conservation.argtypes = [vp, C.POINTER(C.c_double), C.c_int32]
+            L.pic_save.argtypes = [vp, C.c_char_p]
+            L.pic_restore.argtypes = [vp, C.c_char_p]
+            for name in ("pic_conservation", "pic_save", "pic_restore"):
+                getattr(L, name).restype = C.c_int
             L.pic_cnn_stencil.argtypes = [vp, vp, C.c_int64]
             L.pic_tc_gemm_bf16.argtypes = [C.c_int32, C.c_int32, C.c_int32, vp, vp, vp]
             for name in ("pic_cnn_create", "pic_cnn_set_params", "pic_cnn_get_params", "pic_cnn_forward",
@@ -283,6 +290,22 @@ def pic_particles(h, species, out=None):
         out = np.empty((5, n), dtype=np.float64)
     _check(lib().pic_particles(h, species, _ptr(out, True), n), h)
     return out
+
+
+def pic_conservation(h) -> dict:
+    """Momentum, charge and Gauss-law residual of the selected simulation (see pic.h)."""
+    out = (C.c_double * 6)()
+    _check(lib().pic_conservation(h, out, 6), h)
+    return {"momentum": (out[0], out[1], out[2]), "charge": out[3], "gauss_max": out[4],
+            "gauss_rms": out[5]}
+
+
+def pic_save(h, path) -> None:
+    _check(lib().pic_save(h, os.fsencode(path)), h)
+
+
+def pic_restore(h, path) -> None:
+    _check(lib().pic_restore(h, os.fsencode(path)), h)
 
 
 def pic_last_error(h) -> str:

@@ -547,6 +547,21 @@ int fp64_counts(pic_sim* s) {
     return PIC_OK;
 }
 
+// Node charge density of the selected simulation into rho (device, ncell values) and,
+// when mom is given, w * its total momentum added into mom (device, 3 values).
+int charge_density(pic_sim* s, double* rho, double* mom = nullptr) {
+    const GridDev& G = s->hgrids[s->sel];
+    CK(cudaMemsetAsync(rho, 0, G.ncell * sizeof(double), s->stream));
+    if (s->mixed) return mixed_rho_momentum(s->mixed, s->sel, rho, mom, s->stream, s->err);
+    for (int sp = 0; sp < 2; sp++) {
+        if (!s->np[sp]) continue;
+        launch_rho_fp64(G, s->pa[sp][0], s->pa[sp][1], s->np[sp], G.qw[sp] / (G.dx * G.dy), rho, s->stream);
+        if (mom) launch_momentum_fp64(s->pa[sp][2], s->pa[sp][3], s->pa[sp][4], s->np[sp], G.w, mom, s->stream);
+    }
+    CK(cudaGetLastError());
+    return PIC_OK;
+}
+
 int check_species(pic_sim* s, int sp) {
     if (sp < 0 || sp > 1) return fail(s, PIC_EINVAL, "species must be 0 (positrons) or 1 (electrons)");
     return PIC_OK;
@@ -1085,8 +1100,9 @@ int pic_profile(pic_sim* s, int32_t n, double* out, int32_t n_out) {
 int pic_fields(pic_sim* s, int32_t which, double* out, size_t len) {
     if (!s) return PIC_EINVAL;
     cudaSetDevice(s->device);
-    if (which < PIC_EX || which > PIC_RHSZ) return fail(s, PIC_EINVAL, "which must be PIC_EX..PIC_RHSZ");
-    if (which >= PIC_RHSX && !s->bvec) return fail(s, PIC_ESTATE, "the right-hand side is kept in PIC_MIXED32 only");
+    if (which < PIC_EX || which > PIC_RHO) return fail(s, PIC_EINVAL, "which must be PIC_EX..PIC_RHO");
+    if (which >= PIC_RHSX && which <= PIC_RHSZ && !s->bvec)
+        return fail(s, PIC_ESTATE, "the right-hand side is kept in PIC_MIXED32 only");
     const GridDev& G = s->hgrids[s->sel];
     const long long nc = G.ncell, off = G.cell_off;
     if (!out || len < (size_t)nc) return fail(s, PIC_EINVAL, "out must hold nx*ny values");
@@ -1104,8 +1120,11 @@ int pic_fields(pic_sim* s, int32_t which, double* out, size_t len) {
         }
     } else if (which <= PIC_DBZ) {
         src = s->x + (which - PIC_DBX) * s->ntot + off;
-    } else {
+    } else if (which <= PIC_RHSZ) {
         src = s->bvec + (which - PIC_RHSX) * s->ntot + off;
+    } else {
+        if (int rc = charge_density(s, s->tmp)) return rc;
+        src = s->tmp;
     }
     CK(cudaMemcpyAsync(out, src, nc * sizeof(double), cudaMemcpyDefault, s->stream));
     return finish_call(s);
@@ -1176,6 +1195,179 @@ int pic_particles(pic_sim* s, int32_t sp, double* out, int64_t n) {
     cudaFree(t);
     if (e != cudaSuccess) return fail(s, PIC_ECUDA, std::string("pic_particles: ") + cudaGetErrorString(e));
     return PIC_OK;
+}
+
+int pic_conservation(pic_sim* s, double* out, int32_t n_out) {
+    if (!s) return PIC_EINVAL;
+    cudaSetDevice(s->device);
+    if (!out || n_out < 1) return fail(s, PIC_EINVAL, "out is NULL");
+    const GridDev& G = s->hgrids[s->sel];
+    double* mom = nullptr;
+    CK(dalloc(&mom, 3));
+    CK(cudaMemsetAsync(mom, 0, 3 * sizeof(double), s->stream));
+    int rc = charge_density(s, s->tmp, mom);
+    const long long nc = G.ncell;
+    std::vector<double> rho(nc), ex(nc), ey(nc);
+    double hm[3] = {0, 0, 0};
+    if (rc == PIC_OK) {
+        cudaError_t e = cudaMemcpyAsync(rho.data(), s->tmp, nc * sizeof(double), cudaMemcpyDeviceToHost, s->stream);
+        if (e == cudaSuccess)
+            e = cudaMemcpyAsync(ex.data(), s->F + G.cell_off, nc * sizeof(double), cudaMemcpyDeviceToHost, s->stream);
+        if (e == cudaSuccess)
+            e = cudaMemcpyAsync(ey.data(), s->F + s->ntot + G.cell_off, nc * sizeof(double), cudaMemcpyDeviceToHost,
+                                s->stream);
+        if (e == cudaSuccess) e = cudaMemcpyAsync(hm, mom, sizeof hm, cudaMemcpyDeviceToHost, s->stream);
+        if (e == cudaSuccess) e = cudaStreamSynchronize(s->stream);
+        if (e != cudaSuccess) rc = fail(s, PIC_ECUDA, std::string("pic_conservation: ") + cudaGetErrorString(e));
+    }
+    cudaFree(mom);
+    if (rc) return rc;
+    // Gauss's law on the nodes: div E - 4 pi rho (off the wall column with walls, where
+    // the conductor holds the surface charge)
+    double q = 0.0, mx = 0.0, ss = 0.0;
+    long long cnt = 0;
+    for (int j = 0; j < G.ny; j++)
+        for (int i = 0; i < G.nx; i++) {
+            const long long k = (long long)j * G.nx + i;
+            q += rho[k] * G.dx * G.dy;
+            if (G.walls && i == 0) continue;
+            const double exw = ex[(long long)j * G.nx + (i == 0 ? G.nx - 1 : i - 1)];
+            const double eys = ey[(long long)(j == 0 ? G.ny - 1 : j - 1) * G.nx + i];
+            const double r = (ex[k] - exw) * G.idx + (ey[k] - eys) * G.idy - 4.0 * kPi * rho[k];
+            mx = std::max(mx, std::fabs(r));
+            ss += r * r;
+            cnt++;
+        }
+    const double vals[6] = {hm[0], hm[1], hm[2], q, mx, cnt ? std::sqrt(ss / cnt) : 0.0};
+    for (int k = 0; k < n_out && k < 6; k++) out[k] = vals[k];
+    return PIC_OK;
+}
+
+// ---- checkpoints ----------------------------------------------------------------------
+namespace {
+constexpr char kSaveMagic[8] = {'P', 'I', 'C', 'S', 'T', 'A', 'T', 'E'};
+constexpr int32_t kSaveVersion = 1;
+
+bool same_problem(const pic_params& a, const pic_params& b) {
+    return a.nx == b.nx && a.ny == b.ny && a.dx == b.dx && a.dy == b.dy && a.cfl == b.cfl &&
+           a.theta == b.theta && a.shape_order == b.shape_order && a.gamma0 == b.gamma0 && a.ppc == b.ppc &&
+           a.skin_depth == b.skin_depth && a.precision == b.precision && a.bc_x == b.bc_x &&
+           a.inject_x0 == b.inject_x0 && a.u_th == b.u_th && a.seed == b.seed;
+}
+}  // namespace
+
+int pic_save(pic_sim* s, const char* path) {
+    if (!s) return PIC_EINVAL;
+    cudaSetDevice(s->device);
+    if (!path) return fail(s, PIC_EINVAL, "path is NULL");
+    DevStatus hs{};
+    CK(cudaMemcpyAsync(&hs, s->st, sizeof hs, cudaMemcpyDeviceToHost, s->stream));
+    CK(cudaStreamSynchronize(s->stream));
+    FILE* f = fopen(path, "wb");
+    if (!f) return fail(s, PIC_EINVAL, std::string("cannot open ") + path + " for writing");
+    const int sel0 = s->sel;
+    int rc = PIC_OK;
+    bool ok = fwrite(kSaveMagic, 1, 8, f) == 8;
+    const int32_t head[3] = {kSaveVersion, s->ngrids, s->prm.precision};
+    const int64_t steps[2] = {s->steps, (int64_t)hs.steps_done};
+    ok = ok && fwrite(head, sizeof head, 1, f) == 1 && fwrite(steps, sizeof steps, 1, f) == 1;
+    for (int g = 0; ok && rc == PIC_OK && g < s->ngrids; g++) {
+        s->sel = g;
+        const GridDev& G = s->hgrids[g];
+        ok = fwrite(&s->prms[g], sizeof(pic_params), 1, f) == 1;
+        std::vector<double> buf((size_t)G.ncell);
+        for (int c = 0; ok && c < 9; c++) {  // E, B, then the last dB (warm start)
+            const double* src = c < 6 ? s->F + c * s->ntot + G.cell_off : s->x + (c - 6) * s->ntot + G.cell_off;
+            if (cudaMemcpy(buf.data(), src, G.ncell * sizeof(double), cudaMemcpyDeviceToHost) != cudaSuccess) {
+                rc = fail(s, PIC_ECUDA, "pic_save: field copy failed");
+                break;
+            }
+            ok = fwrite(buf.data(), sizeof(double), buf.size(), f) == buf.size();
+        }
+        for (int sp = 0; ok && rc == PIC_OK && sp < 2; sp++) {
+            const int64_t n = pic_particle_count(s, sp);
+            std::vector<double> p((size_t)std::max<int64_t>(1, 5 * n));
+            if (n) rc = pic_particles(s, sp, p.data(), n);
+            ok = ok && fwrite(&n, sizeof n, 1, f) == 1 && (n == 0 || fwrite(p.data(), sizeof(double), 5 * n, f) == (size_t)(5 * n));
+        }
+    }
+    s->sel = sel0;
+    if (fclose(f) != 0) ok = false;
+    if (rc) return rc;
+    if (!ok) return fail(s, PIC_EINVAL, std::string("write to ") + path + " failed");
+    return PIC_OK;
+}
+
+int pic_restore(pic_sim* s, const char* path) {
+    if (!s) return PIC_EINVAL;
+    cudaSetDevice(s->device);
+    if (!path) return fail(s, PIC_EINVAL, "path is NULL");
+    // the whole file is read and checked before anything on the handle changes
+    struct Saved {
+        std::vector<double> fields;     // 9 x ncell: E, B, dB
+        std::vector<double> parts[2];   // 5 x n each
+        int64_t n[2];
+    };
+    std::vector<Saved> saved((size_t)s->ngrids);
+    int64_t steps[2];
+    {
+        FILE* f = fopen(path, "rb");
+        if (!f) return fail(s, PIC_EINVAL, std::string("cannot open ") + path);
+        std::string why;
+        char magic[8];
+        int32_t head[3];
+        if (fread(magic, 1, 8, f) != 8 || memcmp(magic, kSaveMagic, 8) != 0) why = "not a checkpoint file";
+        else if (fread(head, sizeof head, 1, f) != 1 || head[0] != kSaveVersion) why = "unknown checkpoint version";
+        else if (head[1] != s->ngrids || head[2] != s->prm.precision) why = "checkpoint of a different handle";
+        else if (fread(steps, sizeof steps, 1, f) != 1 || steps[0] < 0 || steps[1] < 0) why = "truncated file";
+        for (int g = 0; why.empty() && g < s->ngrids; g++) {
+            pic_params p{};
+            if (fread(&p, sizeof p, 1, f) != 1) { why = "truncated file"; break; }
+            if (!same_problem(p, s->prms[g])) { why = "simulation " + std::to_string(g) + " has other parameters"; break; }
+            Saved& v = saved[g];
+            const size_t nc = (size_t)s->hgrids[g].ncell;
+            v.fields.resize(9 * nc);
+            if (fread(v.fields.data(), sizeof(double), 9 * nc, f) != 9 * nc) { why = "truncated file"; break; }
+            for (int sp = 0; why.empty() && sp < 2; sp++) {
+                if (fread(&v.n[sp], sizeof(int64_t), 1, f) != 1 || v.n[sp] < 0 || v.n[sp] > ((int64_t)1 << 40)) {
+                    why = "truncated file";
+                    break;
+                }
+                v.parts[sp].resize((size_t)(5 * v.n[sp]));
+                if (fread(v.parts[sp].data(), sizeof(double), v.parts[sp].size(), f) != v.parts[sp].size())
+                    why = "truncated file";
+            }
+        }
+        fclose(f);
+        if (!why.empty()) return fail(s, PIC_EINVAL, "pic_restore: " + why);
+    }
+    const int sel0 = s->sel;
+    int rc = PIC_OK;
+    for (int g = 0; g < s->ngrids && rc == PIC_OK; g++) {
+        const GridDev& G = s->hgrids[g];
+        for (int c = 0; c < 9; c++) {
+            double* dst = c < 6 ? s->F + c * s->ntot + G.cell_off : s->x + (c - 6) * s->ntot + G.cell_off;
+            CK(cudaMemcpyAsync(dst, saved[g].fields.data() + c * G.ncell, G.ncell * sizeof(double),
+                               cudaMemcpyHostToDevice, s->stream));
+        }
+        s->sel = g;
+        for (int sp = 0; sp < 2 && rc == PIC_OK; sp++) {
+            const double* pp = saved[g].parts[sp].data();
+            const int64_t n = saved[g].n[sp];
+            rc = pic_load_particles(s, sp, pp, pp + n, pp + 2 * n, pp + 3 * n, pp + 4 * n, n);
+        }
+    }
+    s->sel = sel0;
+    if (rc) return rc;
+    // step counters (the injector's schedule follows them) and the FP32 field copies
+    DevStatus hs{};
+    CK(cudaMemcpyAsync(&hs, s->st, sizeof hs, cudaMemcpyDeviceToHost, s->stream));
+    CK(cudaStreamSynchronize(s->stream));
+    hs.steps_done = (unsigned long long)steps[1];
+    CK(cudaMemcpyAsync(s->st, &hs, sizeof hs, cudaMemcpyHostToDevice, s->stream));
+    s->steps = steps[0];
+    launch_fields_to_f32(field_args(s, 0, 0), s->stream);
+    return finish_call(s);
 }
 
 const char* pic_last_error(const pic_sim* s) {

@@ -99,4 +99,12 @@ struct Fp64InjectArgs {
 };
 void launch_inject_fp64(const Fp64InjectArgs& a, cudaStream_t s);
 
+// Diagnostics of FP64 particles (positions in grid units): rho += node charge density of
+// n particles of charge density q each (one simulation's nx * ny array; G by value), and
+// out[0..2] += w * sum of the momenta.
+void launch_rho_fp64(const GridDev& G, const double* x, const double* y, long long n, double q, double* rho,
+                     cudaStream_t s);
+void launch_momentum_fp64(const double* ux, const double* uy, const double* uz, long long n, double w,
+                          double* out, cudaStream_t s);
+
 }  // namespace pic

@@ -96,4 +96,27 @@ __device__ __forceinline__ void esirkepov(int i0, R f0x, int j0, R f0y, int i1, 
     }
 }
 
+// Node charge density of one macro-particle of charge density q (charge / (dx dy)) at
+// cell/fraction (i + fx, j + fy): rho(node) += q W_p(x - node) W_p(y - node) on the
+// integer lattice. With walls the part beyond a wall folds back as the mirror image's
+// (even); the unstored wall node x = nx is dropped.
+template <int P>
+__device__ __forceinline__ void deposit_rho(const GridDev& G, int i, double fx, int j, double fy, double q,
+                                            double* rho) {
+    int bx, by;
+    double wx[P + 1], wy[P + 1];
+    shape_nodes<P, double>(i, fx, bx, wx);
+    shape_nodes<P, double>(j, fy, by, wy);
+#pragma unroll
+    for (int b = 0; b <= P; b++) {
+        double* row = rho + (long long)wrapi(by + b, G.ny) * G.nx;
+#pragma unroll
+        for (int a = 0; a <= P; a++) {
+            int s = 1, col = wrapi(bx + a, G.nx);
+            if (G.walls) col = wall_col(bx + a, G.nx, false, false, s);
+            if (s) atomicAdd(row + col, s * q * wx[a] * wy[b]);
+        }
+    }
+}
+
 }  // namespace pic

@@ -715,6 +715,29 @@ __global__ void k_gather_overflow(long long n_over, int gs, Slots O, long long b
     to_staging(O.p, k, S, d);
 }
 
+template <int P>
+__global__ void k_rho_staged(long long n, GridDev G, PartArrays S, double q, double* rho) {
+    const long long k = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (k >= n) return;
+    const int c = S.cij[k];
+    deposit_rho<P>(G, c & 0xffff, (double)S.ox[k], c >> 16, (double)S.oy[k], q, rho);
+}
+
+__global__ void k_momentum_staged(long long n, PartArrays S, double w, double* out) {
+    __shared__ double red[32];
+    double s[3] = {0.0, 0.0, 0.0};
+    for (long long k = (long long)blockIdx.x * blockDim.x + threadIdx.x; k < n; k += (long long)gridDim.x * blockDim.x) {
+        s[0] += S.ux[k];
+        s[1] += S.uy[k];
+        s[2] += S.uz[k];
+    }
+    for (int c = 0; c < 3; c++) {
+        const double t = block_sum(s[c], red);
+        if (threadIdx.x == 0) atomicAdd(out + c, w * t);
+        __syncthreads();
+    }
+}
+
 __global__ void k_unstage(long long n, GridDev G, PartArrays S, double* out) {
     const long long k = (long long)blockIdx.x * blockDim.x + threadIdx.x;
     if (k >= n) return;
@@ -1296,6 +1319,33 @@ int mixed_after_steps(MixedState* m, cudaStream_t st, std::string& err) {
 }
 
 long long mixed_count(MixedState* m, int g, int s) { return m->n[2 * g + s]; }
+
+int mixed_rho_momentum(MixedState* m, int g, double* rho, double* mom, cudaStream_t st, std::string& err) {
+    DevStatus hs{};
+    if (int rc = read_status(m, hs, st, err)) return rc;
+    const GridDev& G = m->G[g];
+    for (int s = 0; s < 2; s++) {
+        PartArrays S{};
+        long long n = 0;
+        if (int rc = gather_species(m, g, (int)hs.parity, s, S, n, st, err)) return rc;
+        if (n && rho) {
+            const double q = G.qw[s] / (G.dx * G.dy);
+            switch (G.order) {
+            case 1: k_rho_staged<1><<<grid1(n), 256, 0, st>>>(n, G, S, q, rho); break;
+            case 2: k_rho_staged<2><<<grid1(n), 256, 0, st>>>(n, G, S, q, rho); break;
+            default: k_rho_staged<3><<<grid1(n), 256, 0, st>>>(n, G, S, q, rho); break;
+            }
+        }
+        if (n && mom) k_momentum_staged<<<304, 256, 0, st>>>(n, S, G.w, mom);
+        const cudaError_t e = cudaStreamSynchronize(st);
+        free_parts(S);
+        if (e != cudaSuccess) {
+            err = std::string("diagnostics: ") + cudaGetErrorString(e);
+            return PIC_ECUDA;
+        }
+    }
+    return PIC_OK;
+}
 long long mixed_rebins(MixedState* m) { return m->rebins; }
 long long mixed_generation(MixedState* m) { return m->gen; }
 

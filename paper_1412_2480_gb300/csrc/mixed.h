@@ -31,6 +31,9 @@ void mixed_enqueue(MixedState* m, cudaStream_t s, int part);
 int mixed_before_steps(MixedState* m, cudaStream_t s, std::string& err);
 int mixed_after_steps(MixedState* m, cudaStream_t s, std::string& err);
 long long mixed_count(MixedState* m, int g, int sp);
+// Add simulation g's node charge density into rho (device, ncell values; may be null)
+// and w * its total momentum into mom (device, 3 values; may be null).
+int mixed_rho_momentum(MixedState* m, int g, double* rho, double* mom, cudaStream_t s, std::string& err);
 long long mixed_rebins(MixedState* m);
 // Bumped whenever device buffers are reallocated: step graphs captured before hold stale
 // pointers and must be rebuilt.

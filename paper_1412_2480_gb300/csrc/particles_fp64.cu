@@ -169,7 +169,49 @@ __global__ void k_inject_fp64(const Fp64InjectArgs a) {
     }
 }
 
+template <int P>
+__global__ void k_rho_fp64(GridDev G, const double* __restrict__ x, const double* __restrict__ y, long long n,
+                           double q, double* rho) {
+    const long long k = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (k >= n) return;
+    const int i = (int)floor(x[k]), j = (int)floor(y[k]);
+    deposit_rho<P>(G, i, x[k] - i, j, y[k] - j, q, rho);
+}
+
+__global__ void k_momentum_fp64(const double* __restrict__ ux, const double* __restrict__ uy,
+                                const double* __restrict__ uz, long long n, double w, double* out) {
+    __shared__ double red[32];
+    double s[3] = {0.0, 0.0, 0.0};
+    for (long long k = (long long)blockIdx.x * blockDim.x + threadIdx.x; k < n; k += (long long)gridDim.x * blockDim.x) {
+        s[0] += ux[k];
+        s[1] += uy[k];
+        s[2] += uz[k];
+    }
+    for (int c = 0; c < 3; c++) {
+        const double t = block_sum(s[c], red);
+        if (threadIdx.x == 0) atomicAdd(out + c, w * t);
+        __syncthreads();
+    }
+}
+
 }  // namespace
+
+void launch_rho_fp64(const GridDev& G, const double* x, const double* y, long long n, double q, double* rho,
+                     cudaStream_t s) {
+    if (n <= 0) return;
+    const unsigned nb = (unsigned)((n + 255) / 256);
+    switch (G.order) {
+    case 1: k_rho_fp64<1><<<nb, 256, 0, s>>>(G, x, y, n, q, rho); break;
+    case 2: k_rho_fp64<2><<<nb, 256, 0, s>>>(G, x, y, n, q, rho); break;
+    default: k_rho_fp64<3><<<nb, 256, 0, s>>>(G, x, y, n, q, rho); break;
+    }
+}
+
+void launch_momentum_fp64(const double* ux, const double* uy, const double* uz, long long n, double w, double* out,
+                          cudaStream_t s) {
+    if (n <= 0) return;
+    k_momentum_fp64<<<304, 256, 0, s>>>(ux, uy, uz, n, w, out);
+}
 
 void launch_inject_fp64(const Fp64InjectArgs& a, cudaStream_t s) {
     const long long threads = (long long)a.ny * a.kmax;
