@@ -14,7 +14,7 @@ per species; 87,293,952 particles) in one handle with autotuned tiles; its plain
 comparison runs the 48 simulations one after another in their own handles.
 
   python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
-                  [--workload cfg2|cfg1|cfg2q|scan48]
+                  [--workload cfg2|cfg1|cfg2q|scan48|cfg5]
 
 With N > 1 (launched under torchrun) every rank runs an independent replica with its own
 seed (the path has no data-path exchange); value = particles of all ranks x K / the
@@ -24,6 +24,7 @@ from __future__ import annotations
 
 import argparse
 import hashlib
+import math
 import json
 import os
 import statistics
@@ -45,6 +46,13 @@ WORKLOADS = {
     # a quarter of cfg2 (same density and physics, 16.8M particles): profiling captures
     "cfg2q": (1024, 256, 32, 2, 40.0, 1e-3, 1.0, 0.5, 2),
 }
+SHOCK = {
+    # the shock configuration: a magnetised pair beam (sigma_B 0.1, Bz with the motional
+    # Ey) flowing into the conducting, reflecting wall at x = 0, filling the left half of
+    # the box; the moving injector starts at x = nx/2 and feeds the beam behind it
+    "cfg5": dict(nx=8192, ny=512, ppc=16, order=3, gamma0=40.0, u_th=1e-3, cfl=1.0, theta=0.501,
+                 seed=5, sigma_b=0.1, fill=0.5, inj_seed=105),
+}
 SCAN = "scan48"
 FP32_BYTES_PER_PARTICLE = 48  # 24 B read + 24 B written per MIXED32 particle update
 FP32_BYTES_PER_CELL = 36      # 6 FP32 field components read, 3 FP32 currents written
@@ -60,12 +68,44 @@ def rows_of(name, rank=0):
         for r in rows:
             r["seed"] += 1000 * rank
         return rows
+    if name in SHOCK:
+        c = SHOCK[name]
+        return [{"k": 0, "nx": c["nx"], "ny": c["ny"], "cfl": c["cfl"], "theta": c["theta"],
+                 "order": c["order"], "gamma0": c["gamma0"], "ppc": c["ppc"], "u_th": c["u_th"],
+                 "seed": c["seed"] + rank, "walls": True, "sigma_b": c["sigma_b"],
+                 "inject_x0": c["fill"] * c["nx"], "inj_seed": c["inj_seed"] + rank}]
     nx, ny, ppc, order, g0, uth, cfl, theta, seed = WORKLOADS[name]
     return [{"k": 0, "nx": nx, "ny": ny, "cfl": cfl, "theta": theta, "order": order,
              "gamma0": g0, "ppc": ppc, "u_th": uth, "seed": seed + rank}]
 
 
+def injected_pairs_per_row(r, n):
+    """Pairs per row the moving injector has added after n steps (the schedule pic.h
+    defines: floor(ppc (1 + v) cfl n) while the plane is inside the box)."""
+    if not r.get("walls"):
+        return 0
+    v = math.sqrt(1.0 - 1.0 / (r["gamma0"] ** 2))
+    width = (1.0 + v) * r["cfl"]
+    last = int(math.floor((r["nx"] - r["inject_x0"]) / r["cfl"]))  # steps with injection
+    n = min(n, max(0, last))
+    return int(math.floor(r["ppc"] * width * n))
+
+
+def particle_updates(rows, n0, first, k):
+    """Particle updates of steps first .. first + k - 1 (n0 particles loaded at step 0)."""
+    tot = 0
+    for s in range(first, first + k):
+        tot += n0 + sum(2 * r["ny"] * injected_pairs_per_row(r, s) for r in rows)
+    return tot
+
+
 def describe(name):
+    if name in SHOCK:
+        c = SHOCK[name]
+        return (f"{c['nx']}x{c['ny']} shock: conducting reflecting wall at x = 0, magnetised pair beam "
+                f"(sigma_B {c['sigma_b']}, gamma0 {c['gamma0']:g}, u_th {c['u_th']:g}, {c['ppc']} ppc/species) "
+                f"filling x < {c['fill'] * c['nx']:g} and fed by the moving injector, CFL {c['cfl']}, "
+                f"theta {c['theta']}, order {c['order']}, PCG rtol 1e-10")
     if name == SCAN:
         rows = rows_of(name)
         cells = sum(r["nx"] * r["ny"] for r in rows)
@@ -159,7 +199,19 @@ def make_inputs(rows, pinned=False):
     from paper_1412_2480_gb300 import inputs
     out = []
     for r in rows:
-        w, sp = inputs.drifting_pair_plasma(r["nx"], r["ny"], r["ppc"], r["gamma0"], r["u_th"], r["seed"])
+        if r.get("walls"):
+            # the beam on [0, inject_x0) (a whole number of cells); its uniform fields
+            # (Bz, motional Ey) continue over the rest of the box
+            x0 = int(r["inject_x0"])
+            w, sp, Fh = inputs.shock_beam(x0, r["ny"], r["ppc"], r["gamma0"], r["u_th"], r["seed"],
+                                          sigma_b=r["sigma_b"])
+            F = np.empty((6, r["ny"], r["nx"]))
+            F[:] = Fh[:, :, -1:]
+            F[:, :, :x0] = Fh
+            r["fields"] = F
+        else:
+            w, sp = inputs.drifting_pair_plasma(r["nx"], r["ny"], r["ppc"], r["gamma0"], r["u_th"],
+                                                r["seed"])
         if pinned:
             import torch
             pin = []
@@ -180,12 +232,17 @@ NO_GRAPH = False  # --no-graph: direct launches (profilers skip kernels of condi
 
 def params_of(rows, precision):
     import paper_1412_2480_gb300 as pic
-    return [pic.pic_params_default(nx=r["nx"], ny=r["ny"], cfl=r["cfl"], theta=r["theta"],
-                                   shape_order=r["order"], gamma0=r["gamma0"], ppc=r["ppc"],
-                                   precision=precision, cg_rtol=1e-10, cg_max_iter=200,
-                                   flags=pic.PIC_NO_GRAPH if NO_GRAPH else 0,
-                                   tile_x=r.get("tile_x", 0), tile_y=r.get("tile_y", 0))
-            for r in rows]
+    out = []
+    for r in rows:
+        kw = {}
+        if r.get("walls"):
+            kw = dict(bc_x=pic.PIC_BC_WALLS, inject_x0=r["inject_x0"], u_th=r["u_th"], seed=r["inj_seed"])
+        out.append(pic.pic_params_default(nx=r["nx"], ny=r["ny"], cfl=r["cfl"], theta=r["theta"],
+                                          shape_order=r["order"], gamma0=r["gamma0"], ppc=r["ppc"],
+                                          precision=precision, cg_rtol=1e-10, cg_max_iter=200,
+                                          flags=pic.PIC_NO_GRAPH if NO_GRAPH else 0,
+                                          tile_x=r.get("tile_x", 0), tile_y=r.get("tile_y", 0), **kw))
+    return out
 
 
 def new_sim(params, stream=None):
@@ -196,10 +253,13 @@ def new_sim(params, stream=None):
     return h
 
 
-def load(h, data):
+def load(h, data, rows=None):
     import paper_1412_2480_gb300 as pic
     for k, sp in enumerate(data):
         pic.pic_select(h, k)
+        if rows is not None and rows[k].get("fields") is not None:
+            for c in range(6):
+                pic.pic_set_fields(h, c, np.ascontiguousarray(rows[k]["fields"][c]).ravel())
         for s, d in enumerate(sp):
             pic.pic_load_particles(h, s, d["x"], d["y"], d["ux"], d["uy"], d["uz"])
     pic.pic_select(h, 0)
@@ -212,17 +272,6 @@ def pcg_totals(h, n):
     return m["loop_iters"], m["loop_refinements"]
 
 
-def launches(precision, n_orders, steps, d_iters, d_refine):
-    """Kernels of ours launched in `steps` steps. Per step: step_begin, then
-    MIXED32: mixed_begin, push_overflow, one tile launch per shape order present, swap;
-    FP64: one push launch per species; then zero_x, rhs, update_E, update_B, step_end.
-    The PCG loop runs as long as its slowest simulation: 2 kernels per inner iteration
-    and, in MIXED32, 3 per FP64 refinement (inner start, x update, residual)."""
-    if precision == 1:
-        return steps * (9 + n_orders) + 2 * d_iters + 3 * d_refine
-    return steps * 8 + 2 * d_iters
-
-
 def run_ours(args, dist):
     import torch
 
@@ -233,16 +282,20 @@ def run_ours(args, dist):
     name = args.workload
     rows = rows_of(name, rank)
     nsim = len(rows)
-    npart = sum(2 * r["ppc"] * r["nx"] * r["ny"] for r in rows)
     ncell = sum(r["nx"] * r["ny"] for r in rows)
-    n_orders = len({r["order"] for r in rows})
     stream = torch.cuda.Stream()
     data = make_inputs(rows, pinned=True)
+    npart = sum(d["x"].size for sp in data for d in sp)  # loaded at step 0
     prec = pic.PIC_MIXED32 if args.precision == "mixed" else pic.PIC_FP64
     if nsim > 1 and prec != pic.PIC_MIXED32:
         raise SystemExit("the batched scan runs in MIXED32 (its FP64 comparison is built in)")
     tune = None
-    if prec == pic.PIC_MIXED32:
+    if prec == pic.PIC_MIXED32 and args.tile:
+        tx, ty = (int(v) for v in args.tile.lower().split("x"))
+        for r in rows:
+            r["tile_x"], r["tile_y"] = tx, ty
+        tune = {"fixed": args.tile}
+    elif prec == pic.PIC_MIXED32:
         # tile shapes per shape order from the autotuner (synthetic scratch batches)
         ps = params_of(rows, prec)
         t0 = time.perf_counter()
@@ -272,7 +325,7 @@ def run_ours(args, dist):
     barrier()
     torch.cuda.synchronize()
     t0 = time.perf_counter()
-    load(h, data)
+    load(h, data, rows)
     for _ in range(args.steps):
         pic.pic_step(h, 1)
         pic.pic_moments(h)
@@ -283,17 +336,18 @@ def run_ours(args, dist):
     torch.cuda.synchronize()
     e2e_s = max_over_ranks(time.perf_counter() - t0)
     barrier()
-    h2d = npart * 5 * 8 / args.steps
+    h2d = (npart * 5 * 8 + sum(6 * r["nx"] * r["ny"] * 8 for r in rows if r.get("fields") is not None)) / args.steps
     d2h = (6 * ncell * 8) / args.steps + 176
     pic.pic_free(h)
 
     # ---- device-timed steps with inputs resident ----
     h = new_sim(params, stream)
-    load(h, data)
+    load(h, data, rows)
     clocks = Clocks(dev)
     clocks.start()
     pic.pic_step(h, args.warmup)
     it0, ref0 = pcg_totals(h, nsim)
+    k0 = pic.pic_moments(h)["kernel_launches"]
     ev0 = torch.cuda.Event(enable_timing=True)
     ev1 = torch.cuda.Event(enable_timing=True)
     barrier()
@@ -309,14 +363,24 @@ def run_ours(args, dist):
     barrier()
     it1, ref1 = pcg_totals(h, nsim)
     m1 = pic.pic_moments(h)
-    n_launch = launches(prec, n_orders, args.steps, it1 - it0, ref1 - ref0)
-    # ---- per-phase CUDA-event timing (profiling graphs, one per part of the step) ----
-    prof = pic.pic_profile(h, args.prof_steps)
+    n_launch = m1["kernel_launches"] - k0  # counted by the library (step graph's kernel nodes + PCG loop)
+    pic.pic_free(h)
+    # ---- per-phase CUDA-event timing (one graph per part of the step, events between
+    # them) over the same steps as the timed region: a second handle from the same
+    # inputs, W warm-up steps, then K profiled steps ----
+    h = new_sim(params, stream)
+    load(h, data, rows)
+    pic.pic_step(h, args.warmup)
+    prof = pic.pic_profile(h, args.steps if args.prof_steps <= 0 else args.prof_steps)
     pic.pic_free(h)
 
     res = {"ms": ms_max, "prof": prof, "cg_iters": (it1 - it0) / args.steps,
            "cg_refinements": (ref1 - ref0) / args.steps, "clocks": ck, "launches": n_launch,
            "e2e_s": e2e_s, "h2d": h2d, "d2h": d2h, "npart": npart, "ncell": ncell,
+           "updates_timed": particle_updates(rows, npart, args.warmup, args.steps),
+           "particles_end": sum(m1["n_particles"]) if nsim == 1 else None,
+           "particles_expected": particle_updates(rows, npart, args.warmup + args.steps, 1),
+           "updates_e2e": particle_updates(rows, npart, 0, args.steps),
            "rtol_reached": m1["cg_rel_resid"], "tune": tune}
 
     # ---- plain FP64 GPU path on the same inputs (comparison leg): a single grid, or the
@@ -327,7 +391,7 @@ def run_ours(args, dist):
         tot = field = push = 0.0
         for k in range(nsim):
             h = new_sim([p64[k]], stream)
-            load(h, [data[k]])
+            load(h, [data[k]], [rows[k]])
             pic.pic_step(h, 2)
             e0 = torch.cuda.Event(enable_timing=True)
             e1 = torch.cuda.Event(enable_timing=True)
@@ -340,7 +404,8 @@ def run_ours(args, dist):
             field += prof64["field_ms"]
             push += prof64["push_kernel_ms"]
             pic.pic_free(h)
-        res["fp64"] = {"ms_per_step": tot, "value": npart / (tot * 1e-3),
+        res["fp64"] = {"ms_per_step": tot,
+                       "value": particle_updates(rows, npart, 2, k64) / k64 / (tot * 1e-3),
                        "field_solve_ms_per_step": field, "push_kernel_ms": push, "steps": k64,
                        "how": "one handle" if nsim == 1 else "48 handles one after another"}
     return res
@@ -348,9 +413,10 @@ def run_ours(args, dist):
 
 def oracle_sample(name, seconds_target=12.0):
     """The CPU oracle as it stands, on a bounded sample of the workload: the same physics
-    on a periodic patch (1/8 of each grid dimension, at least 16 cells) with the same
-    particles per cell, timed over whole steps on one host core. For the scan, the sample
-    is its first simulation (128 x 128) whole."""
+    on a patch (1/8 of each grid dimension, at least 16 cells) with the same particles per
+    cell, timed over whole steps on one host core. For the scan, the sample is its first
+    simulation (128 x 128) whole; for the shock, the patch keeps the wall, the beam's
+    fields and the injector (at the same fraction of the box)."""
     import oracle
     from paper_1412_2480_gb300 import inputs
     r = rows_of(name)[0]
@@ -358,20 +424,35 @@ def oracle_sample(name, seconds_target=12.0):
         sx, sy = r["nx"], r["ny"]
     else:
         sx, sy = max(16, r["nx"] // 8), max(16, r["ny"] // 8)
-    w, sp = inputs.drifting_pair_plasma(sx, sy, r["ppc"], r["gamma0"], r["u_th"], r["seed"])
+    F0, inj = None, None
+    if r.get("walls"):
+        w, sp, F0 = inputs.shock_beam(sx, sy, r["ppc"], r["gamma0"], r["u_th"], r["seed"],
+                                      sigma_b=r["sigma_b"])
+        x0 = r["inject_x0"] * sx / r["nx"]
+        for d in sp:
+            keep = d["x"] < x0
+            for key in ("x", "y", "ux", "uy", "uz"):
+                d[key] = np.ascontiguousarray(d[key][keep])
+        inj = dict(x0=x0, ppc=r["ppc"], gamma0=r["gamma0"], u_th=r["u_th"], seed=r["inj_seed"])
+    else:
+        w, sp = inputs.drifting_pair_plasma(sx, sy, r["ppc"], r["gamma0"], r["u_th"], r["seed"])
     species = [oracle.Species(d["qm"], w, d["x"], d["y"], d["ux"], d["uy"], d["uz"]) for d in sp]
-    sim = oracle.OracleSim(sx, sy, r["cfl"], r["theta"], r["order"], species, cg_rtol=1e-10)
+    sim = oracle.OracleSim(sx, sy, r["cfl"], r["theta"], r["order"], species, cg_rtol=1e-10,
+                           fields=F0, walls=bool(r.get("walls")), injector=inj)
     oracle.build()
-    steps, t = 0, 0.0
+    steps, t, upd = 0, 0.0, 0
     while t < seconds_target and steps < 50:
+        n = sum(s.n for s in sim.species)
         t0 = time.perf_counter()
         sim.step(1)
         t += time.perf_counter() - t0
         steps += 1
-    npart = 2 * sx * sy * r["ppc"]
-    return {"value": npart * steps / t, "unit": UNIT, "cores": 1, "kind": "oracle",
-            "sample": f"{sx}x{sy} patch (order {r['order']}, {r['ppc']} ppc/species, gamma0 {r['gamma0']:g}; "
-                      f"{npart} particles), {steps} whole steps in {t:.1f} s on 1 host core"}
+        upd += n
+    kind = "patch" if name != SCAN else "simulation"
+    return {"value": upd / t, "unit": UNIT, "cores": 1, "kind": "oracle",
+            "sample": f"{sx}x{sy} {kind} (order {r['order']}, {r['ppc']} ppc/species, gamma0 {r['gamma0']:g}"
+                      f"{', walls and injector' if r.get('walls') else ''}; {upd // steps} particles per step), "
+                      f"{steps} whole steps in {t:.1f} s on 1 host core"}
 
 
 def main():
@@ -380,10 +461,12 @@ def main():
     ap.add_argument("--steps", type=int, default=200)
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
-    ap.add_argument("--workload", choices=sorted(WORKLOADS) + [SCAN], default="cfg2")
+    ap.add_argument("--workload", choices=sorted(WORKLOADS) + sorted(SHOCK) + [SCAN], default="cfg2")
     ap.add_argument("--precision", choices=["mixed", "fp64"], default="mixed")
-    ap.add_argument("--prof-steps", type=int, default=4)
+    ap.add_argument("--prof-steps", type=int, default=0,
+                    help="steps of per-phase timing (0: the timed steps again, from the same start)")
     ap.add_argument("--skip-fp64", action="store_true")
+    ap.add_argument("--tile", default="", help="fixed MIXED32 tile TXxTY instead of the autotuner's choice")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-graph", action="store_true",
                     help="launch kernels directly (for profiler launch lists), not a bench number")
@@ -397,7 +480,7 @@ def main():
     local_rank = int(os.environ.get("LOCAL_RANK", "0"))
     dist = {"world": world, "rank": rank, "local_rank": local_rank}
     rows = rows_of(args.workload)
-    npart = sum(2 * r["ppc"] * r["nx"] * r["ny"] for r in rows)
+    npart = sum(2 * r["ppc"] * int(r.get("inject_x0", r["nx"])) * r["ny"] for r in rows)
 
     if args.impl == "reference":
         if rank != 0:
@@ -430,13 +513,13 @@ def main():
     res = run_ours(args, dist)
     if rank != 0:
         return
-    npart = res["npart"]
-    value = world * npart * args.steps / (res["ms"] * 1e-3)
+    value = world * res["updates_timed"] / (res["ms"] * 1e-3)
+    npart = res["updates_timed"] / args.steps  # particles per step, averaged over the timed steps
     hbm, src = peaks()
     mixed = args.precision == "mixed"
     bpp = FP32_BYTES_PER_PARTICLE if mixed else FP64_BYTES_PER_PARTICLE
     bpc = FP32_BYTES_PER_CELL if mixed else FP64_BYTES_PER_CELL
-    alg_bytes = bpp * npart + bpc * res["ncell"]
+    alg_bytes = int(bpp * npart + bpc * res["ncell"])
     kms = res["prof"]["push_kernel_ms"]
     achieved = alg_bytes / (kms * 1e-3) / 1e9
     key = "k_push_tile" if mixed else "k_push_fp64"
@@ -456,7 +539,7 @@ def main():
         "particle_ms_per_step": res["prof"]["particle_ms"],
         "cg_iters_per_step": res["cg_iters"],
         "cg_refinements_per_step": res["cg_refinements"],
-        "e2e": {"value": world * npart * args.steps / res["e2e_s"], "unit": UNIT,
+        "e2e": {"value": world * res["updates_e2e"] / res["e2e_s"], "unit": UNIT,
                 "h2d_bytes_per_step": int(res["h2d"]), "d2h_bytes_per_step": int(res["d2h"]),
                 "what": "pic_load_particles from pinned host arrays + K x (pic_step(1) + pic_moments) "
                         "+ pic_fields x 6 per simulation"},
@@ -466,6 +549,7 @@ def main():
                      "algorithmic_bytes_per_launch": alg_bytes,
                      "kernel_ms": kms},
         "gpu_launches": res["launches"],
+        "particles_end": {"counted": res["particles_end"], "schedule": res["particles_expected"]},
         "clocks": res["clocks"],
     }
     if res["tune"]:

@@ -162,6 +162,8 @@ typedef struct pic_moments_t {
     int64_t loop_iters;      /* handle-wide: CG iterations the PCG loop ran (in a batch, as many
                                 per step as its slowest simulation needed) */
     int64_t loop_refinements;/* handle-wide, MIXED32: FP64 refinements the PCG loop ran */
+    int64_t kernel_launches; /* handle-wide: kernels of this library launched by pic_step and
+                                pic_profile so far (the PCG loop's included) */
 } pic_moments_t;
 
 typedef struct pic_sim pic_sim;
@@ -232,7 +234,9 @@ PIC_API int pic_set_fields(pic_sim* s, int32_t which, const double* data, size_t
 /* Advance n >= 0 steps of the particle cycle (Sec. 2, Sec. 3): for each step, gather
  * E^n, B^n; push; move; deposit J^{n+1/2}; solve Eq. (7) by PCG; update E, B by
  * Eqs. (5)-(6). Work is enqueued on the handle's stream and the call returns after the
- * stream has finished (one host synchronisation per call, not per step). Errors
+ * stream has finished (one host synchronisation per call, not per step; MIXED32 also
+ * synchronises every 32 steps, to re-sort particles that found no room in their tile's
+ * bin into larger bins). Errors
  * detected on the device (PIC_ECG_NOCONV, PIC_ECFL, PIC_ENAN) stop the remaining
  * steps of the call; the fields and particles then hold the state after the failing
  * step and pic_moments reports its step count. PIC_ESTATE if warm_start is

@@ -72,7 +72,7 @@ class pic_moments_t(C.Structure):
                 ("cg_rel_resid", C.c_double), ("cfl_violations", C.c_int64),
                 ("overflow_moves", C.c_int64), ("rebins", C.c_int64),
                 ("cg_refinements", C.c_int64), ("loop_iters", C.c_int64),
-                ("loop_refinements", C.c_int64)]
+                ("loop_refinements", C.c_int64), ("kernel_launches", C.c_int64)]
 
 
 class PicError(RuntimeError):

@@ -80,6 +80,8 @@ struct pic_sim {
     CoopSolve coop;
     // bookkeeping
     long long steps = 0;
+    long long kernels = 0;         // kernels of this library launched by pic_step / pic_profile
+    long long graph_kernels = -1;  // kernel nodes of the step graph outside its PCG loop
     unsigned long long seen_cfl = 0, seen_nan = 0, seen_lost = 0;
     unsigned int seen_noconv = 0, seen_sync = 0;
 };
@@ -441,7 +443,45 @@ int capture(pic_sim* s, int mask, cudaGraph_t* gout, cudaGraphExec_t* xout) {
 
 int build_graph(pic_sim* s) {
     drop_graph(s);
-    return capture(s, (1 << kNumParts) - 1, &s->graph, &s->gexec);
+    int rc = capture(s, (1 << kNumParts) - 1, &s->graph, &s->gexec);
+    s->graph_kernels = -1;
+    size_t n = 0;
+    if (rc == PIC_OK && cudaGraphGetNodes(s->graph, nullptr, &n) == cudaSuccess) {
+        std::vector<cudaGraphNode_t> nodes(n);
+        long long k = 0;
+        if (n && cudaGraphGetNodes(s->graph, nodes.data(), &n) == cudaSuccess) {
+            for (cudaGraphNode_t node : nodes) {
+                cudaGraphNodeType t;
+                if (cudaGraphNodeGetType(node, &t) == cudaSuccess && t == cudaGraphNodeTypeKernel) k++;
+            }
+            s->graph_kernels = k;
+        }
+    }
+    cudaGetLastError();
+    return rc;
+}
+
+// Kernels one step launches outside the PCG loop: the step graph's kernel nodes, or
+// the same count from the step's structure for direct launches.
+long long step_kernels(pic_sim* s, bool graph) {
+    if (graph && s->graph_kernels >= 0) return s->graph_kernels;
+    long long k = 6;  // step begin and end, zero_x, rhs, update_E, update_B
+    if (s->prm.precision == PIC_MIXED32) {
+        k += mixed_step_kernels(s->mixed);
+    } else {
+        k += (s->nblk_push[0] > 0 ? 1 : 0) + (s->nblk_push[1] > 0 ? 1 : 0);
+        k += s->hgrids[0].inject ? 1 : 0;
+    }
+    if (s->learned) k += 2;  // k_guess, k_guess_residual
+    if (s->use_coop) k += 1;
+    return k;
+}
+
+// Kernels the PCG loop launched for the given loop-counter increments (none with the
+// cooperative solve: its iterations run inside one launch).
+long long loop_kernels(const pic_sim* s, unsigned long long d_iters, unsigned long long d_refine) {
+    if (s->use_coop) return 0;
+    return 2 * (long long)d_iters + (s->prm.precision == PIC_MIXED32 ? 3 * (long long)d_refine : 0);
 }
 
 // Direct launches (PIC_NO_GRAPH): the PCG loop is driven from the host.
@@ -1007,17 +1047,21 @@ int pic_set_fields(pic_sim* s, int32_t which, const double* data, size_t len) {
     return finish_call(s);
 }
 
-int pic_step(pic_sim* s, int32_t n) {
-    if (!s) return PIC_EINVAL;
-    cudaSetDevice(s->device);
-    if (n < 0) return fail(s, PIC_EINVAL, "n must be >= 0");
-    if (n == 0) return PIC_OK;
-    if (s->learned && !s->has_cnn) return fail(s, PIC_ESTATE, "PIC_WS_LEARNED needs a network (pic_set_cnn)");
-    // a new call starts clean: errors stop the rest of the call that raised them only
+namespace {
+
+// MIXED32 runs a call in chunks of this many steps: particles that found no room in their
+// tile's bin wait in the overflow list (pushed from global memory, far slower) until the
+// host re-sorts them into larger bins after a chunk.
+constexpr int kStepChunk = 32;
+
+int step_chunk(pic_sim* s, int32_t n) {
+    // a new chunk starts clean: errors stop the rest of the chunk that raised them, and
+    // the call returns
     DevStatus hs{};
     CK(cudaMemcpyAsync(&hs, s->st, sizeof hs, cudaMemcpyDeviceToHost, s->stream));
     CK(cudaStreamSynchronize(s->stream));
     const unsigned long long steps0 = hs.steps_done;
+    const unsigned long long li0 = hs.loop_iters[0], lr0 = hs.loop_iters[1];
     hs.stop = 0;
     hs.stop_next = 0;
     CK(cudaMemcpyAsync(s->st, &hs, sizeof hs, cudaMemcpyHostToDevice, s->stream));
@@ -1030,6 +1074,7 @@ int pic_step(pic_sim* s, int32_t n) {
     if (graph && !s->gexec) {
         if (int rc = build_graph(s)) return rc;
     }
+    const long long per_step = step_kernels(s, graph);
     for (int k = 0; k < n; k++) {
         if (graph) {
             CK(cudaGraphLaunch(s->gexec, s->stream));
@@ -1040,17 +1085,34 @@ int pic_step(pic_sim* s, int32_t n) {
     CK(cudaMemcpyAsync(&hs, s->st, sizeof hs, cudaMemcpyDeviceToHost, s->stream));
     if (int rc = finish_call(s)) return rc;
     s->steps += (long long)(hs.steps_done - steps0);
+    s->kernels += n * per_step + loop_kernels(s, hs.loop_iters[0] - li0, hs.loop_iters[1] - lr0);
     if (int rc0 = fp64_counts(s)) return rc0;
     int rc = device_errors(s, hs);
     if (rc == PIC_OK && s->prm.precision == PIC_MIXED32) rc = mixed_after_steps(s->mixed, s->stream, s->err);
     return rc;
 }
 
-int pic_profile(pic_sim* s, int32_t n, double* out, int32_t n_out) {
+}  // namespace
+
+int pic_step(pic_sim* s, int32_t n) {
     if (!s) return PIC_EINVAL;
     cudaSetDevice(s->device);
-    if (n < 1 || !out || n_out < 1) return fail(s, PIC_EINVAL, "need n >= 1 and an output array");
+    if (n < 0) return fail(s, PIC_EINVAL, "n must be >= 0");
+    if (n == 0) return PIC_OK;
     if (s->learned && !s->has_cnn) return fail(s, PIC_ESTATE, "PIC_WS_LEARNED needs a network (pic_set_cnn)");
+    const int chunk = s->prm.precision == PIC_MIXED32 ? kStepChunk : n;
+    for (int done = 0; done < n;) {
+        const int m = std::min(chunk, n - done);
+        if (int rc = step_chunk(s, m)) return rc;
+        done += m;
+    }
+    return PIC_OK;
+}
+
+namespace {
+
+// n profiled steps; per-phase times and PCG iterations are added into acc[0..4].
+int profile_chunk(pic_sim* s, int32_t n, double* acc) {
     for (int k = 0; k < 6; k++)
         if (!s->ev[k]) CK(cudaEventCreate(&s->ev[k]));
     if (s->prm.precision == PIC_MIXED32) {
@@ -1061,13 +1123,13 @@ int pic_profile(pic_sim* s, int32_t n, double* out, int32_t n_out) {
     for (int k = 0; k < kNumParts; k++)
         if (!s->pexec[k])
             if (int rc = capture(s, 1 << k, &s->pgraph[k], &s->pexec[k])) return rc;
-    double acc[5] = {0, 0, 0, 0, 0};
     CgState c0{}, c1{};
     DevStatus hs{};
     CK(cudaMemcpyAsync(&c0, s->cg + s->sel, sizeof c0, cudaMemcpyDeviceToHost, s->stream));
     CK(cudaMemcpyAsync(&hs, s->st, sizeof hs, cudaMemcpyDeviceToHost, s->stream));
     CK(cudaStreamSynchronize(s->stream));
     const unsigned long long steps0 = hs.steps_done;
+    const unsigned long long li0 = hs.loop_iters[0], lr0 = hs.loop_iters[1];
     hs.stop = 0;
     hs.stop_next = 0;
     CK(cudaMemcpyAsync(s->st, &hs, sizeof hs, cudaMemcpyHostToDevice, s->stream));
@@ -1089,12 +1151,30 @@ int pic_profile(pic_sim* s, int32_t n, double* out, int32_t n_out) {
     CK(cudaMemcpyAsync(&hs, s->st, sizeof hs, cudaMemcpyDeviceToHost, s->stream));
     CK(cudaStreamSynchronize(s->stream));
     s->steps += (long long)(hs.steps_done - steps0);
+    s->kernels += n * step_kernels(s, false) + loop_kernels(s, hs.loop_iters[0] - li0, hs.loop_iters[1] - lr0);
     if (int rc0 = fp64_counts(s)) return rc0;
-    acc[4] = (double)(c1.total_iters - c0.total_iters);
-    for (int a = 0; a < n_out && a < 5; a++) out[a] = acc[a] / n;
+    acc[4] += (double)(c1.total_iters - c0.total_iters);
     int rc = device_errors(s, hs);
     if (rc == PIC_OK && s->prm.precision == PIC_MIXED32) rc = mixed_after_steps(s->mixed, s->stream, s->err);
     return rc;
+}
+
+}  // namespace
+
+int pic_profile(pic_sim* s, int32_t n, double* out, int32_t n_out) {
+    if (!s) return PIC_EINVAL;
+    cudaSetDevice(s->device);
+    if (n < 1 || !out || n_out < 1) return fail(s, PIC_EINVAL, "need n >= 1 and an output array");
+    if (s->learned && !s->has_cnn) return fail(s, PIC_ESTATE, "PIC_WS_LEARNED needs a network (pic_set_cnn)");
+    double acc[5] = {0, 0, 0, 0, 0};
+    const int chunk = s->prm.precision == PIC_MIXED32 ? kStepChunk : n;  // as pic_step
+    for (int done = 0; done < n;) {
+        const int m = std::min(chunk, n - done);
+        if (int rc = profile_chunk(s, m, acc)) return rc;
+        done += m;
+    }
+    for (int a = 0; a < n_out && a < 5; a++) out[a] = acc[a] / n;
+    return PIC_OK;
 }
 
 int pic_fields(pic_sim* s, int32_t which, double* out, size_t len) {
@@ -1159,6 +1239,7 @@ int pic_moments(pic_sim* s, pic_moments_t* m) {
     m->cg_refinements = c.total_outer;
     m->loop_iters = (int64_t)hs.loop_iters[0];
     m->loop_refinements = (int64_t)hs.loop_iters[1];
+    m->kernel_launches = s->kernels;
     // the largest-iteration counter restarts at every pic_moments call
     const int zero = 0;
     CK(cudaMemcpyAsync(&s->cg[s->sel].max_iters, &zero, sizeof zero, cudaMemcpyHostToDevice, s->stream));

@@ -1280,6 +1280,12 @@ void mixed_enqueue(MixedState* m, cudaStream_t st, int part) {
 
 int mixed_before_steps(MixedState*, cudaStream_t, std::string&) { return PIC_OK; }
 
+int mixed_step_kernels(const MixedState* m) {
+    int k = 3;  // k_mixed_begin, k_push_overflow, k_mixed_swap
+    for (int P = 1; P <= 3; P++) k += m->order_n[P] > 0 ? 1 : 0;
+    return k + (m->inject_grids ? 1 : 0);
+}
+
 int mixed_after_steps(MixedState* m, cudaStream_t st, std::string& err) {
     DevStatus hs{};
     if (int rc = read_status(m, hs, st, err)) return rc;

@@ -30,6 +30,9 @@ void mixed_enqueue(MixedState* m, cudaStream_t s, int part);
 // Host bookkeeping around a pic_step call (re-bin when bins overflowed).
 int mixed_before_steps(MixedState* m, cudaStream_t s, std::string& err);
 int mixed_after_steps(MixedState* m, cudaStream_t s, std::string& err);
+
+// Kernels mixed_enqueue launches per step (all three parts together).
+int mixed_step_kernels(const MixedState* m);
 long long mixed_count(MixedState* m, int g, int sp);
 // Add simulation g's node charge density into rho (device, ncell values; may be null)
 // and w * its total momentum into mom (device, 3 values; may be null).

@@ -54,6 +54,23 @@ def rel(a, b):
     return float(np.linalg.norm(a - b) / (nb if nb > 0 else 1.0))
 
 
+def match_particles(g, o, scale):
+    """Pairs every particle of g (5 x n: x, y, ux, uy, uz) with its nearest particle of o
+    in coordinates divided by scale (5 values) and returns the largest paired distance,
+    or infinity when the pairing is not one to one. Unlike a comparison of sorted arrays
+    it does not break when two particles closer than the round-off swap their order."""
+    from scipy.spatial import cKDTree
+    if g.shape != o.shape:
+        return float("inf")
+    if g.shape[1] == 0:
+        return 0.0
+    sc = np.asarray(scale, dtype=np.float64)[:, None]
+    d, idx = cKDTree((o / sc).T).query((g / sc).T)
+    if np.unique(idx).size != idx.size:
+        return float("inf")
+    return float(d.max())
+
+
 def periodic_pos_err(a, b, L):
     """Largest position difference modulo the box length."""
     d = np.abs(a - b)

@@ -226,3 +226,34 @@ def test_restore_rejects_other_parameters_and_bad_files(tmp_path):
     finally:
         for h in (h1, h2, h3):
             pic.pic_free(h)
+
+
+@pytest.mark.parametrize("case", ["fp64", "mixed", "mixed_loop", "fp64_walls_injector",
+                                  "mixed_walls_injector"])
+def test_kernel_launch_count_graph_equals_direct(case):
+    # the library counts its launches: in the step graph from its kernel nodes, in
+    # direct launches from the step's structure; the two must agree (PCG loop included)
+    nx, ny, ppc = 64, 16, 2
+    prec = pic.PIC_FP64 if case.startswith("fp64") else pic.PIC_MIXED32
+    if "injector" in case:
+        w, sp, F0 = inputs.shock_beam(nx, ny, ppc, 10.0, 1e-3, seed=7, sigma_b=0.1)
+        for d in sp:
+            keep = d["x"] < 32.0
+            for k in ("x", "y", "ux", "uy", "uz"):
+                d[k] = d[k][keep]
+        kw = dict(walls=True, gamma0=10.0, inject_x0=32.0, u_th=1e-3, seed=3)
+    else:
+        w, sp, F0 = hot(nx, ny, ppc, 97, False)
+        kw = {}
+    counts = []
+    for flags in (0, pic.PIC_NO_GRAPH):
+        if case == "mixed_loop":
+            flags |= pic.PIC_NO_COOP
+        h = make(nx, ny, ppc, 2, sp, F0, prec, flags=flags, **kw)
+        try:
+            pic.pic_step(h, 3)
+            m = pic.pic_moments(h)
+            counts.append(m["kernel_launches"])
+        finally:
+            pic.pic_free(h)
+    assert counts[0] == counts[1] > 3 * 8, counts
