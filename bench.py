@@ -363,6 +363,15 @@ def run_ours(args, dist):
     barrier()
     it1, ref1 = pcg_totals(h, nsim)
     m1 = pic.pic_moments(h)
+    # Fourier diagnostic of B_z (Sec. 3.1): host-timed pic_spectrum calls on the first
+    # simulation, D2H copy of the amplitude map included
+    spec = np.empty((rows[0]["ny"], rows[0]["nx"]))
+    pic.pic_select(h, 0)
+    pic.pic_spectrum(h, pic.PIC_BZ, rows[0]["nx"], rows[0]["ny"])
+    t0 = time.perf_counter()
+    for _ in range(3):
+        spec = pic.pic_spectrum(h, pic.PIC_BZ, rows[0]["nx"], rows[0]["ny"])
+    spectrum_ms = (time.perf_counter() - t0) / 3 * 1e3
     n_launch = m1["kernel_launches"] - k0  # counted by the library (step graph's kernel nodes + PCG loop)
     pic.pic_free(h)
     # ---- per-phase CUDA-event timing (one graph per part of the step, events between
@@ -378,6 +387,7 @@ def run_ours(args, dist):
            "cg_refinements": (ref1 - ref0) / args.steps, "clocks": ck, "launches": n_launch,
            "e2e_s": e2e_s, "h2d": h2d, "d2h": d2h, "npart": npart, "ncell": ncell,
            "updates_timed": particle_updates(rows, npart, args.warmup, args.steps),
+           "spectrum_ms": spectrum_ms,
            "particles_end": sum(m1["n_particles"]) if nsim == 1 else None,
            "particles_expected": particle_updates(rows, npart, args.warmup + args.steps, 1),
            "updates_e2e": particle_updates(rows, npart, 0, args.steps),
@@ -550,6 +560,7 @@ def main():
                      "kernel_ms": kms},
         "gpu_launches": res["launches"],
         "particles_end": {"counted": res["particles_end"], "schedule": res["particles_expected"]},
+        "spectrum_ms": res["spectrum_ms"],
         "clocks": res["clocks"],
     }
     if res["tune"]:

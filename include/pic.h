@@ -371,6 +371,23 @@ PIC_API int pic_set_cnn(pic_sim* s, const pic_cnn* c);
 PIC_API int pic_tc_gemm_bf16(int32_t M, int32_t N, int32_t K, const uint16_t* A, const uint16_t* B,
                              float* D);
 
+/* Fourier diagnostics (the k-space maps of Sec. 3.1, Fig. 3): the amplitude spectrum of
+ * grid quantity `which` (PIC_EX..PIC_RHO) of the selected simulation,
+ *   out[q nx + p] = |sum_{l,m} F(l, m) exp(-2 pi i (p l / nx + q m / ny))| / (nx ny),
+ * p, q in FFT order (p >= nx/2 stands for the wave number 2 pi (p - nx) / (nx dx)). len
+ * >= nx*ny FP64 values (host or device). FP64 FFTs on the GPU (radices 2, 3, 4, 5; other
+ * lengths by the direct sum). Growth maps follow from two spectra: the rate of mode
+ * (p, q) between steps n1 < n2 is ln(out2 / out1) / ((n2 - n1) dt). */
+PIC_API int pic_spectrum(pic_sim* s, int32_t which, double* out, size_t len);
+
+/* The resonance line of numerical Cherenkov radiation, Eq. (17): for a flow at
+ * beta = V/c in (0, 1) and k_x dx in (0, pi], the k_y dy >= 0 at which the flow's mode
+ * omega = V k_x meets the vacuum dispersion surface of the theta = 1/2 scheme, Eq. (15),
+ * with cfl_x = c dt/dx, cfl_y = c dt/dy. Returns PIC_OK and *ky_dy (the line is symmetric:
+ * -ky_dy too), or PIC_EINVAL when no real k_y exists for this k_x (the flow does not
+ * overtake those waves) or an argument is out of range. Host only; needs no handle. */
+PIC_API int pic_resonance_ky(double cfl_x, double cfl_y, double beta, double kx_dx, double* ky_dy);
+
 /* Conservation diagnostics of the selected simulation, computed on demand from the
  * particles and fields (a pass over all particles: not for every step): up to n_out of
  *   out[0..2] total momentum sum w u of both species (units of m c),

@@ -193,6 +193,30 @@ def div_J(g, J):
     return out
 
 
+# ---- Fourier diagnostics (Sec. 3.1, Fig. 3) --------------------------------------------
+def spectrum(F2d):
+    """Amplitude |sum_{l,m} F(l,m) exp(-2 pi i (p l/nx + q m/ny))| / (nx ny) of an (ny, nx)
+    grid quantity, p and q in FFT order; numpy's FFT is the library step."""
+    F2d = np.asarray(F2d, dtype=np.float64)
+    return np.abs(np.fft.fft2(F2d)) / F2d.size
+
+
+def resonance_ky(cfl_x, cfl_y, beta, kx_dx):
+    """Eq. (17): the k_y dy >= 0 at which the flow's mode omega = V k_x (beta = V/c) lies
+    on the theta = 1/2 vacuum dispersion surface, Eq. (15), with S_x = cfl_x sin(k_x dx/2)
+    and cfl = c dt / d. None where the square root or the arcsine has no real value."""
+    half_phase = beta * cfl_x * kx_dx / 2.0  # V k_x dt / 2
+    if not (0.0 < half_phase < math.pi / 2):
+        return None
+    radicand = math.tan(half_phase) ** 2 - (cfl_x * math.sin(kx_dx / 2.0)) ** 2
+    if radicand < 0.0:
+        return None
+    s = math.sqrt(radicand) / cfl_y
+    if s > 1.0:
+        return None
+    return 2.0 * math.asin(s)
+
+
 def field_energy(g, F):
     ue, ub = C.c_double(), C.c_double()
     lib().or_field_energy(C.byref(g), _c(F).ravel(), C.byref(ue), C.byref(ub))

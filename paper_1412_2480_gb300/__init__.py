@@ -51,7 +51,7 @@ EXPORTED = ("pic_params_default", "pic_init", "pic_init_batch", "pic_select", "p
             "pic_cnn_create", "pic_cnn_free", "pic_cnn_last_error", "pic_cnn_set_params",
             "pic_cnn_get_params", "pic_cnn_forward", "pic_cnn_gradient", "pic_cnn_train_step",
             "pic_cnn_stencil", "pic_set_cnn", "pic_tc_gemm_bf16", "pic_conservation", "pic_save",
-            "pic_restore")
+            "pic_restore", "pic_spectrum", "pic_resonance_ky")
 
 
 class pic_params(C.Structure):
@@ -133,7 +133,11 @@ def lib():
             L.pic_conservation.argtypes = [vp, C.POINTER(C.c_double), C.c_int32]
             L.pic_save.argtypes = [vp, C.c_char_p]
             L.pic_restore.argtypes = [vp, C.c_char_p]
-            for name in ("pic_conservation", "pic_save", "pic_restore"):
+            L.pic_spectrum.argtypes = [vp, C.c_int32, vp, C.c_size_t]
+            L.pic_resonance_ky.argtypes = [C.c_double, C.c_double, C.c_double, C.c_double,
+                                           C.POINTER(C.c_double)]
+            for name in ("pic_conservation", "pic_save", "pic_restore", "pic_spectrum",
+                         "pic_resonance_ky"):
                 getattr(L, name).restype = C.c_int
             L.pic_cnn_stencil.argtypes = [vp, vp, C.c_int64]
             L.pic_tc_gemm_bf16.argtypes = [C.c_int32, C.c_int32, C.c_int32, vp, vp, vp]
@@ -298,6 +302,20 @@ def pic_conservation(h) -> dict:
     _check(lib().pic_conservation(h, out, 6), h)
     return {"momentum": (out[0], out[1], out[2]), "charge": out[3], "gauss_max": out[4],
             "gauss_rms": out[5]}
+
+
+def pic_spectrum(h, which, nx, ny):
+    """Amplitude spectrum of a grid quantity as an (ny, nx) array (see pic.h)."""
+    out = np.empty((ny, nx), dtype=np.float64)
+    _check(lib().pic_spectrum(h, int(which), out.ctypes.data, out.size), h)
+    return out
+
+
+def pic_resonance_ky(cfl_x, cfl_y, beta, kx_dx):
+    """k_y dy of the numerical Cherenkov resonance line, Eq. (17), or None."""
+    v = C.c_double(0.0)
+    rc = lib().pic_resonance_ky(float(cfl_x), float(cfl_y), float(beta), float(kx_dx), C.byref(v))
+    return v.value if rc == 0 else None
 
 
 def pic_save(h, path) -> None:

@@ -16,7 +16,7 @@ CSRC = os.path.join(HERE, "csrc")
 INCLUDE = os.path.join(ROOT, "include")
 BUILD = os.path.join(HERE, "_build")
 LIB = os.path.join(HERE, "libpic.so")
-SOURCES = ["capi.cu", "fields.cu", "particles_fp64.cu", "mixed.cu", "noalloc.cu", "cnn.cu", "solve_coop.cu"]
+SOURCES = ["capi.cu", "fields.cu", "particles_fp64.cu", "mixed.cu", "noalloc.cu", "cnn.cu", "solve_coop.cu", "spectrum.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-O3", "-std=c++17", "-lineinfo", "-Xcompiler", "-fPIC", "-Xcompiler", "-fvisibility=hidden",
          "--expt-relaxed-constexpr", "-I", INCLUDE, "-I", CSRC]

@@ -1177,15 +1177,16 @@ int pic_profile(pic_sim* s, int32_t n, double* out, int32_t n_out) {
     return PIC_OK;
 }
 
-int pic_fields(pic_sim* s, int32_t which, double* out, size_t len) {
-    if (!s) return PIC_EINVAL;
-    cudaSetDevice(s->device);
+namespace {
+
+// Device pointer to grid quantity `which` of the selected simulation (J, rho: converted
+// into s->tmp).
+int field_source(pic_sim* s, int32_t which, const double** out_src) {
     if (which < PIC_EX || which > PIC_RHO) return fail(s, PIC_EINVAL, "which must be PIC_EX..PIC_RHO");
     if (which >= PIC_RHSX && which <= PIC_RHSZ && !s->bvec)
         return fail(s, PIC_ESTATE, "the right-hand side is kept in PIC_MIXED32 only");
     const GridDev& G = s->hgrids[s->sel];
     const long long nc = G.ncell, off = G.cell_off;
-    if (!out || len < (size_t)nc) return fail(s, PIC_EINVAL, "out must hold nx*ny values");
     const double* src = nullptr;
     if (which <= PIC_BZ) {
         src = s->F + which * s->ntot + off;
@@ -1206,8 +1207,56 @@ int pic_fields(pic_sim* s, int32_t which, double* out, size_t len) {
         if (int rc = charge_density(s, s->tmp)) return rc;
         src = s->tmp;
     }
+    *out_src = src;
+    return PIC_OK;
+}
+
+}  // namespace
+
+int pic_fields(pic_sim* s, int32_t which, double* out, size_t len) {
+    if (!s) return PIC_EINVAL;
+    cudaSetDevice(s->device);
+    const long long nc = s->hgrids[s->sel].ncell;
+    if (!out || len < (size_t)nc) return fail(s, PIC_EINVAL, "out must hold nx*ny values");
+    const double* src = nullptr;
+    if (int rc = field_source(s, which, &src)) return rc;
     CK(cudaMemcpyAsync(out, src, nc * sizeof(double), cudaMemcpyDefault, s->stream));
     return finish_call(s);
+}
+
+int pic_spectrum(pic_sim* s, int32_t which, double* out, size_t len) {
+    if (!s) return PIC_EINVAL;
+    cudaSetDevice(s->device);
+    const GridDev& G = s->hgrids[s->sel];
+    const long long nc = G.ncell;
+    if (!out || len < (size_t)nc) return fail(s, PIC_EINVAL, "out must hold nx*ny values");
+    const double* src = nullptr;
+    if (int rc = field_source(s, which, &src)) return rc;
+    double* dout = nullptr;
+    CK(dalloc(&dout, nc));
+    int rc = spectrum_2d(src, G.nx, G.ny, dout, s->stream, s->err);
+    if (rc == PIC_OK) {
+        cudaError_t e = cudaMemcpyAsync(out, dout, nc * sizeof(double), cudaMemcpyDefault, s->stream);
+        if (e == cudaSuccess) e = cudaStreamSynchronize(s->stream);
+        if (e != cudaSuccess) rc = fail(s, PIC_ECUDA, std::string("pic_spectrum: ") + cudaGetErrorString(e));
+    }
+    cudaFree(dout);
+    if (rc) return rc;
+    return finish_call(s);
+}
+
+int pic_resonance_ky(double cfl_x, double cfl_y, double beta, double kx_dx, double* ky_dy) {
+    if (!ky_dy || !(cfl_x > 0.0) || !(cfl_y > 0.0) || !(beta > 0.0 && beta < 1.0) || !(kx_dx > 0.0 && kx_dx <= kPi))
+        return PIC_EINVAL;
+    const double a = 0.5 * beta * cfl_x * kx_dx;  // V k_x dt / 2
+    if (a >= 0.5 * kPi) return PIC_EINVAL;
+    const double t = std::tan(a), sx = cfl_x * std::sin(0.5 * kx_dx);
+    const double d = t * t - sx * sx;
+    if (d < 0.0) return PIC_EINVAL;
+    const double arg = std::sqrt(d) / cfl_y;
+    if (arg > 1.0) return PIC_EINVAL;
+    *ky_dy = 2.0 * std::asin(arg);
+    return PIC_OK;
 }
 
 int pic_moments(pic_sim* s, pic_moments_t* m) {

@@ -107,4 +107,8 @@ void launch_rho_fp64(const GridDev& G, const double* x, const double* y, long lo
 void launch_momentum_fp64(const double* ux, const double* uy, const double* uz, long long n, double w,
                           double* out, cudaStream_t s);
 
+// Amplitude spectrum |F^(p, q)| / (nx ny) of an (ny, nx) FP64 grid quantity F (device)
+// into out (device), both in the fields' layout (spectrum.cu).
+int spectrum_2d(const double* F, int nx, int ny, double* out, cudaStream_t st, std::string& err);
+
 }  // namespace pic
