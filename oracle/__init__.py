@@ -76,6 +76,7 @@ def lib():
             L.or_pcg.restype = C.c_int32
             L.or_pcg.argtypes = [G, _P, _P, C.c_double, C.c_int32, C.POINTER(C.c_double)]
             L.or_field_update.argtypes = [G, _P, _P, _P]
+            L.or_explicit_update.argtypes = [G, _P, _P]
             for name in ("or_div_E", "or_div_B", "or_div_J"):
                 getattr(L, name).argtypes = [G, _P, _P]
             L.or_field_energy.argtypes = [G, _P, C.POINTER(C.c_double), C.POINTER(C.c_double)]
@@ -172,6 +173,13 @@ def pcg(g, b, x0=None, rtol=1e-10, maxit=1000):
 def field_update(g, F, dB, J):
     F = _c(F).ravel().copy()
     lib().or_field_update(C.byref(g), F, _c(dB).ravel(), _c(J).ravel())
+    return F
+
+
+def explicit_update(g, F, J):
+    """Explicit FDTD step of the fields, Eqs. (3)-(4) (see oracle.h)."""
+    F = _c(F).ravel().copy()
+    lib().or_explicit_update(C.byref(g), F, _c(J).ravel())
     return F
 
 
@@ -315,8 +323,12 @@ class OracleSim:
 
     def __init__(self, nx, ny, cfl, theta, order, species, dx=1.0, dy=1.0,
                  cg_rtol=1e-10, cg_max_iter=1000, warm_start="zero", fields=None,
-                 deposit=True, walls=False, injector=None):
+                 deposit=True, walls=False, injector=None, solver="implicit"):
         self.g = grid(nx, ny, cfl * dx, theta, order, dx, dy, walls)
+        # "implicit": Eq. (7) by PCG and Eqs. (5)-(6); "explicit": Eqs. (3)-(4)
+        if solver not in ("implicit", "explicit"):
+            raise ValueError("solver must be 'implicit' or 'explicit'")
+        self.solver = solver
         self.N = nx * ny
         self.species = list(species)
         self.F = np.zeros(6 * self.N) if fields is None else _c(fields).ravel().copy()
@@ -344,6 +356,10 @@ class OracleSim:
                 s.uz, self.J, 1 if self.deposit else 0))
 
     def field_solve(self):
+        if self.solver == "explicit":
+            self.F = explicit_update(self.g, self.F, self.J)
+            self.last_cg_iters, self.last_cg_resid = 0, 0.0
+            return
         b = rhs(self.g, self.F, self.J)
         x0 = self.dB if self.warm_start == "prev" else None
         dB, it, rr = pcg(self.g, b, x0, self.cg_rtol, self.cg_max_iter)

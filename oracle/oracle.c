@@ -440,6 +440,23 @@ void or_field_update(const or_grid* g, double* F, const double* dB, const double
     free(curlBh);
 }
 
+/* Explicit FDTD (Eqs. 3-4). Eq. (3) advances B between half-integer time levels; the
+ * particle push needs B at integer levels, so each step splits Eq. (3) into two halves
+ * around Eq. (4): B^{n+1/2} - B^{n-1/2} = -c dt curl E^n still holds step to step. */
+void or_explicit_update(const or_grid* g, double* F, const double* J) {
+    const int64_t N = (int64_t)g->nx * g->ny;
+    double* curl = malloc(3 * N * sizeof(double));
+    curl_E_lattice(g, F, curl); /* curl E^n on the B lattices */
+    for (int64_t k = 0; k < 3 * N; k++) F[3 * N + k] -= 0.5 * g->dt * curl[k];
+    curl_B_lattice(g, F + 3 * N, curl); /* curl B^{n+1/2} on the E lattices */
+    for (int64_t k = 0; k < 3 * N; k++) F[k] += g->dt * (curl[k] - 4.0 * PI * J[k]);
+    if (g->walls) /* the conductor keeps Ey = Ez = 0 on the wall */
+        for (int j = 0; j < g->ny; j++) F[N + at(g, 0, j)] = F[2 * N + at(g, 0, j)] = 0.0;
+    curl_E_lattice(g, F, curl); /* curl E^{n+1} */
+    for (int64_t k = 0; k < 3 * N; k++) F[3 * N + k] -= 0.5 * g->dt * curl[k];
+    free(curl);
+}
+
 void or_div_E(const or_grid* g, const double* F, double* out) {
     const int64_t N = (int64_t)g->nx * g->ny;
     const double *Ex = F, *Ey = F + N;

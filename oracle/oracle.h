@@ -97,6 +97,11 @@ int32_t or_pcg(const or_grid* g, const double* b, double* x, double rtol, int32_
  * then B += dB. */
 void or_field_update(const or_grid* g, double* F, const double* dB, const double* J);
 
+/* Explicit FDTD update, Eqs. (3)-(4), B kept at integer time levels: B^{n+1/2} =
+ * B^n - (c dt/2) curl E^n; E^{n+1} = E^n + c dt curl B^{n+1/2} - 4 pi dt J^{n+1/2};
+ * B^{n+1} = B^{n+1/2} - (c dt/2) curl E^{n+1}. theta is not used. */
+void or_explicit_update(const or_grid* g, double* F, const double* J);
+
 /* Discrete divergences: div E at nodes (nx*ny), div B at cell centres (nx*ny). */
 void or_div_E(const or_grid* g, const double* F, double* out);
 void or_div_B(const or_grid* g, const double* F, double* out);
