@@ -45,7 +45,10 @@ WORKLOADS = {
     "cfg1": (64, 64, 8, 1, 20.0, 1e-3, 1.0, 0.5, 1),
     # a quarter of cfg2 (same density and physics, 16.8M particles): profiling captures
     "cfg2q": (1024, 256, 32, 2, 40.0, 1e-3, 1.0, 0.5, 2),
+    # cfg2's plasma under the explicit FDTD update (Eqs. 3-4) at CFL 0.5
+    "cfg2x": (2048, 512, 32, 2, 40.0, 1e-3, 0.5, 0.5, 2),
 }
+EXPLICIT = {"cfg2x"}
 SHOCK = {
     # the shock configuration: a magnetised pair beam (sigma_B 0.1, Bz with the motional
     # Ey) flowing into the conducting, reflecting wall at x = 0, filling the left half of
@@ -76,7 +79,7 @@ def rows_of(name, rank=0):
                  "inject_x0": c["fill"] * c["nx"], "inj_seed": c["inj_seed"] + rank}]
     nx, ny, ppc, order, g0, uth, cfl, theta, seed = WORKLOADS[name]
     return [{"k": 0, "nx": nx, "ny": ny, "cfl": cfl, "theta": theta, "order": order,
-             "gamma0": g0, "ppc": ppc, "u_th": uth, "seed": seed + rank}]
+             "gamma0": g0, "ppc": ppc, "u_th": uth, "seed": seed + rank, "explicit": name in EXPLICIT}]
 
 
 def injected_pairs_per_row(r, n):
@@ -113,6 +116,9 @@ def describe(name):
                 f"CFL 0.5-1.0, theta 0.5-0.75, orders 1-3, pair plasma gamma0 20, u_th 1e-3, "
                 f"16 ppc/species ({2 * 16 * cells} particles), PCG rtol 1e-10, autotuned tiles")
     nx, ny, ppc, order, g0, uth, cfl, theta, seed = WORKLOADS[name]
+    if name in EXPLICIT:
+        return (f"{nx}x{ny} periodic, explicit FDTD (Eqs. 3-4), CFL {cfl}, order {order}, pair plasma "
+                f"gamma0 {g0:g}, u_th {uth:g}, {ppc} ppc/species ({2 * nx * ny * ppc} particles)")
     return (f"{nx}x{ny} periodic, CFL {cfl}, theta {theta}, order {order}, pair plasma "
             f"gamma0 {g0:g}, u_th {uth:g}, {ppc} ppc/species ({2 * nx * ny * ppc} particles), "
             f"PCG rtol 1e-10")
@@ -237,10 +243,11 @@ def params_of(rows, precision):
         kw = {}
         if r.get("walls"):
             kw = dict(bc_x=pic.PIC_BC_WALLS, inject_x0=r["inject_x0"], u_th=r["u_th"], seed=r["inj_seed"])
+        flags = (pic.PIC_NO_GRAPH if NO_GRAPH else 0) | (pic.PIC_EXPLICIT if r.get("explicit") else 0)
         out.append(pic.pic_params_default(nx=r["nx"], ny=r["ny"], cfl=r["cfl"], theta=r["theta"],
                                           shape_order=r["order"], gamma0=r["gamma0"], ppc=r["ppc"],
                                           precision=precision, cg_rtol=1e-10, cg_max_iter=200,
-                                          flags=pic.PIC_NO_GRAPH if NO_GRAPH else 0,
+                                          flags=flags,
                                           tile_x=r.get("tile_x", 0), tile_y=r.get("tile_y", 0), **kw))
     return out
 
@@ -448,7 +455,8 @@ def oracle_sample(name, seconds_target=12.0):
         w, sp = inputs.drifting_pair_plasma(sx, sy, r["ppc"], r["gamma0"], r["u_th"], r["seed"])
     species = [oracle.Species(d["qm"], w, d["x"], d["y"], d["ux"], d["uy"], d["uz"]) for d in sp]
     sim = oracle.OracleSim(sx, sy, r["cfl"], r["theta"], r["order"], species, cg_rtol=1e-10,
-                           fields=F0, walls=bool(r.get("walls")), injector=inj)
+                           fields=F0, walls=bool(r.get("walls")), injector=inj,
+                           solver="explicit" if r.get("explicit") else "implicit")
     oracle.build()
     steps, t, upd = 0, 0.0, 0
     while t < seconds_target and steps < 50:
@@ -540,8 +548,9 @@ def main():
         "scaling": "weak", "vs_baseline": None, "dtype": "f32" if mixed else "f64",
         "data": "synthetic",
         "config": {"workload": describe(args.workload),
-                   "form": "MIXED32 (int cell + FP32 offset; FP32 gather/push/deposit; FP64 field "
-                           "update and PCG residual with FP32 inner CG)" if mixed else "FP64",
+                   "form": ("MIXED32 (int cell + FP32 offset; FP32 gather/push/deposit; "
+                            + ("FP64 explicit field update)" if args.workload in EXPLICIT else
+                               "FP64 field update and PCG residual with FP32 inner CG)")) if mixed else "FP64",
                    "l2": "inputs larger than L2 (particle state 1.6 GB MIXED32 / 2.7 GB FP64 for cfg2, "
                          "2.1 GB for scan48)",
                    "replicas": world},

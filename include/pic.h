@@ -69,6 +69,10 @@ extern "C" {
 #define PIC_NO_GRAPH 2     /* launch kernels directly instead of a captured CUDA graph */
 #define PIC_NO_COOP 4      /* PIC_MIXED32: run the PCG loop as graph-driven kernel launches instead
                               of one cooperative persistent kernel (same arithmetic) */
+#define PIC_EXPLICIT 8     /* explicit FDTD field update, Eqs. (3)-(4), instead of the implicit
+                              theta scheme (theta and the PCG settings are not used); B is kept
+                              at integer time levels by two half steps of Eq. (3) around Eq. (4).
+                              Needs (c dt)^2 (1/dx^2 + 1/dy^2) <= 1 (Courant limit, Eq. 16) */
 
 /* ---- x boundaries ----
  * PIC_BC_WALLS closes the box in x with two perfectly conducting walls at x = 0 and
@@ -135,7 +139,7 @@ typedef struct pic_params {
     double cg_rtol;        /* stop when ||r||_2 <= cg_rtol ||b||_2, default 1e-10 */
     int32_t cg_max_iter;   /* default 200 */
     int32_t warm_start;    /* PIC_WS_ZERO, PIC_WS_PREV or PIC_WS_LEARNED */
-    int32_t flags;         /* PIC_NO_DEPOSIT | PIC_NO_GRAPH */
+    int32_t flags;         /* PIC_NO_DEPOSIT | PIC_NO_GRAPH | PIC_NO_COOP | PIC_EXPLICIT */
     int32_t tile_x, tile_y;/* MIXED32 tile size in cells; 0 = chosen by the library */
     double bin_slack;      /* MIXED32 bin capacity factor over ppc * tile cells; 0 = 1.5 */
     int32_t bc_x;          /* PIC_BC_PERIODIC or PIC_BC_WALLS (x boundaries; y is periodic) */

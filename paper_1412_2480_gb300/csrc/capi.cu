@@ -142,6 +142,13 @@ int validate(const pic_params* p, std::string& why) {
         return bad("warm_start must be PIC_WS_ZERO, PIC_WS_PREV or PIC_WS_LEARNED");
     if (p->warm_start == PIC_WS_LEARNED && p->precision != PIC_MIXED32)
         return bad("PIC_WS_LEARNED requires PIC_MIXED32");
+    if (p->flags & PIC_EXPLICIT) {
+        // Eq. (16): real frequencies for every mode need (c dt)^2 (1/dx^2 + 1/dy^2) <= 1
+        const double dt = p->cfl * p->dx;
+        if (dt * dt * (1.0 / (p->dx * p->dx) + 1.0 / (p->dy * p->dy)) > 1.0 + 1e-12)
+            return bad("PIC_EXPLICIT needs (c dt)^2 (1/dx^2 + 1/dy^2) <= 1 (Courant limit of Eq. 16)");
+        if (p->warm_start == PIC_WS_LEARNED) return bad("PIC_EXPLICIT has no solve to warm-start");
+    }
     if (p->tile_x < 0 || p->tile_y < 0) return bad("tile sizes must be >= 0");
     const int tx = std::min(p->tile_x > 0 ? p->tile_x : 32, p->nx);
     const int ty = std::min(p->tile_y > 0 ? p->tile_y : 16, p->ny);
@@ -170,7 +177,7 @@ void fill_grid(const pic_params& p, GridDev& G) {
     G.dx = p.dx;
     G.dy = p.dy;
     G.dt = p.cfl * p.dx;
-    G.theta = p.theta;
+    G.theta = (p.flags & PIC_EXPLICIT) ? 1.0 : p.theta;  // explicit: E sees the whole half step
     G.idx = 1.0 / p.dx;
     G.idy = 1.0 / p.dy;
     G.a = (p.theta * G.dt) * (p.theta * G.dt);
@@ -381,6 +388,10 @@ int capture(pic_sim* s, int mask, cudaGraph_t* gout, cudaGraphExec_t* xout) {
             enqueue_part(s, part, st);
             continue;
         }
+        if (s->prm.flags & PIC_EXPLICIT) {
+            launch_explicit_fields(field_args(s, 0, 0), st);
+            continue;
+        }
         if (s->use_coop) {
             // rhs -> (learned guess) -> one cooperative kernel for the whole PCG -> update
             launch_rhs(field_args(s, 0, 0), st);
@@ -465,7 +476,9 @@ int build_graph(pic_sim* s) {
 // the same count from the step's structure for direct launches.
 long long step_kernels(pic_sim* s, bool graph) {
     if (graph && s->graph_kernels >= 0) return s->graph_kernels;
-    long long k = 6;  // step begin and end, zero_x, rhs, update_E, update_B
+    // step begin and end; field part: explicit half step, update_E, explicit_B, or
+    // zero_x, rhs, update_E, update_B (+ the cooperative solve)
+    long long k = (s->prm.flags & PIC_EXPLICIT) ? 5 : 6;
     if (s->prm.precision == PIC_MIXED32) {
         k += mixed_step_kernels(s->mixed);
     } else {
@@ -491,6 +504,12 @@ int run_step_direct(pic_sim* s) {
     enqueue_part(s, kPartPush, st);
     enqueue_part(s, kPartPost, st);
     const FieldArgs a = field_args(s, 0, 0);
+    if (s->prm.flags & PIC_EXPLICIT) {
+        launch_explicit_fields(a, st);
+        enqueue_part(s, kPartEnd, st);
+        CK(cudaGetLastError());
+        return PIC_OK;
+    }
     launch_rhs(a, st);
     if (s->learned) {
         launch_learned_guess(s->guess, s->dgrids, s->cg, s->ntot, s->bvec, s->x, st);
@@ -770,7 +789,7 @@ int init_handle(const pic_params* prm, int n, pic_sim** out) {
     if (s->J64) A(cudaMemset(s->J64, 0, n3 * sizeof(double)));
     if (s->Jfix) A(cudaMemset(s->Jfix, 0, n3 * sizeof(long long)));
     if (s->F32) A(cudaMemset(s->F32, 0, 6 * s->ntot * sizeof(float)));
-    if (prm[0].precision == PIC_MIXED32 && !(prm[0].flags & PIC_NO_COOP)) {
+    if (prm[0].precision == PIC_MIXED32 && !(prm[0].flags & (PIC_NO_COOP | PIC_EXPLICIT))) {
         const int rc = coop_create(&s->coop, s->hgrids.data(), s->ngrids, s->err);
         if (rc == PIC_ECUDA) return bail(rc);
         s->use_coop = rc == PIC_OK;
@@ -899,8 +918,9 @@ int pic_init_batch(const pic_params* prm, int32_t n, pic_sim** out) {
             if (prm[k].precision != PIC_MIXED32)
                 return fail(nullptr, PIC_EINVAL, "a batch of more than one simulation requires PIC_MIXED32");
         for (int k = 1; k < n; k++)
-            if ((prm[k].flags & PIC_NO_GRAPH) != (prm[0].flags & PIC_NO_GRAPH))
-                return fail(nullptr, PIC_EINVAL, "PIC_NO_GRAPH must be the same for every simulation");
+            if ((prm[k].flags & (PIC_NO_GRAPH | PIC_EXPLICIT)) != (prm[0].flags & (PIC_NO_GRAPH | PIC_EXPLICIT)))
+                return fail(nullptr, PIC_EINVAL,
+                            "PIC_NO_GRAPH and PIC_EXPLICIT must be the same for every simulation");
         for (int k = 1; k < n; k++)
             if ((prm[k].warm_start == PIC_WS_LEARNED) != (prm[0].warm_start == PIC_WS_LEARNED))
                 return fail(nullptr, PIC_EINVAL, "PIC_WS_LEARNED must be used by all simulations or none");

@@ -49,6 +49,8 @@ void launch_guess_residual(const FieldArgs& a, cudaStream_t s);
 void launch_cg_iteration(const FieldArgs& a, cudaStream_t s);
 // E, B from Eqs. (5)-(6) with dB; FP32 copies when a.F32 is set.
 void launch_field_update(const FieldArgs& a, cudaStream_t s);
+// Explicit FDTD field step, Eqs. (3)-(4) (PIC_EXPLICIT): three kernels, no solve.
+void launch_explicit_fields(const FieldArgs& a, cudaStream_t s);
 // FP32 copy of the FP64 fields (after pic_set_fields / init).
 void launch_fields_to_f32(const FieldArgs& a, cudaStream_t s);
 

@@ -362,6 +362,79 @@ k_update_E(const GridDev* __restrict__ grids, const int* __restrict__ blk_grid, 
     }
 }
 
+// Explicit FDTD (Eqs. 3-4; PIC_EXPLICIT), with B kept at integer time levels for the
+// gather: x = B^{n+1/2} - B^n = -(c dt/2) curl E^n here, together with the energies of
+// level n; then k_update_E with theta = 1 applies E^{n+1} = E^n + c dt curl B^{n+1/2}
+// - 4 pi dt J; then k_explicit_B forms B^{n+1} = B^{n+1/2} - (c dt/2) curl E^{n+1}.
+__global__ void __launch_bounds__(kFieldThreads)
+k_explicit_half(const GridDev* __restrict__ grids, const int* __restrict__ blk_grid, int nblk_total,
+                long long ntot, const double* __restrict__ F, double* __restrict__ x, CgState* cg,
+                double* part, unsigned int* done, const DevStatus* st) {
+    const int g = blk_grid[blockIdx.x];
+    const GridDev& G = grids[g];
+    double v[2] = {0.0, 0.0};  // |E|^2, |B|^2
+    if (!st->stop) FOR_CELLS(G, g, c) {
+        const double* Ex = F;
+        const double* Ey = F + ntot;
+        const double* Ez = F + 2 * ntot;
+        const double ez = Ez[c.k];
+        const double h = -0.5 * G.dt;
+        x[c.k] = h * (Ez[c.kn] - ez) * G.idy;
+        x[ntot + c.k] = -h * (east_odd(Ez, c) - ez) * G.idx;
+        x[2 * ntot + c.k] = h * ((east_odd(Ey, c) - Ey[c.k]) * G.idx - (Ex[c.kn] - Ex[c.k]) * G.idy);
+        v[0] += Ex[c.k] * Ex[c.k] + Ey[c.k] * Ey[c.k] + ez * ez;
+#pragma unroll
+        for (int a = 0; a < 3; a++) {
+            const double b = F[(3 + a) * ntot + c.k];
+            v[1] += b * b;
+        }
+    }
+    double tot[2];
+    if (!reduce_and_finish<2>(G, g, v, part, nblk_total, done, tot)) return;
+    if (threadIdx.x == 0) {
+        CgState& s = cg[g];
+        const double e = G.dx * G.dy / (8.0 * kPi);
+        s.ue = tot[0] * e;
+        s.ub = tot[1] * e;
+        s.bb = 1.0;  // k_update_E applies x (with theta = 1)
+        s.rr = 0.0;
+        s.rel = 0.0;
+        s.iters = 0;
+        s.outer = 0;
+        s.active = 0;
+    }
+}
+
+__global__ void __launch_bounds__(kFieldThreads)
+k_explicit_B(const GridDev* __restrict__ grids, const int* __restrict__ blk_grid, long long ntot,
+             double* __restrict__ F, const double* __restrict__ x, const DevStatus* st,
+             float* __restrict__ F32) {
+    if (st->stop) return;
+    const int g = blk_grid[blockIdx.x];
+    const GridDev& G = grids[g];
+    const double* Ex = F;
+    const double* Ey = F + ntot;
+    const double* Ez = F + 2 * ntot;
+    const double h = -0.5 * G.dt;
+    FOR_CELLS(G, g, c) {
+        const double ez = Ez[c.k];
+        const double dB[3] = {h * (Ez[c.kn] - ez) * G.idy, -h * (east_odd(Ez, c) - ez) * G.idx,
+                              h * ((east_odd(Ey, c) - Ey[c.k]) * G.idx - (Ex[c.kn] - Ex[c.k]) * G.idy)};
+#pragma unroll
+        for (int a = 0; a < 3; a++) {
+            const long long o = (3 + a) * ntot + c.k;
+            const double b = F[o] + x[a * ntot + c.k] + dB[a];
+            F[o] = b;
+            if (F32) F32[o] = (float)b;
+        }
+        if (F32) {
+            F32[c.k] = (float)Ex[c.k];
+            F32[ntot + c.k] = (float)Ey[c.k];
+            F32[2 * ntot + c.k] = (float)ez;
+        }
+    }
+}
+
 // B^{n+1} = B^n + dB, then the FP32 copies used by the MIXED32 gather.
 __global__ void __launch_bounds__(kFieldThreads)
 k_update_B(const GridDev* __restrict__ grids, const int* __restrict__ blk_grid, long long ntot,
@@ -671,6 +744,18 @@ void launch_mp_refine(const FieldArgs& a, cudaStream_t s) {
     k_mp_r<<<a.nblk, kFieldThreads, 0, s>>>(a.grids, a.blk_grid, a.ngrids, a.nblk, a.ntot, a.b,
                                             a.x, a.r, a.cg, a.part, a.done, a.st, a.cond,
                                             a.use_cond);
+}
+
+void launch_explicit_fields(const FieldArgs& a, cudaStream_t s) {
+    k_explicit_half<<<a.nblk, kFieldThreads, 0, s>>>(a.grids, a.blk_grid, a.nblk, a.ntot, a.F, a.x, a.cg,
+                                                     a.part, a.done, a.st);
+    if (a.Jfix)
+        k_update_E<long long><<<a.nblk, kFieldThreads, 0, s>>>(a.grids, a.blk_grid, a.ntot, a.F, a.Jfix, a.x,
+                                                               a.cg, a.st);
+    else
+        k_update_E<double><<<a.nblk, kFieldThreads, 0, s>>>(a.grids, a.blk_grid, a.ntot, a.F, a.J64, a.x,
+                                                            a.cg, a.st);
+    k_explicit_B<<<a.nblk, kFieldThreads, 0, s>>>(a.grids, a.blk_grid, a.ntot, a.F, a.x, a.st, a.F32);
 }
 
 void launch_cg_iteration(const FieldArgs& a, cudaStream_t s) {
