@@ -49,7 +49,7 @@ def build(force: bool = False) -> str:
 class Grid(C.Structure):
     _fields_ = [("nx", C.c_int32), ("ny", C.c_int32), ("dx", C.c_double),
                 ("dy", C.c_double), ("dt", C.c_double), ("theta", C.c_double),
-                ("order", C.c_int32), ("walls", C.c_int32)]
+                ("order", C.c_int32), ("walls", C.c_int32), ("nodal", C.c_int32)]
 
 
 _P = np.ctypeslib.ndpointer(dtype=np.float64, flags="C_CONTIGUOUS")
@@ -84,11 +84,15 @@ def lib():
     return _lib
 
 
-def grid(nx, ny, dt, theta, order, dx=1.0, dy=1.0, walls=False) -> Grid:
+def grid(nx, ny, dt, theta, order, dx=1.0, dy=1.0, walls=False, gather="staggered") -> Grid:
+    """gather: "staggered" (each component on its own lattice) or "nodal" (fields
+    averaged to the nodes first; periodic only)."""
     if nx < 8 or ny < 8:
         raise ValueError("the oracle needs nx, ny >= 8")
+    if gather not in ("staggered", "nodal") or (gather == "nodal" and walls):
+        raise ValueError("gather must be 'staggered' or 'nodal' (nodal without walls)")
     return Grid(int(nx), int(ny), float(dx), float(dy), float(dt), float(theta), int(order),
-                1 if walls else 0)
+                1 if walls else 0, 1 if gather == "nodal" else 0)
 
 
 def wall_nodes_zeroed(F, nx, ny):
@@ -323,8 +327,8 @@ class OracleSim:
 
     def __init__(self, nx, ny, cfl, theta, order, species, dx=1.0, dy=1.0,
                  cg_rtol=1e-10, cg_max_iter=1000, warm_start="zero", fields=None,
-                 deposit=True, walls=False, injector=None, solver="implicit"):
-        self.g = grid(nx, ny, cfl * dx, theta, order, dx, dy, walls)
+                 deposit=True, walls=False, injector=None, solver="implicit", gather="staggered"):
+        self.g = grid(nx, ny, cfl * dx, theta, order, dx, dy, walls, gather)
         # "implicit": Eq. (7) by PCG and Eqs. (5)-(6); "explicit": Eqs. (3)-(4)
         if solver not in ("implicit", "explicit"):
             raise ValueError("solver must be 'implicit' or 'explicit'")

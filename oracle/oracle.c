@@ -99,9 +99,41 @@ double or_shape(int32_t p, double d) {
  * charge. Each component is gathered on its own staggered lattice:
  *   F(x,y) = sum_{i,j} W_p(x/dx - i - ox) W_p(y/dy - j - oy) F_{ij}.
  * The sum runs over a window wider than any support (|d| < 2); zero weights drop out. */
+/* The alternative reading (nodal = 1): every component is first averaged from its
+ * staggered lattice to the node (i, j) -- over the two neighbours along each staggered
+ * direction: Ex, By along x; Ey, Bx along y; Bz over the four surrounding cells; Ez is a
+ * node quantity -- and then gathered with the node weights of the charge deposit. */
+static double node_average(const or_grid* g, const double* V, int c, int i, int j) {
+    switch (c) {
+    case 0: case 4: return 0.5 * (val(g, V, 1, i - 1, j) + val(g, V, 1, i, j));
+    case 1: case 3: return 0.5 * (val(g, V, 0, i, j - 1) + val(g, V, 0, i, j));
+    case 2: return val(g, V, 0, i, j);
+    default:
+        return 0.25 * (val(g, V, 1, i - 1, j - 1) + val(g, V, 1, i, j - 1) + val(g, V, 1, i - 1, j) +
+                       val(g, V, 1, i, j));
+    }
+}
+
 static void gather_one(const or_grid* g, const double* F, double x, double y, double f[6]) {
     const int64_t N = (int64_t)g->nx * g->ny;
     const double xg = x / g->dx, yg = y / g->dy;
+    if (g->nodal) {
+        const int i0 = (int)floor(xg) - 2, j0 = (int)floor(yg) - 2;
+        for (int c = 0; c < 6; c++) {
+            double acc = 0.0;
+            for (int j = j0; j <= j0 + 5; j++) {
+                const double wy = or_shape(g->order, yg - j);
+                if (wy == 0.0) continue;
+                for (int i = i0; i <= i0 + 5; i++) {
+                    const double wx = or_shape(g->order, xg - i);
+                    if (wx == 0.0) continue;
+                    acc += wx * wy * node_average(g, F + c * N, c, i, j);
+                }
+            }
+            f[c] = acc;
+        }
+        return;
+    }
     for (int c = 0; c < 6; c++) {
         const double sx = xg - OFF_X[c], sy = yg - OFF_Y[c];
         const int i0 = (int)floor(sx) - 2, j0 = (int)floor(sy) - 2;

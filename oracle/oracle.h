@@ -48,6 +48,8 @@ typedef struct {
     double theta;     /* implicitness factor of Eqs. (5)-(6), 0.5 <= theta <= 1 */
     int32_t order;    /* particle shape order 1, 2 or 3 */
     int32_t walls;    /* 0: periodic in x; 1: conducting, reflecting walls at x = 0, nx dx */
+    int32_t nodal;    /* gather reading: 0 each component on its own staggered lattice;
+                         1 the fields averaged to the nodes first (periodic only) */
 } or_grid;
 
 /* Centred cardinal B-spline of order p (degree p): the particle shape. */
