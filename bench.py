@@ -47,8 +47,11 @@ WORKLOADS = {
     "cfg2q": (1024, 256, 32, 2, 40.0, 1e-3, 1.0, 0.5, 2),
     # cfg2's plasma under the explicit FDTD update (Eqs. 3-4) at CFL 0.5
     "cfg2x": (2048, 512, 32, 2, 40.0, 1e-3, 0.5, 0.5, 2),
+    # cfg2 with the node-averaged gather reading
+    "cfg2n": (2048, 512, 32, 2, 40.0, 1e-3, 1.0, 0.5, 2),
 }
 EXPLICIT = {"cfg2x"}
+NODAL = {"cfg2n"}
 SHOCK = {
     # the shock configuration: a magnetised pair beam (sigma_B 0.1, Bz with the motional
     # Ey) flowing into the conducting, reflecting wall at x = 0, filling the left half of
@@ -79,7 +82,8 @@ def rows_of(name, rank=0):
                  "inject_x0": c["fill"] * c["nx"], "inj_seed": c["inj_seed"] + rank}]
     nx, ny, ppc, order, g0, uth, cfl, theta, seed = WORKLOADS[name]
     return [{"k": 0, "nx": nx, "ny": ny, "cfl": cfl, "theta": theta, "order": order,
-             "gamma0": g0, "ppc": ppc, "u_th": uth, "seed": seed + rank, "explicit": name in EXPLICIT}]
+             "gamma0": g0, "ppc": ppc, "u_th": uth, "seed": seed + rank, "explicit": name in EXPLICIT,
+             "nodal": name in NODAL}]
 
 
 def injected_pairs_per_row(r, n):
@@ -119,6 +123,10 @@ def describe(name):
     if name in EXPLICIT:
         return (f"{nx}x{ny} periodic, explicit FDTD (Eqs. 3-4), CFL {cfl}, order {order}, pair plasma "
                 f"gamma0 {g0:g}, u_th {uth:g}, {ppc} ppc/species ({2 * nx * ny * ppc} particles)")
+    if name in NODAL:
+        return (f"{nx}x{ny} periodic, node-averaged gather, CFL {cfl}, theta {theta}, order {order}, "
+                f"pair plasma gamma0 {g0:g}, u_th {uth:g}, {ppc} ppc/species ({2 * nx * ny * ppc} particles), "
+                f"PCG rtol 1e-10")
     return (f"{nx}x{ny} periodic, CFL {cfl}, theta {theta}, order {order}, pair plasma "
             f"gamma0 {g0:g}, u_th {uth:g}, {ppc} ppc/species ({2 * nx * ny * ppc} particles), "
             f"PCG rtol 1e-10")
@@ -244,6 +252,7 @@ def params_of(rows, precision):
         if r.get("walls"):
             kw = dict(bc_x=pic.PIC_BC_WALLS, inject_x0=r["inject_x0"], u_th=r["u_th"], seed=r["inj_seed"])
         flags = (pic.PIC_NO_GRAPH if NO_GRAPH else 0) | (pic.PIC_EXPLICIT if r.get("explicit") else 0)
+        flags |= pic.PIC_GATHER_NODAL if r.get("nodal") else 0
         out.append(pic.pic_params_default(nx=r["nx"], ny=r["ny"], cfl=r["cfl"], theta=r["theta"],
                                           shape_order=r["order"], gamma0=r["gamma0"], ppc=r["ppc"],
                                           precision=precision, cg_rtol=1e-10, cg_max_iter=200,
@@ -456,7 +465,8 @@ def oracle_sample(name, seconds_target=12.0):
     species = [oracle.Species(d["qm"], w, d["x"], d["y"], d["ux"], d["uy"], d["uz"]) for d in sp]
     sim = oracle.OracleSim(sx, sy, r["cfl"], r["theta"], r["order"], species, cg_rtol=1e-10,
                            fields=F0, walls=bool(r.get("walls")), injector=inj,
-                           solver="explicit" if r.get("explicit") else "implicit")
+                           solver="explicit" if r.get("explicit") else "implicit",
+                           gather="nodal" if r.get("nodal") else "staggered")
     oracle.build()
     steps, t, upd = 0, 0.0, 0
     while t < seconds_target and steps < 50:

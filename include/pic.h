@@ -73,6 +73,11 @@ extern "C" {
                               theta scheme (theta and the PCG settings are not used); B is kept
                               at integer time levels by two half steps of Eq. (3) around Eq. (4).
                               Needs (c dt)^2 (1/dx^2 + 1/dy^2) <= 1 (Courant limit, Eq. 16) */
+#define PIC_GATHER_NODAL 16 /* the alternative reading of the momentum-conserving gather: E and B
+                              are first averaged from their staggered lattices to the nodes (Ex, By
+                              over two x-neighbours, Ey, Bx over two y-neighbours, Bz over four
+                              cells) and every component is then gathered with the node weights
+                              of the charge deposit; periodic boundaries only */
 
 /* ---- x boundaries ----
  * PIC_BC_WALLS closes the box in x with two perfectly conducting walls at x = 0 and
@@ -139,7 +144,8 @@ typedef struct pic_params {
     double cg_rtol;        /* stop when ||r||_2 <= cg_rtol ||b||_2, default 1e-10 */
     int32_t cg_max_iter;   /* default 200 */
     int32_t warm_start;    /* PIC_WS_ZERO, PIC_WS_PREV or PIC_WS_LEARNED */
-    int32_t flags;         /* PIC_NO_DEPOSIT | PIC_NO_GRAPH | PIC_NO_COOP | PIC_EXPLICIT */
+    int32_t flags;         /* PIC_NO_DEPOSIT | PIC_NO_GRAPH | PIC_NO_COOP | PIC_EXPLICIT |
+                              PIC_GATHER_NODAL */
     int32_t tile_x, tile_y;/* MIXED32 tile size in cells; 0 = chosen by the library */
     double bin_slack;      /* MIXED32 bin capacity factor over ppc * tile cells; 0 = 1.5 */
     int32_t bc_x;          /* PIC_BC_PERIODIC or PIC_BC_WALLS (x boundaries; y is periodic) */

@@ -43,6 +43,8 @@ struct pic_sim {
     double* J64 = nullptr;  // 3 ntot (FP64)
     long long* Jfix = nullptr;  // 3 ntot fixed-point current (MIXED32)
     float* F32 = nullptr;   // 6 ntot (MIXED32)
+    double* Fn = nullptr;   // 6 ntot node-averaged fields (FP64 with PIC_GATHER_NODAL)
+    bool any_nodal = false;
     double *x = nullptr, *r = nullptr, *p = nullptr, *q = nullptr;
     double* part = nullptr;
     CgState* cg = nullptr;
@@ -142,6 +144,8 @@ int validate(const pic_params* p, std::string& why) {
         return bad("warm_start must be PIC_WS_ZERO, PIC_WS_PREV or PIC_WS_LEARNED");
     if (p->warm_start == PIC_WS_LEARNED && p->precision != PIC_MIXED32)
         return bad("PIC_WS_LEARNED requires PIC_MIXED32");
+    if ((p->flags & PIC_GATHER_NODAL) && p->bc_x == PIC_BC_WALLS)
+        return bad("PIC_GATHER_NODAL needs periodic boundaries");
     if (p->flags & PIC_EXPLICIT) {
         // Eq. (16): real frequencies for every mode need (c dt)^2 (1/dx^2 + 1/dy^2) <= 1
         const double dt = p->cfl * p->dx;
@@ -203,6 +207,7 @@ void fill_grid(const pic_params& p, GridDev& G) {
     G.warm = p.warm_start == PIC_WS_PREV ? 1 : (p.warm_start == PIC_WS_LEARNED ? 2 : 0);
     G.deposit = (p.flags & PIC_NO_DEPOSIT) ? 0 : 1;
     G.walls = p.bc_x == PIC_BC_WALLS ? 1 : 0;
+    G.nodal = (p.flags & PIC_GATHER_NODAL) ? 1 : 0;
     G.inject = (G.walls && p.inject_x0 >= 0.0) ? 1 : 0;
     G.ppc = p.ppc;
     G.inj_x0 = p.inject_x0;
@@ -223,6 +228,8 @@ FieldArgs field_args(pic_sim* s, int use_cond, cudaGraphConditionalHandle cond) 
     a.J64 = s->prm.precision == PIC_FP64 ? s->J64 : nullptr;
     a.Jfix = s->prm.precision == PIC_MIXED32 ? s->Jfix : nullptr;
     a.F32 = s->F32;
+    a.Fn = s->Fn;
+    a.any_nodal = s->any_nodal ? 1 : 0;
     a.x = s->x;
     a.r = s->r;
     a.p = s->p;
@@ -291,7 +298,7 @@ void enqueue_part(pic_sim* s, int part, cudaStream_t st) {
             p.nblk = s->nblk_push[sp];
             p.nsegs = 1;
             p.ntot = s->ntot;
-            p.F = s->F;
+            p.F = s->Fn ? s->Fn : s->F;  // node-averaged copy for the nodal gather
             p.J = s->J64;
             p.x = s->pa[sp][0];
             p.y = s->pa[sp][1];
@@ -390,6 +397,7 @@ int capture(pic_sim* s, int mask, cudaGraph_t* gout, cudaGraphExec_t* xout) {
         }
         if (s->prm.flags & PIC_EXPLICIT) {
             launch_explicit_fields(field_args(s, 0, 0), st);
+            launch_nodal(field_args(s, 0, 0), st);
             continue;
         }
         if (s->use_coop) {
@@ -401,6 +409,7 @@ int capture(pic_sim* s, int mask, cudaGraph_t* gout, cudaGraphExec_t* xout) {
             }
             e = launch_mp_coop(s->coop, field_args(s, 0, 0), st);
             if (e == cudaSuccess) launch_field_update(field_args(s, 0, 0), st);
+            launch_nodal(field_args(s, 0, 0), st);
             continue;
         }
         cudaGraphConditionalHandle h{};
@@ -432,6 +441,7 @@ int capture(pic_sim* s, int mask, cudaGraph_t* gout, cudaGraphExec_t* xout) {
             });
         }
         if (e == cudaSuccess) launch_field_update(field_args(s, 0, 0), st);
+        launch_nodal(field_args(s, 0, 0), st);
     }
     cudaGraph_t g = nullptr;
     cudaError_t e2 = cudaStreamEndCapture(st, &g);
@@ -487,6 +497,7 @@ long long step_kernels(pic_sim* s, bool graph) {
     }
     if (s->learned) k += 2;  // k_guess, k_guess_residual
     if (s->use_coop) k += 1;
+    if (s->any_nodal) k += 1;  // k_nodal
     return k;
 }
 
@@ -506,6 +517,7 @@ int run_step_direct(pic_sim* s) {
     const FieldArgs a = field_args(s, 0, 0);
     if (s->prm.flags & PIC_EXPLICIT) {
         launch_explicit_fields(a, st);
+        launch_nodal(a, st);
         enqueue_part(s, kPartEnd, st);
         CK(cudaGetLastError());
         return PIC_OK;
@@ -518,6 +530,7 @@ int run_step_direct(pic_sim* s) {
     if (s->use_coop) {
         CK(launch_mp_coop(s->coop, a, st));
         launch_field_update(a, st);
+        launch_nodal(a, st);
         enqueue_part(s, kPartEnd, st);
         CK(cudaGetLastError());
         return PIC_OK;
@@ -543,6 +556,7 @@ int run_step_direct(pic_sim* s) {
         CK(cudaStreamSynchronize(st));
     }
     launch_field_update(a, st);
+    launch_nodal(a, st);
     enqueue_part(s, kPartEnd, st);
     CK(cudaGetLastError());
     return PIC_OK;
@@ -773,6 +787,8 @@ int init_handle(const pic_params* prm, int n, pic_sim** out) {
         A(dalloc(&s->e32, n3));
         A(dalloc(&s->F32, 6 * s->ntot));
     }
+    for (int k = 0; k < n; k++) s->any_nodal = s->any_nodal || (prm[k].flags & PIC_GATHER_NODAL);
+    if (s->any_nodal && prm[0].precision == PIC_FP64) A(dalloc(&s->Fn, 6 * s->ntot));
     if (e != cudaSuccess) {
         s->err = std::string("device allocation failed: ") + cudaGetErrorString(e);
         cudaGetLastError();
@@ -789,6 +805,7 @@ int init_handle(const pic_params* prm, int n, pic_sim** out) {
     if (s->J64) A(cudaMemset(s->J64, 0, n3 * sizeof(double)));
     if (s->Jfix) A(cudaMemset(s->Jfix, 0, n3 * sizeof(long long)));
     if (s->F32) A(cudaMemset(s->F32, 0, 6 * s->ntot * sizeof(float)));
+    if (s->Fn) A(cudaMemset(s->Fn, 0, 6 * s->ntot * sizeof(double)));
     if (prm[0].precision == PIC_MIXED32 && !(prm[0].flags & (PIC_NO_COOP | PIC_EXPLICIT))) {
         const int rc = coop_create(&s->coop, s->hgrids.data(), s->ngrids, s->err);
         if (rc == PIC_ECUDA) return bail(rc);
@@ -1532,7 +1549,7 @@ void pic_free(pic_sim* s) {
     if (s->mixed) mixed_destroy(s->mixed);
     cnn_free_guess(&s->guess);
     coop_free(&s->coop);
-    void* ptrs[] = {s->dgrids, s->dblk_grid, s->F, s->J64, s->Jfix, s->F32, s->x, s->r, s->p, s->q,
+    void* ptrs[] = {s->dgrids, s->dblk_grid, s->F, s->J64, s->Jfix, s->F32, s->Fn, s->x, s->r, s->p, s->q,
                     s->part, s->cg, s->done, s->st, s->tmp, s->dsegs, s->dblk_seg[0], s->dblk_seg[1],
                     s->bvec, s->r32, s->p32, s->q32, s->e32};
     for (void* p : ptrs) dfree(p);

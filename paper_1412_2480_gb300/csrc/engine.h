@@ -19,6 +19,8 @@ struct FieldArgs {
     const double* J64;      // 3 * ntot, FP64 current (FP64 particle path) or nullptr
     const long long* Jfix;  // 3 * ntot, fixed-point current (MIXED32 particle path) or nullptr
     float* F32;             // 6 * ntot FP32 copy of the fields for MIXED32 gathers, or nullptr
+    double* Fn;             // 6 * ntot FP64 node-averaged fields (FP64 with PIC_GATHER_NODAL) or nullptr
+    int any_nodal;          // some simulation gathers node-averaged fields
     double *x, *r, *p, *q;  // 3 * ntot each: dB (solution), residual, direction, A p
     CgState* cg;            // [ngrids]
     double* part;           // 4 * nblk block partials
@@ -51,7 +53,9 @@ void launch_cg_iteration(const FieldArgs& a, cudaStream_t s);
 void launch_field_update(const FieldArgs& a, cudaStream_t s);
 // Explicit FDTD field step, Eqs. (3)-(4) (PIC_EXPLICIT): three kernels, no solve.
 void launch_explicit_fields(const FieldArgs& a, cudaStream_t s);
-// FP32 copy of the FP64 fields (after pic_set_fields / init).
+// Node-averaged gather copies (PIC_GATHER_NODAL): into F32 (MIXED32) or Fn (FP64).
+void launch_nodal(const FieldArgs& a, cudaStream_t s);
+// FP32 copy of the FP64 fields (after pic_set_fields / init), node-averaged where asked.
 void launch_fields_to_f32(const FieldArgs& a, cudaStream_t s);
 
 // The MIXED32 solve as one cooperative persistent kernel (solve_coop.cu), used when the

@@ -459,6 +459,34 @@ k_update_B(const GridDev* __restrict__ grids, const int* __restrict__ blk_grid, 
     }
 }
 
+// The alternative gather reading (PIC_GATHER_NODAL): E and B averaged from their
+// staggered lattices to the nodes -- Ex, By over their two x-neighbours, Ey, Bx over
+// their two y-neighbours, Bz over the four surrounding cells; Ez already sits on the
+// nodes -- for the particle kernels, which then gather every component with the node
+// weights of the charge deposit. Periodic boundaries only.
+__global__ void __launch_bounds__(kFieldThreads)
+k_nodal(const GridDev* __restrict__ grids, const int* __restrict__ blk_grid, long long ntot,
+        const double* __restrict__ F, double* __restrict__ Fn, float* __restrict__ F32) {
+    const int g = blk_grid[blockIdx.x];
+    const GridDev& G = grids[g];
+    if (!G.nodal) return;
+    FOR_CELLS(G, g, c) {
+        const long long ksw = c.ks + (c.kw - c.k);  // south-west neighbour
+        double v[6];
+        v[0] = 0.5 * (F[c.kw] + F[c.k]);
+        v[1] = 0.5 * (F[ntot + c.ks] + F[ntot + c.k]);
+        v[2] = F[2 * ntot + c.k];
+        v[3] = 0.5 * (F[3 * ntot + c.ks] + F[3 * ntot + c.k]);
+        v[4] = 0.5 * (F[4 * ntot + c.kw] + F[4 * ntot + c.k]);
+        v[5] = 0.25 * ((F[5 * ntot + ksw] + F[5 * ntot + c.ks]) + (F[5 * ntot + c.kw] + F[5 * ntot + c.k]));
+#pragma unroll
+        for (int a = 0; a < 6; a++) {
+            if (Fn) Fn[a * ntot + c.k] = v[a];
+            if (F32) F32[a * ntot + c.k] = (float)v[a];
+        }
+    }
+}
+
 __global__ void __launch_bounds__(kFieldThreads)
 k_to_f32(const GridDev* __restrict__ grids, const int* __restrict__ blk_grid, long long ntot,
          const double* __restrict__ F, float* __restrict__ F32) {
@@ -777,8 +805,13 @@ void launch_field_update(const FieldArgs& a, cudaStream_t s) {
                                                 a.st, a.F32);
 }
 
+void launch_nodal(const FieldArgs& a, cudaStream_t s) {
+    if (a.any_nodal) k_nodal<<<a.nblk, kFieldThreads, 0, s>>>(a.grids, a.blk_grid, a.ntot, a.F, a.Fn, a.F32);
+}
+
 void launch_fields_to_f32(const FieldArgs& a, cudaStream_t s) {
     if (a.F32) k_to_f32<<<a.nblk, kFieldThreads, 0, s>>>(a.grids, a.blk_grid, a.ntot, a.F, a.F32);
+    launch_nodal(a, s);
 }
 
 }  // namespace pic

@@ -215,6 +215,7 @@ struct PushConst {
     float fx, fy;   // q dx / (dt dx dy), q dy / (dt dx dy)
     float fz;       // q / (dx dy)   (times vz)
     int deposit;
+    int nodal;      // the fields hold node averages: every component on the node lattice
 };
 
 // Gather, Boris push, move with carry into the neighbouring cell, and deposit, for one
@@ -224,17 +225,30 @@ struct PushConst {
 template <int P, typename Mem>
 __device__ __forceinline__ bool push_one(const Mem& M, const PushConst& K, int i, int j, float& ox,
                                          float& oy, float u[3], int& di, int& dj, float& ek) {
-    int bx0, bxh, by0, byh;
-    float wx0[P + 1], wxh[P + 1], wy0[P + 1], wyh[P + 1];
+    int bx0, by0;
+    float wx0[P + 1], wy0[P + 1];
     shape_nodes<P, float>(i, ox, bx0, wx0);
-    shape_nodes_half<P, float>(i, ox, bxh, wxh);
     shape_nodes<P, float>(j, oy, by0, wy0);
-    shape_nodes_half<P, float>(j, oy, byh, wyh);
-    // Ex (i+1/2, j), Ey (i, j+1/2), Ez (i, j), Bx (i, j+1/2), By (i+1/2, j), Bz (i+1/2, j+1/2)
-    const float E[3] = {gather<P>(M, 0, bxh, wxh, by0, wy0), gather<P>(M, 1, bx0, wx0, byh, wyh),
-                        gather<P>(M, 2, bx0, wx0, by0, wy0)};
-    const float B[3] = {gather<P>(M, 3, bx0, wx0, byh, wyh), gather<P>(M, 4, bxh, wxh, by0, wy0),
-                        gather<P>(M, 5, bxh, wxh, byh, wyh)};
+    float E[3], B[3];
+    if (K.nodal) {  // node-averaged fields: the deposit's weights for every component
+#pragma unroll
+        for (int a = 0; a < 3; a++) {
+            E[a] = gather<P>(M, a, bx0, wx0, by0, wy0);
+            B[a] = gather<P>(M, 3 + a, bx0, wx0, by0, wy0);
+        }
+    } else {
+        int bxh, byh;
+        float wxh[P + 1], wyh[P + 1];
+        shape_nodes_half<P, float>(i, ox, bxh, wxh);
+        shape_nodes_half<P, float>(j, oy, byh, wyh);
+        // Ex (i+1/2, j), Ey (i, j+1/2), Ez (i, j), Bx (i, j+1/2), By (i+1/2, j), Bz (i+1/2, j+1/2)
+        E[0] = gather<P>(M, 0, bxh, wxh, by0, wy0);
+        E[1] = gather<P>(M, 1, bx0, wx0, byh, wyh);
+        E[2] = gather<P>(M, 2, bx0, wx0, by0, wy0);
+        B[0] = gather<P>(M, 3, bx0, wx0, byh, wyh);
+        B[1] = gather<P>(M, 4, bxh, wxh, by0, wy0);
+        B[2] = gather<P>(M, 5, bxh, wxh, byh, wyh);
+    }
     const float g_old = sqrtf(1.f + u[0] * u[0] + u[1] * u[1] + u[2] * u[2]);
     boris<float>(K.h, E, B, u);
     const float ig = rsqrtf(1.f + u[0] * u[0] + u[1] * u[1] + u[2] * u[2]);
@@ -266,6 +280,7 @@ __device__ __forceinline__ PushConst push_const(const GridDev& G, int s) {
     K.fy = (float)(G.qw[s] * G.dy / (G.dt * area));
     K.fz = (float)(G.qw[s] / area);
     K.deposit = G.deposit;
+    K.nodal = G.nodal;
     return K;
 }
 

@@ -70,13 +70,22 @@ k_push_fp64(const GridDev* __restrict__ grids, const SegDev* __restrict__ segs,
             }
         }
         const double* base = F + G.cell_off;
-        // Ex (i+1/2, j), Ey (i, j+1/2), Ez (i, j), Bx (i, j+1/2), By (i+1/2, j), Bz (i+1/2, j+1/2)
-        const double E[3] = {gather<P>(base, nx, ch, wxh, r0, wy0),
-                             gather<P>(base + ntot, nx, c0, wx0s, rh, wyh),
-                             gather<P>(base + 2 * ntot, nx, c0, wx0s, r0, wy0)};
-        const double B[3] = {gather<P>(base + 3 * ntot, nx, c0, wx0s, rh, wyh),
-                             gather<P>(base + 4 * ntot, nx, ch, wxh, r0, wy0),
-                             gather<P>(base + 5 * ntot, nx, ch, wxh, rh, wyh)};
+        double E[3], B[3];
+        if (G.nodal) {  // F holds node averages: the deposit's weights for every component
+#pragma unroll
+            for (int a = 0; a < 3; a++) {
+                E[a] = gather<P>(base + a * ntot, nx, c0, wx0, r0, wy0);
+                B[a] = gather<P>(base + (3 + a) * ntot, nx, c0, wx0, r0, wy0);
+            }
+        } else {
+            // Ex (i+1/2, j), Ey (i, j+1/2), Ez (i, j), Bx (i, j+1/2), By (i+1/2, j), Bz (i+1/2, j+1/2)
+            E[0] = gather<P>(base, nx, ch, wxh, r0, wy0);
+            E[1] = gather<P>(base + ntot, nx, c0, wx0s, rh, wyh);
+            E[2] = gather<P>(base + 2 * ntot, nx, c0, wx0s, r0, wy0);
+            B[0] = gather<P>(base + 3 * ntot, nx, c0, wx0s, rh, wyh);
+            B[1] = gather<P>(base + 4 * ntot, nx, ch, wxh, r0, wy0);
+            B[2] = gather<P>(base + 5 * ntot, nx, ch, wxh, rh, wyh);
+        }
         double u[3] = {uxs[k], uys[k], uzs[k]};
         const double g_old = sqrt(1.0 + u[0] * u[0] + u[1] * u[1] + u[2] * u[2]);
         const double qm = G.qm[S.species];

@@ -33,6 +33,7 @@ struct GridDev {
     int maxit, warm;      // warm: 0 zero guess, 1 previous dB, 2 learned guess
     int deposit;          // 0 in test-particle mode
     int walls;            // conducting, reflecting walls at x = 0 and x = nx dx (else periodic)
+    int nodal;            // gather reading: fields averaged to the nodes first (PIC_GATHER_NODAL)
     // moving injector (walls only; include/pic.h)
     int inject, ppc;
     double inj_x0, cfl, gamma0, u_th;

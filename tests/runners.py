@@ -39,10 +39,11 @@ def run_gpu(nx, ny, ppc, sp, F0, steps, order, cfl=1.0, theta=0.5, gamma0=20.0,
 
 
 def run_oracle(nx, ny, w, sp, F0, steps, order, cfl=1.0, theta=0.5, cg_rtol=1e-10,
-               warm_start="zero", deposit=True, walls=False, solver="implicit"):
+               warm_start="zero", deposit=True, walls=False, solver="implicit", gather="staggered"):
     species = [oracle.Species(d["qm"], w, d["x"], d["y"], d["ux"], d["uy"], d["uz"]) for d in sp]
     sim = oracle.OracleSim(nx, ny, cfl, theta, order, species, cg_rtol=cg_rtol, fields=F0,
-                           warm_start=warm_start, deposit=deposit, walls=walls, solver=solver)
+                           warm_start=warm_start, deposit=deposit, walls=walls, solver=solver,
+                           gather=gather)
     sim.step(steps)
     F = np.concatenate([sim.fields(), sim.J.reshape(3, ny, nx), sim.dB.reshape(3, ny, nx)])
     parts = [np.stack([s.x, s.y, s.ux, s.uy, s.uz]) for s in sim.species]

@@ -229,7 +229,8 @@ def test_restore_rejects_other_parameters_and_bad_files(tmp_path):
 
 
 @pytest.mark.parametrize("case", ["fp64", "mixed", "mixed_loop", "fp64_walls_injector",
-                                  "mixed_walls_injector", "fp64_explicit", "mixed_explicit"])
+                                  "mixed_walls_injector", "fp64_explicit", "mixed_explicit",
+                                  "fp64_nodal", "mixed_nodal"])
 def test_kernel_launch_count_graph_equals_direct(case):
     # the library counts its launches: in the step graph from its kernel nodes, in
     # direct launches from the step's structure; the two must agree (PCG loop included)
@@ -252,6 +253,8 @@ def test_kernel_launch_count_graph_equals_direct(case):
         if case.endswith("explicit"):
             flags |= pic.PIC_EXPLICIT
             kw["cfl"] = 0.5
+        if case.endswith("nodal"):
+            flags |= pic.PIC_GATHER_NODAL
         h = make(nx, ny, ppc, 2, sp, F0, prec, flags=flags, **kw)
         try:
             pic.pic_step(h, 3)
