@@ -130,6 +130,9 @@ extern "C" {
 #define PIC_RHSY 13
 #define PIC_RHSZ 14
 #define PIC_RHO 15  /* node charge density of the current particles (computed on demand) */
+#define PIC_DENSITY_P 16  /* positron number density (macro-particles per unit area) on the nodes,
+                             deposited with the particle shape; ppc/(dx dy) in a uniform plasma */
+#define PIC_DENSITY_E 17  /* electron number density, likewise */
 
 typedef struct pic_params {
     int32_t nx, ny;        /* cells (Sec. 3: 128 x 128; Sec. 4: 5650 x 990); >= 8 each */
@@ -263,7 +266,7 @@ PIC_API int pic_step(pic_sim* s, int32_t n);
  * Device-detected errors are reported as by pic_step. */
 PIC_API int pic_profile(pic_sim* s, int32_t n, double* out, int32_t n_out);
 
-/* Copy grid quantity `which` (PIC_EX..PIC_RHO) into out (len >= nx*ny FP64 values,
+/* Copy grid quantity `which` (PIC_EX..PIC_DENSITY_E) into out (len >= nx*ny FP64 values,
  * host or device, caller-owned). */
 PIC_API int pic_fields(pic_sim* s, int32_t which, double* out, size_t len);
 
@@ -382,7 +385,7 @@ PIC_API int pic_tc_gemm_bf16(int32_t M, int32_t N, int32_t K, const uint16_t* A,
                              float* D);
 
 /* Fourier diagnostics (the k-space maps of Sec. 3.1, Fig. 3): the amplitude spectrum of
- * grid quantity `which` (PIC_EX..PIC_RHO) of the selected simulation,
+ * grid quantity `which` (PIC_EX..PIC_DENSITY_E) of the selected simulation,
  *   out[q nx + p] = |sum_{l,m} F(l, m) exp(-2 pi i (p l / nx + q m / ny))| / (nx ny),
  * p, q in FFT order (p >= nx/2 stands for the wave number 2 pi (p - nx) / (nx dx)). len
  * >= nx*ny FP64 values (host or device). FP64 FFTs on the GPU (radices 2, 3, 4, 5; other

@@ -45,6 +45,7 @@ PIC_EX, PIC_EY, PIC_EZ, PIC_BX, PIC_BY, PIC_BZ = range(6)
 PIC_JX, PIC_JY, PIC_JZ, PIC_DBX, PIC_DBY, PIC_DBZ = range(6, 12)
 PIC_RHSX, PIC_RHSY, PIC_RHSZ = range(12, 15)
 PIC_RHO = 15
+PIC_DENSITY_P, PIC_DENSITY_E = 16, 17
 
 EXPORTED = ("pic_params_default", "pic_init", "pic_init_batch", "pic_select", "pic_batch_size",
             "pic_autotune_tiles", "pic_set_stream", "pic_load_particles", "pic_set_fields",

@@ -620,15 +620,20 @@ int fp64_counts(pic_sim* s) {
     return PIC_OK;
 }
 
-// Node charge density of the selected simulation into rho (device, ncell values) and,
-// when mom is given, w * its total momentum added into mom (device, 3 values).
-int charge_density(pic_sim* s, double* rho, double* mom = nullptr) {
+// Node density of the selected simulation into rho (device, ncell values): the charge
+// density (which = PIC_RHO) or one species' number density (PIC_DENSITY_P / _E); when
+// mom is given, w * the total momentum of both species is added into mom (device, 3).
+int charge_density(pic_sim* s, double* rho, double* mom = nullptr, int which = PIC_RHO) {
     const GridDev& G = s->hgrids[s->sel];
+    const double area = G.dx * G.dy;
+    double q[2] = {G.qw[0] / area, G.qw[1] / area};
+    if (which == PIC_DENSITY_P) q[0] = 1.0 / area, q[1] = 0.0;
+    if (which == PIC_DENSITY_E) q[0] = 0.0, q[1] = 1.0 / area;
     CK(cudaMemsetAsync(rho, 0, G.ncell * sizeof(double), s->stream));
-    if (s->mixed) return mixed_rho_momentum(s->mixed, s->sel, rho, mom, s->stream, s->err);
+    if (s->mixed) return mixed_rho_momentum(s->mixed, s->sel, q, rho, mom, s->stream, s->err);
     for (int sp = 0; sp < 2; sp++) {
         if (!s->np[sp]) continue;
-        launch_rho_fp64(G, s->pa[sp][0], s->pa[sp][1], s->np[sp], G.qw[sp] / (G.dx * G.dy), rho, s->stream);
+        if (q[sp] != 0.0) launch_rho_fp64(G, s->pa[sp][0], s->pa[sp][1], s->np[sp], q[sp], rho, s->stream);
         if (mom) launch_momentum_fp64(s->pa[sp][2], s->pa[sp][3], s->pa[sp][4], s->np[sp], G.w, mom, s->stream);
     }
     CK(cudaGetLastError());
@@ -1219,7 +1224,7 @@ namespace {
 // Device pointer to grid quantity `which` of the selected simulation (J, rho: converted
 // into s->tmp).
 int field_source(pic_sim* s, int32_t which, const double** out_src) {
-    if (which < PIC_EX || which > PIC_RHO) return fail(s, PIC_EINVAL, "which must be PIC_EX..PIC_RHO");
+    if (which < PIC_EX || which > PIC_DENSITY_E) return fail(s, PIC_EINVAL, "which must be PIC_EX..PIC_DENSITY_E");
     if (which >= PIC_RHSX && which <= PIC_RHSZ && !s->bvec)
         return fail(s, PIC_ESTATE, "the right-hand side is kept in PIC_MIXED32 only");
     const GridDev& G = s->hgrids[s->sel];
@@ -1241,7 +1246,7 @@ int field_source(pic_sim* s, int32_t which, const double** out_src) {
     } else if (which <= PIC_RHSZ) {
         src = s->bvec + (which - PIC_RHSX) * s->ntot + off;
     } else {
-        if (int rc = charge_density(s, s->tmp)) return rc;
+        if (int rc = charge_density(s, s->tmp, nullptr, which)) return rc;
         src = s->tmp;
     }
     *out_src = src;

@@ -1341,7 +1341,8 @@ int mixed_after_steps(MixedState* m, cudaStream_t st, std::string& err) {
 
 long long mixed_count(MixedState* m, int g, int s) { return m->n[2 * g + s]; }
 
-int mixed_rho_momentum(MixedState* m, int g, double* rho, double* mom, cudaStream_t st, std::string& err) {
+int mixed_rho_momentum(MixedState* m, int g, const double q_s[2], double* rho, double* mom, cudaStream_t st,
+                       std::string& err) {
     DevStatus hs{};
     if (int rc = read_status(m, hs, st, err)) return rc;
     const GridDev& G = m->G[g];
@@ -1349,8 +1350,8 @@ int mixed_rho_momentum(MixedState* m, int g, double* rho, double* mom, cudaStrea
         PartArrays S{};
         long long n = 0;
         if (int rc = gather_species(m, g, (int)hs.parity, s, S, n, st, err)) return rc;
-        if (n && rho) {
-            const double q = G.qw[s] / (G.dx * G.dy);
+        if (n && rho && q_s[s] != 0.0) {
+            const double q = q_s[s];
             switch (G.order) {
             case 1: k_rho_staged<1><<<grid1(n), 256, 0, st>>>(n, G, S, q, rho); break;
             case 2: k_rho_staged<2><<<grid1(n), 256, 0, st>>>(n, G, S, q, rho); break;

@@ -34,9 +34,11 @@ int mixed_after_steps(MixedState* m, cudaStream_t s, std::string& err);
 // Kernels mixed_enqueue launches per step (all three parts together).
 int mixed_step_kernels(const MixedState* m);
 long long mixed_count(MixedState* m, int g, int sp);
-// Add simulation g's node charge density into rho (device, ncell values; may be null)
-// and w * its total momentum into mom (device, 3 values; may be null).
-int mixed_rho_momentum(MixedState* m, int g, double* rho, double* mom, cudaStream_t s, std::string& err);
+// Add simulation g's node density into rho (device, ncell values; may be null), each
+// particle of species s contributing q[s] (0: the species is left out), and w * its
+// total momentum into mom (device, 3 values; may be null).
+int mixed_rho_momentum(MixedState* m, int g, const double q[2], double* rho, double* mom, cudaStream_t s,
+                       std::string& err);
 long long mixed_rebins(MixedState* m);
 // Bumped whenever device buffers are reallocated: step graphs captured before hold stale
 // pointers and must be rebuilt.

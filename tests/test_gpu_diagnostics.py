@@ -87,6 +87,30 @@ def test_rho_matches_oracle_deposit(precision, order, walls):
 
 @pytest.mark.parametrize("walls", [False, True])
 @pytest.mark.parametrize("precision", [pic.PIC_FP64, pic.PIC_MIXED32])
+def test_species_number_density_matches_oracle(precision, walls):
+    # PIC_DENSITY_P / _E: macro-particles per unit area on the nodes, the deposit of a
+    # unit charge per particle of one species
+    nx, ny, ppc, order = 48, 24, 3, 2
+    w, sp, F0 = hot(nx, ny, ppc, 75, walls)
+    h = make(nx, ny, ppc, order, sp, F0, precision, walls)
+    try:
+        pic.pic_step(h, 2)
+        got = [pic.fields_numpy(h, which, nx, ny).ravel() for which in (pic.PIC_DENSITY_P, pic.PIC_DENSITY_E)]
+    finally:
+        pic.pic_free(h)
+    sim = oracle_sim(nx, ny, w, sp, F0, order, walls)
+    sim.step(2)
+    tol = 1e-12 if precision == pic.PIC_FP64 else TOL32
+    for s in range(2):
+        ref = np.zeros(nx * ny)
+        oracle.deposit_rho(sim.g, 1.0, sim.species[s].x, sim.species[s].y, ref)
+        assert rel(got[s], ref) < tol
+        if not walls:  # every particle's weights sum to one
+            assert abs(got[s].sum() - sim.species[s].n) < 1e-9 * sim.species[s].n
+
+
+@pytest.mark.parametrize("walls", [False, True])
+@pytest.mark.parametrize("precision", [pic.PIC_FP64, pic.PIC_MIXED32])
 def test_conservation_moments_match_oracle(precision, walls):
     nx, ny, ppc, order, steps = 48, 24, 3, 2, 6
     w, sp, F0 = hot(nx, ny, ppc, 70, walls)
