@@ -288,6 +288,22 @@ def pcg_totals(h, n):
     return m["loop_iters"], m["loop_refinements"]
 
 
+def max_over_ranks_of(v, world, device):
+    """The largest v over the ranks (the slowest replica's time); v itself on one rank."""
+    if world == 1:
+        return v
+    import torch
+    t = torch.tensor([v], dtype=torch.float64, device=device)
+    torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+    return float(t.item())
+
+
+def job_value(world, updates_per_rank, seconds_max):
+    """Whole-job throughput of N independent replicas of the same workload (weak
+    scaling): the particle updates of all ranks over the slowest rank's time."""
+    return world * updates_per_rank / seconds_max
+
+
 def run_ours(args, dist):
     import torch
 
@@ -327,11 +343,7 @@ def run_ours(args, dist):
             torch.distributed.barrier()
 
     def max_over_ranks(v):
-        if world == 1:
-            return v
-        t = torch.tensor([v], dtype=torch.float64, device="cuda")
-        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
-        return float(t.item())
+        return max_over_ranks_of(v, world, "cuda")
 
     # ---- end to end through the C ABI with host buffers: load (H2D) + K steps +
     # per-step moments (D2H) + final field readback (D2H) ----
@@ -541,7 +553,7 @@ def main():
     res = run_ours(args, dist)
     if rank != 0:
         return
-    value = world * res["updates_timed"] / (res["ms"] * 1e-3)
+    value = job_value(world, res["updates_timed"], res["ms"] * 1e-3)
     npart = res["updates_timed"] / args.steps  # particles per step, averaged over the timed steps
     hbm, src = peaks()
     mixed = args.precision == "mixed"
@@ -568,7 +580,7 @@ def main():
         "particle_ms_per_step": res["prof"]["particle_ms"],
         "cg_iters_per_step": res["cg_iters"],
         "cg_refinements_per_step": res["cg_refinements"],
-        "e2e": {"value": world * res["updates_e2e"] / res["e2e_s"], "unit": UNIT,
+        "e2e": {"value": job_value(world, res["updates_e2e"], res["e2e_s"]), "unit": UNIT,
                 "h2d_bytes_per_step": int(res["h2d"]), "d2h_bytes_per_step": int(res["d2h"]),
                 "what": "pic_load_particles from pinned host arrays + K x (pic_step(1) + pic_moments) "
                         "+ pic_fields x 6 per simulation"},
