@@ -203,8 +203,15 @@ def traffic_for(kernel_key):
     d = json.load(open(p)).get(kernel_key)
     if not d:
         return None
-    h = hashlib.sha256(open(os.path.join(ROOT, d["source"]), "rb").read()).hexdigest()[:16]
-    return d["bytes_per_launch"] if h == d["source_sha"] else None
+    return d["bytes_per_launch"] if sources_sha(d["sources"]) == d["source_sha"] else None
+
+
+def sources_sha(paths):
+    """Hash of the source files a kernel is built from (all of them, in order)."""
+    h = hashlib.sha256()
+    for rel in paths:
+        h.update(open(os.path.join(ROOT, rel), "rb").read())
+    return h.hexdigest()[:16]
 
 
 def make_inputs(rows, pinned=False):

