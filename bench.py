@@ -203,7 +203,8 @@ def traffic_for(kernel_key):
     d = json.load(open(p)).get(kernel_key)
     if not d:
         return None
-    return d["bytes_per_launch"] if sources_sha(d["sources"]) == d["source_sha"] else None
+    srcs = d.get("sources") or [d.get("source")]
+    return d["bytes_per_launch"] if sources_sha(srcs) == d.get("source_sha") else None
 
 
 def sources_sha(paths):
