@@ -152,8 +152,9 @@ struct WinMem {  // tile window in shared memory; indices are window-local
     float js;   // window scale 2^k / u
     float jlb;  // 2^lb
     __device__ __forceinline__ float ld(int c, int ix, int iy) const { return fw[c * nw + iy * wx + ix]; }
-    __device__ __forceinline__ void add(int c, int ix, int iy, float v) const {
-        const float x = v * js;
+    // x: the contribution already in window units (the push folds js into its deposit
+    // constants)
+    __device__ __forceinline__ void add(int c, int ix, int iy, float x) const {
         const float xr = x + kMagic;
         const int hi = __float_as_int(xr) - kMagicBits;
         const float r = x - (xr - kMagic);  // exact: |r| <= 1/2
@@ -181,16 +182,17 @@ struct GlobalMem {  // global grid arrays of one simulation; indices are global
         const int cx = wall_col(ix, nx, half, !half, s);
         return s == 0 ? 0.f : (float)s * __ldg(F + c * ntot + (long long)wrapi(iy, ny) * nx + cx);
     }
+    // v: the contribution already in global fixed-point units (times js)
     __device__ __forceinline__ void add(int c, int ix, int iy, float v) const {
         if (!walls) {
-            atomicAdd(J + c * ntot + at(ix, iy), (unsigned long long)__float2ll_rn(v * js));
+            atomicAdd(J + c * ntot + at(ix, iy), (unsigned long long)__float2ll_rn(v));
             return;
         }
         int s;
         const int cx = wall_col(ix, nx, c == 0, c == 0, s);  // mirror image: Jx odd
         if (s != 0)
             atomicAdd(J + c * ntot + (long long)wrapi(iy, ny) * nx + cx,
-                      (unsigned long long)__float2ll_rn((float)s * v * js));
+                      (unsigned long long)__float2ll_rn((float)s * v));
     }
 };
 
@@ -263,7 +265,8 @@ __device__ __forceinline__ bool push_one(const Mem& M, const PushConst& K, int i
     if (y1 >= 1.f) { y1 -= 1.f; dj = 1; }
     else if (y1 < 0.f) { y1 += 1.f; dj = -1; if (y1 >= 1.f) { y1 = 0.f; dj = 0; } }
     if (K.deposit)
-        esirkepov<P, float>(i, ox, j, oy, i + di, x1, j + dj, y1, K.fx, K.fy, K.fz * (u[2] * ig),
+        esirkepov<P, float>(i, ox, j, oy, i + di, x1, j + dj, y1, K.fx * M.js, K.fy * M.js,
+                            K.fz * (u[2] * ig) * M.js,
                             [M](int c, int ix, int iy, float v) { M.add(c, ix, iy, v); });
     ox = x1;
     oy = y1;
