@@ -144,6 +144,9 @@ __host__ __device__ __forceinline__ void dir_of(int o, int& dx, int& dy) {
 constexpr float kMagic = 12582912.0f;  // 1.5 * 2^23
 constexpr int kMagicBits = 0x4B400000;
 
+// The tile's field window pairs the components that share a lattice -- (Ex, By) at
+// (i+1/2, j) and (Ey, Bx) at (i, j+1/2) -- as float2, so one 64-bit load serves two
+// components; Ez and Bz follow as plain arrays: [(Ex,By) x NW][(Ey,Bx) x NW][Ez][Bz].
 struct WinMem {  // tile window in shared memory; indices are window-local
     const float* fw;
     int* jhi;
@@ -151,7 +154,14 @@ struct WinMem {  // tile window in shared memory; indices are window-local
     int wx, nw;
     float js;   // window scale 2^k / u
     float jlb;  // 2^lb
-    __device__ __forceinline__ float ld(int c, int ix, int iy) const { return fw[c * nw + iy * wx + ix]; }
+    __device__ __forceinline__ float2 ld_exby(int ix, int iy) const {
+        return reinterpret_cast<const float2*>(fw)[iy * wx + ix];
+    }
+    __device__ __forceinline__ float2 ld_eybx(int ix, int iy) const {
+        return reinterpret_cast<const float2*>(fw + 2 * nw)[iy * wx + ix];
+    }
+    __device__ __forceinline__ float ld_ez(int ix, int iy) const { return fw[4 * nw + iy * wx + ix]; }
+    __device__ __forceinline__ float ld_bz(int ix, int iy) const { return fw[5 * nw + iy * wx + ix]; }
     // x: the contribution already in window units (the push folds js into its deposit
     // constants)
     __device__ __forceinline__ void add(int c, int ix, int iy, float x) const {
@@ -210,6 +220,57 @@ __device__ __forceinline__ float gather(const Mem& M, int c, int bx, const float
     return acc;
 }
 
+// All six components at a particle: E, B. (bxe, wxe, bye, wye): the x and y shape of the
+// half-integer-x lattice components (Ex, By, Bz in x; Ey, Bx, Bz in y use (bxh..)); in
+// the node-averaged reading every component uses the node shape.
+template <int P>
+__device__ __forceinline__ void gather_fields(const GlobalMem& M, int bx0, const float wx0[P + 1], int bxh,
+                                              const float wxh[P + 1], int by0, const float wy0[P + 1], int byh,
+                                              const float wyh[P + 1], float E[3], float B[3]) {
+    E[0] = gather<P>(M, 0, bxh, wxh, by0, wy0);
+    E[1] = gather<P>(M, 1, bx0, wx0, byh, wyh);
+    E[2] = gather<P>(M, 2, bx0, wx0, by0, wy0);
+    B[0] = gather<P>(M, 3, bx0, wx0, byh, wyh);
+    B[1] = gather<P>(M, 4, bxh, wxh, by0, wy0);
+    B[2] = gather<P>(M, 5, bxh, wxh, byh, wyh);
+}
+
+template <int P>
+__device__ __forceinline__ void gather_fields(const WinMem& M, int bx0, const float wx0[P + 1], int bxh,
+                                              const float wxh[P + 1], int by0, const float wy0[P + 1], int byh,
+                                              const float wyh[P + 1], float E[3], float B[3]) {
+    float2 a = make_float2(0.f, 0.f), b = make_float2(0.f, 0.f);
+    float ez = 0.f, bz = 0.f;
+#pragma unroll
+    for (int r = 0; r <= P; r++) {
+        float2 ra = make_float2(0.f, 0.f), rb = make_float2(0.f, 0.f);
+        float rz = 0.f, rbz = 0.f;
+#pragma unroll
+        for (int t = 0; t <= P; t++) {
+            const float2 va = M.ld_exby(bxh + t, by0 + r);
+            const float2 vb = M.ld_eybx(bx0 + t, byh + r);
+            ra.x = fmaf(wxh[t], va.x, ra.x);
+            ra.y = fmaf(wxh[t], va.y, ra.y);
+            rb.x = fmaf(wx0[t], vb.x, rb.x);
+            rb.y = fmaf(wx0[t], vb.y, rb.y);
+            rz = fmaf(wx0[t], M.ld_ez(bx0 + t, by0 + r), rz);
+            rbz = fmaf(wxh[t], M.ld_bz(bxh + t, byh + r), rbz);
+        }
+        a.x = fmaf(wy0[r], ra.x, a.x);
+        a.y = fmaf(wy0[r], ra.y, a.y);
+        b.x = fmaf(wyh[r], rb.x, b.x);
+        b.y = fmaf(wyh[r], rb.y, b.y);
+        ez = fmaf(wy0[r], rz, ez);
+        bz = fmaf(wyh[r], rbz, bz);
+    }
+    E[0] = a.x;
+    B[1] = a.y;
+    E[1] = b.x;
+    B[0] = b.y;
+    E[2] = ez;
+    B[2] = bz;
+}
+
 struct PushConst {
     float h;        // (q/m) dt / 2
     float dt_idx;   // dt / dx
@@ -233,23 +294,14 @@ __device__ __forceinline__ bool push_one(const Mem& M, const PushConst& K, int i
     shape_nodes<P, float>(j, oy, by0, wy0);
     float E[3], B[3];
     if (K.nodal) {  // node-averaged fields: the deposit's weights for every component
-#pragma unroll
-        for (int a = 0; a < 3; a++) {
-            E[a] = gather<P>(M, a, bx0, wx0, by0, wy0);
-            B[a] = gather<P>(M, 3 + a, bx0, wx0, by0, wy0);
-        }
+        gather_fields<P>(M, bx0, wx0, bx0, wx0, by0, wy0, by0, wy0, E, B);
     } else {
+        // Ex (i+1/2, j), Ey (i, j+1/2), Ez (i, j), Bx (i, j+1/2), By (i+1/2, j), Bz (i+1/2, j+1/2)
         int bxh, byh;
         float wxh[P + 1], wyh[P + 1];
         shape_nodes_half<P, float>(i, ox, bxh, wxh);
         shape_nodes_half<P, float>(j, oy, byh, wyh);
-        // Ex (i+1/2, j), Ey (i, j+1/2), Ez (i, j), Bx (i, j+1/2), By (i+1/2, j), Bz (i+1/2, j+1/2)
-        E[0] = gather<P>(M, 0, bxh, wxh, by0, wy0);
-        E[1] = gather<P>(M, 1, bx0, wx0, byh, wyh);
-        E[2] = gather<P>(M, 2, bx0, wx0, by0, wy0);
-        B[0] = gather<P>(M, 3, bx0, wx0, byh, wyh);
-        B[1] = gather<P>(M, 4, bxh, wxh, by0, wy0);
-        B[2] = gather<P>(M, 5, bxh, wxh, byh, wyh);
+        gather_fields<P>(M, bx0, wx0, bxh, wxh, by0, wy0, byh, wyh, E, B);
     }
     const float g_old = sqrtf(1.f + u[0] * u[0] + u[1] * u[1] + u[2] * u[2]);
     boris<float>(K.h, E, B, u);
@@ -402,7 +454,10 @@ k_push_tile(const MixedArgs a) {
                 gx = wall_col(X0 - 2 + wx, nx, half, !half, s);
             }
             const int gy = ((Y0 - 2 + wy) % ny + ny) % ny;
-            fw[idx] = s == 0 ? 0.f : (float)s * Fg[c * a.ntot + (long long)gy * nx + gx];
+            // (Ex, By) pairs, (Ey, Bx) pairs, Ez, Bz
+            const int dst = c == 0 ? 2 * w : c == 4 ? 2 * w + 1 : c == 1 ? 2 * NW + 2 * w
+                          : c == 3 ? 2 * NW + 2 * w + 1 : c == 2 ? 4 * NW + w : 5 * NW + w;
+            fw[dst] = s == 0 ? 0.f : (float)s * Fg[c * a.ntot + (long long)gy * nx + gx];
         }
         for (int idx = threadIdx.x; idx < 6 * NW; idx += blockDim.x) jw[idx] = 0;
         __syncthreads();
