@@ -517,8 +517,10 @@ k_push_tile(const MixedArgs a) {
                     }
                 }
                 const unsigned act = __ballot_sync(0xffffffffu, valid);
+                const unsigned stay = __ballot_sync(0xffffffffu, valid && dest == 0);
                 if (valid) {
-                    const unsigned grp = __match_any_sync(act, dest);
+                    // lanes bound for the same bin (usually the whole warp stays in its tile)
+                    const unsigned grp = stay == act ? act : __match_any_sync(act, dest);
                     const int leader = __ffs(grp) - 1;
                     const int rank = __popc(grp & ((1u << lane) - 1u));
                     int b0 = 0;
