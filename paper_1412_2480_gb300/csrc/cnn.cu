@@ -409,14 +409,19 @@ __global__ void k_adam(long long n, float* w, const float* g, float* m1, float* 
 }
 
 // The learned guess of the solver: x0 = K * b + bias rms(b), K the network collapsed
-// into one 9x9 stencil (3 -> 3 channels). One CTA per 32 x 8 cell tile; b (FP64) of the
-// tile and a 4-cell periodic halo is staged in shared memory as FP32.
-constexpr int kGX = 32, kGY = 8, kGH = 4;
+// into one 9x9 stencil (3 -> 3 channels). One CTA of 128 threads per 32 x 32 cell tile;
+// b (FP64) of the tile and a 4-cell periodic halo is staged in shared memory as FP32.
+// Each thread computes a column strip of kStrip cells for all three outputs: for every
+// input channel and tap column it holds the strip's kStrip + 8 inputs in registers and
+// reuses each for up to 9 x 3 products (one shared load per 5 FMAs instead of two per FMA).
+constexpr int kGX = 32, kGY = 32, kGH = 4, kStrip = 8;
+constexpr int kGuessThreads = kGX * (kGY / kStrip);
 
-__global__ void __launch_bounds__(kGX * kGY) k_guess(const GridDev* __restrict__ grids, const int* __restrict__ tile_grid,
-                                                  const int* __restrict__ tile_local, long long ntot,
-                                                  const double* __restrict__ b, double* __restrict__ x,
-                                                  const float* __restrict__ Kg, const CgState* __restrict__ cg) {
+__global__ void __launch_bounds__(kGuessThreads) k_guess(const GridDev* __restrict__ grids,
+                                                         const int* __restrict__ tile_grid,
+                                                         const int* __restrict__ tile_local, long long ntot,
+                                                         const double* __restrict__ b, double* __restrict__ x,
+                                                         const float* __restrict__ Kg, const CgState* __restrict__ cg) {
     constexpr int WX = kGX + 2 * kGH, WY = kGY + 2 * kGH;
     __shared__ float sK[kGuessParams];
     __shared__ float sb[3][WY][WX];
@@ -434,21 +439,44 @@ __global__ void __launch_bounds__(kGX * kGY) k_guess(const GridDev* __restrict__
         sb[c][yy][xx] = (float)b[c * ntot + G.cell_off + (long long)gy * G.nx + gx];
     }
     __syncthreads();
-    const int tx = tid % kGX, ty = tid / kGX;
-    const int i = x0 + tx, j = y0 + ty;
-    if (i >= G.nx || j >= G.ny) return;
+    const int tx = tid % kGX, ys = (tid / kGX) * kStrip;  // this thread's column and first row
+    float acc[3][kStrip];
+#pragma unroll
+    for (int co = 0; co < 3; co++)
+#pragma unroll
+        for (int r = 0; r < kStrip; r++) acc[co][r] = 0.f;
+#pragma unroll 1
+    for (int ci = 0; ci < 3; ci++) {
+#pragma unroll 1
+        for (int dx = 0; dx < kGuessTaps; dx++) {
+            float in[kStrip + kGuessTaps - 1];
+#pragma unroll
+            for (int t = 0; t < kStrip + kGuessTaps - 1; t++) in[t] = sb[ci][ys + t][tx + dx];
+#pragma unroll
+            for (int dy = 0; dy < kGuessTaps; dy++) {
+                const float k0 = sK[((0 * 3 + ci) * kGuessTaps + dy) * kGuessTaps + dx];
+                const float k1 = sK[((1 * 3 + ci) * kGuessTaps + dy) * kGuessTaps + dx];
+                const float k2 = sK[((2 * 3 + ci) * kGuessTaps + dy) * kGuessTaps + dx];
+#pragma unroll
+                for (int r = 0; r < kStrip; r++) {
+                    acc[0][r] = fmaf(k0, in[r + dy], acc[0][r]);
+                    acc[1][r] = fmaf(k1, in[r + dy], acc[1][r]);
+                    acc[2][r] = fmaf(k2, in[r + dy], acc[2][r]);
+                }
+            }
+        }
+    }
+    const int i = x0 + tx;
+    if (i >= G.nx) return;
     const double rms = sqrt(cg[g].bb / (3.0 * G.ncell));
 #pragma unroll
     for (int co = 0; co < 3; co++) {
-        float acc = 0.f;
+        const double bias = (double)sK[kGuessWeights + co] * rms;
 #pragma unroll
-        for (int ci = 0; ci < 3; ci++)
-#pragma unroll
-            for (int dy = 0; dy < kGuessTaps; dy++)
-#pragma unroll
-                for (int dx = 0; dx < kGuessTaps; dx++)
-                    acc = fmaf(sK[((co * 3 + ci) * kGuessTaps + dy) * kGuessTaps + dx], sb[ci][ty + dy][tx + dx], acc);
-        x[co * ntot + G.cell_off + (long long)j * G.nx + i] = (double)acc + (double)sK[kGuessWeights + co] * rms;
+        for (int r = 0; r < kStrip; r++) {
+            const int j = y0 + ys + r;
+            if (j < G.ny) x[co * ntot + G.cell_off + (long long)j * G.nx + i] = (double)acc[co][r] + bias;
+        }
     }
 }
 
@@ -666,7 +694,7 @@ void cnn_free_guess(CnnGuess* g) {
 
 void launch_learned_guess(const CnnGuess& g, const GridDev* grids, const CgState* cg, long long ntot,
                           const double* b, double* x, cudaStream_t st) {
-    k_guess<<<(unsigned)g.ntiles, kGX * kGY, 0, st>>>(grids, g.tile_grid, g.tile_local, ntot, b, x, g.K, cg);
+    k_guess<<<(unsigned)g.ntiles, kGuessThreads, 0, st>>>(grids, g.tile_grid, g.tile_local, ntot, b, x, g.K, cg);
 }
 
 }  // namespace pic
