@@ -54,8 +54,11 @@ struct GState {
     int active, in_active, iters, in_iters, outer, maxit;
 };
 
-// Grid-wide barrier of a cooperative launch (all CTAs resident). Bounded: false if the
-// other CTAs did not arrive within the limit.
+// Grid-wide barrier of a cooperative launch (all CTAs resident): arrivals on one counter
+// (word 0), release by advancing the generation (word 1). Bounded: false if the other
+// CTAs did not arrive within the limit. (A two-level tree of counters was slower here.)
+constexpr int kBarWords = 2;
+
 __device__ bool grid_barrier(unsigned int* bar, unsigned int nblocks, unsigned int* timeout) {
     __shared__ int s_ok;
     __syncthreads();
@@ -452,10 +455,10 @@ int coop_create(CoopSolve* cs, const GridDev* hg, int ngrids, std::string& err) 
     if (e == cudaSuccess) e = cudaMalloc(&cs->gchunk, ngrids * sizeof(int2));
     if (e == cudaSuccess) e = cudaMalloc(&cs->chunk_grid, cg.size() * sizeof(int));
     if (e == cudaSuccess) e = cudaMalloc(&cs->part, 2 * cg.size() * sizeof(double));
-    if (e == cudaSuccess) e = cudaMalloc(&cs->bar, 2 * sizeof(unsigned int));
+    if (e == cudaSuccess) e = cudaMalloc(&cs->bar, kBarWords * sizeof(unsigned int));
     if (e == cudaSuccess) e = cudaMemcpy(cs->gchunk, gc.data(), ngrids * sizeof(int2), cudaMemcpyHostToDevice);
     if (e == cudaSuccess) e = cudaMemcpy(cs->chunk_grid, cg.data(), cg.size() * sizeof(int), cudaMemcpyHostToDevice);
-    if (e == cudaSuccess) e = cudaMemset(cs->bar, 0, 2 * sizeof(unsigned int));
+    if (e == cudaSuccess) e = cudaMemset(cs->bar, 0, kBarWords * sizeof(unsigned int));
     if (e != cudaSuccess) {
         err = std::string("cooperative solve set-up failed: ") + cudaGetErrorString(e);
         cudaGetLastError();
@@ -504,6 +507,10 @@ cudaError_t launch_mp_coop(const CoopSolve& cs, const FieldArgs& f, cudaStream_t
     at[0].val.cooperative = 1;
     cfg.attrs = at;
     cfg.numAttrs = 1;
+    // barrier counters from zero on every launch (a launch that gave up on a barrier
+    // leaves arrivals behind)
+    cudaError_t e = cudaMemsetAsync(cs.bar, 0, kBarWords * sizeof(unsigned int), s);
+    if (e != cudaSuccess) return e;
     return cudaLaunchKernelEx(&cfg, k_mp_coop, a);
 }
 
