@@ -255,9 +255,107 @@ __device__ __forceinline__ void chunk_cells(const CoopArgs& a, const ChunkC& q, 
     }
 }
 
+// The two inner-iteration phases on a full chunk, component by component with the loads
+// of both quads issued before any arithmetic: the stores of one component cannot be
+// proved apart from the loads of the next, so a quad-by-quad order would serialise six
+// L2 round trips per phase.
+constexpr int kQuads = kPerThread / 4;
+
+__device__ __forceinline__ void direction_full(const CoopArgs& a, const ChunkC& q, float& accf) {
+    int k[kQuads], kn[kQuads], ks[kQuads], kw[kQuads], ke[kQuads], ii[kQuads];
+#pragma unroll
+    for (int qq = 0; qq < kQuads; qq++) {
+        const int l = q.l0 + 4 * (qq * kCoopThreads + (int)threadIdx.x);
+        const int j = l / q.nx, i = l - j * q.nx;
+        const int row = j * q.nx;  // cell offsets within the simulation
+        ii[qq] = i;
+        k[qq] = row + i;
+        kw[qq] = row + (i == 0 ? q.nx - 1 : i - 1);
+        ke[qq] = row + (i + 4 == q.nx ? 0 : i + 4);
+        kn[qq] = (j + 1 == q.ny ? 0 : j + 1) * q.nx + i;
+        ks[qq] = (j == 0 ? q.ny - 1 : j - 1) * q.nx + i;
+    }
+    const bool first = q.betaf == 0.f;  // beta = 0: p and q of the last solve are not used
+#pragma unroll
+    for (int c = 0; c < 3; c++) {
+        const float* R = a.r32 + c * q.ntot + q.off;
+        float* Pp = a.p32 + c * q.ntot + q.off;
+        float* Qp = a.q32 + c * q.ntot + q.off;
+        float4 rc[kQuads], rn[kQuads], rs[kQuads], po[kQuads], qo[kQuads];
+        float rw[kQuads], re[kQuads];
+#pragma unroll
+        for (int qq = 0; qq < kQuads; qq++) {
+            rc[qq] = ld4(R + k[qq]);
+            rn[qq] = ld4(R + kn[qq]);
+            rs[qq] = ld4(R + ks[qq]);
+            rw[qq] = __ldcg(R + kw[qq]);
+            re[qq] = __ldcg(R + ke[qq]);
+            po[qq] = ld4(Pp + k[qq]);
+            qo[qq] = ld4(Qp + k[qq]);
+        }
+#pragma unroll
+        for (int qq = 0; qq < kQuads; qq++) {
+            if (q.walls) {  // images at a conducting wall: Bx odd, By and Bz even
+                if (ii[qq] == 0) rw[qq] = c == 0 ? -rc[qq].y : rc[qq].x;
+                if (ii[qq] + 4 == q.nx) re[qq] = c == 0 ? 0.f : rc[qq].w;
+            }
+            const float4 r0 = rc[qq], r1 = rn[qq], r2 = rs[qq];
+            float4 Ar;
+            Ar.x = q.c0f * r0.x - q.cxf * (rw[qq] + r0.y) - q.cyf * (r1.x + r2.x);
+            Ar.y = q.c0f * r0.y - q.cxf * (r0.x + r0.z) - q.cyf * (r1.y + r2.y);
+            Ar.z = q.c0f * r0.z - q.cxf * (r0.y + r0.w) - q.cyf * (r1.z + r2.z);
+            Ar.w = q.c0f * r0.w - q.cxf * (r0.z + re[qq]) - q.cyf * (r1.w + r2.w);
+            const float b = q.betaf;
+            const float4 pn = first ? r0
+                                    : make_float4(fmaf(b, po[qq].x, r0.x), fmaf(b, po[qq].y, r0.y),
+                                                  fmaf(b, po[qq].z, r0.z), fmaf(b, po[qq].w, r0.w));
+            const float4 qn = first ? Ar
+                                    : make_float4(fmaf(b, qo[qq].x, Ar.x), fmaf(b, qo[qq].y, Ar.y),
+                                                  fmaf(b, qo[qq].z, Ar.z), fmaf(b, qo[qq].w, Ar.w));
+            st4(Pp + k[qq], pn);
+            st4(Qp + k[qq], qn);
+            accf = fmaf(pn.x, qn.x, fmaf(pn.y, qn.y, fmaf(pn.z, qn.z, fmaf(pn.w, qn.w, accf))));
+        }
+    }
+}
+
+__device__ __forceinline__ void update_full(const CoopArgs& a, const ChunkC& q, float& accf) {
+    int k[kQuads];
+#pragma unroll
+    for (int qq = 0; qq < kQuads; qq++) k[qq] = q.l0 + 4 * (qq * kCoopThreads + (int)threadIdx.x);
+    const float al = q.alphaf;
+#pragma unroll
+    for (int c = 0; c < 3; c++) {
+        const long long o = c * q.ntot + q.off;
+        float4 e[kQuads], pp[kQuads], qv[kQuads], r[kQuads];
+#pragma unroll
+        for (int qq = 0; qq < kQuads; qq++) {
+            e[qq] = ld4(a.e32 + o + k[qq]);
+            pp[qq] = ld4(a.p32 + o + k[qq]);
+            qv[qq] = ld4(a.q32 + o + k[qq]);
+            r[qq] = ld4(a.r32 + o + k[qq]);
+        }
+#pragma unroll
+        for (int qq = 0; qq < kQuads; qq++) {
+            st4(a.e32 + o + k[qq], make_float4(fmaf(al, pp[qq].x, e[qq].x), fmaf(al, pp[qq].y, e[qq].y),
+                                               fmaf(al, pp[qq].z, e[qq].z), fmaf(al, pp[qq].w, e[qq].w)));
+            const float4 rn = make_float4(fmaf(-al, qv[qq].x, r[qq].x), fmaf(-al, qv[qq].y, r[qq].y),
+                                          fmaf(-al, qv[qq].z, r[qq].z), fmaf(-al, qv[qq].w, r[qq].w));
+            st4(a.r32 + o + k[qq], rn);
+            accf = fmaf(rn.x, rn.x, fmaf(rn.y, rn.y, fmaf(rn.z, rn.z, fmaf(rn.w, rn.w, accf))));
+        }
+    }
+}
+
 template <int PH>
 __device__ __forceinline__ void chunk_phase(const CoopArgs& a, const ChunkC& q, float& accf, double& accd) {
-    if (q.l0 + kChunkCells <= q.ncell) chunk_cells<PH, true>(a, q, accf, accd);
+    const bool full = q.l0 + kChunkCells <= q.ncell;
+    if constexpr (PH == kDirection) {
+        if (full) return direction_full(a, q, accf);
+    } else if constexpr (PH == kUpdate) {
+        if (full) return update_full(a, q, accf);
+    }
+    if (full) chunk_cells<PH, true>(a, q, accf, accd);
     else chunk_cells<PH, false>(a, q, accf, accd);
 }
 
