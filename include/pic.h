@@ -9,7 +9,11 @@
  *   - relativistic Buneman-Boris push (the paper gives no pusher; standard scheme);
  *   - density-decomposition (Esirkepov) charge-conserving current deposit (Sec. 1, 3);
  *   - implicit theta-FDTD Maxwell update, Eqs. (5)-(6), with the elliptic equation
- *     Eq. (7) for dB = B^{n+1} - B^n solved by preconditioned conjugate gradient.
+ *     Eq. (7) for dB = B^{n+1} - B^n solved by preconditioned conjugate gradient
+ *     (or, with PIC_EXPLICIT, the explicit FDTD update of Eqs. (3)-(4)).
+ * Around it: on-demand diagnostics (densities, conservation moments, Fourier spectra
+ * and the resonance line of Eq. 17), checkpoints, batches of simulations per handle,
+ * and a learned initial guess for the solve.
  *
  * Units: Gaussian, c = 1. Lengths in physical units with cell sizes dx, dy; the time
  * step is dt = cfl * dx (CFL number sigma = c dt / dx, Sec. 3.1). Species 0 are
@@ -19,7 +23,8 @@
  *
  * Grid storage (every grid quantity, nx*ny values, index k = j*nx + i) follows the
  * 2D Yee arrangement (Sec. 2, Fig. 1): Ez, Jz, rho at (i, j); Ex, Jx, By at (i+1/2, j);
- * Ey, Jy, Bx at (i, j+1/2); Bz at (i+1/2, j+1/2). Boundaries are periodic in x and y.
+ * Ey, Jy, Bx at (i, j+1/2); Bz at (i+1/2, j+1/2). Boundaries are periodic in y, and in x
+ * periodic or conducting, reflecting walls (PIC_BC_WALLS).
  *
  * Conventions for every call:
  *   - return value PIC_OK (0) or a negative PIC_E* code; nothing aborts or exits;
@@ -150,7 +155,7 @@ typedef struct pic_params {
     int32_t flags;         /* PIC_NO_DEPOSIT | PIC_NO_GRAPH | PIC_NO_COOP | PIC_EXPLICIT |
                               PIC_GATHER_NODAL */
     int32_t tile_x, tile_y;/* MIXED32 tile size in cells; 0 = chosen by the library */
-    double bin_slack;      /* MIXED32 bin capacity factor over ppc * tile cells; 0 = 1.5 */
+    double bin_slack;      /* MIXED32 bin capacity factor over ppc * tile cells; 0 = 1.25 */
     int32_t bc_x;          /* PIC_BC_PERIODIC or PIC_BC_WALLS (x boundaries; y is periodic) */
     double inject_x0;      /* PIC_BC_WALLS: start of the moving injector in cells (< 0: none) */
     double u_th;           /* injector: rest-frame thermal momentum spread (units of c) */
@@ -202,7 +207,7 @@ PIC_API int pic_init(const pic_params* p, pic_sim** out);
  *
  * pic_init_batch: like pic_init for the n parameter sets p[0..n), 1 <= n <= 4096. A batch
  * of more than one simulation requires PIC_MIXED32 in every set and the same
- * PIC_NO_GRAPH flag. Simulation 0 is selected.
+ * PIC_NO_GRAPH and PIC_EXPLICIT flags. Simulation 0 is selected.
  * pic_select: per-simulation calls (pic_load_particles, pic_set_fields, pic_fields,
  * pic_moments, pic_particle_count, pic_particles, and the PCG iteration count of
  * pic_profile) address simulation k from now on. The counters cfl_violations and
@@ -246,7 +251,7 @@ PIC_API int pic_set_fields(pic_sim* s, int32_t which, const double* data, size_t
 
 /* Advance n >= 0 steps of the particle cycle (Sec. 2, Sec. 3): for each step, gather
  * E^n, B^n; push; move; deposit J^{n+1/2}; solve Eq. (7) by PCG; update E, B by
- * Eqs. (5)-(6). Work is enqueued on the handle's stream and the call returns after the
+ * Eqs. (5)-(6) (with PIC_EXPLICIT: Eqs. (3)-(4), no solve). Work is enqueued on the handle's stream and the call returns after the
  * stream has finished (one host synchronisation per call, not per step; MIXED32 also
  * synchronises every 32 steps, to re-sort particles that found no room in their tile's
  * bin into larger bins). Errors
