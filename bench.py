@@ -14,7 +14,7 @@ per species; 87,293,952 particles) in one handle with autotuned tiles; its plain
 comparison runs the 48 simulations one after another in their own handles.
 
   python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
-                  [--workload cfg2|cfg1|cfg2q|scan48|cfg5]
+                  [--workload cfg2|cfg1|cfg2q|scan48|cfg5|cfg2x|cfg2n|cfg4]
 
 With N > 1 (launched under torchrun) every rank runs an independent replica with its own
 seed (the path has no data-path exchange); value = particles of all ranks x K / the
@@ -49,7 +49,13 @@ WORKLOADS = {
     "cfg2x": (2048, 512, 32, 2, 40.0, 1e-3, 0.5, 0.5, 2),
     # cfg2 with the node-averaged gather reading
     "cfg2n": (2048, 512, 32, 2, 40.0, 1e-3, 1.0, 0.5, 2),
+    # config 1's physics on 1024 x 256 with the learned warm start (trained first on
+    # 20k (b, dB) pairs of 64 x 64 runs of the same physics), compared with x0 = 0 and
+    # the previous step's dB
+    "cfg4": (1024, 256, 8, 1, 20.0, 1e-3, 1.0, 0.5, 4),
 }
+LEARNED = {"cfg4"}
+NET = None  # the trained network of the learned warm start (cfg4)
 EXPLICIT = {"cfg2x"}
 NODAL = {"cfg2n"}
 SHOCK = {
@@ -83,7 +89,7 @@ def rows_of(name, rank=0):
     nx, ny, ppc, order, g0, uth, cfl, theta, seed = WORKLOADS[name]
     return [{"k": 0, "nx": nx, "ny": ny, "cfl": cfl, "theta": theta, "order": order,
              "gamma0": g0, "ppc": ppc, "u_th": uth, "seed": seed + rank, "explicit": name in EXPLICIT,
-             "nodal": name in NODAL}]
+             "nodal": name in NODAL, "learned": name in LEARNED}]
 
 
 def injected_pairs_per_row(r, n):
@@ -123,6 +129,10 @@ def describe(name):
     if name in EXPLICIT:
         return (f"{nx}x{ny} periodic, explicit FDTD (Eqs. 3-4), CFL {cfl}, order {order}, pair plasma "
                 f"gamma0 {g0:g}, u_th {uth:g}, {ppc} ppc/species ({2 * nx * ny * ppc} particles)")
+    if name in LEARNED:
+        return (f"{nx}x{ny} periodic, CFL {cfl}, theta {theta}, order {order}, pair plasma gamma0 {g0:g}, "
+                f"u_th {uth:g}, {ppc} ppc/species ({2 * nx * ny * ppc} particles), PCG rtol 1e-10 from the "
+                f"learned warm start (network trained on 20000 (b, dB) pairs of 64x64 runs)")
     if name in NODAL:
         return (f"{nx}x{ny} periodic, node-averaged gather, CFL {cfl}, theta {theta}, order {order}, "
                 f"pair plasma gamma0 {g0:g}, u_th {uth:g}, {ppc} ppc/species ({2 * nx * ny * ppc} particles), "
@@ -261,6 +271,8 @@ def params_of(rows, precision):
             kw = dict(bc_x=pic.PIC_BC_WALLS, inject_x0=r["inject_x0"], u_th=r["u_th"], seed=r["inj_seed"])
         flags = (pic.PIC_NO_GRAPH if NO_GRAPH else 0) | (pic.PIC_EXPLICIT if r.get("explicit") else 0)
         flags |= pic.PIC_GATHER_NODAL if r.get("nodal") else 0
+        if r.get("learned") and precision == pic.PIC_MIXED32:
+            kw["warm_start"] = pic.PIC_WS_LEARNED
         out.append(pic.pic_params_default(nx=r["nx"], ny=r["ny"], cfl=r["cfl"], theta=r["theta"],
                                           shape_order=r["order"], gamma0=r["gamma0"], ppc=r["ppc"],
                                           precision=precision, cg_rtol=1e-10, cg_max_iter=200,
@@ -274,7 +286,21 @@ def new_sim(params, stream=None):
     h = pic.pic_init_batch(params) if len(params) > 1 else pic.pic_init(params[0])
     if stream is not None:
         pic.pic_set_stream(h, stream)
+    if any(p.warm_start == pic.PIC_WS_LEARNED for p in params):
+        pic.pic_set_cnn(h, NET)
     return h
+
+
+def train_warm_start(row):
+    """The learned warm start of a workload: 20000 (b, dB) pairs from 64 x 64 MIXED32 runs
+    of the same CFL, theta and shape order, then 3000 training steps on the GPU."""
+    from paper_1412_2480_gb300 import warmstart
+    t0 = time.perf_counter()
+    B, X = warmstart.generate_pairs(steps=10000, seeds=(11, 12), cfl=row["cfl"], theta=row["theta"],
+                                    order=row["order"], ppc=row["ppc"], gamma0=row["gamma0"], u_th=row["u_th"])
+    t1 = time.perf_counter()
+    net, loss, sec = warmstart.train(B, X, iters=3000)
+    return net, {"pairs": int(len(B)), "pairs_seconds": t1 - t0, "train_seconds": sec, "train_loss": float(loss)}
 
 
 def load(h, data, rows=None):
@@ -326,6 +352,10 @@ def run_ours(args, dist):
     stream = torch.cuda.Stream()
     data = make_inputs(rows, pinned=True)
     npart = sum(d["x"].size for sp in data for d in sp)  # loaded at step 0
+    train_info = None
+    if rows[0].get("learned") and args.precision == "mixed":
+        global NET
+        NET, train_info = train_warm_start(rows[0])
     prec = pic.PIC_MIXED32 if args.precision == "mixed" else pic.PIC_FP64
     if nsim > 1 and prec != pic.PIC_MIXED32:
         raise SystemExit("the batched scan runs in MIXED32 (its FP64 comparison is built in)")
@@ -419,11 +449,27 @@ def run_ours(args, dist):
     prof = pic.pic_profile(h, args.steps if args.prof_steps <= 0 else args.prof_steps)
     pic.pic_free(h)
 
+    # the three initial guesses of the solve on the same steps (learned warm start only)
+    ws_cmp = None
+    if train_info is not None:
+        ws_cmp = {"training": train_info}
+        for nm, ws in (("zero", pic.PIC_WS_ZERO), ("previous_dB", pic.PIC_WS_PREV),
+                       ("learned", pic.PIC_WS_LEARNED)):
+            ps = params_of(rows, prec)
+            for p_ in ps:
+                p_.warm_start = ws
+            h = new_sim(ps, stream)
+            load(h, data, rows)
+            pic.pic_step(h, args.warmup)
+            pr = pic.pic_profile(h, args.steps)
+            ws_cmp[nm] = {"cg_iters_per_step": pr["cg_iters"], "field_solve_ms_per_step": pr["field_ms"],
+                          "ms_per_step": pr["step_ms"]}
+            pic.pic_free(h)
     res = {"ms": ms_max, "prof": prof, "cg_iters": (it1 - it0) / args.steps,
            "cg_refinements": (ref1 - ref0) / args.steps, "clocks": ck, "launches": n_launch,
            "e2e_s": e2e_s, "h2d": h2d, "d2h": d2h, "npart": npart, "ncell": ncell,
            "updates_timed": particle_updates(rows, npart, args.warmup, args.steps),
-           "spectrum_ms": spectrum_ms,
+           "spectrum_ms": spectrum_ms, "warm_start_comparison": ws_cmp,
            "particles_end": sum(m1["n_particles"]) if nsim == 1 else None,
            "particles_expected": particle_updates(rows, npart, args.warmup + args.steps, 1),
            "updates_e2e": particle_updates(rows, npart, 0, args.steps),
@@ -600,6 +646,7 @@ def main():
         "gpu_launches": res["launches"],
         "particles_end": {"counted": res["particles_end"], "schedule": res["particles_expected"]},
         "spectrum_ms": res["spectrum_ms"],
+        **({"warm_start_comparison": res["warm_start_comparison"]} if res.get("warm_start_comparison") else {}),
         "clocks": res["clocks"],
     }
     if res["tune"]:

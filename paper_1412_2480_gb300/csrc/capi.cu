@@ -986,6 +986,7 @@ int pic_autotune_tiles(pic_params* prm, int32_t n, int32_t steps, double* best_m
                 pic_params q = prm[k];
                 q.precision = PIC_MIXED32;
                 q.flags &= ~PIC_NO_GRAPH;
+                if (q.warm_start == PIC_WS_LEARNED) q.warm_start = PIC_WS_ZERO;  // the tiles do not see it
                 q.tile_x = c[0];
                 q.tile_y = c[1];
                 const int tx = std::min(c[0], q.nx), ty = std::min(c[1], q.ny);
