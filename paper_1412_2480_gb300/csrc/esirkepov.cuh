@@ -54,13 +54,17 @@ __device__ __forceinline__ R window_weight(const R w[P + 1], int sh, int k) {
 // Jy running sum is complete one row earlier (its row-P value is zero up to rounding and
 // is not written). A warp whose particles all keep their y base (transverse moves far
 // below a cell, as in a relativistic beam) then writes the P+1 rows only: 30% fewer
-// shared-memory updates. A particle's currents do not depend on the path its warp takes
-// (the full window adds exact zeros in the last row and skips the same Jy value), so
-// results stay independent of how particles are grouped into warps.
+// shared-memory updates. In the full window each such lane skips its last-row updates
+// (exact zeros) and the same Jy value, so a particle's currents do not depend on the path
+// its warp takes, and results stay independent of how particles are grouped into warps.
+// (Skipping the exact-zero last column of a lane that keeps its x base measured slower:
+// the extra predicates cost more than the updates they save.)
 template <int P, int WY, typename R, typename Add>
 __device__ __forceinline__ void esirkepov_window(int ox, int oy, const R S0x[P + 2], const R DSx[P + 2],
                                                  const R S0y[P + 2], const R DSy[P + 2], R fx, R fy, R fz,
                                                  bool ysame, Add add) {
+    // row b of the window is an exact zero for this lane
+    const auto row0 = [&](int b) { return WY == P + 2 && b == P + 1 && ysame; };
 #pragma unroll
     for (int b = 0; b < WY; b++) {
         const R ry = fx * (S0y[b] + R(0.5) * DSy[b]);
@@ -68,7 +72,7 @@ __device__ __forceinline__ void esirkepov_window(int ox, int oy, const R S0x[P +
 #pragma unroll
         for (int a = 0; a <= P; a++) {
             run -= DSx[a] * ry;
-            add(0, ox + a, oy + b, run);
+            if (!row0(b)) add(0, ox + a, oy + b, run);
         }
     }
 #pragma unroll
@@ -86,7 +90,8 @@ __device__ __forceinline__ void esirkepov_window(int ox, int oy, const R S0x[P +
         const R cy0 = fz * (S0y[b] + R(0.5) * DSy[b]);
         const R cy1 = fz * (R(0.5) * S0y[b] + R(1.0 / 3.0) * DSy[b]);
 #pragma unroll
-        for (int a = 0; a < P + 2; a++) add(2, ox + a, oy + b, S0x[a] * cy0 + DSx[a] * cy1);
+        for (int a = 0; a < P + 2; a++)
+            if (!row0(b)) add(2, ox + a, oy + b, S0x[a] * cy0 + DSx[a] * cy1);
     }
 }
 
