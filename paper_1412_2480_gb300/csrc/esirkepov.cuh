@@ -9,22 +9,24 @@ namespace pic {
 // Relativistic Buneman-Boris push (standard scheme; the paper specifies none), c = 1:
 // half electric kick, rotation by t = h B / gamma(u-), s = 2t / (1 + t^2), half kick.
 // h = (q/m) dt / 2.
+// Every rounding is explicit (xmul, xfma, ...; pic_internal.cuh), so each kernel that
+// runs it gives the same bits.
 template <typename R>
 __device__ __forceinline__ void boris(R h, const R E[3], const R B[3], R u[3]) {
-    R um0 = u[0] + h * E[0], um1 = u[1] + h * E[1], um2 = u[2] + h * E[2];
-    const R ig = R(1) / sqrt(R(1) + um0 * um0 + um1 * um1 + um2 * um2);
-    const R t0 = h * B[0] * ig, t1 = h * B[1] * ig, t2 = h * B[2] * ig;
-    const R f = R(2) / (R(1) + t0 * t0 + t1 * t1 + t2 * t2);
-    const R s0 = f * t0, s1 = f * t1, s2 = f * t2;
-    const R p0 = um0 + (um1 * t2 - um2 * t1);
-    const R p1 = um1 + (um2 * t0 - um0 * t2);
-    const R p2 = um2 + (um0 * t1 - um1 * t0);
-    um0 += p1 * s2 - p2 * s1;
-    um1 += p2 * s0 - p0 * s2;
-    um2 += p0 * s1 - p1 * s0;
-    u[0] = um0 + h * E[0];
-    u[1] = um1 + h * E[1];
-    u[2] = um2 + h * E[2];
+    R um0 = xfma(h, E[0], u[0]), um1 = xfma(h, E[1], u[1]), um2 = xfma(h, E[2], u[2]);
+    const R ig = R(1) / sqrt(xfma(um2, um2, xfma(um1, um1, xfma(um0, um0, R(1)))));
+    const R t0 = xmul(xmul(h, B[0]), ig), t1 = xmul(xmul(h, B[1]), ig), t2 = xmul(xmul(h, B[2]), ig);
+    const R f = R(2) / xfma(t2, t2, xfma(t1, t1, xfma(t0, t0, R(1))));
+    const R s0 = xmul(f, t0), s1 = xmul(f, t1), s2 = xmul(f, t2);
+    const R p0 = xadd(um0, xfma(um1, t2, -xmul(um2, t1)));
+    const R p1 = xadd(um1, xfma(um2, t0, -xmul(um0, t2)));
+    const R p2 = xadd(um2, xfma(um0, t1, -xmul(um1, t0)));
+    um0 = xadd(um0, xfma(p1, s2, -xmul(p2, s1)));
+    um1 = xadd(um1, xfma(p2, s0, -xmul(p0, s2)));
+    um2 = xadd(um2, xfma(p0, s1, -xmul(p1, s0)));
+    u[0] = xfma(h, E[0], um0);
+    u[1] = xfma(h, E[1], um1);
+    u[2] = xfma(h, E[2], um2);
 }
 
 // Weight of node k (0..P+1) of a (P+2)-wide window, for a particle whose P+1 weights
@@ -67,31 +69,31 @@ __device__ __forceinline__ void esirkepov_window(int ox, int oy, const R S0x[P +
     const auto row0 = [&](int b) { return WY == P + 2 && b == P + 1 && ysame; };
 #pragma unroll
     for (int b = 0; b < WY; b++) {
-        const R ry = fx * (S0y[b] + R(0.5) * DSy[b]);
+        const R ry = xmul(fx, xfma(R(0.5), DSy[b], S0y[b]));
         R run = R(0);
 #pragma unroll
         for (int a = 0; a <= P; a++) {
-            run -= DSx[a] * ry;
+            run = xfma(-DSx[a], ry, run);
             if (!row0(b)) add(0, ox + a, oy + b, run);
         }
     }
 #pragma unroll
     for (int a = 0; a < P + 2; a++) {
-        const R rx = fy * (S0x[a] + R(0.5) * DSx[a]);
+        const R rx = xmul(fy, xfma(R(0.5), DSx[a], S0x[a]));
         R run = R(0);
 #pragma unroll
         for (int b = 0; b < WY - 1; b++) {
-            run -= DSy[b] * rx;
+            run = xfma(-DSy[b], rx, run);
             if (b < P || !ysame) add(1, ox + a, oy + b, run);
         }
     }
 #pragma unroll
     for (int b = 0; b < WY; b++) {
-        const R cy0 = fz * (S0y[b] + R(0.5) * DSy[b]);
-        const R cy1 = fz * (R(0.5) * S0y[b] + R(1.0 / 3.0) * DSy[b]);
+        const R cy0 = xmul(fz, xfma(R(0.5), DSy[b], S0y[b]));
+        const R cy1 = xmul(fz, xfma(R(1.0 / 3.0), DSy[b], xmul(R(0.5), S0y[b])));
 #pragma unroll
         for (int a = 0; a < P + 2; a++)
-            if (!row0(b)) add(2, ox + a, oy + b, S0x[a] * cy0 + DSx[a] * cy1);
+            if (!row0(b)) add(2, ox + a, oy + b, xfma(S0x[a], cy0, xmul(DSx[a], cy1)));
     }
 }
 
@@ -110,9 +112,9 @@ __device__ __forceinline__ void esirkepov(int i0, R f0x, int j0, R f0y, int i1, 
 #pragma unroll
     for (int k = 0; k < P + 2; k++) {
         S0x[k] = window_weight<P, R>(s0x, h0x, k);
-        DSx[k] = window_weight<P, R>(s1x, h1x, k) - S0x[k];
+        DSx[k] = xsub(window_weight<P, R>(s1x, h1x, k), S0x[k]);
         S0y[k] = window_weight<P, R>(s0y, h0y, k);
-        DSy[k] = window_weight<P, R>(s1y, h1y, k) - S0y[k];
+        DSy[k] = xsub(window_weight<P, R>(s1y, h1y, k), S0y[k]);
     }
     const bool ysame = b0y == b1y;
     if (__all_sync(__activemask(), ysame))  // (only lanes with ysame take the short path)

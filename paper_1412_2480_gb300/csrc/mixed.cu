@@ -26,9 +26,11 @@
 //      window is added to the global fixed-point current at the end;
 //   2. k_mixed_swap: the buffers swap.
 // No global atomics are needed in steady state and no migration kernel runs. A particle
-// found outside its tile is pushed with the same arithmetic on global memory, so
-// correctness never depends on bin capacity; a particle that finds no room goes to the
-// overflow list and the host re-sorts with larger bins after the pic_step call.
+// found outside its tile is pushed with the same arithmetic and the same current
+// rounding on global memory, so results never depend on bin capacity; a particle that
+// finds no room goes to the overflow list and the host re-sorts with larger bins after
+// the pic_step call. Count slots record every particle sent to a segment, parked ones
+// included; readers clamp them to the segment's capacity.
 #include <cub/cub.cuh>
 
 #include <algorithm>
@@ -74,7 +76,8 @@ struct MixedArgs {
     const float* F32;
     long long* Jfix;
     unsigned* buf[2];
-    int* cnt[2];  // [nbins * kSegs] per parity
+    int* cnt[2];     // [nbins * kSegs] per parity: particles sent to each segment
+    int* ovf_in[2];  // [ntiles_total] per parity: particles the overflow kernel moved in
     Slots ovf[2];
     long long ovf_cap;
     CgState* cg;
@@ -92,7 +95,8 @@ struct MixedState {
     DevStatus* st = nullptr;
     unsigned* buf[2] = {nullptr, nullptr};
     Slots ovf[2]{};
-    int* cnt[2] = {nullptr, nullptr};  // [ntiles_total * 2 * kSegs] per parity
+    int* cnt[2] = {nullptr, nullptr};  // [ntiles_total * 2 * kSegs] per parity, then ovf_in
+    int* ovf_in[2] = {nullptr, nullptr};  // [ntiles_total] per parity (inside cnt's block)
     long long nslots = 0, ovf_cap = 0;
     int ntiles_total = 0;
     int* tile_grid = nullptr;     // device [ntiles_total]
@@ -129,6 +133,39 @@ __host__ __device__ __forceinline__ void dir_of(int o, int& dx, int& dy) {
     dy = d / 3 - 1;
 }
 
+// The tile (within its simulation) whose bin holds segment k of the particles tile
+// (txi, tyi) pushes: its own stayers (k = 0), or the outbox k - 1 of the neighbour on the
+// opposite side, which is addressed to it.
+__device__ __forceinline__ int segment_source(const GridDev& G, int txi, int tyi, int k) {
+    if (k == 0) return tyi * G.ntx + txi;
+    int dx, dy;
+    dir_of(k - 1, dx, dy);
+    const int sx = (txi - dx + G.ntx) % G.ntx, sy = (tyi - dy + G.nty) % G.nty;
+    return sy * G.ntx + sx;
+}
+
+// Particles of species s sent to segment k of bin `src` in the last step (count slots of
+// the current buffer). The count includes those that found no room and were parked in
+// the overflow list; the segment itself holds at most its capacity of them.
+__device__ __forceinline__ int segment_sent(const GridDev& G, const int* ccur, int src, int s, int k) {
+    return ccur[((long long)G.tile_first * 2 + (long long)src * 2 + s) * kSegs + k];
+}
+
+// Particles whose cell lies in tile lt at the start of the step, both species, wherever
+// they are stored: those sent to its segments (parked ones included) and those the
+// overflow kernel moved into it. This count does not depend on which particles found
+// room in the bins, so neither does the rounding it sets.
+__device__ __forceinline__ int tile_population(const GridDev& G, const int* ccur, const int* oin, int lt) {
+    const int tyi = lt / G.ntx, txi = lt - tyi * G.ntx;
+    int n = oin[G.tile_first + lt];
+    for (int s = 0; s < 2; s++)
+        for (int k = 0; k < kSegs; k++) n += segment_sent(G, ccur, segment_source(G, txi, tyi, k), s, k);
+    return n;
+}
+
+// Tile (within its simulation) of cell (i, j).
+__device__ __forceinline__ int tile_of(const GridDev& G, int i, int j) { return (j / G.ty) * G.ntx + i / G.tx; }
+
 // ---------------------------------------------------------------------------------
 // Memory views used by the shared push arithmetic.
 // ---------------------------------------------------------------------------------
@@ -138,11 +175,45 @@ __host__ __device__ __forceinline__ void dir_of(int o, int& dx, int& dy) {
 // u/2 (GridDev::jscale = 2^40/u). A contribution v becomes x = v 2^k/u, split into its
 // nearest integer hi and the rest r = x - hi in [-1/2, 1/2], and lo = round(r 2^lb);
 // integers come from one FMA with 1.5 * 2^23 (exact below 2^22 in magnitude). Each tile
-// picks k, lb <= 30 - log2(n + 1) from its particle count n (no word can wrap, whatever
-// the distribution) with k <= 22 and lb <= 16, i.e. a resolution of 2^-(k+lb) u. The
-// flush adds hi 2^(40-k) + lo 2^(40-k-lb) exactly into the 64-bit global current.
+// picks k, lb <= 30 - log2(n + 1) from its population n, the particles whose cell lies in
+// it (no word can wrap, whatever the distribution), with k <= 22 and lb <= 16, i.e. a
+// resolution of 2^-(k+lb) u. The flush adds hi 2^(40-k) + lo 2^(40-k-lb) exactly into
+// the 64-bit global current.
+// A particle pushed on global memory (outside its tile's window, or parked in the
+// overflow list) rounds the same way, with the k and lb of the tile its cell lies in, so
+// a particle's current does not depend on the path it takes and a run is bit-for-bit
+// reproducible whichever particles find room in the bins.
 constexpr float kMagic = 12582912.0f;  // 1.5 * 2^23
 constexpr int kMagicBits = 0x4B400000;
+
+struct FixedScale {
+    int k, lb;
+    float js;   // window scale 2^k / u
+    float jlb;  // 2^lb
+};
+
+__device__ __forceinline__ FixedScale fixed_scale(const GridDev& G, int n_tile) {
+    const int room = 30 - (32 - __clz(n_tile));  // n_tile < 2^(30 - room)
+    FixedScale f;
+    f.k = min(22, room);
+    f.lb = min(16, room);
+    f.js = (float)(G.jscale * exp2((double)(f.k - 40)));
+    f.jlb = (float)(1 << f.lb);
+    return f;
+}
+
+// x (window units) -> the two words (hi, lo)
+__device__ __forceinline__ void fixed_split(float x, float jlb, int& hi, int& lo) {
+    const float xr = xadd(x, kMagic);
+    hi = __float_as_int(xr) - kMagicBits;
+    const float r = xsub(x, xsub(xr, kMagic));  // exact: |r| <= 1/2
+    lo = __float_as_int(xfma(r, jlb, kMagic)) - kMagicBits;
+}
+
+// (hi, lo) summed in a window -> global fixed-point units
+__device__ __forceinline__ long long fixed_value(long long hi, long long lo, const FixedScale& f) {
+    return hi * (1ll << (40 - f.k)) + lo * (1ll << (40 - f.k - f.lb));
+}
 
 // The tile's field window pairs the components that share a lattice -- (Ex, By) at
 // (i+1/2, j) and (Ey, Bx) at (i, j+1/2) -- as float2, so one 64-bit load serves two
@@ -165,10 +236,8 @@ struct WinMem {  // tile window in shared memory; indices are window-local
     // x: the contribution already in window units (the push folds js into its deposit
     // constants)
     __device__ __forceinline__ void add(int c, int ix, int iy, float x) const {
-        const float xr = x + kMagic;
-        const int hi = __float_as_int(xr) - kMagicBits;
-        const float r = x - (xr - kMagic);  // exact: |r| <= 1/2
-        const int lo = __float_as_int(fmaf(r, jlb, kMagic)) - kMagicBits;
+        int hi, lo;
+        fixed_split(x, jlb, hi, lo);
         const int k = c * nw + iy * wx + ix;
         atomicAdd(&jhi[k], hi);
         atomicAdd(&jlo[k], lo);
@@ -180,7 +249,8 @@ struct GlobalMem {  // global grid arrays of one simulation; indices are global
     unsigned long long* J;
     long long ntot;
     int nx, ny;
-    float js;
+    FixedScale f;  // the rounding of the tile the particle's cell lies in
+    float js;      // = f.js: contributions arrive in that tile's window units
     int walls;
     __device__ __forceinline__ long long at(int ix, int iy) const {
         return (long long)wrapi(iy, ny) * nx + wrapi(ix, nx);
@@ -192,17 +262,18 @@ struct GlobalMem {  // global grid arrays of one simulation; indices are global
         const int cx = wall_col(ix, nx, half, !half, s);
         return s == 0 ? 0.f : (float)s * __ldg(F + c * ntot + (long long)wrapi(iy, ny) * nx + cx);
     }
-    // v: the contribution already in global fixed-point units (times js)
-    __device__ __forceinline__ void add(int c, int ix, int iy, float v) const {
+    // x: the contribution in window units (times js), rounded as the window rounds it
+    __device__ __forceinline__ void add(int c, int ix, int iy, float x) const {
+        int hi, lo;
+        fixed_split(x, f.jlb, hi, lo);
+        const long long v = fixed_value(hi, lo, f);
         if (!walls) {
-            atomicAdd(J + c * ntot + at(ix, iy), (unsigned long long)__float2ll_rn(v));
+            atomicAdd(J + c * ntot + at(ix, iy), (unsigned long long)v);
             return;
         }
         int s;
         const int cx = wall_col(ix, nx, c == 0, c == 0, s);  // mirror image: Jx odd
-        if (s != 0)
-            atomicAdd(J + c * ntot + (long long)wrapi(iy, ny) * nx + cx,
-                      (unsigned long long)__float2ll_rn((float)s * v));
+        if (s != 0) atomicAdd(J + c * ntot + (long long)wrapi(iy, ny) * nx + cx, (unsigned long long)(s * v));
     }
 };
 
@@ -303,22 +374,23 @@ __device__ __forceinline__ bool push_one(const Mem& M, const PushConst& K, int i
         shape_nodes_half<P, float>(j, oy, byh, wyh);
         gather_fields<P>(M, bx0, wx0, bxh, wxh, by0, wy0, byh, wyh, E, B);
     }
-    const float g_old = sqrtf(1.f + u[0] * u[0] + u[1] * u[1] + u[2] * u[2]);
+    // (the rounding of the update is explicit: xmul, xfma, ... in pic_internal.cuh)
+    const float g_old = sqrtf(xfma(u[2], u[2], xfma(u[1], u[1], xfma(u[0], u[0], 1.f))));
     boris<float>(K.h, E, B, u);
-    const float ig = rsqrtf(1.f + u[0] * u[0] + u[1] * u[1] + u[2] * u[2]);
-    const float dX = K.dt_idx * u[0] * ig, dY = K.dt_idy * u[1] * ig;
+    const float ig = rsqrtf(xfma(u[2], u[2], xfma(u[1], u[1], xfma(u[0], u[0], 1.f))));
+    const float dX = xmul(xmul(K.dt_idx, u[0]), ig), dY = xmul(xmul(K.dt_idy, u[1]), ig);
     di = 0;
     dj = 0;
     if (!(fabsf(dX) < 1.f && fabsf(dY) < 1.f)) return false;
     ek += g_old + 1.f / ig - 2.f;
-    float x1 = ox + dX, y1 = oy + dY;
-    if (x1 >= 1.f) { x1 -= 1.f; di = 1; }
-    else if (x1 < 0.f) { x1 += 1.f; di = -1; if (x1 >= 1.f) { x1 = 0.f; di = 0; } }
-    if (y1 >= 1.f) { y1 -= 1.f; dj = 1; }
-    else if (y1 < 0.f) { y1 += 1.f; dj = -1; if (y1 >= 1.f) { y1 = 0.f; dj = 0; } }
+    float x1 = xadd(ox, dX), y1 = xadd(oy, dY);
+    if (x1 >= 1.f) { x1 = xsub(x1, 1.f); di = 1; }
+    else if (x1 < 0.f) { x1 = xadd(x1, 1.f); di = -1; if (x1 >= 1.f) { x1 = 0.f; di = 0; } }
+    if (y1 >= 1.f) { y1 = xsub(y1, 1.f); dj = 1; }
+    else if (y1 < 0.f) { y1 = xadd(y1, 1.f); dj = -1; if (y1 >= 1.f) { y1 = 0.f; dj = 0; } }
     if (K.deposit)
-        esirkepov<P, float>(i, ox, j, oy, i + di, x1, j + dj, y1, K.fx * M.js, K.fy * M.js,
-                            K.fz * (u[2] * ig) * M.js,
+        esirkepov<P, float>(i, ox, j, oy, i + di, x1, j + dj, y1, xmul(K.fx, M.js), xmul(K.fy, M.js),
+                            xmul(xmul(K.fz, xmul(u[2], ig)), M.js),
                             [M](int c, int ix, int iy, float v) { M.add(c, ix, iy, v); });
     ox = x1;
     oy = y1;
@@ -398,8 +470,10 @@ k_push_tile(const MixedArgs a) {
     __shared__ int s_start[2][kSegs + 1];     // virtual start of each segment, per species
     __shared__ long long s_base[2][kSegs];     // physical first slot of each segment
     __shared__ int s_out[2][kSegs];            // next-buffer counts (stayers, outboxes)
+    __shared__ int s_sent[2][kSegs + 1];       // particles sent to each segment; [0][kSegs]: moved
+                                               // in by the overflow kernel
     __shared__ double s_red[32];
-    __shared__ int s_item;
+    __shared__ int s_item, s_pop;
     DevStatus* st = a.st;
     if (st->stop) return;
     const int par = (int)st->parity, nxp = par ^ 1;
@@ -425,21 +499,18 @@ k_push_tile(const MixedArgs a) {
         float* fw = reinterpret_cast<float*>(smem_raw + (size_t)6 * NW * sizeof(int));
         if (threadIdx.x < 2 * kSegs) {
             const int s = threadIdx.x / kSegs, k = threadIdx.x - (threadIdx.x / kSegs) * kSegs;
-            int src = lt;
-            long long off = 0, lim = cap;
-            if (k > 0) {
-                int dx, dy;
-                dir_of(k - 1, dx, dy);
-                const int sx = (txi - dx + G.ntx) % G.ntx, sy = (tyi - dy + G.nty) % G.nty;
-                src = sy * G.ntx + sx;
-                off = cap + (long long)(k - 1) * capo;
-                lim = capo;
-            }
+            const int src = segment_source(G, txi, tyi, k);
+            const long long off = k == 0 ? 0 : cap + (long long)(k - 1) * capo;
             const long long b = (long long)src * 2 + s;
-            const int* ccur = par ? a.cnt[1] : a.cnt[0];
-            const int cnt = (int)min((long long)ccur[((long long)G.tile_first * 2 + b) * kSegs + k], lim);
-            s_start[s][k + 1] = cnt;  // prefix-summed below
+            const int sent = segment_sent(G, par ? a.cnt[1] : a.cnt[0], src, s, k);
+            s_sent[s][k] = sent;
+            s_start[s][k + 1] = (int)min((long long)sent, k == 0 ? cap : capo);  // prefix-summed below
             s_base[s][k] = G.bin_off + b * stride + off;
+            if (threadIdx.x == 0) {
+                int* oin = par ? a.ovf_in[1] : a.ovf_in[0];
+                s_sent[0][kSegs] = oin[t];
+                oin[t] = 0;  // read; the overflow kernel of the next step counts into it again
+            }
             s_out[s][k] = 0;
         }
         const float* Fg = a.F32 + G.cell_off;
@@ -465,16 +536,17 @@ k_push_tile(const MixedArgs a) {
             const int s = threadIdx.x;
             s_start[s][0] = 0;
             for (int k = 1; k <= kSegs; k++) s_start[s][k] += s_start[s][k - 1];
+        } else if (threadIdx.x == 2) {  // the sum tile_population() forms
+            int n = s_sent[0][kSegs];
+            for (int s = 0; s < 2; s++)
+                for (int k = 0; k < kSegs; k++) n += s_sent[s][k];
+            s_pop = n;
         }
         __syncthreads();
-        const float js = (float)G.jscale;
-        const int n_tile = s_start[0][kSegs] + s_start[1][kSegs];
-        const int room = 30 - (32 - __clz(n_tile));  // n_tile < 2^(30 - room)
-        const int kwin = min(22, room), lbits = min(16, room);
-        const WinMem W{fw, jw, jw + 3 * NW, WX, NW, (float)(G.jscale * exp2((double)(kwin - 40))),
-                       (float)(1 << lbits)};
+        const FixedScale fs = fixed_scale(G, s_pop);
+        const WinMem W{fw, jw, jw + 3 * NW, WX, NW, fs.js, fs.jlb};
         const GlobalMem M{a.F32 + G.cell_off, reinterpret_cast<unsigned long long*>(a.Jfix + G.cell_off),
-                          a.ntot, nx, ny, js, G.walls};
+                          a.ntot, nx, ny, fs, fs.js, G.walls};
         const unsigned* cur = par ? a.buf[1] : a.buf[0];
         unsigned* nxt = par ? a.buf[0] : a.buf[1];
         float ek = 0.f;
@@ -529,27 +601,30 @@ k_push_tile(const MixedArgs a) {
                     long long slot = -1;
                     if (dest == 0 && b0 < cap) slot = own + b0;
                     else if (dest > 0 && b0 < capo) slot = own + cap + (long long)(dest - 1) * capo + b0;
-                    if (slot >= 0) put(nxt, slot, cnew, ox, oy, u);
-                    else
+                    if (slot >= 0) {
+                        put(nxt, slot, cnew, ox, oy, u);
+                    } else {
                         to_overflow(nxp ? a.ovf[1].p : a.ovf[0].p, nxp ? a.ovf[1].gs : a.ovf[0].gs,
                                     a.ovf_cap, st, nxp, cnew, ox, oy, u[0], u[1], u[2], s | (g << 1));
+                        if (dest < 0)  // sent to no bin: count it in its tile's population
+                            atomicAdd((nxp ? a.ovf_in[1] : a.ovf_in[0]) + G.tile_first +
+                                          tile_of(G, cnew & 0xffff, cnew >> 16), 1);
+                    }
                 }
             }
         }
         __syncthreads();
         if (threadIdx.x < 2 * kSegs) {
             const int s = threadIdx.x / kSegs, k = threadIdx.x - (threadIdx.x / kSegs) * kSegs;
-            const long long lim = k == 0 ? cap : capo;
             int* cnxt = nxp ? a.cnt[1] : a.cnt[0];
-            cnxt[((long long)t * 2 + s) * kSegs + k] = (int)min((long long)s_out[s][k], lim);
+            cnxt[((long long)t * 2 + s) * kSegs + k] = s_out[s][k];  // sent, parked ones included
         }
         // add the current window into the global fixed-point current
         unsigned long long* Jg = reinterpret_cast<unsigned long long*>(a.Jfix + G.cell_off);
         for (int idx = threadIdx.x; idx < 3 * NW; idx += blockDim.x) {
             const int hi = jw[idx], lo = jw[3 * NW + idx];
             if ((hi | lo) == 0) continue;
-            const unsigned long long v = (unsigned long long)((long long)hi * (1ll << (40 - kwin)) +
-                                                              (long long)lo * (1ll << (40 - kwin - lbits)));
+            const unsigned long long v = (unsigned long long)fixed_value(hi, lo, fs);
             const int c = idx / NW;
             const int w = idx - c * NW;
             const int wy = w / WX;
@@ -597,9 +672,12 @@ k_push_overflow(const MixedArgs a) {
         const int gs = O.gs[k];
         const int s = gs & 1, g = gs >> 1;
         const GridDev& G = a.grids[g];
-        const GlobalMem M{a.F32 + G.cell_off, reinterpret_cast<unsigned long long*>(a.Jfix + G.cell_off),
-                          a.ntot, G.nx, G.ny, (float)G.jscale, G.walls};
         const int ci = c & 0xffff, cj = c >> 16;
+        // round the current as the tile the particle's cell lies in rounds its window
+        const FixedScale fs = fixed_scale(G, tile_population(G, par ? a.cnt[1] : a.cnt[0],
+                                                             par ? a.ovf_in[1] : a.ovf_in[0], tile_of(G, ci, cj)));
+        const GlobalMem M{a.F32 + G.cell_off, reinterpret_cast<unsigned long long*>(a.Jfix + G.cell_off),
+                          a.ntot, G.nx, G.ny, fs, fs.js, G.walls};
         int di, dj;
         float ek = 0.f;
         bool ok;
@@ -611,9 +689,11 @@ k_push_overflow(const MixedArgs a) {
         if (!ok) flag_bad(st, u);
         if (ek != 0.f) atomicAdd(&a.cg[g].uk, 0.5 * G.w * (double)ek);
         const int ni = G.walls ? reflect_x(ci + di, G.nx, ox, u[0]) : wrapi(ci + di, G.nx);
-        const int cnew = ni | (wrapi(cj + dj, G.ny) << 16);
+        const int nj = wrapi(cj + dj, G.ny);
+        const int cnew = ni | (nj << 16);
         to_overflow(par ? a.ovf[0].p : a.ovf[1].p, par ? a.ovf[0].gs : a.ovf[1].gs, a.ovf_cap, st,
                     par ^ 1, cnew, ox, oy, u[0], u[1], u[2], gs);
+        atomicAdd((par ? a.ovf_in[0] : a.ovf_in[1]) + G.tile_first + tile_of(G, ni, nj), 1);
     }
 }
 
@@ -875,6 +955,7 @@ MixedArgs make_args(MixedState* m, int order) {
     for (int p = 0; p < 2; p++) {
         a.buf[p] = m->buf[p];
         a.cnt[p] = m->cnt[p];
+        a.ovf_in[p] = m->ovf_in[p];
         a.ovf[p] = m->ovf[p];
     }
     a.ovf_cap = m->ovf_cap;
@@ -1045,7 +1126,7 @@ int alloc_bins(MixedState* m, const std::vector<long long>& cap, const std::vect
             err = "bin allocation failed (" + std::to_string(m->nslots) + " slots per buffer)";
             return PIC_ENOMEM;
         }
-        MCK(cudaMemsetAsync(m->cnt[p], 0, (size_t)m->ntiles_total * 2 * kSegs * sizeof(int), st));
+        MCK(cudaMemsetAsync(m->cnt[p], 0, (size_t)m->ntiles_total * (2 * kSegs + 1) * sizeof(int), st));
     }
     return PIC_OK;
 }
@@ -1184,7 +1265,8 @@ int mixed_create(MixedState** out, const pic_params* p, int ngrids, GridDev* G,
     m->ovf_cap = (m->ovf_cap + 31) / 32 * 32;
     cudaError_t e = cudaSuccess;
     for (int q = 0; q < 2 && e == cudaSuccess; q++) {
-        e = dalloc(&m->cnt[q], (size_t)ntiles * 2 * kSegs);
+        e = dalloc(&m->cnt[q], (size_t)ntiles * (2 * kSegs + 1));
+        if (e == cudaSuccess) m->ovf_in[q] = m->cnt[q] + (size_t)ntiles * 2 * kSegs;
         if (e == cudaSuccess) e = dalloc(&m->ovf[q].p, (size_t)m->ovf_cap * kFields);
         if (e == cudaSuccess) e = dalloc(&m->ovf[q].gs, (size_t)m->ovf_cap);
     }

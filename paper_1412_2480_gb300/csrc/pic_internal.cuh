@@ -91,6 +91,24 @@ struct SegDev {
 };
 
 // ---------------------------------------------------------------------------------
+// Rounded arithmetic of the particle update. The compiler decides per kernel whether a
+// product followed by a sum becomes one fused multiply-add, so the same expression can
+// round differently in two kernels. A particle is pushed by the tile kernel (shared-
+// memory window or global memory) or, when its bin was full, by the overflow kernel; for
+// a run to be bit-for-bit reproducible whichever particles overflow, every rounding of
+// the push, the shapes and the deposit is written out: xmul/xadd/xsub never fuse, xfma
+// is one fused operation.
+// ---------------------------------------------------------------------------------
+__device__ __forceinline__ float xmul(float a, float b) { return __fmul_rn(a, b); }
+__device__ __forceinline__ double xmul(double a, double b) { return __dmul_rn(a, b); }
+__device__ __forceinline__ float xadd(float a, float b) { return __fadd_rn(a, b); }
+__device__ __forceinline__ double xadd(double a, double b) { return __dadd_rn(a, b); }
+__device__ __forceinline__ float xsub(float a, float b) { return __fsub_rn(a, b); }
+__device__ __forceinline__ double xsub(double a, double b) { return __dsub_rn(a, b); }
+__device__ __forceinline__ float xfma(float a, float b, float c) { return __fmaf_rn(a, b, c); }
+__device__ __forceinline__ double xfma(double a, double b, double c) { return __fma_rn(a, b, c); }
+
+// ---------------------------------------------------------------------------------
 // Particle shapes: centred B-splines of order P. Given a coordinate split into an
 // integer cell i and a fraction f in [0,1) on a lattice whose node k sits at k, return
 // the first node `base` and the P+1 weights of nodes base .. base+P.
@@ -99,7 +117,7 @@ template <int P, typename R>
 __device__ __forceinline__ void shape_nodes(int i, R f, int& base, R w[P + 1]) {
     if constexpr (P == 1) {
         base = i;
-        w[0] = R(1) - f;
+        w[0] = xsub(R(1), f);
         w[1] = f;
     } else if constexpr (P == 2) {
         // nearest node c = i (f < 1/2) or i+1; d = x - c in [-1/2, 1/2)
@@ -109,30 +127,30 @@ __device__ __forceinline__ void shape_nodes(int i, R f, int& base, R w[P + 1]) {
             d = f;
         } else {
             base = i;
-            d = f - R(1);
+            d = xsub(f, R(1));
         }
-        const R hm = R(0.5) - d, hp = R(0.5) + d;
-        w[0] = R(0.5) * hm * hm;
-        w[1] = R(0.75) - d * d;
-        w[2] = R(0.5) * hp * hp;
+        const R hm = xsub(R(0.5), d), hp = xadd(R(0.5), d);
+        w[0] = xmul(xmul(R(0.5), hm), hm);
+        w[1] = xfma(-d, d, R(0.75));
+        w[2] = xmul(xmul(R(0.5), hp), hp);
     } else {
         base = i - 1;
-        const R g = R(1) - f;
-        const R f2 = f * f, f3 = f2 * f;
-        w[0] = g * g * g * R(1.0 / 6.0);
-        w[1] = (R(4) - R(6) * f2 + R(3) * f3) * R(1.0 / 6.0);
-        w[2] = (R(1) + R(3) * (f + f2 - f3)) * R(1.0 / 6.0);
-        w[3] = f3 * R(1.0 / 6.0);
+        const R g = xsub(R(1), f);
+        const R f2 = xmul(f, f), f3 = xmul(f2, f);
+        w[0] = xmul(xmul(xmul(g, g), g), R(1.0 / 6.0));
+        w[1] = xmul(xfma(R(3), f3, xfma(R(-6), f2, R(4))), R(1.0 / 6.0));
+        w[2] = xmul(xfma(R(3), xsub(xadd(f, f2), f3), R(1)), R(1.0 / 6.0));
+        w[3] = xmul(f3, R(1.0 / 6.0));
     }
 }
 
 // Same, on the lattice shifted by +1/2 (nodes at k + 1/2, stored at index k).
 template <int P, typename R>
 __device__ __forceinline__ void shape_nodes_half(int i, R f, int& base, R w[P + 1]) {
-    R s = f - R(0.5);
+    R s = xsub(f, R(0.5));
     int c = i;
     if (s < R(0)) {
-        s += R(1);
+        s = xadd(s, R(1));
         c -= 1;
         if (s >= R(1)) {  // s was a tiny negative number and s + 1 rounded up to 1
             s = R(0);
@@ -174,7 +192,7 @@ template <typename R>
 __device__ __forceinline__ int reflect_x(int cell, int nx, R& off, R& ux) {
     if (cell >= 0 && cell < nx) return cell;
     ux = -ux;
-    R o = R(1) - off;  // the position mirrored about the wall, within the wall cell
+    R o = xsub(R(1), off);  // the position mirrored about the wall, within the wall cell
     if (cell < 0) {
         if (o >= R(1)) {  // exactly one cell beyond x = 0: lands on node 1
             off = R(0);

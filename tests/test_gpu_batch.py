@@ -136,19 +136,23 @@ def counter_streaming(k, case):
 
 def test_batch_overflow_rebuild_matches_individual_runs():
     # bins sized with little slack overflow: particles go through the overflow path and
-    # every simulation is re-sorted after the call. Particles that overflow deposit
-    # through the global path, so results agree to rounding instead of bit for bit.
+    # every simulation is re-sorted after the call. Which particles find no room depends
+    # on warp scheduling, but a parked particle is pushed from global memory with the
+    # rounding of its tile's current window, so the runs still agree bit for bit.
     steps = 6
     batch = run_batch(OVF_CASES, steps, inp=counter_streaming, bin_slack=1.05)
-    rebins = 0
+    rebins = moves = 0
     for k, c in enumerate(OVF_CASES):
         Fa, Pa, ma = run_alone(k, c, steps, inp=counter_streaming, bin_slack=1.05)
         Fb, Pb, mb = batch[k]
         rebins = max(rebins, mb["rebins"])
-        for q in range(9):
-            assert rel(Fb[q], Fa[q]) < 1e-6, f"simulation {k}, quantity {q}"
+        moves += ma["overflow_moves"] + mb["overflow_moves"]
+        for q in range(12):
+            assert np.array_equal(Fa[q], Fb[q]), f"simulation {k}, quantity {q}"
+        for s in range(2):
+            assert np.array_equal(Pa[s], Pb[s]), f"simulation {k}, species {s}"
         assert ma["n_particles"] == mb["n_particles"]
-    assert rebins > 0
+    assert rebins > 0 and moves > 0
 
 
 def test_select_out_of_range_is_einval():
