@@ -60,7 +60,12 @@ extern "C" {
 #define PIC_ENAN (-6)        /* a non-finite particle momentum or position appeared */
 #define PIC_ESTATE (-8)      /* call not valid in the handle's current state */
 
-/* ---- precision of the particle half (the field solve is always FP64) ---- */
+/* ---- precision of the particle half (the field solve is always FP64) ----
+ * PIC_MIXED32 runs are bit-for-bit reproducible: the same inputs and parameters give the
+ * same fields, currents and particle sets on every run, alone or inside a batch, whatever
+ * the order particles are stored in and whichever of them overflow their bins (the
+ * current is summed in fixed point). PIC_FP64 sums its current with FP64 atomics and
+ * reproduces a run to rounding only. */
 #define PIC_FP64 0    /* positions, momenta, gather, push and deposit in FP64 */
 #define PIC_MIXED32 1 /* int cell + FP32 offset, FP32 momenta, FP32 gather/push/deposit */
 
