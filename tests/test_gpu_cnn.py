@@ -16,7 +16,7 @@ import pytest
 import paper_1412_2480_gb300 as pic
 from closed_forms import spectral_solve
 from oracle import cnn
-from runners import workload
+from runners import rel, run_oracle, workload
 
 pytestmark = pytest.mark.gpu
 
@@ -264,3 +264,36 @@ def test_learned_warm_start_cuts_pcg_iterations_in_a_pic_run(trained):
     # at least 10 % fewer iterations (measured 15-18 %; the exact figure varies with the
     # training, whose weight gradients are summed with unordered FP32 atomics)
     assert it_learned.sum() <= 0.90 * it_zero.sum(), (it_learned.sum(), it_zero.sum())
+
+
+def test_learned_warm_start_at_full_size_matches_oracle(trained):
+    # the benchmark's learned-warm-start workload size: 1024 x 256 cells, order 1, 8
+    # particles per cell per species (4.2M particles), one step from smooth random fields
+    # with the network's guess (trained on 64 x 64 runs; the collapsed stencil applies at
+    # any size), against the oracle's whole step from the zero guess, same tolerance
+    c, _, _ = trained
+    nx, ny, ppc, tol = 1024, 256, 8, 2e-5
+    w, sp, F0 = workload(nx, ny, ppc, gamma0=20.0, u_th=1e-3, seed=21, field_amp=0.05)
+    prm = pic.pic_params_default(nx=nx, ny=ny, shape_order=1, gamma0=20.0, ppc=ppc,
+                                 precision=pic.PIC_MIXED32, cg_rtol=1e-10, warm_start=pic.PIC_WS_LEARNED)
+    h = pic.pic_init(prm)
+    try:
+        pic.pic_set_cnn(h, c)
+        for k in range(6):
+            pic.pic_set_fields(h, k, np.ascontiguousarray(F0[k]).ravel())
+        for s, d in enumerate(sp):
+            pic.pic_load_particles(h, s, d["x"], d["y"], d["ux"], d["uy"], d["uz"])
+        pic.pic_step(h, 1)
+        m = pic.pic_moments(h)
+        Fg = np.stack([pic.fields_numpy(h, k, nx, ny) for k in range(9)])
+        Pg = [pic.pic_particles(h, s) for s in range(2)]
+    finally:
+        pic.pic_free(h)
+    assert 0.0 < m["cg_rel_resid"] <= 1e-10
+    Fo, po, _ = run_oracle(nx, ny, w, sp, F0, 1, 1, cg_rtol=1e-10)
+    Jp, _, _ = run_oracle(nx, ny, w, sp[:1], F0, 1, 1, cg_rtol=1e-10)  # one species' current
+    for k in range(6):
+        assert rel(Fg[k], Fo[k]) < tol, f"field {k}: {rel(Fg[k], Fo[k]):.2e}"
+    assert np.linalg.norm(Fg[6:9] - Fo[6:9]) / np.linalg.norm(Jp[6:9]) < tol
+    for s in range(2):
+        assert rel(np.sort(Pg[s][2:], axis=1), np.sort(po[s][2:], axis=1)) < tol
