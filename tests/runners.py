@@ -51,8 +51,38 @@ def run_oracle(nx, ny, w, sp, F0, steps, order, cfl=1.0, theta=0.5, cg_rtol=1e-1
 
 
 def rel(a, b):
+    """Norm-wise relative difference ||a - b|| / ||b||."""
     nb = np.linalg.norm(b)
     return float(np.linalg.norm(a - b) / (nb if nb > 0 else 1.0))
+
+
+def relmax(a, b, scale=None):
+    """Element-wise relative difference max|a - b| / max|b| (or / scale when given):
+    a wrong tile-edge column or wall node is not diluted by the grid size here."""
+    a = np.asarray(a, dtype=np.float64)
+    b = np.asarray(b, dtype=np.float64)
+    if a.size == 0:
+        return 0.0
+    m = float(np.abs(b).max()) if scale is None else float(scale)
+    return float(np.abs(a - b).max() / (m if m > 0 else 1.0))
+
+
+def check(a, b, tol, what="", scale=None):
+    """Parity of one quantity: both the norm-wise and the element-wise relative
+    difference within tol. With scale (the magnitude of the summed terms, e.g. one
+    species' current where two species cancel) both are taken relative to it."""
+    if scale is None:
+        r, m = rel(a, b), relmax(a, b)
+    else:
+        r = float(np.linalg.norm(np.asarray(a) - np.asarray(b)) / scale)
+        m = relmax(a, b, scale)
+    assert r < tol and m < tol, f"{what}: norm-wise {r:.2e}, element-wise {m:.2e} (bound {tol:.0e})"
+
+
+def check_rows(a, b, tol, what=""):
+    """check() for each row (component) of two arrays shaped (components, n)."""
+    for k in range(np.asarray(b).shape[0]):
+        check(np.asarray(a)[k], np.asarray(b)[k], tol, f"{what} row {k}")
 
 
 def match_particles(g, o, scale):

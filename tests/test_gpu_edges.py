@@ -11,7 +11,7 @@ import oracle
 import paper_1412_2480_gb300 as pic
 from closed_forms import amplification
 from paper_1412_2480_gb300 import inputs
-from runners import match_particles, rel, run_gpu
+from runners import check, match_particles, rel, run_gpu
 
 pytestmark = pytest.mark.gpu
 TOL32 = 2e-5
@@ -38,7 +38,7 @@ def test_rectangular_cells_match_oracle(precision, order):
     Fo, po = oracle_run(nx, ny, w, sp, F0, 2, order, cfl, dx=dx, dy=dy)
     tol = 1e-12 if precision == pic.PIC_FP64 else TOL32
     for c in range(9):
-        assert rel(Fg[c], Fo[c]) < tol, f"quantity {c}: {rel(Fg[c], Fo[c]):.2e}"
+        check(Fg[c], Fo[c], tol, f"quantity {c}")
     for s in range(2):
         d = match_particles(pg[s], po[s], [nx * dx, ny * dy, 3.0, 3.0, 3.0])
         assert d < (1e-12 if precision == pic.PIC_FP64 else 1e-5), d
@@ -83,7 +83,7 @@ def test_particles_on_cell_and_half_cell_boundaries(precision, order):
     Fo, po = oracle_run(nx, ny, w, sp, F0, 1, order, 1.0)
     tol = 1e-12 if precision == pic.PIC_FP64 else TOL32
     for c in range(9):
-        assert rel(Fg[c], Fo[c]) < tol, f"quantity {c}: {rel(Fg[c], Fo[c]):.2e}"
+        check(Fg[c], Fo[c], tol, f"quantity {c}")
 
 
 @pytest.mark.parametrize("nx,ny", [(4096, 8), (8, 2048), (1002, 24)])
@@ -96,4 +96,4 @@ def test_long_thin_grids_match_oracle(precision, nx, ny):
     Fo, po = oracle_run(nx, ny, w, sp, F0, 1, 2, 1.0)
     tol = 1e-12 if precision == pic.PIC_FP64 else TOL32
     for c in range(9):
-        assert rel(Fg[c], Fo[c]) < tol, f"quantity {c}: {rel(Fg[c], Fo[c]):.2e}"
+        check(Fg[c], Fo[c], tol, f"quantity {c}")

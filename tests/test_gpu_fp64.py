@@ -11,7 +11,7 @@ import pytest
 
 import paper_1412_2480_gb300 as pic
 from closed_forms import amplification
-from runners import periodic_pos_err, rel, run_gpu, run_oracle, workload
+from runners import check, check_rows, periodic_pos_err, rel, run_gpu, run_oracle, workload
 
 pytestmark = pytest.mark.gpu
 
@@ -27,13 +27,15 @@ def test_fp64_step_matches_oracle(order, steps):
     assert mom["macro_weight"] == pytest.approx(w, rel=1e-15)
     assert mom["step"] == steps
     for c in range(6):
-        assert rel(Fg[c], Fo[c]) < 1e-12, f"field {c}"
+        check(Fg[c], Fo[c], 1e-12, f"field {c}")
     for c in range(6, 9):
-        assert rel(Fg[c], Fo[c]) < 1e-12, f"current {c - 6}"
+        check(Fg[c], Fo[c], 1e-12, f"current {c - 6}")
+    for c in range(9, 12):
+        check(Fg[c], Fo[c], 1e-12, f"dB {c - 9}")
     for s in range(2):
         assert periodic_pos_err(pg[s][0], po[s][0], nx) < 1e-12
         assert periodic_pos_err(pg[s][1], po[s][1], ny) < 1e-12
-        assert rel(pg[s][2:], po[s][2:]) < 1e-12
+        check_rows(pg[s][2:], po[s][2:], 1e-12, f"species {s} momenta")
     assert mom["cg_iters_last"] == sim.last_cg_iters
 
 

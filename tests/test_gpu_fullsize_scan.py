@@ -13,7 +13,7 @@ import pytest
 import oracle
 import paper_1412_2480_gb300 as pic
 from paper_1412_2480_gb300 import inputs
-from runners import rel
+from runners import check, check_rows, rel
 
 pytestmark = pytest.mark.gpu
 TOL32 = 2e-5
@@ -74,8 +74,8 @@ def test_scan48_batch_members_match_oracle():
         w1.push_deposit()
         j_scale = np.linalg.norm(w1.J)
         for c in range(6):
-            assert rel(Fg[c], Fo[c]) < TOL32, f"simulation {k}, field {c}: {rel(Fg[c], Fo[c]):.2e}"
+            check(Fg[c], Fo[c], TOL32, f"simulation {k}, field {c}")
         assert np.linalg.norm(Fg[6:9] - Fo[6:9]) / j_scale < TOL32, f"simulation {k}, current"
         for s in range(2):
             o = np.stack([species[s].x, species[s].y, species[s].ux, species[s].uy, species[s].uz])
-            assert rel(np.sort(Pg[s][2:], axis=1), np.sort(o[2:], axis=1)) < TOL32, f"simulation {k}, species {s}"
+            check_rows(np.sort(Pg[s][2:], axis=1), np.sort(o[2:], axis=1), TOL32, f"simulation {k}, species {s}")

@@ -7,7 +7,7 @@ import numpy as np
 import pytest
 
 import paper_1412_2480_gb300 as pic
-from runners import match_particles, rel, run_gpu, run_oracle, workload
+from runners import check, check_rows, match_particles, rel, run_gpu, run_oracle, workload
 
 pytestmark = pytest.mark.gpu
 TOL32 = 2e-5
@@ -26,7 +26,7 @@ def test_nodal_step_matches_oracle(precision, order):
     Fs, ps, _ = run_oracle(nx, ny, w, sp, F0, 1, order, cg_rtol=1e-13)
     tol = 1e-12 if precision == pic.PIC_FP64 else TOL32
     for c in range(9):
-        assert rel(Fg[c], Fo[c]) < tol, f"quantity {c}: {rel(Fg[c], Fo[c]):.2e}"
+        check(Fg[c], Fo[c], tol, f"quantity {c}")
     for s in range(2):
         d = match_particles(pg[s], po[s], [nx, ny, 3.0, 3.0, 3.0])
         assert d < (1e-12 if precision == pic.PIC_FP64 else 1e-5), d

@@ -111,6 +111,83 @@ def test_boris_pure_electric_kick():
         np.testing.assert_allclose(u, u0 + qm * 0.37 * E, rtol=0, atol=1e-15)
 
 
+def _boris_by_rotation(qm, dt, E, B, u):
+    """One Boris step written as what its t/s construction amounts to: a half electric
+    kick, an exact rotation of u- about B by 2 atan(|h||B|/gamma-) (Rodrigues' formula,
+    sense of u x B for q > 0), where gamma- = sqrt(1 + |u-|^2) is taken AFTER the first
+    kick, then the second half kick. Independent of the oracle's cross products."""
+    h = 0.5 * qm * dt
+    um = u + h * E
+    gm = math.sqrt(1.0 + um @ um)
+    bn = np.linalg.norm(B)
+    if bn == 0.0:
+        return um + h * E
+    phi = 2.0 * math.atan(abs(h) * bn / gm)
+    return rodrigues(B, -math.copysign(1.0, qm) * phi, um) + h * E
+
+
+@pytest.mark.parametrize("qm", [1.0, -1.0])
+def test_boris_parallel_e_and_b_closed_form(qm):
+    # E parallel to B: the kicks act along B only, so u_par gains exactly (q/m) dt |E|
+    # per step, while u_perp keeps its length and turns by 2 atan(|h||B|/gamma-) with
+    # gamma- = sqrt(1 + |u^{n-1/2} + h E|^2). A gamma from u^{n-1/2} (before the first
+    # kick) gives a different angle at every step and fails this.
+    rng = np.random.default_rng(6)
+    bhat = np.array([0.36, -0.48, 0.8])
+    B = 1.7 * bhat
+    E = 0.9 * bhat
+    dt = 0.6
+    h = 0.5 * qm * dt
+    u = rng.standard_normal(3) * 3
+    upar = u @ bhat
+    uperp = u - upar * bhat
+    for n in range(1, 31):
+        gm = math.sqrt(1.0 + (upar + h * 0.9) ** 2 + uperp @ uperp)
+        uperp = rodrigues(bhat, -math.copysign(1.0, qm) * 2.0 * math.atan(abs(h) * 1.7 / gm), uperp)
+        upar = upar + 2.0 * h * 0.9
+        u = oracle.boris(qm, dt, E[None, :], B[None, :], u[None, :])[0]
+        assert abs(u @ bhat - upar) < 1e-12 * max(1.0, abs(upar))
+        np.testing.assert_allclose(u - (u @ bhat) * bhat, uperp, rtol=0, atol=1e-12 * np.linalg.norm(uperp))
+
+
+@pytest.mark.parametrize("qm", [1.0, -1.0])
+def test_boris_crossed_e_and_b_against_rotation_form(qm):
+    # E perpendicular (and oblique) to B, relativistic momenta: every step equals the
+    # kick - exact rotation - kick sequence written independently above. Applying the
+    # second kick before the rotation, or one full kick, or gamma of u^{n-1/2}, all
+    # fail here because the kick does not commute with the rotation.
+    rng = np.random.default_rng(7)
+    dt = 0.45
+    for trial in range(20):
+        B = rng.standard_normal(3) * 2
+        E = np.cross(B, rng.standard_normal(3)) if trial % 2 == 0 else rng.standard_normal(3)
+        u = rng.standard_normal(3) * 4
+        for _ in range(25):
+            ref = _boris_by_rotation(qm, dt, E, B, u)
+            u = oracle.boris(qm, dt, E[None, :], B[None, :], u[None, :])[0]
+            np.testing.assert_allclose(u, ref, rtol=0, atol=2e-13 * max(1.0, np.linalg.norm(ref)))
+
+
+def test_boris_exb_drift():
+    # Uniform E perpendicular to B with |E| << |B|: averaged over whole gyrations the
+    # velocity u/gamma approaches the drift E x B / |B|^2 for either charge sign
+    # (non-relativistic limit of the exact motion).
+    B = np.array([0.0, 0.0, 1.0])
+    E = np.array([0.0, 2e-3, 0.0])
+    dt = 0.05
+    vd = np.cross(E, B) / (B @ B)
+    for qm in (1.0, -1.0):
+        u = np.array([[0.0, 0.0, 0.0]])
+        nper = int(round(2 * math.pi / dt))  # one gyration per 2 pi (gamma = 1 + O(1e-6))
+        vs = []
+        for _ in range(40 * nper):
+            u = oracle.boris(qm, dt, E[None, :], B[None, :], u)
+            g = math.sqrt(1.0 + (u[0] @ u[0]))
+            vs.append(u[0] / g)
+        vbar = np.mean(vs, axis=0)
+        np.testing.assert_allclose(vbar, vd, rtol=0, atol=2e-2 * np.linalg.norm(vd))
+
+
 def _rho_scipy(p, nx, ny, q, x, y):
     W = bspline(p)
     rho = np.zeros((ny, nx))
