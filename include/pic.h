@@ -301,7 +301,9 @@ PIC_API int pic_particles(pic_sim* s, int32_t species, double* out5xn, int64_t n
  * that has no access to the CUDA allocation calls at all. pic_field_solve_noalloc gives
  * them the field solve of pic_step without any allocation: it builds the right-hand side
  * b of Eq. (7) from the fields F and the current J, then runs the same Jacobi-PCG, from a
- * zero initial guess, until ||r||_2 <= cg_rtol ||b||_2, and writes dB.
+ * zero initial guess, until ||r||_2 <= cg_rtol ||b||_2, and writes dB. It solves the
+ * periodic operator only (the grid is periodic in x and y; a handle with PIC_BC_WALLS
+ * solves a different operator), with dt = cfl * dx as in pic_params.
  *
  * Its scratch (three solver vectors of 3*nx*ny FP64 values, reduction partials, solver
  * state) is a fixed array in the library's device memory, sized for
@@ -312,19 +314,25 @@ PIC_API int pic_particles(pic_sim* s, int32_t species, double* out5xn, int64_t n
  *
  *   nx, ny          grid size; nx, ny >= 8 and nx*ny <= PIC_NOALLOC_MAX_CELLS
  *   dx, dy, cfl, theta, cg_rtol, cg_max_iter   as in pic_params
- *   F               device pointer, 6*nx*ny FP64: Ex, Ey, Ez, Bx, By, Bz (the layout of
+ *   F               device pointer (memory of the current device, or managed memory),
+ *                   6*nx*ny FP64: Ex, Ey, Ez, Bx, By, Bz (the layout of
  *                   pic_fields, component-major, index j*nx + i)
  *   J               device pointer, 3*nx*ny FP64: Jx, Jy, Jz
  *   dB              device pointer, 3*nx*ny FP64, written: dBx, dBy, dBz
  *   iters, rel_resid  optional outputs (NULL allowed): PCG iterations and ||r||/||b||
  *   stream          cudaStream_t as void* (NULL = the legacy default stream)
  *   errbuf, errlen  optional caller-owned buffer for a message (NULL allowed)
- * Returns PIC_OK, PIC_EINVAL (sizes beyond the maximum, bad parameters, or a pointer
- * that is not device memory), PIC_ECUDA, or PIC_ECG_NOCONV.
+ * The library cannot see the lengths of F, J and dB: they must hold at least the counts
+ * above (the Python binding checks them). Returns PIC_OK, PIC_EINVAL (sizes beyond the
+ * maximum, bad parameters, or a pointer that is not memory of the current device),
+ * PIC_ECUDA, or PIC_ECG_NOCONV.
  *
  * The first call on a device does a one-time set-up on that device (it looks up the
  * device address of the scratch array); make that first call before any stream capture
- * on the device. All calls on a device share the one array and each starts by clearing
+ * on the device. With CUDA's lazy module loading (the default since CUDA 12.2) that
+ * set-up is also when the array is reserved and the solver's kernels are loaded, so it
+ * can itself need device memory: make the first call before the caller's allocator
+ * takes the GPU's memory. Later calls need none. All calls on a device share the one array and each starts by clearing
  * what must start at zero: calls that overlap on the GPU (on different streams or from
  * different host threads) race and produce wrong results, so serialise them. */
 #define PIC_NOALLOC_MAX_CELLS 65536

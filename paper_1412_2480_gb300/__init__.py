@@ -354,6 +354,21 @@ def pic_field_solve_noalloc(nx, ny, dx, dy, cfl, theta, cg_rtol, cg_max_iter, F,
                                               C.c_void_p, C.c_char_p, C.c_size_t]
         L.pic_field_solve_noalloc.restype = C.c_int
         L._noalloc_typed = True
+    # The C ABI sees bare pointers, so the lengths and the device are checked here:
+    # an undersized or foreign-device buffer would be read or written out of bounds.
+    try:
+        import torch
+        cur = torch.cuda.current_device()
+    except Exception:  # no usable CUDA: the library call reports it
+        torch, cur = None, None
+    for name, a, n in (("F", F, 6), ("J", J, 3), ("dB", dB, 3)):
+        on_dev = (torch is not None and isinstance(a, torch.Tensor) and a.is_cuda
+                  and a.device.index == cur)
+        if not on_dev:
+            raise PicError(PIC_EINVAL, f"{name} must be a CUDA tensor on the current device")
+        if _len(a) != n * int(nx) * int(ny):
+            raise PicError(PIC_EINVAL, f"{name} must hold {n}*nx*ny = {n * int(nx) * int(ny)} "
+                                       f"values, not {_len(a)}")
     it, rr = C.c_int32(0), C.c_double(0.0)
     msg = C.create_string_buffer(256)
     sp = getattr(stream, "cuda_stream", stream)

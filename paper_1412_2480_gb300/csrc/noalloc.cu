@@ -67,20 +67,24 @@ extern "C" PIC_API int pic_field_solve_noalloc(int32_t nx, int32_t ny, double dx
         set_err(errbuf, errlen, "invalid dx, dy, cfl, theta, cg_rtol or cg_max_iter");
         return PIC_EINVAL;
     }
-    const void* ptrs[3] = {F, J, dB};
-    for (const void* q : ptrs) {
-        cudaPointerAttributes at{};
-        if (!q || cudaPointerGetAttributes(&at, q) != cudaSuccess ||
-            (at.type != cudaMemoryTypeDevice && at.type != cudaMemoryTypeManaged)) {
-            cudaGetLastError();
-            set_err(errbuf, errlen, "F, J and dB must be device (or managed) pointers");
-            return PIC_EINVAL;
-        }
-    }
     int dev = 0;
     if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= kMaxDevices) {
         set_err(errbuf, errlen, "no usable CUDA device");
         return PIC_ECUDA;
+    }
+    // device memory of the current device, or managed memory; memory of another GPU
+    // would be read across the interconnect (or fault without peer access)
+    const void* ptrs[3] = {F, J, dB};
+    for (const void* q : ptrs) {
+        cudaPointerAttributes at{};
+        const bool ok = q && cudaPointerGetAttributes(&at, q) == cudaSuccess &&
+                        (at.type == cudaMemoryTypeManaged ||
+                         (at.type == cudaMemoryTypeDevice && at.device == dev));
+        if (!ok) {
+            cudaGetLastError();
+            set_err(errbuf, errlen, "F, J and dB must be device memory of the current device (or managed)");
+            return PIC_EINVAL;
+        }
     }
     unsigned char* base = nullptr;
     {
