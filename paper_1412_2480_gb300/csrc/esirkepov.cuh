@@ -6,6 +6,15 @@
 
 namespace pic {
 
+// 1/sqrt(x) and 1/x inside the push. FP32: the hardware approximations (MUFU; a few ulp,
+// far below the FP32 parity tolerance, and one fixed instruction, so every kernel that
+// pushes a particle still gives the same bits) instead of the correctly rounded sequences,
+// which cost ten or more instructions each. FP64: the correctly rounded operations.
+__device__ __forceinline__ float rsqrt_push(float x) { return rsqrtf(x); }
+__device__ __forceinline__ double rsqrt_push(double x) { return 1.0 / sqrt(x); }
+__device__ __forceinline__ float rcp_push(float x) { return __fdividef(1.0f, x); }
+__device__ __forceinline__ double rcp_push(double x) { return 1.0 / x; }
+
 // Relativistic Buneman-Boris push (standard scheme; the paper specifies none), c = 1:
 // half electric kick, rotation by t = h B / gamma(u-), s = 2t / (1 + t^2), half kick.
 // h = (q/m) dt / 2.
@@ -14,9 +23,9 @@ namespace pic {
 template <typename R>
 __device__ __forceinline__ void boris(R h, const R E[3], const R B[3], R u[3]) {
     R um0 = xfma(h, E[0], u[0]), um1 = xfma(h, E[1], u[1]), um2 = xfma(h, E[2], u[2]);
-    const R ig = R(1) / sqrt(xfma(um2, um2, xfma(um1, um1, xfma(um0, um0, R(1)))));
+    const R ig = rsqrt_push(xfma(um2, um2, xfma(um1, um1, xfma(um0, um0, R(1)))));
     const R t0 = xmul(xmul(h, B[0]), ig), t1 = xmul(xmul(h, B[1]), ig), t2 = xmul(xmul(h, B[2]), ig);
-    const R f = R(2) / xfma(t2, t2, xfma(t1, t1, xfma(t0, t0, R(1))));
+    const R f = xmul(R(2), rcp_push(xfma(t2, t2, xfma(t1, t1, xfma(t0, t0, R(1))))));
     const R s0 = xmul(f, t0), s1 = xmul(f, t1), s2 = xmul(f, t2);
     const R p0 = xadd(um0, xfma(um1, t2, -xmul(um2, t1)));
     const R p1 = xadd(um1, xfma(um2, t0, -xmul(um0, t2)));
@@ -29,15 +38,15 @@ __device__ __forceinline__ void boris(R h, const R E[3], const R B[3], R u[3]) {
     u[2] = xfma(h, E[2], um2);
 }
 
-// Weight of node k (0..P+1) of a (P+2)-wide window, for a particle whose P+1 weights
-// start `sh` (0 or 1) nodes into the window.
+// Weight of node k (0..P+1, a compile-time constant once unrolled) of a (P+2)-wide
+// window, for a particle whose P+1 weights start `sh` nodes into the window. For every
+// move below one cell the shape bases before and after differ by at most one node, so
+// sh is 0 or 1 and each window node is a single select.
 template <int P, typename R>
-__device__ __forceinline__ R window_weight(const R w[P + 1], int sh, int k) {
-    const int m = k - sh;
-    R v = R(0);
-#pragma unroll
-    for (int t = 0; t <= P; t++) v = (m == t) ? w[t] : v;
-    return v;
+__device__ __forceinline__ R window_weight(const R w[P + 1], bool sh, int k) {
+    const R at0 = k <= P ? w[k <= P ? k : 0] : R(0);     // sh = 0
+    const R at1 = k >= 1 ? w[k >= 1 ? k - 1 : 0] : R(0);  // sh = 1
+    return sh ? at1 : at0;
 }
 
 // Density-decomposition (Esirkepov) current of one particle moving from cell/fraction
@@ -107,7 +116,7 @@ __device__ __forceinline__ void esirkepov(int i0, R f0x, int j0, R f0y, int i1, 
     shape_nodes<P, R>(j0, f0y, b0y, s0y);
     shape_nodes<P, R>(j1, f1y, b1y, s1y);
     const int ox = min(b0x, b1x), oy = min(b0y, b1y);
-    const int h0x = b0x - ox, h1x = b1x - ox, h0y = b0y - oy, h1y = b1y - oy;
+    const bool h0x = b0x != ox, h1x = b1x != ox, h0y = b0y != oy, h1y = b1y != oy;
     R S0x[P + 2], DSx[P + 2], S0y[P + 2], DSy[P + 2];
 #pragma unroll
     for (int k = 0; k < P + 2; k++) {

@@ -375,14 +375,14 @@ __device__ __forceinline__ bool push_one(const Mem& M, const PushConst& K, int i
         gather_fields<P>(M, bx0, wx0, bxh, wxh, by0, wy0, byh, wyh, E, B);
     }
     // (the rounding of the update is explicit: xmul, xfma, ... in pic_internal.cuh)
-    const float g_old = sqrtf(xfma(u[2], u[2], xfma(u[1], u[1], xfma(u[0], u[0], 1.f))));
+    const float g2_old = xfma(u[2], u[2], xfma(u[1], u[1], xfma(u[0], u[0], 1.f)));
     boris<float>(K.h, E, B, u);
     const float ig = rsqrtf(xfma(u[2], u[2], xfma(u[1], u[1], xfma(u[0], u[0], 1.f))));
     const float dX = xmul(xmul(K.dt_idx, u[0]), ig), dY = xmul(xmul(K.dt_idy, u[1]), ig);
     di = 0;
     dj = 0;
     if (!(fabsf(dX) < 1.f && fabsf(dY) < 1.f)) return false;
-    ek += g_old + 1.f / ig - 2.f;
+    ek += xmul(g2_old, rsqrtf(g2_old)) + rcp_push(ig) - 2.f;  // gamma before + gamma after - 2
     float x1 = xadd(ox, dX), y1 = xadd(oy, dY);
     if (x1 >= 1.f) { x1 = xsub(x1, 1.f); di = 1; }
     else if (x1 < 0.f) { x1 = xadd(x1, 1.f); di = -1; if (x1 >= 1.f) { x1 = 0.f; di = 0; } }
@@ -554,15 +554,20 @@ k_push_tile(const MixedArgs a) {
             const PushConst K = push_const(G, s);
             const int total = s_start[s][kSegs];
             const long long own = G.bin_off + ((long long)lt * 2 + s) * stride;
+            const int st1 = s_start[s][1];  // end of the stayer segment
             for (int c0 = warp * 32; c0 < total; c0 += nwarp * 32) {
                 const int v = c0 + lane;
                 const bool valid = v < total;
                 int dest = -1, cnew = 0;
                 float ox = 0.f, oy = 0.f, u[3] = {0.f, 0.f, 0.f};
                 if (valid) {
+                    // segment of slot v: the stayers, else one of the outboxes addressed here
                     int seg = 0;
+                    if (v >= st1) {
+                        seg = 1;
 #pragma unroll
-                    for (int k = 1; k < kSegs; k++) seg += (v >= s_start[s][k]) ? 1 : 0;
+                        for (int k = 2; k < kSegs; k++) seg += (v >= s_start[s][k]) ? 1 : 0;
+                    }
                     const long long e = s_base[s][seg] + (v - s_start[s][seg]);
                     int c;
                     get(cur, e, c, ox, oy, u);

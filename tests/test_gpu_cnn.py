@@ -295,7 +295,7 @@ def test_learned_warm_start_at_full_size_matches_oracle(trained):
     for k in range(6):
         check(Fg[k], Fo[k], tol, f"field {k}")
     assert np.linalg.norm(Fg[6:9] - Fo[6:9]) / np.linalg.norm(Jp[6:9]) < tol
-    for k in range(3):  # element-wise against one species' largest current
-        check(Fg[6 + k], Fo[6 + k], tol, f"current {k}", scale=np.abs(Jp[6 + k]).max())
+    for k in range(3):  # element-wise against one species' largest current component
+        check(Fg[6 + k], Fo[6 + k], tol, f"current {k}", scale=np.abs(Jp[6:9]).max())
     for s in range(2):
         check_rows(np.sort(Pg[s][2:], axis=1), np.sort(po[s][2:], axis=1), tol, f"species {s} momenta")

@@ -69,8 +69,11 @@ def test_noalloc_rejects_oversize_and_host_pointers():
     J = torch.zeros(3 * n * n, dtype=torch.float64, device="cuda")
     dB = torch.zeros(3 * n * n, dtype=torch.float64, device="cuda")
     big = 512  # 512 x 256 cells exceeds PIC_NOALLOC_MAX_CELLS
+    Fb = torch.zeros(6 * big * 256, dtype=torch.float64, device="cuda")
+    Jb = torch.zeros(3 * big * 256, dtype=torch.float64, device="cuda")
+    dBb = torch.zeros(3 * big * 256, dtype=torch.float64, device="cuda")
     with pytest.raises(pic.PicError) as e:
-        pic.pic_field_solve_noalloc(big, 256, 1.0, 1.0, 1.0, 0.5, 1e-10, 50, F, J, dB)
+        pic.pic_field_solve_noalloc(big, 256, 1.0, 1.0, 1.0, 0.5, 1e-10, 50, Fb, Jb, dBb)
     assert e.value.code == pic.PIC_EINVAL and "PIC_NOALLOC_MAX_CELLS" in str(e.value)
     with pytest.raises(pic.PicError) as e:
         pic.pic_field_solve_noalloc(n, n, 1.0, 1.0, 1.0, 0.5, 1e-10, 50, F.cpu(), J, dB)
