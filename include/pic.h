@@ -58,6 +58,7 @@ extern "C" {
 #define PIC_ECG_NOCONV (-4)  /* PCG reached cg_max_iter before cg_rtol */
 #define PIC_ECFL (-5)        /* a particle moved one cell or more in one step */
 #define PIC_ENAN (-6)        /* a non-finite particle momentum or position appeared */
+#define PIC_ETIMEOUT (-7)    /* a bounded wait inside a kernel gave up (see pic_set_wait_limit) */
 #define PIC_ESTATE (-8)      /* call not valid in the handle's current state */
 
 /* ---- precision of the particle half (the field solve is always FP64) ----
@@ -368,8 +369,8 @@ PIC_API int pic_field_solve_noalloc(int32_t nx, int32_t ny, double dx, double dy
  *
  * Image arrays (in, out, target) hold nimg images of [3][ny][nx] FP32 values, host or
  * device; nx*ny must be a multiple of 128. Every call synchronises the network's own
- * stream. Errors: PIC_EINVAL (sizes, NULL arrays), PIC_ENOMEM, PIC_ECUDA (including a
- * tensor-core completion wait that timed out); pic_cnn_last_error gives the message. */
+ * stream. Errors: PIC_EINVAL (sizes, NULL arrays), PIC_ENOMEM, PIC_ECUDA, PIC_ETIMEOUT (a
+ * tensor-core completion wait ran out); pic_cnn_last_error gives the message. */
 typedef struct pic_cnn pic_cnn;
 #define PIC_CNN_NPARAMS 20259
 PIC_API int pic_cnn_create(pic_cnn** out); /* all parameters zero */
@@ -443,6 +444,24 @@ PIC_API int pic_restore(pic_sim* s, const char* path);
 /* Message of the last failure on this handle (or of the last failed pic_init when s
  * is NULL). The string stays valid until the next call on the handle. */
 PIC_API const char* pic_last_error(const pic_sim* s);
+
+/* ---- bounded device-side waits -----------------------------------------------------
+ * The paper has no counterpart: these are services of this library for testing its
+ * failure paths. Every wait inside the library's kernels is bounded. The grid barriers
+ * of the cooperative PCG (a persistent kernel whose blocks meet through global memory)
+ * poll at most 2^22 times; the tensor-core completion waits of the network's kernels
+ * at most 2^24 times. A wait that runs out makes the kernel record the failure and
+ * return (a tensor-core wait that gave up first waits, with the default bound, for the
+ * matrix operations it has in flight, and only then frees its tensor memory); the call
+ * reports PIC_ETIMEOUT and the device stays usable.
+ *
+ * These calls lower the bound so that a test can make the waits run out on purpose:
+ * spins >= 1 polls per wait, 0 restores the default. pic_set_wait_limit applies to the
+ * handle's cooperative solve (MIXED32) from the next step on; a handle that solves
+ * without it is unaffected. pic_cnn_set_wait_limit applies to the network's next calls
+ * (forward, gradient, training). Both return PIC_OK or PIC_EINVAL (spins < 0). */
+PIC_API int pic_set_wait_limit(pic_sim* s, int32_t spins);
+PIC_API int pic_cnn_set_wait_limit(pic_cnn* c, int32_t spins);
 
 /* Release the handle and all its device memory. NULL is a no-op. */
 PIC_API void pic_free(pic_sim* s);

@@ -27,6 +27,7 @@ PIC_ECUDA = -3
 PIC_ECG_NOCONV = -4
 PIC_ECFL = -5
 PIC_ENAN = -6
+PIC_ETIMEOUT = -7
 PIC_ESTATE = -8
 PIC_FP64 = 0
 PIC_MIXED32 = 1
@@ -54,7 +55,8 @@ EXPORTED = ("pic_params_default", "pic_init", "pic_init_batch", "pic_select", "p
             "pic_cnn_create", "pic_cnn_free", "pic_cnn_last_error", "pic_cnn_set_params",
             "pic_cnn_get_params", "pic_cnn_forward", "pic_cnn_gradient", "pic_cnn_train_step",
             "pic_cnn_stencil", "pic_set_cnn", "pic_tc_gemm_bf16", "pic_conservation", "pic_save",
-            "pic_restore", "pic_spectrum", "pic_resonance_ky")
+            "pic_restore", "pic_spectrum", "pic_resonance_ky", "pic_set_wait_limit",
+            "pic_cnn_set_wait_limit")
 
 
 class pic_params(C.Structure):
@@ -142,6 +144,10 @@ def lib():
             for name in ("pic_conservation", "pic_save", "pic_restore", "pic_spectrum",
                          "pic_resonance_ky"):
                 getattr(L, name).restype = C.c_int
+            L.pic_set_wait_limit.argtypes = [vp, C.c_int32]
+            L.pic_set_wait_limit.restype = C.c_int
+            L.pic_cnn_set_wait_limit.argtypes = [vp, C.c_int32]
+            L.pic_cnn_set_wait_limit.restype = C.c_int
             L.pic_cnn_stencil.argtypes = [vp, vp, C.c_int64]
             L.pic_tc_gemm_bf16.argtypes = [C.c_int32, C.c_int32, C.c_int32, vp, vp, vp]
             for name in ("pic_cnn_create", "pic_cnn_set_params", "pic_cnn_get_params", "pic_cnn_forward",
@@ -218,6 +224,12 @@ def pic_init_batch(params) -> int:
 
 def pic_select(h, k) -> None:
     _check(lib().pic_select(h, int(k)), h)
+
+
+def pic_set_wait_limit(h, spins) -> None:
+    """Polls a grid-barrier wait of the handle's cooperative solve makes before it gives up
+    (the step then fails with PIC_ETIMEOUT); 0 restores the default (include/pic.h)."""
+    _check(lib().pic_set_wait_limit(h, int(spins)), h)
 
 
 def pic_batch_size(h) -> int:
@@ -413,6 +425,11 @@ def pic_cnn_create() -> int:
 
 def pic_cnn_free(c) -> None:
     lib().pic_cnn_free(c)
+
+
+def pic_cnn_set_wait_limit(c, spins) -> None:
+    """Polls of the network kernels' tensor-core completion waits (0: the default)."""
+    _ccheck(lib().pic_cnn_set_wait_limit(c, int(spins)), c)
 
 
 def pic_cnn_set_params(c, p) -> None:

@@ -73,6 +73,7 @@ struct pic_sim {
     // MIXED32 mixed-precision PCG: FP64 right-hand side and FP32 inner vectors
     double* bvec = nullptr;
     float *r32 = nullptr, *p32 = nullptr, *q32 = nullptr, *e32 = nullptr;
+    float *r32b = nullptr, *z32 = nullptr;  // second inner residual buffer, z = M r
     // learned warm start: the network's forward weights and its buffers
     bool learned = false;
     bool has_cnn = false;
@@ -188,6 +189,19 @@ void fill_grid(const pic_params& p, GridDev& G) {
     G.cx = G.a / (p.dx * p.dx);
     G.cy = G.a / (p.dy * p.dy);
     G.c0 = 1.0 + 2.0 * G.cx + 2.0 * G.cy;
+    {
+        // Chebyshev-optimal degree-1 preconditioner p(A) on A's spectrum [l1, l2] =
+        // [c0 - 2cx - 2cy, c0 + 2cx + 2cy] = [1, 1 + 4cx + 4cy] (Gershgorin; the periodic
+        // and the wall operators alike): with d = (l1 + l2)/2 = c0 and hw = (l2 - l1)/2,
+        // p(lambda) = 2 (2d - lambda) / (2 d^2 - hw^2), so that 1 - lambda p(lambda) is the
+        // scaled Chebyshev polynomial T2 (at most 1 / T2(d / hw) in magnitude); p(A) =
+        // (2 / D) (c0 I + cx (E + W) + cy (N + S)), D = 2 c0^2 - hw^2.
+        const double hw = 2.0 * (G.cx + G.cy);
+        const double D = 2.0 * G.c0 * G.c0 - hw * hw;
+        G.pc0 = 2.0 * G.c0 / D;
+        G.pcx = 2.0 * G.cx / D;
+        G.pcy = 2.0 * G.cy / D;
+    }
     // omega_pe^2 = 4 pi n q^2 / (m gamma0), n = ppc/(dx dy), q = m = w (Sec. 4 definition)
     const double wpe = 1.0 / p.skin_depth;
     G.w = wpe * wpe * p.gamma0 * p.dx * p.dy / (4.0 * kPi * p.ppc);
@@ -202,6 +216,16 @@ void fill_grid(const pic_params& p, GridDev& G) {
                                           1.0 / (p.dx * p.dy));
     G.jscale = std::ldexp(1.0, 40) / u;
     G.jinv = 1.0 / G.jscale;
+    const double area = G.dx * G.dy;
+    for (int s = 0; s < 2; s++) {
+        G.pk_h[s] = (float)(0.5 * G.qm[s] * G.dt);
+        G.pk_fx[s] = (float)(G.qw[s] * G.dx / (G.dt * area));
+        G.pk_fy[s] = (float)(G.qw[s] * G.dy / (G.dt * area));
+        G.pk_fz[s] = (float)(G.qw[s] / area);
+    }
+    G.pk_dtx = (float)(G.dt * G.idx);
+    G.pk_dty = (float)(G.dt * G.idy);
+    G.js40 = (float)(G.jscale * std::ldexp(1.0, -40));
     G.rtol = p.cg_rtol;
     G.maxit = p.cg_max_iter;
     G.warm = p.warm_start == PIC_WS_PREV ? 1 : (p.warm_start == PIC_WS_LEARNED ? 2 : 0);
@@ -245,6 +269,8 @@ FieldArgs field_args(pic_sim* s, int use_cond, cudaGraphConditionalHandle cond) 
     a.p32 = s->p32;
     a.q32 = s->q32;
     a.e32 = s->e32;
+    a.r32b = s->r32b;
+    a.z32 = s->z32;
     return a;
 }
 
@@ -687,7 +713,7 @@ __global__ void k_fix_to_f64(long long n, const long long* a, double jinv, doubl
 int device_errors(pic_sim* s, const DevStatus& hs) {
     int rc = PIC_OK;
     if (hs.sync_timeout != s->seen_sync) {
-        rc = fail(s, PIC_ECUDA, "a grid barrier of the cooperative PCG timed out");
+        rc = fail(s, PIC_ETIMEOUT, "a grid barrier of the cooperative PCG timed out");
     } else if (hs.cg_noconv != s->seen_noconv) {
         rc = fail(s, PIC_ECG_NOCONV, "PCG reached cg_max_iter before cg_rtol");
     } else if (hs.nan_count != s->seen_nan) {
@@ -790,6 +816,8 @@ int init_handle(const pic_params* prm, int n, pic_sim** out) {
         A(dalloc(&s->p32, n3));
         A(dalloc(&s->q32, n3));
         A(dalloc(&s->e32, n3));
+        A(dalloc(&s->r32b, n3));
+        A(dalloc(&s->z32, n3));
         A(dalloc(&s->F32, 6 * s->ntot));
     }
     for (int k = 0; k < n; k++) s->any_nodal = s->any_nodal || (prm[k].flags & PIC_GATHER_NODAL);
@@ -1136,6 +1164,18 @@ int step_chunk(pic_sim* s, int32_t n) {
 }
 
 }  // namespace
+
+int pic_set_wait_limit(pic_sim* s, int32_t spins) {
+    if (!s) return PIC_EINVAL;
+    cudaSetDevice(s->device);
+    if (spins < 0) return fail(s, PIC_EINVAL, "spins must be >= 0");
+    DevStatus hs{};
+    CK(cudaMemcpyAsync(&hs, s->st, sizeof hs, cudaMemcpyDeviceToHost, s->stream));
+    CK(cudaStreamSynchronize(s->stream));
+    hs.spin_limit = (unsigned int)spins;
+    CK(cudaMemcpyAsync(s->st, &hs, sizeof hs, cudaMemcpyHostToDevice, s->stream));
+    return finish_call(s);
+}
 
 int pic_step(pic_sim* s, int32_t n) {
     if (!s) return PIC_EINVAL;
@@ -1557,7 +1597,7 @@ void pic_free(pic_sim* s) {
     coop_free(&s->coop);
     void* ptrs[] = {s->dgrids, s->dblk_grid, s->F, s->J64, s->Jfix, s->F32, s->Fn, s->x, s->r, s->p, s->q,
                     s->part, s->cg, s->done, s->st, s->tmp, s->dsegs, s->dblk_seg[0], s->dblk_seg[1],
-                    s->bvec, s->r32, s->p32, s->q32, s->e32};
+                    s->bvec, s->r32, s->p32, s->q32, s->e32, s->r32b, s->z32};
     for (void* p : ptrs) dfree(p);
     for (int sp = 0; sp < 2; sp++)
         for (int a = 0; a < 5; a++) dfree(s->pa[sp][a]);

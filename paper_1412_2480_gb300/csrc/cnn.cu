@@ -135,7 +135,8 @@ __global__ void __launch_bounds__(kTile) k_conv(const ConvArgs a) {
                          idesc, s > 0 ? 1u : 0u);
         tc::mma_commit(&bar);
     }
-    const bool ok = __syncthreads_and(tc::mbar_wait(&bar, 0) ? 1 : 0) != 0;
+    // err[1]: the wait's poll limit (0: the default bound)
+    const bool ok = __syncthreads_and(tc::mbar_wait_lim(&bar, 0, __ldg(a.err + 1)) ? 1 : 0) != 0;
     tc::fence_after_sync();
     if (ok) {
         float acc[NOUT];
@@ -169,6 +170,7 @@ __global__ void __launch_bounds__(kTile) k_conv(const ConvArgs a) {
         }
     } else if (tid == 0) {
         atomicExch(a.err, 1u);
+        tc::mbar_wait(&bar, 0);  // drain: the MMA still reads shared and writes tensor memory
     }
     tc::fence_before_sync();
     __syncthreads();
@@ -215,11 +217,15 @@ __global__ void __launch_bounds__(128) k_wgrad(const WgradArgs a) {
     const uint32_t tmem = s_tmem;
     const long long c0 = (long long)blockIdx.x * a.chunks_per_cta;
     const long long c1 = min(a.nchunks, c0 + a.chunks_per_cta);
+    const uint32_t lim = __ldg(a.err + 1);  // the waits' poll limit (0: the default bound)
     bool ok = true;
     for (long long c = c0; c < c1; c++) {
         const int q = (int)(c - c0);
-        if (q > 0) ok = __syncthreads_and((ok && tc::mbar_wait(&bar, (uint32_t)((q - 1) & 1))) ? 1 : 0) != 0;
-        if (!ok) break;
+        if (q > 0) ok = __syncthreads_and((ok && tc::mbar_wait_lim(&bar, (uint32_t)((q - 1) & 1), lim)) ? 1 : 0) != 0;
+        if (!ok) {  // drain the round in flight before the shared and tensor memory go
+            if (tid == 0) tc::mbar_wait(&bar, (uint32_t)((q - 1) & 1));
+            break;
+        }
         const long long pix0 = c * kChunk;
         const CnnImg im = a.imgs[a.tile_img[pix0 / kTile]];
         for (int idx = tid; idx < kChunk * 9; idx += 128) {
@@ -262,7 +268,10 @@ __global__ void __launch_bounds__(128) k_wgrad(const WgradArgs a) {
         }
     }
     const int nq = (int)(c1 - c0);
-    if (ok && nq > 0) ok = __syncthreads_and(tc::mbar_wait(&bar, (uint32_t)((nq - 1) & 1)) ? 1 : 0) != 0;
+    if (ok && nq > 0) {
+        ok = __syncthreads_and(tc::mbar_wait_lim(&bar, (uint32_t)((nq - 1) & 1), lim) ? 1 : 0) != 0;
+        if (!ok && tid == 0) tc::mbar_wait(&bar, (uint32_t)((nq - 1) & 1));  // drain
+    }
     tc::fence_after_sync();
     if (ok && nq > 0) {
 #pragma unroll 1
@@ -516,7 +525,7 @@ __global__ void __launch_bounds__(128) k_tc_gemm(int N, int K, const uint16_t* _
                          idesc, s > 0 ? 1u : 0u);
         tc::mma_commit(&bar);
     }
-    const bool ok = __syncthreads_and(tc::mbar_wait(&bar, 0) ? 1 : 0) != 0;
+    const bool ok = __syncthreads_and(tc::mbar_wait_lim(&bar, 0, __ldg(err + 1)) ? 1 : 0) != 0;
     tc::fence_after_sync();
     if (ok) {
         float* drow = D + ((long long)blockIdx.x * 128 + tid) * N;
@@ -528,6 +537,7 @@ __global__ void __launch_bounds__(128) k_tc_gemm(int N, int K, const uint16_t* _
         }
     } else if (tid == 0) {
         atomicExch(err, 1u);
+        tc::mbar_wait(&bar, 0);  // drain
     }
     tc::fence_before_sync();
     __syncthreads();
@@ -786,7 +796,11 @@ int check_err(pic_cnn* c) {
     unsigned int h = 0;
     CCK(cudaMemcpyAsync(&h, c->d_err, sizeof h, cudaMemcpyDeviceToHost, c->stream));
     CCK(cudaStreamSynchronize(c->stream));
-    if (h) return cfail(c, PIC_ECUDA, "a tensor-core completion wait timed out");
+    if (h) {
+        CCK(cudaMemsetAsync(c->d_err, 0, sizeof(unsigned int), c->stream));  // reported once
+        CCK(cudaStreamSynchronize(c->stream));
+        return cfail(c, PIC_ETIMEOUT, "a tensor-core completion wait timed out");
+    }
     return PIC_OK;
 }
 
@@ -842,11 +856,11 @@ int pic_cnn_create(pic_cnn** out) {
         if (e == cudaSuccess && L) e = dalloc(&c->wd[L], (size_t)kL[L].cin * 9 * kL[L].cout_pad);
     }
     if (e == cudaSuccess) e = dalloc(&c->d_loss, 1);
-    if (e == cudaSuccess) e = dalloc(&c->d_err, 1);
+    if (e == cudaSuccess) e = dalloc(&c->d_err, 2);  // [0] a wait ran out, [1] the waits' poll limit
     if (e == cudaSuccess) e = cudaMemset(c->params, 0, kNParams * sizeof(float));
     if (e == cudaSuccess) e = cudaMemset(c->m1, 0, kNParams * sizeof(float));
     if (e == cudaSuccess) e = cudaMemset(c->m2, 0, kNParams * sizeof(float));
-    if (e == cudaSuccess) e = cudaMemset(c->d_err, 0, sizeof(unsigned int));
+    if (e == cudaSuccess) e = cudaMemset(c->d_err, 0, 2 * sizeof(unsigned int));
     if (e == cudaSuccess) e = set_smem_once();
     if (e == cudaSuccess && pack(c) != PIC_OK) e = cudaErrorUnknown;
     if (e == cudaSuccess) e = cudaStreamSynchronize(c->stream);
@@ -967,13 +981,13 @@ int pic_tc_gemm_bf16(int32_t M, int32_t N, int32_t K, const uint16_t* A, const u
     unsigned int* err = nullptr;
     uint16_t *dA = nullptr, *dB = nullptr;
     float* dD = nullptr;
-    CCK(dalloc(&err, 1));
+    CCK(dalloc(&err, 2));
     CCK(dalloc(&dA, (size_t)M * K));
     CCK(dalloc(&dB, (size_t)N * K));
     CCK(dalloc(&dD, (size_t)M * N));
     CCK(cudaMemcpy(dA, A, (size_t)M * K * 2, cudaMemcpyDefault));
     CCK(cudaMemcpy(dB, B, (size_t)N * K * 2, cudaMemcpyDefault));
-    CCK(cudaMemset(err, 0, sizeof(unsigned int)));
+    CCK(cudaMemset(err, 0, 2 * sizeof(unsigned int)));
     k_tc_gemm<<<M / 128, 128, (size_t)(128 + N) * K * 2>>>(N, K, dA, dB, dD, err);
     CCK(cudaGetLastError());
     unsigned int h = 0;
@@ -983,7 +997,17 @@ int pic_tc_gemm_bf16(int32_t M, int32_t N, int32_t K, const uint16_t* A, const u
     cudaFree(dA);
     cudaFree(dB);
     cudaFree(dD);
-    if (h) return cfail(c, PIC_ECUDA, "a tensor-core completion wait timed out");
+    if (h) return cfail(c, PIC_ETIMEOUT, "a tensor-core completion wait timed out");
+    return PIC_OK;
+}
+
+int pic_cnn_set_wait_limit(pic_cnn* c, int32_t spins) {
+    if (!c) return PIC_EINVAL;
+    cudaSetDevice(c->device);
+    if (spins < 0) return cfail(c, PIC_EINVAL, "spins must be >= 0");
+    const unsigned int v = (unsigned int)spins;
+    CCK(cudaMemcpyAsync(c->d_err + 1, &v, sizeof v, cudaMemcpyHostToDevice, c->stream));
+    CCK(cudaStreamSynchronize(c->stream));
     return PIC_OK;
 }
 

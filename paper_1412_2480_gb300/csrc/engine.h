@@ -31,6 +31,7 @@ struct FieldArgs {
     // mixed-precision refinement (MIXED32 only; nullptr otherwise)
     double* b;                         // 3 * ntot right-hand side of Eq. (7)
     float *r32, *p32, *q32, *e32;      // 3 * ntot each, inner FP32 CG vectors
+    float *r32b, *z32;                 // 3 * ntot each: second residual buffer, z = M r
     cudaGraphConditionalHandle cond_in;  // WHILE-node handle of the inner loop
 };
 
@@ -65,7 +66,7 @@ constexpr int kCoopMaxGrids = 64;
 struct CoopSolve {
     int2* gchunk = nullptr;       // per simulation: first chunk, chunk count
     int* chunk_grid = nullptr;    // per chunk: simulation
-    double* part = nullptr;       // 2 x nchunks chunk partial sums
+    double* part = nullptr;       // 2 buffers x 2 values x nchunks chunk partial sums
     unsigned int* bar = nullptr;  // grid barrier: arrivals, generation
     int nchunks = 0, nblocks = 0, ngrids = 0;
 };

@@ -527,47 +527,60 @@ __global__ void k_step_end(int ngrids, CgState* cg, const DevStatus* st) {
 // the tolerance of the plain FP64 PCG while most vector traffic and arithmetic is FP32.
 constexpr int kMaxInnerIters = 64;
 
+// Inner preconditioned CG (MIXED32): z = M r with M = pc0 I + pcx (E + W) + pcy (N + S)
+// (GridDev), the same 5-point shape and wall images as A.
+template <typename T>
+__device__ __forceinline__ T precond_at(const GridDev& G, const T* V, const Cell& c, int a) {
+    return T(G.pc0) * V[c.k] + T(G.pcx) * nbx(V, c, a) + T(G.pcy) * (V[c.kn] + V[c.ks]);
+}
+
+// r32 = r / rms(r) (buffer 0), e = 0, z = M r32; (r, r) and (r, z).
 __global__ void __launch_bounds__(kFieldThreads)
 k_mp_begin(const GridDev* __restrict__ grids, const int* __restrict__ blk_grid, int ngrids,
            int nblk_total, long long ntot, const double* __restrict__ r, float* __restrict__ r32,
-           float* __restrict__ e32, CgState* cg, double* part, unsigned int* done, DevStatus* st,
-           cudaGraphConditionalHandle cond_in, int use_cond) {
+           float* __restrict__ z32, float* __restrict__ e32, CgState* cg, double* part, unsigned int* done,
+           DevStatus* st, cudaGraphConditionalHandle cond_in, int use_cond) {
     const int g = blk_grid[blockIdx.x];
     const unsigned n_part = st->n_active;
     if (!cg[g].active) return;
     const GridDev& G = grids[g];
     const double scale = sqrt(3.0 * G.ncell / cg[g].rr);  // r32 of unit RMS
-    float acc = 0.f;
+    float acc = 0.f, acc2 = 0.f;
     FOR_CELLS(G, g, c) {
 #pragma unroll
         for (int a = 0; a < 3; a++) {
             const long long o = a * ntot + c.k;
             const float f = (float)(r[o] * scale);
+            const float z = (float)(precond_at(G, r + a * ntot, c, a) * scale);
             r32[o] = f;
+            z32[o] = z;
             e32[o] = 0.f;
             acc = fmaf(f, f, acc);
+            acc2 = fmaf(f, z, acc2);
         }
     }
-    double v[1] = {(double)acc};
-    double tot[1];
-    if (!reduce_and_finish<1>(G, g, v, part, nblk_total, done, tot)) return;
+    double v[2] = {(double)acc, (double)acc2};
+    double tot[2];
+    if (!reduce_and_finish<2>(G, g, v, part, nblk_total, done, tot)) return;
     if (threadIdx.x == 0) {
         CgState& s = cg[g];
         s.rr_in0 = tot[0];
         s.rr_in = tot[0];
+        s.rz_in = tot[1];
         s.beta_in = 0.0;
         s.in_iters = 0;
         s.in_scale = scale;
         // ask the inner loop for what the outer test still needs, within FP32's reach
         s.tol_in = fmax(2e-6, 0.5 * G.rtol * sqrt(s.bb / fmax(s.rr, 1e-300)));
-        s.in_active = tot[0] > 0.0 ? 1 : 0;
+        s.in_active = (tot[0] > 0.0 && tot[1] > 0.0) ? 1 : 0;
     }
     finish_all_grids<true>(ngrids, (int)n_part, cg, st, cond_in, use_cond);
 }
 
+// p = z + beta p, q = A z + beta q (= A p); alpha = (r, z) / (p, q).
 __global__ void __launch_bounds__(kFieldThreads)
 k_mp_direction(const GridDev* __restrict__ grids, const int* __restrict__ blk_grid, int ngrids,
-               int nblk_total, long long ntot, const float* __restrict__ r32, float* __restrict__ p32,
+               int nblk_total, long long ntot, const float* __restrict__ z32, float* __restrict__ p32,
                float* __restrict__ q32, CgState* cg, double* part, unsigned int* done) {
     const int g = blk_grid[blockIdx.x];
     if (!cg[g].in_active) return;
@@ -579,16 +592,16 @@ k_mp_direction(const GridDev* __restrict__ grids, const int* __restrict__ blk_gr
 #pragma unroll
         for (int a = 0; a < 3; a++) {
             const long long o = a * ntot;
-            const float* R = r32 + o;
-            const float rc = R[c.k];
-            const float Ar = c0 * rc - cx * nbx(R, c, a) - cy * (R[c.kn] + R[c.ks]);
+            const float* Z = z32 + o;
+            const float zc = Z[c.k];
+            const float Az = c0 * zc - cx * nbx(Z, c, a) - cy * (Z[c.kn] + Z[c.ks]);
             float pn, qn;
             if (beta == 0.f) {
-                pn = rc;
-                qn = Ar;
+                pn = zc;
+                qn = Az;
             } else {
-                pn = fmaf(beta, p32[o + c.k], rc);
-                qn = fmaf(beta, q32[o + c.k], Ar);
+                pn = fmaf(beta, p32[o + c.k], zc);
+                qn = fmaf(beta, q32[o + c.k], Az);
             }
             p32[o + c.k] = pn;
             q32[o + c.k] = qn;
@@ -598,40 +611,58 @@ k_mp_direction(const GridDev* __restrict__ grids, const int* __restrict__ blk_gr
     double v[1] = {(double)acc};
     double tot[1];
     if (!reduce_and_finish<1>(G, g, v, part, nblk_total, done, tot)) return;
-    if (threadIdx.x == 0) cg[g].alpha_in = cg[g].rr_in / tot[0];
+    if (threadIdx.x == 0) cg[g].alpha_in = cg[g].rz_in / tot[0];
 }
 
+// r' = r - alpha q into the other residual buffer, e += alpha p, z = M r' (formed from r
+// and q at the neighbours, which this kernel does not change); beta = (r', z) / (r, z).
 __global__ void __launch_bounds__(kFieldThreads)
 k_mp_update(const GridDev* __restrict__ grids, const int* __restrict__ blk_grid, int ngrids,
-            int nblk_total, long long ntot, float* __restrict__ e32, float* __restrict__ r32,
-            const float* __restrict__ p32, const float* __restrict__ q32, CgState* cg, double* part,
-            unsigned int* done, DevStatus* st, cudaGraphConditionalHandle cond_in, int use_cond) {
+            int nblk_total, long long ntot, float* __restrict__ e32, float* __restrict__ r32a,
+            float* __restrict__ r32b, float* __restrict__ z32, const float* __restrict__ p32,
+            const float* __restrict__ q32, CgState* cg, double* part, unsigned int* done, DevStatus* st,
+            cudaGraphConditionalHandle cond_in, int use_cond) {
     const int g = blk_grid[blockIdx.x];
     const unsigned n_part = st->n_in_active;
     if (!cg[g].in_active) return;
     const GridDev& G = grids[g];
     const float alpha = (float)cg[g].alpha_in;
-    float acc = 0.f;
+    const float pc0 = (float)G.pc0, pcx = (float)G.pcx, pcy = (float)G.pcy;
+    const bool odd = cg[g].in_iters & 1;  // buffer b holds r after an odd number of updates
+    const float* Rc = odd ? r32b : r32a;
+    float* Rn = odd ? r32a : r32b;
+    float acc = 0.f, acc2 = 0.f;
     FOR_CELLS(G, g, c) {
 #pragma unroll
         for (int a = 0; a < 3; a++) {
-            const long long o = a * ntot + c.k;
-            e32[o] = fmaf(alpha, p32[o], e32[o]);
-            const float rn = fmaf(-alpha, q32[o], r32[o]);
-            r32[o] = rn;
-            acc = fmaf(rn, rn, acc);
+            const long long o = a * ntot;
+            const float* R = Rc + o;
+            const float* Q = q32 + o;
+            const auto w = [&](long long k) { return fmaf(-alpha, Q[k], R[k]); };
+            const float wc = w(c.k);
+            float wx;  // sum of the two x-neighbours, images at the walls as in nbx
+            if (a == 0) wx = (c.ew ? 0.f : w(c.ke)) + (c.ww ? -w(c.k + 1) : w(c.kw));
+            else wx = (c.ew ? wc : w(c.ke)) + (c.ww ? wc : w(c.kw));
+            const float z = fmaf(pc0, wc, fmaf(pcx, wx, pcy * (w(c.kn) + w(c.ks))));
+            Rn[o + c.k] = wc;
+            z32[o + c.k] = z;
+            e32[o + c.k] = fmaf(alpha, p32[o + c.k], e32[o + c.k]);
+            acc = fmaf(wc, wc, acc);
+            acc2 = fmaf(wc, z, acc2);
         }
     }
-    double v[1] = {(double)acc};
-    double tot[1];
-    if (!reduce_and_finish<1>(G, g, v, part, nblk_total, done, tot)) return;
+    double v[2] = {(double)acc, (double)acc2};
+    double tot[2];
+    if (!reduce_and_finish<2>(G, g, v, part, nblk_total, done, tot)) return;
     if (threadIdx.x == 0) {
         CgState& s = cg[g];
-        s.beta_in = tot[0] / s.rr_in;
+        s.beta_in = tot[1] / s.rz_in;
+        s.rz_in = tot[1];
         s.rr_in = tot[0];
         s.in_iters += 1;
         s.iters += 1;
-        if (sqrt(tot[0] / s.rr_in0) <= s.tol_in || s.in_iters >= kMaxInnerIters || s.iters >= G.maxit)
+        if (sqrt(tot[0] / s.rr_in0) <= s.tol_in || s.in_iters >= kMaxInnerIters || s.iters >= G.maxit ||
+            !(tot[1] > 0.0))
             s.in_active = 0;
     }
     finish_all_grids<true>(ngrids, (int)n_part, cg, st, cond_in, use_cond, 0);
@@ -755,16 +786,16 @@ void launch_rhs(const FieldArgs& a, cudaStream_t s) {
 
 void launch_mp_inner_begin(const FieldArgs& a, cudaStream_t s) {
     k_mp_begin<<<a.nblk, kFieldThreads, 0, s>>>(a.grids, a.blk_grid, a.ngrids, a.nblk, a.ntot, a.r,
-                                                a.r32, a.e32, a.cg, a.part, a.done, a.st, a.cond_in,
+                                                a.r32, a.z32, a.e32, a.cg, a.part, a.done, a.st, a.cond_in,
                                                 a.use_cond);
 }
 
 void launch_mp_inner_iteration(const FieldArgs& a, cudaStream_t s) {
     k_mp_direction<<<a.nblk, kFieldThreads, 0, s>>>(a.grids, a.blk_grid, a.ngrids, a.nblk, a.ntot,
-                                                    a.r32, a.p32, a.q32, a.cg, a.part, a.done);
+                                                    a.z32, a.p32, a.q32, a.cg, a.part, a.done);
     k_mp_update<<<a.nblk, kFieldThreads, 0, s>>>(a.grids, a.blk_grid, a.ngrids, a.nblk, a.ntot,
-                                                 a.e32, a.r32, a.p32, a.q32, a.cg, a.part, a.done,
-                                                 a.st, a.cond_in, a.use_cond);
+                                                 a.e32, a.r32, a.r32b, a.z32, a.p32, a.q32, a.cg, a.part,
+                                                 a.done, a.st, a.cond_in, a.use_cond);
 }
 
 void launch_mp_refine(const FieldArgs& a, cudaStream_t s) {

@@ -197,7 +197,7 @@ __device__ __forceinline__ FixedScale fixed_scale(const GridDev& G, int n_tile) 
     FixedScale f;
     f.k = min(22, room);
     f.lb = min(16, room);
-    f.js = (float)(G.jscale * exp2((double)(f.k - 40)));
+    f.js = G.js40 * __int_as_float((127 + f.k) << 23);  // js40 2^k: exact, = jscale 2^(k-40) rounded
     f.jlb = (float)(1 << f.lb);
     return f;
 }
@@ -399,13 +399,12 @@ __device__ __forceinline__ bool push_one(const Mem& M, const PushConst& K, int i
 
 __device__ __forceinline__ PushConst push_const(const GridDev& G, int s) {
     PushConst K;
-    K.h = (float)(0.5 * G.qm[s] * G.dt);
-    K.dt_idx = (float)(G.dt * G.idx);
-    K.dt_idy = (float)(G.dt * G.idy);
-    const double area = G.dx * G.dy;
-    K.fx = (float)(G.qw[s] * G.dx / (G.dt * area));
-    K.fy = (float)(G.qw[s] * G.dy / (G.dt * area));
-    K.fz = (float)(G.qw[s] / area);
+    K.h = G.pk_h[s];
+    K.dt_idx = G.pk_dtx;
+    K.dt_idy = G.pk_dty;
+    K.fx = G.pk_fx[s];
+    K.fy = G.pk_fy[s];
+    K.fz = G.pk_fz[s];
     K.deposit = G.deposit;
     K.nodal = G.nodal;
     return K;

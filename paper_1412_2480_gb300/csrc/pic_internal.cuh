@@ -25,6 +25,11 @@ struct GridDev {
     double idx, idy;      // 1/dx, 1/dy
     double a;             // (theta dt)^2, the coefficient of Eq. (7)
     double c0, cx, cy;    // A v = c0 v - cx (v_e + v_w) - cy (v_n + v_s)
+    // Preconditioner of the MIXED32 inner CG, z = M r with M = pc0 I + pcx (E + W) +
+    // pcy (N + S) = p(A): the degree-1 polynomial that minimises max |1 - lambda p(lambda)|
+    // over A's spectrum [1, c0 + 2 cx + 2 cy] (Chebyshev; the same 5-point shape and wall
+    // images as A)
+    double pc0, pcx, pcy;
     long long cell_off;
     int blk_first, nblk;  // this simulation's blocks in field-kernel launches
     double qw[2], qm[2];  // charge per macro-particle and charge-to-mass sign per species
@@ -49,6 +54,12 @@ struct GridDev {
     long long bin_off;    // first particle slot of this simulation's bins
     // MIXED32 current: 64-bit fixed point, J = (double)Jfix * jinv
     double jscale, jinv;
+    // MIXED32 push constants, formed once on the host from the FP64 parameters (the FP64
+    // pipe is slow on this part, and every thread of a tile would otherwise form them):
+    // per species h = (q/m) dt/2, fx = q dx/(dt dx dy), fy = q dy/(dt dx dy),
+    // fz = q/(dx dy); dt/dx, dt/dy; js40 = jscale 2^-40 (a tile's window scale is js40 2^k)
+    float pk_h[2], pk_fx[2], pk_fy[2], pk_fz[2];
+    float pk_dtx, pk_dty, js40;
 };
 
 // Per-simulation state of the PCG solve of Eq. (7).
@@ -59,6 +70,7 @@ struct CgState {
     long long total_iters;
     // mixed-precision refinement (MIXED32): FP32 inner CG on A e = r
     double rr_in, rr_in0, alpha_in, beta_in, tol_in;
+    double rz_in;     // (r, z) of the preconditioned inner CG
     double in_scale;  // r32 = r * in_scale (unit RMS), e = e32 / in_scale
     int in_active, in_iters, outer, pad;
     long long total_outer;  // FP64 refinements (outer iterations) of all steps
@@ -82,6 +94,7 @@ struct DevStatus {
     unsigned long long loop_iters[2]; // PCG loop iterations run: [0] CG (inner) iterations,
                                       // [1] FP64 refinements (MIXED32 outer iterations)
     unsigned int sync_timeout;        // a grid barrier of the cooperative solve ran out
+    unsigned int spin_limit;          // polls of a grid-barrier wait before it gives up (0: 2^22)
 };
 
 // One contiguous range of FP64 particles of one species in one simulation.

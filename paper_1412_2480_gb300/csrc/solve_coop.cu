@@ -2,9 +2,18 @@
 //
 // After the right-hand side b and the initial residual r = b - A x0 (FP64), the whole
 // mixed-precision PCG runs inside one launch: iterative refinement in FP64 around an
-// FP32 inner CG on A e = r, as the WHILE-node version in fields.cu does, but with grid
-// barriers between the phases of an iteration instead of kernel boundaries, so an inner
-// iteration costs two barriers and two passes over L2-resident FP32 vectors.
+// FP32 inner preconditioned CG on A e = r, as the WHILE-node version in fields.cu does,
+// but with grid barriers between the phases of an iteration instead of kernel
+// boundaries, so an inner iteration costs two barriers and two passes over L2-resident
+// FP32 vectors.
+//
+// Inner PCG with z = M r (M = p(A), GridDev::pc0..pcy), per iteration:
+//   direction pass: p = z + beta p, q = A z + beta q (= A p), partial (p, q)  -> alpha
+//   update pass:    r' = r - alpha q, e += alpha p, z = M r', partials (r', r'), (r', z)
+//                   -> beta = (r', z) / (r, z)
+// The update pass forms M r' at a cell from r and q at its four neighbours (r' there is
+// r - alpha q, both unchanged in this pass), so r' goes to the other of two residual
+// buffers and no third barrier is needed.
 //
 // Work is cut into fixed chunks of 2048 cells of one simulation; a chunk's partial sums
 // are formed in a fixed order and written to its own slot, and every CTA forms each
@@ -27,7 +36,7 @@ constexpr int kCoopThreads = 256;
 constexpr int kChunkCells = 2048;
 constexpr int kPerThread = kChunkCells / kCoopThreads;
 constexpr int kInnerMax = 64;  // inner iterations per refinement, as in the WHILE-node solve
-constexpr int kCoopMaxChunks = 4096;  // partials staged in shared memory: 32 KB
+constexpr int kCoopMaxChunks = 4096;  // two partials per chunk staged in shared memory: 64 KB
 
 struct CoopArgs {
     const GridDev* grids;
@@ -39,27 +48,30 @@ struct CoopArgs {
     const double* b;
     double* x;
     double* r;
-    float* r32;
+    float* r32[2];          // the inner residual, alternating between update passes
+    float* z32;             // M r
     float* p32;
     float* q32;
     float* e32;
-    double* part;           // 2 x nchunks, alternating between phases
+    double* part;           // 2 buffers x 2 values x nchunks, alternating between phases
     unsigned int* bar;      // [0] arrivals, [1] generation
     CgState* cg;
     DevStatus* st;
 };
 
 struct GState {
-    double rr, bb, scale, rr_in0, rr_in, alpha, beta, tol_in, rel, rtol;
+    double rr, bb, scale, rr_in0, rr_in, rz, alpha, beta, tol_in, rel, rtol;
     int active, in_active, iters, in_iters, outer, maxit;
 };
 
 // Grid-wide barrier of a cooperative launch (all CTAs resident): arrivals on one counter
 // (word 0), release by advancing the generation (word 1). Bounded: false if the other
-// CTAs did not arrive within the limit. (A two-level tree of counters was slower here.)
+// CTAs did not arrive within `limit` polls; the CTA then leaves the kernel, and so do
+// the others at their next barrier (none waits for ever). (A two-level tree of
+// counters was slower here.)
 constexpr int kBarWords = 2;
 
-__device__ bool grid_barrier(unsigned int* bar, unsigned int nblocks, unsigned int* timeout) {
+__device__ bool grid_barrier(unsigned int* bar, unsigned int nblocks, unsigned int* timeout, unsigned int limit) {
     __shared__ int s_ok;
     __syncthreads();
     if (threadIdx.x == 0) {
@@ -74,7 +86,7 @@ __device__ bool grid_barrier(unsigned int* bar, unsigned int nblocks, unsigned i
         } else {
             unsigned int it = 0;
             while (*gen == g0) {
-                if (++it > (1u << 22)) {
+                if (++it > limit) {
                     atomicExch(timeout, 1u);
                     ok = 0;
                     break;
@@ -119,11 +131,34 @@ enum Phase { kBegin, kDirection, kUpdate, kX, kResidual };
 
 // Per-chunk constants, in registers.
 struct ChunkC {
-    int nx, ny, ncell, l0, walls;
+    int nx, ny, ncell, l0, walls, rb;  // rb: residual buffer holding the current r
     long long off, ntot;
     double c0, cx, cy, scale, inv;
-    float c0f, cxf, cyf, betaf, alphaf;
+    float c0f, cxf, cyf, betaf, alphaf, pc0f, pcxf, pcyf;
 };
+
+// M v for the four cells of a quad: centre quad v, north and south quads, west and east
+// scalars (images already applied).
+__device__ __forceinline__ float4 precond4(const ChunkC& q, float4 c, float4 n, float4 s, float w, float e) {
+    float4 z;
+    z.x = fmaf(q.pc0f, c.x, fmaf(q.pcxf, w + c.y, q.pcyf * (n.x + s.x)));
+    z.y = fmaf(q.pc0f, c.y, fmaf(q.pcxf, c.x + c.z, q.pcyf * (n.y + s.y)));
+    z.z = fmaf(q.pc0f, c.z, fmaf(q.pcxf, c.y + c.w, q.pcyf * (n.z + s.z)));
+    z.w = fmaf(q.pc0f, c.w, fmaf(q.pcxf, c.z + e, q.pcyf * (n.w + s.w)));
+    return z;
+}
+
+// West / east neighbours of a quad at a conducting wall (images: Bx odd and zero on the
+// wall node x = nx, By and Bz even), the same rule for every stencil on the B lattices.
+__device__ __forceinline__ void wall_images(const ChunkC& q, int i, int c, float4 v, float& w, float& e) {
+    if (!q.walls) return;
+    if (i == 0) w = c == 0 ? -v.y : v.x;
+    if (i + 4 == q.nx) e = c == 0 ? 0.f : v.w;
+}
+
+__device__ __forceinline__ float dot4(float4 a, float4 b, float acc) {
+    return fmaf(a.x, b.x, fmaf(a.y, b.y, fmaf(a.z, b.z, fmaf(a.w, b.w, acc))));
+}
 
 __device__ __forceinline__ float4 ld4(const float* p) { return __ldcg(reinterpret_cast<const float4*>(p)); }
 __device__ __forceinline__ void st4(float* p, float4 v) { *reinterpret_cast<float4*>(p) = v; }
@@ -144,9 +179,11 @@ __device__ __forceinline__ void st4d(double* p, const double v[4]) {
 // 4 (q0 + qq 256 + tid) .. + 3 of the simulation), read and written as float4 / double2
 // vectors; the west and east neighbours of a quad are two scalar loads. nx is a
 // multiple of 4, so a quad never crosses a row. FULL: the chunk has all its cells, so
-// there is no bounds test and the loads of both quads can be in flight together.
+// there is no bounds test. acc1, acc2: FP32 partial sums of the phase (r.r and r.z for
+// kBegin and kUpdate, p.q for kDirection); accd: the FP64 residual's r.r.
 template <int PH, bool FULL>
-__device__ __forceinline__ void chunk_cells(const CoopArgs& a, const ChunkC& q, float& accf, double& accd) {
+__device__ __forceinline__ void chunk_cells(const CoopArgs& a, const ChunkC& q, float& acc1, float& acc2,
+                                            double& accd) {
     const long long ntot = q.ntot;
 #pragma unroll
     for (int qq = 0; qq < kPerThread / 4; qq++) {
@@ -155,61 +192,85 @@ __device__ __forceinline__ void chunk_cells(const CoopArgs& a, const ChunkC& q, 
         const int j = l / q.nx, i = l - j * q.nx;
         const long long row = q.off + (long long)j * q.nx;
         const long long k = row + i;
+        const long long kwv = row + (i == 0 ? q.nx - 1 : i - 1);
+        const long long kev = row + (i + 4 == q.nx ? 0 : i + 4);
+        const long long kn = q.off + (long long)(j + 1 == q.ny ? 0 : j + 1) * q.nx + i;
+        const long long ks = q.off + (long long)(j == 0 ? q.ny - 1 : j - 1) * q.nx + i;
         if constexpr (PH == kBegin) {
+            // r32 = r / rms(r) in buffer 0, e = 0, z = M r32 (neighbours scaled alike)
 #pragma unroll
             for (int c = 0; c < 3; c++) {
-                double rv[4];
-                ld4d(a.r + c * ntot + k, rv);
-                const float4 f = make_float4((float)(rv[0] * q.scale), (float)(rv[1] * q.scale),
-                                             (float)(rv[2] * q.scale), (float)(rv[3] * q.scale));
-                st4(a.r32 + c * ntot + k, f);
+                const double* R = a.r + c * ntot;
+                double rv[4], rn[4], rs[4];
+                ld4d(R + k, rv);
+                ld4d(R + kn, rn);
+                ld4d(R + ks, rs);
+                const auto f4 = [&](const double v[4]) {
+                    return make_float4((float)(v[0] * q.scale), (float)(v[1] * q.scale), (float)(v[2] * q.scale),
+                                       (float)(v[3] * q.scale));
+                };
+                const float4 fc = f4(rv), fn = f4(rn), fs = f4(rs);
+                float fw = (float)(__ldcg(R + kwv) * q.scale), fe = (float)(__ldcg(R + kev) * q.scale);
+                wall_images(q, i, c, fc, fw, fe);
+                const float4 z = precond4(q, fc, fn, fs, fw, fe);
+                st4(a.r32[0] + c * ntot + k, fc);
+                st4(a.z32 + c * ntot + k, z);
                 st4(a.e32 + c * ntot + k, make_float4(0.f, 0.f, 0.f, 0.f));
-                accf = fmaf(f.x, f.x, fmaf(f.y, f.y, fmaf(f.z, f.z, fmaf(f.w, f.w, accf))));
+                acc1 = dot4(fc, fc, acc1);
+                acc2 = dot4(fc, z, acc2);
             }
         } else if constexpr (PH == kDirection) {
-            const long long kwv = row + (i == 0 ? q.nx - 1 : i - 1);
-            const long long kev = row + (i + 4 == q.nx ? 0 : i + 4);
-            const long long kn = q.off + (long long)(j + 1 == q.ny ? 0 : j + 1) * q.nx + i;
-            const long long ks = q.off + (long long)(j == 0 ? q.ny - 1 : j - 1) * q.nx + i;
 #pragma unroll
             for (int c = 0; c < 3; c++) {
-                const float* R = a.r32 + c * ntot;
-                const float4 rc = ld4(R + k), rn = ld4(R + kn), rs = ld4(R + ks);
-                float rw = __ldcg(R + kwv), re = __ldcg(R + kev);
-                if (q.walls) {  // images at a conducting wall: Bx odd, By and Bz even
-                    if (i == 0) rw = c == 0 ? -rc.y : rc.x;
-                    if (i + 4 == q.nx) re = c == 0 ? 0.f : rc.w;
-                }
+                const float* Z = a.z32 + c * ntot;
+                const float4 zc = ld4(Z + k), zn = ld4(Z + kn), zs = ld4(Z + ks);
+                float zw = __ldcg(Z + kwv), ze = __ldcg(Z + kev);
+                wall_images(q, i, c, zc, zw, ze);
                 const float4 po = ld4(a.p32 + c * ntot + k), qo = ld4(a.q32 + c * ntot + k);
-                float4 Ar;
-                Ar.x = q.c0f * rc.x - q.cxf * (rw + rc.y) - q.cyf * (rn.x + rs.x);
-                Ar.y = q.c0f * rc.y - q.cxf * (rc.x + rc.z) - q.cyf * (rn.y + rs.y);
-                Ar.z = q.c0f * rc.z - q.cxf * (rc.y + rc.w) - q.cyf * (rn.z + rs.z);
-                Ar.w = q.c0f * rc.w - q.cxf * (rc.z + re) - q.cyf * (rn.w + rs.w);
+                float4 Az;
+                Az.x = q.c0f * zc.x - q.cxf * (zw + zc.y) - q.cyf * (zn.x + zs.x);
+                Az.y = q.c0f * zc.y - q.cxf * (zc.x + zc.z) - q.cyf * (zn.y + zs.y);
+                Az.z = q.c0f * zc.z - q.cxf * (zc.y + zc.w) - q.cyf * (zn.z + zs.z);
+                Az.w = q.c0f * zc.w - q.cxf * (zc.z + ze) - q.cyf * (zn.w + zs.w);
                 // beta = 0 on the first iteration: p and q of the last solve are not used
                 const bool first = q.betaf == 0.f;
-                const float4 pn = first ? rc
-                                        : make_float4(fmaf(q.betaf, po.x, rc.x), fmaf(q.betaf, po.y, rc.y),
-                                                      fmaf(q.betaf, po.z, rc.z), fmaf(q.betaf, po.w, rc.w));
-                const float4 qn = first ? Ar
-                                        : make_float4(fmaf(q.betaf, qo.x, Ar.x), fmaf(q.betaf, qo.y, Ar.y),
-                                                      fmaf(q.betaf, qo.z, Ar.z), fmaf(q.betaf, qo.w, Ar.w));
+                const float b = q.betaf;
+                const float4 pn = first ? zc
+                                        : make_float4(fmaf(b, po.x, zc.x), fmaf(b, po.y, zc.y),
+                                                      fmaf(b, po.z, zc.z), fmaf(b, po.w, zc.w));
+                const float4 qn = first ? Az
+                                        : make_float4(fmaf(b, qo.x, Az.x), fmaf(b, qo.y, Az.y),
+                                                      fmaf(b, qo.z, Az.z), fmaf(b, qo.w, Az.w));
                 st4(a.p32 + c * ntot + k, pn);
                 st4(a.q32 + c * ntot + k, qn);
-                accf = fmaf(pn.x, qn.x, fmaf(pn.y, qn.y, fmaf(pn.z, qn.z, fmaf(pn.w, qn.w, accf))));
+                acc1 = dot4(pn, qn, acc1);
             }
         } else if constexpr (PH == kUpdate) {
+            const float al = q.alphaf;
+            const float* Rc = a.r32[q.rb];
+            float* Rn = a.r32[q.rb ^ 1];
 #pragma unroll
             for (int c = 0; c < 3; c++) {
-                const long long o = c * ntot + k;
-                const float4 e = ld4(a.e32 + o), pp = ld4(a.p32 + o), qv = ld4(a.q32 + o), r = ld4(a.r32 + o);
-                const float al = q.alphaf;
-                st4(a.e32 + o, make_float4(fmaf(al, pp.x, e.x), fmaf(al, pp.y, e.y), fmaf(al, pp.z, e.z),
-                                           fmaf(al, pp.w, e.w)));
-                const float4 rn = make_float4(fmaf(-al, qv.x, r.x), fmaf(-al, qv.y, r.y), fmaf(-al, qv.z, r.z),
-                                              fmaf(-al, qv.w, r.w));
-                st4(a.r32 + o, rn);
-                accf = fmaf(rn.x, rn.x, fmaf(rn.y, rn.y, fmaf(rn.z, rn.z, fmaf(rn.w, rn.w, accf))));
+                const long long o = c * ntot;
+                const float4 rc = ld4(Rc + o + k), rn = ld4(Rc + o + kn), rs = ld4(Rc + o + ks);
+                const float4 qc = ld4(a.q32 + o + k), qn = ld4(a.q32 + o + kn), qs = ld4(a.q32 + o + ks);
+                const float rw = __ldcg(Rc + o + kwv), re = __ldcg(Rc + o + kev);
+                const float qw = __ldcg(a.q32 + o + kwv), qe = __ldcg(a.q32 + o + kev);
+                const float4 pp = ld4(a.p32 + o + k), e = ld4(a.e32 + o + k);
+                const auto upd = [al](float4 r, float4 v) {
+                    return make_float4(fmaf(-al, v.x, r.x), fmaf(-al, v.y, r.y), fmaf(-al, v.z, r.z),
+                                       fmaf(-al, v.w, r.w));
+                };
+                const float4 wc = upd(rc, qc), wn = upd(rn, qn), ws = upd(rs, qs);
+                float ww = fmaf(-al, qw, rw), we = fmaf(-al, qe, re);
+                wall_images(q, i, c, wc, ww, we);
+                const float4 z = precond4(q, wc, wn, ws, ww, we);
+                st4(Rn + o + k, wc);
+                st4(a.z32 + o + k, z);
+                st4(a.e32 + o + k, make_float4(fmaf(al, pp.x, e.x), fmaf(al, pp.y, e.y), fmaf(al, pp.z, e.z),
+                                               fmaf(al, pp.w, e.w)));
+                acc1 = dot4(wc, wc, acc1);
+                acc2 = dot4(wc, z, acc2);
             }
         } else if constexpr (PH == kX) {
 #pragma unroll
@@ -225,10 +286,6 @@ __device__ __forceinline__ void chunk_cells(const CoopArgs& a, const ChunkC& q, 
                 st4d(a.x + o, xv);
             }
         } else {  // kResidual: r = b - A x in FP64
-            const long long kwv = row + (i == 0 ? q.nx - 1 : i - 1);
-            const long long kev = row + (i + 4 == q.nx ? 0 : i + 4);
-            const long long kn = q.off + (long long)(j + 1 == q.ny ? 0 : j + 1) * q.nx + i;
-            const long long ks = q.off + (long long)(j == 0 ? q.ny - 1 : j - 1) * q.nx + i;
 #pragma unroll
             for (int c = 0; c < 3; c++) {
                 const double* X = a.x + c * ntot;
@@ -255,13 +312,13 @@ __device__ __forceinline__ void chunk_cells(const CoopArgs& a, const ChunkC& q, 
     }
 }
 
-// The two inner-iteration phases on a full chunk, component by component with the loads
-// of both quads issued before any arithmetic: the stores of one component cannot be
-// proved apart from the loads of the next, so a quad-by-quad order would serialise six
-// L2 round trips per phase.
+// The direction pass on a full chunk, component by component with the loads of both
+// quads issued before any arithmetic: the stores of one component cannot be proved
+// apart from the loads of the next, so a quad-by-quad order would serialise six L2
+// round trips per phase.
 constexpr int kQuads = kPerThread / 4;
 
-__device__ __forceinline__ void direction_full(const CoopArgs& a, const ChunkC& q, float& accf) {
+__device__ __forceinline__ void direction_full(const CoopArgs& a, const ChunkC& q, float& acc1) {
     int k[kQuads], kn[kQuads], ks[kQuads], kw[kQuads], ke[kQuads], ii[kQuads];
 #pragma unroll
     for (int qq = 0; qq < kQuads; qq++) {
@@ -278,85 +335,53 @@ __device__ __forceinline__ void direction_full(const CoopArgs& a, const ChunkC& 
     const bool first = q.betaf == 0.f;  // beta = 0: p and q of the last solve are not used
 #pragma unroll
     for (int c = 0; c < 3; c++) {
-        const float* R = a.r32 + c * q.ntot + q.off;
+        const float* Z = a.z32 + c * q.ntot + q.off;
         float* Pp = a.p32 + c * q.ntot + q.off;
         float* Qp = a.q32 + c * q.ntot + q.off;
-        float4 rc[kQuads], rn[kQuads], rs[kQuads], po[kQuads], qo[kQuads];
-        float rw[kQuads], re[kQuads];
+        float4 zc[kQuads], zn[kQuads], zs[kQuads], po[kQuads], qo[kQuads];
+        float zw[kQuads], ze[kQuads];
 #pragma unroll
         for (int qq = 0; qq < kQuads; qq++) {
-            rc[qq] = ld4(R + k[qq]);
-            rn[qq] = ld4(R + kn[qq]);
-            rs[qq] = ld4(R + ks[qq]);
-            rw[qq] = __ldcg(R + kw[qq]);
-            re[qq] = __ldcg(R + ke[qq]);
+            zc[qq] = ld4(Z + k[qq]);
+            zn[qq] = ld4(Z + kn[qq]);
+            zs[qq] = ld4(Z + ks[qq]);
+            zw[qq] = __ldcg(Z + kw[qq]);
+            ze[qq] = __ldcg(Z + ke[qq]);
             po[qq] = ld4(Pp + k[qq]);
             qo[qq] = ld4(Qp + k[qq]);
         }
 #pragma unroll
         for (int qq = 0; qq < kQuads; qq++) {
-            if (q.walls) {  // images at a conducting wall: Bx odd, By and Bz even
-                if (ii[qq] == 0) rw[qq] = c == 0 ? -rc[qq].y : rc[qq].x;
-                if (ii[qq] + 4 == q.nx) re[qq] = c == 0 ? 0.f : rc[qq].w;
-            }
-            const float4 r0 = rc[qq], r1 = rn[qq], r2 = rs[qq];
-            float4 Ar;
-            Ar.x = q.c0f * r0.x - q.cxf * (rw[qq] + r0.y) - q.cyf * (r1.x + r2.x);
-            Ar.y = q.c0f * r0.y - q.cxf * (r0.x + r0.z) - q.cyf * (r1.y + r2.y);
-            Ar.z = q.c0f * r0.z - q.cxf * (r0.y + r0.w) - q.cyf * (r1.z + r2.z);
-            Ar.w = q.c0f * r0.w - q.cxf * (r0.z + re[qq]) - q.cyf * (r1.w + r2.w);
+            wall_images(q, ii[qq], c, zc[qq], zw[qq], ze[qq]);
+            const float4 r0 = zc[qq], r1 = zn[qq], r2 = zs[qq];
+            float4 Az;
+            Az.x = q.c0f * r0.x - q.cxf * (zw[qq] + r0.y) - q.cyf * (r1.x + r2.x);
+            Az.y = q.c0f * r0.y - q.cxf * (r0.x + r0.z) - q.cyf * (r1.y + r2.y);
+            Az.z = q.c0f * r0.z - q.cxf * (r0.y + r0.w) - q.cyf * (r1.z + r2.z);
+            Az.w = q.c0f * r0.w - q.cxf * (r0.z + ze[qq]) - q.cyf * (r1.w + r2.w);
             const float b = q.betaf;
             const float4 pn = first ? r0
                                     : make_float4(fmaf(b, po[qq].x, r0.x), fmaf(b, po[qq].y, r0.y),
                                                   fmaf(b, po[qq].z, r0.z), fmaf(b, po[qq].w, r0.w));
-            const float4 qn = first ? Ar
-                                    : make_float4(fmaf(b, qo[qq].x, Ar.x), fmaf(b, qo[qq].y, Ar.y),
-                                                  fmaf(b, qo[qq].z, Ar.z), fmaf(b, qo[qq].w, Ar.w));
+            const float4 qn = first ? Az
+                                    : make_float4(fmaf(b, qo[qq].x, Az.x), fmaf(b, qo[qq].y, Az.y),
+                                                  fmaf(b, qo[qq].z, Az.z), fmaf(b, qo[qq].w, Az.w));
             st4(Pp + k[qq], pn);
             st4(Qp + k[qq], qn);
-            accf = fmaf(pn.x, qn.x, fmaf(pn.y, qn.y, fmaf(pn.z, qn.z, fmaf(pn.w, qn.w, accf))));
-        }
-    }
-}
-
-__device__ __forceinline__ void update_full(const CoopArgs& a, const ChunkC& q, float& accf) {
-    int k[kQuads];
-#pragma unroll
-    for (int qq = 0; qq < kQuads; qq++) k[qq] = q.l0 + 4 * (qq * kCoopThreads + (int)threadIdx.x);
-    const float al = q.alphaf;
-#pragma unroll
-    for (int c = 0; c < 3; c++) {
-        const long long o = c * q.ntot + q.off;
-        float4 e[kQuads], pp[kQuads], qv[kQuads], r[kQuads];
-#pragma unroll
-        for (int qq = 0; qq < kQuads; qq++) {
-            e[qq] = ld4(a.e32 + o + k[qq]);
-            pp[qq] = ld4(a.p32 + o + k[qq]);
-            qv[qq] = ld4(a.q32 + o + k[qq]);
-            r[qq] = ld4(a.r32 + o + k[qq]);
-        }
-#pragma unroll
-        for (int qq = 0; qq < kQuads; qq++) {
-            st4(a.e32 + o + k[qq], make_float4(fmaf(al, pp[qq].x, e[qq].x), fmaf(al, pp[qq].y, e[qq].y),
-                                               fmaf(al, pp[qq].z, e[qq].z), fmaf(al, pp[qq].w, e[qq].w)));
-            const float4 rn = make_float4(fmaf(-al, qv[qq].x, r[qq].x), fmaf(-al, qv[qq].y, r[qq].y),
-                                          fmaf(-al, qv[qq].z, r[qq].z), fmaf(-al, qv[qq].w, r[qq].w));
-            st4(a.r32 + o + k[qq], rn);
-            accf = fmaf(rn.x, rn.x, fmaf(rn.y, rn.y, fmaf(rn.z, rn.z, fmaf(rn.w, rn.w, accf))));
+            acc1 = dot4(pn, qn, acc1);
         }
     }
 }
 
 template <int PH>
-__device__ __forceinline__ void chunk_phase(const CoopArgs& a, const ChunkC& q, float& accf, double& accd) {
+__device__ __forceinline__ void chunk_phase(const CoopArgs& a, const ChunkC& q, float& acc1, float& acc2,
+                                            double& accd) {
     const bool full = q.l0 + kChunkCells <= q.ncell;
     if constexpr (PH == kDirection) {
-        if (full) return direction_full(a, q, accf);
-    } else if constexpr (PH == kUpdate) {
-        if (full) return update_full(a, q, accf);
+        if (full) return direction_full(a, q, acc1);
     }
-    if (full) chunk_cells<PH, true>(a, q, accf, accd);
-    else chunk_cells<PH, false>(a, q, accf, accd);
+    if (full) chunk_cells<PH, true>(a, q, acc1, acc2, accd);
+    else chunk_cells<PH, false>(a, q, acc1, acc2, accd);
 }
 
 // 4 CTAs per SM (64 registers): 608 resident CTAs, so a 2048 x 512 grid (512 chunks)
@@ -364,11 +389,12 @@ __device__ __forceinline__ void chunk_phase(const CoopArgs& a, const ChunkC& q, 
 __global__ void __launch_bounds__(kCoopThreads, 4) k_mp_coop(const CoopArgs a) {
     __shared__ GState gs[kCoopMaxGrids];
     __shared__ double red[32];
-    extern __shared__ double sp[];  // nchunks staged partial sums
+    extern __shared__ double sp[];  // 2 x nchunks staged partial sums
     DevStatus* st = a.st;
     if (st->stop) return;  // the same for every CTA: stop changes only between launches
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
     const unsigned int nb = gridDim.x;
+    const unsigned int lim = st->spin_limit ? st->spin_limit : (1u << 22);  // the same in every CTA
     for (int g = tid; g < a.ngrids; g += blockDim.x) {
         const CgState& c = a.cg[g];
         GState s{};
@@ -384,12 +410,14 @@ __global__ void __launch_bounds__(kCoopThreads, 4) k_mp_coop(const CoopArgs a) {
     }
     __syncthreads();
     int buf = 0;
+    int rb = 0;  // residual buffer holding the current inner r (the same in every CTA)
     bool ok = true;
+    const auto two = [](Phase ph) { return ph == kBegin || ph == kUpdate; };  // phases with two sums
 
     // One pass over this CTA's chunks of the simulations taking part in `ph`, with
     // per-chunk partial sums into buffer `buf` where the phase reduces.
     auto pass = [&](Phase ph) {
-        double* part = a.part + (size_t)buf * a.nchunks;
+        double* part = a.part + (size_t)buf * 2 * a.nchunks;
         for (int ch = blockIdx.x; ch < a.nchunks; ch += nb) {
             const int g = __ldg(a.chunk_grid + ch);
             const GState& s = gs[g];
@@ -405,58 +433,73 @@ __global__ void __launch_bounds__(kCoopThreads, 4) k_mp_coop(const CoopArgs a) {
             q.walls = __ldg(&Gp->walls);
             q.off = __ldg(&Gp->cell_off);
             q.ntot = a.ntot;
+            q.rb = rb;
             q.c0 = __ldg(&Gp->c0);
             q.cx = __ldg(&Gp->cx);
             q.cy = __ldg(&Gp->cy);
             q.c0f = (float)q.c0;
             q.cxf = (float)q.cx;
             q.cyf = (float)q.cy;
+            q.pc0f = (float)__ldg(&Gp->pc0);
+            q.pcxf = (float)__ldg(&Gp->pcx);
+            q.pcyf = (float)__ldg(&Gp->pcy);
             q.betaf = (float)s.beta;
             q.alphaf = (float)s.alpha;
             q.scale = s.scale;
             q.inv = 1.0 / s.scale;
             q.l0 = (ch - __ldg(&a.gchunk[g].x)) * kChunkCells;
-            float accf = 0.f;
+            float acc1 = 0.f, acc2 = 0.f;
             double accd = 0.0;
             switch (ph) {
-            case kBegin: chunk_phase<kBegin>(a, q, accf, accd); break;
-            case kDirection: chunk_phase<kDirection>(a, q, accf, accd); break;
-            case kUpdate: chunk_phase<kUpdate>(a, q, accf, accd); break;
-            case kX: chunk_phase<kX>(a, q, accf, accd); break;
-            default: chunk_phase<kResidual>(a, q, accf, accd); break;
+            case kBegin: chunk_phase<kBegin>(a, q, acc1, acc2, accd); break;
+            case kDirection: chunk_phase<kDirection>(a, q, acc1, acc2, accd); break;
+            case kUpdate: chunk_phase<kUpdate>(a, q, acc1, acc2, accd); break;
+            case kX: chunk_phase<kX>(a, q, acc1, acc2, accd); break;
+            default: chunk_phase<kResidual>(a, q, acc1, acc2, accd); break;
             }
             if (ph != kX) {
-                const double tot = block_sum(ph == kResidual ? accd : (double)accf, red);
-                if (tid == 0) part[ch] = tot;
-                __syncthreads();  // red is reused by the next chunk
+                const double t1 = block_sum(ph == kResidual ? accd : (double)acc1, red);
+                if (tid == 0) part[ch] = t1;
+                __syncthreads();  // red is reused next
+                if (two(ph)) {
+                    const double t2 = block_sum((double)acc2, red);
+                    if (tid == 0) part[a.nchunks + ch] = t2;
+                    __syncthreads();
+                }
             }
         }
     };
     // After a barrier: every CTA forms the sums of the phase for all simulations taking
     // part, then updates their scalars identically.
     auto reduce = [&](Phase ph) {
-        stage_partials(a.part + (size_t)buf * a.nchunks, a.nchunks, sp);
+        const double* part = a.part + (size_t)buf * 2 * a.nchunks;
+        stage_partials(part, two(ph) ? 2 * a.nchunks : a.nchunks, sp);
         for (int g = warp; g < a.ngrids; g += kCoopThreads / 32) {
             GState& s = gs[g];
             const bool on = (ph == kDirection || ph == kUpdate) ? (s.active && s.in_active) : s.active;
             if (!on) continue;
             const double t = chunk_sum(sp, a.gchunk[g]);
+            const double t2 = two(ph) ? chunk_sum(sp + a.nchunks, a.gchunk[g]) : 0.0;
             if (lane != 0) continue;
             if (ph == kBegin) {
                 s.rr_in0 = t;
                 s.rr_in = t;
+                s.rz = t2;
                 s.beta = 0.0;
                 s.in_iters = 0;
                 s.tol_in = fmax(2e-6, 0.5 * s.rtol * sqrt(s.bb / fmax(s.rr, 1e-300)));
-                s.in_active = t > 0.0 ? 1 : 0;
+                s.in_active = (t > 0.0 && t2 > 0.0) ? 1 : 0;
             } else if (ph == kDirection) {
-                s.alpha = s.rr_in / t;
+                s.alpha = s.rz / t;
             } else if (ph == kUpdate) {
-                s.beta = t / s.rr_in;
+                s.beta = t2 / s.rz;
+                s.rz = t2;
                 s.rr_in = t;
                 s.in_iters += 1;
                 s.iters += 1;
-                if (sqrt(t / s.rr_in0) <= s.tol_in || s.in_iters >= kInnerMax || s.iters >= s.maxit) s.in_active = 0;
+                if (sqrt(t / s.rr_in0) <= s.tol_in || s.in_iters >= kInnerMax || s.iters >= s.maxit ||
+                    !(t2 > 0.0))
+                    s.in_active = 0;
             } else if (ph == kResidual) {
                 s.rr = t;
                 s.rel = sqrt(t / s.bb);
@@ -486,26 +529,28 @@ __global__ void __launch_bounds__(kCoopThreads, 4) k_mp_coop(const CoopArgs a) {
             if (gs[g].active) gs[g].scale = sqrt(3.0 * a.grids[g].ncell / gs[g].rr);  // r32 of unit RMS
         __syncthreads();
         pass(kBegin);
-        ok = grid_barrier(a.bar, nb, &st->sync_timeout);
+        rb = 0;
+        ok = grid_barrier(a.bar, nb, &st->sync_timeout, lim);
         if (!ok) break;
         reduce(kBegin);
         while (any(true)) {
             pass(kDirection);
-            ok = grid_barrier(a.bar, nb, &st->sync_timeout);
+            ok = grid_barrier(a.bar, nb, &st->sync_timeout, lim);
             if (!ok) break;
             reduce(kDirection);
             pass(kUpdate);
-            ok = grid_barrier(a.bar, nb, &st->sync_timeout);
+            rb ^= 1;  // the update pass wrote r' into the other buffer
+            ok = grid_barrier(a.bar, nb, &st->sync_timeout, lim);
             if (!ok) break;
             reduce(kUpdate);
             if (blockIdx.x == 0 && tid == 0) st->loop_iters[0] += 1ull;
         }
         if (!ok) break;
         pass(kX);
-        ok = grid_barrier(a.bar, nb, &st->sync_timeout);
+        ok = grid_barrier(a.bar, nb, &st->sync_timeout, lim);
         if (!ok) break;
         pass(kResidual);
-        ok = grid_barrier(a.bar, nb, &st->sync_timeout);
+        ok = grid_barrier(a.bar, nb, &st->sync_timeout, lim);
         if (!ok) break;
         reduce(kResidual);
         if (blockIdx.x == 0 && tid == 0) st->loop_iters[1] += 1ull;
@@ -547,12 +592,12 @@ int coop_create(CoopSolve* cs, const GridDev* hg, int ngrids, std::string& err) 
     if (e == cudaSuccess) e = cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
     if (e == cudaSuccess) e = cudaDeviceGetAttribute(&coop, cudaDevAttrCooperativeLaunch, dev);
     if ((int)cg.size() > kCoopMaxChunks) return PIC_EINVAL;
-    const size_t smem = cg.size() * sizeof(double);
+    const size_t smem = 2 * cg.size() * sizeof(double);
     if (e == cudaSuccess) e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k_mp_coop, kCoopThreads, smem);
     if (e == cudaSuccess && (!coop || occ < 1)) return PIC_EINVAL;
     if (e == cudaSuccess) e = cudaMalloc(&cs->gchunk, ngrids * sizeof(int2));
     if (e == cudaSuccess) e = cudaMalloc(&cs->chunk_grid, cg.size() * sizeof(int));
-    if (e == cudaSuccess) e = cudaMalloc(&cs->part, 2 * cg.size() * sizeof(double));
+    if (e == cudaSuccess) e = cudaMalloc(&cs->part, 4 * cg.size() * sizeof(double));
     if (e == cudaSuccess) e = cudaMalloc(&cs->bar, kBarWords * sizeof(unsigned int));
     if (e == cudaSuccess) e = cudaMemcpy(cs->gchunk, gc.data(), ngrids * sizeof(int2), cudaMemcpyHostToDevice);
     if (e == cudaSuccess) e = cudaMemcpy(cs->chunk_grid, cg.data(), cg.size() * sizeof(int), cudaMemcpyHostToDevice);
@@ -587,7 +632,9 @@ cudaError_t launch_mp_coop(const CoopSolve& cs, const FieldArgs& f, cudaStream_t
     a.b = f.b;
     a.x = f.x;
     a.r = f.r;
-    a.r32 = f.r32;
+    a.r32[0] = f.r32;
+    a.r32[1] = f.r32b;
+    a.z32 = f.z32;
     a.p32 = f.p32;
     a.q32 = f.q32;
     a.e32 = f.e32;
@@ -598,7 +645,7 @@ cudaError_t launch_mp_coop(const CoopSolve& cs, const FieldArgs& f, cudaStream_t
     cudaLaunchConfig_t cfg{};
     cfg.gridDim = dim3((unsigned)cs.nblocks);
     cfg.blockDim = dim3(kCoopThreads);
-    cfg.dynamicSmemBytes = (size_t)cs.nchunks * sizeof(double);
+    cfg.dynamicSmemBytes = 2 * (size_t)cs.nchunks * sizeof(double);
     cfg.stream = s;
     cudaLaunchAttribute at[1];
     at[0].id = cudaLaunchAttributeCooperative;

@@ -85,6 +85,32 @@ __device__ __forceinline__ bool mbar_wait(uint64_t* bar, uint32_t phase) {
     return false;
 }
 
+// Non-blocking test whether phase `phase` of the barrier has completed.
+__device__ __forceinline__ bool mbar_test_wait(uint64_t* bar, uint32_t phase) {
+    uint32_t ok;
+    asm volatile(
+        "{\n"
+        " .reg .pred p;\n"
+        " mbarrier.test_wait.parity.shared::cta.b64 p, [%1], %2;\n"
+        " selp.u32 %0, 1, 0, p;\n"
+        "}\n"
+        : "=r"(ok)
+        : "r"(smem_addr(bar)), "r"(phase)
+        : "memory");
+    return ok != 0;
+}
+
+// The wait with a caller's limit: `limit` non-blocking polls when limit > 0 (a short
+// limit lets a test make the wait run out), the default bound of mbar_wait otherwise.
+// After a false return the operation is still in flight: the caller drains it with
+// mbar_wait before it frees the memory the operation uses.
+__device__ __forceinline__ bool mbar_wait_lim(uint64_t* bar, uint32_t phase, uint32_t limit) {
+    if (limit == 0) return mbar_wait(bar, phase);
+    for (uint32_t it = 0; it < limit; ++it)
+        if (mbar_test_wait(bar, phase)) return true;
+    return false;
+}
+
 // D (tensor memory) = A B^T (+ D when accumulate != 0), A and B from descriptors.
 __device__ __forceinline__ void mma_bf16(uint32_t d_tmem, uint64_t adesc, uint64_t bdesc, uint32_t idesc,
                                          uint32_t accumulate) {

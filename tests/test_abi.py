@@ -101,3 +101,12 @@ def test_walls_parameter_validation_on_host():
         with pytest.raises(pic.PicError) as e:
             pic.pic_init(pic.pic_params_default(**kw))
         assert e.value.code == pic.PIC_EINVAL
+
+
+def test_return_codes_match_header():
+    text = open(os.path.join(ROOT, "include", "pic.h")).read()
+    codes = dict((k, int(v)) for k, v in re.findall(r"#define (PIC_E\w+|PIC_OK) \((-?\d+)\)", text))
+    codes.update((k, int(v)) for k, v in re.findall(r"#define (PIC_OK) (\d+)", text))
+    assert "PIC_ETIMEOUT" in codes and len(codes) >= 9
+    for name, value in codes.items():
+        assert getattr(pic, name) == value, name
