@@ -31,8 +31,6 @@
 // finds no room goes to the overflow list and the host re-sorts with larger bins after
 // the pic_step call. Count slots record every particle sent to a segment, parked ones
 // included; readers clamp them to the segment's capacity.
-#include <cub/cub.cuh>
-
 #include <algorithm>
 #include <cmath>
 #include <vector>
@@ -789,11 +787,19 @@ __global__ void k_stage_fp64(long long n, const double* x, const double* y, cons
     S.uz[k] = (float)c;
 }
 
-// Sort key of a staged particle: (tile, rank in its cell, cell in tile). Sorted, a bin
-// lists one particle of every cell, then a second of every cell, and so on, so the 32
-// lanes of a warp work on 32 different cells (no shared-memory address conflicts).
-__global__ void k_keys(long long n, GridDev G, const int* cij, unsigned int* cellcnt,
-                       int* bincnt, unsigned long long* keys, unsigned int* idx) {
+// ---- the load / re-sort into tile bins (a counting sort, no library) ------------------
+// A bin lists one particle of every cell of its tile, then a second of every cell, and
+// so on, so that the 32 lanes of a warp work on 32 different cells: the particle of rank
+// r in its cell (0, 1, ...) at cell cin of the tile goes to the slot that the key
+// r * cells_per_tile + cin has among the tile's occupied keys. Keys are unique within a
+// tile, so the slot is a prefix count over an occupancy bitmap of the tile's key range:
+//   k_rank      rank within the cell (counter per cell), the tile and the key; tile
+//               counts; the largest rank;
+//   k_setbits   one bit per particle in its tile's bitmap;
+//   k_scanbits  per tile, the exclusive prefix of the bitmap words' bit counts;
+//   k_scatter   slot = prefix of the key's word + bits below the key within the word.
+__global__ void k_rank(long long n, GridDev G, const int* cij, unsigned int* cellcnt, int* bincnt,
+                       unsigned int* maxrank, unsigned int* key, int* tile) {
     const long long k = (long long)blockIdx.x * blockDim.x + threadIdx.x;
     const bool valid = k < n;
     const int c = valid ? cij[k] : 0;
@@ -811,24 +817,66 @@ __global__ void k_keys(long long n, GridDev G, const int* cij, unsigned int* cel
     const int t = (j / G.ty) * G.ntx + i / G.tx;
     const unsigned grpt = __match_any_sync(act, t);
     if (lane == __ffs(grpt) - 1) atomicAdd(&bincnt[t], __popc(grpt));
+    const unsigned rmax = __reduce_max_sync(act, rank);
+    if (lane == __ffs(act) - 1) atomicMax(maxrank, rmax);
     const unsigned cin = (unsigned)((j - (j / G.ty) * G.ty) * G.tx + (i - (i / G.tx) * G.tx));
-    const unsigned cpt = (unsigned)(G.tx * G.ty);
-    const unsigned r = min(rank, (0xffffffffu / cpt) - 1u);
-    keys[k] = ((unsigned long long)t << 32) | (unsigned long long)(r * cpt + cin);
-    idx[k] = (unsigned)k;
+    key[k] = rank * (unsigned)(G.tx * G.ty) + cin;
+    tile[k] = t;
 }
 
-__global__ void k_scatter(long long n, GridDev G, int s, const unsigned long long* keys,
-                          const unsigned int* idx, const long long* binstart, PartArrays S,
-                          unsigned* B) {
+// words: bitmap words per tile; the bitmap holds tiles t0 .. t0 + ntg - 1
+__global__ void k_setbits(long long n, const unsigned int* key, const int* tile, int t0, int ntg, long long words,
+                          unsigned int* bits) {
+    const long long k = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (k >= n) return;
+    const int t = tile[k] - t0;
+    if (t < 0 || t >= ntg) return;
+    const unsigned q = key[k];
+    atomicOr(bits + (long long)t * words + (q >> 5), 1u << (q & 31));
+}
+
+// One block per tile: pref[w] = bits set in words 0 .. w-1 of the tile's bitmap.
+__global__ void __launch_bounds__(256) k_scanbits(long long words, const unsigned int* bits, unsigned int* pref) {
+    __shared__ unsigned int s_warp[8];
+    __shared__ unsigned int s_carry;
+    const unsigned int* b = bits + (long long)blockIdx.x * words;
+    unsigned int* o = pref + (long long)blockIdx.x * words;
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    if (threadIdx.x == 0) s_carry = 0;
+    __syncthreads();
+    for (long long w0 = 0; w0 < words; w0 += blockDim.x) {
+        const long long w = w0 + threadIdx.x;
+        const unsigned v = w < words ? (unsigned)__popc(b[w]) : 0u;
+        unsigned x = v;  // inclusive scan within the warp
+#pragma unroll
+        for (int d = 1; d < 32; d <<= 1) {
+            const unsigned y = __shfl_up_sync(0xffffffffu, x, d);
+            if (lane >= d) x += y;
+        }
+        if (lane == 31) s_warp[warp] = x;
+        __syncthreads();
+        unsigned before = s_carry;
+        for (int q = 0; q < warp; q++) before += s_warp[q];
+        if (w < words) o[w] = before + x - v;
+        __syncthreads();
+        if (threadIdx.x == blockDim.x - 1) s_carry = before + x;
+        __syncthreads();
+    }
+}
+
+__global__ void k_scatter(long long n, GridDev G, int s, const unsigned int* key, const int* tile, int t0,
+                          int ntg, long long words, const unsigned int* bits, const unsigned int* pref,
+                          PartArrays S, unsigned* B) {
     const long long p = (long long)blockIdx.x * blockDim.x + threadIdx.x;
     if (p >= n) return;
-    const int t = (int)(keys[p] >> 32);
-    const long long r = p - binstart[t];
+    const int t = tile[p];
+    if (t < t0 || t >= t0 + ntg) return;
+    const unsigned q = key[p];
+    const long long wq = (long long)(t - t0) * words + (q >> 5);
+    const long long r = (long long)pref[wq] + __popc(bits[wq] & ((1u << (q & 31)) - 1u));
     const long long dst = G.bin_off + ((long long)t * 2 + s) * bin_stride(G) + r;
-    const unsigned src = idx[p];
-    const float u[3] = {S.ux[src], S.uy[src], S.uz[src]};
-    put(B, dst, S.cij[src], S.ox[src], S.oy[src], u);
+    const float u[3] = {S.ux[p], S.uy[p], S.uz[p]};
+    put(B, dst, S.cij[p], S.ox[p], S.oy[p], u);
 }
 
 // cnt points at the simulation's first count slot.
@@ -1000,11 +1048,9 @@ int sort_into_bins(MixedState* m, int g, int par, int s, PartArrays S, long long
     const int ntiles = G.ntiles;
     unsigned int* cellcnt = nullptr;
     int* bincnt = nullptr;
-    long long* binstart = nullptr;
-    unsigned long long *k0 = nullptr, *k1 = nullptr;
-    unsigned int *i0 = nullptr, *i1 = nullptr;
-    void* tmp = nullptr;
-    size_t tmpb = 0;
+    unsigned int* maxrank = nullptr;
+    unsigned int *key = nullptr, *bits = nullptr, *pref = nullptr;
+    int* tile = nullptr;
     int rc = PIC_OK;
     cudaError_t e = cudaSuccess;
     auto A = [&](cudaError_t r) {
@@ -1012,52 +1058,59 @@ int sort_into_bins(MixedState* m, int g, int par, int s, PartArrays S, long long
     };
     A(dalloc(&cellcnt, (size_t)G.ncell));
     A(dalloc(&bincnt, (size_t)ntiles));
-    A(dalloc(&binstart, (size_t)ntiles + 1));
-    A(dalloc(&k0, (size_t)n));
-    A(dalloc(&k1, (size_t)n));
-    A(dalloc(&i0, (size_t)n));
-    A(dalloc(&i1, (size_t)n));
+    A(dalloc(&maxrank, 1));
+    A(dalloc(&key, (size_t)n));
+    A(dalloc(&tile, (size_t)n));
     if (e == cudaSuccess) {
         A(cudaMemsetAsync(cellcnt, 0, G.ncell * sizeof(unsigned), st));
         A(cudaMemsetAsync(bincnt, 0, ntiles * sizeof(int), st));
-        if (n) k_keys<<<grid1(n), 256, 0, st>>>(n, G, S.cij, cellcnt, bincnt, k0, i0);
+        A(cudaMemsetAsync(maxrank, 0, sizeof(unsigned), st));
+        if (n) k_rank<<<grid1(n), 256, 0, st>>>(n, G, S.cij, cellcnt, bincnt, maxrank, key, tile);
         A(cudaGetLastError());
     }
     std::vector<int> hcnt(ntiles);
+    unsigned int hmax = 0;
     if (e == cudaSuccess) {
         A(cudaMemcpyAsync(hcnt.data(), bincnt, ntiles * sizeof(int), cudaMemcpyDeviceToHost, st));
+        A(cudaMemcpyAsync(&hmax, maxrank, sizeof hmax, cudaMemcpyDeviceToHost, st));
         A(cudaStreamSynchronize(st));
     }
     if (e == cudaSuccess) {
         long long mx = 0;
-        std::vector<long long> start(ntiles + 1, 0);
-        for (int t = 0; t < ntiles; t++) {
-            mx = std::max<long long>(mx, hcnt[t]);
-            start[t + 1] = start[t] + hcnt[t];
-        }
+        for (int t = 0; t < ntiles; t++) mx = std::max<long long>(mx, hcnt[t]);
         if (need) *need = mx;
+        const long long cpt = (long long)G.tx * G.ty;
         if (mx > G.cap) {
             rc = PIC_ENOMEM;  // caller grows the bins and retries
+        } else if ((long long)hmax + 1 > (long long)(0xffffffffu / cpt)) {
+            err = "a cell holds too many particles of one species for the bin keys";
+            rc = PIC_EINVAL;  // (not PIC_ENOMEM: larger bins would not help)
         } else {
-            A(cudaMemcpyAsync(binstart, start.data(), (ntiles + 1) * sizeof(long long),
-                              cudaMemcpyHostToDevice, st));
-            cub::DoubleBuffer<unsigned long long> kb(k0, k1);
-            cub::DoubleBuffer<unsigned int> vb(i0, i1);
-            int endbit = 32;
-            while ((1ll << (endbit - 32)) < ntiles) endbit++;
-            A(cub::DeviceRadixSort::SortPairs(nullptr, tmpb, kb, vb, (int)n, 0, endbit, st));
-            A(dalloc((char**)&tmp, tmpb));
-            if (e == cudaSuccess && n)
-                A(cub::DeviceRadixSort::SortPairs(tmp, tmpb, kb, vb, (int)n, 0, endbit, st));
-            if (e == cudaSuccess && n)
-                k_scatter<<<grid1(n), 256, 0, st>>>(n, G, s, kb.Current(), vb.Current(), binstart, S,
-                                                    m->buf[par]);
-            k_set_counts<<<grid1(ntiles), 256, 0, st>>>(ntiles, s, bincnt, cnt_of(m, par, g));
-            A(cudaGetLastError());
-            A(cudaStreamSynchronize(st));
+            // a tile's keys are rank * cells + cell: ranks 0 .. hmax. Tiles go in groups
+            // whose bitmaps fit a fixed budget (one group unless cells are very uneven).
+            const long long words = ((long long)(hmax + 1) * cpt + 31) / 32;
+            const long long budget = 64ll << 20;  // bitmap words per group (256 MB)
+            const int group = (int)std::max(1ll, std::min<long long>(ntiles, budget / words));
+            A(dalloc(&bits, (size_t)group * words));
+            A(dalloc(&pref, (size_t)group * words));
+            for (int t0 = 0; t0 < ntiles && e == cudaSuccess; t0 += group) {
+                const int ntg = std::min(group, ntiles - t0);
+                A(cudaMemsetAsync(bits, 0, (size_t)ntg * words * sizeof(unsigned), st));
+                if (n) k_setbits<<<grid1(n), 256, 0, st>>>(n, key, tile, t0, ntg, words, bits);
+                k_scanbits<<<(unsigned)ntg, 256, 0, st>>>(words, bits, pref);
+                if (n)
+                    k_scatter<<<grid1(n), 256, 0, st>>>(n, G, s, key, tile, t0, ntg, words, bits, pref, S,
+                                                        m->buf[par]);
+                A(cudaGetLastError());
+            }
+            if (e == cudaSuccess) {
+                k_set_counts<<<grid1(ntiles), 256, 0, st>>>(ntiles, s, bincnt, cnt_of(m, par, g));
+                A(cudaGetLastError());
+                A(cudaStreamSynchronize(st));
+            }
         }
     }
-    void* ps[] = {cellcnt, bincnt, binstart, k0, k1, i0, i1, tmp};
+    void* ps[] = {cellcnt, bincnt, maxrank, key, tile, bits, pref};
     for (void* p : ps)
         if (p) cudaFree(p);
     if (e != cudaSuccess) {
