@@ -148,10 +148,22 @@ k_rhs(const GridDev* __restrict__ grids, const int* __restrict__ blk_grid, int n
       int nblk_total, long long ntot, const double* __restrict__ F, const JT* __restrict__ J,
       double* __restrict__ x, double* __restrict__ r, CgState* cg, double* part,
       unsigned int* done, DevStatus* st, cudaGraphConditionalHandle cond, int use_cond,
-      double* __restrict__ bout) {
+      double* __restrict__ bout, float* __restrict__ r32) {
     const int g = blk_grid[blockIdx.x];
     const GridDev& G = grids[g];
     double v[4] = {0.0, 0.0, 0.0, 0.0};  // b.b, r.r, |E|^2, |B|^2
+    // Constants folded so that each term is one multiply-add on this part's slow FP64 pipe:
+    //   b = ax (nbx(B) - 2 B) + ay (B_n + B_s - 2 B) + kj (curl J) - dt (curl E)
+    // with ax = theta dt^2 / dx^2, ay = theta dt^2 / dy^2 (the Laplacian's differences are
+    // formed first, so a uniform field gives exactly zero), and the current's differences
+    // (exact integer differences of the fixed-point words) scaled by kj = 4 pi theta dt^2
+    // times the fixed-point unit over dx or dy.
+    const double th_dt2 = G.theta * G.dt * G.dt;
+    const double ax = th_dt2 * G.idx * G.idx, ay = th_dt2 * G.idy * G.idy;
+    // (the fixed-point unit jinv is 1 for an FP64 current)
+    const double ji = (sizeof(JT) == 8 && JT(1) / JT(2) == JT(0)) ? G.jinv : 1.0;
+    const double kjx = 4.0 * kPi * th_dt2 * ji * G.idx, kjy = 4.0 * kPi * th_dt2 * ji * G.idy;
+    const double dtx = G.dt * G.idx, dty = G.dt * G.idy;
     if (!st->stop) FOR_CELLS(G, g, c) {
         const double* Ex = F;
         const double* Ey = F + ntot;
@@ -159,54 +171,49 @@ k_rhs(const GridDev* __restrict__ grids, const int* __restrict__ blk_grid, int n
         const JT* Jx = J;
         const JT* Jy = J + ntot;
         const JT* Jz = J + 2 * ntot;
-        const double th_dt2 = G.theta * G.dt * G.dt;
-        const double idx = G.idx, idy = G.idy;
-        // curl E and curl J on the B lattices
+        // dt curl E and theta dt^2 4 pi curl J on the B lattices
         const double ez = Ez[c.k];
-        const double cEx = (Ez[c.kn] - ez) * idy;
-        const double cEy = -(east_odd(Ez, c) - ez) * idx;
-        const double cEz = (east_odd(Ey, c) - Ey[c.k]) * idx - (Ex[c.kn] - Ex[c.k]) * idy;
-        // (the fixed-point unit jinv is 1 for an FP64 current)
-        const double ji = (sizeof(JT) == 8 && JT(1) / JT(2) == JT(0)) ? G.jinv : 1.0;
-        const double jx_ = ji * idx, jy_ = ji * idy;
-        double cJx, cJy, cJz;
+        const double eEx = dty * (Ez[c.kn] - ez);
+        const double eEy = -dtx * (east_odd(Ez, c) - ez);
+        const double eEz = fma(dtx, east_odd(Ey, c) - Ey[c.k], -dty * (Ex[c.kn] - Ex[c.k]));
+        double jJx, jJy, jJz;
         if (!G.walls) {
-            cJx = dld(Jz, c.kn, c.k, jy_);
-            cJy = -dld(Jz, c.ke, c.k, jx_);
-            cJz = dld(Jy, c.ke, c.k, jx_) - dld(Jx, c.kn, c.k, jy_);
+            jJx = dld(Jz, c.kn, c.k, kjy);
+            jJy = -dld(Jz, c.ke, c.k, kjx);
+            jJz = dld(Jy, c.ke, c.k, kjx) - dld(Jx, c.kn, c.k, kjy);
         } else {
             // the conductor carries the current of its wall nodes: Jy = Jz = 0 there
             const bool w0 = c.i == 0;
-            const double jzc = w0 ? 0.0 : ld(Jz, c.k, ji), jzn = w0 ? 0.0 : ld(Jz, c.kn, ji);
-            const double jze = c.ew ? 0.0 : ld(Jz, c.ke, ji);
-            const double jyc = w0 ? 0.0 : ld(Jy, c.k, ji), jye = c.ew ? 0.0 : ld(Jy, c.ke, ji);
-            cJx = (jzn - jzc) * idy;
-            cJy = -(jze - jzc) * idx;
-            cJz = (jye - jyc) * idx - (ld(Jx, c.kn, ji) - ld(Jx, c.k, ji)) * idy;
+            const double jzc = w0 ? 0.0 : ld(Jz, c.k, 1.0), jzn = w0 ? 0.0 : ld(Jz, c.kn, 1.0);
+            const double jze = c.ew ? 0.0 : ld(Jz, c.ke, 1.0);
+            const double jyc = w0 ? 0.0 : ld(Jy, c.k, 1.0), jye = c.ew ? 0.0 : ld(Jy, c.ke, 1.0);
+            jJx = (jzn - jzc) * kjy;
+            jJy = -(jze - jzc) * kjx;
+            jJz = (jye - jyc) * kjx - (ld(Jx, c.kn, 1.0) - ld(Jx, c.k, 1.0)) * kjy;
         }
-        const double cE[3] = {cEx, cEy, cEz};
-        const double cJ[3] = {cJx, cJy, cJz};
-        const double idx2 = idx * idx, idy2 = idy * idy;
+        const double eE[3] = {eEx, eEy, eEz};
+        const double jJ[3] = {jJx, jJy, jJz};
 #pragma unroll
         for (int a = 0; a < 3; a++) {
             const double* B = F + (3 + a) * ntot;
             const double bc = B[c.k];
-            const double lap = (nbx(B, c, a) - 2.0 * bc) * idx2 + (B[c.kn] - 2.0 * bc + B[c.ks]) * idy2;
-            const double b = th_dt2 * (lap + 4.0 * kPi * cJ[a]) - G.dt * cE[a];
+            const double b2 = bc + bc;
+            const double b = fma(ax, nbx(B, c, a) - b2, fma(ay, (B[c.kn] + B[c.ks]) - b2, jJ[a] - eE[a]));
             double res = b;
             const long long o = a * ntot;
             if (G.warm == 1) {  // previous step's dB as the initial guess
                 const double* X = x + o;
                 const double Ax = G.c0 * X[c.k] - G.cx * nbx(X, c, a) - G.cy * (X[c.kn] + X[c.ks]);
                 res = b - Ax;
+                v[1] = fma(res, res, v[1]);
             }
             r[o + c.k] = res;
+            if (r32) r32[o + c.k] = (float)res;  // FP32 copy for the cooperative solve
             if (bout) bout[o + c.k] = b;
-            v[0] += b * b;
-            v[1] += res * res;
-            v[3] += bc * bc;
+            v[0] = fma(b, b, v[0]);
+            v[3] = fma(bc, bc, v[3]);
         }
-        v[2] += Ex[c.k] * Ex[c.k] + Ey[c.k] * Ey[c.k] + ez * ez;
+        v[2] = fma(Ex[c.k], Ex[c.k], fma(Ey[c.k], Ey[c.k], fma(ez, ez, v[2])));
     }
     double tot[4];
     if (!reduce_and_finish<4>(G, g, v, part, nblk_total, done, tot)) return;
@@ -216,11 +223,11 @@ k_rhs(const GridDev* __restrict__ grids, const int* __restrict__ blk_grid, int n
         s.ue = tot[2] * e;
         s.ub = tot[3] * e;
         s.bb = tot[0];
-        s.rr = tot[1];
+        s.rr = G.warm == 1 ? tot[1] : tot[0];  // r = b unless the previous dB is the guess
         s.beta = 0.0;
         s.iters = 0;
         s.outer = 0;
-        s.rel = tot[0] > 0.0 ? sqrt(tot[1] / tot[0]) : 0.0;
+        s.rel = tot[0] > 0.0 ? sqrt(s.rr / tot[0]) : 0.0;
         s.active = (!st->stop && tot[0] > 0.0 && s.rel > G.rtol) ? 1 : 0;
     }
     finish_all_grids(ngrids, ngrids, cg, st, cond, use_cond);
@@ -345,19 +352,19 @@ k_update_E(const GridDev* __restrict__ grids, const int* __restrict__ blk_grid, 
     auto hx = [&](long long k) { return Bx[k] + th * Xx[k]; };
     auto hy = [&](long long k) { return By[k] + th * Xy[k]; };
     auto hz = [&](long long k) { return Bz[k] + th * Xz[k]; };
-    const double f = 4.0 * kPi * G.dt;
+    // (constants folded: each term is one multiply-add on this part's slow FP64 pipe)
+    const double fj = 4.0 * kPi * G.dt * ((sizeof(JT) == 8 && JT(1) / JT(2) == JT(0)) ? G.jinv : 1.0);
+    const double dtx = G.dt * G.idx, dty = G.dt * G.idy;
     FOR_CELLS(G, g, c) {
         const double hzc = hz(c.k);
-        const double cx = (hzc - hz(c.ks)) * G.idy;
-        const double cy = -(hzc - hz(c.ww ? c.k : c.kw)) * G.idx;  // Bz, By even at a wall
-        const double cz = (hy(c.k) - hy(c.ww ? c.k : c.kw)) * G.idx - (hx(c.k) - hx(c.ks)) * G.idy;
-        F[c.k] += G.dt * cx - f * ld(J, c.k, G.jinv);
+        const long long kw = c.ww ? c.k : c.kw;  // Bz, By even at a wall
+        F[c.k] += fma(dty, hzc - hz(c.ks), -fj * (double)J[c.k]);
         if (c.ww) {  // the conductor keeps Ey = Ez = 0 on the wall
             F[ntot + c.k] = 0.0;
             F[2 * ntot + c.k] = 0.0;
         } else {
-            F[ntot + c.k] += G.dt * cy - f * ld(J, ntot + c.k, G.jinv);
-            F[2 * ntot + c.k] += G.dt * cz - f * ld(J, 2 * ntot + c.k, G.jinv);
+            F[ntot + c.k] += fma(-dtx, hzc - hz(kw), -fj * (double)J[ntot + c.k]);
+            F[2 * ntot + c.k] += fma(dtx, hy(c.k) - hy(kw), fma(-dty, hx(c.k) - hx(c.ks), -fj * (double)J[2 * ntot + c.k]));
         }
     }
 }
@@ -729,7 +736,7 @@ __global__ void __launch_bounds__(kFieldThreads)
 k_guess_residual(const GridDev* __restrict__ grids, const int* __restrict__ blk_grid, int ngrids,
                  int nblk_total, long long ntot, const double* __restrict__ b, const double* __restrict__ x,
                  double* __restrict__ r, CgState* cg, double* part, unsigned int* done, DevStatus* st,
-                 cudaGraphConditionalHandle cond, int use_cond) {
+                 cudaGraphConditionalHandle cond, int use_cond, float* __restrict__ r32) {
     const int g = blk_grid[blockIdx.x];
     const GridDev& G = grids[g];
     double v[1] = {0.0};
@@ -741,6 +748,7 @@ k_guess_residual(const GridDev* __restrict__ grids, const int* __restrict__ blk_
             const double Ax = G.c0 * X[c.k] - G.cx * nbx(X, c, a) - G.cy * (X[c.kn] + X[c.ks]);
             const double rn = b[o + c.k] - Ax;
             r[o + c.k] = rn;
+            if (r32) r32[o + c.k] = (float)rn;  // FP32 copy for the cooperative solve
             v[0] += rn * rn;
         }
     }
@@ -759,7 +767,7 @@ k_guess_residual(const GridDev* __restrict__ grids, const int* __restrict__ blk_
 
 void launch_guess_residual(const FieldArgs& a, cudaStream_t s) {
     k_guess_residual<<<a.nblk, kFieldThreads, 0, s>>>(a.grids, a.blk_grid, a.ngrids, a.nblk, a.ntot, a.b, a.x,
-                                                      a.r, a.cg, a.part, a.done, a.st, a.cond, a.use_cond);
+                                                      a.r, a.cg, a.part, a.done, a.st, a.cond, a.use_cond, a.r32);
 }
 
 void launch_step_begin(const FieldArgs& a, cudaStream_t s) {
@@ -776,12 +784,12 @@ void launch_rhs(const FieldArgs& a, cudaStream_t s) {
         k_rhs<long long><<<a.nblk, kFieldThreads, 0, s>>>(a.grids, a.blk_grid, a.ngrids, a.nblk,
                                                           a.ntot, a.F, a.Jfix, a.x, a.r, a.cg,
                                                           a.part, a.done, a.st, a.cond, a.use_cond,
-                                                          a.b);
+                                                          a.b, a.r32);
     else
         k_rhs<double><<<a.nblk, kFieldThreads, 0, s>>>(a.grids, a.blk_grid, a.ngrids, a.nblk,
                                                        a.ntot, a.F, a.J64, a.x, a.r, a.cg,
                                                        a.part, a.done, a.st, a.cond, a.use_cond,
-                                                       a.b);
+                                                       a.b, a.r32);
 }
 
 void launch_mp_inner_begin(const FieldArgs& a, cudaStream_t s) {

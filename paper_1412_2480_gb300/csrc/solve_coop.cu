@@ -197,23 +197,19 @@ __device__ __forceinline__ void chunk_cells(const CoopArgs& a, const ChunkC& q, 
         const long long kn = q.off + (long long)(j + 1 == q.ny ? 0 : j + 1) * q.nx + i;
         const long long ks = q.off + (long long)(j == 0 ? q.ny - 1 : j - 1) * q.nx + i;
         if constexpr (PH == kBegin) {
-            // r32 = r / rms(r) in buffer 0, e = 0, z = M r32 (neighbours scaled alike)
+            // the FP64 residual's FP32 copy (buffer 0, written with it) times the scale, a
+            // power of two (so this equals rounding r * scale), into buffer 1; e = 0;
+            // z = M r from the neighbours' copies, scaled alike
+            const float sc = (float)q.scale;
 #pragma unroll
             for (int c = 0; c < 3; c++) {
-                const double* R = a.r + c * ntot;
-                double rv[4], rn[4], rs[4];
-                ld4d(R + k, rv);
-                ld4d(R + kn, rn);
-                ld4d(R + ks, rs);
-                const auto f4 = [&](const double v[4]) {
-                    return make_float4((float)(v[0] * q.scale), (float)(v[1] * q.scale), (float)(v[2] * q.scale),
-                                       (float)(v[3] * q.scale));
-                };
-                const float4 fc = f4(rv), fn = f4(rn), fs = f4(rs);
-                float fw = (float)(__ldcg(R + kwv) * q.scale), fe = (float)(__ldcg(R + kev) * q.scale);
+                const float* R = a.r32[0] + c * ntot;
+                const auto sc4 = [sc](float4 v) { return make_float4(v.x * sc, v.y * sc, v.z * sc, v.w * sc); };
+                const float4 fc = sc4(ld4(R + k)), fn = sc4(ld4(R + kn)), fs = sc4(ld4(R + ks));
+                float fw = __ldcg(R + kwv) * sc, fe = __ldcg(R + kev) * sc;
                 wall_images(q, i, c, fc, fw, fe);
                 const float4 z = precond4(q, fc, fn, fs, fw, fe);
-                st4(a.r32[0] + c * ntot + k, fc);
+                st4(a.r32[1] + c * ntot + k, fc);
                 st4(a.z32 + c * ntot + k, z);
                 st4(a.e32 + c * ntot + k, make_float4(0.f, 0.f, 0.f, 0.f));
                 acc1 = dot4(fc, fc, acc1);
@@ -307,6 +303,8 @@ __device__ __forceinline__ void chunk_cells(const CoopArgs& a, const ChunkC& q, 
                     accd += rv[u] * rv[u];
                 }
                 st4d(a.r + c * ntot + k, rv);
+                // its FP32 copy for the next inner solve's first pass
+                st4(a.r32[0] + c * ntot + k, make_float4((float)rv[0], (float)rv[1], (float)rv[2], (float)rv[3]));
             }
         }
     }
@@ -526,10 +524,15 @@ __global__ void __launch_bounds__(kCoopThreads, 4) k_mp_coop(const CoopArgs a) {
 
     while (ok && any(false)) {
         for (int g = tid; g < a.ngrids; g += blockDim.x)
-            if (gs[g].active) gs[g].scale = sqrt(3.0 * a.grids[g].ncell / gs[g].rr);  // r32 of unit RMS
+            if (gs[g].active) {
+                // r32 of about unit RMS: the power of two in [s/2, s), s = sqrt(3 ncell / (r, r))
+                int ex;
+                frexp(sqrt(3.0 * a.grids[g].ncell / gs[g].rr), &ex);
+                gs[g].scale = ldexp(1.0, ex - 1);
+            }
         __syncthreads();
         pass(kBegin);
-        rb = 0;
+        rb = 1;  // the first pass wrote the scaled residual into buffer 1
         ok = grid_barrier(a.bar, nb, &st->sync_timeout, lim);
         if (!ok) break;
         reduce(kBegin);
