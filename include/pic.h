@@ -99,8 +99,9 @@ extern "C" {
  * rows for Bx and Neumann rows for By, Bz and stays symmetric positive definite. A
  * particle's deposit folds back at a wall as its mirror image's (Jx odd, Jy, Jz even);
  * the conductor carries the current of its wall nodes. Loaded positions must lie in
- * [0, nx dx). pic_set_fields zeroes Ey, Ez, Bx on the wall column. Not combinable with
- * PIC_WS_LEARNED (its guess is periodic). */
+ * [0, nx dx). pic_set_fields zeroes Ey, Ez, Bx on the wall column. With PIC_WS_LEARNED
+ * the network's stencil is applied to the conductor's images of the right-hand side
+ * near the walls (the network itself is trained on periodic grids). */
 #define PIC_BC_PERIODIC 0
 #define PIC_BC_WALLS 1
 

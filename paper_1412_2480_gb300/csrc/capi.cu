@@ -163,8 +163,6 @@ int validate(const pic_params* p, std::string& why) {
     }
     if (p->bin_slack < 0) return bad("bin_slack must be >= 0");
     if (p->bc_x != PIC_BC_PERIODIC && p->bc_x != PIC_BC_WALLS) return bad("bc_x must be PIC_BC_PERIODIC or PIC_BC_WALLS");
-    if (p->bc_x == PIC_BC_WALLS && p->warm_start == PIC_WS_LEARNED)
-        return bad("PIC_WS_LEARNED cannot be combined with PIC_BC_WALLS");
     if (p->inject_x0 >= 0.0) {
         if (p->bc_x != PIC_BC_WALLS) return bad("the injector needs PIC_BC_WALLS");
         if (p->inject_x0 < 2.0 * p->cfl || p->inject_x0 > p->nx) return bad("inject_x0 must lie in [2 cfl, nx]");
@@ -430,8 +428,10 @@ int capture(pic_sim* s, int mask, cudaGraph_t* gout, cudaGraphExec_t* xout) {
             // rhs -> (learned guess) -> one cooperative kernel for the whole PCG -> update
             launch_rhs(field_args(s, 0, 0), st);
             if (s->learned) {
-                launch_learned_guess(s->guess, s->dgrids, s->cg, s->ntot, s->bvec, s->x, st);
-                launch_guess_residual(field_args(s, 0, 0), st);
+                // the guess also in FP32 (into e32) and its residual in FP32: that only
+                // starts the first inner solve of the cooperative kernel
+                launch_learned_guess(s->guess, s->dgrids, s->cg, s->ntot, s->bvec, s->x, s->e32, st);
+                launch_guess_residual32(field_args(s, 0, 0), st);
             }
             e = launch_mp_coop(s->coop, field_args(s, 0, 0), st);
             if (e == cudaSuccess) launch_field_update(field_args(s, 0, 0), st);
@@ -442,7 +442,7 @@ int capture(pic_sim* s, int mask, cudaGraph_t* gout, cudaGraphExec_t* xout) {
         e = new_handle(st, &h);
         if (e == cudaSuccess) launch_rhs(field_args(s, 1, h), st);
         if (e == cudaSuccess && s->learned) {
-            launch_learned_guess(s->guess, s->dgrids, s->cg, s->ntot, s->bvec, s->x, st);
+            launch_learned_guess(s->guess, s->dgrids, s->cg, s->ntot, s->bvec, s->x, nullptr, st);
             launch_guess_residual(field_args(s, 1, h), st);
         }
         if (e == cudaSuccess && s->prm.precision == PIC_FP64) {
@@ -550,8 +550,13 @@ int run_step_direct(pic_sim* s) {
     }
     launch_rhs(a, st);
     if (s->learned) {
-        launch_learned_guess(s->guess, s->dgrids, s->cg, s->ntot, s->bvec, s->x, st);
-        launch_guess_residual(a, st);
+        if (s->use_coop) {
+            launch_learned_guess(s->guess, s->dgrids, s->cg, s->ntot, s->bvec, s->x, s->e32, st);
+            launch_guess_residual32(a, st);
+        } else {
+            launch_learned_guess(s->guess, s->dgrids, s->cg, s->ntot, s->bvec, s->x, nullptr, st);
+            launch_guess_residual(a, st);
+        }
     }
     if (s->use_coop) {
         CK(launch_mp_coop(s->coop, a, st));

@@ -430,6 +430,7 @@ __global__ void __launch_bounds__(kGuessThreads) k_guess(const GridDev* __restri
                                                          const int* __restrict__ tile_grid,
                                                          const int* __restrict__ tile_local, long long ntot,
                                                          const double* __restrict__ b, double* __restrict__ x,
+                                                         float* __restrict__ x32,
                                                          const float* __restrict__ Kg, const CgState* __restrict__ cg) {
     constexpr int WX = kGX + 2 * kGH, WY = kGY + 2 * kGH;
     __shared__ float sK[kGuessParams];
@@ -443,9 +444,12 @@ __global__ void __launch_bounds__(kGuessThreads) k_guess(const GridDev* __restri
     for (int k = tid; k < kGuessParams; k += blockDim.x) sK[k] = Kg[k];
     for (int k = tid; k < 3 * WY * WX; k += blockDim.x) {
         const int c = k / (WY * WX), r = k - c * (WY * WX), yy = r / WX, xx = r - yy * WX;
-        const int gx = ((x0 - kGH + xx) % G.nx + G.nx) % G.nx;
+        int gx = ((x0 - kGH + xx) % G.nx + G.nx) % G.nx, sgn = 1;
+        // with walls the halo holds the conductor's images of b: Bx odd on the integer-x
+        // lattice, By and Bz even on the half-integer one (the images of the field solve)
+        if (G.walls) gx = wall_col(x0 - kGH + xx, G.nx, c != 0, c == 0, sgn);
         const int gy = ((y0 - kGH + yy) % G.ny + G.ny) % G.ny;
-        sb[c][yy][xx] = (float)b[c * ntot + G.cell_off + (long long)gy * G.nx + gx];
+        sb[c][yy][xx] = sgn == 0 ? 0.f : (float)sgn * (float)b[c * ntot + G.cell_off + (long long)gy * G.nx + gx];
     }
     __syncthreads();
     const int tx = tid % kGX, ys = (tid / kGX) * kStrip;  // this thread's column and first row
@@ -481,10 +485,14 @@ __global__ void __launch_bounds__(kGuessThreads) k_guess(const GridDev* __restri
 #pragma unroll
     for (int co = 0; co < 3; co++) {
         const double bias = (double)sK[kGuessWeights + co] * rms;
+        const float biasf = (float)bias;
 #pragma unroll
         for (int r = 0; r < kStrip; r++) {
             const int j = y0 + ys + r;
-            if (j < G.ny) x[co * ntot + G.cell_off + (long long)j * G.nx + i] = (double)acc[co][r] + bias;
+            if (j >= G.ny) continue;
+            const long long o = co * ntot + G.cell_off + (long long)j * G.nx + i;
+            x[o] = (double)acc[co][r] + bias;
+            if (x32) x32[o] = acc[co][r] + biasf;  // the guess in FP32 for an FP32 residual
         }
     }
 }
@@ -703,8 +711,9 @@ void cnn_free_guess(CnnGuess* g) {
 }
 
 void launch_learned_guess(const CnnGuess& g, const GridDev* grids, const CgState* cg, long long ntot,
-                          const double* b, double* x, cudaStream_t st) {
-    k_guess<<<(unsigned)g.ntiles, kGuessThreads, 0, st>>>(grids, g.tile_grid, g.tile_local, ntot, b, x, g.K, cg);
+                          const double* b, double* x, float* x32, cudaStream_t st) {
+    k_guess<<<(unsigned)g.ntiles, kGuessThreads, 0, st>>>(grids, g.tile_grid, g.tile_local, ntot, b, x, x32, g.K,
+                                                          cg);
 }
 
 }  // namespace pic

@@ -48,6 +48,9 @@ void launch_step_end(const FieldArgs& a, cudaStream_t s);
 void launch_rhs(const FieldArgs& a, cudaStream_t s);
 // r = b - A x for an initial guess x written after launch_rhs (the learned guess).
 void launch_guess_residual(const FieldArgs& a, cudaStream_t s);
+// The same in FP32 for the cooperative solve, from the guess's FP32 copy in a.e32 into
+// a.r32 (which holds the FP32 copy of b): the first inner solve needs no more.
+void launch_guess_residual32(const FieldArgs& a, cudaStream_t s);
 // One PCG iteration: A-product and direction update, then solution/residual update.
 void launch_cg_iteration(const FieldArgs& a, cudaStream_t s);
 // E, B from Eqs. (5)-(6) with dB; FP32 copies when a.F32 is set.

@@ -763,7 +763,47 @@ k_guess_residual(const GridDev* __restrict__ grids, const int* __restrict__ blk_
     finish_all_grids(ngrids, ngrids, cg, st, cond, use_cond);
 }
 
+// The same for the cooperative solve, in FP32: r32 (the FP32 copy of b that k_rhs left)
+// minus A x0 from the guess's FP32 copy. This residual only starts the first inner FP32
+// solve; the refinement after it forms the FP64 residual of the updated solution.
+__global__ void __launch_bounds__(kFieldThreads)
+k_guess_residual32(const GridDev* __restrict__ grids, const int* __restrict__ blk_grid, int ngrids,
+                   int nblk_total, long long ntot, const float* __restrict__ x32, float* __restrict__ r32,
+                   CgState* cg, double* part, unsigned int* done, DevStatus* st, cudaGraphConditionalHandle cond,
+                   int use_cond) {
+    const int g = blk_grid[blockIdx.x];
+    const GridDev& G = grids[g];
+    const float c0 = (float)G.c0, cx = (float)G.cx, cy = (float)G.cy;
+    float acc = 0.f;
+    if (!st->stop) FOR_CELLS(G, g, c) {
+#pragma unroll
+        for (int a = 0; a < 3; a++) {
+            const long long o = a * ntot;
+            const float* X = x32 + o;
+            const float Ax = c0 * X[c.k] - cx * nbx(X, c, a) - cy * (X[c.kn] + X[c.ks]);
+            const float rn = r32[o + c.k] - Ax;
+            r32[o + c.k] = rn;
+            acc = fmaf(rn, rn, acc);
+        }
+    }
+    double v[1] = {(double)acc};
+    double tot[1];
+    if (!reduce_and_finish<1>(G, g, v, part, nblk_total, done, tot)) return;
+    if (threadIdx.x == 0) {
+        CgState& s = cg[g];
+        s.rr = tot[0];
+        s.rel = s.bb > 0.0 ? sqrt(tot[0] / s.bb) : 0.0;
+        s.active = (!st->stop && s.bb > 0.0 && s.rel > G.rtol) ? 1 : 0;
+    }
+    finish_all_grids(ngrids, ngrids, cg, st, cond, use_cond);
+}
+
 }  // namespace
+
+void launch_guess_residual32(const FieldArgs& a, cudaStream_t s) {
+    k_guess_residual32<<<a.nblk, kFieldThreads, 0, s>>>(a.grids, a.blk_grid, a.ngrids, a.nblk, a.ntot, a.e32,
+                                                        a.r32, a.cg, a.part, a.done, a.st, a.cond, a.use_cond);
+}
 
 void launch_guess_residual(const FieldArgs& a, cudaStream_t s) {
     k_guess_residual<<<a.nblk, kFieldThreads, 0, s>>>(a.grids, a.blk_grid, a.ngrids, a.nblk, a.ntot, a.b, a.x,

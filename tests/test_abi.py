@@ -96,7 +96,7 @@ def test_batch_validation_on_host():
 
 
 def test_walls_parameter_validation_on_host():
-    for kw in (dict(bc_x=2), dict(bc_x=pic.PIC_BC_WALLS, precision=pic.PIC_MIXED32,
+    for kw in (dict(bc_x=2), dict(bc_x=pic.PIC_BC_WALLS, precision=pic.PIC_FP64,
                                   warm_start=pic.PIC_WS_LEARNED)):
         with pytest.raises(pic.PicError) as e:
             pic.pic_init(pic.pic_params_default(**kw))
