@@ -337,3 +337,49 @@ def test_learned_warm_start_with_walls(trained):
     print(f"walls: PCG iterations over {steps} steps, zero guess {i0}, learned {il}")
     assert relnorm(Fl, F0s) < 1e-6
     assert il < i0
+
+
+def exact_params(rng):
+    """Weights +-1, three per output channel, placed so that every input channel of the
+    32-channel layers feeds at most three (output channel, tap) pairs; biases in
+    {-1, 0, 1}. With inputs in {-1, 0, 1} every activation is an integer below 256 and
+    every gradient a small integer: exact in BF16, and every FP32 sum is an exact integer
+    whatever its order, so the GPU and the reference must agree bit for bit."""
+    p = np.zeros(cnn.NPARAMS)
+    for (ci, co), (wo, bo) in zip(cnn.LAYERS, cnn.offsets()):
+        W = np.zeros((co, 9, ci))
+        for o in range(co):
+            taps = rng.choice(9, size=3, replace=False)
+            for k in range(3):
+                W[o, taps[k], (3 * o + k) % ci] = rng.choice([-1.0, 1.0])
+        p[wo:wo + W.size] = W.ravel()
+        p[bo:bo + co] = rng.integers(-1, 2, co)
+    return p
+
+
+@pytest.mark.parametrize("nimg,nx,ny", [(1, 16, 8), (2, 32, 8)])
+def test_network_exact_arithmetic_matches_reference_bitwise(nimg, nx, ny):
+    rng = np.random.default_rng(40 + nimg)
+    params = exact_params(rng)
+    inp = rng.integers(-1, 2, (nimg, 3, ny, nx)).astype(np.float32)
+    ref_out = cnn.forward(params, inp, quantize=True)
+    assert np.abs(ref_out).max() < 256 and np.all(ref_out == np.round(ref_out))
+    c = pic.pic_cnn_create()
+    try:
+        pic.pic_cnn_set_params(c, params.astype(np.float32))
+        out = pic.pic_cnn_forward(c, inp).astype(np.float64)
+        np.testing.assert_array_equal(out, ref_out)  # forward, element by element
+        # targets that make the loss gradient at the output exactly delta in {-1, 0, 1}:
+        # d(loss)/d(out) = 2 (out - t) / (3 P) with P the pixels of all images
+        P = nimg * nx * ny
+        delta = rng.integers(-1, 2, out.shape)
+        tgt = (ref_out - 1.5 * P * delta).astype(np.float32)
+        g, loss = pic.pic_cnn_gradient(c, inp, tgt)
+    finally:
+        pic.pic_cnn_free(c)
+    L_ref, g_ref = cnn.loss_and_grad(params, inp, tgt.astype(np.float64), quantize=True)
+    assert np.all(g_ref == np.round(g_ref)) and np.abs(g_ref).max() < 2 ** 24
+    # weight and bias gradients of all four layers (the input gradients of layers 4, 3, 2
+    # feed them), element by element
+    np.testing.assert_array_equal(g.astype(np.float64), g_ref)
+    assert loss == pytest.approx(L_ref, rel=1e-14)
