@@ -428,9 +428,10 @@ int capture(pic_sim* s, int mask, cudaGraph_t* gout, cudaGraphExec_t* xout) {
             // rhs -> (learned guess) -> one cooperative kernel for the whole PCG -> update
             launch_rhs(field_args(s, 0, 0), st);
             if (s->learned) {
-                // the guess also in FP32 (into e32) and its residual in FP32: that only
-                // starts the first inner solve of the cooperative kernel
-                launch_learned_guess(s->guess, s->dgrids, s->cg, s->ntot, s->bvec, s->x, s->e32, st);
+                // the guess from b's FP32 copy, into the FP64 solution (the refinements'
+                // base) and an FP32 copy (in e32) for its residual, formed in FP32: that
+                // residual only starts the first inner solve
+                launch_learned_guess(s->guess, s->dgrids, s->cg, s->ntot, s->bvec, s->r32, s->x, s->e32, st);
                 launch_guess_residual32(field_args(s, 0, 0), st);
             }
             e = launch_mp_coop(s->coop, field_args(s, 0, 0), st);
@@ -442,7 +443,7 @@ int capture(pic_sim* s, int mask, cudaGraph_t* gout, cudaGraphExec_t* xout) {
         e = new_handle(st, &h);
         if (e == cudaSuccess) launch_rhs(field_args(s, 1, h), st);
         if (e == cudaSuccess && s->learned) {
-            launch_learned_guess(s->guess, s->dgrids, s->cg, s->ntot, s->bvec, s->x, nullptr, st);
+            launch_learned_guess(s->guess, s->dgrids, s->cg, s->ntot, s->bvec, nullptr, s->x, nullptr, st);
             launch_guess_residual(field_args(s, 1, h), st);
         }
         if (e == cudaSuccess && s->prm.precision == PIC_FP64) {
@@ -551,10 +552,10 @@ int run_step_direct(pic_sim* s) {
     launch_rhs(a, st);
     if (s->learned) {
         if (s->use_coop) {
-            launch_learned_guess(s->guess, s->dgrids, s->cg, s->ntot, s->bvec, s->x, s->e32, st);
+            launch_learned_guess(s->guess, s->dgrids, s->cg, s->ntot, s->bvec, s->r32, s->x, s->e32, st);
             launch_guess_residual32(a, st);
         } else {
-            launch_learned_guess(s->guess, s->dgrids, s->cg, s->ntot, s->bvec, s->x, nullptr, st);
+            launch_learned_guess(s->guess, s->dgrids, s->cg, s->ntot, s->bvec, nullptr, s->x, nullptr, st);
             launch_guess_residual(a, st);
         }
     }

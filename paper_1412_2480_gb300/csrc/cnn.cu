@@ -429,8 +429,8 @@ constexpr int kGuessThreads = kGX * (kGY / kStrip);
 __global__ void __launch_bounds__(kGuessThreads) k_guess(const GridDev* __restrict__ grids,
                                                          const int* __restrict__ tile_grid,
                                                          const int* __restrict__ tile_local, long long ntot,
-                                                         const double* __restrict__ b, double* __restrict__ x,
-                                                         float* __restrict__ x32,
+                                                         const double* __restrict__ b, const float* __restrict__ b32,
+                                                         double* __restrict__ x, float* __restrict__ x32,
                                                          const float* __restrict__ Kg, const CgState* __restrict__ cg) {
     constexpr int WX = kGX + 2 * kGH, WY = kGY + 2 * kGH;
     __shared__ float sK[kGuessParams];
@@ -449,7 +449,8 @@ __global__ void __launch_bounds__(kGuessThreads) k_guess(const GridDev* __restri
         // lattice, By and Bz even on the half-integer one (the images of the field solve)
         if (G.walls) gx = wall_col(x0 - kGH + xx, G.nx, c != 0, c == 0, sgn);
         const int gy = ((y0 - kGH + yy) % G.ny + G.ny) % G.ny;
-        sb[c][yy][xx] = sgn == 0 ? 0.f : (float)sgn * (float)b[c * ntot + G.cell_off + (long long)gy * G.nx + gx];
+        const long long o = c * ntot + G.cell_off + (long long)gy * G.nx + gx;
+        sb[c][yy][xx] = sgn == 0 ? 0.f : (float)sgn * (b32 ? b32[o] : (float)b[o]);
     }
     __syncthreads();
     const int tx = tid % kGX, ys = (tid / kGX) * kStrip;  // this thread's column and first row
@@ -491,7 +492,7 @@ __global__ void __launch_bounds__(kGuessThreads) k_guess(const GridDev* __restri
             const int j = y0 + ys + r;
             if (j >= G.ny) continue;
             const long long o = co * ntot + G.cell_off + (long long)j * G.nx + i;
-            x[o] = (double)acc[co][r] + bias;
+            if (x) x[o] = (double)acc[co][r] + bias;
             if (x32) x32[o] = acc[co][r] + biasf;  // the guess in FP32 for an FP32 residual
         }
     }
@@ -711,9 +712,9 @@ void cnn_free_guess(CnnGuess* g) {
 }
 
 void launch_learned_guess(const CnnGuess& g, const GridDev* grids, const CgState* cg, long long ntot,
-                          const double* b, double* x, float* x32, cudaStream_t st) {
-    k_guess<<<(unsigned)g.ntiles, kGuessThreads, 0, st>>>(grids, g.tile_grid, g.tile_local, ntot, b, x, x32, g.K,
-                                                          cg);
+                          const double* b, const float* b32, double* x, float* x32, cudaStream_t st) {
+    k_guess<<<(unsigned)g.ntiles, kGuessThreads, 0, st>>>(grids, g.tile_grid, g.tile_local, ntot, b, b32, x, x32,
+                                                          g.K, cg);
 }
 
 }  // namespace pic

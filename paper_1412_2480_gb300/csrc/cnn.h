@@ -37,10 +37,10 @@ int cnn_make_guess(const pic_cnn* net, const GridDev* hgrids, int ngrids, CnnGue
 void cnn_free_guess(CnnGuess* g);
 
 // Enqueue x0 = K * b + bias rms(b) for every simulation (rms over its 3 ncell values of
-// b, from cg[g].bb): the network's output for input b / rms(b), scaled back by rms(b),
-// into x (FP64) and, when x32 is set, also into x32 (FP32). With walls the stencil sees
-// the conductor's images of b.
+// b, from cg[g].bb): the network's output for input b / rms(b), scaled back by rms(b).
+// b is read from b32 (an FP32 copy) when set, else from b; x0 goes to x (FP64) and/or
+// x32 (FP32), whichever is set. With walls the stencil sees the conductor's images of b.
 void launch_learned_guess(const CnnGuess& g, const GridDev* grids, const CgState* cg, long long ntot,
-                          const double* b, double* x, float* x32, cudaStream_t st);
+                          const double* b, const float* b32, double* x, float* x32, cudaStream_t st);
 
 }  // namespace pic
