@@ -261,6 +261,7 @@ def make_inputs(rows, pinned=False):
 
 
 NO_GRAPH = False  # --no-graph: direct launches (profilers skip kernels of conditional graphs)
+NO_COOP = False   # --no-coop: the MIXED32 solve as separate kernels, not one cooperative launch
 
 
 def params_of(rows, precision):
@@ -272,6 +273,7 @@ def params_of(rows, precision):
             kw = dict(bc_x=pic.PIC_BC_WALLS, inject_x0=r["inject_x0"], u_th=r["u_th"], seed=r["inj_seed"])
         flags = (pic.PIC_NO_GRAPH if NO_GRAPH else 0) | (pic.PIC_EXPLICIT if r.get("explicit") else 0)
         flags |= pic.PIC_GATHER_NODAL if r.get("nodal") else 0
+        flags |= pic.PIC_NO_COOP if NO_COOP else 0
         if r.get("learned") and precision == pic.PIC_MIXED32:
             kw["warm_start"] = pic.PIC_WS_LEARNED
         out.append(pic.pic_params_default(nx=r["nx"], ny=r["ny"], cfl=r["cfl"], theta=r["theta"],
@@ -639,10 +641,13 @@ def main():
                     help="skip the comparison of the solve's initial guesses (zero, previous dB, learned)")
     ap.add_argument("--no-graph", action="store_true",
                     help="launch kernels directly (for profiler launch lists), not a bench number")
+    ap.add_argument("--no-coop", action="store_true",
+                    help="run the MIXED32 solve as separate kernels (the comparison path)")
     args = ap.parse_args()
     args.warmup = max(args.warmup, 3)
-    global NO_GRAPH
+    global NO_GRAPH, NO_COOP
     NO_GRAPH = args.no_graph
+    NO_COOP = args.no_coop
 
     world = int(os.environ.get("WORLD_SIZE", "1"))
     rank = int(os.environ.get("RANK", "0"))
@@ -713,7 +718,8 @@ def main():
         "config": {"workload": describe(args.workload),
                    "form": ("MIXED32 (int cell + FP32 offset; FP32 gather/push/deposit; "
                             + ("FP64 explicit field update)" if args.workload in EXPLICIT else
-                               "FP64 field update and PCG residual with FP32 inner CG)")) if mixed else "FP64",
+                               "FP64 field update and PCG residual with FP32 inner CG)")
+                            + (", solve as separate kernels" if NO_COOP else "")) if mixed else "FP64",
                    "l2": "inputs larger than L2 (particle state 1.6 GB MIXED32 / 2.7 GB FP64 for cfg2, "
                          "2.1 GB for scan48)",
                    "replicas": world},
