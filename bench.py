@@ -262,6 +262,7 @@ def make_inputs(rows, pinned=False):
 
 NO_GRAPH = False  # --no-graph: direct launches (profilers skip kernels of conditional graphs)
 NO_COOP = False   # --no-coop: the MIXED32 solve as separate kernels, not one cooperative launch
+CG_INNER = False  # --cg-inner: the inner FP32 solve by CG instead of the Chebyshev tiles
 
 
 def params_of(rows, precision):
@@ -274,6 +275,7 @@ def params_of(rows, precision):
         flags = (pic.PIC_NO_GRAPH if NO_GRAPH else 0) | (pic.PIC_EXPLICIT if r.get("explicit") else 0)
         flags |= pic.PIC_GATHER_NODAL if r.get("nodal") else 0
         flags |= pic.PIC_NO_COOP if NO_COOP else 0
+        flags |= pic.PIC_CG_INNER if CG_INNER else 0
         if r.get("learned") and precision == pic.PIC_MIXED32:
             kw["warm_start"] = pic.PIC_WS_LEARNED
         out.append(pic.pic_params_default(nx=r["nx"], ny=r["ny"], cfl=r["cfl"], theta=r["theta"],
@@ -643,11 +645,14 @@ def main():
                     help="launch kernels directly (for profiler launch lists), not a bench number")
     ap.add_argument("--no-coop", action="store_true",
                     help="run the MIXED32 solve as separate kernels (the comparison path)")
+    ap.add_argument("--cg-inner", action="store_true",
+                    help="MIXED32 inner solve by CG instead of the Chebyshev tiles (the comparison path)")
     args = ap.parse_args()
     args.warmup = max(args.warmup, 3)
-    global NO_GRAPH, NO_COOP
+    global NO_GRAPH, NO_COOP, CG_INNER
     NO_GRAPH = args.no_graph
     NO_COOP = args.no_coop
+    CG_INNER = args.cg_inner
 
     world = int(os.environ.get("WORLD_SIZE", "1"))
     rank = int(os.environ.get("RANK", "0"))
@@ -719,7 +724,8 @@ def main():
                    "form": ("MIXED32 (int cell + FP32 offset; FP32 gather/push/deposit; "
                             + ("FP64 explicit field update)" if args.workload in EXPLICIT else
                                "FP64 field update and PCG residual with FP32 inner CG)")
-                            + (", solve as separate kernels" if NO_COOP else "")) if mixed else "FP64",
+                            + (", solve as separate kernels" if NO_COOP else "")
+                            + (", inner CG" if CG_INNER or NO_COOP else ", inner Chebyshev tiles")) if mixed else "FP64",
                    "l2": "inputs larger than L2 (particle state 1.6 GB MIXED32 / 2.7 GB FP64 for cfg2, "
                          "2.1 GB for scan48)",
                    "replicas": world},

@@ -40,6 +40,7 @@ PIC_NO_GRAPH = 2
 PIC_NO_COOP = 4
 PIC_EXPLICIT = 8
 PIC_GATHER_NODAL = 16
+PIC_CG_INNER = 32
 PIC_BC_PERIODIC = 0
 PIC_BC_WALLS = 1
 PIC_EX, PIC_EY, PIC_EZ, PIC_BX, PIC_BY, PIC_BZ = range(6)

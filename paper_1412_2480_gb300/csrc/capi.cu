@@ -744,6 +744,8 @@ int finish_call(pic_sim* s) {
 }
 
 constexpr int kMaxBatch = 4096;
+// flags that hold for a whole handle: every simulation of a batch gives the same
+constexpr int kHandleFlags = PIC_NO_GRAPH | PIC_NO_COOP | PIC_EXPLICIT | PIC_CG_INNER;
 
 int init_handle(const pic_params* prm, int n, pic_sim** out) {
     pic_sim* s = nullptr;
@@ -846,7 +848,8 @@ int init_handle(const pic_params* prm, int n, pic_sim** out) {
     if (s->F32) A(cudaMemset(s->F32, 0, 6 * s->ntot * sizeof(float)));
     if (s->Fn) A(cudaMemset(s->Fn, 0, 6 * s->ntot * sizeof(double)));
     if (prm[0].precision == PIC_MIXED32 && !(prm[0].flags & (PIC_NO_COOP | PIC_EXPLICIT))) {
-        const int rc = coop_create(&s->coop, s->hgrids.data(), s->ngrids, s->err);
+        const int rc = coop_create(&s->coop, s->hgrids.data(), s->ngrids, (prm[0].flags & PIC_CG_INNER) != 0,
+                                   s->err);
         if (rc == PIC_ECUDA) return bail(rc);
         s->use_coop = rc == PIC_OK;
     }
@@ -974,9 +977,10 @@ int pic_init_batch(const pic_params* prm, int32_t n, pic_sim** out) {
             if (prm[k].precision != PIC_MIXED32)
                 return fail(nullptr, PIC_EINVAL, "a batch of more than one simulation requires PIC_MIXED32");
         for (int k = 1; k < n; k++)
-            if ((prm[k].flags & (PIC_NO_GRAPH | PIC_EXPLICIT)) != (prm[0].flags & (PIC_NO_GRAPH | PIC_EXPLICIT)))
+            if ((prm[k].flags & kHandleFlags) != (prm[0].flags & kHandleFlags))
                 return fail(nullptr, PIC_EINVAL,
-                            "PIC_NO_GRAPH and PIC_EXPLICIT must be the same for every simulation");
+                            "PIC_NO_GRAPH, PIC_NO_COOP, PIC_EXPLICIT and PIC_CG_INNER must be the same for "
+                            "every simulation");
         for (int k = 1; k < n; k++)
             if ((prm[k].warm_start == PIC_WS_LEARNED) != (prm[0].warm_start == PIC_WS_LEARNED))
                 return fail(nullptr, PIC_EINVAL, "PIC_WS_LEARNED must be used by all simulations or none");

@@ -69,12 +69,18 @@ constexpr int kCoopMaxGrids = 64;
 struct CoopSolve {
     int2* gchunk = nullptr;       // per simulation: first chunk, chunk count
     int* chunk_grid = nullptr;    // per chunk: simulation
+    int* tile_grid = nullptr;     // per 32 x 64 Chebyshev tile: simulation
+    int2* tile_xy = nullptr;      // per tile: first cell (x, y)
     double* part = nullptr;       // 2 buffers x 2 values x nchunks chunk partial sums
     unsigned int* bar = nullptr;  // grid barrier: arrivals, generation
-    int nchunks = 0, nblocks = 0, ngrids = 0;
+    int nchunks = 0, nblocks = 0, ngrids = 0, ntiles = 0, cg_inner = 0;
+    int cheb = 0;                 // some simulation takes the Chebyshev inner solve
 };
-// PIC_OK, PIC_EINVAL (not applicable: keep the WHILE-node solve) or PIC_ECUDA.
-int coop_create(CoopSolve* cs, const GridDev* hgrids, int ngrids, std::string& err);
+// PIC_OK, PIC_EINVAL (not applicable: keep the WHILE-node solve) or PIC_ECUDA. cg_inner:
+// the inner solve is always the CG (PIC_CG_INNER).
+int coop_create(CoopSolve* cs, const GridDev* hgrids, int ngrids, bool cg_inner, std::string& err);
+// Dynamic shared memory of the cooperative solve's launch.
+size_t coop_smem(const CoopSolve& cs);
 void coop_free(CoopSolve* cs);
 // The solve after launch_rhs (and a learned guess): needs a.b, a.x, a.r and the FP32 vectors.
 cudaError_t launch_mp_coop(const CoopSolve& cs, const FieldArgs& a, cudaStream_t s);

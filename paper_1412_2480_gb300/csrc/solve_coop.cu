@@ -15,6 +15,22 @@
 // r - alpha q, both unchanged in this pass), so r' goes to the other of two residual
 // buffers and no third barrier is needed.
 //
+// Where the operator's spectrum allows it (every simulation of the batch with
+// T_13(sigma) >= 1e3 below; CFL <= 2.4 at theta = 1/2) the inner solve is instead a
+// Chebyshev iteration, done tile by tile with no grid-wide step at all: A's spectrum
+// lies in [c0 - 2 (cx + cy), c0 + 2 (cx + cy)] (Gershgorin; the interval is exact for
+// periodic boxes and holds with the wall images, which keep A symmetric positive
+// definite), so m steps of the three-term Chebyshev recurrence on that interval reduce
+// every error component by 1/T_m(sigma), sigma = c0 / (2 (cx + cy)), with no inner
+// products. Step k at a cell needs step k-1 at its four neighbours, so a tile of
+// 32 x 32 cells loaded with a halo of m - 1 cells in shared memory computes all m steps
+// by itself (the halo's outer ring goes stale one cell per step and never reaches the
+// interior) and adds its interior's correction to x. m is chosen per refinement from
+// the reduction it needs (as the CG's inner tolerance is), at most 13 (1/T_13(2) =
+// 7e-8 at CFL 1, theta 1/2, near the FP32 floor). A refinement then costs two grid
+// barriers (tiles, residual) instead of two per inner iteration. PIC_CG_INNER keeps the
+// CG.
+//
 // Work is cut into fixed chunks of 2048 cells of one simulation; a chunk's partial sums
 // are formed in a fixed order and written to its own slot, and every CTA forms each
 // simulation's sums from its chunk partials in a fixed order. Results therefore depend
@@ -38,12 +54,33 @@ constexpr int kPerThread = kChunkCells / kCoopThreads;
 constexpr int kInnerMax = 64;  // inner iterations per refinement, as in the WHILE-node solve
 constexpr int kCoopMaxChunks = 4096;  // two partials per chunk staged in shared memory: 64 KB
 
+// Chebyshev inner solve: interior tile (32 x 64 cells), most steps per solve (the
+// window's halo is kChebMaxIt - 1 cells on every side, whatever the steps), the window
+// (56 x 88 cells: 4 strips of 22 rows, one column per thread, 224 threads), its row
+// pitch and height in shared memory with a ring of zero ghost cells, one buffer's size.
+constexpr int kChebTileX = 32;
+constexpr int kChebTileY = 64;
+constexpr int kChebMaxIt = 13;
+constexpr int kChebHalo = kChebMaxIt - 1;
+constexpr int kChebW = kChebTileX + 2 * kChebHalo;
+constexpr int kChebH = kChebTileY + 2 * kChebHalo;
+constexpr int kChebStrips = 4;
+constexpr int kChebRows = kChebH / kChebStrips;
+constexpr int kChebPitch = kChebW + 2;
+constexpr int kChebCells = kChebPitch * (kChebH + 2);
+static_assert(kChebRows * kChebStrips == kChebH && kChebW * kChebStrips <= kCoopThreads, "window layout");
+constexpr double kChebFloor = 1e-7;
+constexpr double kChebWorst = 1e-3;
+
 struct CoopArgs {
     const GridDev* grids;
     int ngrids;
     const int2* gchunk;     // per simulation: first chunk, chunk count
     const int* chunk_grid;  // per chunk: simulation
     int nchunks;
+    const int* tile_grid;   // Chebyshev tiles: simulation, first cell (x, y)
+    const int2* tile_xy;
+    int ntiles;
     long long ntot;
     const double* b;
     double* x;
@@ -62,6 +99,8 @@ struct CoopArgs {
 struct GState {
     double rr, bb, scale, rr_in0, rr_in, rz, alpha, beta, tol_in, rel, rtol;
     int active, in_active, iters, in_iters, outer, maxit;
+    int cheb, m;  // inner solve by the Chebyshev iteration; its steps this refinement
+    float sig;    // c0 / (2 (cx + cy))
 };
 
 // Grid-wide barrier of a cooperative launch (all CTAs resident): arrivals on one counter
@@ -382,9 +421,112 @@ __device__ __forceinline__ void chunk_phase(const CoopArgs& a, const ChunkC& q, 
     else chunk_cells<PH, false>(a, q, acc1, acc2, accd);
 }
 
-// 4 CTAs per SM (64 registers): 608 resident CTAs, so a 2048 x 512 grid (512 chunks)
-// gives every CTA at most one chunk per phase
-__global__ void __launch_bounds__(kCoopThreads, 4) k_mp_coop(const CoopArgs a) {
+// The Chebyshev inner solve of A e = r sc (r = the FP32 copy of the residual, sc its
+// power-of-two scale) on one component of one tile, then x += e / sc on the tile's
+// interior. With theta_c = c0, delta = 2 (cx + cy), sigma = theta_c / delta (the
+// three-term recurrence of the Chebyshev iteration, e.g. Saad, Iterative Methods for
+// Sparse Linear Systems, Sec. 12.3):
+//   e_1 = d_0 = t_0 / theta_c, rho_0 = 1 / sigma, t_0 = r sc;
+//   k = 1 .. m-1:  t_k = r sc - A e_k, rho_k = 1 / (2 sigma - rho_{k-1}),
+//                  d_k = rho_k rho_{k-1} d_{k-1} + (2 rho_k / delta) t_k,  e_{k+1} = e_k + d_k.
+// The window holds the tile and kChebHalo >= m - 1 cells around it (wrapped
+// periodically; at a wall the columns beyond it are dead and the wall's images are
+// applied exactly). Thread tid < 224 owns window column tid % 56 and the 22-row strip
+// tid / 56: r sc, d and e of its cells stay in registers; e also goes to shared memory
+// each step (two buffers, one barrier per step) for the neighbouring columns and the
+// strips above and below. The ring of ghost cells around the window stays zero.
+
+// One step on a thread's strip: reads the old e of its neighbours from src, writes the
+// new e to dst (distinct buffers).
+__device__ __forceinline__ void cheb_step(const float* __restrict__ src, float* __restrict__ dst, int base,
+                                          float (&e)[kChebRows], float (&d)[kChebRows],
+                                          const float (&rs)[kChebRows], float c0f, float cxf, float cyf,
+                                          float ca, float cb, bool wl, bool wr, bool odd) {
+    float up = src[base - kChebPitch];
+#pragma unroll
+    for (int k = 0; k < kChebRows; k++) {
+        const int l = base + k * kChebPitch;
+        const float ec = e[k];
+        const float dn = k + 1 < kChebRows ? e[k + 1 < kChebRows ? k + 1 : k] : src[l + kChebPitch];
+        float wv = src[l - 1], ev = src[l + 1];
+        if (wl) wv = odd ? -ev : ec;  // conductor images: Bx odd and zero on the wall node
+        if (wr) ev = odd ? 0.f : ec;  // x = nx, By and Bz even
+        const float Ae = fmaf(c0f, ec, -fmaf(cxf, wv + ev, cyf * (up + dn)));
+        d[k] = fmaf(ca, d[k], cb * (rs[k] - Ae));
+        up = ec;
+        e[k] = ec + d[k];
+        dst[l] = e[k];
+    }
+}
+
+__device__ __forceinline__ void cheb_tile(const CoopArgs& a, const GState& s, int g, int t, int c, float* ew) {
+    const GridDev* Gp = a.grids + g;
+    const int nx = __ldg(&Gp->nx), ny = __ldg(&Gp->ny), walls = __ldg(&Gp->walls);
+    const long long off = __ldg(&Gp->cell_off);
+    const float c0f = (float)__ldg(&Gp->c0), cxf = (float)__ldg(&Gp->cx), cyf = (float)__ldg(&Gp->cy);
+    const int2 t0 = __ldg(a.tile_xy + t);
+    const int X0 = t0.x, Y0 = t0.y;
+    const int X1 = min(X0 + kChebTileX, nx), Y1 = min(Y0 + kChebTileY, ny);
+    const int m = s.m;
+    const int tid = threadIdx.x;
+    const bool act = tid < kChebW * kChebStrips;
+    const int col = tid % kChebW, strip = tid / kChebW;
+    const int r0 = strip * kChebRows;
+    const int base = (r0 + 1) * kChebPitch + col + 1;
+    const int gx = X0 - kChebHalo + col;                       // unwrapped column
+    const bool live = act && (!walls || (gx >= 0 && gx < nx));  // dead: beyond a wall
+    const bool wl = walls && gx == 0, wr = walls && gx == nx - 1;
+    int gxw = gx;
+    while (gxw < 0) gxw += nx;
+    while (gxw >= nx) gxw -= nx;
+    int gy = Y0 - kChebHalo + r0;  // first row of the strip, wrapped
+    while (gy < 0) gy += ny;
+    while (gy >= ny) gy -= ny;
+    const float sc = (float)s.scale;
+    const float sig = s.sig, delta = c0f / sig, ith = 1.f / c0f;
+    const float* Rg = a.r32[0] + c * a.ntot + off + gxw;
+    float rs[kChebRows], d[kChebRows], e[kChebRows];
+    float* ea = ew;
+    float* eb = ew + kChebCells;
+#pragma unroll
+    for (int k = 0; k < kChebRows; k++) {
+        rs[k] = live ? __ldcg(Rg + (long long)gy * nx) * sc : 0.f;
+        d[k] = rs[k] * ith;
+        e[k] = d[k];
+        if (act) ea[base + k * kChebPitch] = e[k];
+        if (++gy == ny) gy = 0;
+    }
+    __syncthreads();
+    float rho = 1.f / sig;
+    for (int it = 1; it < m; it++) {
+        const float rn = 1.f / (2.f * sig - rho);
+        const float ca = rn * rho, cb = 2.f * rn / delta;
+        rho = rn;
+        if (act) cheb_step(ea, eb, base, e, d, rs, c0f, cxf, cyf, ca, cb, wl, wr, c == 0);
+        __syncthreads();
+        float* tmp = ea;
+        ea = eb;
+        eb = tmp;
+    }
+    // interior: x += e / sc (FP64; 1 / sc is a power of two, exact in FP32)
+    if (act && gx >= X0 && gx < X1) {
+        const float invf = (float)(1.0 / s.scale);
+        double* Xc = a.x + c * a.ntot + off + gx;
+        const int y0 = Y0 - kChebHalo + r0;
+#pragma unroll
+        for (int k = 0; k < kChebRows; k++) {
+            const int y = y0 + k;
+            if (y >= Y0 && y < Y1) Xc[(long long)y * nx] += (double)(e[k] * invf);
+        }
+    }
+    __syncthreads();  // the window is reused by the next item
+}
+
+// CG inner solve: 4 CTAs per SM (64 registers), 608 resident CTAs, so a 2048 x 512
+// grid (512 chunks) gives every CTA at most one chunk per phase. With Chebyshev tiles
+// (CHEB): 2 CTAs per SM, so that a thread holds its column strip in registers.
+template <bool CHEB>
+__global__ void __launch_bounds__(kCoopThreads, CHEB ? 2 : 4) k_mp_coop(const CoopArgs a) {
     __shared__ GState gs[kCoopMaxGrids];
     __shared__ double red[32];
     extern __shared__ double sp[];  // 2 x nchunks staged partial sums
@@ -404,14 +546,33 @@ __global__ void __launch_bounds__(kCoopThreads, 4) k_mp_coop(const CoopArgs a) {
         s.outer = 0;
         s.rtol = a.grids[g].rtol;
         s.maxit = a.grids[g].maxit;
+        const double c0 = a.grids[g].c0, dl = 2.0 * (a.grids[g].cx + a.grids[g].cy);
+        const double sig = dl > 0.0 ? c0 / dl : 0.0;
+        // Chebyshev when 13 steps reduce the error by kChebWorst at least (T_13(sigma) =
+        // cosh(13 acosh sigma) >= 1 / kChebWorst) and the tiles cover the simulation
+        s.cheb = CHEB && sig > 1.0 && kChebMaxIt * acosh(sig) >= acosh(1.0 / kChebWorst);
+        s.sig = (float)sig;
+        s.m = 0;
         gs[g] = s;
     }
     __syncthreads();
+    // window of the Chebyshev tiles after the staged partial sums: two e buffers whose
+    // ghost rings stay zero (the steps write window cells only)
+    float* ew = reinterpret_cast<float*>(sp + 2 * a.nchunks);
+    if constexpr (CHEB)
+        for (int k = tid; k < 2 * kChebCells; k += blockDim.x) ew[k] = 0.f;
     int buf = 0;
     int rb = 0;  // residual buffer holding the current inner r (the same in every CTA)
     bool ok = true;
     const auto two = [](Phase ph) { return ph == kBegin || ph == kUpdate; };  // phases with two sums
 
+    // Whether simulation state s takes part in phase ph (the inner CG phases only for
+    // simulations without the Chebyshev solve).
+    const auto takes = [](Phase ph, const GState& s) {
+        if (ph == kDirection || ph == kUpdate) return s.active && s.in_active;
+        if (ph == kBegin || ph == kX) return s.active && !s.cheb;
+        return s.active != 0;
+    };
     // One pass over this CTA's chunks of the simulations taking part in `ph`, with
     // per-chunk partial sums into buffer `buf` where the phase reduces.
     auto pass = [&](Phase ph) {
@@ -419,8 +580,7 @@ __global__ void __launch_bounds__(kCoopThreads, 4) k_mp_coop(const CoopArgs a) {
         for (int ch = blockIdx.x; ch < a.nchunks; ch += nb) {
             const int g = __ldg(a.chunk_grid + ch);
             const GState& s = gs[g];
-            const bool on = (ph == kDirection || ph == kUpdate) ? (s.active && s.in_active) : s.active;
-            if (!on) continue;  // uniform over the CTA
+            if (!takes(ph, s)) continue;  // uniform over the CTA
             // per-chunk constants in registers (FP64 -> FP32 conversions run on the slow
             // FP64 pipe: once per chunk, not per cell)
             const GridDev* Gp = a.grids + g;
@@ -474,8 +634,7 @@ __global__ void __launch_bounds__(kCoopThreads, 4) k_mp_coop(const CoopArgs a) {
         stage_partials(part, two(ph) ? 2 * a.nchunks : a.nchunks, sp);
         for (int g = warp; g < a.ngrids; g += kCoopThreads / 32) {
             GState& s = gs[g];
-            const bool on = (ph == kDirection || ph == kUpdate) ? (s.active && s.in_active) : s.active;
-            if (!on) continue;
+            if (!takes(ph, s)) continue;
             const double t = chunk_sum(sp, a.gchunk[g]);
             const double t2 = two(ph) ? chunk_sum(sp + a.nchunks, a.gchunk[g]) : 0.0;
             if (lane != 0) continue;
@@ -521,16 +680,58 @@ __global__ void __launch_bounds__(kCoopThreads, 4) k_mp_coop(const CoopArgs a) {
         for (int g = 0; g < a.ngrids; g++) n += inner ? (gs[g].active && gs[g].in_active) : gs[g].active;
         return n > 0;
     };
+    auto any_mode = [&](int cheb) {
+        int n = 0;
+        for (int g = 0; g < a.ngrids; g++) n += gs[g].active && gs[g].cheb == cheb;
+        return n > 0;
+    };
 
     while (ok && any(false)) {
         for (int g = tid; g < a.ngrids; g += blockDim.x)
             if (gs[g].active) {
+                GState& s = gs[g];
                 // r32 of about unit RMS: the power of two in [s/2, s), s = sqrt(3 ncell / (r, r))
                 int ex;
-                frexp(sqrt(3.0 * a.grids[g].ncell / gs[g].rr), &ex);
-                gs[g].scale = ldexp(1.0, ex - 1);
+                frexp(sqrt(3.0 * a.grids[g].ncell / s.rr), &ex);
+                s.scale = ldexp(1.0, ex - 1);
+                s.in_active = 0;
+                if (s.cheb) {
+                    // the reduction this refinement needs (the CG's inner tolerance), in
+                    // Chebyshev steps: 1 / T_m(sigma) <= tgt
+                    const double tgt = fmax(kChebFloor, 0.5 * s.rtol * sqrt(s.bb / fmax(s.rr, 1e-300)));
+                    const int m = (int)ceil(acosh(1.0 / tgt) / acosh((double)s.sig));
+                    s.m = max(1, min(kChebMaxIt, m));
+                }
             }
         __syncthreads();
+        if (CHEB && any_mode(1)) {
+            const int nitems = 3 * a.ntiles;
+            for (int it = blockIdx.x; it < nitems; it += nb) {
+                const int t = it / 3, c = it - 3 * (it / 3);
+                const int g = __ldg(a.tile_grid + t);
+                if (!(gs[g].active && gs[g].cheb)) continue;  // uniform over the CTA
+                if constexpr (CHEB) cheb_tile(a, gs[g], g, t, c, ew);
+            }
+            for (int g = tid; g < a.ngrids; g += blockDim.x)
+                if (gs[g].active && gs[g].cheb) gs[g].iters += gs[g].m;
+            if (blockIdx.x == 0 && tid == 0) {
+                int mx = 0;
+                for (int g = 0; g < a.ngrids; g++)
+                    if (gs[g].active && gs[g].cheb) mx = max(mx, gs[g].m);
+                st->loop_iters[0] += (unsigned long long)mx;
+            }
+            __syncthreads();
+        }
+        if (!any_mode(0)) {
+            ok = grid_barrier(a.bar, nb, &st->sync_timeout, lim);
+            if (!ok) break;
+            pass(kResidual);
+            ok = grid_barrier(a.bar, nb, &st->sync_timeout, lim);
+            if (!ok) break;
+            reduce(kResidual);
+            if (blockIdx.x == 0 && tid == 0) st->loop_iters[1] += 1ull;
+            continue;
+        }
         pass(kBegin);
         rb = 1;  // the first pass wrote the scaled residual into buffer 1
         ok = grid_barrier(a.bar, nb, &st->sync_timeout, lim);
@@ -578,32 +779,63 @@ __global__ void __launch_bounds__(kCoopThreads, 4) k_mp_coop(const CoopArgs a) {
 
 }  // namespace
 
-int coop_create(CoopSolve* cs, const GridDev* hg, int ngrids, std::string& err) {
+size_t coop_smem(const CoopSolve& cs) {
+    return 2 * (size_t)cs.nchunks * sizeof(double) + (cs.cheb ? 2 * (size_t)kChebCells * sizeof(float) : 0);
+}
+
+// Whether simulation g can take the Chebyshev inner solve (as the kernel decides).
+bool cheb_ok(const GridDev& G) {
+    const double dl = 2.0 * (G.cx + G.cy);
+    const double sig = dl > 0.0 ? G.c0 / dl : 0.0;
+    return sig > 1.0 && kChebMaxIt * std::acosh(sig) >= std::acosh(1.0 / kChebWorst);
+}
+
+int coop_create(CoopSolve* cs, const GridDev* hg, int ngrids, bool cg_inner, std::string& err) {
     coop_free(cs);
     if (ngrids > kCoopMaxGrids) return PIC_EINVAL;  // the caller keeps the WHILE-node solve
     for (int g = 0; g < ngrids; g++)
         if (hg[g].nx % 4) return PIC_EINVAL;  // quads of 4 cells along x
     std::vector<int2> gc(ngrids);
     std::vector<int> cg;
+    std::vector<int> tg;
+    std::vector<int2> txy;
     for (int g = 0; g < ngrids; g++) {
         const int n = (hg[g].ncell + kChunkCells - 1) / kChunkCells;
         gc[g] = make_int2((int)cg.size(), n);
         cg.insert(cg.end(), n, g);
+        for (int y = 0; y < hg[g].ny; y += kChebTileY)
+            for (int x = 0; x < hg[g].nx; x += kChebTileX) {
+                tg.push_back(g);
+                txy.push_back(make_int2(x, y));
+            }
     }
     int dev = 0, nsm = 0, occ = 0, coop = 0;
     cudaError_t e = cudaGetDevice(&dev);
     if (e == cudaSuccess) e = cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
     if (e == cudaSuccess) e = cudaDeviceGetAttribute(&coop, cudaDevAttrCooperativeLaunch, dev);
     if ((int)cg.size() > kCoopMaxChunks) return PIC_EINVAL;
-    const size_t smem = 2 * cg.size() * sizeof(double);
-    if (e == cudaSuccess) e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k_mp_coop, kCoopThreads, smem);
-    if (e == cudaSuccess && (!coop || occ < 1)) return PIC_EINVAL;
+    cs->nchunks = (int)cg.size();
+    cs->cg_inner = cg_inner ? 1 : 0;
+    cs->cheb = 0;
+    for (int g = 0; g < ngrids && !cg_inner; g++) cs->cheb |= cheb_ok(hg[g]) ? 1 : 0;
+    const size_t smem = coop_smem(*cs);
+    const auto kern = cs->cheb ? k_mp_coop<true> : k_mp_coop<false>;
+    if (e == cudaSuccess) e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e == cudaSuccess) e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, kern, kCoopThreads, smem);
+    if (e == cudaSuccess && (!coop || occ < 1)) {
+        *cs = CoopSolve{};
+        return PIC_EINVAL;
+    }
     if (e == cudaSuccess) e = cudaMalloc(&cs->gchunk, ngrids * sizeof(int2));
     if (e == cudaSuccess) e = cudaMalloc(&cs->chunk_grid, cg.size() * sizeof(int));
+    if (e == cudaSuccess) e = cudaMalloc(&cs->tile_grid, tg.size() * sizeof(int));
+    if (e == cudaSuccess) e = cudaMalloc(&cs->tile_xy, txy.size() * sizeof(int2));
     if (e == cudaSuccess) e = cudaMalloc(&cs->part, 4 * cg.size() * sizeof(double));
     if (e == cudaSuccess) e = cudaMalloc(&cs->bar, kBarWords * sizeof(unsigned int));
     if (e == cudaSuccess) e = cudaMemcpy(cs->gchunk, gc.data(), ngrids * sizeof(int2), cudaMemcpyHostToDevice);
     if (e == cudaSuccess) e = cudaMemcpy(cs->chunk_grid, cg.data(), cg.size() * sizeof(int), cudaMemcpyHostToDevice);
+    if (e == cudaSuccess) e = cudaMemcpy(cs->tile_grid, tg.data(), tg.size() * sizeof(int), cudaMemcpyHostToDevice);
+    if (e == cudaSuccess) e = cudaMemcpy(cs->tile_xy, txy.data(), txy.size() * sizeof(int2), cudaMemcpyHostToDevice);
     if (e == cudaSuccess) e = cudaMemset(cs->bar, 0, kBarWords * sizeof(unsigned int));
     if (e != cudaSuccess) {
         err = std::string("cooperative solve set-up failed: ") + cudaGetErrorString(e);
@@ -612,13 +844,16 @@ int coop_create(CoopSolve* cs, const GridDev* hg, int ngrids, std::string& err) 
         return PIC_ECUDA;
     }
     cs->ngrids = ngrids;
-    cs->nchunks = (int)cg.size();
-    cs->nblocks = std::max(1, std::min(cs->nchunks, occ * nsm));
+    cs->ntiles = (int)tg.size();
+    // enough CTAs for the chunks (and the Chebyshev tiles' three components), no more
+    // than are resident at once
+    const int items = cs->cheb ? std::max(cs->nchunks, 3 * cs->ntiles) : cs->nchunks;
+    cs->nblocks = std::max(1, std::min(items, occ * nsm));
     return PIC_OK;
 }
 
 void coop_free(CoopSolve* cs) {
-    void* ps[] = {cs->gchunk, cs->chunk_grid, cs->part, cs->bar};
+    void* ps[] = {cs->gchunk, cs->chunk_grid, cs->tile_grid, cs->tile_xy, cs->part, cs->bar};
     for (void* p : ps)
         if (p) cudaFree(p);
     *cs = CoopSolve{};
@@ -631,6 +866,9 @@ cudaError_t launch_mp_coop(const CoopSolve& cs, const FieldArgs& f, cudaStream_t
     a.gchunk = cs.gchunk;
     a.chunk_grid = cs.chunk_grid;
     a.nchunks = cs.nchunks;
+    a.tile_grid = cs.tile_grid;
+    a.tile_xy = cs.tile_xy;
+    a.ntiles = cs.ntiles;
     a.ntot = f.ntot;
     a.b = f.b;
     a.x = f.x;
@@ -648,7 +886,7 @@ cudaError_t launch_mp_coop(const CoopSolve& cs, const FieldArgs& f, cudaStream_t
     cudaLaunchConfig_t cfg{};
     cfg.gridDim = dim3((unsigned)cs.nblocks);
     cfg.blockDim = dim3(kCoopThreads);
-    cfg.dynamicSmemBytes = 2 * (size_t)cs.nchunks * sizeof(double);
+    cfg.dynamicSmemBytes = coop_smem(cs);
     cfg.stream = s;
     cudaLaunchAttribute at[1];
     at[0].id = cudaLaunchAttributeCooperative;
@@ -659,7 +897,7 @@ cudaError_t launch_mp_coop(const CoopSolve& cs, const FieldArgs& f, cudaStream_t
     // leaves arrivals behind)
     cudaError_t e = cudaMemsetAsync(cs.bar, 0, kBarWords * sizeof(unsigned int), s);
     if (e != cudaSuccess) return e;
-    return cudaLaunchKernelEx(&cfg, k_mp_coop, a);
+    return cs.cheb ? cudaLaunchKernelEx(&cfg, k_mp_coop<true>, a) : cudaLaunchKernelEx(&cfg, k_mp_coop<false>, a);
 }
 
 }  // namespace pic

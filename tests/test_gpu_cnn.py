@@ -155,10 +155,10 @@ def pic_pairs(nsteps, nx=64, ny=64):
     return np.array(B, dtype=np.float32), np.array(X, dtype=np.float32), (w, sp, F0)
 
 
-def run_warm(ws, net, inputs, steps, nx=64, ny=64):
+def run_warm(ws, net, inputs, steps, nx=64, ny=64, flags=0):
     w, sp, F0 = inputs
     prm = pic.pic_params_default(nx=nx, ny=ny, shape_order=1, gamma0=20.0, ppc=8,
-                                 precision=pic.PIC_MIXED32, cg_rtol=1e-10, warm_start=ws)
+                                 precision=pic.PIC_MIXED32, cg_rtol=1e-10, warm_start=ws, flags=flags)
     h = pic.pic_init(prm)
     try:
         if net is not None:
@@ -256,8 +256,9 @@ def test_learned_warm_start_cuts_pcg_iterations_in_a_pic_run(trained):
     with pytest.raises(pic.PicError) as e:
         run_warm(pic.PIC_WS_LEARNED, None, inputs, 1)
     assert e.value.code == pic.PIC_ESTATE
-    it_learned, F_learned = run_warm(pic.PIC_WS_LEARNED, c, inputs, 40)
-    it_zero, F_zero = run_warm(pic.PIC_WS_ZERO, None, inputs, 40)
+    # the inner CG (PIC_CG_INNER) adapts its iterations to the smaller initial residual
+    it_learned, F_learned = run_warm(pic.PIC_WS_LEARNED, c, inputs, 40, flags=pic.PIC_CG_INNER)
+    it_zero, F_zero = run_warm(pic.PIC_WS_ZERO, None, inputs, 40, flags=pic.PIC_CG_INNER)
     print(f"PCG iterations over 40 steps: zero guess {it_zero.sum()}, learned {it_learned.sum()}; "
           f"fields differ by {relnorm(F_learned, F_zero):.2e}")
     # same solution to the solver tolerance, in fewer iterations
@@ -265,6 +266,13 @@ def test_learned_warm_start_cuts_pcg_iterations_in_a_pic_run(trained):
     # at least 10 % fewer iterations (measured 15-18 %; the exact figure varies with the
     # training, whose weight gradients are summed with unordered FP32 atomics)
     assert it_learned.sum() <= 0.90 * it_zero.sum(), (it_learned.sum(), it_zero.sum())
+    # the default Chebyshev tiles take their steps from the reduction each refinement
+    # needs: the same solution, and no more steps
+    ic_learned, Fc_learned = run_warm(pic.PIC_WS_LEARNED, c, inputs, 40)
+    ic_zero, Fc_zero = run_warm(pic.PIC_WS_ZERO, None, inputs, 40)
+    print(f"Chebyshev steps over 40 steps: zero guess {ic_zero.sum()}, learned {ic_learned.sum()}")
+    assert relnorm(Fc_learned, Fc_zero) < 1e-6 and relnorm(Fc_learned, F_learned) < 1e-6
+    assert ic_learned.sum() <= ic_zero.sum()
 
 
 def test_learned_warm_start_at_full_size_matches_oracle(trained):
@@ -314,7 +322,7 @@ def test_learned_warm_start_with_walls(trained):
     for ws in (pic.PIC_WS_ZERO, pic.PIC_WS_LEARNED):
         prm = pic.pic_params_default(nx=nx, ny=ny, shape_order=2, gamma0=20.0, ppc=ppc, u_th=1e-3,
                                      precision=pic.PIC_MIXED32, cg_rtol=1e-10, warm_start=ws,
-                                     bc_x=pic.PIC_BC_WALLS, tile_x=16, tile_y=8)
+                                     bc_x=pic.PIC_BC_WALLS, tile_x=16, tile_y=8, flags=pic.PIC_CG_INNER)
         h = pic.pic_init(prm)
         try:
             if ws == pic.PIC_WS_LEARNED:

@@ -160,10 +160,13 @@ def test_mixed_empty_and_single_species():
         check(Fg[c], Fo[c], TOL32, f"quantity {c}")
 
 
-@pytest.mark.parametrize("theta,cfl", [(0.5, 1.0), (0.75, 0.9)])
-def test_mixed_precision_field_solve_meets_fp64_tolerance(theta, cfl):
-    # The MIXED32 solve refines FP32 inner CG sweeps against the FP64 residual, so the
-    # vacuum mode must still follow the exact root of Eq. (10) to FP64 accuracy.
+@pytest.mark.parametrize("theta,cfl,flags", [(0.5, 1.0, 0), (0.75, 0.9, 0), (0.5, 1.0, pic.PIC_CG_INNER),
+                                             (1.0, 1.0, 0)])
+def test_mixed_precision_field_solve_meets_fp64_tolerance(theta, cfl, flags):
+    # The MIXED32 solve refines FP32 inner solves (Chebyshev tiles, or CG with
+    # PIC_CG_INNER; theta = 1 at CFL 1 has sigma = 9/8, beyond the Chebyshev solve's
+    # range, and takes the CG) against the FP64 residual, so the vacuum mode must still
+    # follow the exact root of Eq. (10) to FP64 accuracy.
     import math
     from closed_forms import amplification
     nx, ny, mx, my = 48, 32, 5, 3
@@ -174,24 +177,80 @@ def test_mixed_precision_field_solve_meets_fp64_tolerance(theta, cfl):
     lam = amplification(theta, cfl * math.hypot(math.sin(kx / 2), math.sin(ky / 2)))
     for n in (1, 6):
         Fg, _, mom = run_gpu(nx, ny, 1, [], F0, n, 2, cfl=cfl, theta=theta, cg_rtol=1e-13,
-                             precision=pic.PIC_MIXED32, want_particles=False)
+                             precision=pic.PIC_MIXED32, want_particles=False, flags=flags)
         np.testing.assert_allclose(Fg[5], (lam**n).real * F0[5], rtol=0, atol=1e-12)
         assert 0 < mom["cg_rel_resid"] <= 1e-13
 
 
 @pytest.mark.parametrize("order", [1, 3])
 def test_cooperative_solve_agrees_with_graph_loop_solve(order):
-    # the one-kernel cooperative PCG and the WHILE-node PCG run the same mixed-precision
-    # iteration; their reductions are partitioned differently, so they agree to the
-    # solver tolerance rather than bit for bit
+    # the one-kernel cooperative PCG (with PIC_CG_INNER) and the WHILE-node PCG run the
+    # same mixed-precision iteration; their reductions are partitioned differently, so
+    # they agree to the solver tolerance rather than bit for bit
     nx, ny, ppc = 96, 64, 3
     w, sp, F0 = workload(nx, ny, ppc, gamma0=5.0, u_th=0.2, seed=30 + order, field_amp=0.05,
                          colocated=False)
     Fc, pc, mc = run_gpu(nx, ny, ppc, sp, F0, 3, order, gamma0=5.0, cg_rtol=1e-12,
-                         precision=pic.PIC_MIXED32)
+                         precision=pic.PIC_MIXED32, flags=pic.PIC_CG_INNER)
     Fl, pl, ml = run_gpu(nx, ny, ppc, sp, F0, 3, order, gamma0=5.0, cg_rtol=1e-12,
                          precision=pic.PIC_MIXED32, flags=pic.PIC_NO_COOP)
     for c in range(12):
         assert rel(Fc[c], Fl[c]) < 1e-9, c
     assert mc["cg_rel_resid"] <= 1e-12 and ml["cg_rel_resid"] <= 1e-12
     assert abs(mc["cg_iters_total"] - ml["cg_iters_total"]) <= 3
+
+
+@pytest.mark.parametrize("nx,ny,walls", [(96, 64, False), (200, 72, False), (96, 40, True), (16, 12, False)])
+def test_chebyshev_inner_solve_agrees_with_cg(nx, ny, walls):
+    # the Chebyshev tiles and the inner CG solve the same FP64-refined system to the same
+    # FP64 tolerance, on grids with ragged tiles (200 x 72), conducting walls, and a grid
+    # smaller than one tile and its halo (16 x 12, the window wraps around it)
+    ppc, order = 3, 2
+    w, sp, F0 = workload(nx, ny, ppc, gamma0=5.0, u_th=0.2, seed=7 + nx, field_amp=0.05, colocated=False)
+    kw = dict(gamma0=5.0, cg_rtol=1e-12, precision=pic.PIC_MIXED32)
+    if walls:
+        kw["bc_x"] = pic.PIC_BC_WALLS
+        for d in sp:
+            d["x"] = np.clip(d["x"], 1e-3, nx - 1e-3)
+        F0 = F0.copy()
+        F0[1][:, 0] = F0[2][:, 0] = F0[3][:, 0] = 0.0  # Ey, Ez, Bx vanish on the wall nodes
+    Fc, pc, mc = run_gpu(nx, ny, ppc, sp, F0, 3, order, **kw)
+    Fg, pg, mg = run_gpu(nx, ny, ppc, sp, F0, 3, order, flags=pic.PIC_CG_INNER, **kw)
+    for c in range(12):
+        assert rel(Fc[c], Fg[c]) < 1e-9, c
+    assert mc["cg_rel_resid"] <= 1e-12 and mg["cg_rel_resid"] <= 1e-12
+    assert mc["cg_refinements"] >= 1 and mc["cg_iters_total"] > 0
+
+
+def test_chebyshev_inner_solve_is_independent_of_the_batch():
+    # a simulation's Chebyshev tiles read only its own cells: alone or in a batch with an
+    # unlike neighbour it gives the same fields bit for bit
+    nx, ny, ppc = 64, 64, 3
+    w, sp, F0 = workload(nx, ny, ppc, gamma0=5.0, u_th=0.2, seed=5, field_amp=0.05, colocated=False)
+    prm = [pic.pic_params_default(nx=nx, ny=ny, shape_order=2, gamma0=5.0, ppc=ppc, cg_rtol=1e-12,
+                                  precision=pic.PIC_MIXED32),
+           pic.pic_params_default(nx=96, ny=32, shape_order=1, gamma0=5.0, ppc=ppc, cg_rtol=1e-12,
+                                  precision=pic.PIC_MIXED32, cfl=0.7)]
+    out = []
+    for batch in (False, True):
+        h = pic.pic_init_batch(prm) if batch else pic.pic_init(prm[0])
+        try:
+            pic.pic_select(h, 0) if batch else None
+            for c in range(6):
+                pic.pic_set_fields(h, c, np.ascontiguousarray(F0[c]).ravel())
+            for s, d in enumerate(sp):
+                pic.pic_load_particles(h, s, d["x"], d["y"], d["ux"], d["uy"], d["uz"])
+            pic.pic_step(h, 3)
+            pic.pic_select(h, 0) if batch else None
+            out.append(np.stack([pic.fields_numpy(h, c, nx, ny) for c in range(12)]))
+        finally:
+            pic.pic_free(h)
+    assert np.array_equal(out[0], out[1])
+
+
+def test_batch_rejects_unlike_handle_flags():
+    prm = [pic.pic_params_default(nx=32, ny=32, precision=pic.PIC_MIXED32),
+           pic.pic_params_default(nx=32, ny=32, precision=pic.PIC_MIXED32, flags=pic.PIC_CG_INNER)]
+    with pytest.raises(pic.PicError) as e:
+        pic.pic_init_batch(prm)
+    assert e.value.code == pic.PIC_EINVAL
