@@ -70,6 +70,7 @@ constexpr int kChebPitch = kChebW + 2;
 constexpr int kChebCells = kChebPitch * (kChebH + 2);
 static_assert(kChebRows * kChebStrips == kChebH && kChebW * kChebStrips <= kCoopThreads, "window layout");
 constexpr double kChebFloor = 1e-7;
+constexpr double kChebRtolMin = 1e-13;  // the FP32-pair residual resolves about 1e-14 of ||b||
 constexpr double kChebWorst = 1e-3;
 
 struct CoopArgs {
@@ -100,6 +101,7 @@ struct GState {
     double rr, bb, scale, rr_in0, rr_in, rz, alpha, beta, tol_in, rel, rtol;
     int active, in_active, iters, in_iters, outer, maxit;
     int cheb, m;  // inner solve by the Chebyshev iteration; its steps this refinement
+    int dw;       // x is held as FP32 pairs in (p32, q32) until the final join
     float sig;    // c0 / (2 (cx + cy))
 };
 
@@ -166,11 +168,12 @@ __device__ __forceinline__ void stage_partials(const double* part, int n, double
     __syncthreads();
 }
 
-enum Phase { kBegin, kDirection, kUpdate, kX, kResidual };
+enum Phase { kBegin, kDirection, kUpdate, kX, kResidual, kJoin, kResidualDW };
 
 // Per-chunk constants, in registers.
 struct ChunkC {
     int nx, ny, ncell, l0, walls, rb;  // rb: residual buffer holding the current r
+    int dw;                            // x lives as FP32 pairs (a.p32, a.q32): the Chebyshev path
     long long off, ntot;
     double c0, cx, cy, scale, inv;
     float c0f, cxf, cyf, betaf, alphaf, pc0f, pcxf, pcyf;
@@ -213,6 +216,70 @@ __device__ __forceinline__ void st4d(double* p, const double v[4]) {
     reinterpret_cast<double2*>(p)[0] = make_double2(v[0], v[1]);
     reinterpret_cast<double2*>(p)[1] = make_double2(v[2], v[3]);
 }
+
+// ---- double-word (FP32 pair) arithmetic for the Chebyshev solve's FP64-class steps ----
+// GB300 retires about one FP64 operation per SM per cycle against 128 FP32 ones, so the
+// residual r = b - A x and the update x += e of the refinements run on pairs
+// (h, l) of FP32 numbers, x = h + l with |l| <= ulp(h) / 2: 47 significant bits, about
+// 7e-15 relative, far below the solver tolerances this path accepts (rtol >= 1e-13).
+// Building blocks: Knuth's TwoSum and Dekker's FastTwoSum (exact sums), the FMA-based
+// exact product, and the "sloppy" pair sum and pair-times-pair product analysed by
+// Joldes, Muller and Popescu (ACM TOMS 44, 2017). Explicit round-to-nearest intrinsics
+// keep the compiler from contracting or reassociating them.
+struct DW {
+    float h, l;
+};
+__device__ __forceinline__ DW two_sum(float a, float b) {
+    const float s = __fadd_rn(a, b), bb = __fsub_rn(s, a);
+    return {s, __fadd_rn(__fsub_rn(a, __fsub_rn(s, bb)), __fsub_rn(b, bb))};
+}
+__device__ __forceinline__ DW fast_two_sum(float a, float b) {  // |a| >= |b| (or a = 0)
+    const float s = __fadd_rn(a, b);
+    return {s, __fsub_rn(b, __fsub_rn(s, a))};
+}
+__device__ __forceinline__ DW dw_add(DW x, DW y) {
+    const DW s = two_sum(x.h, y.h);
+    return fast_two_sum(s.h, __fadd_rn(s.l, __fadd_rn(x.l, y.l)));
+}
+__device__ __forceinline__ DW dw_neg(DW x) { return {-x.h, -x.l}; }
+__device__ __forceinline__ DW dw_add_f(DW x, float y) {
+    const DW s = two_sum(x.h, y);
+    return fast_two_sum(s.h, __fadd_rn(s.l, x.l));
+}
+__device__ __forceinline__ DW dw_mul(DW x, DW y) {
+    const float p = __fmul_rn(x.h, y.h);
+    float e = __fmaf_rn(x.h, y.h, -p);
+    e = __fmaf_rn(x.h, y.l, __fmaf_rn(x.l, y.h, e));
+    return fast_two_sum(p, e);
+}
+// FP64 -> pair by bit manipulation (no FP64 instruction): h = x truncated to 24
+// significant bits, l = the next 23 bits; magnitudes below 2^-126 (and l below 2^-126)
+// flush to zero.
+__device__ __forceinline__ DW dw_from(double x) {
+    const unsigned long long b = (unsigned long long)__double_as_longlong(x);
+    const unsigned int hw = (unsigned int)(b >> 32), lw = (unsigned int)b;
+    const unsigned int sgn = hw & 0x80000000u;
+    const int E = (int)((hw >> 20) & 0x7ffu);
+    const int fe = E - 896;  // float exponent field of h (1023 - 127 = 896)
+    const float h = (fe > 0 && fe < 255)
+                        ? __uint_as_float(sgn | ((unsigned int)fe << 23) | ((hw & 0xfffffu) << 3) | (lw >> 29))
+                        : 0.f;
+    // the next 23 mantissa bits m, worth m 2^(E - 1023 - 46): exactly (2^23 + m) - 2^23
+    const float m = __fsub_rn(__uint_as_float(0x4b000000u | ((lw >> 6) & 0x7fffffu)), 8388608.f);
+    const int se = E - 1023 - 46 + 127;
+    const float l = (fe > 0 && fe < 255 && se > 0) ? __fmul_rn(m, __uint_as_float((unsigned int)se << 23)) : 0.f;
+    return fast_two_sum(h, sgn ? -l : l);
+}
+// float -> double by bit manipulation (exact; zero and subnormal inputs give zero)
+__device__ __forceinline__ double f64_of(float f) {
+    const unsigned int u = __float_as_uint(f);
+    const unsigned int e = (u >> 23) & 0xffu;
+    if (e == 0u) return 0.0;
+    const unsigned long long d = ((unsigned long long)(u & 0x80000000u) << 32) |
+                                 ((unsigned long long)(e + 896u) << 52) | ((unsigned long long)(u & 0x7fffffu) << 29);
+    return __longlong_as_double((long long)d);
+}
+__device__ __forceinline__ double dw_join(DW x) { return f64_of(x.h) + f64_of(x.l); }
 
 // One phase on the cells of a chunk this thread owns: quads of 4 cells along x (cells
 // 4 (q0 + qq 256 + tid) .. + 3 of the simulation), read and written as float4 / double2
@@ -319,6 +386,46 @@ __device__ __forceinline__ void chunk_cells(const CoopArgs& a, const ChunkC& q, 
                 xv[2] += (double)e.z * q.inv;
                 xv[3] += (double)e.w * q.inv;
                 st4d(a.x + o, xv);
+            }
+        } else if constexpr (PH == kJoin) {  // x = h + l (FP64), the solve's result
+#pragma unroll
+            for (int c = 0; c < 3; c++) {
+                const long long o = c * ntot + k;
+                const float4 h = ld4(a.p32 + o), lo = ld4(a.q32 + o);
+                const double xv[4] = {dw_join({h.x, lo.x}), dw_join({h.y, lo.y}), dw_join({h.z, lo.z}),
+                                      dw_join({h.w, lo.w})};
+                st4d(a.x + o, xv);
+            }
+        } else if constexpr (PH == kResidualDW) {  // on the pairs: r = b - A x, its FP32 copy, (r, r)
+            const DW C0 = dw_from(q.c0), CX = dw_from(q.cx), CY = dw_from(q.cy);
+#pragma unroll
+            for (int c = 0; c < 3; c++) {
+                const float* XH = a.p32 + c * ntot;
+                const float* XL = a.q32 + c * ntot;
+                const float4 hc = ld4(XH + k), lc = ld4(XL + k), hn = ld4(XH + kn), ln = ld4(XL + kn);
+                const float4 hs = ld4(XH + ks), ls = ld4(XL + ks);
+                DW xw{__ldcg(XH + kwv), __ldcg(XL + kwv)}, xe{__ldcg(XH + kev), __ldcg(XL + kev)};
+                double bv[4];
+                ld4d(a.b + c * ntot + k, bv);
+                const DW xc[4] = {{hc.x, lc.x}, {hc.y, lc.y}, {hc.z, lc.z}, {hc.w, lc.w}};
+                const DW xn[4] = {{hn.x, ln.x}, {hn.y, ln.y}, {hn.z, ln.z}, {hn.w, ln.w}};
+                const DW xs[4] = {{hs.x, ls.x}, {hs.y, ls.y}, {hs.z, ls.z}, {hs.w, ls.w}};
+                if (q.walls) {
+                    if (i == 0) xw = c == 0 ? dw_neg(xc[1]) : xc[0];
+                    if (i + 4 == q.nx) xe = c == 0 ? DW{0.f, 0.f} : xc[3];
+                }
+                float rf[4];
+#pragma unroll
+                for (int u = 0; u < 4; u++) {
+                    const DW w = u == 0 ? xw : xc[u - 1];
+                    const DW e = u == 3 ? xe : xc[u + 1];
+                    const DW off = dw_add(dw_mul(CX, dw_add(w, e)), dw_mul(CY, dw_add(xn[u], xs[u])));
+                    const DW Ax = dw_add(dw_mul(C0, xc[u]), dw_neg(off));
+                    const DW r = dw_add(dw_from(bv[u]), dw_neg(Ax));
+                    rf[u] = r.h;
+                    acc1 = fmaf(r.h, r.h, acc1);
+                }
+                st4(a.r32[0] + c * ntot + k, make_float4(rf[0], rf[1], rf[2], rf[3]));
             }
         } else {  // kResidual: r = b - A x in FP64
 #pragma unroll
@@ -508,15 +615,34 @@ __device__ __forceinline__ void cheb_tile(const CoopArgs& a, const GState& s, in
         ea = eb;
         eb = tmp;
     }
-    // interior: x += e / sc (FP64; 1 / sc is a power of two, exact in FP32)
+    // interior: x += e / sc in FP32 pairs (1 / sc is a power of two, exact in FP32); the
+    // first refinement of the solve takes x from its FP64 array
     if (act && gx >= X0 && gx < X1) {
         const float invf = (float)(1.0 / s.scale);
-        double* Xc = a.x + c * a.ntot + off + gx;
+        const long long o0 = c * a.ntot + off + gx;
+        const double* Xc = a.x + o0;
+        float* XH = a.p32 + o0;
+        float* XL = a.q32 + o0;
         const int y0 = Y0 - kChebHalo + r0;
+        // all loads first: a store to XH or XL cannot be proved apart from the next
+        // row's loads, so row by row would serialise 22 L2 round trips
+        DW v[kChebRows];
 #pragma unroll
         for (int k = 0; k < kChebRows; k++) {
             const int y = y0 + k;
-            if (y >= Y0 && y < Y1) Xc[(long long)y * nx] += (double)(e[k] * invf);
+            const long long o = (long long)y * nx;
+            v[k] = DW{0.f, 0.f};
+            if (y >= Y0 && y < Y1) v[k] = s.dw ? DW{__ldcg(XH + o), __ldcg(XL + o)} : dw_from(__ldcg(Xc + o));
+        }
+#pragma unroll
+        for (int k = 0; k < kChebRows; k++) {
+            const int y = y0 + k;
+            if (y >= Y0 && y < Y1) {
+                const long long o = (long long)y * nx;
+                const DW w = dw_add_f(v[k], __fmul_rn(e[k], invf));
+                XH[o] = w.h;
+                XL[o] = w.l;
+            }
         }
     }
     __syncthreads();  // the window is reused by the next item
@@ -550,7 +676,8 @@ __global__ void __launch_bounds__(kCoopThreads, CHEB ? 2 : 4) k_mp_coop(const Co
         const double sig = dl > 0.0 ? c0 / dl : 0.0;
         // Chebyshev when 13 steps reduce the error by kChebWorst at least (T_13(sigma) =
         // cosh(13 acosh sigma) >= 1 / kChebWorst) and the tiles cover the simulation
-        s.cheb = CHEB && sig > 1.0 && kChebMaxIt * acosh(sig) >= acosh(1.0 / kChebWorst);
+        s.cheb = CHEB && sig > 1.0 && kChebMaxIt * acosh(sig) >= acosh(1.0 / kChebWorst) && s.rtol >= kChebRtolMin;
+        s.dw = 0;
         s.sig = (float)sig;
         s.m = 0;
         gs[g] = s;
@@ -571,6 +698,7 @@ __global__ void __launch_bounds__(kCoopThreads, CHEB ? 2 : 4) k_mp_coop(const Co
     const auto takes = [](Phase ph, const GState& s) {
         if (ph == kDirection || ph == kUpdate) return s.active && s.in_active;
         if (ph == kBegin || ph == kX) return s.active && !s.cheb;
+        if (ph == kJoin) return s.dw != 0;
         return s.active != 0;
     };
     // One pass over this CTA's chunks of the simulations taking part in `ph`, with
@@ -605,6 +733,7 @@ __global__ void __launch_bounds__(kCoopThreads, CHEB ? 2 : 4) k_mp_coop(const Co
             q.alphaf = (float)s.alpha;
             q.scale = s.scale;
             q.inv = 1.0 / s.scale;
+            q.dw = s.dw;
             q.l0 = (ch - __ldg(&a.gchunk[g].x)) * kChunkCells;
             float acc1 = 0.f, acc2 = 0.f;
             double accd = 0.0;
@@ -613,10 +742,20 @@ __global__ void __launch_bounds__(kCoopThreads, CHEB ? 2 : 4) k_mp_coop(const Co
             case kDirection: chunk_phase<kDirection>(a, q, acc1, acc2, accd); break;
             case kUpdate: chunk_phase<kUpdate>(a, q, acc1, acc2, accd); break;
             case kX: chunk_phase<kX>(a, q, acc1, acc2, accd); break;
-            default: chunk_phase<kResidual>(a, q, acc1, acc2, accd); break;
+            case kJoin:
+                if constexpr (CHEB) chunk_phase<kJoin>(a, q, acc1, acc2, accd);
+                break;
+            default:
+                if constexpr (CHEB)
+                    if (q.dw) {
+                        chunk_phase<kResidualDW>(a, q, acc1, acc2, accd);
+                        break;
+                    }
+                chunk_phase<kResidual>(a, q, acc1, acc2, accd);
+                break;
             }
-            if (ph != kX) {
-                const double t1 = block_sum(ph == kResidual ? accd : (double)acc1, red);
+            if (ph != kX && ph != kJoin) {
+                const double t1 = block_sum(ph == kResidual && !q.dw ? accd : (double)acc1, red);
                 if (tid == 0) part[ch] = t1;
                 __syncthreads();  // red is reused next
                 if (two(ph)) {
@@ -713,7 +852,10 @@ __global__ void __launch_bounds__(kCoopThreads, CHEB ? 2 : 4) k_mp_coop(const Co
                 if constexpr (CHEB) cheb_tile(a, gs[g], g, t, c, ew);
             }
             for (int g = tid; g < a.ngrids; g += blockDim.x)
-                if (gs[g].active && gs[g].cheb) gs[g].iters += gs[g].m;
+                if (gs[g].active && gs[g].cheb) {
+                    gs[g].iters += gs[g].m;
+                    gs[g].dw = 1;  // the tiles wrote x as pairs
+                }
             if (blockIdx.x == 0 && tid == 0) {
                 int mx = 0;
                 for (int g = 0; g < a.ngrids; g++)
@@ -763,6 +905,7 @@ __global__ void __launch_bounds__(kCoopThreads, CHEB ? 2 : 4) k_mp_coop(const Co
         if (tid == 0) st->stop_next = 1u;
         return;
     }
+    if (CHEB) pass(kJoin);  // no barrier after: nothing in this launch reads x again
     if (blockIdx.x == 0) {
         for (int g = tid; g < a.ngrids; g += blockDim.x) {
             CgState& c = a.cg[g];
