@@ -550,12 +550,18 @@ __device__ __forceinline__ void cheb_step(const float* __restrict__ src, float* 
                                           const float (&rs)[kChebRows], float c0f, float cxf, float cyf,
                                           float ca, float cb, bool wl, bool wr, bool odd) {
     float up = src[base - kChebPitch];
+    float wn = src[base - 1], en = src[base + 1];  // the next row's west and east neighbours
+    const float last = src[base + kChebRows * kChebPitch];  // the row below the strip
 #pragma unroll
     for (int k = 0; k < kChebRows; k++) {
         const int l = base + k * kChebPitch;
         const float ec = e[k];
-        const float dn = k + 1 < kChebRows ? e[k + 1 < kChebRows ? k + 1 : k] : src[l + kChebPitch];
-        float wv = src[l - 1], ev = src[l + 1];
+        const float dn = k + 1 < kChebRows ? e[k + 1 < kChebRows ? k + 1 : k] : last;
+        float wv = wn, ev = en;
+        if (k + 1 < kChebRows) {  // loads one row ahead of the arithmetic
+            wn = src[l + kChebPitch - 1];
+            en = src[l + kChebPitch + 1];
+        }
         if (wl) wv = odd ? -ev : ec;  // conductor images: Bx odd and zero on the wall node
         if (wr) ev = odd ? 0.f : ec;  // x = nx, By and Bz even
         const float Ae = fmaf(c0f, ec, -fmaf(cxf, wv + ev, cyf * (up + dn)));
