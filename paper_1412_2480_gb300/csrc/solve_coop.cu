@@ -97,12 +97,22 @@ struct CoopArgs {
     DevStatus* st;
 };
 
+struct DW {  // a double-word number h + l (FP32 pair), see the pair arithmetic below
+    float h, l;
+};
+
 struct GState {
     double rr, bb, scale, rr_in0, rr_in, rz, alpha, beta, tol_in, rel, rtol;
     int active, in_active, iters, in_iters, outer, maxit;
     int cheb, m;  // inner solve by the Chebyshev iteration; its steps this refinement
     int dw;       // x is held as FP32 pairs in (p32, q32) until the final join
     float sig;    // c0 / (2 (cx + cy))
+    // FP32 and pair forms of the simulation's constants and of the refinement's scale,
+    // formed by one thread per simulation: on this part every FP64 operation (a
+    // conversion included) costs as much as ~100 FP32 ones, too much to repeat per thread
+    float c0f, cxf, cyf, pc0f, pcxf, pcyf, scf, invf, alphaf, betaf;
+    double inv;
+    DW C0, CX, CY;
 };
 
 // Grid-wide barrier of a cooperative launch (all CTAs resident): arrivals on one counter
@@ -175,8 +185,9 @@ struct ChunkC {
     int nx, ny, ncell, l0, walls, rb;  // rb: residual buffer holding the current r
     int dw;                            // x lives as FP32 pairs (a.p32, a.q32): the Chebyshev path
     long long off, ntot;
-    double c0, cx, cy, scale, inv;
-    float c0f, cxf, cyf, betaf, alphaf, pc0f, pcxf, pcyf;
+    double c0, cx, cy, inv;
+    float c0f, cxf, cyf, betaf, alphaf, pc0f, pcxf, pcyf, scf;
+    DW C0, CX, CY;
 };
 
 // M v for the four cells of a quad: centre quad v, north and south quads, west and east
@@ -226,9 +237,6 @@ __device__ __forceinline__ void st4d(double* p, const double v[4]) {
 // exact product, and the "sloppy" pair sum and pair-times-pair product analysed by
 // Joldes, Muller and Popescu (ACM TOMS 44, 2017). Explicit round-to-nearest intrinsics
 // keep the compiler from contracting or reassociating them.
-struct DW {
-    float h, l;
-};
 __device__ __forceinline__ DW two_sum(float a, float b) {
     const float s = __fadd_rn(a, b), bb = __fsub_rn(s, a);
     return {s, __fadd_rn(__fsub_rn(a, __fsub_rn(s, bb)), __fsub_rn(b, bb))};
@@ -306,7 +314,7 @@ __device__ __forceinline__ void chunk_cells(const CoopArgs& a, const ChunkC& q, 
             // the FP64 residual's FP32 copy (buffer 0, written with it) times the scale, a
             // power of two (so this equals rounding r * scale), into buffer 1; e = 0;
             // z = M r from the neighbours' copies, scaled alike
-            const float sc = (float)q.scale;
+            const float sc = q.scf;
 #pragma unroll
             for (int c = 0; c < 3; c++) {
                 const float* R = a.r32[0] + c * ntot;
@@ -397,7 +405,7 @@ __device__ __forceinline__ void chunk_cells(const CoopArgs& a, const ChunkC& q, 
                 st4d(a.x + o, xv);
             }
         } else if constexpr (PH == kResidualDW) {  // on the pairs: r = b - A x, its FP32 copy, (r, r)
-            const DW C0 = dw_from(q.c0), CX = dw_from(q.cx), CY = dw_from(q.cy);
+            const DW C0 = q.C0, CX = q.CX, CY = q.CY;
 #pragma unroll
             for (int c = 0; c < 3; c++) {
                 const float* XH = a.p32 + c * ntot;
@@ -576,7 +584,7 @@ __device__ __forceinline__ void cheb_tile(const CoopArgs& a, const GState& s, in
     const GridDev* Gp = a.grids + g;
     const int nx = __ldg(&Gp->nx), ny = __ldg(&Gp->ny), walls = __ldg(&Gp->walls);
     const long long off = __ldg(&Gp->cell_off);
-    const float c0f = (float)__ldg(&Gp->c0), cxf = (float)__ldg(&Gp->cx), cyf = (float)__ldg(&Gp->cy);
+    const float c0f = s.c0f, cxf = s.cxf, cyf = s.cyf;
     const int2 t0 = __ldg(a.tile_xy + t);
     const int X0 = t0.x, Y0 = t0.y;
     const int X1 = min(X0 + kChebTileX, nx), Y1 = min(Y0 + kChebTileY, ny);
@@ -595,7 +603,7 @@ __device__ __forceinline__ void cheb_tile(const CoopArgs& a, const GState& s, in
     int gy = Y0 - kChebHalo + r0;  // first row of the strip, wrapped
     while (gy < 0) gy += ny;
     while (gy >= ny) gy -= ny;
-    const float sc = (float)s.scale;
+    const float sc = s.scf;
     const float sig = s.sig, delta = c0f / sig, ith = 1.f / c0f;
     const float* Rg = a.r32[0] + c * a.ntot + off + gxw;
     float rs[kChebRows], d[kChebRows], e[kChebRows];
@@ -624,7 +632,7 @@ __device__ __forceinline__ void cheb_tile(const CoopArgs& a, const GState& s, in
     // interior: x += e / sc in FP32 pairs (1 / sc is a power of two, exact in FP32); the
     // first refinement of the solve takes x from its FP64 array
     if (act && gx >= X0 && gx < X1) {
-        const float invf = (float)(1.0 / s.scale);
+        const float invf = s.invf;
         const long long o0 = c * a.ntot + off + gx;
         const double* Xc = a.x + o0;
         float* XH = a.p32 + o0;
@@ -686,6 +694,16 @@ __global__ void __launch_bounds__(kCoopThreads, CHEB ? 2 : 4) k_mp_coop(const Co
         s.dw = 0;
         s.sig = (float)sig;
         s.m = 0;
+        const GridDev& G = a.grids[g];
+        s.c0f = (float)G.c0;
+        s.cxf = (float)G.cx;
+        s.cyf = (float)G.cy;
+        s.pc0f = (float)G.pc0;
+        s.pcxf = (float)G.pcx;
+        s.pcyf = (float)G.pcy;
+        s.C0 = dw_from(G.c0);
+        s.CX = dw_from(G.cx);
+        s.CY = dw_from(G.cy);
         gs[g] = s;
     }
     __syncthreads();
@@ -729,16 +747,19 @@ __global__ void __launch_bounds__(kCoopThreads, CHEB ? 2 : 4) k_mp_coop(const Co
             q.c0 = __ldg(&Gp->c0);
             q.cx = __ldg(&Gp->cx);
             q.cy = __ldg(&Gp->cy);
-            q.c0f = (float)q.c0;
-            q.cxf = (float)q.cx;
-            q.cyf = (float)q.cy;
-            q.pc0f = (float)__ldg(&Gp->pc0);
-            q.pcxf = (float)__ldg(&Gp->pcx);
-            q.pcyf = (float)__ldg(&Gp->pcy);
-            q.betaf = (float)s.beta;
-            q.alphaf = (float)s.alpha;
-            q.scale = s.scale;
-            q.inv = 1.0 / s.scale;
+            q.c0f = s.c0f;
+            q.cxf = s.cxf;
+            q.cyf = s.cyf;
+            q.pc0f = s.pc0f;
+            q.pcxf = s.pcxf;
+            q.pcyf = s.pcyf;
+            q.C0 = s.C0;
+            q.CX = s.CX;
+            q.CY = s.CY;
+            q.betaf = s.betaf;
+            q.alphaf = s.alphaf;
+            q.scf = s.scf;
+            q.inv = s.inv;
             q.dw = s.dw;
             q.l0 = (ch - __ldg(&a.gchunk[g].x)) * kChunkCells;
             float acc1 = 0.f, acc2 = 0.f;
@@ -788,13 +809,16 @@ __global__ void __launch_bounds__(kCoopThreads, CHEB ? 2 : 4) k_mp_coop(const Co
                 s.rr_in = t;
                 s.rz = t2;
                 s.beta = 0.0;
+                s.betaf = 0.f;
                 s.in_iters = 0;
                 s.tol_in = fmax(2e-6, 0.5 * s.rtol * sqrt(s.bb / fmax(s.rr, 1e-300)));
                 s.in_active = (t > 0.0 && t2 > 0.0) ? 1 : 0;
             } else if (ph == kDirection) {
                 s.alpha = s.rz / t;
+                s.alphaf = (float)s.alpha;
             } else if (ph == kUpdate) {
                 s.beta = t2 / s.rz;
+                s.betaf = (float)s.beta;
                 s.rz = t2;
                 s.rr_in = t;
                 s.in_iters += 1;
@@ -839,6 +863,9 @@ __global__ void __launch_bounds__(kCoopThreads, CHEB ? 2 : 4) k_mp_coop(const Co
                 int ex;
                 frexp(sqrt(3.0 * a.grids[g].ncell / s.rr), &ex);
                 s.scale = ldexp(1.0, ex - 1);
+                s.inv = ldexp(1.0, 1 - ex);
+                s.scf = (float)s.scale;
+                s.invf = (float)s.inv;
                 s.in_active = 0;
                 if (s.cheb) {
                     // the reduction this refinement needs (the CG's inner tolerance), in
