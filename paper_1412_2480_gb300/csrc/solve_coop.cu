@@ -638,24 +638,37 @@ __device__ __forceinline__ void cheb_tile(const CoopArgs& a, const GState& s, in
         float* XH = a.p32 + o0;
         float* XL = a.q32 + o0;
         const int y0 = Y0 - kChebHalo + r0;
-        // all loads first: a store to XH or XL cannot be proved apart from the next
-        // row's loads, so row by row would serialise 22 L2 round trips
-        DW v[kChebRows];
+        // loads in blocks of 8 rows ahead of their stores: a store to XH or XL cannot be
+        // proved apart from a later row's loads, so row by row would serialise 22 L2
+        // round trips, and all 22 rows at once would need 44 more registers
+        constexpr int kBlk = 8;
+        const bool pairs = s.dw != 0;
 #pragma unroll
-        for (int k = 0; k < kChebRows; k++) {
-            const int y = y0 + k;
-            const long long o = (long long)y * nx;
-            v[k] = DW{0.f, 0.f};
-            if (y >= Y0 && y < Y1) v[k] = s.dw ? DW{__ldcg(XH + o), __ldcg(XL + o)} : dw_from(__ldcg(Xc + o));
-        }
+        for (int k0 = 0; k0 < kChebRows; k0 += kBlk) {
+            DW v[kBlk];
 #pragma unroll
-        for (int k = 0; k < kChebRows; k++) {
-            const int y = y0 + k;
-            if (y >= Y0 && y < Y1) {
+            for (int u = 0; u < kBlk; u++) {
+                const int k = k0 + u, y = y0 + k;
                 const long long o = (long long)y * nx;
-                const DW w = dw_add_f(v[k], __fmul_rn(e[k], invf));
-                XH[o] = w.h;
-                XL[o] = w.l;
+                v[u] = DW{0.f, 0.f};
+                if (k < kChebRows && y >= Y0 && y < Y1) {
+                    if (pairs) {
+                        v[u].h = __ldcg(XH + o);
+                        v[u].l = __ldcg(XL + o);
+                    } else {
+                        v[u] = dw_from(__ldcg(Xc + o));
+                    }
+                }
+            }
+#pragma unroll
+            for (int u = 0; u < kBlk; u++) {
+                const int k = k0 + u, y = y0 + k;
+                if (k < kChebRows && y >= Y0 && y < Y1) {
+                    const long long o = (long long)y * nx;
+                    const DW w = dw_add_f(v[u], __fmul_rn(e[k < kChebRows ? k : 0], invf));
+                    XH[o] = w.h;
+                    XL[o] = w.l;
+                }
             }
         }
     }
