@@ -630,44 +630,41 @@ __device__ __forceinline__ void cheb_tile(const CoopArgs& a, const GState& s, in
         eb = tmp;
     }
     // interior: x += e / sc in FP32 pairs (1 / sc is a power of two, exact in FP32); the
-    // first refinement of the solve takes x from its FP64 array
-    if (act && gx >= X0 && gx < X1) {
-        const float invf = s.invf;
-        const long long o0 = c * a.ntot + off + gx;
-        const double* Xc = a.x + o0;
-        float* XH = a.p32 + o0;
-        float* XL = a.q32 + o0;
-        const int y0 = Y0 - kChebHalo + r0;
-        // loads in blocks of 8 rows ahead of their stores: a store to XH or XL cannot be
-        // proved apart from a later row's loads, so row by row would serialise 22 L2
-        // round trips, and all 22 rows at once would need 44 more registers
-        constexpr int kBlk = 8;
-        const bool pairs = s.dw != 0;
+    // first refinement of the solve takes x from its FP64 array. e is read back from the
+    // window so that warp w updates rows w, w + 8, ... with one lane per column: whole
+    // 128-byte rows per access, all eight loads of a lane in flight at once.
+    {
+        constexpr int kWarps = kCoopThreads / 32, kPer = kChebTileY / kWarps;
+        const int lane = tid & 31, wp = tid >> 5;
+        const int gxl = X0 + lane;
+        if (gxl < X1) {
+            const float invf = s.invf;
+            const long long o0 = c * a.ntot + off + gxl;
+            const bool pairs = s.dw != 0;
+            DW v[kPer];
 #pragma unroll
-        for (int k0 = 0; k0 < kChebRows; k0 += kBlk) {
-            DW v[kBlk];
-#pragma unroll
-            for (int u = 0; u < kBlk; u++) {
-                const int k = k0 + u, y = y0 + k;
-                const long long o = (long long)y * nx;
-                v[u] = DW{0.f, 0.f};
-                if (k < kChebRows && y >= Y0 && y < Y1) {
+            for (int j = 0; j < kPer; j++) {
+                const int y = Y0 + wp + kWarps * j;
+                v[j] = DW{0.f, 0.f};
+                if (y < Y1) {
+                    const long long o = o0 + (long long)y * nx;
                     if (pairs) {
-                        v[u].h = __ldcg(XH + o);
-                        v[u].l = __ldcg(XL + o);
+                        v[j].h = __ldcg(a.p32 + o);
+                        v[j].l = __ldcg(a.q32 + o);
                     } else {
-                        v[u] = dw_from(__ldcg(Xc + o));
+                        v[j] = dw_from(__ldcg(a.x + o));
                     }
                 }
             }
 #pragma unroll
-            for (int u = 0; u < kBlk; u++) {
-                const int k = k0 + u, y = y0 + k;
-                if (k < kChebRows && y >= Y0 && y < Y1) {
-                    const long long o = (long long)y * nx;
-                    const DW w = dw_add_f(v[u], __fmul_rn(e[k < kChebRows ? k : 0], invf));
-                    XH[o] = w.h;
-                    XL[o] = w.l;
+            for (int j = 0; j < kPer; j++) {
+                const int y = Y0 + wp + kWarps * j;
+                if (y < Y1) {
+                    const float ev = ea[(y - Y0 + kChebHalo + 1) * kChebPitch + lane + kChebHalo + 1];
+                    const DW w = dw_add_f(v[j], __fmul_rn(ev, invf));
+                    const long long o = o0 + (long long)y * nx;
+                    a.p32[o] = w.h;
+                    a.q32[o] = w.l;
                 }
             }
         }
