@@ -68,6 +68,7 @@ constexpr int kChebStrips = 4;
 constexpr int kChebRows = kChebH / kChebStrips;
 constexpr int kChebPitch = kChebW + 2;
 constexpr int kChebCells = kChebPitch * (kChebH + 2);
+constexpr int kChebTileCells = kChebTileX * kChebTileY;  // the interior, staged for the x update
 static_assert(kChebRows * kChebStrips == kChebH && kChebW * kChebStrips <= kCoopThreads, "window layout");
 constexpr double kChebFloor = 1e-7;
 constexpr double kChebRtolMin = 1e-13;  // the FP32-pair residual resolves about 1e-14 of ||b||
@@ -551,6 +552,15 @@ __device__ __forceinline__ void chunk_phase(const CoopArgs& a, const ChunkC& q, 
 // each step (two buffers, one barrier per step) for the neighbouring columns and the
 // strips above and below. The ring of ghost cells around the window stays zero.
 
+// 16-byte asynchronous global -> shared copies (cp.async, sm_80 and later): the tile's
+// x is fetched while its Chebyshev steps run.
+__device__ __forceinline__ void cp_async16(void* smem, const void* gmem) {
+    const unsigned int sa = (unsigned int)__cvta_generic_to_shared(smem);
+    asm volatile("cp.async.cg.shared.global [%0], [%1], 16;\n" ::"r"(sa), "l"(gmem) : "memory");
+}
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;\n" ::: "memory"); }
+__device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wait_all;\n" ::: "memory"); }
+
 // One step on a thread's strip: reads the old e of its neighbours from src, writes the
 // new e to dst (distinct buffers).
 __device__ __forceinline__ void cheb_step(const float* __restrict__ src, float* __restrict__ dst, int base,
@@ -609,6 +619,28 @@ __device__ __forceinline__ void cheb_tile(const CoopArgs& a, const GState& s, in
     float rs[kChebRows], d[kChebRows], e[kChebRows];
     float* ea = ew;
     float* eb = ew + kChebCells;
+    // the interior's x, staged asynchronously during the steps: pairs (h rows, then l
+    // rows) or, in the solve's first refinement, FP64 values; rows of kChebTileX, 16-byte
+    // chunks (nx, the offsets and X0 are multiples of 4 cells, so chunks stay aligned)
+    float* xst = ew + 2 * kChebCells;
+    const int nrow = Y1 - Y0, ncol = X1 - X0;
+    const long long ob = c * a.ntot + off + (long long)Y0 * nx + X0;
+    if (s.dw) {
+        for (int q = tid; q < 2 * kChebTileY * (kChebTileX / 4); q += kCoopThreads) {
+            const int arr = q / (kChebTileY * (kChebTileX / 4)), rem = q - arr * (kChebTileY * (kChebTileX / 4));
+            const int y = rem / (kChebTileX / 4), x4 = 4 * (rem - y * (kChebTileX / 4));
+            if (y < nrow && x4 < ncol)
+                cp_async16(xst + arr * kChebTileCells + y * kChebTileX + x4,
+                           (arr ? a.q32 : a.p32) + ob + (long long)y * nx + x4);
+        }
+    } else {
+        double* xd = reinterpret_cast<double*>(xst);
+        for (int q = tid; q < kChebTileY * (kChebTileX / 2); q += kCoopThreads) {
+            const int y = q / (kChebTileX / 2), x2 = 2 * (q - y * (kChebTileX / 2));
+            if (y < nrow && x2 < ncol) cp_async16(xd + y * kChebTileX + x2, a.x + ob + (long long)y * nx + x2);
+        }
+    }
+    cp_async_commit();
 #pragma unroll
     for (int k = 0; k < kChebRows; k++) {
         rs[k] = live ? __ldcg(Rg + (long long)gy * nx) * sc : 0.f;
@@ -633,6 +665,8 @@ __device__ __forceinline__ void cheb_tile(const CoopArgs& a, const GState& s, in
     // first refinement of the solve takes x from its FP64 array. e is read back from the
     // window so that warp w updates rows w, w + 8, ... with one lane per column: whole
     // 128-byte rows per access, all eight loads of a lane in flight at once.
+    cp_async_wait_all();
+    __syncthreads();  // every thread's staged chunks visible
     {
         constexpr int kWarps = kCoopThreads / 32, kPer = kChebTileY / kWarps;
         const int lane = tid & 31, wp = tid >> 5;
@@ -644,17 +678,9 @@ __device__ __forceinline__ void cheb_tile(const CoopArgs& a, const GState& s, in
             DW v[kPer];
 #pragma unroll
             for (int j = 0; j < kPer; j++) {
-                const int y = Y0 + wp + kWarps * j;
-                v[j] = DW{0.f, 0.f};
-                if (y < Y1) {
-                    const long long o = o0 + (long long)y * nx;
-                    if (pairs) {
-                        v[j].h = __ldcg(a.p32 + o);
-                        v[j].l = __ldcg(a.q32 + o);
-                    } else {
-                        v[j] = dw_from(__ldcg(a.x + o));
-                    }
-                }
+                const int yl = wp + kWarps * j, q = yl * kChebTileX + lane;
+                v[j] = pairs ? DW{xst[q], xst[kChebTileCells + q]}
+                             : dw_from(reinterpret_cast<const double*>(xst)[q]);
             }
 #pragma unroll
             for (int j = 0; j < kPer; j++) {
@@ -679,7 +705,7 @@ template <bool CHEB>
 __global__ void __launch_bounds__(kCoopThreads, CHEB ? 2 : 4) k_mp_coop(const CoopArgs a) {
     __shared__ GState gs[kCoopMaxGrids];
     __shared__ double red[32];
-    extern __shared__ double sp[];  // 2 x nchunks staged partial sums
+    extern __shared__ __align__(16) double sp[];  // 2 x nchunks staged partial sums
     DevStatus* st = a.st;
     if (st->stop) return;  // the same for every CTA: stop changes only between launches
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
@@ -966,7 +992,8 @@ __global__ void __launch_bounds__(kCoopThreads, CHEB ? 2 : 4) k_mp_coop(const Co
 }  // namespace
 
 size_t coop_smem(const CoopSolve& cs) {
-    return 2 * (size_t)cs.nchunks * sizeof(double) + (cs.cheb ? 2 * (size_t)kChebCells * sizeof(float) : 0);
+    return 2 * (size_t)cs.nchunks * sizeof(double) +
+           (cs.cheb ? (2 * (size_t)kChebCells + 2 * (size_t)kChebTileCells) * sizeof(float) : 0);
 }
 
 // Whether simulation g can take the Chebyshev inner solve (as the kernel decides).
