@@ -224,6 +224,24 @@ void fill_grid(const pic_params& p, GridDev& G) {
     G.pk_dtx = (float)(G.dt * G.idx);
     G.pk_dty = (float)(G.dt * G.idy);
     G.js40 = (float)(G.jscale * std::ldexp(1.0, -40));
+    {
+        const auto pair = [](double v, float out[2]) {
+            out[0] = (float)v;
+            out[1] = (float)(v - (double)out[0]);
+        };
+        const double th_dt2 = G.theta * G.dt * G.dt;
+        pair(th_dt2 * G.idx * G.idx, G.dw_ax);
+        pair(th_dt2 * G.idy * G.idy, G.dw_ay);
+        pair(4.0 * kPi * th_dt2 * G.jinv * G.idx, G.dw_kjx);
+        pair(4.0 * kPi * th_dt2 * G.jinv * G.idy, G.dw_kjy);
+        pair(G.dt * G.idx, G.dw_dtx);
+        pair(G.dt * G.idy, G.dw_dty);
+        pair(G.c0, G.dw_c0);
+        pair(G.cx, G.dw_cx);
+        pair(G.cy, G.dw_cy);
+        pair(4.0 * kPi * G.dt * G.jinv, G.dw_fj);
+        pair(G.theta, G.dw_th);
+    }
     G.rtol = p.cg_rtol;
     G.maxit = p.cg_max_iter;
     G.warm = p.warm_start == PIC_WS_PREV ? 1 : (p.warm_start == PIC_WS_LEARNED ? 2 : 0);

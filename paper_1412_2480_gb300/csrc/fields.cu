@@ -10,6 +10,7 @@
 //
 // Staggering (Sec. 2, Fig. 1; index k = j*nx + i): Ez at (i,j); Ex, By at (i+1/2,j);
 // Ey, Bx at (i,j+1/2); Bz at (i+1/2,j+1/2). J shares the E lattices.
+#include "dword.cuh"
 #include "engine.h"
 
 namespace pic {
@@ -233,6 +234,113 @@ k_rhs(const GridDev* __restrict__ grids, const int* __restrict__ blk_grid, int n
     finish_all_grids(ngrids, ngrids, cg, st, cond, use_cond);
 }
 
+// ---- the same right-hand side for the MIXED32 solve, in FP32-pair arithmetic ---------
+// Same formula, cells and outputs as k_rhs<long long>, but every sum and product runs on
+// FP32 pairs (dword.cuh: 47 significant bits) instead of the FP64 pipe: the FP64 values
+// read are split by bit manipulation, the current's exact integer differences are
+// converted once each, and b and r are joined back to FP64 with one add. The sums of
+// squares (||b||, ||r||, the energies U_E, U_B) are formed from the pairs' leading
+// words in FP32 per thread and in FP64 over the block.
+__device__ __forceinline__ DW dwp(const float (&v)[2]) { return {v[0], v[1]}; }
+__device__ __forceinline__ DW dw_i64(long long d) { return dw_from((double)d); }
+// x-neighbours of a B-lattice component as pairs, with the conductor's images
+__device__ __forceinline__ DW dw_nbx(const double* V, const Cell& c, int a) {
+    DW e, w;
+    if (a == 0) {  // odd
+        e = c.ew ? DW{0.f, 0.f} : dw_from(V[c.ke]);
+        w = c.ww ? dw_neg(dw_from(V[c.k + 1])) : dw_from(V[c.kw]);
+    } else {
+        e = dw_from(c.ew ? V[c.k] : V[c.ke]);
+        w = dw_from(c.ww ? V[c.k] : V[c.kw]);
+    }
+    return dw_add(e, w);
+}
+
+__global__ void __launch_bounds__(kFieldThreads)
+k_rhs_dw(const GridDev* __restrict__ grids, const int* __restrict__ blk_grid, int ngrids, int nblk_total,
+         long long ntot, const double* __restrict__ F, const long long* __restrict__ J, double* __restrict__ x,
+         double* __restrict__ r, CgState* cg, double* part, unsigned int* done, DevStatus* st,
+         cudaGraphConditionalHandle cond, int use_cond, double* __restrict__ bout, float* __restrict__ r32) {
+    const int g = blk_grid[blockIdx.x];
+    const GridDev& G = grids[g];
+    float v[4] = {0.f, 0.f, 0.f, 0.f};  // b.b, r.r, |E|^2, |B|^2
+    const DW AX = dwp(G.dw_ax), AY = dwp(G.dw_ay), KJX = dwp(G.dw_kjx), KJY = dwp(G.dw_kjy);
+    const DW DTX = dwp(G.dw_dtx), DTY = dwp(G.dw_dty), C0 = dwp(G.dw_c0), CX = dwp(G.dw_cx), CY = dwp(G.dw_cy);
+    if (!st->stop) FOR_CELLS(G, g, c) {
+        const double* Ex = F;
+        const double* Ey = F + ntot;
+        const double* Ez = F + 2 * ntot;
+        const long long* Jx = J;
+        const long long* Jy = J + ntot;
+        const long long* Jz = J + 2 * ntot;
+        const DW ez = dw_from(Ez[c.k]), ey = dw_from(Ey[c.k]), ex = dw_from(Ex[c.k]);
+        // dt curl E on the B lattices
+        const DW eEx = dw_mul(DTY, dw_sub(dw_from(Ez[c.kn]), ez));
+        const DW eEy = dw_neg(dw_mul(DTX, dw_sub(c.ew ? DW{0.f, 0.f} : dw_from(Ez[c.ke]), ez)));
+        const DW eEz = dw_sub(dw_mul(DTX, dw_sub(c.ew ? DW{0.f, 0.f} : dw_from(Ey[c.ke]), ey)),
+                              dw_mul(DTY, dw_sub(dw_from(Ex[c.kn]), ex)));
+        // theta dt^2 4 pi curl J (the fixed-point unit folded into KJX, KJY)
+        DW jJx, jJy, jJz;
+        if (!G.walls) {
+            jJx = dw_mul(KJY, dw_i64(Jz[c.kn] - Jz[c.k]));
+            jJy = dw_neg(dw_mul(KJX, dw_i64(Jz[c.ke] - Jz[c.k])));
+            jJz = dw_sub(dw_mul(KJX, dw_i64(Jy[c.ke] - Jy[c.k])), dw_mul(KJY, dw_i64(Jx[c.kn] - Jx[c.k])));
+        } else {
+            // the conductor carries the current of its wall nodes: Jy = Jz = 0 there
+            const bool w0 = c.i == 0;
+            const long long jzc = w0 ? 0 : Jz[c.k], jzn = w0 ? 0 : Jz[c.kn], jze = c.ew ? 0 : Jz[c.ke];
+            const long long jyc = w0 ? 0 : Jy[c.k], jye = c.ew ? 0 : Jy[c.ke];
+            jJx = dw_mul(KJY, dw_i64(jzn - jzc));
+            jJy = dw_neg(dw_mul(KJX, dw_i64(jze - jzc)));
+            jJz = dw_sub(dw_mul(KJX, dw_i64(jye - jyc)), dw_mul(KJY, dw_i64(Jx[c.kn] - Jx[c.k])));
+        }
+        const DW eE[3] = {eEx, eEy, eEz};
+        const DW jJ[3] = {jJx, jJy, jJz};
+#pragma unroll
+        for (int a = 0; a < 3; a++) {
+            const double* B = F + (3 + a) * ntot;
+            const DW bc = dw_from(B[c.k]);
+            const DW b2 = dw_twice(bc);
+            const DW lap = dw_add(dw_mul(AX, dw_sub(dw_nbx(B, c, a), b2)),
+                                  dw_mul(AY, dw_sub(dw_add(dw_from(B[c.kn]), dw_from(B[c.ks])), b2)));
+            const DW b = dw_add(lap, dw_sub(jJ[a], eE[a]));
+            DW res = b;
+            const long long o = a * ntot;
+            if (G.warm == 1) {  // previous step's dB as the initial guess
+                const double* X = x + o;
+                const DW Ax = dw_sub(dw_mul(C0, dw_from(X[c.k])),
+                                     dw_add(dw_mul(CX, dw_nbx(X, c, a)),
+                                            dw_mul(CY, dw_add(dw_from(X[c.kn]), dw_from(X[c.ks])))));
+                res = dw_sub(b, Ax);
+                v[1] = fmaf(res.h, res.h, v[1]);
+            }
+            r[o + c.k] = dw_join(res);
+            if (r32) r32[o + c.k] = res.h;  // FP32 copy for the cooperative solve
+            if (bout) bout[o + c.k] = dw_join(b);
+            v[0] = fmaf(b.h, b.h, v[0]);
+            v[3] = fmaf(bc.h, bc.h, v[3]);
+        }
+        v[2] = fmaf(ex.h, ex.h, fmaf(ey.h, ey.h, fmaf(ez.h, ez.h, v[2])));
+    }
+    double vd[4] = {f64_of(v[0]), f64_of(v[1]), f64_of(v[2]), f64_of(v[3])};
+    double tot[4];
+    if (!reduce_and_finish<4>(G, g, vd, part, nblk_total, done, tot)) return;
+    if (threadIdx.x == 0) {
+        CgState& s = cg[g];
+        const double e = G.dx * G.dy / (8.0 * kPi);
+        s.ue = tot[2] * e;
+        s.ub = tot[3] * e;
+        s.bb = tot[0];
+        s.rr = G.warm == 1 ? tot[1] : tot[0];  // r = b unless the previous dB is the guess
+        s.beta = 0.0;
+        s.iters = 0;
+        s.outer = 0;
+        s.rel = tot[0] > 0.0 ? sqrt(s.rr / tot[0]) : 0.0;
+        s.active = (!st->stop && tot[0] > 0.0 && s.rel > G.rtol) ? 1 : 0;
+    }
+    finish_all_grids(ngrids, ngrids, cg, st, cond, use_cond);
+}
+
 // Zero the solution where the warm start is off (x0 = 0). Separate from k_rhs because
 // k_rhs reads x at neighbours when warm starting.
 __global__ void __launch_bounds__(kFieldThreads)
@@ -369,6 +477,43 @@ k_update_E(const GridDev* __restrict__ grids, const int* __restrict__ blk_grid, 
     }
 }
 
+// The MIXED32 E update in FP32-pair arithmetic: the same formula and cells as
+// k_update_E<long long>, joined back to FP64 with one add per component.
+__global__ void __launch_bounds__(kFieldThreads)
+k_update_E_dw(const GridDev* __restrict__ grids, const int* __restrict__ blk_grid, long long ntot,
+              double* __restrict__ F, const long long* __restrict__ J, const double* __restrict__ x,
+              const CgState* __restrict__ cg, const DevStatus* st) {
+    if (st->stop) return;
+    const int g = blk_grid[blockIdx.x];
+    const GridDev& G = grids[g];
+    const DW TH = cg[g].bb > 0.0 ? dwp(G.dw_th) : DW{0.f, 0.f};  // dB = 0 when b = 0
+    const DW FJ = dwp(G.dw_fj), DTX = dwp(G.dw_dtx), DTY = dwp(G.dw_dty);
+    const double* Bx = F + 3 * ntot;
+    const double* By = F + 4 * ntot;
+    const double* Bz = F + 5 * ntot;
+    const double* Xx = x;
+    const double* Xy = x + ntot;
+    const double* Xz = x + 2 * ntot;
+    auto h = [&](const double* B, const double* X, long long k) { return dw_add(dw_from(B[k]), dw_mul(TH, dw_from(X[k]))); };
+    FOR_CELLS(G, g, c) {
+        const DW hzc = h(Bz, Xz, c.k);
+        const long long kw = c.ww ? c.k : c.kw;  // Bz, By even at a wall
+        const DW dEx = dw_sub(dw_mul(DTY, dw_sub(hzc, h(Bz, Xz, c.ks))), dw_mul(FJ, dw_i64(J[c.k])));
+        F[c.k] = dw_join(dw_add(dw_from(F[c.k]), dEx));
+        if (c.ww) {  // the conductor keeps Ey = Ez = 0 on the wall
+            F[ntot + c.k] = 0.0;
+            F[2 * ntot + c.k] = 0.0;
+        } else {
+            const DW dEy = dw_neg(dw_add(dw_mul(DTX, dw_sub(hzc, h(Bz, Xz, kw))), dw_mul(FJ, dw_i64(J[ntot + c.k]))));
+            const DW dEz = dw_sub(dw_sub(dw_mul(DTX, dw_sub(h(By, Xy, c.k), h(By, Xy, kw))),
+                                         dw_mul(DTY, dw_sub(h(Bx, Xx, c.k), h(Bx, Xx, c.ks)))),
+                                  dw_mul(FJ, dw_i64(J[2 * ntot + c.k])));
+            F[ntot + c.k] = dw_join(dw_add(dw_from(F[ntot + c.k]), dEy));
+            F[2 * ntot + c.k] = dw_join(dw_add(dw_from(F[2 * ntot + c.k]), dEz));
+        }
+    }
+}
+
 // Explicit FDTD (Eqs. 3-4; PIC_EXPLICIT), with B kept at integer time levels for the
 // gather: x = B^{n+1/2} - B^n = -(c dt/2) curl E^n here, together with the energies of
 // level n; then k_update_E with theta = 1 applies E^{n+1} = E^n + c dt curl B^{n+1/2}
@@ -457,11 +602,11 @@ k_update_B(const GridDev* __restrict__ grids, const int* __restrict__ blk_grid, 
             const long long o = (3 + a) * ntot + c.k;
             const double b = F[o] + (have ? x[a * ntot + c.k] : 0.0);
             F[o] = b;
-            if (F32) F32[o] = (float)b;
+            if (F32) F32[o] = f32_rn(b);  // (float)b, by bit manipulation off the FP64 pipe
         }
         if (F32) {
 #pragma unroll
-            for (int a = 0; a < 3; a++) F32[a * ntot + c.k] = (float)F[a * ntot + c.k];
+            for (int a = 0; a < 3; a++) F32[a * ntot + c.k] = f32_rn(F[a * ntot + c.k]);
         }
     }
 }
@@ -821,10 +966,9 @@ void launch_step_end(const FieldArgs& a, cudaStream_t s) {
 void launch_rhs(const FieldArgs& a, cudaStream_t s) {
     k_zero_x<<<a.nblk, kFieldThreads, 0, s>>>(a.grids, a.blk_grid, a.ntot, a.x);
     if (a.Jfix)
-        k_rhs<long long><<<a.nblk, kFieldThreads, 0, s>>>(a.grids, a.blk_grid, a.ngrids, a.nblk,
-                                                          a.ntot, a.F, a.Jfix, a.x, a.r, a.cg,
-                                                          a.part, a.done, a.st, a.cond, a.use_cond,
-                                                          a.b, a.r32);
+        k_rhs_dw<<<a.nblk, kFieldThreads, 0, s>>>(a.grids, a.blk_grid, a.ngrids, a.nblk, a.ntot, a.F, a.Jfix, a.x,
+                                                  a.r, a.cg, a.part, a.done, a.st, a.cond, a.use_cond, a.b,
+                                                  a.r32);
     else
         k_rhs<double><<<a.nblk, kFieldThreads, 0, s>>>(a.grids, a.blk_grid, a.ngrids, a.nblk,
                                                        a.ntot, a.F, a.J64, a.x, a.r, a.cg,
@@ -875,8 +1019,8 @@ void launch_cg_iteration(const FieldArgs& a, cudaStream_t s) {
 
 void launch_field_update(const FieldArgs& a, cudaStream_t s) {
     if (a.Jfix)
-        k_update_E<long long><<<a.nblk, kFieldThreads, 0, s>>>(a.grids, a.blk_grid, a.ntot, a.F,
-                                                               a.Jfix, a.x, a.cg, a.st);
+        k_update_E_dw<<<a.nblk, kFieldThreads, 0, s>>>(a.grids, a.blk_grid, a.ntot, a.F, a.Jfix, a.x, a.cg,
+                                                       a.st);
     else
         k_update_E<double><<<a.nblk, kFieldThreads, 0, s>>>(a.grids, a.blk_grid, a.ntot, a.F,
                                                             a.J64, a.x, a.cg, a.st);

@@ -60,6 +60,11 @@ struct GridDev {
     // fz = q/(dx dy); dt/dx, dt/dy; js40 = jscale 2^-40 (a tile's window scale is js40 2^k)
     float pk_h[2], pk_fx[2], pk_fy[2], pk_fz[2];
     float pk_dtx, pk_dty, js40;
+    // MIXED32 field constants as FP32 pairs (h, l), formed once on the host: the
+    // right-hand side's theta dt^2/dx^2, theta dt^2/dy^2, 4 pi theta dt^2 jinv/dx and /dy,
+    // dt/dx, dt/dy; A's c0, cx, cy; the E update's 4 pi dt jinv and theta
+    float dw_ax[2], dw_ay[2], dw_kjx[2], dw_kjy[2], dw_dtx[2], dw_dty[2];
+    float dw_c0[2], dw_cx[2], dw_cy[2], dw_fj[2], dw_th[2];
 };
 
 // Per-simulation state of the PCG solve of Eq. (7).

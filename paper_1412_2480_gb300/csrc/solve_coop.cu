@@ -41,6 +41,7 @@
 #include <string>
 #include <vector>
 
+#include "dword.cuh"
 #include "engine.h"
 #include "pic.h"
 
@@ -96,10 +97,6 @@ struct CoopArgs {
     unsigned int* bar;      // [0] arrivals, [1] generation
     CgState* cg;
     DevStatus* st;
-};
-
-struct DW {  // a double-word number h + l (FP32 pair), see the pair arithmetic below
-    float h, l;
 };
 
 struct GState {
@@ -228,67 +225,6 @@ __device__ __forceinline__ void st4d(double* p, const double v[4]) {
     reinterpret_cast<double2*>(p)[0] = make_double2(v[0], v[1]);
     reinterpret_cast<double2*>(p)[1] = make_double2(v[2], v[3]);
 }
-
-// ---- double-word (FP32 pair) arithmetic for the Chebyshev solve's FP64-class steps ----
-// GB300 retires about one FP64 operation per SM per cycle against 128 FP32 ones, so the
-// residual r = b - A x and the update x += e of the refinements run on pairs
-// (h, l) of FP32 numbers, x = h + l with |l| <= ulp(h) / 2: 47 significant bits, about
-// 7e-15 relative, far below the solver tolerances this path accepts (rtol >= 1e-13).
-// Building blocks: Knuth's TwoSum and Dekker's FastTwoSum (exact sums), the FMA-based
-// exact product, and the "sloppy" pair sum and pair-times-pair product analysed by
-// Joldes, Muller and Popescu (ACM TOMS 44, 2017). Explicit round-to-nearest intrinsics
-// keep the compiler from contracting or reassociating them.
-__device__ __forceinline__ DW two_sum(float a, float b) {
-    const float s = __fadd_rn(a, b), bb = __fsub_rn(s, a);
-    return {s, __fadd_rn(__fsub_rn(a, __fsub_rn(s, bb)), __fsub_rn(b, bb))};
-}
-__device__ __forceinline__ DW fast_two_sum(float a, float b) {  // |a| >= |b| (or a = 0)
-    const float s = __fadd_rn(a, b);
-    return {s, __fsub_rn(b, __fsub_rn(s, a))};
-}
-__device__ __forceinline__ DW dw_add(DW x, DW y) {
-    const DW s = two_sum(x.h, y.h);
-    return fast_two_sum(s.h, __fadd_rn(s.l, __fadd_rn(x.l, y.l)));
-}
-__device__ __forceinline__ DW dw_neg(DW x) { return {-x.h, -x.l}; }
-__device__ __forceinline__ DW dw_add_f(DW x, float y) {
-    const DW s = two_sum(x.h, y);
-    return fast_two_sum(s.h, __fadd_rn(s.l, x.l));
-}
-__device__ __forceinline__ DW dw_mul(DW x, DW y) {
-    const float p = __fmul_rn(x.h, y.h);
-    float e = __fmaf_rn(x.h, y.h, -p);
-    e = __fmaf_rn(x.h, y.l, __fmaf_rn(x.l, y.h, e));
-    return fast_two_sum(p, e);
-}
-// FP64 -> pair by bit manipulation (no FP64 instruction): h = x truncated to 24
-// significant bits, l = the next 23 bits; magnitudes below 2^-126 (and l below 2^-126)
-// flush to zero.
-__device__ __forceinline__ DW dw_from(double x) {
-    const unsigned long long b = (unsigned long long)__double_as_longlong(x);
-    const unsigned int hw = (unsigned int)(b >> 32), lw = (unsigned int)b;
-    const unsigned int sgn = hw & 0x80000000u;
-    const int E = (int)((hw >> 20) & 0x7ffu);
-    const int fe = E - 896;  // float exponent field of h (1023 - 127 = 896)
-    const float h = (fe > 0 && fe < 255)
-                        ? __uint_as_float(sgn | ((unsigned int)fe << 23) | ((hw & 0xfffffu) << 3) | (lw >> 29))
-                        : 0.f;
-    // the next 23 mantissa bits m, worth m 2^(E - 1023 - 46): exactly (2^23 + m) - 2^23
-    const float m = __fsub_rn(__uint_as_float(0x4b000000u | ((lw >> 6) & 0x7fffffu)), 8388608.f);
-    const int se = E - 1023 - 46 + 127;
-    const float l = (fe > 0 && fe < 255 && se > 0) ? __fmul_rn(m, __uint_as_float((unsigned int)se << 23)) : 0.f;
-    return fast_two_sum(h, sgn ? -l : l);
-}
-// float -> double by bit manipulation (exact; zero and subnormal inputs give zero)
-__device__ __forceinline__ double f64_of(float f) {
-    const unsigned int u = __float_as_uint(f);
-    const unsigned int e = (u >> 23) & 0xffu;
-    if (e == 0u) return 0.0;
-    const unsigned long long d = ((unsigned long long)(u & 0x80000000u) << 32) |
-                                 ((unsigned long long)(e + 896u) << 52) | ((unsigned long long)(u & 0x7fffffu) << 29);
-    return __longlong_as_double((long long)d);
-}
-__device__ __forceinline__ double dw_join(DW x) { return f64_of(x.h) + f64_of(x.l); }
 
 // One phase on the cells of a chunk this thread owns: quads of 4 cells along x (cells
 // 4 (q0 + qq 256 + tid) .. + 3 of the simulation), read and written as float4 / double2
