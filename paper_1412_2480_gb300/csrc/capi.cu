@@ -270,6 +270,7 @@ FieldArgs field_args(pic_sim* s, int use_cond, cudaGraphConditionalHandle cond) 
     a.F32 = s->F32;
     a.Fn = s->Fn;
     a.any_nodal = s->any_nodal ? 1 : 0;
+    a.coop = s->use_coop ? 1 : 0;
     a.x = s->x;
     a.r = s->r;
     a.p = s->p;

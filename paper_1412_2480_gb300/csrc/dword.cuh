@@ -89,4 +89,32 @@ __device__ __forceinline__ float f32_rn(double x) {
     return __uint_as_float(sgn | (mag + up));  // a carry into the exponent is the correct rounding
 }
 
+// int64 -> pair by integer operations: h = the leading 24 bits, l = the next 23 (exact
+// for |d| < 2^47; relative 2^-47 beyond)
+__device__ __forceinline__ DW dw_from_i64(long long d) {
+    if (d == 0) return {0.f, 0.f};
+    const bool neg = d < 0;
+    const unsigned long long a = neg ? 0ull - (unsigned long long)d : (unsigned long long)d;
+    const int lz = __clzll((long long)a);
+    const unsigned long long n = a << lz;  // leading one at bit 63: a = n 2^-lz
+    // h = (n >> 40) 2^(40 - lz): float exponent field 63 - lz + 127
+    const unsigned int hb = ((unsigned int)(190 - lz) << 23) | ((unsigned int)(n >> 40) & 0x7fffffu);
+    // the next 23 bits, worth (n >> 17 & 0x7fffff) 2^(17 - lz)
+    const float m = __fsub_rn(__uint_as_float(0x4b000000u | ((unsigned int)(n >> 17) & 0x7fffffu)), 8388608.f);
+    const float l = __fmul_rn(m, __uint_as_float((unsigned int)(144 - lz) << 23));  // 2^(17 - lz)
+    const DW r = fast_two_sum(__uint_as_float(hb), l);
+    return neg ? dw_neg(r) : r;
+}
+
+// Sum over a warp; every lane gets the same pair (the pair sum is symmetric in its
+// operands).
+__device__ __forceinline__ DW warp_sum_dw(DW v) {
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+        const DW w{__shfl_xor_sync(0xffffffffu, v.h, o), __shfl_xor_sync(0xffffffffu, v.l, o)};
+        v = dw_add(v, w);
+    }
+    return v;
+}
+
 }  // namespace pic

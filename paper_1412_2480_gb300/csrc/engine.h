@@ -21,6 +21,7 @@ struct FieldArgs {
     float* F32;             // 6 * ntot FP32 copy of the fields for MIXED32 gathers, or nullptr
     double* Fn;             // 6 * ntot FP64 node-averaged fields (FP64 with PIC_GATHER_NODAL) or nullptr
     int any_nodal;          // some simulation gathers node-averaged fields
+    int coop;               // the cooperative solve follows (it reads the FP32 copy of r only)
     double *x, *r, *p, *q;  // 3 * ntot each: dB (solution), residual, direction, A p
     CgState* cg;            // [ngrids]
     double* part;           // 4 * nblk block partials

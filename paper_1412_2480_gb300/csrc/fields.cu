@@ -242,7 +242,49 @@ k_rhs(const GridDev* __restrict__ grids, const int* __restrict__ blk_grid, int n
 // squares (||b||, ||r||, the energies U_E, U_B) are formed from the pairs' leading
 // words in FP32 per thread and in FP64 over the block.
 __device__ __forceinline__ DW dwp(const float (&v)[2]) { return {v[0], v[1]}; }
-__device__ __forceinline__ DW dw_i64(long long d) { return dw_from((double)d); }
+__device__ __forceinline__ DW dw_i64(long long d) { return dw_from_i64(d); }
+
+// reduce_and_finish for FP32-pair values: the block's sums are formed in pair arithmetic
+// (a block_sum in FP64 would cost ten FP64 additions per thread and value on this part)
+// and stored as FP64 partials; the finishing block then proceeds as reduce_and_finish.
+template <int NV>
+__device__ bool reduce_and_finish_dw(const GridDev& G, int g, DW v[NV], double* part, int nblk_total,
+                                     unsigned int* done, double tot[NV]) {
+    __shared__ DW wsum[NV][32];
+    __shared__ double scratch[32];
+    __shared__ bool last;
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5, nw = (blockDim.x + 31) >> 5;
+#pragma unroll
+    for (int a = 0; a < NV; a++) {
+        const DW w = warp_sum_dw(v[a]);
+        if (lane == 0) wsum[a][wid] = w;
+    }
+    __syncthreads();
+    if (wid == 0) {
+#pragma unroll
+        for (int a = 0; a < NV; a++) {
+            const DW w = warp_sum_dw(lane < nw ? wsum[a][lane] : DW{0.f, 0.f});
+            if (lane == 0) part[a * nblk_total + blockIdx.x] = dw_join(w);
+        }
+    }
+    if (threadIdx.x == 0) {
+        __threadfence();
+        const unsigned t = atomicAdd(&done[g], 1u);
+        last = (t == (unsigned)G.nblk - 1u);
+    }
+    __syncthreads();
+    if (!last) return false;
+    __threadfence();
+#pragma unroll
+    for (int a = 0; a < NV; a++) {
+        double acc = 0.0;
+        for (int b = threadIdx.x; b < G.nblk; b += blockDim.x)
+            acc += __ldcg(&part[a * nblk_total + G.blk_first + b]);
+        tot[a] = block_sum(acc, scratch);
+    }
+    if (threadIdx.x == 0) done[g] = 0u;
+    return true;
+}
 // x-neighbours of a B-lattice component as pairs, with the conductor's images
 __device__ __forceinline__ DW dw_nbx(const double* V, const Cell& c, int a) {
     DW e, w;
@@ -314,17 +356,17 @@ k_rhs_dw(const GridDev* __restrict__ grids, const int* __restrict__ blk_grid, in
                 res = dw_sub(b, Ax);
                 v[1] = fmaf(res.h, res.h, v[1]);
             }
-            r[o + c.k] = dw_join(res);
-            if (r32) r32[o + c.k] = res.h;  // FP32 copy for the cooperative solve
+            if (r) r[o + c.k] = dw_join(res);  // (the cooperative solve reads only the FP32 copy)
+            if (r32) r32[o + c.k] = res.h;
             if (bout) bout[o + c.k] = dw_join(b);
             v[0] = fmaf(b.h, b.h, v[0]);
             v[3] = fmaf(bc.h, bc.h, v[3]);
         }
         v[2] = fmaf(ex.h, ex.h, fmaf(ey.h, ey.h, fmaf(ez.h, ez.h, v[2])));
     }
-    double vd[4] = {f64_of(v[0]), f64_of(v[1]), f64_of(v[2]), f64_of(v[3])};
+    DW vd[4] = {{v[0], 0.f}, {v[1], 0.f}, {v[2], 0.f}, {v[3], 0.f}};
     double tot[4];
-    if (!reduce_and_finish<4>(G, g, vd, part, nblk_total, done, tot)) return;
+    if (!reduce_and_finish_dw<4>(G, g, vd, part, nblk_total, done, tot)) return;
     if (threadIdx.x == 0) {
         CgState& s = cg[g];
         const double e = G.dx * G.dy / (8.0 * kPi);
@@ -967,8 +1009,8 @@ void launch_rhs(const FieldArgs& a, cudaStream_t s) {
     k_zero_x<<<a.nblk, kFieldThreads, 0, s>>>(a.grids, a.blk_grid, a.ntot, a.x);
     if (a.Jfix)
         k_rhs_dw<<<a.nblk, kFieldThreads, 0, s>>>(a.grids, a.blk_grid, a.ngrids, a.nblk, a.ntot, a.F, a.Jfix, a.x,
-                                                  a.r, a.cg, a.part, a.done, a.st, a.cond, a.use_cond, a.b,
-                                                  a.r32);
+                                                  a.coop ? nullptr : a.r, a.cg, a.part, a.done, a.st, a.cond,
+                                                  a.use_cond, a.b, a.r32);
     else
         k_rhs<double><<<a.nblk, kFieldThreads, 0, s>>>(a.grids, a.blk_grid, a.ngrids, a.nblk,
                                                        a.ntot, a.F, a.J64, a.x, a.r, a.cg,
