@@ -475,6 +475,23 @@ PIC_API int pic_cnn_set_wait_limit(pic_cnn* c, int32_t spins);
 /* Release the handle and all its device memory. NULL is a no-op. */
 PIC_API void pic_free(pic_sim* s);
 
+/* ---- check of the FP32-pair arithmetic ------------------------------------------------
+ * The MIXED32 right-hand side of Eq. (7), its E update and the refinements of the
+ * Chebyshev solve compute in pairs of FP32 numbers h + l (47 significant bits) instead
+ * of FP64 (the paper fixes no precision; this part's FP64 pipe is slow). This entry runs
+ * the device's building blocks on n inputs so that a test can hold them against exact
+ * host arithmetic. With a = x[i], b = x[(i + 1) mod n], k = d[i], for i < n:
+ *   out[10 i + 0], out[10 i + 1]  the pair of a (h, l)
+ *   out[10 i + 2]                 a rounded to FP32 (to nearest, ties to even)
+ *   out[10 i + 3], out[10 i + 4]  the pair of the integer k
+ *   out[10 i + 5], out[10 i + 6]  pair(a) + pair(b)
+ *   out[10 i + 7], out[10 i + 8]  pair(a) x pair(b)
+ *   out[10 i + 9]                 (pair(a) joined back to FP64) - a, rounded to FP32
+ * x, d and out are host arrays of n, n and 10 n values; 1 <= n <= 2^24. Returns PIC_OK,
+ * PIC_EINVAL (n out of range or a NULL pointer) or PIC_ECUDA, with the message in
+ * pic_last_error(NULL). No handle is needed; the call uses the current device. */
+PIC_API int pic_dword_check(const double* x, const int64_t* d, int64_t n, float* out);
+
 #ifdef __cplusplus
 }
 #endif

@@ -55,7 +55,7 @@ EXPORTED = ("pic_params_default", "pic_init", "pic_init_batch", "pic_select", "p
             "pic_particles", "pic_field_solve_noalloc", "pic_last_error", "pic_free",
             "pic_cnn_create", "pic_cnn_free", "pic_cnn_last_error", "pic_cnn_set_params",
             "pic_cnn_get_params", "pic_cnn_forward", "pic_cnn_gradient", "pic_cnn_train_step",
-            "pic_cnn_stencil", "pic_set_cnn", "pic_tc_gemm_bf16", "pic_conservation", "pic_save",
+            "pic_cnn_stencil", "pic_set_cnn", "pic_tc_gemm_bf16", "pic_dword_check", "pic_conservation", "pic_save",
             "pic_restore", "pic_spectrum", "pic_resonance_ky", "pic_set_wait_limit",
             "pic_cnn_set_wait_limit")
 
@@ -151,6 +151,8 @@ def lib():
             L.pic_cnn_set_wait_limit.restype = C.c_int
             L.pic_cnn_stencil.argtypes = [vp, vp, C.c_int64]
             L.pic_tc_gemm_bf16.argtypes = [C.c_int32, C.c_int32, C.c_int32, vp, vp, vp]
+            L.pic_dword_check.argtypes = [vp, vp, C.c_int64, vp]
+            L.pic_dword_check.restype = C.c_int
             for name in ("pic_cnn_create", "pic_cnn_set_params", "pic_cnn_get_params", "pic_cnn_forward",
                          "pic_cnn_gradient", "pic_cnn_train_step", "pic_set_cnn", "pic_tc_gemm_bf16",
                          "pic_cnn_stencil"):
@@ -502,6 +504,18 @@ def pic_tc_gemm_bf16(A, B, D=None):
     _ccheck(lib().pic_tc_gemm_bf16(M, N, K, _fptr(A, np.uint16), _fptr(B, np.uint16),
                                    _fptr(D, np.float32, True)), None)
     return D
+
+
+def pic_dword_check(x, d):
+    """The device's FP32-pair building blocks on x (float64) and d (int64), n each: an
+    (n, 10) float32 array laid out as include/pic.h describes."""
+    x = np.ascontiguousarray(x, dtype=np.float64)
+    d = np.ascontiguousarray(d, dtype=np.int64)
+    if x.shape != d.shape or x.ndim != 1:
+        raise ValueError("x and d must be 1-D arrays of the same length")
+    out = np.empty((x.size, 10), dtype=np.float32)
+    _check(lib().pic_dword_check(x.ctypes.data, d.ctypes.data, x.size, out.ctypes.data), None)
+    return out
 
 
 # ---- conveniences built only from the calls above ----------------------------------

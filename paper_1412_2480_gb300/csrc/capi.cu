@@ -17,6 +17,7 @@
 #include <vector>
 
 #include "cnn.h"
+#include "dword.cuh"
 #include "engine.h"
 #include "mixed.h"
 #include "pic.h"
@@ -1639,3 +1640,45 @@ void pic_free(pic_sim* s) {
 }
 
 }  // extern "C"
+
+// ---- check of the FP32-pair building blocks (include/pic.h) ----------------------------
+static __global__ void k_dword_check(const double* x, const long long* d, long long n, float* out) {
+    const long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    const double a = x[i], b = x[(i + 1) % n];
+    const pic::DW pa = pic::dw_from(a), pb = pic::dw_from(b), pk = pic::dw_from_i64(d[i]);
+    const pic::DW s = pic::dw_add(pa, pb), m = pic::dw_mul(pa, pb);
+    float* o = out + 10 * i;
+    o[0] = pa.h;
+    o[1] = pa.l;
+    o[2] = pic::f32_rn(a);
+    o[3] = pk.h;
+    o[4] = pk.l;
+    o[5] = s.h;
+    o[6] = s.l;
+    o[7] = m.h;
+    o[8] = m.l;
+    o[9] = (float)(pic::dw_join(pa) - a);
+}
+
+int pic_dword_check(const double* x, const int64_t* d, int64_t n, float* out) {
+    if (!x || !d || !out || n < 1 || n > (1ll << 24)) return fail(nullptr, PIC_EINVAL, "bad arguments");
+    double* dx = nullptr;
+    long long* dd = nullptr;
+    float* dout = nullptr;
+    cudaError_t e = cudaMalloc(&dx, n * sizeof(double));
+    if (e == cudaSuccess) e = cudaMalloc(&dd, n * sizeof(long long));
+    if (e == cudaSuccess) e = cudaMalloc(&dout, 10 * n * sizeof(float));
+    if (e == cudaSuccess) e = cudaMemcpy(dx, x, n * sizeof(double), cudaMemcpyHostToDevice);
+    if (e == cudaSuccess) e = cudaMemcpy(dd, d, n * sizeof(long long), cudaMemcpyHostToDevice);
+    if (e == cudaSuccess) {
+        k_dword_check<<<(unsigned)((n + 255) / 256), 256>>>(dx, dd, n, dout);
+        e = cudaGetLastError();
+    }
+    if (e == cudaSuccess) e = cudaMemcpy(out, dout, 10 * n * sizeof(float), cudaMemcpyDeviceToHost);
+    cudaFree(dx);
+    cudaFree(dd);
+    cudaFree(dout);
+    if (e != cudaSuccess) return fail(nullptr, PIC_ECUDA, std::string("pic_dword_check: ") + cudaGetErrorString(e));
+    return PIC_OK;
+}
