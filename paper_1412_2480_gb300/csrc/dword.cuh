@@ -8,7 +8,10 @@
 // relative. Building blocks: Knuth's TwoSum and Dekker's FastTwoSum (exact sums), the
 // FMA-based exact product, and the "sloppy" pair sum and pair-times-pair product
 // analysed by Joldes, Muller and Popescu (ACM TOMS 44, 2017): each result carries an
-// absolute error of a few 2^-47 times its operands' magnitude. Explicit
+// absolute error of a few 2^-47 times its operands' magnitude, as long as the low words
+// and error terms stay normal FP32 numbers: magnitudes above about 2^-75 (products above
+// 2^-70; the fields, currents and residuals of the simulations here are many orders
+// larger). Explicit
 // round-to-nearest intrinsics keep the compiler from contracting or reassociating them.
 #pragma once
 
