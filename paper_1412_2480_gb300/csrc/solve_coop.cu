@@ -462,12 +462,80 @@ __device__ __forceinline__ void direction_full(const CoopArgs& a, const ChunkC& 
     }
 }
 
+// The pair residual on a full chunk, component by component with the loads of both
+// quads issued before any arithmetic (as direction_full, for the same reason).
+__device__ __forceinline__ void residual_dw_full(const CoopArgs& a, const ChunkC& q, float& acc1) {
+    int k[kQuads], kn[kQuads], ks[kQuads], kw[kQuads], ke[kQuads], ii[kQuads];
+#pragma unroll
+    for (int qq = 0; qq < kQuads; qq++) {
+        const int l = q.l0 + 4 * (qq * kCoopThreads + (int)threadIdx.x);
+        const int j = l / q.nx, i = l - j * q.nx;
+        const int row = j * q.nx;
+        ii[qq] = i;
+        k[qq] = row + i;
+        kw[qq] = row + (i == 0 ? q.nx - 1 : i - 1);
+        ke[qq] = row + (i + 4 == q.nx ? 0 : i + 4);
+        kn[qq] = (j + 1 == q.ny ? 0 : j + 1) * q.nx + i;
+        ks[qq] = (j == 0 ? q.ny - 1 : j - 1) * q.nx + i;
+    }
+    const DW C0 = q.C0, CX = q.CX, CY = q.CY;
+#pragma unroll
+    for (int c = 0; c < 3; c++) {
+        const long long o = c * q.ntot + q.off;
+        const float* XH = a.p32 + o;
+        const float* XL = a.q32 + o;
+        float4 hc[kQuads], lc[kQuads], hn[kQuads], ln[kQuads], hs[kQuads], ls[kQuads];
+        float hw[kQuads], lw[kQuads], he[kQuads], le[kQuads];
+        double bv[kQuads][4];
+#pragma unroll
+        for (int qq = 0; qq < kQuads; qq++) {
+            hc[qq] = ld4(XH + k[qq]);
+            lc[qq] = ld4(XL + k[qq]);
+            hn[qq] = ld4(XH + kn[qq]);
+            ln[qq] = ld4(XL + kn[qq]);
+            hs[qq] = ld4(XH + ks[qq]);
+            ls[qq] = ld4(XL + ks[qq]);
+            hw[qq] = __ldcg(XH + kw[qq]);
+            lw[qq] = __ldcg(XL + kw[qq]);
+            he[qq] = __ldcg(XH + ke[qq]);
+            le[qq] = __ldcg(XL + ke[qq]);
+            ld4d(a.b + o + k[qq], bv[qq]);
+        }
+#pragma unroll
+        for (int qq = 0; qq < kQuads; qq++) {
+            const DW xc[4] = {{hc[qq].x, lc[qq].x}, {hc[qq].y, lc[qq].y}, {hc[qq].z, lc[qq].z}, {hc[qq].w, lc[qq].w}};
+            const DW xn[4] = {{hn[qq].x, ln[qq].x}, {hn[qq].y, ln[qq].y}, {hn[qq].z, ln[qq].z}, {hn[qq].w, ln[qq].w}};
+            const DW xs[4] = {{hs[qq].x, ls[qq].x}, {hs[qq].y, ls[qq].y}, {hs[qq].z, ls[qq].z}, {hs[qq].w, ls[qq].w}};
+            DW xw{hw[qq], lw[qq]}, xe{he[qq], le[qq]};
+            if (q.walls) {
+                if (ii[qq] == 0) xw = c == 0 ? dw_neg(xc[1]) : xc[0];
+                if (ii[qq] + 4 == q.nx) xe = c == 0 ? DW{0.f, 0.f} : xc[3];
+            }
+            float rf[4];
+#pragma unroll
+            for (int u = 0; u < 4; u++) {
+                const DW w = u == 0 ? xw : xc[u - 1];
+                const DW e = u == 3 ? xe : xc[u + 1];
+                const DW off = dw_add(dw_mul(CX, dw_add(w, e)), dw_mul(CY, dw_add(xn[u], xs[u])));
+                const DW Ax = dw_add(dw_mul(C0, xc[u]), dw_neg(off));
+                const DW r = dw_add(dw_from(bv[qq][u]), dw_neg(Ax));
+                rf[u] = r.h;
+                acc1 = fmaf(r.h, r.h, acc1);
+            }
+            st4(a.r32[0] + o + k[qq], make_float4(rf[0], rf[1], rf[2], rf[3]));
+        }
+    }
+}
+
 template <int PH>
 __device__ __forceinline__ void chunk_phase(const CoopArgs& a, const ChunkC& q, float& acc1, float& acc2,
                                             double& accd) {
     const bool full = q.l0 + kChunkCells <= q.ncell;
     if constexpr (PH == kDirection) {
         if (full) return direction_full(a, q, acc1);
+    }
+    if constexpr (PH == kResidualDW) {
+        if (full) return residual_dw_full(a, q, acc1);
     }
     if (full) chunk_cells<PH, true>(a, q, acc1, acc2, accd);
     else chunk_cells<PH, false>(a, q, acc1, acc2, accd);
