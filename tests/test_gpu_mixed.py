@@ -254,3 +254,37 @@ def test_batch_rejects_unlike_handle_flags():
     with pytest.raises(pic.PicError) as e:
         pic.pic_init_batch(prm)
     assert e.value.code == pic.PIC_EINVAL
+
+
+def test_batch_mixing_chebyshev_and_cg_simulations_matches_individual_runs():
+    # theta = 1 at CFL 1 (sigma = 9/8) takes the inner CG inside the Chebyshev-form
+    # kernel; its batch neighbour (theta = 1/2) takes the tiles. Each gives the fields it
+    # gives alone, bit for bit.
+    nx, ny, ppc = 64, 64, 3
+    w, sp, F0 = workload(nx, ny, ppc, gamma0=5.0, u_th=0.2, seed=21, field_amp=0.05, colocated=False)
+    prm = [pic.pic_params_default(nx=nx, ny=ny, shape_order=2, gamma0=5.0, ppc=ppc, cg_rtol=1e-12,
+                                  precision=pic.PIC_MIXED32, theta=th) for th in (0.5, 1.0)]
+
+    def run(params, k):
+        h = pic.pic_init_batch(params) if len(params) > 1 else pic.pic_init(params[0])
+        try:
+            for q in range(len(params)):
+                if len(params) > 1:
+                    pic.pic_select(h, q)
+                for c in range(6):
+                    pic.pic_set_fields(h, c, np.ascontiguousarray(F0[c]).ravel())
+                for s, d in enumerate(sp):
+                    pic.pic_load_particles(h, s, d["x"], d["y"], d["ux"], d["uy"], d["uz"])
+            pic.pic_step(h, 3)
+            if len(params) > 1:
+                pic.pic_select(h, k)
+            m = pic.pic_moments(h)
+            return np.stack([pic.fields_numpy(h, c, nx, ny) for c in range(12)]), m
+        finally:
+            pic.pic_free(h)
+
+    for k in range(2):
+        Fb, mb = run(prm, k)
+        Fa, ma = run([prm[k]], 0)
+        assert np.array_equal(Fb, Fa), k
+        assert mb["cg_rel_resid"] <= 1e-12 and ma["cg_iters_total"] == mb["cg_iters_total"]
