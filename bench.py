@@ -396,6 +396,12 @@ def run_ours(args, dist):
 
     # ---- end to end through the C ABI with host buffers: load (H2D) + K steps +
     # per-step moments (D2H) + final field readback (D2H) ----
+    # warm-up of the load path on a scratch handle, untimed: the first DMA from freshly
+    # pinned host pages maps them for the device (several times slower on a host whose
+    # memory is fragmented), and the library's temporary pool grows to the load's size
+    hw = new_sim(params, stream)
+    load(hw, data, rows)
+    pic.pic_free(hw)
     h = new_sim(params, stream)
     out_fields = torch.empty(max(r["nx"] * r["ny"] for r in rows), dtype=torch.float64,
                              pin_memory=True).numpy()

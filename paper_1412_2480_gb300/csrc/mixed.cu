@@ -33,6 +33,7 @@
 // included; readers clamp them to the segment's capacity.
 #include <algorithm>
 #include <cmath>
+#include <mutex>
 #include <vector>
 
 #include "esirkepov.cuh"
@@ -964,23 +965,68 @@ cudaError_t dalloc(T** p, size_t n) {
     return cudaMalloc((void**)p, (n ? n : 1) * sizeof(T));
 }
 
-void free_parts(PartArrays& A) {
+// Temporaries of loads, re-sorts and diagnostics (staging arrays, sort keys, bitmaps)
+// come from a library-owned stream-ordered memory pool that keeps its memory for the
+// next call (release threshold: never), so that a load or a re-sort does not map and
+// unmap gigabytes of device memory each time (cudaMalloc / cudaFree of that size cost
+// from tens to hundreds of ms, depending on the device's history).
+cudaMemPool_t temp_pool(cudaError_t* e) {
+    static std::mutex mu;
+    static cudaMemPool_t pools[64] = {};
+    int dev = 0;
+    *e = cudaGetDevice(&dev);
+    if (*e != cudaSuccess) return nullptr;
+    if (dev < 0 || dev >= 64) {
+        *e = cudaErrorInvalidDevice;
+        return nullptr;
+    }
+    std::lock_guard<std::mutex> lk(mu);
+    if (!pools[dev]) {
+        cudaMemPoolProps pp{};
+        pp.allocType = cudaMemAllocationTypePinned;
+        pp.location.type = cudaMemLocationTypeDevice;
+        pp.location.id = dev;
+        *e = cudaMemPoolCreate(&pools[dev], &pp);
+        if (*e != cudaSuccess) {
+            pools[dev] = nullptr;
+            return nullptr;
+        }
+        unsigned long long keep = ~0ull;  // the attribute is a 64-bit unsigned
+        *e = cudaMemPoolSetAttribute(pools[dev], cudaMemPoolAttrReleaseThreshold, &keep);
+        if (*e != cudaSuccess) return nullptr;
+    }
+    return pools[dev];
+}
+
+template <typename T>
+cudaError_t talloc(T** p, size_t n, cudaStream_t st) {
+    *p = nullptr;
+    cudaError_t e = cudaSuccess;
+    cudaMemPool_t pool = temp_pool(&e);
+    if (!pool) return e == cudaSuccess ? cudaErrorMemoryAllocation : e;
+    return cudaMallocFromPoolAsync(reinterpret_cast<void**>(p), (n ? n : 1) * sizeof(T), pool, st);
+}
+
+void tfree(void* p, cudaStream_t st) {
+    if (p) cudaFreeAsync(p, st);
+}
+
+void free_parts(PartArrays& A, cudaStream_t st) {
     void* ps[] = {A.cij, A.ox, A.oy, A.ux, A.uy, A.uz, A.gs};
-    for (void* p : ps)
-        if (p) cudaFree(p);
+    for (void* p : ps) tfree(p, st);
     A = PartArrays{};
 }
 
-cudaError_t alloc_parts(PartArrays& A, size_t n, bool with_gs) {
+cudaError_t alloc_parts(PartArrays& A, size_t n, bool with_gs, cudaStream_t st) {
     A = PartArrays{};
-    cudaError_t e = dalloc(&A.cij, n);
-    if (e == cudaSuccess) e = dalloc(&A.ox, n);
-    if (e == cudaSuccess) e = dalloc(&A.oy, n);
-    if (e == cudaSuccess) e = dalloc(&A.ux, n);
-    if (e == cudaSuccess) e = dalloc(&A.uy, n);
-    if (e == cudaSuccess) e = dalloc(&A.uz, n);
-    if (e == cudaSuccess && with_gs) e = dalloc(&A.gs, n);
-    if (e != cudaSuccess) free_parts(A);
+    cudaError_t e = talloc(&A.cij, n, st);
+    if (e == cudaSuccess) e = talloc(&A.ox, n, st);
+    if (e == cudaSuccess) e = talloc(&A.oy, n, st);
+    if (e == cudaSuccess) e = talloc(&A.ux, n, st);
+    if (e == cudaSuccess) e = talloc(&A.uy, n, st);
+    if (e == cudaSuccess) e = talloc(&A.uz, n, st);
+    if (e == cudaSuccess && with_gs) e = talloc(&A.gs, n, st);
+    if (e != cudaSuccess) free_parts(A, st);
     return e;
 }
 
@@ -988,9 +1034,10 @@ cudaError_t alloc_parts(PartArrays& A, size_t n, bool with_gs) {
 struct Staged {
     std::vector<PartArrays> S;
     std::vector<long long> n;
-    explicit Staged(int ngrids) : S(2 * ngrids), n(2 * ngrids, 0) {}
+    cudaStream_t st;
+    Staged(int ngrids, cudaStream_t stream) : S(2 * ngrids), n(2 * ngrids, 0), st(stream) {}
     ~Staged() {
-        for (PartArrays& a : S) free_parts(a);
+        for (PartArrays& a : S) free_parts(a, st);
     }
 };
 
@@ -1056,11 +1103,11 @@ int sort_into_bins(MixedState* m, int g, int par, int s, PartArrays S, long long
     auto A = [&](cudaError_t r) {
         if (e == cudaSuccess) e = r;
     };
-    A(dalloc(&cellcnt, (size_t)G.ncell));
-    A(dalloc(&bincnt, (size_t)ntiles));
-    A(dalloc(&maxrank, 1));
-    A(dalloc(&key, (size_t)n));
-    A(dalloc(&tile, (size_t)n));
+    A(talloc(&cellcnt, (size_t)G.ncell, st));
+    A(talloc(&bincnt, (size_t)ntiles, st));
+    A(talloc(&maxrank, 1, st));
+    A(talloc(&key, (size_t)n, st));
+    A(talloc(&tile, (size_t)n, st));
     if (e == cudaSuccess) {
         A(cudaMemsetAsync(cellcnt, 0, G.ncell * sizeof(unsigned), st));
         A(cudaMemsetAsync(bincnt, 0, ntiles * sizeof(int), st));
@@ -1091,8 +1138,8 @@ int sort_into_bins(MixedState* m, int g, int par, int s, PartArrays S, long long
             const long long words = ((long long)(hmax + 1) * cpt + 31) / 32;
             const long long budget = 64ll << 20;  // bitmap words per group (256 MB)
             const int group = (int)std::max(1ll, std::min<long long>(ntiles, budget / words));
-            A(dalloc(&bits, (size_t)group * words));
-            A(dalloc(&pref, (size_t)group * words));
+            A(talloc(&bits, (size_t)group * words, st));
+            A(talloc(&pref, (size_t)group * words, st));
             for (int t0 = 0; t0 < ntiles && e == cudaSuccess; t0 += group) {
                 const int ntg = std::min(group, ntiles - t0);
                 A(cudaMemsetAsync(bits, 0, (size_t)ntg * words * sizeof(unsigned), st));
@@ -1111,8 +1158,7 @@ int sort_into_bins(MixedState* m, int g, int par, int s, PartArrays S, long long
         }
     }
     void* ps[] = {cellcnt, bincnt, maxrank, key, tile, bits, pref};
-    for (void* p : ps)
-        if (p) cudaFree(p);
+    for (void* p : ps) tfree(p, st);
     if (e != cudaSuccess) {
         err = std::string("bin sort failed: ") + cudaGetErrorString(e);
         return PIC_ECUDA;
@@ -1140,11 +1186,11 @@ int gather_species(MixedState* m, int g, int par, int s, PartArrays& S, long lon
         }
     const long long nb = off[nb_seg];
     const long long no = std::min<long long>((long long)hs.ovf_count[par], m->ovf_cap);
-    MCK(alloc_parts(S, (size_t)(nb + no), false));
+    MCK(alloc_parts(S, (size_t)(nb + no), false, st));
     long long* doff = nullptr;
     unsigned long long* cursor = nullptr;
-    MCK(dalloc(&doff, off.size()));
-    MCK(dalloc(&cursor, 1));
+    MCK(talloc(&doff, off.size(), st));
+    MCK(talloc(&cursor, 1, st));
     MCK(cudaMemcpyAsync(doff, off.data(), off.size() * sizeof(long long), cudaMemcpyHostToDevice, st));
     MCK(cudaMemsetAsync(cursor, 0, sizeof(unsigned long long), st));
     k_gather_bins<<<(unsigned)nb_seg, 256, 0, st>>>(G, s, cnt_of(m, par, g), doff, m->buf[par], S);
@@ -1152,8 +1198,8 @@ int gather_species(MixedState* m, int g, int par, int s, PartArrays& S, long lon
     unsigned long long hcur = 0;
     MCK(cudaMemcpyAsync(&hcur, cursor, sizeof hcur, cudaMemcpyDeviceToHost, st));
     MCK(cudaStreamSynchronize(st));
-    cudaFree(doff);
-    cudaFree(cursor);
+    tfree(doff, st);
+    tfree(cursor, st);
     n = nb + (long long)hcur;
     return PIC_OK;
 }
@@ -1234,7 +1280,7 @@ int rebuild(MixedState* m, std::vector<long long> cap_min, std::vector<long long
     DevStatus hs{};
     if (int rc = read_status(m, hs, st, err)) return rc;
     const int par = (int)hs.parity;
-    Staged A(m->ngrids);
+    Staged A(m->ngrids, st);
     if (int rc = gather_all(m, par, A, st, err)) return rc;
     for (int g = 0; g < m->ngrids; g++) {
         cap_min[g] = std::max(cap_min[g], m->G[g].cap);
@@ -1424,12 +1470,12 @@ int mixed_load(MixedState* m, int g, int s, const double* x, const double* y, co
     double* in = nullptr;
     PartArrays S{};
     unsigned long long* nbad = nullptr;
-    MCK(dalloc(&in, 5 * (size_t)std::max<long long>(n, 1)));
+    MCK(talloc(&in, 5 * (size_t)std::max<long long>(n, 1), st));
     const double* src[5] = {x, y, ux, uy, uz};
     for (int a = 0; a < 5 && n; a++)
         MCK(cudaMemcpyAsync(in + a * n, src[a], n * sizeof(double), cudaMemcpyDefault, st));
-    MCK(alloc_parts(S, (size_t)n, false));
-    MCK(dalloc(&nbad, 1));
+    MCK(alloc_parts(S, (size_t)n, false, st));
+    MCK(talloc(&nbad, 1, st));
     MCK(cudaMemsetAsync(nbad, 0, sizeof(unsigned long long), st));
     if (n)
         k_stage_fp64<<<grid1(n), 256, 0, st>>>(n, in, in + n, in + 2 * n, in + 3 * n, in + 4 * n, m->G[g],
@@ -1437,10 +1483,10 @@ int mixed_load(MixedState* m, int g, int s, const double* x, const double* y, co
     unsigned long long hbad = 0;
     MCK(cudaMemcpyAsync(&hbad, nbad, sizeof hbad, cudaMemcpyDeviceToHost, st));
     MCK(cudaStreamSynchronize(st));
-    cudaFree(in);
-    cudaFree(nbad);
+    tfree(in, st);
+    tfree(nbad, st);
     if (hbad) {
-        free_parts(S);
+        free_parts(S, st);
         err = "non-finite particle position or momentum, or a position outside the walls";
         return PIC_EINVAL;
     }
@@ -1448,10 +1494,10 @@ int mixed_load(MixedState* m, int g, int s, const double* x, const double* y, co
     int rc = sort_into_bins(m, g, par, s, S, n, st, &need, err);  // also zeroes s's outbox counts
     if (rc == PIC_ENOMEM) {
         // a bin would overflow: re-sort everything with larger bins for this simulation
-        Staged A(m->ngrids);
+        Staged A(m->ngrids, st);
         rc = gather_all(m, par, A, st, err);
         if (rc == PIC_OK) {
-            free_parts(A.S[2 * g + s]);
+            free_parts(A.S[2 * g + s], st);
             A.S[2 * g + s] = S;
             A.n[2 * g + s] = n;
             S = PartArrays{};
@@ -1465,7 +1511,7 @@ int mixed_load(MixedState* m, int g, int s, const double* x, const double* y, co
         MCK(cudaStreamSynchronize(st));
         m->n[2 * g + s] = n;
     }
-    free_parts(S);
+    free_parts(S, st);
     return rc;
 }
 
@@ -1559,7 +1605,7 @@ int mixed_rho_momentum(MixedState* m, int g, const double q_s[2], double* rho, d
         }
         if (n && mom) k_momentum_staged<<<304, 256, 0, st>>>(n, S, G.w, mom);
         const cudaError_t e = cudaStreamSynchronize(st);
-        free_parts(S);
+        free_parts(S, st);
         if (e != cudaSuccess) {
             err = std::string("diagnostics: ") + cudaGetErrorString(e);
             return PIC_ECUDA;
@@ -1579,17 +1625,17 @@ int mixed_particles(MixedState* m, int g, int s, double* out, long long n, cudaS
     int rc = gather_species(m, g, (int)hs.parity, s, S, got, st, err);
     if (rc) return rc;
     if (got != n) {
-        free_parts(S);
+        free_parts(S, st);
         err = "particle count mismatch (" + std::to_string(got) + " live, " + std::to_string(n) + " requested)";
         return PIC_ESTATE;
     }
     double* t = nullptr;
-    MCK(dalloc(&t, 5 * (size_t)std::max<long long>(n, 1)));
+    MCK(talloc(&t, 5 * (size_t)std::max<long long>(n, 1), st));
     if (n) k_unstage<<<grid1(n), 256, 0, st>>>(n, m->G[g], S, t);
     MCK(cudaMemcpyAsync(out, t, 5 * n * sizeof(double), cudaMemcpyDefault, st));
     MCK(cudaStreamSynchronize(st));
-    cudaFree(t);
-    free_parts(S);
+    tfree(t, st);
+    free_parts(S, st);
     return PIC_OK;
 }
 
