@@ -255,8 +255,11 @@ PIC_API int pic_set_stream(pic_sim* s, void* cuda_stream);
  * macro-particles: physical positions x in [0, nx dx), y in [0, ny dy) and momenta
  * u = gamma v (units of c). Arrays are FP64, host or device; they are copied. Positions
  * outside the box are wrapped periodically. MIXED32 converts to cell + FP32 offset and
- * FP32 momenta and sorts into tiles. Returns PIC_EINVAL for bad species, n < 0, NULL
- * arrays with n > 0, or non-finite values. */
+ * FP32 momenta and sorts into tiles; its temporaries (about 56 bytes per particle:
+ * the FP64 copy, the staged FP32 form, the sort keys) come from a stream-ordered pool
+ * of the library's that keeps its memory for the next load, re-sort or diagnostic call
+ * of any handle in the process. Returns PIC_EINVAL for bad species, n < 0, NULL arrays
+ * with n > 0, or non-finite values. */
 PIC_API int pic_load_particles(pic_sim* s, int32_t species, const double* x, const double* y,
                        const double* ux, const double* uy, const double* uz, int64_t n);
 
