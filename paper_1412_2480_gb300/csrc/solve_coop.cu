@@ -15,21 +15,22 @@
 // r - alpha q, both unchanged in this pass), so r' goes to the other of two residual
 // buffers and no third barrier is needed.
 //
-// Where the operator's spectrum allows it (every simulation of the batch with
-// T_13(sigma) >= 1e3 below; CFL <= 2.4 at theta = 1/2) the inner solve is instead a
-// Chebyshev iteration, done tile by tile with no grid-wide step at all: A's spectrum
-// lies in [c0 - 2 (cx + cy), c0 + 2 (cx + cy)] (Gershgorin; the interval is exact for
-// periodic boxes and holds with the wall images, which keep A symmetric positive
-// definite), so m steps of the three-term Chebyshev recurrence on that interval reduce
-// every error component by 1/T_m(sigma), sigma = c0 / (2 (cx + cy)), with no inner
-// products. Step k at a cell needs step k-1 at its four neighbours, so a tile of
-// 32 x 32 cells loaded with a halo of m - 1 cells in shared memory computes all m steps
-// by itself (the halo's outer ring goes stale one cell per step and never reaches the
-// interior) and adds its interior's correction to x. m is chosen per refinement from
-// the reduction it needs (as the CG's inner tolerance is), at most 13 (1/T_13(2) =
-// 7e-8 at CFL 1, theta 1/2, near the FP32 floor). A refinement then costs two grid
-// barriers (tiles, residual) instead of two per inner iteration. PIC_CG_INNER keeps the
-// CG.
+// By default the inner solve is instead a Chebyshev iteration, done tile by tile with
+// no grid-wide step at all: A's spectrum lies in [c0 - 2 (cx + cy), c0 + 2 (cx + cy)]
+// (Gershgorin; the interval is exact for periodic boxes and holds with the wall images,
+// which keep A symmetric positive definite), so m steps of the three-term Chebyshev
+// recurrence on that interval reduce every error component by 1/T_m(sigma),
+// sigma = c0 / (2 (cx + cy)) >= 5/4 here, with no inner products. Step k at a cell needs
+// step k-1 at its four neighbours, so a tile of 32 x 64 cells loaded with a halo of 12
+// >= m - 1 cells in shared memory computes all m steps by itself (the halo's outer ring
+// goes stale one cell per step and never reaches the interior) and adds its interior's
+// correction to x. m is chosen per refinement from the reduction it needs (as the CG's
+// inner tolerance is), at most 13 (1/T_13(2) = 7e-8 at CFL 1, theta 1/2, near the FP32
+// floor). During the solve x is held as FP32 pairs and the residual pass runs in pair
+// arithmetic (dword.cuh), so no FP64 instruction is spent inside a refinement; x is
+// joined back to FP64 at the end. A refinement costs two grid barriers (tiles,
+// residual) instead of two per inner iteration. PIC_CG_INNER, or a simulation's
+// cg_rtol below 1e-13, keeps the CG.
 //
 // Work is cut into fixed chunks of 2048 cells of one simulation; a chunk's partial sums
 // are formed in a fixed order and written to its own slot, and every CTA forms each
