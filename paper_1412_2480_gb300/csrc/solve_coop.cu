@@ -568,6 +568,9 @@ __device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wai
 
 // One step on a thread's strip: reads the old e of its neighbours from src, writes the
 // new e to dst (distinct buffers).
+// WALL: this column is a wall column (wl or wr set); the other columns take the form
+// without the image selects.
+template <bool WALL>
 __device__ __forceinline__ void cheb_step(const float* __restrict__ src, float* __restrict__ dst, int base,
                                           float (&e)[kChebRows], float (&d)[kChebRows],
                                           const float (&rs)[kChebRows], float c0f, float cxf, float cyf,
@@ -585,8 +588,10 @@ __device__ __forceinline__ void cheb_step(const float* __restrict__ src, float* 
             wn = src[l + kChebPitch - 1];
             en = src[l + kChebPitch + 1];
         }
-        if (wl) wv = odd ? -ev : ec;  // conductor images: Bx odd and zero on the wall node
-        if (wr) ev = odd ? 0.f : ec;  // x = nx, By and Bz even
+        if (WALL) {
+            if (wl) wv = odd ? -ev : ec;  // conductor images: Bx odd and zero on the wall node
+            if (wr) ev = odd ? 0.f : ec;  // x = nx, By and Bz even
+        }
         const float Ae = fmaf(c0f, ec, -fmaf(cxf, wv + ev, cyf * (up + dn)));
         d[k] = fmaf(ca, d[k], cb * (rs[k] - Ae));
         up = ec;
@@ -660,7 +665,10 @@ __device__ __forceinline__ void cheb_tile(const CoopArgs& a, const GState& s, in
         const float rn = 1.f / (2.f * sig - rho);
         const float ca = rn * rho, cb = 2.f * rn / delta;
         rho = rn;
-        if (act) cheb_step(ea, eb, base, e, d, rs, c0f, cxf, cyf, ca, cb, wl, wr, c == 0);
+        if (act) {
+            if (wl || wr) cheb_step<true>(ea, eb, base, e, d, rs, c0f, cxf, cyf, ca, cb, wl, wr, c == 0);
+            else cheb_step<false>(ea, eb, base, e, d, rs, c0f, cxf, cyf, ca, cb, false, false, false);
+        }
         __syncthreads();
         float* tmp = ea;
         ea = eb;
