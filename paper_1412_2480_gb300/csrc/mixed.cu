@@ -233,12 +233,17 @@ struct WinMem {  // tile window in shared memory; indices are window-local
     __device__ __forceinline__ float ld_ez(int ix, int iy) const { return fw[4 * nw + iy * wx + ix]; }
     __device__ __forceinline__ float ld_bz(int ix, int iy) const { return fw[5 * nw + iy * wx + ix]; }
     // x: the contribution already in window units (the push folds js into its deposit
-    // constants)
+    // constants). A lane whose high word is zero leaves it alone for Jy and Jz (c, a
+    // constant once the deposit is unrolled): below half a window unit, as the transverse
+    // currents of a relativistic beam are, a contribution lives in the low word only, and
+    // an atomic with fewer active lanes takes fewer shared-memory wavefronts (its bank
+    // conflicts are among the active lanes). Jx, large along the beam, skips the test.
+    // Adding zero changes nothing, so the current is the same to the bit.
     __device__ __forceinline__ void add(int c, int ix, int iy, float x) const {
         int hi, lo;
         fixed_split(x, jlb, hi, lo);
         const int k = c * nw + iy * wx + ix;
-        atomicAdd(&jhi[k], hi);
+        if (c == 0 || hi != 0) atomicAdd(&jhi[k], hi);
         atomicAdd(&jlo[k], lo);
     }
 };
