@@ -46,6 +46,7 @@ struct pic_sim {
     float* F32 = nullptr;   // 6 ntot (MIXED32)
     double* Fn = nullptr;   // 6 ntot node-averaged fields (FP64 with PIC_GATHER_NODAL)
     bool any_nodal = false;
+    bool quads = false;  // every simulation's nx is a multiple of 4
     double *x = nullptr, *r = nullptr, *p = nullptr, *q = nullptr;
     double* part = nullptr;
     CgState* cg = nullptr;
@@ -272,6 +273,7 @@ FieldArgs field_args(pic_sim* s, int use_cond, cudaGraphConditionalHandle cond) 
     a.Fn = s->Fn;
     a.any_nodal = s->any_nodal ? 1 : 0;
     a.coop = s->use_coop ? 1 : 0;
+    a.quads = s->quads ? 1 : 0;
     a.x = s->x;
     a.r = s->r;
     a.p = s->p;
@@ -849,6 +851,8 @@ int init_handle(const pic_params* prm, int n, pic_sim** out) {
         A(dalloc(&s->F32, 6 * s->ntot));
     }
     for (int k = 0; k < n; k++) s->any_nodal = s->any_nodal || (prm[k].flags & PIC_GATHER_NODAL);
+    s->quads = true;
+    for (int k = 0; k < n; k++) s->quads = s->quads && prm[k].nx % 4 == 0;
     if (s->any_nodal && prm[0].precision == PIC_FP64) A(dalloc(&s->Fn, 6 * s->ntot));
     if (e != cudaSuccess) {
         s->err = std::string("device allocation failed: ") + cudaGetErrorString(e);

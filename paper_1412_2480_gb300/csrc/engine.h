@@ -22,6 +22,8 @@ struct FieldArgs {
     double* Fn;             // 6 * ntot FP64 node-averaged fields (FP64 with PIC_GATHER_NODAL) or nullptr
     int any_nodal;          // some simulation gathers node-averaged fields
     int coop;               // the cooperative solve follows (it reads the FP32 copy of r only)
+    int quads;              // every simulation's nx is a multiple of 4: the MIXED32 E and B
+                            // updates take quads of cells with vector loads
     double *x, *r, *p, *q;  // 3 * ntot each: dB (solution), residual, direction, A p
     CgState* cg;            // [ngrids]
     double* part;           // 4 * nblk block partials

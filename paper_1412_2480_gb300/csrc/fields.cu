@@ -556,6 +556,143 @@ k_update_E_dw(const GridDev* __restrict__ grids, const int* __restrict__ blk_gri
     }
 }
 
+// Vector access to four consecutive FP64 values (16-byte aligned: cell offsets and nx are
+// multiples of 4 where the quad kernels run).
+__device__ __forceinline__ void ld4d(const double* p, double v[4]) {
+    const double2 a = reinterpret_cast<const double2*>(p)[0];
+    const double2 b = reinterpret_cast<const double2*>(p)[1];
+    v[0] = a.x;
+    v[1] = a.y;
+    v[2] = b.x;
+    v[3] = b.y;
+}
+__device__ __forceinline__ void st4d(double* p, const double v[4]) {
+    reinterpret_cast<double2*>(p)[0] = make_double2(v[0], v[1]);
+    reinterpret_cast<double2*>(p)[1] = make_double2(v[2], v[3]);
+}
+
+// Grid-stride loop over the quads (4 cells along x) of simulation g, for nx a multiple
+// of 4: quad q covers cells 4q .. 4q + 3 of the simulation, in one row.
+#define FOR_QUADS(G, l)                                                                        \
+    for (int q_ = (blockIdx.x - (G).blk_first) * blockDim.x + threadIdx.x; q_ < ((G).ncell >> 2); \
+         q_ += (G).nblk * blockDim.x)                                                          \
+        if (const int l = 4 * q_; true)
+
+// k_update_E_dw on quads of cells, for nx a multiple of 4: the same pair arithmetic per
+// cell (so the same bits), with B, dB, E and J moved as vectors and more loads in flight
+// per thread. The quad's west neighbour is one scalar load.
+__global__ void __launch_bounds__(kFieldThreads)
+k_update_E_dw4(const GridDev* __restrict__ grids, const int* __restrict__ blk_grid, long long ntot,
+               double* __restrict__ F, const long long* __restrict__ J, const double* __restrict__ x,
+               const CgState* __restrict__ cg, const DevStatus* st) {
+    if (st->stop) return;
+    const int g = blk_grid[blockIdx.x];
+    const GridDev& G = grids[g];
+    const DW TH = cg[g].bb > 0.0 ? dwp(G.dw_th) : DW{0.f, 0.f};  // dB = 0 when b = 0
+    const DW FJ = dwp(G.dw_fj), DTX = dwp(G.dw_dtx), DTY = dwp(G.dw_dty);
+    const double* B = F + 3 * ntot;
+    // B + theta dB of component c at the quad starting at k, and at one cell
+    const auto h4 = [&](int c, long long k, DW h[4]) {
+        double bv[4], xv[4];
+        ld4d(B + c * ntot + k, bv);
+        ld4d(x + c * ntot + k, xv);
+#pragma unroll
+        for (int u = 0; u < 4; u++) h[u] = dw_add(dw_from(bv[u]), dw_mul(TH, dw_from(xv[u])));
+    };
+    const auto h1 = [&](int c, long long k) {
+        return dw_add(dw_from(B[c * ntot + k]), dw_mul(TH, dw_from(x[c * ntot + k])));
+    };
+    const auto j4 = [&](int c, long long k, DW j[4]) {
+        const longlong2 v0 = reinterpret_cast<const longlong2*>(J + c * ntot + k)[0];
+        const longlong2 v1 = reinterpret_cast<const longlong2*>(J + c * ntot + k)[1];
+        j[0] = dw_mul(FJ, dw_i64(v0.x));
+        j[1] = dw_mul(FJ, dw_i64(v0.y));
+        j[2] = dw_mul(FJ, dw_i64(v1.x));
+        j[3] = dw_mul(FJ, dw_i64(v1.y));
+    };
+    FOR_QUADS(G, l) {
+        const int jr = l / G.nx, i = l - jr * G.nx;
+        const long long row = G.cell_off + (long long)jr * G.nx;
+        const long long k = row + i;
+        const bool ww = G.walls && i == 0;
+        const long long kw = ww ? k : row + (i == 0 ? G.nx - 1 : i - 1);  // Bz, By even at a wall
+        const long long ks = G.cell_off + (long long)(jr == 0 ? G.ny - 1 : jr - 1) * G.nx + i;
+        DW hz[4], t[4], jj[4];
+        double e[4];
+        h4(2, k, hz);
+        h4(2, ks, t);
+        j4(0, k, jj);
+        ld4d(F + k, e);  // Ex
+#pragma unroll
+        for (int u = 0; u < 4; u++) e[u] = dw_join(dw_add(dw_from(e[u]), dw_sub(dw_mul(DTY, dw_sub(hz[u], t[u])), jj[u])));
+        st4d(F + k, e);
+        {
+            const DW hzw = h1(2, kw);
+            j4(1, k, jj);
+            ld4d(F + ntot + k, e);  // Ey
+#pragma unroll
+            for (int u = 0; u < 4; u++)
+                e[u] = dw_join(dw_add(dw_from(e[u]), dw_neg(dw_add(dw_mul(DTX, dw_sub(hz[u], u == 0 ? hzw : hz[u - 1])), jj[u]))));
+            if (ww) e[0] = 0.0;  // the conductor keeps Ey = Ez = 0 on the wall
+            st4d(F + ntot + k, e);
+        }
+        {
+            DW hy[4];
+            const DW hyw = h1(1, kw);
+            h4(1, k, hy);
+            h4(0, k, hz);  // Bx + theta dBx at the quad
+            h4(0, ks, t);  // and south of it
+            j4(2, k, jj);
+            ld4d(F + 2 * ntot + k, e);  // Ez
+#pragma unroll
+            for (int u = 0; u < 4; u++)
+                e[u] = dw_join(dw_add(dw_from(e[u]), dw_sub(dw_sub(dw_mul(DTX, dw_sub(hy[u], u == 0 ? hyw : hy[u - 1])),
+                                                                 dw_mul(DTY, dw_sub(hz[u], t[u]))),
+                                                          jj[u])));
+            if (ww) e[0] = 0.0;
+            st4d(F + 2 * ntot + k, e);
+        }
+    }
+}
+
+// k_update_B on quads of cells (nx a multiple of 4): B += dB and the FP32 copies.
+__global__ void __launch_bounds__(kFieldThreads)
+k_update_B4(const GridDev* __restrict__ grids, const int* __restrict__ blk_grid, long long ntot,
+            double* __restrict__ F, const double* __restrict__ x, const CgState* __restrict__ cg,
+            const DevStatus* st, float* __restrict__ F32) {
+    if (st->stop) return;
+    const int g = blk_grid[blockIdx.x];
+    const GridDev& G = grids[g];
+    const bool have = cg[g].bb > 0.0;
+    FOR_QUADS(G, l) {
+        const long long k = G.cell_off + l;
+        double bv[3][4], xv[3][4], ev[3][4];
+#pragma unroll
+        for (int a = 0; a < 3; a++) {  // every load first
+            ld4d(F + (3 + a) * ntot + k, bv[a]);
+            if (have) {
+                ld4d(x + a * ntot + k, xv[a]);
+            } else {
+#pragma unroll
+                for (int u = 0; u < 4; u++) xv[a][u] = 0.0;
+            }
+            if (F32) ld4d(F + a * ntot + k, ev[a]);
+        }
+#pragma unroll
+        for (int a = 0; a < 3; a++) {
+#pragma unroll
+            for (int u = 0; u < 4; u++) bv[a][u] += xv[a][u];
+            st4d(F + (3 + a) * ntot + k, bv[a]);
+            if (F32) {  // (float) by bit manipulation off the FP64 pipe
+                reinterpret_cast<float4*>(F32 + (3 + a) * ntot + k)[0] =
+                    make_float4(f32_rn(bv[a][0]), f32_rn(bv[a][1]), f32_rn(bv[a][2]), f32_rn(bv[a][3]));
+                reinterpret_cast<float4*>(F32 + a * ntot + k)[0] =
+                    make_float4(f32_rn(ev[a][0]), f32_rn(ev[a][1]), f32_rn(ev[a][2]), f32_rn(ev[a][3]));
+            }
+        }
+    }
+}
+
 // Explicit FDTD (Eqs. 3-4; PIC_EXPLICIT), with B kept at integer time levels for the
 // gather: x = B^{n+1/2} - B^n = -(c dt/2) curl E^n here, together with the energies of
 // level n; then k_update_E with theta = 1 applies E^{n+1} = E^n + c dt curl B^{n+1/2}
@@ -1060,14 +1197,21 @@ void launch_cg_iteration(const FieldArgs& a, cudaStream_t s) {
 }
 
 void launch_field_update(const FieldArgs& a, cudaStream_t s) {
-    if (a.Jfix)
+    if (a.Jfix && a.quads)
+        k_update_E_dw4<<<a.nblk, kFieldThreads, 0, s>>>(a.grids, a.blk_grid, a.ntot, a.F, a.Jfix, a.x, a.cg,
+                                                        a.st);
+    else if (a.Jfix)
         k_update_E_dw<<<a.nblk, kFieldThreads, 0, s>>>(a.grids, a.blk_grid, a.ntot, a.F, a.Jfix, a.x, a.cg,
                                                        a.st);
     else
         k_update_E<double><<<a.nblk, kFieldThreads, 0, s>>>(a.grids, a.blk_grid, a.ntot, a.F,
                                                             a.J64, a.x, a.cg, a.st);
-    k_update_B<<<a.nblk, kFieldThreads, 0, s>>>(a.grids, a.blk_grid, a.ntot, a.F, a.x, a.cg,
-                                                a.st, a.F32);
+    if (a.Jfix && a.quads)
+        k_update_B4<<<a.nblk, kFieldThreads, 0, s>>>(a.grids, a.blk_grid, a.ntot, a.F, a.x, a.cg, a.st,
+                                                     a.F32);
+    else
+        k_update_B<<<a.nblk, kFieldThreads, 0, s>>>(a.grids, a.blk_grid, a.ntot, a.F, a.x, a.cg,
+                                                    a.st, a.F32);
 }
 
 void launch_nodal(const FieldArgs& a, cudaStream_t s) {
