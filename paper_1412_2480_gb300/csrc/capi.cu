@@ -538,6 +538,7 @@ long long step_kernels(pic_sim* s, bool graph) {
     // step begin and end; field part: explicit half step, update_E, explicit_B, or
     // zero_x, rhs, update_E, update_B (+ the cooperative solve)
     long long k = (s->prm.flags & PIC_EXPLICIT) ? 5 : 6;
+    if (!(s->prm.flags & PIC_EXPLICIT) && s->prm.precision == PIC_MIXED32) k -= 1;  // k_rhs_dw zeroes x itself
     if (s->prm.precision == PIC_MIXED32) {
         k += mixed_step_kernels(s->mixed);
     } else {

@@ -240,7 +240,8 @@ k_rhs(const GridDev* __restrict__ grids, const int* __restrict__ blk_grid, int n
 // read are split by bit manipulation, the current's exact integer differences are
 // converted once each, and b and r are joined back to FP64 with one add. The sums of
 // squares (||b||, ||r||, the energies U_E, U_B) are formed from the pairs' leading
-// words in FP32 per thread and in FP64 over the block.
+// words in FP32 per thread and in FP64 over the block. Where the warm start is off it
+// also zeroes x at its cells (it reads no x then), in place of a k_zero_x launch.
 __device__ __forceinline__ DW dwp(const float (&v)[2]) { return {v[0], v[1]}; }
 __device__ __forceinline__ DW dw_i64(long long d) { return dw_from_i64(d); }
 
@@ -359,6 +360,7 @@ k_rhs_dw(const GridDev* __restrict__ grids, const int* __restrict__ blk_grid, in
             if (r) r[o + c.k] = dw_join(res);  // (the cooperative solve reads only the FP32 copy)
             if (r32) r32[o + c.k] = res.h;
             if (bout) bout[o + c.k] = dw_join(b);
+            if (G.warm != 1) x[o + c.k] = 0.0;  // x0 = 0 (nothing here reads x then)
             v[0] = fmaf(b.h, b.h, v[0]);
             v[3] = fmaf(bc.h, bc.h, v[3]);
         }
@@ -383,8 +385,8 @@ k_rhs_dw(const GridDev* __restrict__ grids, const int* __restrict__ blk_grid, in
     finish_all_grids(ngrids, ngrids, cg, st, cond, use_cond);
 }
 
-// Zero the solution where the warm start is off (x0 = 0). Separate from k_rhs because
-// k_rhs reads x at neighbours when warm starting.
+// Zero the solution where the warm start is off (x0 = 0), for the FP64 path. Separate
+// from k_rhs because k_rhs reads x at neighbours when warm starting.
 __global__ void __launch_bounds__(kFieldThreads)
 k_zero_x(const GridDev* __restrict__ grids, const int* __restrict__ blk_grid, long long ntot,
          double* __restrict__ x) {
@@ -1143,7 +1145,7 @@ void launch_step_end(const FieldArgs& a, cudaStream_t s) {
 }
 
 void launch_rhs(const FieldArgs& a, cudaStream_t s) {
-    k_zero_x<<<a.nblk, kFieldThreads, 0, s>>>(a.grids, a.blk_grid, a.ntot, a.x);
+    if (!a.Jfix) k_zero_x<<<a.nblk, kFieldThreads, 0, s>>>(a.grids, a.blk_grid, a.ntot, a.x);  // (k_rhs_dw zeroes x itself)
     if (a.Jfix)
         k_rhs_dw<<<a.nblk, kFieldThreads, 0, s>>>(a.grids, a.blk_grid, a.ngrids, a.nblk, a.ntot, a.F, a.Jfix, a.x,
                                                   a.coop ? nullptr : a.r, a.cg, a.part, a.done, a.st, a.cond,
